@@ -1,0 +1,109 @@
+"""Pins for the oracle's constructions: Fig. 1 (values printed in the paper), Example 3.3's
+rank, nested hat projections (Corollary 4.3), interpolation on hats (Section 4), and the
+Eckart-Young identity of the SVD construction (Section 5.1)."""
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import construct as C
+from oracle import expansion as E
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(example):
+    vals = np.loadtxt(os.path.join(GOLDEN, f"fig1_spectrum_{example}.txt"), comments="#")
+    return vals[:, 1]
+
+
+@pytest.mark.parametrize("example,count,tol", [(1, 10, 1e-10), (2, 10, 1e-13), (3, 2, 1e-11)])
+def test_fig1_singular_values(example, count, tol):
+    """Fig. 1: the leading singular values of J printed in the paper."""
+    ref = _golden(example)
+    s = C.fig1_singular_values(example)
+    rel = np.abs(s[:count] / ref[:count] - 1.0)
+    assert np.max(rel) < tol, rel
+
+
+def test_fig1_whole_curves_agree_above_rounding():
+    # Every printed value above the rounding floor (1e-13 of the first) is reproduced
+    # to 1e-6 relative, up to an absolute SVD rounding error of 1e-16 of the first.
+    for ex in (1, 2, 3):
+        ref = _golden(ex)
+        s = C.fig1_singular_values(ex)
+        big = ref > 1e-13 * ref[0]
+        err = np.abs(s[big] - ref[big])
+        assert np.all(err <= 1e-6 * ref[big] + 1e-16 * ref[0]), np.max(err / ref[big])
+
+
+def test_example_3_3_has_rank_two():
+    s = C.fig1_singular_values(3)
+    assert s[2] < 1e-13 * s[0]
+    assert s[1] > 0.1 * s[0]
+
+
+def test_projection_error_non_increasing_on_nested_hat_spaces():
+    """Corollary 4.3: nested hat spaces (dyadic m) give a non-increasing L2 error, rate m^-2."""
+    n = 512
+    t = np.arange(n) / n
+    x = t - np.floor(t + 0.5)
+    s = 0.08 + 0.02 * np.cos(2 * np.pi * t)
+    T = np.exp(-(x[:, None] ** 2) / (2 * s[None, :] ** 2))     # T(x_i, y_j), periodic in y
+    errs = [np.linalg.norm(T - C.project_on_hats(T, m)) for m in (4, 8, 16, 32, 64)]
+    assert all(b <= a * (1 + 1e-12) for a, b in zip(errs, errs[1:])), errs
+    slope = np.log(errs[-1] / errs[-2]) / np.log(2)
+    assert -2.3 < slope < -1.7, slope
+    # the projection never loses to interpolation on the same space
+    for m in (8, 32):
+        assert (np.linalg.norm(T - C.project_on_hats(T, m))
+                <= np.linalg.norm(T - C.interpolate_on_hats(T, m)) * (1 + 1e-12))
+
+
+def test_interpolation_is_cardinal_and_exact_at_nodes():
+    n, m = 64, 8
+    B = C.hat_basis(n, m)
+    nodes = np.arange(m) * n // m
+    assert np.array_equal(B[nodes], np.eye(m))
+    assert np.allclose(B.sum(axis=1), 1.0, atol=1e-15)
+    T = np.random.default_rng(0).standard_normal((16, n))
+    Tm = C.interpolate_on_hats(T, m)
+    assert np.allclose(Tm[:, nodes], T[:, nodes], atol=1e-14)
+
+
+def test_svd_truncation_error_is_tail_of_spectrum():
+    T = C.fig1_matrix(1, 128)
+    s = np.linalg.svd(T, compute_uv=False)
+    for m in (1, 3, 6):
+        err = np.linalg.norm(T - C.svd_truncate(T, m))
+        assert abs(err - np.sqrt(np.sum(s[m:] ** 2))) < 1e-12 * s[0]
+
+
+def test_interpolated_expansion_error_decreases_with_m():
+    """H_m built like the 1D workload (hats at k/m, h_k = T(., y_k)) approaches the
+    quadrature of the true kernel K(x, y) = g_sigma(y)(x - y) as m grows (O1 vs O3)."""
+    N = 256
+
+    def kernel(x, y):
+        x = x[..., 0]
+        y = y[..., 0]
+        s = 0.01 + 0.005 * np.sin(2 * np.pi * y)
+        d = x - y
+        d = d - np.floor(d + 0.5)
+        g = 0.0
+        for j in (-1.0, 0.0, 1.0):
+            g = g + np.exp(-((d + j) ** 2) / (2 * s ** 2))
+        return g / (np.sqrt(2 * np.pi) * s)
+
+    eye = np.eye(N)
+    Hq = E.quadrature(kernel, eye, (N,))                       # rows: H e_j
+    errs = []
+    for m in (4, 8, 16, 32, 64):
+        w = synth.hat_windows_1d(N, m).astype(np.float64)
+        h = np.stack([synth.gaussian_psf_1d(N, synth.sigma_1d(k / m)) for k in range(m)])
+        Hm = E.apply(eye, w, h)
+        errs.append(np.linalg.norm(Hq - Hm) / np.linalg.norm(Hq))
+    assert all(b < a for a, b in zip(errs, errs[1:])), errs
+    slope = np.log(errs[-1] / errs[-2]) / np.log(2)
+    assert -2.4 < slope < -1.6, (errs, slope)
