@@ -1,0 +1,417 @@
+"""Benchmark of the convolution-product expansion apply (Eq. 1.4) and its adjoint.
+
+One step = one forward apply y = H_m u and one adjoint apply x = H_m^* u of a
+whole batch of right-hand sides (every kernel of the hot path runs once per
+chunk of the batch).  Metric: applies per second, counting each right-hand
+side of each direction as one apply.
+
+Default workload: 2D periodic 1024 x 1024 float32 images, batch 8, m = 16
+bilinear hat windows on a 4 x 4 node grid, anisotropic rotated Gaussian PSFs
+(sigma_x = 1.5 + y1, sigma_y = 1.5 + y2 px, theta = pi y1 y2), u ~ U[0,1).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl reference]
+
+Under torchrun (N > 1) every rank runs its own batch (weak scaling: the
+right-hand sides are independent, no data-path collective), the step time is
+the max over ranks and rank 0 prints the JSON line.  ``--impl reference``
+times the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "H·u and H*·v applies/sec (fused FP32 path, rel-l2 <= 1e-5 vs FP64 oracle)"
+UNIT = "applies/s"
+SM_COUNT_NOMINAL = 152
+FP32_LANES_PER_SM = 128
+
+
+# ------------------------------------------------------------- algorithmic work
+
+def work_model(pr: synth.Problem, boxes, nb: int) -> dict:
+    """Algorithmic flops and bytes per launch of each kernel kind for a chunk of nb right-hand sides.
+
+    Flops are the nominal FFT counts (5 N log2 N per complex N-point FFT,
+    2.5 N log2 N per real one), 8 per complex multiply-add, 1 per window
+    multiply.  Bytes are the compulsory global traffic of the kernel: its
+    inputs read once and its outputs written once.
+    """
+    if len(pr.shape) == 1:
+        n = pr.shape[0]
+        m = pr.m
+        fft_r = 2.5 * n * math.log2(n)
+        fl = nb * (m * (fft_r + n + 8 * (n // 2 + 1)) + fft_r)
+        by = nb * n * 8 + m * (n // 2 + 1) * 8 + m * n * 4
+        return {"fwd_1d": (fl, by), "adj_1d": (fl, by)}
+    ny, nx = pr.shape
+    m = pr.m
+    nxh = nx // 2
+    rows = sum(b[1] for b in boxes)
+    box_px = sum(b[1] * b[3] for b in boxes)
+    lx, ly = math.log2(nx), math.log2(ny)
+    f_row_r2c = 2.5 * nx * lx
+    f_col = 5.0 * ny * ly
+    hbytes = m * ny * (nxh + 1) * 8
+    zbytes = nb * rows * nxh * 8
+    abytes = nb * ny * nxh * 8
+    ubytes = nb * ny * nx * 4
+    return {
+        "rows_r2c_window": (nb * (rows * f_row_r2c + box_px), ubytes + box_px * 4 + zbytes),
+        "cols_fwd": (nb * ((m + 1) * (nxh + 1) * f_col + m * 8 * ny * (nxh + 1)),
+                     zbytes + hbytes + abytes),
+        "rows_c2r": (nb * ny * f_row_r2c, abytes + ubytes),
+        "rows_r2c": (nb * ny * f_row_r2c, ubytes + abytes),
+        "cols_adj": (nb * ((m + 1) * (nxh + 1) * f_col + m * 8 * ny * (nxh + 1)),
+                     abytes + hbytes + zbytes),
+        "rows_adj": (nb * (rows * f_row_r2c + box_px), zbytes + box_px * 4 + ubytes),
+    }
+
+
+def path_bytes(pr: synth.Problem, boxes) -> float:
+    """Algorithmic HBM bytes of one forward + one adjoint apply of the batch:
+    u and y (x and v) once, hhat once, w on its support box once, per direction."""
+    if len(pr.shape) == 1:
+        n = pr.shape[0]
+        per = 2 * pr.batch * n * 4 + pr.m * (n // 2 + 1) * 8 + pr.m * n * 4
+        return 2 * per
+    ny, nx = pr.shape
+    per = 2 * pr.batch * ny * nx * 4 + pr.m * ny * (nx // 2 + 1) * 8 + sum(b[1] * b[3] for b in boxes) * 4
+    return 2 * per
+
+
+# --------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows: list[list[str]] = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        return False
+
+    def summary(self) -> dict:
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[4 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            with open(path) as f:
+                return json.load(f)
+        except (OSError, ValueError):
+            pass
+    return {}
+
+
+# ----------------------------------------------------------------- CPU oracle
+
+def oracle_sample_rate(pr: synth.Problem, target_s: float = 12.0, seed: int = 5) -> dict:
+    """Time the FP64 oracle (gather form) on sampled outputs of right-hand side 0.
+
+    Returns applies/s extrapolated from the fraction of outputs computed: one
+    forward and one adjoint output per sampled pixel; P sampled outputs of
+    one direction count as one apply.
+    """
+    from oracle import expansion as E
+    P = int(np.prod(pr.shape))
+    rng = np.random.default_rng(seed)
+    u0 = pr.u[:1]
+
+    def run(count):
+        pts = np.stack([rng.integers(0, n, count) for n in pr.shape], axis=-1)
+        t0 = time.perf_counter()
+        for i in range(0, count, 1024):          # bounded gather arrays
+            E.apply_at(u0, pr.w, pr.h, pts[i:i + 1024])
+            E.apply_adjoint_at(u0, pr.w, pr.h, pts[i:i + 1024])
+        return time.perf_counter() - t0
+
+    count = 16
+    dt = run(count)
+    while dt < 0.5 and count < P:
+        count = min(P, count * 4)
+        dt = run(count)
+    total_pts, total_t = 0, 0.0
+    while total_t < target_s and total_pts < P:
+        c = int(min(P, max(count, count * (target_s - total_t) / max(dt, 1e-9) / 2)))
+        t = run(c)
+        total_pts += c
+        total_t += t
+    applies = 2.0 * total_pts / P
+    return {"value": applies / total_t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{total_pts} sampled output pixels x (forward + adjoint) of right-hand side 0 "
+                      f"of {pr.name}, FP64 gather form, {total_t:.1f} s",
+            "seconds": total_t}
+
+
+def reference_arm(args, pr: synth.Problem, rank: int) -> None:
+    if rank != 0:
+        return
+    steps = []
+    for _ in range(args.warmup):
+        oracle_sample_rate(pr, target_s=min(2.0, args.ref_seconds), seed=1)
+    last = None
+    per_step = max(1.0, min(args.ref_seconds, 150.0 / max(1, args.steps)))
+    for s in range(args.steps):
+        last = oracle_sample_rate(pr, target_s=per_step, seed=100 + s)
+        steps.append(last)
+    value = statistics.median([s["value"] for s in steps])
+    ms_per_step = 1000.0 * 2 * pr.batch / value
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": pr.name},
+        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1,
+                         "sample": last["sample"] if last else ""},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------- GPU arm
+
+def gpu_arm(args, pr: synth.Problem, rank: int, world: int) -> None:
+    import torch
+    from paper_1604_04374_gb300 import Plan, build
+    build.build()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    w = torch.from_numpy(pr.w).to(dev)
+    h = torch.from_numpy(pr.h).to(dev)
+    u = torch.from_numpy(pr.u).to(dev)
+    plan = Plan(w, h=h)
+    m, boxes, scratch = plan.info()
+    del w, h
+    y = torch.empty_like(u)
+    x = torch.empty_like(u)
+    B = pr.batch
+    P = int(np.prod(pr.shape))
+    # L2 flush buffer (larger than the 129 MB L2), written between timed steps
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan.apply(u, out=y)
+        plan.apply_adjoint(u, out=x)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    plan.set_timing(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.__enter__()
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if sampler:
+        sampler.__exit__(None, None, None)
+    kern = plan.timing()
+    plan.set_timing(False)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    dev_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([dev_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dev_ms = float(t.item())
+        dist.barrier()
+    launches_per_step = plan.launch_count(False, B) + plan.launch_count(True, B)
+
+    # end to end: pinned host input -> device -> forward + adjoint -> host outputs
+    u_host = torch.from_numpy(pr.u).pin_memory()
+    y_host = torch.empty_like(u_host).pin_memory()
+    x_host = torch.empty_like(u_host).pin_memory()
+    u_dev = torch.empty_like(u)
+
+    def e2e_step():
+        u_dev.copy_(u_host, non_blocking=True)
+        plan.apply(u_dev, out=y)
+        plan.apply_adjoint(u_dev, out=x)
+        y_host.copy_(y, non_blocking=True)
+        x_host.copy_(x, non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    if rank == 0:
+        applies = 2.0 * B * args.steps * world
+        value = applies / (dev_ms / 1000.0)
+        e2e_value = applies / (e2e_ms / 1000.0)
+        clocks = sampler.summary() if sampler else {}
+        sm_max = clocks.get("sm_max_mhz") or 2070.0
+        # FP32 ALU peak from unit counts and clock: SMs x 128 lanes x 2 (FMA) x max SM clock
+        props = torch.cuda.get_device_properties(dev)
+        sms = getattr(props, "multi_processor_count", SM_COUNT_NOMINAL)
+        fp32_peak_tflops = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+        peaks = measured_peaks()
+        hbm_peak = peaks.get("hbm_gbs")
+        hbm_src = "measured" if hbm_peak else "fallback"
+        hbm_peak = hbm_peak or 6800.0
+        chunk = plan_chunk(plan, B)
+        model = work_model(pr, boxes, chunk)
+        kernels = {}
+        for name, (ms, n) in kern.items():
+            fl, by = model.get(name, (0.0, 0.0))
+            avg = ms / n
+            kernels[name] = {"launches": n, "avg_us": 1000.0 * avg, "share": None,
+                             "tflops": fl / (avg / 1000.0) / 1e12 if fl else None,
+                             "gbs": by / (avg / 1000.0) / 1e9 if by else None}
+        tot = sum(v["avg_us"] * v["launches"] for v in kernels.values()) or 1.0
+        for v in kernels.values():
+            v["share"] = v["avg_us"] * v["launches"] / tot
+        dom = max(kernels, key=lambda k: kernels[k]["share"]) if kernels else None
+        roof = None
+        if dom:
+            d = kernels[dom]
+            roof = {"kernel": dom, "bound": "alu", "achieved": d["tflops"], "peak": fp32_peak_tflops,
+                    "unit": "TFLOP/s", "frac": d["tflops"] / fp32_peak_tflops,
+                    "peak_source": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",
+                    "traffic": None, "hbm_gbs": d["gbs"], "hbm_frac_of_" + hbm_src: d["gbs"] / hbm_peak}
+        pbytes = path_bytes(pr, boxes)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": pr.name, "shape": list(pr.shape), "m": pr.m, "batch_per_gpu": B,
+                       "global_batch": B * world, "parallelism": f"replicas x{world}",
+                       "l2": "flushed between timed steps (256 MB write, outside the step events)",
+                       "step": "forward + adjoint apply of the batch"},
+            "roofline": roof,
+            "path_hbm": {"algorithmic_bytes_per_step": pbytes,
+                         "gbs": pbytes * args.steps / (dev_ms / 1000.0) / 1e9,
+                         "peak_gbs": hbm_peak, "peak_source": hbm_src,
+                         "frac": pbytes * args.steps / (dev_ms / 1000.0) / 1e9 / hbm_peak},
+            "kernels": kernels,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": B * P * 4,
+                    "d2h_bytes_per_step": 2 * B * P * 4},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clocks,
+            "wall_s": wall,
+            "scratch_bytes": scratch,
+        }
+        if args.cpu_baseline and world >= 1:
+            line["cpu_baseline"] = {k: v for k, v in oracle_sample_rate(pr, args.ref_seconds).items()
+                                    if k != "seconds"}
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def plan_chunk(plan, batch: int) -> int:
+    """Right-hand sides per launch: batch / launches-per-direction (2D), batch (1D)."""
+    n = plan.launch_count(False, batch)
+    per = 3 if len(plan.shape) == 2 else 1
+    chunks = max(1, n // per)
+    return math.ceil(batch / chunks)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="2d_1024_m16_b8", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--ref-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    pr = synth.workload(args.workload)
+    if args.impl == "reference":
+        reference_arm(args, pr, rank)
+        return
+    if args.warmup < 3:
+        args.warmup = 3
+    gpu_arm(args, pr, rank, world)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,178 @@
+/*
+ * pce.h -- C ABI of the convolution-product expansion library.
+ *
+ * The library applies the convolution-product expansion of order m
+ *
+ *     H_m u = sum_{k=0}^{m-1} h_k * (w_k . u)                 (Eq. 1.4)
+ *
+ * and its adjoint
+ *
+ *     H_m^* v = sum_{k=0}^{m-1} conj(w_k) . (h~_k * v),   h~_k[i] = conj(h_k[-i]),
+ *
+ * on a periodic 1D grid of N points or a periodic 2D grid of Ny x Nx points.
+ * "*" is the periodic discrete convolution of Section 3.5,
+ * v[i] = sum_j u[i - j] h[j] with indices taken modulo the grid size (per
+ * axis), and "." the pointwise product.  The paper asks for products with
+ * both H_m and H_m^* (Introduction; Corollaries 4.2 and 4.4); the adjoint
+ * formula follows from the reality of h_k and w_k.  Every product is
+ * evaluated with the FFT convolution identity of Section 3.5: one forward
+ * FFT of w_k . u per term, a pointwise product with the precomputed spectrum
+ * hhat_k, accumulation of the m products, one inverse FFT.
+ *
+ * Conventions shared by all entry points
+ * --------------------------------------
+ * - Arrays are float32, row-major, contiguous.  A 2D array is [Ny][Nx] with
+ *   x fastest; a batch of right-hand sides is [batch][Ny][Nx] (or [batch][N]).
+ * - h_k is given with its origin at index 0 (offset -d stored at index N-d).
+ * - Spectra are R2C half spectra along x: [Ny][Nx/2+1] complex64 (interleaved
+ *   re, im), forward DFT X[f] = sum_j x[j] exp(-2 i pi j f / N) (the sign of
+ *   the Fourier atoms of Section 2), unnormalised; inverses carry 1/N.
+ * - Sizes are powers of two: N in [16, 8192] in 1D, Ny and Nx in [16, 2048]
+ *   in 2D.  m >= 1.  Other sizes return PCE_ERR_UNSUPPORTED.
+ * - Pointers named "device" must be CUDA device (or managed) memory of the
+ *   current device; a host pointer returns PCE_ERR_INVALID.
+ * - Calls are stream-ordered on `stream` (a cudaStream_t; NULL is the legacy
+ *   default stream).  pce_apply and pce_apply_adjoint never synchronise the
+ *   host and allocate nothing.
+ * - Errors are returned as pce_status, never by aborting; the message of the
+ *   last failure on the calling thread is available from
+ *   pce_last_error_string().  A failed call leaves its outputs unspecified.
+ * - A plan owns scratch buffers that every apply on it uses: two applies of
+ *   the same plan must not run concurrently (e.g. on two streams).
+ */
+#ifndef PCE_H_
+#define PCE_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PCE_OK = 0,
+    PCE_ERR_INVALID = 1,      /* bad argument: null/host pointer, in-place call, bad m or batch */
+    PCE_ERR_UNSUPPORTED = 2,  /* size outside the supported set */
+    PCE_ERR_OOM = 3,          /* a device allocation of the plan failed */
+    PCE_ERR_CUDA = 4,         /* a CUDA runtime call or kernel launch failed */
+    PCE_ERR_TIMEOUT = 5       /* a bounded device-side wait gave up */
+} pce_status;
+
+typedef struct pce_plan* pce_plan_t;
+
+/* Plan flags. */
+#define PCE_FLAG_NONE 0u
+
+/*
+ * pce_plan_create -- precompute everything an operator needs (Eq. 1.4).
+ *
+ *   out    : receives the plan handle (host pointer to a handle).
+ *   ndims  : 1 or 2.
+ *   shape  : host array [ndims]: {N} or {Ny, Nx}.
+ *   m      : number of terms.
+ *   w      : device, [m][shape] float32 windows w_k.
+ *   h      : device, [m][shape] float32 impulse responses h_k, origin at index 0.
+ *   flags  : PCE_FLAG_NONE.
+ *   stream : cudaStream_t used for the set-up work.
+ *
+ * The plan finds the support box of every w_k (the smallest periodic
+ * rectangle holding its nonzeros: rows and columns outside it are skipped by
+ * the forward row pass and the adjoint row pass, Lemma 3.2), keeps a copy of
+ * w_k restricted to that box, computes hhat_k = R2C(h_k) with the library's
+ * own FFT and FP32 twiddles generated in FP64, and allocates its scratch.
+ * w and h are only read during the call and may be freed afterwards.  The
+ * call synchronises `stream` before it returns.
+ */
+pce_status pce_plan_create(pce_plan_t* out, int ndims, const int64_t* shape, int m,
+                           const float* w, const float* h, uint32_t flags, void* stream);
+
+/*
+ * pce_plan_create_from_spectra -- as pce_plan_create, with the impulse
+ * responses given by their half spectra.
+ *
+ *   hhat : device, [m][Ny][Nx/2+1] (2D) or [m][N/2+1] (1D) complex64,
+ *          interleaved float pairs.
+ *
+ * The operator is y = C2R( sum_k hhat_k . R2C(w_k . u) ) with the standard
+ * C2R: the imaginary parts of the DC and Nyquist bins of the last axis are
+ * discarded (in 2D: the DC and Nyquist columns are replaced by their
+ * Hermitian parts along y).  With hhat_k = R2C(h_k) this is the same operator
+ * as pce_plan_create.
+ */
+pce_status pce_plan_create_from_spectra(pce_plan_t* out, int ndims, const int64_t* shape, int m,
+                                        const float* w, const float* hhat, uint32_t flags,
+                                        void* stream);
+
+/*
+ * pce_apply -- y = H_m u for `batch` right-hand sides (Eq. 1.4).
+ *
+ *   u : device, [batch][shape] float32 input.
+ *   y : device, [batch][shape] float32 output; must not overlap u
+ *       (PCE_ERR_INVALID if y == u).
+ *   batch >= 0 (0 is a no-op).
+ */
+pce_status pce_apply(pce_plan_t plan, const float* u, float* y, int64_t batch, void* stream);
+
+/*
+ * pce_apply_adjoint -- x = H_m^* v for `batch` right-hand sides.
+ *
+ *   v : device, [batch][shape] float32 input.
+ *   x : device, [batch][shape] float32 output; must not overlap v.
+ */
+pce_status pce_apply_adjoint(pce_plan_t plan, const float* v, float* x, int64_t batch,
+                             void* stream);
+
+/*
+ * pce_plan_info -- read back plan facts (host pointers, may be NULL):
+ *   m_out, box_out[4*m] = (r0, nr, c0, nc) support box of each w_k
+ *   (1D: r0 = 0, nr = 1), scratch_bytes_out = device scratch the plan holds.
+ */
+pce_status pce_plan_info(pce_plan_t plan, int* m_out, int* box_out, int64_t* scratch_bytes_out);
+
+/*
+ * pce_plan_hhat -- copy the plan's spectra to `hhat` (device,
+ * [m][Ny][Nx/2+1] or [m][N/2+1] complex64), stream-ordered on `stream`.
+ * DC and Nyquist bins come back in the form the plan uses (see
+ * pce_plan_create_from_spectra).
+ */
+pce_status pce_plan_hhat(pce_plan_t plan, float* hhat, void* stream);
+
+/* pce_plan_destroy -- free the plan and all its device memory (synchronises the device). */
+pce_status pce_plan_destroy(pce_plan_t plan);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* pce_last_error_string(void);
+
+/* Number of kernel launches one pce_apply / pce_apply_adjoint of `batch` issues. */
+int64_t pce_launch_count(pce_plan_t plan, int adjoint, int64_t batch);
+
+/*
+ * Per-kernel timing (measurement support; no counterpart in the paper).
+ *
+ * pce_plan_set_timing(plan, 1) makes every later apply on the plan bracket
+ * each kernel it launches with a pair of CUDA events recorded on the apply's
+ * stream; pce_plan_set_timing(plan, 0) stops recording and discards the
+ * events.  pce_plan_timing() waits for the recorded events and returns, for
+ * kernel kind `kind` (PCE_KERNEL_*), the summed device time in milliseconds
+ * and the number of launches since timing was enabled.  Up to 65536 launches
+ * are recorded; later launches run untimed.
+ */
+enum {
+    PCE_KERNEL_ROWS_R2C_WINDOW = 0,  /* forward row pass: window, R2C (2D) */
+    PCE_KERNEL_COLS_FWD = 1,         /* forward column FFT, spectral MAC, inverse column FFT (2D) */
+    PCE_KERNEL_ROWS_C2R = 2,         /* forward row C2R (2D) */
+    PCE_KERNEL_ROWS_R2C = 3,         /* adjoint row R2C of v (2D) */
+    PCE_KERNEL_COLS_ADJ = 4,         /* adjoint column FFT, conj spectra, per-term inverse (2D) */
+    PCE_KERNEL_ROWS_ADJ = 5,         /* adjoint row C2R, window, accumulate (2D) */
+    PCE_KERNEL_FWD_1D = 6,           /* 1D forward, one CTA per right-hand side */
+    PCE_KERNEL_ADJ_1D = 7,           /* 1D adjoint, one CTA per right-hand side */
+    PCE_KERNEL_KINDS = 8
+};
+pce_status pce_plan_set_timing(pce_plan_t plan, int enable);
+pce_status pce_plan_timing(pce_plan_t plan, int kind, double* total_ms, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PCE_H_ */

@@ -1,0 +1,103 @@
+// cols.cu -- instances of the column-pass kernels for NY = 16 .. 2048.
+#include "kernels.cuh"
+#include "launch.h"
+
+namespace pce {
+
+#define PCE_COL_SIZES(X) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048)
+
+int cols_threads(int ny) {
+    switch (ny) {
+#define X(N) case N: return ColCfg<N>::NT;
+        PCE_COL_SIZES(X)
+#undef X
+    }
+    return 0;
+}
+int cols_columns_per_cta(int ny) {
+    switch (ny) {
+#define X(N) case N: return ColCfg<N>::C;
+        PCE_COL_SIZES(X)
+#undef X
+    }
+    return 0;
+}
+int cols_smem(int ny) {
+    switch (ny) {
+#define X(N) case N: return ColCfg<N>::SMEM;
+        PCE_COL_SIZES(X)
+#undef X
+    }
+    return 0;
+}
+
+cudaError_t prepare_cols() {
+    cudaError_t e = cudaSuccess;
+#define X(N)                                                                                   \
+    if (e == cudaSuccess)                                                                      \
+        e = cudaFuncSetAttribute(k_cols_fwd<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                 ColCfg<N>::SMEM);                                             \
+    if (e == cudaSuccess)                                                                      \
+        e = cudaFuncSetAttribute(k_cols_adj<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                 ColCfg<N>::SMEM);                                             \
+    if (e == cudaSuccess)                                                                      \
+        e = cudaFuncSetAttribute(k_cols_spec<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                                 ColCfg<N>::SMEM);
+    PCE_COL_SIZES(X)
+#undef X
+    return e;
+}
+
+cudaError_t launch_cols_fwd(int ny, dim3 grid, cudaStream_t s, const float2* Z, long long z_bstride,
+                            long long z_kstride, const float2* hh, const float2* hN, int m,
+                            const Box* box, int nxh, float2* A, long long a_bstride,
+                            const float2* tw) {
+    switch (ny) {
+#define X(N)                                                                                  \
+    case N:                                                                                   \
+        k_cols_fwd<N><<<grid, ColCfg<N>::NT, ColCfg<N>::SMEM, s>>>(Z, z_bstride, z_kstride, hh, \
+                                                                   hN, m, box, nxh, A,         \
+                                                                   a_bstride, tw);             \
+        break;
+        PCE_COL_SIZES(X)
+#undef X
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cols_adj(int ny, dim3 grid, cudaStream_t s, const float2* V, long long v_bstride,
+                            const float2* hh, const float2* hN, int m, const Box* box, int nxh,
+                            float2* Q, long long q_bstride, long long q_kstride, const float2* tw) {
+    switch (ny) {
+#define X(N)                                                                                  \
+    case N:                                                                                   \
+        k_cols_adj<N><<<grid, ColCfg<N>::NT, ColCfg<N>::SMEM, s>>>(V, v_bstride, hh, hN, m, box, \
+                                                                   nxh, Q, q_bstride,          \
+                                                                   q_kstride, tw);             \
+        break;
+        PCE_COL_SIZES(X)
+#undef X
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cols_spec(int ny, dim3 grid, cudaStream_t s, const float2* S, int nxh,
+                             float2* hh, float2* hN, const float2* tw) {
+    switch (ny) {
+#define X(N)                                                                                   \
+    case N:                                                                                    \
+        k_cols_spec<N><<<grid, ColCfg<N>::NT, ColCfg<N>::SMEM, s>>>(S, nxh, hh, hN, tw);        \
+        break;
+        PCE_COL_SIZES(X)
+#undef X
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace pce

@@ -1,0 +1,687 @@
+// kernels.cuh -- CUDA kernels of the convolution-product expansion (Eq. 1.4).
+//
+// 2D forward  y_b = C2R( sum_k hhat_k . R2C(w_k . u_b) ) / P, three passes:
+//   F1 k_rows_r2c<WINDOW=true>: for every active row of w_k's support box,
+//      w_k . u_b restricted to the box columns, R2C along x (two real rows
+//      per complex FFT), written to the intermediate Z[b][k][row in box].
+//   F2 k_cols_fwd: per column of the half spectrum: for each k the column
+//      FFT of Z_{b,k} (input nonzero only on the box rows), times hhat_k,
+//      accumulated in registers; then one inverse column FFT.
+//   F3 k_rows_c2r: C2R along x, times 1/P.
+// 2D adjoint  x_b = sum_k w_k . C2R( conj(hhat_k) . R2C(v_b) ) / P:
+//   G1 k_rows_r2c<WINDOW=false>, G2 k_cols_adj (column FFT once, then per k
+//   the product with conj(hhat_k) and an inverse column FFT whose output is
+//   kept only on w_k's box rows), G3 k_rows_adj (per row: C2R of each term
+//   whose box holds the row, times w_k, accumulated in registers).
+// 1D (N <= 8192): one CTA per right-hand side does all of it (k_fwd_1d,
+//   k_adj_1d).
+//
+// Half-spectrum layout ("packed"): a real row of NX samples has its R2C
+// spectrum stored as NX/2 complex values, slot 0 holding (X[0], X[NX/2]) (both
+// real) and slot f = X[f] for 0 < f < NX/2.  In 2D the column FFT of slot 0
+// therefore transforms DC + i * Nyquist; the two are separated with
+// A[f] = (Z[f] + conj Z[-f]) / 2, B[f] = (Z[f] - conj Z[-f]) / (2i).
+#pragma once
+
+#include "fft.cuh"
+
+namespace pce {
+
+struct Box {          // periodic support box of w_k and its compacted copy
+    int r0, nr;       // first row, number of rows (rows r0 .. r0+nr-1 mod Ny)
+    int c0, nc;       // first column, number of columns (mod Nx)
+    long long woff;   // offset of the [nr][ldw] box copy in the window buffer
+    int ldw;          // row stride of the box copy
+    int pad_;
+};
+
+__device__ __forceinline__ int wrap(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+// ---------------------------------------------------------------- rows R2C
+// Real rows -> packed half spectra, two rows per complex FFT.
+// WINDOW: item = (k, p) -> box rows 2p, 2p+1 of w_k (global rows r0+2p, r0+2p+1),
+//         multiplied by the box copy of w_k, output rows 2p, 2p+1 of dst[b][k].
+// !WINDOW: item = p -> rows 2p, 2p+1 (< nrows), output rows 2p, 2p+1 of dst[b].
+template <int NX, bool WINDOW>
+__global__ void __launch_bounds__(256)
+k_rows_r2c(const float* __restrict__ src, long long src_bstride, int nrows,
+           const float* __restrict__ wbox, const Box* __restrict__ box,
+           const int2* __restrict__ items, int nitems,
+           float2* __restrict__ dst, long long dst_bstride, long long dst_kstride,
+           const float2* __restrict__ tw) {
+    constexpr int T = NX / kR;
+    constexpr int FPC = 256 / T;
+    constexpr int NXh = NX / 2;
+    __shared__ float2 sbuf[FPC][2][pad_len(NX)];
+    const int slot = threadIdx.x / T;
+    const int j = threadIdx.x - slot * T;
+    const int item = blockIdx.x * FPC + slot;
+    const int b = blockIdx.y;
+    const bool active = item < nitems;
+
+    int k = 0, la, lb, ra, rb;
+    bool va, vb;
+    Box bx;
+    if (WINDOW) {
+        const int2 it = active ? items[item] : make_int2(0, 0);
+        k = it.x;
+        bx = box[k];
+        la = 2 * it.y;
+        lb = la + 1;
+        va = active && la < bx.nr;
+        vb = active && lb < bx.nr;
+        ra = (bx.r0 + la) % nrows;
+        rb = (bx.r0 + lb) % nrows;
+    } else {
+        la = 2 * item;
+        lb = la + 1;
+        va = active && la < nrows;
+        vb = active && lb < nrows;
+        ra = va ? la : 0;
+        rb = vb ? lb : 0;
+    }
+    const float* sa = src + b * src_bstride + (long long)ra * NX;
+    const float* sb = src + b * src_bstride + (long long)rb * NX;
+
+    float2 v[kR];
+#pragma unroll
+    for (int r = 0; r < kR; ++r) {
+        const int n = j + r * T;
+        float xa = 0.f, xb = 0.f;
+        if (WINDOW) {
+            const int cc = wrap(n - bx.c0, NX);
+            if (cc < bx.nc) {
+                const float* wr = wbox + bx.woff;
+                if (va) xa = __ldg(wr + (long long)la * bx.ldw + cc) * __ldg(sa + n);
+                if (vb) xb = __ldg(wr + (long long)lb * bx.ldw + cc) * __ldg(sb + n);
+            }
+        } else {
+            if (va) xa = __ldg(sa + n);
+            if (vb) xb = __ldg(sb + n);
+        }
+        v[r] = make_float2(xa, xb);
+    }
+    fft<NX, false>(v, j, sbuf[slot][0], sbuf[slot][1], tw);
+
+    // split the spectra of the two real rows
+    float2* xs = sbuf[slot][0];
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kR; ++r) xs[padi(j + r * T)] = v[r];
+    __syncthreads();
+    float2* da = dst + b * dst_bstride + k * dst_kstride + (long long)la * NXh;
+    float2* db = dst + b * dst_bstride + k * dst_kstride + (long long)lb * NXh;
+#pragma unroll
+    for (int r = 0; r < kR / 2; ++r) {
+        const int f = j + r * T;
+        float2 A, B;
+        if (f == 0) {
+            A = make_float2(v[0].x, v[kR / 2].x);
+            B = make_float2(v[0].y, v[kR / 2].y);
+        } else {
+            const float2 z = v[r];
+            const float2 zm = xs[padi(NX - f)];
+            A = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
+            B = make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
+        }
+        if (va) da[f] = A;
+        if (vb) db[f] = B;
+    }
+}
+
+// ---------------------------------------------------------------- rows C2R
+// Packed half spectra -> real rows (two rows per complex inverse FFT), times scale.
+// Value at frequency f in [0, NX) of the spectrum whose packed half is p
+// (Hermitian extension; DC and Nyquist are the real parts kept in slot 0).
+template <int NX>
+__device__ __forceinline__ float2 load_half(const float2* p, int f) {
+    constexpr int NXh = NX / 2;
+    if (f == 0) return make_float2(p[0].x, 0.f);
+    if (f == NXh) return make_float2(p[0].y, 0.f);
+    if (f < NXh) return p[f];
+    return cconj(p[NX - f]);
+}
+
+template <int NX>
+__global__ void __launch_bounds__(256)
+k_rows_c2r(const float2* __restrict__ src, long long src_bstride, int nrows,
+           float* __restrict__ dst, long long dst_bstride, float scale,
+           const float2* __restrict__ tw) {
+    constexpr int T = NX / kR;
+    constexpr int FPC = 256 / T;
+    constexpr int NXh = NX / 2;
+    __shared__ float2 sbuf[FPC][2][pad_len(NX)];
+    const int slot = threadIdx.x / T;
+    const int j = threadIdx.x - slot * T;
+    const int p = blockIdx.x * FPC + slot;
+    const int b = blockIdx.y;
+    const int la = 2 * p, lb = la + 1;
+    const bool va = la < nrows, vb = lb < nrows;
+    const float2* pa = src + b * src_bstride + (long long)(va ? la : 0) * NXh;
+    const float2* pb = src + b * src_bstride + (long long)(vb ? lb : 0) * NXh;
+    float2 v[kR];
+#pragma unroll
+    for (int r = 0; r < kR; ++r) {
+        const int f = j + r * T;
+        const float2 xa = va ? load_half<NX>(pa, f) : make_float2(0.f, 0.f);
+        const float2 xb = vb ? load_half<NX>(pb, f) : make_float2(0.f, 0.f);
+        v[r] = make_float2(xa.x - xb.y, xa.y + xb.x);
+    }
+    fft<NX, true>(v, j, sbuf[slot][0], sbuf[slot][1], tw);
+    float* ya = dst + b * dst_bstride + (long long)la * NX;
+    float* yb = dst + b * dst_bstride + (long long)lb * NX;
+#pragma unroll
+    for (int r = 0; r < kR; ++r) {
+        const int n = j + r * T;
+        if (va) ya[n] = v[r].x * scale;
+        if (vb) yb[n] = v[r].y * scale;
+    }
+}
+
+// ------------------------------------------------------ rows C2R, adjoint G3
+// Row pair (2p, 2p+1): x = sum over the terms k whose box holds the row of
+// w_k . C2R(Q_{b,k}[row]), times scale.  Q rows are indexed inside the box.
+template <int NX>
+__global__ void __launch_bounds__(256)
+k_rows_adj(const float2* __restrict__ Q, long long q_bstride, long long q_kstride, int nrows,
+           const float* __restrict__ wbox, const Box* __restrict__ box,
+           const int* __restrict__ kptr, const int* __restrict__ klist,
+           float* __restrict__ dst, long long dst_bstride, float scale,
+           const float2* __restrict__ tw) {
+    constexpr int T = NX / kR;
+    constexpr int FPC = 256 / T;
+    constexpr int NXh = NX / 2;
+    __shared__ float2 sbuf[FPC][2][pad_len(NX)];
+    const int slot = threadIdx.x / T;
+    const int j = threadIdx.x - slot * T;
+    const int npairs = (nrows + 1) / 2;
+    const int p = blockIdx.x * FPC + slot;
+    const int b = blockIdx.y;
+    const bool pv = p < npairs;
+    const int ga = 2 * p, gb = ga + 1;
+
+    // uniform trip count over the CTA's row pairs
+    int nk = 0;
+    for (int s = 0; s < FPC; ++s) {
+        const int ps = blockIdx.x * FPC + s;
+        if (ps < npairs) nk = max(nk, __ldg(&kptr[ps + 1]) - __ldg(&kptr[ps]));
+    }
+    const int kbeg = pv ? __ldg(&kptr[p]) : 0;
+    const int kcnt = pv ? __ldg(&kptr[p + 1]) - kbeg : 0;
+
+    float2 acc[kR];
+#pragma unroll
+    for (int r = 0; r < kR; ++r) acc[r] = make_float2(0.f, 0.f);
+
+    for (int t = 0; t < nk; ++t) {
+        const bool act = t < kcnt;
+        const int k = act ? __ldg(&klist[kbeg + t]) : 0;
+        const Box bx = box[k];
+        const int la = wrap(ga - bx.r0, nrows);
+        const int lb = wrap(gb - bx.r0, nrows);
+        const bool va = act && la < bx.nr;
+        const bool vb = act && gb < nrows && lb < bx.nr;
+        const float2* pa = Q + b * q_bstride + k * q_kstride + (long long)(va ? la : 0) * NXh;
+        const float2* pb = Q + b * q_bstride + k * q_kstride + (long long)(vb ? lb : 0) * NXh;
+        float2 v[kR];
+#pragma unroll
+        for (int r = 0; r < kR; ++r) {
+            const int f = j + r * T;
+            const float2 xa = va ? load_half<NX>(pa, f) : make_float2(0.f, 0.f);
+            const float2 xb = vb ? load_half<NX>(pb, f) : make_float2(0.f, 0.f);
+            v[r] = make_float2(xa.x - xb.y, xa.y + xb.x);
+        }
+        fft<NX, true>(v, j, sbuf[slot][0], sbuf[slot][1], tw);
+        const float* wr = wbox + bx.woff;
+#pragma unroll
+        for (int r = 0; r < kR; ++r) {
+            const int n = j + r * T;
+            const int cc = wrap(n - bx.c0, NX);
+            if (cc < bx.nc) {
+                if (va) acc[r].x = fmaf(__ldg(wr + (long long)la * bx.ldw + cc), v[r].x, acc[r].x);
+                if (vb) acc[r].y = fmaf(__ldg(wr + (long long)lb * bx.ldw + cc), v[r].y, acc[r].y);
+            }
+        }
+    }
+    float* xa = dst + b * dst_bstride + (long long)ga * NX;
+    float* xb = dst + b * dst_bstride + (long long)gb * NX;
+#pragma unroll
+    for (int r = 0; r < kR; ++r) {
+        const int n = j + r * T;
+        if (pv) xa[n] = acc[r].x * scale;
+        if (pv && gb < nrows) xb[n] = acc[r].y * scale;
+    }
+}
+
+// ------------------------------------------------------------ column passes
+template <int NY>
+struct ColCfg {
+    static constexpr int T = NY / kR;
+    static constexpr int C = (4 * T >= 128) ? 4 : 128 / T;   // columns per CTA
+    static constexpr int NT = T * C;                          // threads per CTA
+    static constexpr int SMEM = (C * 2 + 1) * pad_len(NY) * (int)sizeof(float2);
+};
+
+// Separate the column FFT Z of (DC + i Nyquist) at frequency f.
+__device__ __forceinline__ void split_dc_nyq(float2 z, float2 zm, float2& A, float2& B) {
+    A = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
+    B = make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
+}
+
+// F2: forward column pass.  Grid (NXh / C, batch).  hh: [m][NY][NXh] (column
+// 0 = DC column spectrum), hN: [m][NY] (Nyquist column spectrum).
+template <int NY>
+__global__ void __launch_bounds__(ColCfg<NY>::NT)
+k_cols_fwd(const float2* __restrict__ Z, long long z_bstride, long long z_kstride,
+           const float2* __restrict__ hh, const float2* __restrict__ hN, int m,
+           const Box* __restrict__ box, int NXh,
+           float2* __restrict__ A, long long a_bstride, const float2* __restrict__ tw) {
+    using CC = ColCfg<NY>;
+    constexpr int T = CC::T;
+    constexpr int C = CC::C;
+    extern __shared__ float2 smem[];
+    const int c = threadIdx.x % C;
+    const int j = threadIdx.x / C;
+    float2* b0 = smem + (2 * c) * pad_len(NY);
+    float2* b1 = b0 + pad_len(NY);
+    float2* xbuf = smem + 2 * C * pad_len(NY);
+    const int col = blockIdx.x * C + c;
+    const bool cv = col < NXh;
+    const int b = blockIdx.y;
+    const bool tile0 = blockIdx.x == 0;
+    const bool dcn = tile0 && c == 0;
+
+    float2 acc[kR];
+#pragma unroll
+    for (int r = 0; r < kR; ++r) acc[r] = make_float2(0.f, 0.f);
+
+    for (int k = 0; k < m; ++k) {
+        const Box bx = box[k];
+        if (bx.nr == 0) continue;
+        const float2* Zk = Z + b * z_bstride + k * z_kstride;
+        float2 v[kR];
+#pragma unroll
+        for (int r = 0; r < kR; ++r) {
+            const int i = wrap(j + r * T - bx.r0, NY);
+            v[r] = (cv && i < bx.nr) ? __ldg(&Zk[(long long)i * NXh + col]) : make_float2(0.f, 0.f);
+        }
+        fft<NY, false>(v, j, b0, b1, tw);
+        const float2* hk = hh + (long long)k * NY * NXh;
+        if (tile0) {
+            if (dcn) {
+#pragma unroll
+                for (int r = 0; r < kR; ++r) xbuf[padi(j + r * T)] = v[r];
+            }
+            __syncthreads();
+        }
+        if (dcn) {
+#pragma unroll
+            for (int r = 0; r < kR; ++r) {
+                const int f = j + r * T;
+                float2 a, bb;
+                split_dc_nyq(v[r], xbuf[padi((NY - f) & (NY - 1))], a, bb);
+                acc[r] = cfma(__ldg(&hk[(long long)f * NXh]), a, acc[r]);
+                const float2 t = cmul(__ldg(&hN[(long long)k * NY + f]), bb);
+                acc[r].x -= t.y;
+                acc[r].y += t.x;
+            }
+        } else if (cv) {
+#pragma unroll
+            for (int r = 0; r < kR; ++r) {
+                const int f = j + r * T;
+                acc[r] = cfma(__ldg(&hk[(long long)f * NXh + col]), v[r], acc[r]);
+            }
+        }
+    }
+    fft<NY, true>(acc, j, b0, b1, tw);
+    if (cv) {
+        float2* Ab = A + b * a_bstride;
+#pragma unroll
+        for (int r = 0; r < kR; ++r) Ab[(long long)(j + r * T) * NXh + col] = acc[r];
+    }
+}
+
+// G1b + G2: adjoint column pass.  Column FFT of V once; per k the product
+// with conj(hhat_k), an inverse column FFT, and a store of the box rows only.
+template <int NY>
+__global__ void __launch_bounds__(ColCfg<NY>::NT)
+k_cols_adj(const float2* __restrict__ V, long long v_bstride,
+           const float2* __restrict__ hh, const float2* __restrict__ hN, int m,
+           const Box* __restrict__ box, int NXh,
+           float2* __restrict__ Q, long long q_bstride, long long q_kstride,
+           const float2* __restrict__ tw) {
+    using CC = ColCfg<NY>;
+    constexpr int T = CC::T;
+    constexpr int C = CC::C;
+    extern __shared__ float2 smem[];
+    const int c = threadIdx.x % C;
+    const int j = threadIdx.x / C;
+    float2* b0 = smem + (2 * c) * pad_len(NY);
+    float2* b1 = b0 + pad_len(NY);
+    float2* xbuf = smem + 2 * C * pad_len(NY);
+    const int col = blockIdx.x * C + c;
+    const bool cv = col < NXh;
+    const int b = blockIdx.y;
+    const bool tile0 = blockIdx.x == 0;
+    const bool dcn = tile0 && c == 0;
+
+    float2 vv[kR];
+    const float2* Vb = V + b * v_bstride;
+#pragma unroll
+    for (int r = 0; r < kR; ++r)
+        vv[r] = cv ? __ldg(&Vb[(long long)(j + r * T) * NXh + col]) : make_float2(0.f, 0.f);
+    fft<NY, false>(vv, j, b0, b1, tw);
+    if (tile0) {
+        if (dcn) {
+#pragma unroll
+            for (int r = 0; r < kR; ++r) xbuf[padi(j + r * T)] = vv[r];
+        }
+        __syncthreads();
+    }
+    for (int k = 0; k < m; ++k) {
+        const Box bx = box[k];
+        if (bx.nr == 0) continue;
+        const float2* hk = hh + (long long)k * NY * NXh;
+        float2 p[kR];
+#pragma unroll
+        for (int r = 0; r < kR; ++r) {
+            const int f = j + r * T;
+            if (dcn) {
+                float2 a, bb;
+                split_dc_nyq(vv[r], xbuf[padi((NY - f) & (NY - 1))], a, bb);
+                float2 t = cmulc(a, __ldg(&hk[(long long)f * NXh]));
+                const float2 s = cmulc(bb, __ldg(&hN[(long long)k * NY + f]));
+                t.x -= s.y;
+                t.y += s.x;
+                p[r] = t;
+            } else {
+                p[r] = cv ? cmulc(vv[r], __ldg(&hk[(long long)f * NXh + col])) : make_float2(0.f, 0.f);
+            }
+        }
+        fft<NY, true>(p, j, b0, b1, tw);
+        if (cv) {
+            float2* Qk = Q + b * q_bstride + k * q_kstride;
+#pragma unroll
+            for (int r = 0; r < kR; ++r) {
+                const int i = wrap(j + r * T - bx.r0, NY);
+                if (i < bx.nr) Qk[(long long)i * NXh + col] = p[r];
+            }
+        }
+    }
+}
+
+// Plan: column FFT of the row spectra of h_k -> hh (column 0 = DC column
+// spectrum) and hN (Nyquist column spectrum).  Grid (NXh / C, m).
+template <int NY>
+__global__ void __launch_bounds__(ColCfg<NY>::NT)
+k_cols_spec(const float2* __restrict__ S, int NXh, float2* __restrict__ hh,
+            float2* __restrict__ hN, const float2* __restrict__ tw) {
+    using CC = ColCfg<NY>;
+    constexpr int T = CC::T;
+    constexpr int C = CC::C;
+    extern __shared__ float2 smem[];
+    const int c = threadIdx.x % C;
+    const int j = threadIdx.x / C;
+    float2* b0 = smem + (2 * c) * pad_len(NY);
+    float2* b1 = b0 + pad_len(NY);
+    float2* xbuf = smem + 2 * C * pad_len(NY);
+    const int col = blockIdx.x * C + c;
+    const bool cv = col < NXh;
+    const int k = blockIdx.y;
+    const bool tile0 = blockIdx.x == 0;
+    const bool dcn = tile0 && c == 0;
+    const float2* Sk = S + (long long)k * NY * NXh;
+    float2 v[kR];
+#pragma unroll
+    for (int r = 0; r < kR; ++r)
+        v[r] = cv ? __ldg(&Sk[(long long)(j + r * T) * NXh + col]) : make_float2(0.f, 0.f);
+    fft<NY, false>(v, j, b0, b1, tw);
+    if (tile0) {
+        if (dcn) {
+#pragma unroll
+            for (int r = 0; r < kR; ++r) xbuf[padi(j + r * T)] = v[r];
+        }
+        __syncthreads();
+    }
+    float2* hk = hh + (long long)k * NY * NXh;
+#pragma unroll
+    for (int r = 0; r < kR; ++r) {
+        const int f = j + r * T;
+        if (dcn) {
+            float2 a, bb;
+            split_dc_nyq(v[r], xbuf[padi((NY - f) & (NY - 1))], a, bb);
+            hk[(long long)f * NXh] = a;
+            hN[(long long)k * NY + f] = bb;
+        } else if (cv) {
+            hk[(long long)f * NXh + col] = v[r];
+        }
+    }
+}
+
+// ------------------------------------------------------------------- 1D
+template <int N>
+struct Cfg1d {
+    static constexpr int T = N / kR;
+    static constexpr int G = (256 / T) > 0 ? (256 / T) : 1;   // FFT slots per CTA
+    static constexpr int NT = T * G;
+    static constexpr int SMEM = G * 2 * pad_len(N) * (int)sizeof(float2);
+};
+
+// y_b = (1/N) C2R( sum_k hhat_k . R2C(w_k . u_b) ).  One CTA per b; each
+// slot takes pairs of terms (w_k u + i w_{k+1} u in one complex FFT) and
+// accumulates the half spectrum in registers; the slots' sums are reduced in
+// shared memory and one inverse FFT follows.  hp: [m][N/2] packed spectra.
+template <int N>
+__global__ void __launch_bounds__(Cfg1d<N>::NT)
+k_fwd_1d(const float* __restrict__ u, const float* __restrict__ w,
+         const float2* __restrict__ hp, int m, float* __restrict__ y, float scale,
+         const float2* __restrict__ tw) {
+    using CF = Cfg1d<N>;
+    constexpr int T = CF::T;
+    constexpr int G = CF::G;
+    constexpr int Nh = N / 2;
+    extern __shared__ float2 smem[];
+    const int slot = threadIdx.x / T;
+    const int j = threadIdx.x - slot * T;
+    float2* b0 = smem + (2 * slot) * pad_len(N);
+    float2* b1 = b0 + pad_len(N);
+    const int b = blockIdx.x;
+    const float* ub = u + (long long)b * N;
+    float ureg[kR];
+#pragma unroll
+    for (int r = 0; r < kR; ++r) ureg[r] = __ldg(ub + j + r * T);
+    float2 acc[kR / 2];
+#pragma unroll
+    for (int r = 0; r < kR / 2; ++r) acc[r] = make_float2(0.f, 0.f);
+
+    const int npairs = (m + 1) / 2;
+    const int iters = (npairs + G - 1) / G;
+    for (int it = 0; it < iters; ++it) {
+        const int pr = it * G + slot;
+        const bool a0 = pr < npairs;
+        const int k0 = 2 * pr, k1 = k0 + 1;
+        const bool a1 = a0 && k1 < m;
+        float2 v[kR];
+#pragma unroll
+        for (int r = 0; r < kR; ++r) {
+            const int n = j + r * T;
+            v[r] = make_float2(a0 ? __ldg(w + (long long)k0 * N + n) * ureg[r] : 0.f,
+                               a1 ? __ldg(w + (long long)k1 * N + n) * ureg[r] : 0.f);
+        }
+        fft<N, false>(v, j, b0, b1, tw);
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kR; ++r) b0[padi(j + r * T)] = v[r];
+        __syncthreads();
+        if (a0) {
+            const float2* h0 = hp + (long long)k0 * Nh;
+            const float2* h1 = hp + (long long)(a1 ? k1 : k0) * Nh;
+#pragma unroll
+            for (int r = 0; r < kR / 2; ++r) {
+                const int f = j + r * T;
+                if (f == 0) {
+                    // the DC and Nyquist terms are real: acc[0] of thread 0 packs (DC, Nyquist)
+                    const float2 p0 = __ldg(&h0[0]);
+                    acc[0].x = fmaf(p0.x, v[0].x, acc[0].x);
+                    acc[0].y = fmaf(p0.y, v[kR / 2].x, acc[0].y);
+                    if (a1) {
+                        const float2 p1 = __ldg(&h1[0]);
+                        acc[0].x = fmaf(p1.x, v[0].y, acc[0].x);
+                        acc[0].y = fmaf(p1.y, v[kR / 2].y, acc[0].y);
+                    }
+                } else {
+                    float2 A, B;
+                    split_dc_nyq(v[r], b0[padi(N - f)], A, B);
+                    acc[r] = cfma(__ldg(&h0[f]), A, acc[r]);
+                    if (a1) acc[r] = cfma(__ldg(&h1[f]), B, acc[r]);
+                }
+            }
+        }
+    }
+    // reduce over slots into slot 0's second buffer (packed half spectrum)
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kR / 2; ++r) b0[j + r * T] = acc[r];
+    __syncthreads();
+    float2* red = smem + pad_len(N);
+    if (slot == 0) {
+#pragma unroll
+        for (int r = 0; r < kR / 2; ++r) {
+            float2 s = smem[j + r * T];
+            for (int g = 1; g < G; ++g) s = cadd(s, smem[(2 * g) * pad_len(N) + j + r * T]);
+            red[j + r * T] = s;
+        }
+    }
+    __syncthreads();
+    float2 v[kR];
+#pragma unroll
+    for (int r = 0; r < kR; ++r)
+        v[r] = (slot == 0) ? load_half<N>(red, j + r * T) : make_float2(0.f, 0.f);
+    fft<N, true>(v, j, b0, b1, tw);
+    if (slot == 0) {
+        float* yb = y + (long long)b * N;
+#pragma unroll
+        for (int r = 0; r < kR; ++r) yb[j + r * T] = v[r].x * scale;
+    }
+}
+
+// x_b = (1/N) sum_k w_k . IFFT( conj(hhat_k) . FFT(v_b) ).  One CTA per b;
+// every slot forms FFT(v_b) and takes pairs of terms: the two inverse FFTs
+// of a pair are real, so they share one complex inverse FFT.
+template <int N>
+__global__ void __launch_bounds__(Cfg1d<N>::NT)
+k_adj_1d(const float* __restrict__ vin, const float* __restrict__ w,
+         const float2* __restrict__ hp, int m, float* __restrict__ x, float scale,
+         const float2* __restrict__ tw) {
+    using CF = Cfg1d<N>;
+    constexpr int T = CF::T;
+    constexpr int G = CF::G;
+    constexpr int Nh = N / 2;
+    extern __shared__ float2 smem[];
+    const int slot = threadIdx.x / T;
+    const int j = threadIdx.x - slot * T;
+    float2* b0 = smem + (2 * slot) * pad_len(N);
+    float2* b1 = b0 + pad_len(N);
+    const int b = blockIdx.x;
+    const float* vb = vin + (long long)b * N;
+    float2 V[kR];
+#pragma unroll
+    for (int r = 0; r < kR; ++r) V[r] = make_float2(__ldg(vb + j + r * T), 0.f);
+    fft<N, false>(V, j, b0, b1, tw);
+    float ax[kR];
+#pragma unroll
+    for (int r = 0; r < kR; ++r) ax[r] = 0.f;
+
+    const int npairs = (m + 1) / 2;
+    const int iters = (npairs + G - 1) / G;
+    for (int it = 0; it < iters; ++it) {
+        const int pr = it * G + slot;
+        const bool a0 = pr < npairs;
+        const int k0 = 2 * pr, k1 = k0 + 1;
+        const bool a1 = a0 && k1 < m;
+        const float2* h0 = hp + (long long)(a0 ? k0 : 0) * Nh;
+        const float2* h1 = hp + (long long)(a1 ? k1 : 0) * Nh;
+        float2 p[kR];
+#pragma unroll
+        for (int r = 0; r < kR; ++r) {
+            const int f = j + r * T;
+            float2 t = make_float2(0.f, 0.f);
+            if (a0) t = cmulc(V[r], load_half<N>(h0, f));
+            if (a1) {
+                const float2 s = cmulc(V[r], load_half<N>(h1, f));
+                t.x -= s.y;
+                t.y += s.x;
+            }
+            p[r] = t;
+        }
+        fft<N, true>(p, j, b0, b1, tw);
+#pragma unroll
+        for (int r = 0; r < kR; ++r) {
+            const int n = j + r * T;
+            if (a0) ax[r] = fmaf(__ldg(w + (long long)k0 * N + n), p[r].x, ax[r]);
+            if (a1) ax[r] = fmaf(__ldg(w + (long long)k1 * N + n), p[r].y, ax[r]);
+        }
+    }
+    __syncthreads();
+    float* fb = reinterpret_cast<float*>(b0);
+#pragma unroll
+    for (int r = 0; r < kR; ++r) fb[j + r * T] = ax[r];
+    __syncthreads();
+    if (slot == 0) {
+        float* xb = x + (long long)b * N;
+#pragma unroll
+        for (int r = 0; r < kR; ++r) {
+            float s = fb[j + r * T];
+            for (int g = 1; g < G; ++g)
+                s += reinterpret_cast<const float*>(smem + (2 * g) * pad_len(N))[j + r * T];
+            xb[j + r * T] = s * scale;
+        }
+    }
+}
+
+// Plan (1D): packed R2C spectra of the impulse responses, two per complex
+// FFT (h_k + i h_{k+1}).  Grid: ceil(ceil(m/2) / G).
+template <int N>
+__global__ void __launch_bounds__(Cfg1d<N>::NT)
+k_spec_1d(const float* __restrict__ h, int m, float2* __restrict__ hp,
+          const float2* __restrict__ tw) {
+    using CF = Cfg1d<N>;
+    constexpr int T = CF::T;
+    constexpr int G = CF::G;
+    constexpr int Nh = N / 2;
+    extern __shared__ float2 smem[];
+    const int slot = threadIdx.x / T;
+    const int j = threadIdx.x - slot * T;
+    float2* b0 = smem + (2 * slot) * pad_len(N);
+    float2* b1 = b0 + pad_len(N);
+    const int pr = blockIdx.x * G + slot;
+    const int k0 = 2 * pr, k1 = k0 + 1;
+    const bool a0 = k0 < m, a1 = k1 < m;
+    float2 v[kR];
+#pragma unroll
+    for (int r = 0; r < kR; ++r) {
+        const int n = j + r * T;
+        v[r] = make_float2(a0 ? __ldg(h + (long long)k0 * N + n) : 0.f,
+                           a1 ? __ldg(h + (long long)k1 * N + n) : 0.f);
+    }
+    fft<N, false>(v, j, b0, b1, tw);
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kR; ++r) b0[padi(j + r * T)] = v[r];
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kR / 2; ++r) {
+        const int f = j + r * T;
+        float2 A, B;
+        if (f == 0) {
+            A = make_float2(v[0].x, v[kR / 2].x);
+            B = make_float2(v[0].y, v[kR / 2].y);
+        } else {
+            split_dc_nyq(v[r], b0[padi(N - f)], A, B);
+        }
+        if (a0) hp[(long long)k0 * Nh + f] = A;
+        if (a1) hp[(long long)k1 * Nh + f] = B;
+    }
+}
+
+}  // namespace pce

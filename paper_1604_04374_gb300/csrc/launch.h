@@ -1,0 +1,61 @@
+// launch.h -- size-dispatching launchers for the kernels in kernels.cuh.
+// Every launcher picks the template instance for its transform length and
+// returns the launch status (cudaGetLastError after the launch).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace pce {
+
+struct Box;
+
+// Shared-memory bytes and threads of the column kernels for a column length.
+int cols_threads(int ny);
+int cols_columns_per_cta(int ny);
+int cols_smem(int ny);
+// Rows handled per CTA of the row kernels (two rows per FFT).
+int rows_pairs_per_cta(int nx);
+// 1D kernels.
+int fft1d_threads(int n);
+int fft1d_smem(int n);
+
+// Raise the dynamic shared-memory limit of every kernel that needs it (once per device).
+cudaError_t prepare_kernels();
+
+cudaError_t launch_rows_r2c(int nx, bool window, dim3 grid, cudaStream_t s,
+                            const float* src, long long src_bstride, int nrows,
+                            const float* wbox, const Box* box, const int2* items, int nitems,
+                            float2* dst, long long dst_bstride, long long dst_kstride,
+                            const float2* tw);
+
+cudaError_t launch_rows_c2r(int nx, dim3 grid, cudaStream_t s, const float2* src,
+                            long long src_bstride, int nrows, float* dst, long long dst_bstride,
+                            float scale, const float2* tw);
+
+cudaError_t launch_rows_adj(int nx, dim3 grid, cudaStream_t s, const float2* Q, long long q_bstride,
+                            long long q_kstride, int nrows, const float* wbox, const Box* box,
+                            const int* kptr, const int* klist, float* dst, long long dst_bstride,
+                            float scale, const float2* tw);
+
+cudaError_t launch_cols_fwd(int ny, dim3 grid, cudaStream_t s, const float2* Z, long long z_bstride,
+                            long long z_kstride, const float2* hh, const float2* hN, int m,
+                            const Box* box, int nxh, float2* A, long long a_bstride,
+                            const float2* tw);
+
+cudaError_t launch_cols_adj(int ny, dim3 grid, cudaStream_t s, const float2* V, long long v_bstride,
+                            const float2* hh, const float2* hN, int m, const Box* box, int nxh,
+                            float2* Q, long long q_bstride, long long q_kstride, const float2* tw);
+
+cudaError_t launch_cols_spec(int ny, dim3 grid, cudaStream_t s, const float2* S, int nxh,
+                             float2* hh, float2* hN, const float2* tw);
+
+cudaError_t launch_fwd_1d(int n, int batch, cudaStream_t s, const float* u, const float* w,
+                          const float2* hp, int m, float* y, float scale, const float2* tw);
+
+cudaError_t launch_adj_1d(int n, int batch, cudaStream_t s, const float* v, const float* w,
+                          const float2* hp, int m, float* x, float scale, const float2* tw);
+
+cudaError_t launch_spec_1d(int n, int m, cudaStream_t s, const float* h, float2* hp,
+                           const float2* tw);
+
+}  // namespace pce

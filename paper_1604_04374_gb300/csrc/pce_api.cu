@@ -1,0 +1,711 @@
+// pce_api.cu -- plan builder and C ABI (include/pce.h).
+//
+// The plan holds, on the device: the support box copy of every window w_k,
+// the spectra hhat_k in the kernels' layout, FP32 twiddle tables generated in
+// FP64, the work lists of the row passes, and the scratch intermediates of
+// the 2D passes (Z/Q: per-term row spectra restricted to the box rows; A/V:
+// per-right-hand-side spectra).  Applies only launch kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "launch.h"
+#include "pce.h"
+
+using pce::Box;
+
+namespace {
+
+thread_local std::string g_err;
+
+pce_status fail(pce_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define PCE_CK(call)                                                                       \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail(e_ == cudaErrorMemoryAllocation ? PCE_ERR_OOM : PCE_ERR_CUDA,      \
+                        "%s failed: %s", #call, cudaGetErrorString(e_));                   \
+    } while (0)
+
+constexpr long long kScratchBudget = 1ll << 30;   // bytes of 2D scratch a plan aims for
+constexpr int kMaxChunk = 64;
+
+bool is_pow2(long long n) { return n > 0 && (n & (n - 1)) == 0; }
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// ------------------------------------------------------------ plan kernels
+// Twiddle table of an N-point FFT (layout of pce::FftPlan), from FP64 sincospi.
+__global__ void k_twiddles(float2* tw, int n) {
+    const int L = pce::ilog2(n);
+    const int nfull = L / 3, rem = L % 3;
+    const int nst = nfull + (rem ? 1 : 0);
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    int off = 0;
+    for (int s = 1; s < nst; ++s) {
+        const int rs = s < nfull ? 8 : (1 << rem);
+        const int ns = 1 << (3 * s);
+        const int cnt = (rs - 1) * ns;
+        if (idx < off + cnt) {
+            const int e = idx - off;
+            const int q = e / ns + 1;
+            const int k = e % ns;
+            const long long len = (long long)ns * rs;
+            double sn, cs;
+            sincospi(-2.0 * (double)((long long)q * k) / (double)len, &sn, &cs);
+            tw[idx] = make_float2((float)cs, (float)sn);
+            return;
+        }
+        off += cnt;
+    }
+}
+
+int twiddle_len(int n) {
+    const int L = pce::ilog2(n);
+    const int nfull = L / 3, rem = L % 3;
+    const int nst = nfull + (rem ? 1 : 0);
+    int len = 0;
+    for (int s = 1; s < nst; ++s) len += ((s < nfull ? 8 : (1 << rem)) - 1) * (1 << (3 * s));
+    return len;
+}
+
+// Row/column nonzero flags of every window.
+__global__ void k_support(const float* __restrict__ w, int m, int ny, int nx,
+                          unsigned char* rowf, unsigned char* colf) {
+    const long long total = (long long)m * ny * nx;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (w[i] != 0.f) {
+            const int c = (int)(i % nx);
+            const long long kr = i / nx;
+            const int r = (int)(kr % ny);
+            const int k = (int)(kr / ny);
+            rowf[(long long)k * ny + r] = 1;
+            colf[(long long)k * nx + c] = 1;
+        }
+    }
+}
+
+// Box copy of w_k: wbox[woff + i*ldw + cc] = w_k[(r0+i) % ny][(c0+cc) % nx] (0 beyond nc).
+__global__ void k_wbox(const float* __restrict__ w, int ny, int nx, Box bx, float* wbox) {
+    const long long total = (long long)bx.nr * bx.ldw;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int cc = (int)(i % bx.ldw);
+        const int r = (int)(i / bx.ldw);
+        float v = 0.f;
+        if (cc < bx.nc) v = w[(long long)((bx.r0 + r) % ny) * nx + (bx.c0 + cc) % nx];
+        wbox[bx.woff + i] = v;
+    }
+}
+
+// hhat [m][ny][nxh+1] (natural) -> hh [m][ny][nxh] (column 0 = Hermitian part
+// of the DC column), hN [m][ny] (Hermitian part of the Nyquist column).
+__global__ void k_from_half2d(const float2* __restrict__ hhat, int m, int ny, int nxh,
+                              float2* hh, float2* hN) {
+    const long long total = (long long)m * ny * (nxh + 1);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % (nxh + 1));
+        const long long kf = i / (nxh + 1);
+        const int f = (int)(kf % ny);
+        const int k = (int)(kf / ny);
+        const float2 a = hhat[i];
+        if (c > 0 && c < nxh) {
+            hh[((long long)k * ny + f) * nxh + c] = a;
+        } else {
+            const int fm = (ny - f) & (ny - 1);
+            const float2 b = hhat[((long long)k * ny + fm) * (nxh + 1) + c];
+            const float2 hs = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
+            if (c == 0) hh[((long long)k * ny + f) * nxh] = hs;
+            else hN[(long long)k * ny + f] = hs;
+        }
+    }
+}
+
+__global__ void k_to_half2d(const float2* __restrict__ hh, const float2* __restrict__ hN, int m,
+                            int ny, int nxh, float2* hhat) {
+    const long long total = (long long)m * ny * (nxh + 1);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % (nxh + 1));
+        const long long kf = i / (nxh + 1);
+        hhat[i] = c < nxh ? hh[kf * nxh + c] : hN[kf];
+    }
+}
+
+// hhat [m][n/2+1] -> packed [m][n/2] (slot 0 = (Re DC, Re Nyquist)) and back.
+__global__ void k_from_half1d(const float2* __restrict__ hhat, int m, int nh, float2* hp) {
+    const long long total = (long long)m * nh;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int f = (int)(i % nh);
+        const long long k = i / nh;
+        const float2* src = hhat + k * (nh + 1);
+        hp[i] = f == 0 ? make_float2(src[0].x, src[nh].x) : src[f];
+    }
+}
+
+__global__ void k_to_half1d(const float2* __restrict__ hp, int m, int nh, float2* hhat) {
+    const long long total = (long long)m * (nh + 1);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int f = (int)(i % (nh + 1));
+        const long long k = i / (nh + 1);
+        const float2* src = hp + k * nh;
+        float2 v;
+        if (f == 0) v = make_float2(src[0].x, 0.f);
+        else if (f == nh) v = make_float2(src[0].y, 0.f);
+        else v = src[f];
+        hhat[i] = v;
+    }
+}
+
+unsigned grid_for(long long total, int threads = 256) {
+    long long g = (total + threads - 1) / threads;
+    return (unsigned)std::max<long long>(1, std::min<long long>(g, 1 << 20));
+}
+
+// Smallest periodic interval [start, start+len) holding every set flag.
+void cyclic_support(const unsigned char* f, int n, int& start, int& len) {
+    int nz = 0;
+    for (int i = 0; i < n; ++i) nz += f[i] != 0;
+    if (nz == 0) { start = 0; len = 0; return; }
+    if (nz == n) { start = 0; len = n; return; }
+    // longest cyclic run of zeros
+    int best = 0, best_end = 0, run = 0;
+    for (int t = 0; t < 2 * n; ++t) {
+        if (!f[t % n]) {
+            ++run;
+            if (run > best && run <= n) { best = run; best_end = t; }
+        } else {
+            run = 0;
+        }
+    }
+    start = (best_end + 1) % n;
+    len = n - best;
+}
+
+template <class T>
+pce_status dev_alloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) return PCE_OK;
+    PCE_CK(cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T)));
+    return PCE_OK;
+}
+
+}  // namespace
+
+struct pce_plan {
+    int ndims = 0, ny = 1, nx = 0, m = 0;
+    uint32_t flags = 0;
+    int device = 0;
+    // windows
+    std::vector<Box> box;
+    Box* d_box = nullptr;
+    float* wbox = nullptr;      // 2D: box copies; 1D: dense [m][N]
+    // spectra
+    float2* hh = nullptr;       // 2D [m][ny][nx/2]; 1D packed [m][n/2]
+    float2* hN = nullptr;       // 2D [m][ny]
+    // twiddles
+    float2* twx = nullptr;
+    float2* twy = nullptr;
+    // work lists
+    int2* items = nullptr;
+    int nitems = 0;
+    int* kptr = nullptr;
+    int* klist = nullptr;
+    // scratch
+    float2* scrZ = nullptr;
+    float2* scrA = nullptr;
+    int nrmax = 0;
+    int bchunk = 1;
+    long long scratch_bytes = 0;
+    // per-kernel timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;          // pairs (start, stop)
+    std::vector<int> ev_kind;
+    size_t ev_used = 0;
+
+    void drop_events() {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        ev.clear();
+        ev_kind.clear();
+        ev_used = 0;
+    }
+
+    ~pce_plan() {
+        drop_events();
+        void* ptrs[] = {d_box, wbox, hh, hN, twx, twy == twx ? nullptr : twy, items, kptr, klist,
+                        scrZ, scrA};
+        for (void* p : ptrs)
+            if (p) cudaFree(p);
+    }
+};
+
+namespace {
+
+pce_status validate_shape(int ndims, const int64_t* shape, int& ny, int& nx) {
+    if (ndims != 1 && ndims != 2) return fail(PCE_ERR_INVALID, "ndims must be 1 or 2 (got %d)", ndims);
+    if (!shape) return fail(PCE_ERR_INVALID, "shape is NULL");
+    if (ndims == 1) {
+        ny = 1;
+        if (!is_pow2(shape[0]) || shape[0] < 16 || shape[0] > 8192)
+            return fail(PCE_ERR_UNSUPPORTED, "1D size must be a power of two in [16, 8192] (got %lld)",
+                        (long long)shape[0]);
+        nx = (int)shape[0];
+    } else {
+        for (int d = 0; d < 2; ++d)
+            if (!is_pow2(shape[d]) || shape[d] < 16 || shape[d] > 2048)
+                return fail(PCE_ERR_UNSUPPORTED,
+                            "2D sizes must be powers of two in [16, 2048] (got %lld x %lld)",
+                            (long long)shape[0], (long long)shape[1]);
+        ny = (int)shape[0];
+        nx = (int)shape[1];
+    }
+    return PCE_OK;
+}
+
+pce_status make_twiddles(pce_plan* p, cudaStream_t s) {
+    pce_status st = dev_alloc(&p->twx, (size_t)std::max(1, twiddle_len(p->nx)));
+    if (st) return st;
+    k_twiddles<<<grid_for(twiddle_len(p->nx)), 256, 0, s>>>(p->twx, p->nx);
+    PCE_CK(cudaGetLastError());
+    if (p->ndims == 2) {
+        if (p->ny == p->nx) {
+            p->twy = p->twx;
+        } else {
+            st = dev_alloc(&p->twy, (size_t)std::max(1, twiddle_len(p->ny)));
+            if (st) return st;
+            k_twiddles<<<grid_for(twiddle_len(p->ny)), 256, 0, s>>>(p->twy, p->ny);
+            PCE_CK(cudaGetLastError());
+        }
+    }
+    return PCE_OK;
+}
+
+// Windows: support boxes, box copies, work lists, scratch (2D); dense copy (1D).
+pce_status setup_windows(pce_plan* p, const float* w, cudaStream_t s) {
+    const int m = p->m, ny = p->ny, nx = p->nx;
+    if (p->ndims == 1) {
+        pce_status st = dev_alloc(&p->wbox, (size_t)m * nx);
+        if (st) return st;
+        PCE_CK(cudaMemcpyAsync(p->wbox, w, sizeof(float) * m * nx, cudaMemcpyDeviceToDevice, s));
+        p->box.assign(m, Box{0, 1, 0, nx, 0, nx, 0});
+        return PCE_OK;
+    }
+    unsigned char* flags = nullptr;
+    const size_t nflags = (size_t)m * (ny + nx);
+    PCE_CK(cudaMalloc(&flags, nflags));
+    cudaError_t e = cudaMemsetAsync(flags, 0, nflags, s);
+    if (e == cudaSuccess) {
+        k_support<<<grid_for((long long)m * ny * nx), 256, 0, s>>>(w, m, ny, nx, flags,
+                                                                   flags + (size_t)m * ny);
+        e = cudaGetLastError();
+    }
+    std::vector<unsigned char> hf(nflags);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hf.data(), flags, nflags, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(flags);
+    PCE_CK(e);
+
+    p->box.resize(m);
+    long long woff = 0;
+    for (int k = 0; k < m; ++k) {
+        Box b{};
+        cyclic_support(&hf[(size_t)k * ny], ny, b.r0, b.nr);
+        cyclic_support(&hf[(size_t)m * ny + (size_t)k * nx], nx, b.c0, b.nc);
+        if (b.nr == 0 || b.nc == 0) { b.nr = 0; b.nc = 0; }
+        b.ldw = (b.nc + 3) & ~3;
+        b.woff = woff;
+        woff += (long long)b.nr * b.ldw;
+        p->box[k] = b;
+        p->nrmax = std::max(p->nrmax, b.nr);
+    }
+    pce_status st = dev_alloc(&p->wbox, (size_t)std::max<long long>(woff, 4));
+    if (st) return st;
+    for (int k = 0; k < m; ++k) {
+        const Box& b = p->box[k];
+        if (b.nr == 0) continue;
+        k_wbox<<<grid_for((long long)b.nr * b.ldw), 256, 0, s>>>(w + (size_t)k * ny * nx, ny, nx, b,
+                                                                 p->wbox);
+        PCE_CK(cudaGetLastError());
+    }
+
+    // F1 items: (k, row pair inside the box)
+    std::vector<int2> items;
+    for (int k = 0; k < m; ++k)
+        for (int q = 0; q < (p->box[k].nr + 1) / 2; ++q) items.push_back(make_int2(k, q));
+    p->nitems = (int)items.size();
+    // G3 lists: terms whose box holds row 2q or 2q+1
+    const int npairs = (ny + 1) / 2;
+    std::vector<int> kptr(npairs + 1, 0), klist;
+    for (int q = 0; q < npairs; ++q) {
+        for (int k = 0; k < m; ++k) {
+            const Box& b = p->box[k];
+            if (b.nr == 0) continue;
+            bool hit = false;
+            for (int g = 2 * q; g < std::min(2 * q + 2, ny); ++g) {
+                int i = g - b.r0;
+                if (i < 0) i += ny;
+                if (i < b.nr) hit = true;
+            }
+            if (hit) klist.push_back(k);
+        }
+        kptr[q + 1] = (int)klist.size();
+    }
+    if ((st = dev_alloc(&p->d_box, (size_t)m))) return st;
+    if ((st = dev_alloc(&p->items, std::max<size_t>(items.size(), 1)))) return st;
+    if ((st = dev_alloc(&p->kptr, kptr.size()))) return st;
+    if ((st = dev_alloc(&p->klist, std::max<size_t>(klist.size(), 1)))) return st;
+    PCE_CK(cudaMemcpyAsync(p->d_box, p->box.data(), sizeof(Box) * m, cudaMemcpyHostToDevice, s));
+    if (!items.empty())
+        PCE_CK(cudaMemcpyAsync(p->items, items.data(), sizeof(int2) * items.size(),
+                               cudaMemcpyHostToDevice, s));
+    PCE_CK(cudaMemcpyAsync(p->kptr, kptr.data(), sizeof(int) * kptr.size(), cudaMemcpyHostToDevice, s));
+    if (!klist.empty())
+        PCE_CK(cudaMemcpyAsync(p->klist, klist.data(), sizeof(int) * klist.size(),
+                               cudaMemcpyHostToDevice, s));
+    // the host vectors die at return: make the copies complete first
+    PCE_CK(cudaStreamSynchronize(s));
+
+    // scratch: Z/Q [bchunk][m][nrmax][nx/2], A/V [bchunk][ny][nx/2]
+    const long long nxh = nx / 2;
+    const long long zb = (long long)m * p->nrmax * nxh;
+    const long long ab = (long long)ny * nxh;
+    const long long per_b = (zb + ab) * (long long)sizeof(float2);
+    p->bchunk = (int)std::max<long long>(1, std::min<long long>(kMaxChunk, kScratchBudget / per_b));
+    if ((st = dev_alloc(&p->scrZ, (size_t)std::max<long long>(1, zb * p->bchunk)))) return st;
+    if ((st = dev_alloc(&p->scrA, (size_t)(ab * p->bchunk)))) return st;
+    p->scratch_bytes = per_b * p->bchunk;
+    return PCE_OK;
+}
+
+pce_status check_plan(pce_plan_t p) {
+    if (!p) return fail(PCE_ERR_INVALID, "plan is NULL");
+    return PCE_OK;
+}
+
+pce_status create_common(pce_plan_t* out, int ndims, const int64_t* shape, int m, const float* w,
+                         const float* h, bool spectra, uint32_t flags, void* stream) {
+    if (!out) return fail(PCE_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    int ny = 1, nx = 0;
+    pce_status st = validate_shape(ndims, shape, ny, nx);
+    if (st) return st;
+    if (m < 1) return fail(PCE_ERR_INVALID, "m must be >= 1 (got %d)", m);
+    if (!is_device_ptr(w)) return fail(PCE_ERR_INVALID, "w must be a device pointer");
+    if (!is_device_ptr(h)) return fail(PCE_ERR_INVALID, spectra ? "hhat must be a device pointer"
+                                                                : "h must be a device pointer");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    static bool prepared[64] = {false};
+    int dev = 0;
+    PCE_CK(cudaGetDevice(&dev));
+    if (dev < 64 && !prepared[dev]) {
+        PCE_CK(pce::prepare_kernels());
+        prepared[dev] = true;
+    }
+    pce_plan* p = new pce_plan();
+    p->ndims = ndims;
+    p->ny = ny;
+    p->nx = nx;
+    p->m = m;
+    p->flags = flags;
+    p->device = dev;
+    auto bail = [&](pce_status e) {
+        cudaStreamSynchronize(s);
+        delete p;
+        return e;
+    };
+    if ((st = make_twiddles(p, s))) return bail(st);
+    if ((st = setup_windows(p, w, s))) return bail(st);
+    const int nxh = nx / 2;
+    if (ndims == 1) {
+        if ((st = dev_alloc(&p->hh, (size_t)m * nxh))) return bail(st);
+        if (spectra) {
+            k_from_half1d<<<grid_for((long long)m * nxh), 256, 0, s>>>(
+                reinterpret_cast<const float2*>(h), m, nxh, p->hh);
+            cudaError_t e = cudaGetLastError();
+            if (e) return bail(fail(PCE_ERR_CUDA, "spectrum conversion: %s", cudaGetErrorString(e)));
+        } else {
+            cudaError_t e = pce::launch_spec_1d(nx, m, s, h, p->hh, p->twx);
+            if (e) return bail(fail(PCE_ERR_CUDA, "spectrum of h: %s", cudaGetErrorString(e)));
+        }
+    } else {
+        if ((st = dev_alloc(&p->hh, (size_t)m * ny * nxh))) return bail(st);
+        if ((st = dev_alloc(&p->hN, (size_t)m * ny))) return bail(st);
+        if (spectra) {
+            k_from_half2d<<<grid_for((long long)m * ny * (nxh + 1)), 256, 0, s>>>(
+                reinterpret_cast<const float2*>(h), m, ny, nxh, p->hh, p->hN);
+            cudaError_t e = cudaGetLastError();
+            if (e) return bail(fail(PCE_ERR_CUDA, "spectrum conversion: %s", cudaGetErrorString(e)));
+        } else {
+            // hhat = column FFT of the row R2C spectra of h (rows of all m terms at once)
+            float2* S = nullptr;
+            if ((st = dev_alloc(&S, (size_t)m * ny * nxh))) return bail(st);
+            const int fpc = pce::rows_pairs_per_cta(nx);
+            const int npairs = (ny + 1) / 2;
+            cudaError_t e = pce::launch_rows_r2c(nx, false, dim3((npairs + fpc - 1) / fpc, m), s, h,
+                                                 (long long)ny * nx, ny, nullptr, nullptr, nullptr,
+                                                 npairs, S, (long long)ny * nxh, 0, p->twx);
+            const int cpc = pce::cols_columns_per_cta(ny);
+            if (e == cudaSuccess)
+                e = pce::launch_cols_spec(ny, dim3((nxh + cpc - 1) / cpc, m), s, S, nxh, p->hh, p->hN,
+                                          p->twy);
+            cudaError_t e2 = cudaStreamSynchronize(s);
+            cudaFree(S);
+            if (e == cudaSuccess) e = e2;
+            if (e) return bail(fail(PCE_ERR_CUDA, "spectrum of h: %s", cudaGetErrorString(e)));
+        }
+    }
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e) return bail(fail(PCE_ERR_CUDA, "plan set-up: %s", cudaGetErrorString(e)));
+    *out = p;
+    return PCE_OK;
+}
+
+pce_status check_io(pce_plan_t p, const float* in, const float* out, int64_t batch) {
+    if (batch < 0) return fail(PCE_ERR_INVALID, "batch must be >= 0");
+    if (batch == 0) return PCE_OK;
+    if (batch > (1ll << 31) - 1) return fail(PCE_ERR_INVALID, "batch too large");
+    if (!is_device_ptr(in) || !is_device_ptr(out))
+        return fail(PCE_ERR_INVALID, "input and output must be device pointers");
+    const long long P = (long long)p->ny * p->nx;
+    const char* a = reinterpret_cast<const char*>(in);
+    const char* b = reinterpret_cast<const char*>(out);
+    const long long bytes = P * batch * (long long)sizeof(float);
+    if (a < b + bytes && b < a + bytes) return fail(PCE_ERR_INVALID, "input and output overlap");
+    int dev = 0;
+    PCE_CK(cudaGetDevice(&dev));
+    if (dev != p->device) return fail(PCE_ERR_INVALID, "plan belongs to device %d, current is %d",
+                                      p->device, dev);
+    return PCE_OK;
+}
+
+constexpr size_t kMaxTimed = 65536;
+
+// Run one launch, bracketed by events when the plan records timings.
+template <class F>
+cudaError_t timed(pce_plan_t p, int kind, cudaStream_t s, F&& launch) {
+    if (!p->timing || p->ev_used >= 2 * kMaxTimed) return launch();
+    if (p->ev_used + 2 > p->ev.size()) {
+        for (int i = 0; i < 64; ++i) {
+            cudaEvent_t e;
+            cudaError_t err = cudaEventCreate(&e);
+            if (err != cudaSuccess) return err;
+            p->ev.push_back(e);
+        }
+    }
+    cudaEvent_t a = p->ev[p->ev_used], b = p->ev[p->ev_used + 1];
+    cudaError_t err = cudaEventRecord(a, s);
+    if (err == cudaSuccess) err = launch();
+    if (err == cudaSuccess) err = cudaEventRecord(b, s);
+    if (err == cudaSuccess) {
+        p->ev_used += 2;
+        p->ev_kind.push_back(kind);
+    }
+    return err;
+}
+
+pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, bool adjoint,
+                      cudaStream_t s) {
+    const int ny = p->ny, nx = p->nx, m = p->m, nxh = nx / 2;
+    const long long P = (long long)ny * nx;
+    const float scale = 1.0f / (float)P;
+    cudaError_t e = cudaSuccess;
+    if (p->ndims == 1) {
+        e = timed(p, adjoint ? PCE_KERNEL_ADJ_1D : PCE_KERNEL_FWD_1D, s, [&] {
+            return adjoint
+                ? pce::launch_adj_1d(nx, (int)batch, s, in, p->wbox, p->hh, m, out, scale, p->twx)
+                : pce::launch_fwd_1d(nx, (int)batch, s, in, p->wbox, p->hh, m, out, scale, p->twx);
+        });
+        if (e) return fail(PCE_ERR_CUDA, "1D apply launch: %s", cudaGetErrorString(e));
+        return PCE_OK;
+    }
+    const long long zk = (long long)p->nrmax * nxh;
+    const long long zb = (long long)m * zk;
+    const long long ab = (long long)ny * nxh;
+    const int fpc = pce::rows_pairs_per_cta(nx);
+    const int cpc = pce::cols_columns_per_cta(ny);
+    const int npairs = (ny + 1) / 2;
+    for (long long b0 = 0; b0 < batch && e == cudaSuccess; b0 += p->bchunk) {
+        const int nb = (int)std::min<long long>(p->bchunk, batch - b0);
+        const float* src = in + b0 * P;
+        float* dst = out + b0 * P;
+        if (!adjoint) {
+            if (p->nitems > 0)
+                e = timed(p, PCE_KERNEL_ROWS_R2C_WINDOW, s, [&] {
+                    return pce::launch_rows_r2c(nx, true, dim3((p->nitems + fpc - 1) / fpc, nb), s, src,
+                                                P, ny, p->wbox, p->d_box, p->items, p->nitems, p->scrZ,
+                                                zb, zk, p->twx);
+                });
+            if (e == cudaSuccess)
+                e = timed(p, PCE_KERNEL_COLS_FWD, s, [&] {
+                    return pce::launch_cols_fwd(ny, dim3((nxh + cpc - 1) / cpc, nb), s, p->scrZ, zb, zk,
+                                                p->hh, p->hN, m, p->d_box, nxh, p->scrA, ab, p->twy);
+                });
+            if (e == cudaSuccess)
+                e = timed(p, PCE_KERNEL_ROWS_C2R, s, [&] {
+                    return pce::launch_rows_c2r(nx, dim3((npairs + fpc - 1) / fpc, nb), s, p->scrA, ab,
+                                                ny, dst, P, scale, p->twx);
+                });
+        } else {
+            e = timed(p, PCE_KERNEL_ROWS_R2C, s, [&] {
+                return pce::launch_rows_r2c(nx, false, dim3((npairs + fpc - 1) / fpc, nb), s, src, P,
+                                            ny, nullptr, nullptr, nullptr, npairs, p->scrA, ab, 0,
+                                            p->twx);
+            });
+            if (e == cudaSuccess)
+                e = timed(p, PCE_KERNEL_COLS_ADJ, s, [&] {
+                    return pce::launch_cols_adj(ny, dim3((nxh + cpc - 1) / cpc, nb), s, p->scrA, ab,
+                                                p->hh, p->hN, m, p->d_box, nxh, p->scrZ, zb, zk, p->twy);
+                });
+            if (e == cudaSuccess)
+                e = timed(p, PCE_KERNEL_ROWS_ADJ, s, [&] {
+                    return pce::launch_rows_adj(nx, dim3((npairs + fpc - 1) / fpc, nb), s, p->scrZ, zb,
+                                                zk, ny, p->wbox, p->d_box, p->kptr, p->klist, dst, P,
+                                                scale, p->twx);
+                });
+        }
+    }
+    if (e) return fail(PCE_ERR_CUDA, "2D apply launch: %s", cudaGetErrorString(e));
+    return PCE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pce_status pce_plan_create(pce_plan_t* out, int ndims, const int64_t* shape, int m, const float* w,
+                           const float* h, uint32_t flags, void* stream) {
+    return create_common(out, ndims, shape, m, w, h, false, flags, stream);
+}
+
+pce_status pce_plan_create_from_spectra(pce_plan_t* out, int ndims, const int64_t* shape, int m,
+                                        const float* w, const float* hhat, uint32_t flags,
+                                        void* stream) {
+    return create_common(out, ndims, shape, m, w, hhat, true, flags, stream);
+}
+
+pce_status pce_apply(pce_plan_t plan, const float* u, float* y, int64_t batch, void* stream) {
+    pce_status st = check_plan(plan);
+    if (st) return st;
+    if ((st = check_io(plan, u, y, batch))) return st;
+    if (batch == 0) return PCE_OK;
+    return apply_impl(plan, u, y, batch, false, static_cast<cudaStream_t>(stream));
+}
+
+pce_status pce_apply_adjoint(pce_plan_t plan, const float* v, float* x, int64_t batch,
+                             void* stream) {
+    pce_status st = check_plan(plan);
+    if (st) return st;
+    if ((st = check_io(plan, v, x, batch))) return st;
+    if (batch == 0) return PCE_OK;
+    return apply_impl(plan, v, x, batch, true, static_cast<cudaStream_t>(stream));
+}
+
+pce_status pce_plan_info(pce_plan_t plan, int* m_out, int* box_out, int64_t* scratch_bytes_out) {
+    pce_status st = check_plan(plan);
+    if (st) return st;
+    if (m_out) *m_out = plan->m;
+    if (box_out)
+        for (int k = 0; k < plan->m; ++k) {
+            box_out[4 * k + 0] = plan->box[k].r0;
+            box_out[4 * k + 1] = plan->box[k].nr;
+            box_out[4 * k + 2] = plan->box[k].c0;
+            box_out[4 * k + 3] = plan->box[k].nc;
+        }
+    if (scratch_bytes_out) *scratch_bytes_out = plan->scratch_bytes;
+    return PCE_OK;
+}
+
+pce_status pce_plan_hhat(pce_plan_t plan, float* hhat, void* stream) {
+    pce_status st = check_plan(plan);
+    if (st) return st;
+    if (!is_device_ptr(hhat)) return fail(PCE_ERR_INVALID, "hhat must be a device pointer");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int nxh = plan->nx / 2;
+    if (plan->ndims == 1)
+        k_to_half1d<<<grid_for((long long)plan->m * (nxh + 1)), 256, 0, s>>>(
+            plan->hh, plan->m, nxh, reinterpret_cast<float2*>(hhat));
+    else
+        k_to_half2d<<<grid_for((long long)plan->m * plan->ny * (nxh + 1)), 256, 0, s>>>(
+            plan->hh, plan->hN, plan->m, plan->ny, nxh, reinterpret_cast<float2*>(hhat));
+    PCE_CK(cudaGetLastError());
+    return PCE_OK;
+}
+
+pce_status pce_plan_destroy(pce_plan_t plan) {
+    if (!plan) return PCE_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    delete plan;
+    if (e != cudaSuccess) return fail(PCE_ERR_CUDA, "synchronise before free: %s", cudaGetErrorString(e));
+    return PCE_OK;
+}
+
+const char* pce_last_error_string(void) { return g_err.c_str(); }
+
+pce_status pce_plan_set_timing(pce_plan_t plan, int enable) {
+    pce_status st = check_plan(plan);
+    if (st) return st;
+    if (!enable || plan->timing) {
+        // a pending record must finish before its events are destroyed
+        for (size_t i = 0; i < plan->ev_used; ++i) cudaEventSynchronize(plan->ev[i]);
+        plan->drop_events();
+    }
+    plan->timing = enable != 0;
+    return PCE_OK;
+}
+
+pce_status pce_plan_timing(pce_plan_t plan, int kind, double* total_ms, int64_t* launches) {
+    pce_status st = check_plan(plan);
+    if (st) return st;
+    if (kind < 0 || kind >= PCE_KERNEL_KINDS) return fail(PCE_ERR_INVALID, "bad kernel kind %d", kind);
+    double tot = 0.0;
+    int64_t n = 0;
+    for (size_t i = 0; i < plan->ev_kind.size(); ++i) {
+        if (plan->ev_kind[i] != kind) continue;
+        PCE_CK(cudaEventSynchronize(plan->ev[2 * i + 1]));
+        float ms = 0.f;
+        PCE_CK(cudaEventElapsedTime(&ms, plan->ev[2 * i], plan->ev[2 * i + 1]));
+        tot += ms;
+        ++n;
+    }
+    if (total_ms) *total_ms = tot;
+    if (launches) *launches = n;
+    return PCE_OK;
+}
+
+int64_t pce_launch_count(pce_plan_t plan, int adjoint, int64_t batch) {
+    (void)adjoint;
+    if (!plan || batch <= 0) return 0;
+    if (plan->ndims == 1) return 1;
+    const int64_t chunks = (batch + plan->bchunk - 1) / plan->bchunk;
+    const int64_t per = (!adjoint && plan->nitems == 0) ? 2 : 3;
+    return chunks * per;
+}
+
+}  // extern "C"

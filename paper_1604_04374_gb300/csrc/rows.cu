@@ -1,0 +1,69 @@
+// rows.cu -- instances of the row-pass kernels for NX = 16 .. 2048.
+#include "kernels.cuh"
+#include "launch.h"
+
+namespace pce {
+
+int rows_pairs_per_cta(int nx) { return 256 / (nx / kR); }
+
+#define PCE_ROW_SIZES(X) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048)
+
+cudaError_t launch_rows_r2c(int nx, bool window, dim3 grid, cudaStream_t s,
+                            const float* src, long long src_bstride, int nrows,
+                            const float* wbox, const Box* box, const int2* items, int nitems,
+                            float2* dst, long long dst_bstride, long long dst_kstride,
+                            const float2* tw) {
+    switch (nx) {
+#define X(N)                                                                                   \
+    case N:                                                                                    \
+        if (window)                                                                            \
+            k_rows_r2c<N, true><<<grid, 256, 0, s>>>(src, src_bstride, nrows, wbox, box, items, \
+                                                     nitems, dst, dst_bstride, dst_kstride, tw); \
+        else                                                                                   \
+            k_rows_r2c<N, false><<<grid, 256, 0, s>>>(src, src_bstride, nrows, wbox, box,       \
+                                                      items, nitems, dst, dst_bstride,         \
+                                                      dst_kstride, tw);                        \
+        break;
+        PCE_ROW_SIZES(X)
+#undef X
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rows_c2r(int nx, dim3 grid, cudaStream_t s, const float2* src,
+                            long long src_bstride, int nrows, float* dst, long long dst_bstride,
+                            float scale, const float2* tw) {
+    switch (nx) {
+#define X(N)                                                                                  \
+    case N:                                                                                   \
+        k_rows_c2r<N><<<grid, 256, 0, s>>>(src, src_bstride, nrows, dst, dst_bstride, scale, tw); \
+        break;
+        PCE_ROW_SIZES(X)
+#undef X
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rows_adj(int nx, dim3 grid, cudaStream_t s, const float2* Q, long long q_bstride,
+                            long long q_kstride, int nrows, const float* wbox, const Box* box,
+                            const int* kptr, const int* klist, float* dst, long long dst_bstride,
+                            float scale, const float2* tw) {
+    switch (nx) {
+#define X(N)                                                                                   \
+    case N:                                                                                    \
+        k_rows_adj<N><<<grid, 256, 0, s>>>(Q, q_bstride, q_kstride, nrows, wbox, box, kptr,     \
+                                           klist, dst, dst_bstride, scale, tw);                \
+        break;
+        PCE_ROW_SIZES(X)
+#undef X
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace pce

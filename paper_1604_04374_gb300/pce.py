@@ -1,0 +1,247 @@
+"""ctypes binding of include/pce.h (argument marshalling only).
+
+The functions named pce_* take and return the same things as their C
+counterparts, with device pointers and streams passed as Python integers.
+``Plan`` wraps a plan handle around torch CUDA tensors.  Every failing call
+raises PceError carrying the status and pce_last_error_string().
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+PCE_OK, PCE_ERR_INVALID, PCE_ERR_UNSUPPORTED, PCE_ERR_OOM, PCE_ERR_CUDA, PCE_ERR_TIMEOUT = range(6)
+STATUS_NAMES = {0: "PCE_OK", 1: "PCE_ERR_INVALID", 2: "PCE_ERR_UNSUPPORTED", 3: "PCE_ERR_OOM",
+                4: "PCE_ERR_CUDA", 5: "PCE_ERR_TIMEOUT"}
+
+_lib = None
+
+
+class PceError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def load_library(path: str | None = None) -> ctypes.CDLL:
+    """Load libpce.so (built in-tree by paper_1604_04374_gb300.build.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_1604_04374_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    i64 = ctypes.c_int64
+    lib.pce_plan_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(i64), ctypes.c_int,
+                                    P, P, ctypes.c_uint32, P]
+    lib.pce_plan_create_from_spectra.argtypes = lib.pce_plan_create.argtypes
+    lib.pce_apply.argtypes = [P, P, P, i64, P]
+    lib.pce_apply_adjoint.argtypes = [P, P, P, i64, P]
+    lib.pce_plan_info.argtypes = [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                  ctypes.POINTER(i64)]
+    lib.pce_plan_hhat.argtypes = [P, P, P]
+    lib.pce_plan_destroy.argtypes = [P]
+    lib.pce_last_error_string.restype = ctypes.c_char_p
+    lib.pce_last_error_string.argtypes = []
+    lib.pce_launch_count.argtypes = [P, ctypes.c_int, i64]
+    lib.pce_launch_count.restype = i64
+    lib.pce_plan_set_timing.argtypes = [P, ctypes.c_int]
+    lib.pce_plan_timing.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(i64)]
+    for name in ("pce_plan_create", "pce_plan_create_from_spectra", "pce_apply", "pce_apply_adjoint",
+                 "pce_plan_info", "pce_plan_hhat", "pce_plan_destroy", "pce_plan_set_timing",
+                 "pce_plan_timing"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status: int) -> None:
+    if status != PCE_OK:
+        raise PceError(status, pce_last_error_string())
+
+
+def pce_last_error_string() -> str:
+    return load_library().pce_last_error_string().decode()
+
+
+def pce_plan_create(ndims: int, shape, m: int, w_ptr: int, h_ptr: int, flags: int = 0,
+                    stream: int = 0) -> int:
+    handle = ctypes.c_void_p()
+    shp = (ctypes.c_int64 * len(shape))(*shape)
+    _check(load_library().pce_plan_create(ctypes.byref(handle), ndims, shp, m, w_ptr, h_ptr,
+                                          flags, stream))
+    return handle.value
+
+
+def pce_plan_create_from_spectra(ndims: int, shape, m: int, w_ptr: int, hhat_ptr: int,
+                                 flags: int = 0, stream: int = 0) -> int:
+    handle = ctypes.c_void_p()
+    shp = (ctypes.c_int64 * len(shape))(*shape)
+    _check(load_library().pce_plan_create_from_spectra(ctypes.byref(handle), ndims, shp, m, w_ptr,
+                                                       hhat_ptr, flags, stream))
+    return handle.value
+
+
+def pce_apply(plan: int, u_ptr: int, y_ptr: int, batch: int, stream: int = 0) -> None:
+    _check(load_library().pce_apply(plan, u_ptr, y_ptr, batch, stream))
+
+
+def pce_apply_adjoint(plan: int, v_ptr: int, x_ptr: int, batch: int, stream: int = 0) -> None:
+    _check(load_library().pce_apply_adjoint(plan, v_ptr, x_ptr, batch, stream))
+
+
+def pce_plan_info(plan: int, m: int):
+    mm = ctypes.c_int()
+    boxes = (ctypes.c_int * (4 * m))()
+    scratch = ctypes.c_int64()
+    _check(load_library().pce_plan_info(plan, ctypes.byref(mm), boxes, ctypes.byref(scratch)))
+    return mm.value, [tuple(boxes[4 * k:4 * k + 4]) for k in range(m)], scratch.value
+
+
+def pce_plan_hhat(plan: int, hhat_ptr: int, stream: int = 0) -> None:
+    _check(load_library().pce_plan_hhat(plan, hhat_ptr, stream))
+
+
+def pce_plan_destroy(plan: int) -> None:
+    _check(load_library().pce_plan_destroy(plan))
+
+
+def pce_launch_count(plan: int, adjoint: bool, batch: int) -> int:
+    return int(load_library().pce_launch_count(plan, 1 if adjoint else 0, batch))
+
+
+KERNEL_KINDS = ("rows_r2c_window", "cols_fwd", "rows_c2r", "rows_r2c", "cols_adj", "rows_adj",
+                "fwd_1d", "adj_1d")
+
+
+def pce_plan_set_timing(plan: int, enable: bool) -> None:
+    _check(load_library().pce_plan_set_timing(plan, 1 if enable else 0))
+
+
+def pce_plan_timing(plan: int, kind: int):
+    """(summed device milliseconds, launches) of kernel kind ``kind`` since timing was enabled."""
+    ms = ctypes.c_double()
+    n = ctypes.c_int64()
+    _check(load_library().pce_plan_timing(plan, kind, ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
+
+
+# ----------------------------------------------------------------- torch side
+
+def _stream_handle(stream) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _need_cuda_f32(t, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float32:
+        raise ValueError(f"{name} must be float32")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+class Plan:
+    """A convolution-product operator H_m on one CUDA device.
+
+    ``w``: float32 CUDA tensor [m, *shape]; exactly one of ``h`` (float32
+    [m, *shape], origin at index 0) or ``hhat`` (complex64 [m, Ny, Nx/2+1] or
+    [m, N/2+1]).  ``shape`` is (N,) or (Ny, Nx).
+    """
+
+    def __init__(self, w, h=None, hhat=None, stream=None, flags: int = 0):
+        import torch
+        _need_cuda_f32(w, "w")
+        self.m = int(w.shape[0])
+        self.shape = tuple(int(s) for s in w.shape[1:])
+        self.ndims = len(self.shape)
+        self.device = w.device
+        sh = _stream_handle(stream)
+        with torch.cuda.device(self.device):
+            if (h is None) == (hhat is None):
+                raise ValueError("give exactly one of h and hhat")
+            if h is not None:
+                _need_cuda_f32(h, "h")
+                if tuple(h.shape) != tuple(w.shape):
+                    raise ValueError("h and w must have the same shape")
+                self.handle = pce_plan_create(self.ndims, self.shape, self.m, w.data_ptr(), h.data_ptr(),
+                                              flags, sh)
+            else:
+                if hhat.dtype != torch.complex64 or not hhat.is_cuda or not hhat.is_contiguous():
+                    raise ValueError("hhat must be a contiguous complex64 CUDA tensor")
+                want = (self.m,) + self.shape[:-1] + (self.shape[-1] // 2 + 1,)
+                if tuple(hhat.shape) != want:
+                    raise ValueError(f"hhat must have shape {want}")
+                self.handle = pce_plan_create_from_spectra(self.ndims, self.shape, self.m, w.data_ptr(),
+                                                           hhat.data_ptr(), flags, sh)
+
+    def _io(self, x, out, name):
+        import torch
+        _need_cuda_f32(x, name)
+        if tuple(x.shape[-self.ndims:]) != self.shape:
+            raise ValueError(f"{name} must end with shape {self.shape}")
+        batch = x.numel() // max(1, int(torch.tensor(self.shape).prod()))
+        if out is None:
+            out = torch.empty_like(x)
+        else:
+            _need_cuda_f32(out, "out")
+            if out.shape != x.shape:
+                raise ValueError("out must have the input's shape")
+        return batch, out
+
+    def apply(self, u, out=None, stream=None):
+        """y = H_m u for u of shape [..., *shape]."""
+        batch, out = self._io(u, out, "u")
+        pce_apply(self.handle, u.data_ptr(), out.data_ptr(), batch, _stream_handle(stream))
+        return out
+
+    def apply_adjoint(self, v, out=None, stream=None):
+        """x = H_m^* v for v of shape [..., *shape]."""
+        batch, out = self._io(v, out, "v")
+        pce_apply_adjoint(self.handle, v.data_ptr(), out.data_ptr(), batch, _stream_handle(stream))
+        return out
+
+    def info(self):
+        """(m, support boxes [(r0, nr, c0, nc)], scratch bytes)."""
+        return pce_plan_info(self.handle, self.m)
+
+    def hhat(self, stream=None):
+        import torch
+        out = torch.empty((self.m,) + self.shape[:-1] + (self.shape[-1] // 2 + 1,),
+                          dtype=torch.complex64, device=self.device)
+        pce_plan_hhat(self.handle, out.data_ptr(), _stream_handle(stream))
+        return out
+
+    def launch_count(self, adjoint: bool, batch: int) -> int:
+        return pce_launch_count(self.handle, adjoint, batch)
+
+    def set_timing(self, enable: bool) -> None:
+        pce_plan_set_timing(self.handle, enable)
+
+    def timing(self) -> dict:
+        """{kernel kind: (device ms, launches)} recorded since set_timing(True)."""
+        out = {}
+        for kind, name in enumerate(KERNEL_KINDS):
+            ms, n = pce_plan_timing(self.handle, kind)
+            if n:
+                out[name] = (ms, n)
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            pce_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

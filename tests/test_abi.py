@@ -1,0 +1,64 @@
+"""The C-ABI library builds, loads and exports every entry point include/pce.h declares.
+
+These run without a GPU: they only load libpce.so and call entry points on
+argument errors that are rejected before any CUDA call.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include"))
+           if f.endswith(".h")]
+
+
+def _declared():
+    names = set()
+    for h in HEADERS:
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(pce_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1604_04374_gb300 import build, load_library
+    build.build()
+    return load_library()
+
+
+def test_header_declares_the_call_set():
+    names = _declared()
+    for n in ("pce_plan_create", "pce_plan_create_from_spectra", "pce_apply", "pce_apply_adjoint",
+              "pce_plan_destroy", "pce_last_error_string"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in sorted(_declared()):
+        assert hasattr(lib, name), name
+        assert ctypes.cast(getattr(lib, name), ctypes.c_void_p).value
+
+
+def test_argument_errors_are_status_codes(lib):
+    from paper_1604_04374_gb300 import pce
+    # NULL plan handles are rejected before any CUDA call
+    assert lib.pce_apply(None, None, None, 1, None) == pce.PCE_ERR_INVALID
+    assert b"plan" in lib.pce_last_error_string()
+    assert lib.pce_apply_adjoint(None, None, None, 1, None) == pce.PCE_ERR_INVALID
+    assert lib.pce_plan_destroy(None) == pce.PCE_OK
+    # bad ndims / unsupported size / m < 1, all before any device pointer is touched
+    out = ctypes.c_void_p()
+    shp = (ctypes.c_int64 * 2)(1024, 1024)
+    assert lib.pce_plan_create(ctypes.byref(out), 3, shp, 4, None, None, 0, None) == pce.PCE_ERR_INVALID
+    shp_bad = (ctypes.c_int64 * 2)(1000, 1024)
+    assert lib.pce_plan_create(ctypes.byref(out), 2, shp_bad, 4, None, None, 0, None) == pce.PCE_ERR_UNSUPPORTED
+    shp_big = (ctypes.c_int64 * 1)(1 << 16)
+    assert lib.pce_plan_create(ctypes.byref(out), 1, shp_big, 4, None, None, 0, None) == pce.PCE_ERR_UNSUPPORTED
+    assert lib.pce_plan_create(ctypes.byref(out), 2, shp, 0, None, None, 0, None) == pce.PCE_ERR_INVALID
+    assert lib.pce_plan_create(None, 2, shp, 4, None, None, 0, None) == pce.PCE_ERR_INVALID
+    assert lib.pce_launch_count(None, 0, 8) == 0
