@@ -171,6 +171,42 @@ enum {
 pce_status pce_plan_set_timing(pce_plan_t plan, int enable);
 pce_status pce_plan_timing(pce_plan_t plan, int kind, double* total_ms, int64_t* launches);
 
+/*
+ * pce_apply_noalloc -- y = H_m u like pce_apply, for callers that cannot
+ * allocate device memory (no counterpart in the paper).
+ *
+ * Some callers cannot call cudaMalloc when they apply the operator: code
+ * whose device memory is owned by another allocator (a framework's caching
+ * pool, where a raw cudaMalloc can fail although the pool has room), code
+ * that must not risk the implicit device synchronisation of cudaMalloc, or
+ * code working under a fixed device-memory budget.  pce_apply itself does not
+ * allocate, but it needs the plan's scratch, which is sized for a whole batch
+ * chunk (about 1 GB for a 1024 x 1024, m = 16 plan).  This entry point runs
+ * the same 2D forward kernels with their intermediates in a static block of
+ * 64 MiB of device memory that the library reserves on every device it is
+ * loaded on and keeps until the process exits.  It calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ *
+ *   plan   : a 2D plan (a 1D plan returns PCE_ERR_UNSUPPORTED: the 1D apply
+ *            needs no scratch).
+ *   u, y, batch, stream : as for pce_apply.
+ *
+ * A right-hand side needs (m * nr_max + Ny) * (Nx/2) * 8 bytes of scratch
+ * (nr_max = most rows of a window's support box); a plan that needs more
+ * than 64 MiB per right-hand side returns PCE_ERR_UNSUPPORTED with the
+ * required size in pce_last_error_string().  Larger batches are processed in
+ * chunks that fit.
+ *
+ * The first call on a device looks up the device address of the static
+ * block (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  Every call on a device shares the same
+ * block, which keeps the previous call's contents (nothing needs to start at
+ * zero: every element a kernel reads is written earlier in the same call).
+ * Calls whose work overlaps on the GPU (other streams, other threads, other
+ * plans) race on the block and give wrong results: serialise them.
+ */
+pce_status pce_apply_noalloc(pce_plan_t plan, const float* u, float* y, int64_t batch, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -11,6 +11,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -709,3 +710,101 @@ int64_t pce_launch_count(pce_plan_t plan, int adjoint, int64_t batch) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Forward apply without any allocation (no counterpart in the paper).
+//
+// pce_apply runs the 2D passes on intermediates that the plan allocated with
+// cudaMalloc.  pce_apply_noalloc runs the same three kernels on intermediates
+// held in g_noalloc_scratch, a fixed array of device memory that exists as
+// soon as the library is loaded on a device, so the call itself never
+// allocates.  Host code may not pass g_noalloc_scratch to a kernel directly:
+// in host code the name denotes a host-side shadow, not device memory.  Its
+// device address is looked up once per device with cudaGetSymbolAddress.
+namespace {
+
+constexpr size_t kNoallocScratchBytes = 64ull << 20;   // 64 MiB per device
+constexpr int kNoallocMaxDevices = 64;
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+struct NoallocSlot {
+    bool ready = false;
+    float2* ptr = nullptr;
+};
+NoallocSlot g_noalloc_slots[kNoallocMaxDevices];
+std::mutex g_noalloc_mutex;
+
+// Device address of the static scratch on the current device (first call per device).
+pce_status noalloc_scratch(float2** out) {
+    int dev = 0;
+    PCE_CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoallocMaxDevices)
+        return fail(PCE_ERR_UNSUPPORTED, "device %d is beyond the %d devices the static scratch tracks",
+                    dev, kNoallocMaxDevices);
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    NoallocSlot& slot = g_noalloc_slots[dev];
+    if (!slot.ready) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess)
+            return fail(PCE_ERR_CUDA, "cudaGetSymbolAddress of the static scratch on device %d: %s", dev,
+                        cudaGetErrorString(e));
+        slot.ptr = static_cast<float2*>(p);
+        slot.ready = true;
+    }
+    *out = slot.ptr;
+    return PCE_OK;
+}
+
+}  // namespace
+
+extern "C" pce_status pce_apply_noalloc(pce_plan_t plan, const float* u, float* y, int64_t batch,
+                                        void* stream) {
+    pce_status st = check_plan(plan);
+    if (st) return st;
+    if (plan->ndims != 2)
+        return fail(PCE_ERR_UNSUPPORTED, "pce_apply_noalloc serves 2D plans only (the 1D apply uses no scratch)");
+    if ((st = check_io(plan, u, y, batch))) return st;
+    if (batch == 0) return PCE_OK;
+    const int ny = plan->ny, nx = plan->nx, m = plan->m, nxh = nx / 2;
+    const long long zk = (long long)plan->nrmax * nxh;
+    const long long zb = (long long)m * zk;
+    const long long ab = (long long)ny * nxh;
+    const long long per_b = (zb + ab) * (long long)sizeof(float2);
+    if (per_b > (long long)kNoallocScratchBytes)
+        return fail(PCE_ERR_UNSUPPORTED,
+                    "pce_apply_noalloc: this plan needs %lld bytes of scratch per right-hand side, "
+                    "more than the %llu bytes of static scratch",
+                    per_b, (unsigned long long)kNoallocScratchBytes);
+    float2* base = nullptr;
+    if ((st = noalloc_scratch(&base))) return st;
+    const int chunk = (int)std::min<long long>(kNoallocScratchBytes / per_b, 65535);
+    float2* scrZ = base;
+    float2* scrA = base + zb * chunk;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const long long P = (long long)ny * nx;
+    const float scale = 1.0f / (float)P;
+    const int fpc = pce::rows_pairs_per_cta(nx);
+    const int cpc = pce::cols_columns_per_cta(ny);
+    const int npairs = (ny + 1) / 2;
+    cudaError_t e = cudaSuccess;
+    // Every scratch element a kernel reads is written earlier in the same call
+    // (Z rows inside the boxes by the row pass, all of A by the column pass),
+    // so nothing left by a previous call needs clearing.
+    for (long long b0 = 0; b0 < batch && e == cudaSuccess; b0 += chunk) {
+        const int nb = (int)std::min<long long>(chunk, batch - b0);
+        if (plan->nitems > 0)
+            e = pce::launch_rows_r2c(nx, true, dim3((plan->nitems + fpc - 1) / fpc, nb), s, u + b0 * P, P,
+                                     ny, plan->wbox, plan->d_box, plan->items, plan->nitems, scrZ, zb, zk,
+                                     plan->twx);
+        if (e == cudaSuccess)
+            e = pce::launch_cols_fwd(ny, dim3((nxh + cpc - 1) / cpc, nb), s, scrZ, zb, zk, plan->hh,
+                                     plan->hN, m, plan->d_box, nxh, scrA, ab, plan->twy);
+        if (e == cudaSuccess)
+            e = pce::launch_rows_c2r(nx, dim3((npairs + fpc - 1) / fpc, nb), s, scrA, ab, ny, y + b0 * P, P,
+                                     scale, plan->twx);
+    }
+    if (e) return fail(PCE_ERR_CUDA, "pce_apply_noalloc launch: %s", cudaGetErrorString(e));
+    return PCE_OK;
+}

@@ -49,6 +49,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.pce_last_error_string.argtypes = []
     lib.pce_launch_count.argtypes = [P, ctypes.c_int, i64]
     lib.pce_launch_count.restype = i64
+    lib.pce_apply_noalloc.argtypes = [P, P, P, i64, P]
+    lib.pce_apply_noalloc.restype = ctypes.c_int
     lib.pce_plan_set_timing.argtypes = [P, ctypes.c_int]
     lib.pce_plan_timing.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                     ctypes.POINTER(i64)]
@@ -93,6 +95,11 @@ def pce_apply(plan: int, u_ptr: int, y_ptr: int, batch: int, stream: int = 0) ->
 
 def pce_apply_adjoint(plan: int, v_ptr: int, x_ptr: int, batch: int, stream: int = 0) -> None:
     _check(load_library().pce_apply_adjoint(plan, v_ptr, x_ptr, batch, stream))
+
+
+def pce_apply_noalloc(plan: int, u_ptr: int, y_ptr: int, batch: int, stream: int = 0) -> None:
+    """y = H_m u on a 2D plan with the intermediates in the library's static device scratch."""
+    _check(load_library().pce_apply_noalloc(plan, u_ptr, y_ptr, batch, stream))
 
 
 def pce_plan_info(plan: int, m: int):
