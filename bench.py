@@ -224,6 +224,24 @@ def reference_arm(args, pr: synth.Problem, rank: int) -> None:
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------ rank combining
+
+def max_over_ranks(value_ms: float, dist=None, device=None) -> float:
+    """Max of a per-rank time over all ranks (identity without a process group)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value_ms)
+    import torch
+    t = torch.tensor([float(value_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(batch_per_rank: int, steps: int, world: int, max_ms: float) -> float:
+    """Whole-job applies/s: every rank applies forward + adjoint to its own batch each
+    step; the job takes the slowest rank's time."""
+    return 2.0 * batch_per_rank * steps * world / (max_ms / 1000.0)
+
+
 # ------------------------------------------------------------------- GPU arm
 
 def gpu_arm(args, pr: synth.Problem, rank: int, world: int) -> None:
@@ -282,13 +300,37 @@ def gpu_arm(args, pr: synth.Problem, rank: int, world: int) -> None:
     kern = plan.timing()
     plan.set_timing(False)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    dev_ms = sum(step_ms)
+    dev_ms = max_over_ranks(sum(step_ms), dist, dev)
     if dist:
-        t = torch.tensor([dev_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev_ms = float(t.item())
         dist.barrier()
     launches_per_step = plan.launch_count(False, B) + plan.launch_count(True, B)
+
+    # comparator: the plain unfused FP32 per-term pipeline on the same inputs
+    comparator = None
+    if args.comparator:
+        from paper_1604_04374_gb300.pce import PCE_FLAG_UNFUSED
+        plain = Plan(torch.from_numpy(pr.w).to(dev), h=torch.from_numpy(pr.h).to(dev), flags=PCE_FLAG_UNFUSED)
+
+        def plain_step():
+            plain.apply(u, out=y)
+            plain.apply_adjoint(u, out=x)
+
+        for _ in range(args.warmup):
+            plain_step()
+        torch.cuda.synchronize()
+        cms = 0.0
+        for i in range(args.steps):
+            flush.zero_()
+            starts[i].record(stream)
+            plain_step()
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+        cms = max_over_ranks(sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)), dist, dev)
+        comparator = {"impl": "plain unfused FP32 per-term pipeline (PCE_FLAG_UNFUSED), same FFT core",
+                      "value": weak_scaling_value(B, args.steps, world, cms), "unit": UNIT,
+                      "ms_per_step": cms / args.steps,
+                      "launches_per_step": plain.launch_count(False, B) + plain.launch_count(True, B)}
+        plain.close()
 
     # end to end: pinned host input -> device -> forward + adjoint -> host outputs
     u_host = torch.from_numpy(pr.u).pin_memory()
@@ -313,16 +355,11 @@ def gpu_arm(args, pr: synth.Problem, rank: int, world: int) -> None:
         e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
 
     if rank == 0:
-        applies = 2.0 * B * args.steps * world
-        value = applies / (dev_ms / 1000.0)
-        e2e_value = applies / (e2e_ms / 1000.0)
+        value = weak_scaling_value(B, args.steps, world, dev_ms)
+        e2e_value = weak_scaling_value(B, args.steps, world, e2e_ms)
         clocks = sampler.summary() if sampler else {}
         sm_max = clocks.get("sm_max_mhz") or 2070.0
         # FP32 ALU peak from unit counts and clock: SMs x 128 lanes x 2 (FMA) x max SM clock
@@ -368,6 +405,7 @@ def gpu_arm(args, pr: synth.Problem, rank: int, world: int) -> None:
                          "peak_gbs": hbm_peak, "peak_source": hbm_src,
                          "frac": pbytes * args.steps / (dev_ms / 1000.0) / 1e9 / hbm_peak},
             "kernels": kernels,
+            "comparator": dict(comparator, speedup=value / comparator["value"]) if comparator else None,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": B * P * 4,
                     "d2h_bytes_per_step": 2 * B * P * 4},
             "gpu_launches": launches_per_step * args.steps,
@@ -401,6 +439,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--ref-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-comparator", dest="comparator", action="store_false")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

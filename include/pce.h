@@ -62,6 +62,16 @@ typedef struct pce_plan* pce_plan_t;
 
 /* Plan flags. */
 #define PCE_FLAG_NONE 0u
+/*
+ * PCE_FLAG_UNFUSED: applies on this plan run the plain unfused per-term
+ * pipeline instead of the fused kernels (2D plans; 1D plans ignore it).  For
+ * every term: a window kernel writes w_k . u to memory, a full 2D R2C (row
+ * pass, column pass) writes its spectrum to memory, a kernel multiplies it by
+ * hhat_k and accumulates; one inverse 2D FFT ends the forward apply (the
+ * adjoint mirrors this).  It computes the same operator with the same FFT
+ * core and exists as the baseline the fused path is measured against.
+ */
+#define PCE_FLAG_UNFUSED 1u
 
 /*
  * pce_plan_create -- precompute everything an operator needs (Eq. 1.4).
@@ -72,7 +82,7 @@ typedef struct pce_plan* pce_plan_t;
  *   m      : number of terms.
  *   w      : device, [m][shape] float32 windows w_k.
  *   h      : device, [m][shape] float32 impulse responses h_k, origin at index 0.
- *   flags  : PCE_FLAG_NONE.
+ *   flags  : PCE_FLAG_NONE or PCE_FLAG_UNFUSED; other bits return PCE_ERR_INVALID.
  *   stream : cudaStream_t used for the set-up work.
  *
  * The plan finds the support box of every w_k (the smallest periodic
@@ -166,7 +176,8 @@ enum {
     PCE_KERNEL_ROWS_ADJ = 5,         /* adjoint row C2R, window, accumulate (2D) */
     PCE_KERNEL_FWD_1D = 6,           /* 1D forward, one CTA per right-hand side */
     PCE_KERNEL_ADJ_1D = 7,           /* 1D adjoint, one CTA per right-hand side */
-    PCE_KERNEL_KINDS = 8
+    PCE_KERNEL_PLAIN = 8,            /* any kernel of the unfused pipeline (PCE_FLAG_UNFUSED) */
+    PCE_KERNEL_KINDS = 9
 };
 pce_status pce_plan_set_timing(pce_plan_t plan, int enable);
 pce_status pce_plan_timing(pce_plan_t plan, int kind, double* total_ms, int64_t* launches);

@@ -42,7 +42,10 @@ cudaError_t prepare_cols() {
                                  ColCfg<N>::SMEM);                                             \
     if (e == cudaSuccess)                                                                      \
         e = cudaFuncSetAttribute(k_cols_spec<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
-                                 ColCfg<N>::SMEM);
+                                 ColCfg<N>::SMEM);                                             \
+    if (e == cudaSuccess)                                                                      \
+        e = cudaFuncSetAttribute(k_plain_cols_inv<N>,                                          \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, ColCfg<N>::SMEM);
     PCE_COL_SIZES(X)
 #undef X
     return e;
@@ -91,6 +94,21 @@ cudaError_t launch_cols_spec(int ny, dim3 grid, cudaStream_t s, const float2* S,
 #define X(N)                                                                                   \
     case N:                                                                                    \
         k_cols_spec<N><<<grid, ColCfg<N>::NT, ColCfg<N>::SMEM, s>>>(S, nxh, hh, hN, tw);        \
+        break;
+        PCE_COL_SIZES(X)
+#undef X
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_plain_cols_inv(int ny, dim3 grid, cudaStream_t s, const float2* acc,
+                                  const float2* accN, int nxh, float2* A, const float2* tw) {
+    switch (ny) {
+#define X(N)                                                                                   \
+    case N:                                                                                    \
+        k_plain_cols_inv<N><<<grid, ColCfg<N>::NT, ColCfg<N>::SMEM, s>>>(acc, accN, nxh, A, tw); \
         break;
         PCE_COL_SIZES(X)
 #undef X

@@ -10,8 +10,10 @@
 // current sub-transform length Ns: butterfly j' reads x[j' + q N/Rs], applies
 // the twiddles W_{Ns Rs}^{q k} (k = j' mod Ns) and writes
 // y[(j'/Ns) Ns Rs + k + q Ns].  Between stages data goes through a padded
-// shared-memory buffer (one float2 of padding per 8, which keeps the strided
-// writes of the first stages free of bank conflicts).
+// shared-memory buffer: one float2 of padding per 16, so that every write
+// and read pattern of the stages touches each 8-byte bank pair exactly twice
+// per warp (two wavefronts, the minimum for 64-bit accesses), also when one
+// warp spans several FFTs whose buffers are staggered by 4 float2.
 //
 // Twiddles come from a per-N table generated once per plan in FP64 and
 // rounded to FP32 (layout: per stage s >= 1, entries [q-1][k] =
@@ -29,8 +31,11 @@ constexpr int kR = 8;   // elements per thread
 
 __host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n >> 1); }
 
-__device__ __forceinline__ int padi(int i) { return i + (i >> 3); }
-__host__ __device__ constexpr int pad_len(int n) { return n + (n >> 3); }
+__device__ __forceinline__ int padi(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int pad_len(int n) { return n + (n >> 4); }
+// Shared-memory float2 count of one FFT's two buffers plus the skew that
+// staggers neighbouring FFTs by 32 bytes (8 banks).
+__host__ __device__ constexpr int fft_region(int n) { return 2 * pad_len(n) + 4; }
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
@@ -141,7 +146,7 @@ struct FftPlan {
     static_assert((N & (N - 1)) == 0, "FFT length must be a power of two");
 };
 
-// One Stockham stage.  buf: this FFT's shared buffer (pad_len(N) float2).
+// One Stockham stage.  buf: one of this FFT's two shared buffers (pad_len(N) float2).
 template <int N, int S, bool INV>
 __device__ __forceinline__ void fft_stage(float2 (&v)[kR], int j, float2* buf,
                                           const float2* __restrict__ tw) {
@@ -170,15 +175,32 @@ __device__ __forceinline__ void fft_stage(float2 (&v)[kR], int j, float2* buf,
 #pragma unroll
             for (int q = 0; q < RS; ++q) v[i + q * G] = a[q];
         } else {
+            // padded address of base + q NS, strength-reduced: the low four bits
+            // of base + q NS only come from k (NS >= 16), from k < 8 plus 8 q
+            // (NS = 8), or from q < 8 on base = 8 jp (NS = 1)
             const int base = (jp / NS) * NS * RS + k;
+            const int pb = padi(base);
 #pragma unroll
-            for (int q = 0; q < RS; ++q) buf[padi(base + q * NS)] = a[q];
+            for (int q = 0; q < RS; ++q) {
+                int addr;
+                if constexpr (NS >= 16) addr = pb + q * (NS + NS / 16);
+                else if constexpr (NS == 8) addr = pb + 8 * q + (q >> 1);
+                else if constexpr (NS == 1 && RS == kR) addr = pb + q;
+                else addr = padi(base + q * NS);
+                buf[addr] = a[q];
+            }
         }
     }
     if (!LAST) {
         __syncthreads();
+        if constexpr (T % 16 == 0) {
+            const int pj = padi(j);
 #pragma unroll
-        for (int r = 0; r < kR; ++r) v[r] = buf[padi(j + r * T)];
+            for (int r = 0; r < kR; ++r) v[r] = buf[pj + r * (T + T / 16)];
+        } else {
+#pragma unroll
+            for (int r = 0; r < kR; ++r) v[r] = buf[padi(j + r * T)];
+        }
     }
 }
 

@@ -35,7 +35,8 @@ struct Box {          // periodic support box of w_k and its compacted copy
     int pad_;
 };
 
-__device__ __forceinline__ int wrap(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+// i mod n for a power of two n (two's complement: also for negative i)
+__device__ __forceinline__ int wrap(int i, int n) { return i & (n - 1); }
 
 // ---------------------------------------------------------------- rows R2C
 // Real rows -> packed half spectra, two rows per complex FFT.
@@ -52,9 +53,11 @@ k_rows_r2c(const float* __restrict__ src, long long src_bstride, int nrows,
     constexpr int T = NX / kR;
     constexpr int FPC = 256 / T;
     constexpr int NXh = NX / 2;
-    __shared__ float2 sbuf[FPC][2][pad_len(NX)];
+    __shared__ float2 sbuf[FPC * fft_region(NX)];
     const int slot = threadIdx.x / T;
     const int j = threadIdx.x - slot * T;
+    float2* b0 = sbuf + slot * fft_region(NX);
+    float2* b1 = b0 + pad_len(NX);
     const int item = blockIdx.x * FPC + slot;
     const int b = blockIdx.y;
     const bool active = item < nitems;
@@ -70,8 +73,8 @@ k_rows_r2c(const float* __restrict__ src, long long src_bstride, int nrows,
         lb = la + 1;
         va = active && la < bx.nr;
         vb = active && lb < bx.nr;
-        ra = (bx.r0 + la) % nrows;
-        rb = (bx.r0 + lb) % nrows;
+        ra = wrap(bx.r0 + la, nrows);
+        rb = wrap(bx.r0 + lb, nrows);
     } else {
         la = 2 * item;
         lb = la + 1;
@@ -101,10 +104,10 @@ k_rows_r2c(const float* __restrict__ src, long long src_bstride, int nrows,
         }
         v[r] = make_float2(xa, xb);
     }
-    fft<NX, false>(v, j, sbuf[slot][0], sbuf[slot][1], tw);
+    fft<NX, false>(v, j, b0, b1, tw);
 
     // split the spectra of the two real rows
-    float2* xs = sbuf[slot][0];
+    float2* xs = b0;
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < kR; ++r) xs[padi(j + r * T)] = v[r];
@@ -150,9 +153,11 @@ k_rows_c2r(const float2* __restrict__ src, long long src_bstride, int nrows,
     constexpr int T = NX / kR;
     constexpr int FPC = 256 / T;
     constexpr int NXh = NX / 2;
-    __shared__ float2 sbuf[FPC][2][pad_len(NX)];
+    __shared__ float2 sbuf[FPC * fft_region(NX)];
     const int slot = threadIdx.x / T;
     const int j = threadIdx.x - slot * T;
+    float2* b0 = sbuf + slot * fft_region(NX);
+    float2* b1 = b0 + pad_len(NX);
     const int p = blockIdx.x * FPC + slot;
     const int b = blockIdx.y;
     const int la = 2 * p, lb = la + 1;
@@ -167,7 +172,7 @@ k_rows_c2r(const float2* __restrict__ src, long long src_bstride, int nrows,
         const float2 xb = vb ? load_half<NX>(pb, f) : make_float2(0.f, 0.f);
         v[r] = make_float2(xa.x - xb.y, xa.y + xb.x);
     }
-    fft<NX, true>(v, j, sbuf[slot][0], sbuf[slot][1], tw);
+    fft<NX, true>(v, j, b0, b1, tw);
     float* ya = dst + b * dst_bstride + (long long)la * NX;
     float* yb = dst + b * dst_bstride + (long long)lb * NX;
 #pragma unroll
@@ -191,9 +196,11 @@ k_rows_adj(const float2* __restrict__ Q, long long q_bstride, long long q_kstrid
     constexpr int T = NX / kR;
     constexpr int FPC = 256 / T;
     constexpr int NXh = NX / 2;
-    __shared__ float2 sbuf[FPC][2][pad_len(NX)];
+    __shared__ float2 sbuf[FPC * fft_region(NX)];
     const int slot = threadIdx.x / T;
     const int j = threadIdx.x - slot * T;
+    float2* b0 = sbuf + slot * fft_region(NX);
+    float2* b1 = b0 + pad_len(NX);
     const int npairs = (nrows + 1) / 2;
     const int p = blockIdx.x * FPC + slot;
     const int b = blockIdx.y;
@@ -231,7 +238,7 @@ k_rows_adj(const float2* __restrict__ Q, long long q_bstride, long long q_kstrid
             const float2 xb = vb ? load_half<NX>(pb, f) : make_float2(0.f, 0.f);
             v[r] = make_float2(xa.x - xb.y, xa.y + xb.x);
         }
-        fft<NX, true>(v, j, sbuf[slot][0], sbuf[slot][1], tw);
+        fft<NX, true>(v, j, b0, b1, tw);
         const float* wr = wbox + bx.woff;
 #pragma unroll
         for (int r = 0; r < kR; ++r) {
@@ -254,12 +261,18 @@ k_rows_adj(const float2* __restrict__ Q, long long q_bstride, long long q_kstrid
 }
 
 // ------------------------------------------------------------ column passes
+// CTA = C columns x T threads; thread (j, c) = threadIdx (j * C + c), so a
+// warp reads C consecutive columns of 8 rows (32-byte segments for C = 4).
+// Each column owns two FFT buffers; consecutive columns' buffers are skewed
+// by 4 float2 (32 bytes) so that the C columns of a warp fall on distinct
+// shared-memory banks.
 template <int NY>
 struct ColCfg {
     static constexpr int T = NY / kR;
-    static constexpr int C = (4 * T >= 128) ? 4 : 128 / T;   // columns per CTA
+    static constexpr int C = (4 * T >= 128) ? (T >= 256 ? 2 : 4) : 128 / T;   // columns per CTA
     static constexpr int NT = T * C;                          // threads per CTA
-    static constexpr int SMEM = (C * 2 + 1) * pad_len(NY) * (int)sizeof(float2);
+    static constexpr int CS = fft_region(NY);                 // per-column region (float2)
+    static constexpr int SMEM = (C * CS + pad_len(NY)) * (int)sizeof(float2);
 };
 
 // Separate the column FFT Z of (DC + i Nyquist) at frequency f.
@@ -268,8 +281,22 @@ __device__ __forceinline__ void split_dc_nyq(float2 z, float2 zm, float2& A, flo
     B = make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
 }
 
-// F2: forward column pass.  Grid (NXh / C, batch).  hh: [m][NY][NXh] (column
-// 0 = DC column spectrum), hN: [m][NY] (Nyquist column spectrum).
+template <int NY>
+__device__ __forceinline__ void load_col(float2 (&v)[kR], const float2* __restrict__ Zk, const Box& bx,
+                                         int j, int col, int nxh, bool cv) {
+    constexpr int T = NY / kR;
+#pragma unroll
+    for (int r = 0; r < kR; ++r) {
+        const int i = wrap(j + r * T - bx.r0, NY);
+        v[r] = (cv && i < bx.nr) ? __ldg(&Zk[(long long)i * nxh + col]) : make_float2(0.f, 0.f);
+    }
+}
+
+// F2: forward column pass.  Grid (batch, NXh / C): the right-hand sides of a
+// column tile are neighbours in launch order and share hhat_k through L2.
+// hh: [m][NY][NXh] (column 0 = DC column spectrum), hN: [m][NY] (Nyquist).
+// The next term's Z column and this term's spectrum are loaded before the
+// FFT so that their latency overlaps it.
 template <int NY>
 __global__ void __launch_bounds__(ColCfg<NY>::NT)
 k_cols_fwd(const float2* __restrict__ Z, long long z_bstride, long long z_kstride,
@@ -282,31 +309,56 @@ k_cols_fwd(const float2* __restrict__ Z, long long z_bstride, long long z_kstrid
     extern __shared__ float2 smem[];
     const int c = threadIdx.x % C;
     const int j = threadIdx.x / C;
-    float2* b0 = smem + (2 * c) * pad_len(NY);
+    float2* b0 = smem + c * CC::CS;
     float2* b1 = b0 + pad_len(NY);
-    float2* xbuf = smem + 2 * C * pad_len(NY);
-    const int col = blockIdx.x * C + c;
+    float2* xbuf = smem + C * CC::CS;
+    const int b = blockIdx.x;
+    const int tile = blockIdx.y;
+    const int col = tile * C + c;
     const bool cv = col < NXh;
-    const int b = blockIdx.y;
-    const bool tile0 = blockIdx.x == 0;
+    const bool tile0 = tile == 0;
     const bool dcn = tile0 && c == 0;
+    const float2* Zb = Z + b * z_bstride;
 
     float2 acc[kR];
 #pragma unroll
     for (int r = 0; r < kR; ++r) acc[r] = make_float2(0.f, 0.f);
 
-    for (int k = 0; k < m; ++k) {
-        const Box bx = box[k];
-        if (bx.nr == 0) continue;
-        const float2* Zk = Z + b * z_bstride + k * z_kstride;
-        float2 v[kR];
+    // first term with a nonempty box
+    int k = 0;
+    while (k < m && box[k].nr == 0) ++k;
+    if (k >= m) {
+        // every window is zero: the output spectrum is zero
+        fft<NY, true>(acc, j, b0, b1, tw);
+        if (cv) {
+            float2* Ab = A + b * a_bstride;
 #pragma unroll
-        for (int r = 0; r < kR; ++r) {
-            const int i = wrap(j + r * T - bx.r0, NY);
-            v[r] = (cv && i < bx.nr) ? __ldg(&Zk[(long long)i * NXh + col]) : make_float2(0.f, 0.f);
+            for (int r = 0; r < kR; ++r) Ab[(long long)(j + r * T) * NXh + col] = acc[r];
+        }
+        return;
+    }
+    Box bx = box[k];
+    float2 v[kR];
+    load_col<NY>(v, Zb + k * z_kstride, bx, j, col, NXh, cv);
+
+    while (k < m) {
+        // next term with a nonempty box
+        int kn = k + 1;
+        while (kn < m && box[kn].nr == 0) ++kn;
+        // spectrum of term k at this thread's frequencies
+        const float2* hk = hh + (long long)k * NY * NXh;
+        float2 hv[kR];
+#pragma unroll
+        for (int r = 0; r < kR; ++r)
+            hv[r] = cv ? __ldg(&hk[(long long)(j + r * T) * NXh + col]) : make_float2(0.f, 0.f);
+        // Z column of the next term
+        float2 zn[kR];
+        Box bn = bx;
+        if (kn < m) {
+            bn = box[kn];
+            load_col<NY>(zn, Zb + kn * z_kstride, bn, j, col, NXh, cv);
         }
         fft<NY, false>(v, j, b0, b1, tw);
-        const float2* hk = hh + (long long)k * NY * NXh;
         if (tile0) {
             if (dcn) {
 #pragma unroll
@@ -320,18 +372,21 @@ k_cols_fwd(const float2* __restrict__ Z, long long z_bstride, long long z_kstrid
                 const int f = j + r * T;
                 float2 a, bb;
                 split_dc_nyq(v[r], xbuf[padi((NY - f) & (NY - 1))], a, bb);
-                acc[r] = cfma(__ldg(&hk[(long long)f * NXh]), a, acc[r]);
+                acc[r] = cfma(hv[r], a, acc[r]);
                 const float2 t = cmul(__ldg(&hN[(long long)k * NY + f]), bb);
                 acc[r].x -= t.y;
                 acc[r].y += t.x;
             }
-        } else if (cv) {
+        } else {
 #pragma unroll
-            for (int r = 0; r < kR; ++r) {
-                const int f = j + r * T;
-                acc[r] = cfma(__ldg(&hk[(long long)f * NXh + col]), v[r], acc[r]);
-            }
+            for (int r = 0; r < kR; ++r) acc[r] = cfma(hv[r], v[r], acc[r]);
         }
+        if (kn < m) {
+#pragma unroll
+            for (int r = 0; r < kR; ++r) v[r] = zn[r];
+        }
+        k = kn;
+        bx = bn;
     }
     fft<NY, true>(acc, j, b0, b1, tw);
     if (cv) {
@@ -343,6 +398,8 @@ k_cols_fwd(const float2* __restrict__ Z, long long z_bstride, long long z_kstrid
 
 // G1b + G2: adjoint column pass.  Column FFT of V once; per k the product
 // with conj(hhat_k), an inverse column FFT, and a store of the box rows only.
+// Grid (batch, NXh / C).  The next term's spectrum is loaded before the
+// current inverse FFT.
 template <int NY>
 __global__ void __launch_bounds__(ColCfg<NY>::NT)
 k_cols_adj(const float2* __restrict__ V, long long v_bstride,
@@ -356,13 +413,14 @@ k_cols_adj(const float2* __restrict__ V, long long v_bstride,
     extern __shared__ float2 smem[];
     const int c = threadIdx.x % C;
     const int j = threadIdx.x / C;
-    float2* b0 = smem + (2 * c) * pad_len(NY);
+    float2* b0 = smem + c * CC::CS;
     float2* b1 = b0 + pad_len(NY);
-    float2* xbuf = smem + 2 * C * pad_len(NY);
-    const int col = blockIdx.x * C + c;
+    float2* xbuf = smem + C * CC::CS;
+    const int b = blockIdx.x;
+    const int tile = blockIdx.y;
+    const int col = tile * C + c;
     const bool cv = col < NXh;
-    const int b = blockIdx.y;
-    const bool tile0 = blockIdx.x == 0;
+    const bool tile0 = tile == 0;
     const bool dcn = tile0 && c == 0;
 
     float2 vv[kR];
@@ -370,6 +428,15 @@ k_cols_adj(const float2* __restrict__ V, long long v_bstride,
 #pragma unroll
     for (int r = 0; r < kR; ++r)
         vv[r] = cv ? __ldg(&Vb[(long long)(j + r * T) * NXh + col]) : make_float2(0.f, 0.f);
+    int k = 0;
+    while (k < m && box[k].nr == 0) ++k;
+    float2 hv[kR];
+    if (k < m) {
+        const float2* hk = hh + (long long)k * NY * NXh;
+#pragma unroll
+        for (int r = 0; r < kR; ++r)
+            hv[r] = cv ? __ldg(&hk[(long long)(j + r * T) * NXh + col]) : make_float2(0.f, 0.f);
+    }
     fft<NY, false>(vv, j, b0, b1, tw);
     if (tile0) {
         if (dcn) {
@@ -378,10 +445,10 @@ k_cols_adj(const float2* __restrict__ V, long long v_bstride,
         }
         __syncthreads();
     }
-    for (int k = 0; k < m; ++k) {
+    while (k < m) {
+        int kn = k + 1;
+        while (kn < m && box[kn].nr == 0) ++kn;
         const Box bx = box[k];
-        if (bx.nr == 0) continue;
-        const float2* hk = hh + (long long)k * NY * NXh;
         float2 p[kR];
 #pragma unroll
         for (int r = 0; r < kR; ++r) {
@@ -389,14 +456,20 @@ k_cols_adj(const float2* __restrict__ V, long long v_bstride,
             if (dcn) {
                 float2 a, bb;
                 split_dc_nyq(vv[r], xbuf[padi((NY - f) & (NY - 1))], a, bb);
-                float2 t = cmulc(a, __ldg(&hk[(long long)f * NXh]));
+                float2 t = cmulc(a, hv[r]);
                 const float2 s = cmulc(bb, __ldg(&hN[(long long)k * NY + f]));
                 t.x -= s.y;
                 t.y += s.x;
                 p[r] = t;
             } else {
-                p[r] = cv ? cmulc(vv[r], __ldg(&hk[(long long)f * NXh + col])) : make_float2(0.f, 0.f);
+                p[r] = cmulc(vv[r], hv[r]);
             }
+        }
+        if (kn < m) {
+            const float2* hk = hh + (long long)kn * NY * NXh;
+#pragma unroll
+            for (int r = 0; r < kR; ++r)
+                hv[r] = cv ? __ldg(&hk[(long long)(j + r * T) * NXh + col]) : make_float2(0.f, 0.f);
         }
         fft<NY, true>(p, j, b0, b1, tw);
         if (cv) {
@@ -407,11 +480,12 @@ k_cols_adj(const float2* __restrict__ V, long long v_bstride,
                 if (i < bx.nr) Qk[(long long)i * NXh + col] = p[r];
             }
         }
+        k = kn;
     }
 }
 
 // Plan: column FFT of the row spectra of h_k -> hh (column 0 = DC column
-// spectrum) and hN (Nyquist column spectrum).  Grid (NXh / C, m).
+// spectrum) and hN (Nyquist column spectrum).  Grid (m, NXh / C).
 template <int NY>
 __global__ void __launch_bounds__(ColCfg<NY>::NT)
 k_cols_spec(const float2* __restrict__ S, int NXh, float2* __restrict__ hh,
@@ -422,13 +496,14 @@ k_cols_spec(const float2* __restrict__ S, int NXh, float2* __restrict__ hh,
     extern __shared__ float2 smem[];
     const int c = threadIdx.x % C;
     const int j = threadIdx.x / C;
-    float2* b0 = smem + (2 * c) * pad_len(NY);
+    float2* b0 = smem + c * CC::CS;
     float2* b1 = b0 + pad_len(NY);
-    float2* xbuf = smem + 2 * C * pad_len(NY);
-    const int col = blockIdx.x * C + c;
+    float2* xbuf = smem + C * CC::CS;
+    const int k = blockIdx.x;
+    const int tile = blockIdx.y;
+    const int col = tile * C + c;
     const bool cv = col < NXh;
-    const int k = blockIdx.y;
-    const bool tile0 = blockIdx.x == 0;
+    const bool tile0 = tile == 0;
     const bool dcn = tile0 && c == 0;
     const float2* Sk = S + (long long)k * NY * NXh;
     float2 v[kR];
@@ -458,13 +533,56 @@ k_cols_spec(const float2* __restrict__ S, int NXh, float2* __restrict__ hh,
     }
 }
 
+// ------------------------------------------- plain unfused per-term path
+// The comparator the fused kernels are measured against: for every term a
+// window kernel, a full 2D R2C (row pass + column pass), and a spectral
+// multiply-accumulate, each through global memory, then one inverse.
+
+// Inverse column FFT from the [nb][ny][nxh] + Nyquist layout to packed row
+// spectra A[nb][ny][nxh] (column 0 = IFFT(DC + i Nyquist)).  Grid (nb, NXh / C).
+template <int NY>
+__global__ void __launch_bounds__(ColCfg<NY>::NT)
+k_plain_cols_inv(const float2* __restrict__ acc, const float2* __restrict__ accN, int NXh,
+                 float2* __restrict__ A, const float2* __restrict__ tw) {
+    using CC = ColCfg<NY>;
+    constexpr int T = CC::T;
+    constexpr int C = CC::C;
+    extern __shared__ float2 smem[];
+    const int c = threadIdx.x % C;
+    const int j = threadIdx.x / C;
+    float2* b0 = smem + c * CC::CS;
+    float2* b1 = b0 + pad_len(NY);
+    const int b = blockIdx.x;
+    const int col = blockIdx.y * C + c;
+    const bool cv = col < NXh;
+    const float2* ab = acc + (long long)b * NY * NXh;
+    float2 v[kR];
+#pragma unroll
+    for (int r = 0; r < kR; ++r) {
+        const int f = j + r * T;
+        float2 x = cv ? ab[(long long)f * NXh + col] : make_float2(0.f, 0.f);
+        if (col == 0) {
+            const float2 n = accN[(long long)b * NY + f];
+            x.x -= n.y;
+            x.y += n.x;
+        }
+        v[r] = x;
+    }
+    fft<NY, true>(v, j, b0, b1, tw);
+    if (cv) {
+        float2* Ab = A + (long long)b * NY * NXh;
+#pragma unroll
+        for (int r = 0; r < kR; ++r) Ab[(long long)(j + r * T) * NXh + col] = v[r];
+    }
+}
+
 // ------------------------------------------------------------------- 1D
 template <int N>
 struct Cfg1d {
     static constexpr int T = N / kR;
     static constexpr int G = (256 / T) > 0 ? (256 / T) : 1;   // FFT slots per CTA
     static constexpr int NT = T * G;
-    static constexpr int SMEM = G * 2 * pad_len(N) * (int)sizeof(float2);
+    static constexpr int SMEM = G * fft_region(N) * (int)sizeof(float2);
 };
 
 // y_b = (1/N) C2R( sum_k hhat_k . R2C(w_k . u_b) ).  One CTA per b; each
@@ -483,7 +601,7 @@ k_fwd_1d(const float* __restrict__ u, const float* __restrict__ w,
     extern __shared__ float2 smem[];
     const int slot = threadIdx.x / T;
     const int j = threadIdx.x - slot * T;
-    float2* b0 = smem + (2 * slot) * pad_len(N);
+    float2* b0 = smem + slot * fft_region(N);
     float2* b1 = b0 + pad_len(N);
     const int b = blockIdx.x;
     const float* ub = u + (long long)b * N;
@@ -548,7 +666,7 @@ k_fwd_1d(const float* __restrict__ u, const float* __restrict__ w,
 #pragma unroll
         for (int r = 0; r < kR / 2; ++r) {
             float2 s = smem[j + r * T];
-            for (int g = 1; g < G; ++g) s = cadd(s, smem[(2 * g) * pad_len(N) + j + r * T]);
+            for (int g = 1; g < G; ++g) s = cadd(s, smem[g * fft_region(N) + j + r * T]);
             red[j + r * T] = s;
         }
     }
@@ -580,7 +698,7 @@ k_adj_1d(const float* __restrict__ vin, const float* __restrict__ w,
     extern __shared__ float2 smem[];
     const int slot = threadIdx.x / T;
     const int j = threadIdx.x - slot * T;
-    float2* b0 = smem + (2 * slot) * pad_len(N);
+    float2* b0 = smem + slot * fft_region(N);
     float2* b1 = b0 + pad_len(N);
     const int b = blockIdx.x;
     const float* vb = vin + (long long)b * N;
@@ -633,7 +751,7 @@ k_adj_1d(const float* __restrict__ vin, const float* __restrict__ w,
         for (int r = 0; r < kR; ++r) {
             float s = fb[j + r * T];
             for (int g = 1; g < G; ++g)
-                s += reinterpret_cast<const float*>(smem + (2 * g) * pad_len(N))[j + r * T];
+                s += reinterpret_cast<const float*>(smem + g * fft_region(N))[j + r * T];
             xb[j + r * T] = s * scale;
         }
     }
@@ -652,7 +770,7 @@ k_spec_1d(const float* __restrict__ h, int m, float2* __restrict__ hp,
     extern __shared__ float2 smem[];
     const int slot = threadIdx.x / T;
     const int j = threadIdx.x - slot * T;
-    float2* b0 = smem + (2 * slot) * pad_len(N);
+    float2* b0 = smem + slot * fft_region(N);
     float2* b1 = b0 + pad_len(N);
     const int pr = blockIdx.x * G + slot;
     const int k0 = 2 * pr, k1 = k0 + 1;

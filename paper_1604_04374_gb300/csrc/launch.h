@@ -49,6 +49,9 @@ cudaError_t launch_cols_adj(int ny, dim3 grid, cudaStream_t s, const float2* V, 
 cudaError_t launch_cols_spec(int ny, dim3 grid, cudaStream_t s, const float2* S, int nxh,
                              float2* hh, float2* hN, const float2* tw);
 
+cudaError_t launch_plain_cols_inv(int ny, dim3 grid, cudaStream_t s, const float2* acc,
+                                  const float2* accN, int nxh, float2* A, const float2* tw);
+
 cudaError_t launch_fwd_1d(int n, int batch, cudaStream_t s, const float* u, const float* w,
                           const float2* hp, int m, float* y, float scale, const float2* tw);
 

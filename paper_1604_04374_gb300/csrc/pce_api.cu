@@ -185,6 +185,68 @@ __global__ void k_to_half1d(const float2* __restrict__ hp, int m, int nh, float2
     }
 }
 
+// ----- kernels of the plain unfused per-term pipeline (PCE_FLAG_UNFUSED)
+// tmp[b] = w_k . u_b on the whole grid (zero outside w_k's box).  Grid-stride.
+__global__ void k_plain_window(const float* __restrict__ u, long long P, int ny, int nx, int nb,
+                               const float* __restrict__ wbox, Box bx, float* __restrict__ tmp) {
+    const long long total = (long long)nb * P;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long pix = i % P;
+        const int r = (int)(pix / nx), c = (int)(pix % nx);
+        const int ir = pce::wrap(r - bx.r0, ny), cc = pce::wrap(c - bx.c0, nx);
+        float v = 0.f;
+        if (ir < bx.nr && cc < bx.nc) v = wbox[bx.woff + (long long)ir * bx.ldw + cc] * u[i];
+        tmp[i] = v;
+    }
+}
+
+// x[b] (+)= w_k . t[b] (whole grid).  first: overwrite instead of accumulate.
+__global__ void k_plain_window_acc(const float* __restrict__ t, long long P, int ny, int nx, int nb,
+                                   const float* __restrict__ wbox, Box bx, float* __restrict__ x,
+                                   int first) {
+    const long long total = (long long)nb * P;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long pix = i % P;
+        const int r = (int)(pix / nx), c = (int)(pix % nx);
+        const int ir = pce::wrap(r - bx.r0, ny), cc = pce::wrap(c - bx.c0, nx);
+        float v = 0.f;
+        if (ir < bx.nr && cc < bx.nc) v = wbox[bx.woff + (long long)ir * bx.ldw + cc] * t[i];
+        x[i] = first ? v : x[i] + v;
+    }
+}
+
+// Spectral product on the [nb][ny][nxh] (+ Nyquist [nb][ny]) layout:
+// mode 0: acc += hhat_k . S ; mode 1: acc = conj(hhat_k) . S.
+__global__ void k_plain_spec_mac(const float2* __restrict__ S, const float2* __restrict__ SN,
+                                 const float2* __restrict__ hk, const float2* __restrict__ hNk,
+                                 int ny, int nxh, int nb, float2* __restrict__ acc,
+                                 float2* __restrict__ accN, int mode) {
+    const long long per = (long long)ny * (nxh + 1);
+    const long long total = (long long)nb * per;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long b = i / per;
+        const long long e = i % per;
+        const int f = (int)(e / (nxh + 1));
+        const int c = (int)(e % (nxh + 1));
+        float2 h, x;
+        float2* dst;
+        if (c < nxh) {
+            h = hk[(long long)f * nxh + c];
+            x = S[(b * ny + f) * nxh + c];
+            dst = acc + (b * ny + f) * nxh + c;
+        } else {
+            h = hNk[f];
+            x = SN[b * ny + f];
+            dst = accN + b * ny + f;
+        }
+        if (mode == 0) *dst = pce::cfma(h, x, *dst);
+        else *dst = pce::cmulc(x, h);
+    }
+}
+
 unsigned grid_for(long long total, int threads = 256) {
     long long g = (total + threads - 1) / threads;
     return (unsigned)std::max<long long>(1, std::min<long long>(g, 1 << 20));
@@ -244,6 +306,7 @@ struct pce_plan {
     float2* scrA = nullptr;
     int nrmax = 0;
     int bchunk = 1;
+    long long zalloc = 0;   // Z scratch per right-hand side (float2)
     long long scratch_bytes = 0;
     // per-kernel timing
     bool timing = false;
@@ -397,9 +460,14 @@ pce_status setup_windows(pce_plan* p, const float* w, cudaStream_t s) {
     const long long nxh = nx / 2;
     const long long zb = (long long)m * p->nrmax * nxh;
     const long long ab = (long long)ny * nxh;
-    const long long per_b = (zb + ab) * (long long)sizeof(float2);
+    // the unfused pipeline keeps tmp (P floats), S, S2, acc (P/2 complex each) and two
+    // Nyquist columns per right-hand side in the Z scratch
+    const long long zplain = (p->flags & PCE_FLAG_UNFUSED) ? 2ll * ny * nx + 2ll * ny : 0;
+    const long long zalloc = std::max(zb, zplain);
+    p->zalloc = zalloc;
+    const long long per_b = (zalloc + ab) * (long long)sizeof(float2);
     p->bchunk = (int)std::max<long long>(1, std::min<long long>(kMaxChunk, kScratchBudget / per_b));
-    if ((st = dev_alloc(&p->scrZ, (size_t)std::max<long long>(1, zb * p->bchunk)))) return st;
+    if ((st = dev_alloc(&p->scrZ, (size_t)std::max<long long>(1, zalloc * p->bchunk)))) return st;
     if ((st = dev_alloc(&p->scrA, (size_t)(ab * p->bchunk)))) return st;
     p->scratch_bytes = per_b * p->bchunk;
     return PCE_OK;
@@ -418,6 +486,7 @@ pce_status create_common(pce_plan_t* out, int ndims, const int64_t* shape, int m
     pce_status st = validate_shape(ndims, shape, ny, nx);
     if (st) return st;
     if (m < 1) return fail(PCE_ERR_INVALID, "m must be >= 1 (got %d)", m);
+    if (flags & ~(uint32_t)PCE_FLAG_UNFUSED) return fail(PCE_ERR_INVALID, "unknown flag bits 0x%x", flags);
     if (!is_device_ptr(w)) return fail(PCE_ERR_INVALID, "w must be a device pointer");
     if (!is_device_ptr(h)) return fail(PCE_ERR_INVALID, spectra ? "hhat must be a device pointer"
                                                                 : "h must be a device pointer");
@@ -474,7 +543,7 @@ pce_status create_common(pce_plan_t* out, int ndims, const int64_t* shape, int m
                                                  npairs, S, (long long)ny * nxh, 0, p->twx);
             const int cpc = pce::cols_columns_per_cta(ny);
             if (e == cudaSuccess)
-                e = pce::launch_cols_spec(ny, dim3((nxh + cpc - 1) / cpc, m), s, S, nxh, p->hh, p->hN,
+                e = pce::launch_cols_spec(ny, dim3(m, (nxh + cpc - 1) / cpc), s, S, nxh, p->hh, p->hN,
                                           p->twy);
             cudaError_t e2 = cudaStreamSynchronize(s);
             cudaFree(S);
@@ -531,6 +600,110 @@ cudaError_t timed(pce_plan_t p, int kind, cudaStream_t s, F&& launch) {
     return err;
 }
 
+// The plain unfused per-term pipeline (PCE_FLAG_UNFUSED), 2D.
+pce_status apply_plain(pce_plan_t p, const float* in, float* out, int64_t batch, bool adjoint,
+                       cudaStream_t s) {
+    const int ny = p->ny, nx = p->nx, m = p->m, nxh = nx / 2;
+    const long long P = (long long)ny * nx;
+    const long long H = (long long)ny * nxh;
+    const float scale = 1.0f / (float)P;
+    const int fpc = pce::rows_pairs_per_cta(nx);
+    const int cpc = pce::cols_columns_per_cta(ny);
+    const int npairs = (ny + 1) / 2;
+    const int tiles = (nxh + cpc - 1) / cpc;
+    cudaError_t e = cudaSuccess;
+    auto grid1 = [](long long total) { return grid_for(total, 256); };
+    for (long long b0 = 0; b0 < batch && e == cudaSuccess; b0 += p->bchunk) {
+        const int nb = (int)std::min<long long>(p->bchunk, batch - b0);
+        const float* src = in + b0 * P;
+        float* dst = out + b0 * P;
+        float* tmp = reinterpret_cast<float*>(p->scrZ);
+        float2* S = p->scrZ + (long long)nb * P / 2;
+        float2* S2 = S + nb * H;
+        float2* S2N = S2 + nb * H;
+        float2* acc = S2N + (long long)nb * ny;
+        float2* accN = acc + nb * H;
+        if (!adjoint) {
+            e = cudaMemsetAsync(acc, 0, sizeof(float2) * (size_t)nb * (H + ny), s);
+            for (int k = 0; k < m && e == cudaSuccess; ++k) {
+                const Box bx = p->box[k];
+                if (bx.nr == 0) continue;
+                e = timed(p, PCE_KERNEL_PLAIN, s, [&] {
+                    k_plain_window<<<grid1(nb * P), 256, 0, s>>>(src, P, ny, nx, nb, p->wbox, bx, tmp);
+                    return cudaGetLastError();
+                });
+                if (e == cudaSuccess)
+                    e = timed(p, PCE_KERNEL_PLAIN, s, [&] {
+                        return pce::launch_rows_r2c(nx, false, dim3((npairs + fpc - 1) / fpc, nb), s, tmp,
+                                                    P, ny, nullptr, nullptr, nullptr, npairs, S, H, 0,
+                                                    p->twx);
+                    });
+                if (e == cudaSuccess)
+                    e = timed(p, PCE_KERNEL_PLAIN, s, [&] {
+                        return pce::launch_cols_spec(ny, dim3(nb, tiles), s, S, nxh, S2, S2N, p->twy);
+                    });
+                if (e == cudaSuccess)
+                    e = timed(p, PCE_KERNEL_PLAIN, s, [&] {
+                        k_plain_spec_mac<<<grid1(nb * (H + ny)), 256, 0, s>>>(
+                            S2, S2N, p->hh + (long long)k * H, p->hN + (long long)k * ny, ny, nxh, nb, acc,
+                            accN, 0);
+                        return cudaGetLastError();
+                    });
+            }
+            if (e == cudaSuccess)
+                e = timed(p, PCE_KERNEL_PLAIN, s, [&] {
+                    return pce::launch_plain_cols_inv(ny, dim3(nb, tiles), s, acc, accN, nxh, p->scrA,
+                                                      p->twy);
+                });
+            if (e == cudaSuccess)
+                e = timed(p, PCE_KERNEL_PLAIN, s, [&] {
+                    return pce::launch_rows_c2r(nx, dim3((npairs + fpc - 1) / fpc, nb), s, p->scrA, H, ny,
+                                                dst, P, scale, p->twx);
+                });
+        } else {
+            e = timed(p, PCE_KERNEL_PLAIN, s, [&] {
+                return pce::launch_rows_r2c(nx, false, dim3((npairs + fpc - 1) / fpc, nb), s, src, P, ny,
+                                            nullptr, nullptr, nullptr, npairs, S, H, 0, p->twx);
+            });
+            if (e == cudaSuccess)
+                e = timed(p, PCE_KERNEL_PLAIN, s, [&] {
+                    return pce::launch_cols_spec(ny, dim3(nb, tiles), s, S, nxh, S2, S2N, p->twy);
+                });
+            bool first = true;
+            for (int k = 0; k < m && e == cudaSuccess; ++k) {
+                const Box bx = p->box[k];
+                if (bx.nr == 0) continue;
+                e = timed(p, PCE_KERNEL_PLAIN, s, [&] {
+                    k_plain_spec_mac<<<grid1(nb * (H + ny)), 256, 0, s>>>(
+                        S2, S2N, p->hh + (long long)k * H, p->hN + (long long)k * ny, ny, nxh, nb, acc,
+                        accN, 1);
+                    return cudaGetLastError();
+                });
+                if (e == cudaSuccess)
+                    e = timed(p, PCE_KERNEL_PLAIN, s, [&] {
+                        return pce::launch_plain_cols_inv(ny, dim3(nb, tiles), s, acc, accN, nxh, p->scrA,
+                                                          p->twy);
+                    });
+                if (e == cudaSuccess)
+                    e = timed(p, PCE_KERNEL_PLAIN, s, [&] {
+                        return pce::launch_rows_c2r(nx, dim3((npairs + fpc - 1) / fpc, nb), s, p->scrA, H,
+                                                    ny, tmp, P, scale, p->twx);
+                    });
+                if (e == cudaSuccess)
+                    e = timed(p, PCE_KERNEL_PLAIN, s, [&] {
+                        k_plain_window_acc<<<grid1(nb * P), 256, 0, s>>>(tmp, P, ny, nx, nb, p->wbox,
+                                                                              bx, dst, first ? 1 : 0);
+                        return cudaGetLastError();
+                    });
+                first = false;
+            }
+            if (e == cudaSuccess && first) e = cudaMemsetAsync(dst, 0, sizeof(float) * (size_t)nb * P, s);
+        }
+    }
+    if (e) return fail(PCE_ERR_CUDA, "unfused apply launch: %s", cudaGetErrorString(e));
+    return PCE_OK;
+}
+
 pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, bool adjoint,
                       cudaStream_t s) {
     const int ny = p->ny, nx = p->nx, m = p->m, nxh = nx / 2;
@@ -546,8 +719,9 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
         if (e) return fail(PCE_ERR_CUDA, "1D apply launch: %s", cudaGetErrorString(e));
         return PCE_OK;
     }
+    if (p->flags & PCE_FLAG_UNFUSED) return apply_plain(p, in, out, batch, adjoint, s);
     const long long zk = (long long)p->nrmax * nxh;
-    const long long zb = (long long)m * zk;
+    const long long zb = (long long)p->zalloc;
     const long long ab = (long long)ny * nxh;
     const int fpc = pce::rows_pairs_per_cta(nx);
     const int cpc = pce::cols_columns_per_cta(ny);
@@ -565,7 +739,7 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
                 });
             if (e == cudaSuccess)
                 e = timed(p, PCE_KERNEL_COLS_FWD, s, [&] {
-                    return pce::launch_cols_fwd(ny, dim3((nxh + cpc - 1) / cpc, nb), s, p->scrZ, zb, zk,
+                    return pce::launch_cols_fwd(ny, dim3(nb, (nxh + cpc - 1) / cpc), s, p->scrZ, zb, zk,
                                                 p->hh, p->hN, m, p->d_box, nxh, p->scrA, ab, p->twy);
                 });
             if (e == cudaSuccess)
@@ -581,7 +755,7 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
             });
             if (e == cudaSuccess)
                 e = timed(p, PCE_KERNEL_COLS_ADJ, s, [&] {
-                    return pce::launch_cols_adj(ny, dim3((nxh + cpc - 1) / cpc, nb), s, p->scrA, ab,
+                    return pce::launch_cols_adj(ny, dim3(nb, (nxh + cpc - 1) / cpc), s, p->scrA, ab,
                                                 p->hh, p->hN, m, p->d_box, nxh, p->scrZ, zb, zk, p->twy);
                 });
             if (e == cudaSuccess)
@@ -705,6 +879,11 @@ int64_t pce_launch_count(pce_plan_t plan, int adjoint, int64_t batch) {
     if (!plan || batch <= 0) return 0;
     if (plan->ndims == 1) return 1;
     const int64_t chunks = (batch + plan->bchunk - 1) / plan->bchunk;
+    if (plan->flags & PCE_FLAG_UNFUSED) {
+        int64_t mk = 0;
+        for (const Box& b : plan->box) mk += b.nr > 0;
+        return chunks * (4 * mk + 2);
+    }
     const int64_t per = (!adjoint && plan->nitems == 0) ? 2 : 3;
     return chunks * per;
 }
@@ -799,7 +978,7 @@ extern "C" pce_status pce_apply_noalloc(pce_plan_t plan, const float* u, float* 
                                      ny, plan->wbox, plan->d_box, plan->items, plan->nitems, scrZ, zb, zk,
                                      plan->twx);
         if (e == cudaSuccess)
-            e = pce::launch_cols_fwd(ny, dim3((nxh + cpc - 1) / cpc, nb), s, scrZ, zb, zk, plan->hh,
+            e = pce::launch_cols_fwd(ny, dim3(nb, (nxh + cpc - 1) / cpc), s, scrZ, zb, zk, plan->hh,
                                      plan->hN, m, plan->d_box, nxh, scrA, ab, plan->twy);
         if (e == cudaSuccess)
             e = pce::launch_rows_c2r(nx, dim3((npairs + fpc - 1) / fpc, nb), s, scrA, ab, ny, y + b0 * P, P,

@@ -13,6 +13,8 @@ import os
 from . import build as _build
 
 PCE_OK, PCE_ERR_INVALID, PCE_ERR_UNSUPPORTED, PCE_ERR_OOM, PCE_ERR_CUDA, PCE_ERR_TIMEOUT = range(6)
+PCE_FLAG_NONE = 0
+PCE_FLAG_UNFUSED = 1
 STATUS_NAMES = {0: "PCE_OK", 1: "PCE_ERR_INVALID", 2: "PCE_ERR_UNSUPPORTED", 3: "PCE_ERR_OOM",
                 4: "PCE_ERR_CUDA", 5: "PCE_ERR_TIMEOUT"}
 
@@ -123,7 +125,7 @@ def pce_launch_count(plan: int, adjoint: bool, batch: int) -> int:
 
 
 KERNEL_KINDS = ("rows_r2c_window", "cols_fwd", "rows_c2r", "rows_r2c", "cols_adj", "rows_adj",
-                "fwd_1d", "adj_1d")
+                "fwd_1d", "adj_1d", "plain")
 
 
 def pce_plan_set_timing(plan: int, enable: bool) -> None:

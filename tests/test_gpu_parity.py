@@ -209,6 +209,35 @@ def test_plan_from_exported_spectra_matches(torch_cuda):
     assert np.max(np.abs(a - b)) <= 1e-6 * np.max(np.abs(a))
 
 
+# ------------------------------------------- plain unfused comparator path
+
+@pytest.mark.parametrize("ny,nx,m,batch", [(64, 64, 4, 3), (32, 128, 8, 2), (16, 16, 4, 1)])
+def test_unfused_pipeline_matches_oracle(torch_cuda, ny, nx, m, batch):
+    torch = torch_cuda
+    from paper_1604_04374_gb300 import Plan
+    from paper_1604_04374_gb300.pce import PCE_FLAG_UNFUSED
+    pr = synth.problem_2d(ny, nx, m, batch, 300 + ny + nx, "normal")
+    plan = Plan(dev(torch, pr.w), h=dev(torch, pr.h), flags=PCE_FLAG_UNFUSED)
+    y, x = run_both(torch, pr, plan)
+    assert rel_l2(y, E.apply(pr.u, pr.w, pr.h)) < TOL
+    assert rel_l2(x, E.apply_adjoint(pr.u, pr.w, pr.h)) < TOL
+
+
+def test_unfused_pipeline_matches_fused_on_workload(torch_cuda):
+    torch = torch_cuda
+    from paper_1604_04374_gb300 import Plan
+    from paper_1604_04374_gb300.pce import PCE_FLAG_UNFUSED
+    pr = synth.workload("2d_1024_m16_b8")
+    fused = plan_for(torch, pr)
+    plain = Plan(dev(torch, pr.w), h=dev(torch, pr.h), flags=PCE_FLAG_UNFUSED)
+    u = dev(torch, pr.u)
+    for direction in ("apply", "apply_adjoint"):
+        a = host(getattr(fused, direction)(u))
+        b = host(getattr(plain, direction)(u))
+        assert rel_l2(a, b) < TOL
+    assert plain.launch_count(False, 8) > fused.launch_count(False, 8)
+
+
 # ------------------------------------------------------- workload sizes
 
 def _sample_points(shape, count, seed):
