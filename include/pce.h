@@ -183,6 +183,35 @@ pce_status pce_plan_set_timing(pce_plan_t plan, int enable);
 pce_status pce_plan_timing(pce_plan_t plan, int kind, double* total_ms, int64_t* launches);
 
 /*
+ * Gradients (autograd support).
+ *
+ * For a scalar loss L(y) with y = H_m u, given r = dL/dy, pce_backward
+ * computes
+ *   du    = dL/du = H_m^* r                                  [batch][shape]
+ *   dw    = dL/dw_k = sum_b u_b . (h~_k * r_b)              [m][shape]
+ *   dhhat = dL/dRe hhat_k + i dL/dIm hhat_k                  [m][Ny][Nx/2+1] (2D)
+ *         = sum_b (c_f / P) R2C(r_b) . conj(R2C(w_k . u_b))  or [m][N/2+1] (1D)
+ * where hhat_k are the spectra of the operator as pce_plan_create_from_spectra
+ * defines it (c_f = 2 on the interior bins of the half spectrum, 1 on DC and
+ * Nyquist).  The per-term spectra R2C(w_k . u_b) are recomputed, not kept by
+ * the forward apply.  dw is dense: the gradient is nonzero also outside the
+ * support of w_k.
+ *
+ *   u, r            : device, [batch][shape] float32 (forward input, dL/dy).
+ *   du, dw, dhhat   : device outputs; any may be NULL to skip it.
+ *   workspace       : device scratch of at least
+ *                     pce_backward_workspace_bytes(plan, batch) bytes; the
+ *                     call allocates nothing itself.
+ *   batch >= 0 (batch = 0 writes zero gradients).
+ * Stream-ordered on `stream`; uses the plan's scratch too (not concurrent
+ * with applies of the same plan).
+ */
+int64_t pce_backward_workspace_bytes(pce_plan_t plan, int64_t batch);
+pce_status pce_backward(pce_plan_t plan, const float* u, const float* r, float* du, float* dw,
+                        float* dhhat, int64_t batch, void* workspace, int64_t workspace_bytes,
+                        void* stream);
+
+/*
  * pce_apply_noalloc -- y = H_m u like pce_apply, for callers that cannot
  * allocate device memory (no counterpart in the paper).
  *

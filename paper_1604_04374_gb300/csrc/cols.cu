@@ -38,8 +38,14 @@ cudaError_t prepare_cols() {
         e = cudaFuncSetAttribute(k_cols_fwd<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
                                  ColCfg<N>::SMEM);                                             \
     if (e == cudaSuccess)                                                                      \
-        e = cudaFuncSetAttribute(k_cols_adj<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
-                                 ColCfg<N>::SMEM);                                             \
+        e = cudaFuncSetAttribute(k_cols_adj<N, false>,                                         \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, ColCfg<N>::SMEM); \
+    if (e == cudaSuccess)                                                                      \
+        e = cudaFuncSetAttribute(k_cols_adj<N, true>,                                          \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, ColCfg<N>::SMEM); \
+    if (e == cudaSuccess)                                                                      \
+        e = cudaFuncSetAttribute(k_cols_grad_h<N>,                                             \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, ColCfg<N>::SMEM); \
     if (e == cudaSuccess)                                                                      \
         e = cudaFuncSetAttribute(k_cols_spec<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
                                  ColCfg<N>::SMEM);                                             \
@@ -76,7 +82,7 @@ cudaError_t launch_cols_adj(int ny, dim3 grid, cudaStream_t s, const float2* V, 
     switch (ny) {
 #define X(N)                                                                                  \
     case N:                                                                                   \
-        k_cols_adj<N><<<grid, ColCfg<N>::NT, ColCfg<N>::SMEM, s>>>(V, v_bstride, hh, hN, m, box, \
+        k_cols_adj<N, false><<<grid, ColCfg<N>::NT, ColCfg<N>::SMEM, s>>>(V, v_bstride, hh, hN, m, box, \
                                                                    nxh, Q, q_bstride,          \
                                                                    q_kstride, tw);             \
         break;
@@ -109,6 +115,43 @@ cudaError_t launch_plain_cols_inv(int ny, dim3 grid, cudaStream_t s, const float
 #define X(N)                                                                                   \
     case N:                                                                                    \
         k_plain_cols_inv<N><<<grid, ColCfg<N>::NT, ColCfg<N>::SMEM, s>>>(acc, accN, nxh, A, tw); \
+        break;
+        PCE_COL_SIZES(X)
+#undef X
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cols_adj_full(int ny, dim3 grid, cudaStream_t s, const float2* V, long long v_bstride,
+                                 const float2* hh, const float2* hN, int m, const Box* box, int nxh,
+                                 float2* Q, long long q_bstride, long long q_kstride,
+                                 const float2* tw) {
+    switch (ny) {
+#define X(N)                                                                                   \
+    case N:                                                                                    \
+        k_cols_adj<N, true><<<grid, ColCfg<N>::NT, ColCfg<N>::SMEM, s>>>(V, v_bstride, hh, hN, m, \
+                                                                         box, nxh, Q, q_bstride, \
+                                                                         q_kstride, tw);       \
+        break;
+        PCE_COL_SIZES(X)
+#undef X
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cols_grad_h(int ny, dim3 grid, cudaStream_t s, const float2* Z, long long z_bstride,
+                               long long z_kstride, int nb, const float2* Rh, const float2* RhN,
+                               const Box* box, int nxh, float2* dhh, float scale, int accumulate,
+                               const float2* tw) {
+    switch (ny) {
+#define X(N)                                                                                   \
+    case N:                                                                                    \
+        k_cols_grad_h<N><<<grid, ColCfg<N>::NT, ColCfg<N>::SMEM, s>>>(                          \
+            Z, z_bstride, z_kstride, nb, Rh, RhN, box, nxh, dhh, scale, accumulate, tw);       \
         break;
         PCE_COL_SIZES(X)
 #undef X

@@ -10,10 +10,18 @@
 // current sub-transform length Ns: butterfly j' reads x[j' + q N/Rs], applies
 // the twiddles W_{Ns Rs}^{q k} (k = j' mod Ns) and writes
 // y[(j'/Ns) Ns Rs + k + q Ns].  Between stages data goes through a padded
-// shared-memory buffer: one float2 of padding per 16, so that every write
-// and read pattern of the stages touches each 8-byte bank pair exactly twice
-// per warp (two wavefronts, the minimum for 64-bit accesses), also when one
-// warp spans several FFTs whose buffers are staggered by 4 float2.
+// shared-memory buffer, alternating between two buffers.  64-bit shared
+// accesses are serviced per half-warp, so a half-warp's 16 lanes must hit 16
+// distinct 8-byte bank pairs; the padding is chosen per exchange for the two
+// thread layouts the kernels use:
+//   kRowLayout: a half-warp is 16 consecutive j of one FFT.  The exchange
+//     after stage 0 (writes with stride 8) and after stages >= 2 (contiguous
+//     writes) pads one float2 per 16; the exchange after stage 1 (two runs
+//     of 8 that lie 64 apart) shifts every 64-element block by 8.
+//   kColLayout: a half-warp is 4 consecutive j of 4 FFTs whose buffers are
+//     staggered by 4 float2: one float2 of padding per 8 throughout.
+// The twiddles of a stage are loaded before the barrier that precedes it, so
+// their latency overlaps the exchange.
 //
 // Twiddles come from a per-N table generated once per plan in FP64 and
 // rounded to FP32 (layout: per stage s >= 1, entries [q-1][k] =
@@ -31,11 +39,22 @@ constexpr int kR = 8;   // elements per thread
 
 __host__ __device__ constexpr int ilog2(int n) { return n <= 1 ? 0 : 1 + ilog2(n >> 1); }
 
+enum FftLayout { kRowLayout = 0, kColLayout = 1 };
+
+// Generic padding used outside the stages (one float2 per 16).
 __device__ __forceinline__ int padi(int i) { return i + (i >> 4); }
-__host__ __device__ constexpr int pad_len(int n) { return n + (n >> 4); }
-// Shared-memory float2 count of one FFT's two buffers plus the skew that
-// staggers neighbouring FFTs by 32 bytes (8 banks).
+// float2 count of one exchange buffer (room for every exchange's padding).
+__host__ __device__ constexpr int pad_len(int n) { return n + n / 8 + 8; }
+// One FFT's two buffers plus a 4-float2 skew that staggers neighbouring FFTs.
 __host__ __device__ constexpr int fft_region(int n) { return 2 * pad_len(n) + 4; }
+
+// Address of element i in the buffer written by stage E.
+template <int L, int E>
+__device__ __forceinline__ int xaddr(int i) {
+    if constexpr (L == kColLayout) return i + (i >> 3);
+    else if constexpr (E == 1) return i + ((i >> 6) << 3);
+    else return i + (i >> 4);
+}
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
@@ -146,16 +165,33 @@ struct FftPlan {
     static_assert((N & (N - 1)) == 0, "FFT length must be a power of two");
 };
 
-// One Stockham stage.  buf: one of this FFT's two shared buffers (pad_len(N) float2).
-template <int N, int S, bool INV>
-__device__ __forceinline__ void fft_stage(float2 (&v)[kR], int j, float2* buf,
-                                          const float2* __restrict__ tw) {
+// Twiddles one thread applies in stage S (S >= 1): G butterflies x (RS - 1).
+template <int N, int S>
+__device__ __forceinline__ void load_tw(float2 (&t)[kR - 1], int j, const float2* __restrict__ tw) {
+    using P = FftPlan<N>;
+    constexpr int RS = P::radix(S);
+    constexpr int NS = P::ns(S);
+    constexpr int G = kR / RS;
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
+        const int k = (j + i * P::T) & (NS - 1);
+#pragma unroll
+        for (int q = 1; q < RS; ++q) t[i * (RS - 1) + q - 1] = __ldg(&tw[P::twoff(S) + (q - 1) * NS + k]);
+    }
+}
+
+// Stage S of the FFT and, by recursion, every later stage.  t holds this
+// stage's twiddles (unused for S = 0).
+template <int N, int S, bool INV, int L>
+__device__ __forceinline__ void fft_stage(float2 (&v)[kR], int j, float2* b0, float2* b1,
+                                          const float2 (&t)[kR - 1], const float2* __restrict__ tw) {
     using P = FftPlan<N>;
     constexpr int RS = P::radix(S);
     constexpr int NS = P::ns(S);
     constexpr int G = kR / RS;
     constexpr bool LAST = (S == P::NSTAGES - 1);
     constexpr int T = P::T;
+    float2* buf = (S & 1) ? b1 : b0;
 #pragma unroll
     for (int i = 0; i < G; ++i) {
         const int jp = j + i * T;
@@ -163,70 +199,65 @@ __device__ __forceinline__ void fft_stage(float2 (&v)[kR], int j, float2* buf,
         float2 a[RS];
 #pragma unroll
         for (int q = 0; q < RS; ++q) a[q] = v[i + q * G];
-        if (S > 0) {
+        if constexpr (S > 0) {
 #pragma unroll
-            for (int q = 1; q < RS; ++q) {
-                const float2 t = __ldg(&tw[P::twoff(S) + (q - 1) * NS + k]);
-                a[q] = INV ? cmulc(a[q], t) : cmul(a[q], t);
-            }
+            for (int q = 1; q < RS; ++q)
+                a[q] = INV ? cmulc(a[q], t[i * (RS - 1) + q - 1]) : cmul(a[q], t[i * (RS - 1) + q - 1]);
         }
         Dft<RS, INV>::run(a);
-        if (LAST) {
+        if constexpr (LAST) {
 #pragma unroll
             for (int q = 0; q < RS; ++q) v[i + q * G] = a[q];
         } else {
-            // padded address of base + q NS, strength-reduced: the low four bits
-            // of base + q NS only come from k (NS >= 16), from k < 8 plus 8 q
-            // (NS = 8), or from q < 8 on base = 8 jp (NS = 1)
+            // address of base + q NS, strength-reduced where the padding allows
             const int base = (jp / NS) * NS * RS + k;
-            const int pb = padi(base);
+            const int pb = xaddr<L, S>(base);
 #pragma unroll
             for (int q = 0; q < RS; ++q) {
                 int addr;
-                if constexpr (NS >= 16) addr = pb + q * (NS + NS / 16);
-                else if constexpr (NS == 8) addr = pb + 8 * q + (q >> 1);
+                if constexpr (L == kColLayout && NS >= 8) addr = pb + q * (NS + NS / 8);
+                else if constexpr (L == kRowLayout && S != 1 && NS >= 16) addr = pb + q * (NS + NS / 16);
+                else if constexpr (L == kRowLayout && S == 1 && NS == 8 && RS == kR) addr = pb + 8 * q;
                 else if constexpr (NS == 1 && RS == kR) addr = pb + q;
-                else addr = padi(base + q * NS);
+                else addr = xaddr<L, S>(base + q * NS);
                 buf[addr] = a[q];
             }
         }
     }
-    if (!LAST) {
+    if constexpr (!LAST) {
+        float2 tn[kR - 1];
+        load_tw<N, S + 1>(tn, j, tw);
         __syncthreads();
-        if constexpr (T % 16 == 0) {
-            const int pj = padi(j);
+        if constexpr (L == kColLayout && T % 8 == 0) {
+            const int pj = xaddr<L, S>(j);
+#pragma unroll
+            for (int r = 0; r < kR; ++r) v[r] = buf[pj + r * (T + T / 8)];
+        } else if constexpr (L == kRowLayout && S == 1 && T % 64 == 0) {
+            const int pj = xaddr<L, S>(j);
+#pragma unroll
+            for (int r = 0; r < kR; ++r) v[r] = buf[pj + r * (T + T / 8)];
+        } else if constexpr (L == kRowLayout && S != 1 && T % 16 == 0) {
+            const int pj = xaddr<L, S>(j);
 #pragma unroll
             for (int r = 0; r < kR; ++r) v[r] = buf[pj + r * (T + T / 16)];
         } else {
 #pragma unroll
-            for (int r = 0; r < kR; ++r) v[r] = buf[padi(j + r * T)];
+            for (int r = 0; r < kR; ++r) v[r] = buf[xaddr<L, S>(j + r * T)];
         }
+        fft_stage<N, S + 1, INV, L>(v, j, b0, b1, tn, tw);
     }
 }
-
-template <int N, int S, bool INV>
-struct FftStages {
-    __device__ __forceinline__ static void run(float2 (&v)[kR], int j, float2* b0, float2* b1,
-                                               const float2* __restrict__ tw) {
-        fft_stage<N, S, INV>(v, j, (S & 1) ? b1 : b0, tw);
-        FftStages<N, S + 1, INV>::run(v, j, b0, b1, tw);
-    }
-};
-template <int N, bool INV>
-struct FftStages<N, FftPlan<N>::NSTAGES, INV> {
-    __device__ __forceinline__ static void run(float2 (&)[kR], int, float2*, float2*,
-                                               const float2* __restrict__) {}
-};
 
 // Complex FFT of N points held as v[r] = x[j + r*T] by threads j = 0..T-1.
 // b0, b1: two shared buffers of pad_len(N) float2 private to this FFT.
 // Begins with a CTA barrier so that the buffers may be reused freely by the
 // caller between FFTs.  All threads of the CTA must call it.
-template <int N, bool INV>
+template <int N, bool INV, int L = kRowLayout>
 __device__ __forceinline__ void fft(float2 (&v)[kR], int j, float2* b0, float2* b1,
                                     const float2* __restrict__ tw) {
+    float2 t0[kR - 1];
     __syncthreads();
-    FftStages<N, 0, INV>::run(v, j, b0, b1, tw);
+    fft_stage<N, 0, INV, L>(v, j, b0, b1, t0, tw);
 }
 
 }  // namespace pce

@@ -36,6 +36,9 @@ cudaError_t prepare_kernels() {
                                  Cfg1d<N>::SMEM);                                              \
     if (e == cudaSuccess)                                                                      \
         e = cudaFuncSetAttribute(k_spec_1d<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
+                                 Cfg1d<N>::SMEM);                                              \
+    if (e == cudaSuccess)                                                                      \
+        e = cudaFuncSetAttribute(k_grad_1d<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
                                  Cfg1d<N>::SMEM);
     PCE_1D_SIZES(X)
 #undef X
@@ -82,6 +85,23 @@ cudaError_t launch_spec_1d(int n, int m, cudaStream_t s, const float* h, float2*
         k_spec_1d<N><<<grid, Cfg1d<N>::NT, Cfg1d<N>::SMEM, s>>>(h, m, hp, tw);                 \
         break;                                                                                 \
     }
+        PCE_1D_SIZES(X)
+#undef X
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grad_1d(int n, int m, cudaStream_t s, const float* u, const float* r,
+                           const float* w, const float2* hp, int nb, float2* dh, float* dw,
+                           float scale, int accumulate, const float2* tw) {
+    switch (n) {
+#define X(N)                                                                                   \
+    case N:                                                                                    \
+        k_grad_1d<N><<<m, Cfg1d<N>::NT, Cfg1d<N>::SMEM, s>>>(u, r, w, hp, nb, dh, dw, scale,   \
+                                                             accumulate, tw);                  \
+        break;
         PCE_1D_SIZES(X)
 #undef X
         default:

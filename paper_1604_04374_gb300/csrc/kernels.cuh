@@ -43,6 +43,76 @@ __device__ __forceinline__ int wrap(int i, int n) { return i & (n - 1); }
 // WINDOW: item = (k, p) -> box rows 2p, 2p+1 of w_k (global rows r0+2p, r0+2p+1),
 //         multiplied by the box copy of w_k, output rows 2p, 2p+1 of dst[b][k].
 // !WINDOW: item = p -> rows 2p, 2p+1 (< nrows), output rows 2p, 2p+1 of dst[b].
+// Each slot handles kRowIters items one after the other; the inputs of the
+// next item are loaded before the FFT of the current one.
+constexpr int kRowIters = 1;
+
+struct RowItem {
+    int k, la, lb;
+    bool va, vb;
+    const float* sa;
+    const float* sb;
+    const float* wa;   // window row of la (WINDOW), nullptr otherwise
+    const float* wb;
+    int c0, nc;
+};
+
+template <int NX, bool WINDOW>
+__device__ __forceinline__ RowItem row_item(int item, int nitems, const float* __restrict__ src, int nrows,
+                                            const float* __restrict__ wbox, const Box* __restrict__ box,
+                                            const int2* __restrict__ items) {
+    RowItem it;
+    const bool active = item < nitems;
+    if (WINDOW) {
+        const int2 kp = active ? items[item] : make_int2(0, 0);
+        const Box bx = box[kp.x];
+        it.k = kp.x;
+        it.la = 2 * kp.y;
+        it.lb = it.la + 1;
+        it.va = active && it.la < bx.nr;
+        it.vb = active && it.lb < bx.nr;
+        it.sa = src + (long long)wrap(bx.r0 + it.la, nrows) * NX;
+        it.sb = src + (long long)wrap(bx.r0 + it.lb, nrows) * NX;
+        it.wa = wbox + bx.woff + (long long)it.la * bx.ldw;
+        it.wb = wbox + bx.woff + (long long)it.lb * bx.ldw;
+        it.c0 = bx.c0;
+        it.nc = bx.nc;
+    } else {
+        it.k = 0;
+        it.la = 2 * item;
+        it.lb = it.la + 1;
+        it.va = active && it.la < nrows;
+        it.vb = active && it.lb < nrows;
+        it.sa = src + (long long)(it.va ? it.la : 0) * NX;
+        it.sb = src + (long long)(it.vb ? it.lb : 0) * NX;
+        it.wa = it.wb = nullptr;
+        it.c0 = 0;
+        it.nc = NX;
+    }
+    return it;
+}
+
+template <int NX, bool WINDOW>
+__device__ __forceinline__ void row_load(float2 (&v)[kR], const RowItem& it, int j) {
+    constexpr int T = NX / kR;
+#pragma unroll
+    for (int r = 0; r < kR; ++r) {
+        const int n = j + r * T;
+        float xa = 0.f, xb = 0.f;
+        if (WINDOW) {
+            const int cc = wrap(n - it.c0, NX);
+            if (cc < it.nc) {
+                if (it.va) xa = __ldg(it.wa + cc) * __ldg(it.sa + n);
+                if (it.vb) xb = __ldg(it.wb + cc) * __ldg(it.sb + n);
+            }
+        } else {
+            if (it.va) xa = __ldg(it.sa + n);
+            if (it.vb) xb = __ldg(it.sb + n);
+        }
+        v[r] = make_float2(xa, xb);
+    }
+}
+
 template <int NX, bool WINDOW>
 __global__ void __launch_bounds__(256)
 k_rows_r2c(const float* __restrict__ src, long long src_bstride, int nrows,
@@ -58,77 +128,52 @@ k_rows_r2c(const float* __restrict__ src, long long src_bstride, int nrows,
     const int j = threadIdx.x - slot * T;
     float2* b0 = sbuf + slot * fft_region(NX);
     float2* b1 = b0 + pad_len(NX);
-    const int item = blockIdx.x * FPC + slot;
     const int b = blockIdx.y;
-    const bool active = item < nitems;
+    const float* srcb = src + b * src_bstride;
+    const int first = blockIdx.x * kRowIters * FPC + slot;
 
-    int k = 0, la, lb, ra, rb;
-    bool va, vb;
-    Box bx;
-    if (WINDOW) {
-        const int2 it = active ? items[item] : make_int2(0, 0);
-        k = it.x;
-        bx = box[k];
-        la = 2 * it.y;
-        lb = la + 1;
-        va = active && la < bx.nr;
-        vb = active && lb < bx.nr;
-        ra = wrap(bx.r0 + la, nrows);
-        rb = wrap(bx.r0 + lb, nrows);
-    } else {
-        la = 2 * item;
-        lb = la + 1;
-        va = active && la < nrows;
-        vb = active && lb < nrows;
-        ra = va ? la : 0;
-        rb = vb ? lb : 0;
-    }
-    const float* sa = src + b * src_bstride + (long long)ra * NX;
-    const float* sb = src + b * src_bstride + (long long)rb * NX;
-
+    RowItem cur = row_item<NX, WINDOW>(first, nitems, srcb, nrows, wbox, box, items);
     float2 v[kR];
-#pragma unroll
-    for (int r = 0; r < kR; ++r) {
-        const int n = j + r * T;
-        float xa = 0.f, xb = 0.f;
-        if (WINDOW) {
-            const int cc = wrap(n - bx.c0, NX);
-            if (cc < bx.nc) {
-                const float* wr = wbox + bx.woff;
-                if (va) xa = __ldg(wr + (long long)la * bx.ldw + cc) * __ldg(sa + n);
-                if (vb) xb = __ldg(wr + (long long)lb * bx.ldw + cc) * __ldg(sb + n);
-            }
-        } else {
-            if (va) xa = __ldg(sa + n);
-            if (vb) xb = __ldg(sb + n);
+    row_load<NX, WINDOW>(v, cur, j);
+    for (int it = 0; it < kRowIters; ++it) {
+        RowItem nxt;
+        float2 vn[kR];
+        const bool more = it + 1 < kRowIters;
+        if (more) {
+            nxt = row_item<NX, WINDOW>(first + (it + 1) * FPC, nitems, srcb, nrows, wbox, box, items);
+            row_load<NX, WINDOW>(vn, nxt, j);
         }
-        v[r] = make_float2(xa, xb);
-    }
-    fft<NX, false>(v, j, b0, b1, tw);
+        fft<NX, false>(v, j, b0, b1, tw);
 
-    // split the spectra of the two real rows
-    float2* xs = b0;
-    __syncthreads();
+        // split the spectra of the two real rows
+        float2* xs = b0;
+        __syncthreads();
 #pragma unroll
-    for (int r = 0; r < kR; ++r) xs[padi(j + r * T)] = v[r];
-    __syncthreads();
-    float2* da = dst + b * dst_bstride + k * dst_kstride + (long long)la * NXh;
-    float2* db = dst + b * dst_bstride + k * dst_kstride + (long long)lb * NXh;
+        for (int r = 0; r < kR; ++r) xs[padi(j + r * T)] = v[r];
+        __syncthreads();
+        float2* da = dst + b * dst_bstride + cur.k * dst_kstride + (long long)cur.la * NXh;
+        float2* db = dst + b * dst_bstride + cur.k * dst_kstride + (long long)cur.lb * NXh;
 #pragma unroll
-    for (int r = 0; r < kR / 2; ++r) {
-        const int f = j + r * T;
-        float2 A, B;
-        if (f == 0) {
-            A = make_float2(v[0].x, v[kR / 2].x);
-            B = make_float2(v[0].y, v[kR / 2].y);
-        } else {
-            const float2 z = v[r];
-            const float2 zm = xs[padi(NX - f)];
-            A = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
-            B = make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
+        for (int r = 0; r < kR / 2; ++r) {
+            const int f = j + r * T;
+            float2 A, B;
+            if (f == 0) {
+                A = make_float2(v[0].x, v[kR / 2].x);
+                B = make_float2(v[0].y, v[kR / 2].y);
+            } else {
+                const float2 z = v[r];
+                const float2 zm = xs[padi(NX - f)];
+                A = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
+                B = make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
+            }
+            if (cur.va) da[f] = A;
+            if (cur.vb) db[f] = B;
         }
-        if (va) da[f] = A;
-        if (vb) db[f] = B;
+        if (more) {
+            cur = nxt;
+#pragma unroll
+            for (int r = 0; r < kR; ++r) v[r] = vn[r];
+        }
     }
 }
 
@@ -186,6 +231,34 @@ k_rows_c2r(const float2* __restrict__ src, long long src_bstride, int nrows,
 // ------------------------------------------------------ rows C2R, adjoint G3
 // Row pair (2p, 2p+1): x = sum over the terms k whose box holds the row of
 // w_k . C2R(Q_{b,k}[row]), times scale.  Q rows are indexed inside the box.
+// The next term's Q rows and window values are loaded before the inverse
+// FFT of the current term.
+struct AdjTerm {
+    const float2* pa;
+    const float2* pb;
+    const float* wa;
+    const float* wb;
+    bool va, vb;
+    int c0, nc;
+};
+
+template <int NX>
+__device__ __forceinline__ void adj_load(float2 (&v)[kR], float (&wa)[kR], float (&wb)[kR],
+                                         const AdjTerm& q, int j) {
+    constexpr int T = NX / kR;
+#pragma unroll
+    for (int r = 0; r < kR; ++r) {
+        const int f = j + r * T;
+        const float2 xa = q.va ? load_half<NX>(q.pa, f) : make_float2(0.f, 0.f);
+        const float2 xb = q.vb ? load_half<NX>(q.pb, f) : make_float2(0.f, 0.f);
+        v[r] = make_float2(xa.x - xb.y, xa.y + xb.x);
+        const int cc = wrap(f - q.c0, NX);     // f doubles as the output column n = j + r*T
+        const bool in = cc < q.nc;
+        wa[r] = (q.va && in) ? __ldg(q.wa + cc) : 0.f;
+        wb[r] = (q.vb && in) ? __ldg(q.wb + cc) : 0.f;
+    }
+}
+
 template <int NX>
 __global__ void __launch_bounds__(256)
 k_rows_adj(const float2* __restrict__ Q, long long q_bstride, long long q_kstride, int nrows,
@@ -216,37 +289,48 @@ k_rows_adj(const float2* __restrict__ Q, long long q_bstride, long long q_kstrid
     const int kbeg = pv ? __ldg(&kptr[p]) : 0;
     const int kcnt = pv ? __ldg(&kptr[p + 1]) - kbeg : 0;
 
-    float2 acc[kR];
-#pragma unroll
-    for (int r = 0; r < kR; ++r) acc[r] = make_float2(0.f, 0.f);
-
-    for (int t = 0; t < nk; ++t) {
+    auto term = [&](int t) {
+        AdjTerm q;
         const bool act = t < kcnt;
         const int k = act ? __ldg(&klist[kbeg + t]) : 0;
         const Box bx = box[k];
         const int la = wrap(ga - bx.r0, nrows);
         const int lb = wrap(gb - bx.r0, nrows);
-        const bool va = act && la < bx.nr;
-        const bool vb = act && gb < nrows && lb < bx.nr;
-        const float2* pa = Q + b * q_bstride + k * q_kstride + (long long)(va ? la : 0) * NXh;
-        const float2* pb = Q + b * q_bstride + k * q_kstride + (long long)(vb ? lb : 0) * NXh;
-        float2 v[kR];
+        q.va = act && la < bx.nr;
+        q.vb = act && gb < nrows && lb < bx.nr;
+        q.pa = Q + b * q_bstride + k * q_kstride + (long long)(q.va ? la : 0) * NXh;
+        q.pb = Q + b * q_bstride + k * q_kstride + (long long)(q.vb ? lb : 0) * NXh;
+        q.wa = wbox + bx.woff + (long long)(q.va ? la : 0) * bx.ldw;
+        q.wb = wbox + bx.woff + (long long)(q.vb ? lb : 0) * bx.ldw;
+        q.c0 = bx.c0;
+        q.nc = bx.nc;
+        return q;
+    };
+
+    float2 acc[kR];
 #pragma unroll
-        for (int r = 0; r < kR; ++r) {
-            const int f = j + r * T;
-            const float2 xa = va ? load_half<NX>(pa, f) : make_float2(0.f, 0.f);
-            const float2 xb = vb ? load_half<NX>(pb, f) : make_float2(0.f, 0.f);
-            v[r] = make_float2(xa.x - xb.y, xa.y + xb.x);
-        }
+    for (int r = 0; r < kR; ++r) acc[r] = make_float2(0.f, 0.f);
+
+    float2 v[kR];
+    float wa[kR], wb[kR];
+    if (nk > 0) adj_load<NX>(v, wa, wb, term(0), j);
+    for (int t = 0; t < nk; ++t) {
+        float2 vn[kR];
+        float wan[kR], wbn[kR];
+        const bool more = t + 1 < nk;
+        if (more) adj_load<NX>(vn, wan, wbn, term(t + 1), j);
         fft<NX, true>(v, j, b0, b1, tw);
-        const float* wr = wbox + bx.woff;
 #pragma unroll
         for (int r = 0; r < kR; ++r) {
-            const int n = j + r * T;
-            const int cc = wrap(n - bx.c0, NX);
-            if (cc < bx.nc) {
-                if (va) acc[r].x = fmaf(__ldg(wr + (long long)la * bx.ldw + cc), v[r].x, acc[r].x);
-                if (vb) acc[r].y = fmaf(__ldg(wr + (long long)lb * bx.ldw + cc), v[r].y, acc[r].y);
+            acc[r].x = fmaf(wa[r], v[r].x, acc[r].x);
+            acc[r].y = fmaf(wb[r], v[r].y, acc[r].y);
+        }
+        if (more) {
+#pragma unroll
+            for (int r = 0; r < kR; ++r) {
+                v[r] = vn[r];
+                wa[r] = wan[r];
+                wb[r] = wbn[r];
             }
         }
     }
@@ -329,7 +413,7 @@ k_cols_fwd(const float2* __restrict__ Z, long long z_bstride, long long z_kstrid
     while (k < m && box[k].nr == 0) ++k;
     if (k >= m) {
         // every window is zero: the output spectrum is zero
-        fft<NY, true>(acc, j, b0, b1, tw);
+        fft<NY, true, kColLayout>(acc, j, b0, b1, tw);
         if (cv) {
             float2* Ab = A + b * a_bstride;
 #pragma unroll
@@ -358,7 +442,7 @@ k_cols_fwd(const float2* __restrict__ Z, long long z_bstride, long long z_kstrid
             bn = box[kn];
             load_col<NY>(zn, Zb + kn * z_kstride, bn, j, col, NXh, cv);
         }
-        fft<NY, false>(v, j, b0, b1, tw);
+        fft<NY, false, kColLayout>(v, j, b0, b1, tw);
         if (tile0) {
             if (dcn) {
 #pragma unroll
@@ -388,7 +472,7 @@ k_cols_fwd(const float2* __restrict__ Z, long long z_bstride, long long z_kstrid
         k = kn;
         bx = bn;
     }
-    fft<NY, true>(acc, j, b0, b1, tw);
+    fft<NY, true, kColLayout>(acc, j, b0, b1, tw);
     if (cv) {
         float2* Ab = A + b * a_bstride;
 #pragma unroll
@@ -397,10 +481,11 @@ k_cols_fwd(const float2* __restrict__ Z, long long z_bstride, long long z_kstrid
 }
 
 // G1b + G2: adjoint column pass.  Column FFT of V once; per k the product
-// with conj(hhat_k), an inverse column FFT, and a store of the box rows only.
+// with conj(hhat_k), an inverse column FFT, and a store of the box rows only
+// (FULL: of every row, Q[b][k][NY][NXh], for the window gradient).
 // Grid (batch, NXh / C).  The next term's spectrum is loaded before the
 // current inverse FFT.
-template <int NY>
+template <int NY, bool FULL>
 __global__ void __launch_bounds__(ColCfg<NY>::NT)
 k_cols_adj(const float2* __restrict__ V, long long v_bstride,
            const float2* __restrict__ hh, const float2* __restrict__ hN, int m,
@@ -429,7 +514,7 @@ k_cols_adj(const float2* __restrict__ V, long long v_bstride,
     for (int r = 0; r < kR; ++r)
         vv[r] = cv ? __ldg(&Vb[(long long)(j + r * T) * NXh + col]) : make_float2(0.f, 0.f);
     int k = 0;
-    while (k < m && box[k].nr == 0) ++k;
+    while (k < m && !FULL && box[k].nr == 0) ++k;
     float2 hv[kR];
     if (k < m) {
         const float2* hk = hh + (long long)k * NY * NXh;
@@ -437,7 +522,7 @@ k_cols_adj(const float2* __restrict__ V, long long v_bstride,
         for (int r = 0; r < kR; ++r)
             hv[r] = cv ? __ldg(&hk[(long long)(j + r * T) * NXh + col]) : make_float2(0.f, 0.f);
     }
-    fft<NY, false>(vv, j, b0, b1, tw);
+    fft<NY, false, kColLayout>(vv, j, b0, b1, tw);
     if (tile0) {
         if (dcn) {
 #pragma unroll
@@ -447,7 +532,7 @@ k_cols_adj(const float2* __restrict__ V, long long v_bstride,
     }
     while (k < m) {
         int kn = k + 1;
-        while (kn < m && box[kn].nr == 0) ++kn;
+        while (kn < m && !FULL && box[kn].nr == 0) ++kn;
         const Box bx = box[k];
         float2 p[kR];
 #pragma unroll
@@ -471,13 +556,17 @@ k_cols_adj(const float2* __restrict__ V, long long v_bstride,
             for (int r = 0; r < kR; ++r)
                 hv[r] = cv ? __ldg(&hk[(long long)(j + r * T) * NXh + col]) : make_float2(0.f, 0.f);
         }
-        fft<NY, true>(p, j, b0, b1, tw);
+        fft<NY, true, kColLayout>(p, j, b0, b1, tw);
         if (cv) {
             float2* Qk = Q + b * q_bstride + k * q_kstride;
 #pragma unroll
             for (int r = 0; r < kR; ++r) {
-                const int i = wrap(j + r * T - bx.r0, NY);
-                if (i < bx.nr) Qk[(long long)i * NXh + col] = p[r];
+                if (FULL) {
+                    Qk[(long long)(j + r * T) * NXh + col] = p[r];
+                } else {
+                    const int i = wrap(j + r * T - bx.r0, NY);
+                    if (i < bx.nr) Qk[(long long)i * NXh + col] = p[r];
+                }
             }
         }
         k = kn;
@@ -510,7 +599,7 @@ k_cols_spec(const float2* __restrict__ S, int NXh, float2* __restrict__ hh,
 #pragma unroll
     for (int r = 0; r < kR; ++r)
         v[r] = cv ? __ldg(&Sk[(long long)(j + r * T) * NXh + col]) : make_float2(0.f, 0.f);
-    fft<NY, false>(v, j, b0, b1, tw);
+    fft<NY, false, kColLayout>(v, j, b0, b1, tw);
     if (tile0) {
         if (dcn) {
 #pragma unroll
@@ -568,11 +657,177 @@ k_plain_cols_inv(const float2* __restrict__ acc, const float2* __restrict__ accN
         }
         v[r] = x;
     }
-    fft<NY, true>(v, j, b0, b1, tw);
+    fft<NY, true, kColLayout>(v, j, b0, b1, tw);
     if (cv) {
         float2* Ab = A + (long long)b * NY * NXh;
 #pragma unroll
         for (int r = 0; r < kR; ++r) Ab[(long long)(j + r * T) * NXh + col] = v[r];
+    }
+}
+
+// ------------------------------------------------------------- gradients
+// Backward of L(y), y = C2R( sum_k hhat_k . R2C(w_k . u) ), given r = dL/dy.
+// With R_b = R2C(r_b) and X_{b,k} = R2C(w_k . u_b) (recomputed, not stored):
+//   dL/dhhat_k = sum_b (c_f / P) R_b . conj(X_{b,k})   (c_f = 2 on the interior
+//                columns of the half spectrum, 1 on DC and Nyquist; the
+//                convention dL/dRe + i dL/dIm)
+//   dL/dw_k    = sum_b u_b . C2R( conj(hhat_k) . R_b ) / P
+//   dL/du_b    = H_m^* r_b (the adjoint apply).
+
+// dhhat: grid (m, NXh / C).  Z: forward row spectra [nb][m][nr][NXh];
+// Rh/RhN: column spectra of r in the kernels' layout.  Output natural
+// [m][NY][NXh+1] complex; accumulate adds to it.
+template <int NY>
+__global__ void __launch_bounds__(ColCfg<NY>::NT)
+k_cols_grad_h(const float2* __restrict__ Z, long long z_bstride, long long z_kstride, int nb,
+              const float2* __restrict__ Rh, const float2* __restrict__ RhN,
+              const Box* __restrict__ box, int NXh, float2* __restrict__ dhh, float scale,
+              int accumulate, const float2* __restrict__ tw) {
+    using CC = ColCfg<NY>;
+    constexpr int T = CC::T;
+    constexpr int C = CC::C;
+    extern __shared__ float2 smem[];
+    const int c = threadIdx.x % C;
+    const int j = threadIdx.x / C;
+    float2* b0 = smem + c * CC::CS;
+    float2* b1 = b0 + pad_len(NY);
+    float2* xbuf = smem + C * CC::CS;
+    const int k = blockIdx.x;
+    const int tile = blockIdx.y;
+    const int col = tile * C + c;
+    const bool cv = col < NXh;
+    const bool tile0 = tile == 0;
+    const bool dcn = tile0 && c == 0;
+    const Box bx = box[k];
+    float2 acc[kR], accN[kR];
+#pragma unroll
+    for (int r = 0; r < kR; ++r) acc[r] = accN[r] = make_float2(0.f, 0.f);
+    if (bx.nr > 0) {
+        float2 v[kR];
+        load_col<NY>(v, Z + k * z_kstride, bx, j, col, NXh, cv);
+        for (int b = 0; b < nb; ++b) {
+            const bool more = b + 1 < nb;
+            float2 vn[kR], rv[kR];
+            if (more) load_col<NY>(vn, Z + (b + 1) * z_bstride + k * z_kstride, bx, j, col, NXh, cv);
+            const float2* Rb = Rh + (long long)b * NY * NXh;
+#pragma unroll
+            for (int r = 0; r < kR; ++r)
+                rv[r] = cv ? __ldg(&Rb[(long long)(j + r * T) * NXh + col]) : make_float2(0.f, 0.f);
+            fft<NY, false, kColLayout>(v, j, b0, b1, tw);
+            if (tile0) {
+                if (dcn) {
+#pragma unroll
+                    for (int r = 0; r < kR; ++r) xbuf[padi(j + r * T)] = v[r];
+                }
+                __syncthreads();
+            }
+            if (dcn) {
+#pragma unroll
+                for (int r = 0; r < kR; ++r) {
+                    const int f = j + r * T;
+                    float2 a, bb;
+                    split_dc_nyq(v[r], xbuf[padi((NY - f) & (NY - 1))], a, bb);
+                    acc[r] = cfmac(a, rv[r], acc[r]);
+                    accN[r] = cfmac(bb, __ldg(&RhN[(long long)b * NY + f]), accN[r]);
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < kR; ++r) acc[r] = cfmac(v[r], rv[r], acc[r]);
+            }
+            if (more) {
+#pragma unroll
+                for (int r = 0; r < kR; ++r) v[r] = vn[r];
+            }
+        }
+    }
+    float2* dk = dhh + (long long)k * NY * (NXh + 1);
+#pragma unroll
+    for (int r = 0; r < kR; ++r) {
+        const long long row = (long long)(j + r * T) * (NXh + 1);
+        if (dcn) {
+            float2 g0 = cscale(acc[r], scale), gn = cscale(accN[r], scale);
+            if (accumulate) {
+                g0 = cadd(g0, dk[row]);
+                gn = cadd(gn, dk[row + NXh]);
+            }
+            dk[row] = g0;
+            dk[row + NXh] = gn;
+        } else if (cv) {
+            float2 g = cscale(acc[r], 2.f * scale);
+            if (accumulate) g = cadd(g, dk[row + col]);
+            dk[row + col] = g;
+        }
+    }
+}
+
+// dw: grid (ceil(npairs / FPC), m).  Qf: [nb][m][nrows][NXh] packed row spectra
+// of conj(hhat_k) . R_b (every row).  dw: [m][nrows][NX]; accumulate adds.
+template <int NX>
+__global__ void __launch_bounds__(256)
+k_rows_grad_w(const float2* __restrict__ Qf, long long q_bstride, long long q_kstride, int nrows,
+              int nb, const float* __restrict__ u, long long u_bstride, float* __restrict__ dw,
+              float scale, int accumulate, const float2* __restrict__ tw) {
+    constexpr int T = NX / kR;
+    constexpr int FPC = 256 / T;
+    constexpr int NXh = NX / 2;
+    __shared__ float2 sbuf[FPC * fft_region(NX)];
+    const int slot = threadIdx.x / T;
+    const int j = threadIdx.x - slot * T;
+    float2* b0 = sbuf + slot * fft_region(NX);
+    float2* b1 = b0 + pad_len(NX);
+    const int p = blockIdx.x * FPC + slot;
+    const int k = blockIdx.y;
+    const int ga = 2 * p, gb = ga + 1;
+    const bool va = ga < nrows, vb = gb < nrows;
+
+    auto load = [&](int b, float2 (&v)[kR], float (&ua)[kR], float (&ub)[kR]) {
+        const float2* pa = Qf + b * q_bstride + k * q_kstride + (long long)(va ? ga : 0) * NXh;
+        const float2* pb = Qf + b * q_bstride + k * q_kstride + (long long)(vb ? gb : 0) * NXh;
+        const float* sa = u + b * u_bstride + (long long)(va ? ga : 0) * NX;
+        const float* sb = u + b * u_bstride + (long long)(vb ? gb : 0) * NX;
+#pragma unroll
+        for (int r = 0; r < kR; ++r) {
+            const int f = j + r * T;
+            const float2 xa = va ? load_half<NX>(pa, f) : make_float2(0.f, 0.f);
+            const float2 xb = vb ? load_half<NX>(pb, f) : make_float2(0.f, 0.f);
+            v[r] = make_float2(xa.x - xb.y, xa.y + xb.x);
+            ua[r] = va ? __ldg(sa + f) : 0.f;
+            ub[r] = vb ? __ldg(sb + f) : 0.f;
+        }
+    };
+    float2 acc[kR];
+#pragma unroll
+    for (int r = 0; r < kR; ++r) acc[r] = make_float2(0.f, 0.f);
+    float2 v[kR];
+    float ua[kR], ub[kR];
+    load(0, v, ua, ub);
+    for (int b = 0; b < nb; ++b) {
+        const bool more = b + 1 < nb;
+        float2 vn[kR];
+        float uan[kR], ubn[kR];
+        if (more) load(b + 1, vn, uan, ubn);
+        fft<NX, true>(v, j, b0, b1, tw);
+#pragma unroll
+        for (int r = 0; r < kR; ++r) {
+            acc[r].x = fmaf(ua[r], v[r].x, acc[r].x);
+            acc[r].y = fmaf(ub[r], v[r].y, acc[r].y);
+        }
+        if (more) {
+#pragma unroll
+            for (int r = 0; r < kR; ++r) {
+                v[r] = vn[r];
+                ua[r] = uan[r];
+                ub[r] = ubn[r];
+            }
+        }
+    }
+    float* da = dw + ((long long)k * nrows + ga) * NX;
+    float* db = dw + ((long long)k * nrows + gb) * NX;
+#pragma unroll
+    for (int r = 0; r < kR; ++r) {
+        const int n = j + r * T;
+        if (va) da[n] = acc[r].x * scale + (accumulate ? da[n] : 0.f);
+        if (vb) db[n] = acc[r].y * scale + (accumulate ? db[n] : 0.f);
     }
 }
 
@@ -799,6 +1054,111 @@ k_spec_1d(const float* __restrict__ h, int m, float2* __restrict__ hp,
         }
         if (a0) hp[(long long)k0 * Nh + f] = A;
         if (a1) hp[(long long)k1 * Nh + f] = B;
+    }
+}
+
+// 1D backward for term k = blockIdx.x: dhhat_k (natural [N/2+1]) and dw_k
+// ([N]); slots take right-hand sides.  w_k . u_b + i r_b share one FFT; the
+// inverse FFT of conj(hhat_k) . R_b gives the correlation of r_b with h_k.
+template <int N>
+__global__ void __launch_bounds__(Cfg1d<N>::NT)
+k_grad_1d(const float* __restrict__ u, const float* __restrict__ rr, const float* __restrict__ w,
+          const float2* __restrict__ hp, int nb, float2* __restrict__ dh, float* __restrict__ dw,
+          float scale, int accumulate, const float2* __restrict__ tw) {
+    using CF = Cfg1d<N>;
+    constexpr int T = CF::T;
+    constexpr int G = CF::G;
+    constexpr int Nh = N / 2;
+    extern __shared__ float2 smem[];
+    const int slot = threadIdx.x / T;
+    const int j = threadIdx.x - slot * T;
+    float2* b0 = smem + slot * fft_region(N);
+    float2* b1 = b0 + pad_len(N);
+    const int k = blockIdx.x;
+    const float2* hk = hp + (long long)k * Nh;
+    float wk[kR];
+#pragma unroll
+    for (int r = 0; r < kR; ++r) wk[r] = __ldg(w + (long long)k * N + j + r * T);
+    float2 ah[kR / 2];
+    float aw[kR];
+    float ahn = 0.f;   // Nyquist (thread j = 0)
+#pragma unroll
+    for (int r = 0; r < kR / 2; ++r) ah[r] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int r = 0; r < kR; ++r) aw[r] = 0.f;
+    const int iters = (nb + G - 1) / G;
+    for (int it = 0; it < iters; ++it) {
+        const int b = it * G + slot;
+        const bool act = b < nb;
+        float2 v[kR];
+        float ub[kR];
+#pragma unroll
+        for (int r = 0; r < kR; ++r) {
+            const int n = j + r * T;
+            ub[r] = act ? __ldg(u + (long long)b * N + n) : 0.f;
+            v[r] = make_float2(wk[r] * ub[r], act ? __ldg(rr + (long long)b * N + n) : 0.f);
+        }
+        fft<N, false>(v, j, b0, b1, tw);
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kR; ++r) b0[padi(j + r * T)] = v[r];
+        __syncthreads();
+        float2 p[kR];
+#pragma unroll
+        for (int r = 0; r < kR; ++r) {
+            const int f = j + r * T;
+            float2 X, R;
+            split_dc_nyq(v[r], b0[padi((N - f) & (N - 1))], X, R);
+            if (r < kR / 2) {
+                if (f == 0) {
+                    ah[0].x = fmaf(R.x, X.x, ah[0].x);
+                } else {
+                    ah[r] = cfmac(X, R, ah[r]);
+                }
+            }
+            if (f == Nh) ahn = fmaf(R.x, X.x, ahn);
+            p[r] = cmulc(R, load_half<N>(hk, f));
+        }
+        fft<N, true>(p, j, b0, b1, tw);
+#pragma unroll
+        for (int r = 0; r < kR; ++r) aw[r] = fmaf(ub[r], p[r].x, aw[r]);
+    }
+    // reduce over slots: half spectrum into b0 (float2), window gradient into b1 (float)
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kR / 2; ++r) b0[j + r * T] = ah[r];
+    if (j == 0) b0[Nh] = make_float2(ahn, 0.f);
+    float* fw = reinterpret_cast<float*>(b1);
+#pragma unroll
+    for (int r = 0; r < kR; ++r) fw[j + r * T] = aw[r];
+    __syncthreads();
+    if (slot == 0) {
+        float2* dk = dh + (long long)k * (Nh + 1);
+        float* wk_out = dw + (long long)k * N;
+#pragma unroll
+        for (int r = 0; r < kR / 2; ++r) {
+            const int f = j + r * T;
+            float2 s = smem[f];
+            for (int g = 1; g < G; ++g) s = cadd(s, smem[g * fft_region(N) + f]);
+            float2 out = f == 0 ? make_float2(s.x * scale, 0.f) : cscale(s, 2.f * scale);
+            if (accumulate) out = cadd(out, dk[f]);
+            dk[f] = out;
+        }
+        if (j == 0) {
+            float sn = smem[Nh].x;
+            for (int g = 1; g < G; ++g) sn += smem[g * fft_region(N) + Nh].x;
+            float2 out = make_float2(sn * scale, 0.f);
+            if (accumulate) out = cadd(out, dk[Nh]);
+            dk[Nh] = out;
+        }
+#pragma unroll
+        for (int r = 0; r < kR; ++r) {
+            const int n = j + r * T;
+            float s = fw[n];
+            for (int g = 1; g < G; ++g)
+                s += reinterpret_cast<const float*>(smem + g * fft_region(N) + pad_len(N))[n];
+            wk_out[n] = s * scale + (accumulate ? wk_out[n] : 0.f);
+        }
     }
 }
 

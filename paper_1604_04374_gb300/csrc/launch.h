@@ -15,6 +15,8 @@ int cols_columns_per_cta(int ny);
 int cols_smem(int ny);
 // Rows handled per CTA of the row kernels (two rows per FFT).
 int rows_pairs_per_cta(int nx);
+// Items (row pairs) handled per CTA of the R2C row kernel.
+int rows_r2c_items_per_cta(int nx);
 // 1D kernels.
 int fft1d_threads(int n);
 int fft1d_smem(int n);
@@ -51,6 +53,25 @@ cudaError_t launch_cols_spec(int ny, dim3 grid, cudaStream_t s, const float2* S,
 
 cudaError_t launch_plain_cols_inv(int ny, dim3 grid, cudaStream_t s, const float2* acc,
                                   const float2* accN, int nxh, float2* A, const float2* tw);
+
+cudaError_t launch_cols_adj_full(int ny, dim3 grid, cudaStream_t s, const float2* V, long long v_bstride,
+                                 const float2* hh, const float2* hN, int m, const Box* box, int nxh,
+                                 float2* Q, long long q_bstride, long long q_kstride,
+                                 const float2* tw);
+
+cudaError_t launch_cols_grad_h(int ny, dim3 grid, cudaStream_t s, const float2* Z, long long z_bstride,
+                               long long z_kstride, int nb, const float2* Rh, const float2* RhN,
+                               const Box* box, int nxh, float2* dhh, float scale, int accumulate,
+                               const float2* tw);
+
+cudaError_t launch_rows_grad_w(int nx, dim3 grid, cudaStream_t s, const float2* Qf, long long q_bstride,
+                               long long q_kstride, int nrows, int nb, const float* u,
+                               long long u_bstride, float* dw, float scale, int accumulate,
+                               const float2* tw);
+
+cudaError_t launch_grad_1d(int n, int m, cudaStream_t s, const float* u, const float* r,
+                           const float* w, const float2* hp, int nb, float2* dh, float* dw,
+                           float scale, int accumulate, const float2* tw);
 
 cudaError_t launch_fwd_1d(int n, int batch, cudaStream_t s, const float* u, const float* w,
                           const float2* hp, int m, float* y, float scale, const float2* tw);

@@ -247,6 +247,12 @@ __global__ void k_plain_spec_mac(const float2* __restrict__ S, const float2* __r
     }
 }
 
+// CTAs of the R2C row kernel for `items` row pairs of length nx.
+unsigned r2c_blocks(int items, int nx) {
+    const int ipc = pce::rows_r2c_items_per_cta(nx);
+    return (unsigned)((items + ipc - 1) / ipc);
+}
+
 unsigned grid_for(long long total, int threads = 256) {
     long long g = (total + threads - 1) / threads;
     return (unsigned)std::max<long long>(1, std::min<long long>(g, 1 << 20));
@@ -538,7 +544,7 @@ pce_status create_common(pce_plan_t* out, int ndims, const int64_t* shape, int m
             if ((st = dev_alloc(&S, (size_t)m * ny * nxh))) return bail(st);
             const int fpc = pce::rows_pairs_per_cta(nx);
             const int npairs = (ny + 1) / 2;
-            cudaError_t e = pce::launch_rows_r2c(nx, false, dim3((npairs + fpc - 1) / fpc, m), s, h,
+            cudaError_t e = pce::launch_rows_r2c(nx, false, dim3(r2c_blocks(npairs, nx), m), s, h,
                                                  (long long)ny * nx, ny, nullptr, nullptr, nullptr,
                                                  npairs, S, (long long)ny * nxh, 0, p->twx);
             const int cpc = pce::cols_columns_per_cta(ny);
@@ -634,7 +640,7 @@ pce_status apply_plain(pce_plan_t p, const float* in, float* out, int64_t batch,
                 });
                 if (e == cudaSuccess)
                     e = timed(p, PCE_KERNEL_PLAIN, s, [&] {
-                        return pce::launch_rows_r2c(nx, false, dim3((npairs + fpc - 1) / fpc, nb), s, tmp,
+                        return pce::launch_rows_r2c(nx, false, dim3(r2c_blocks(npairs, nx), nb), s, tmp,
                                                     P, ny, nullptr, nullptr, nullptr, npairs, S, H, 0,
                                                     p->twx);
                     });
@@ -662,7 +668,7 @@ pce_status apply_plain(pce_plan_t p, const float* in, float* out, int64_t batch,
                 });
         } else {
             e = timed(p, PCE_KERNEL_PLAIN, s, [&] {
-                return pce::launch_rows_r2c(nx, false, dim3((npairs + fpc - 1) / fpc, nb), s, src, P, ny,
+                return pce::launch_rows_r2c(nx, false, dim3(r2c_blocks(npairs, nx), nb), s, src, P, ny,
                                             nullptr, nullptr, nullptr, npairs, S, H, 0, p->twx);
             });
             if (e == cudaSuccess)
@@ -733,7 +739,7 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
         if (!adjoint) {
             if (p->nitems > 0)
                 e = timed(p, PCE_KERNEL_ROWS_R2C_WINDOW, s, [&] {
-                    return pce::launch_rows_r2c(nx, true, dim3((p->nitems + fpc - 1) / fpc, nb), s, src,
+                    return pce::launch_rows_r2c(nx, true, dim3(r2c_blocks(p->nitems, nx), nb), s, src,
                                                 P, ny, p->wbox, p->d_box, p->items, p->nitems, p->scrZ,
                                                 zb, zk, p->twx);
                 });
@@ -749,7 +755,7 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
                 });
         } else {
             e = timed(p, PCE_KERNEL_ROWS_R2C, s, [&] {
-                return pce::launch_rows_r2c(nx, false, dim3((npairs + fpc - 1) / fpc, nb), s, src, P,
+                return pce::launch_rows_r2c(nx, false, dim3(r2c_blocks(npairs, nx), nb), s, src, P,
                                             ny, nullptr, nullptr, nullptr, npairs, p->scrA, ab, 0,
                                             p->twx);
             });
@@ -891,6 +897,114 @@ int64_t pce_launch_count(pce_plan_t plan, int adjoint, int64_t batch) {
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
+// Gradients.
+namespace {
+
+constexpr long long kBackwardBudget = 2ll << 30;   // bytes of workspace per call at most
+
+// Right-hand sides per chunk of the 2D backward and workspace float2 per right-hand side.
+void backward_layout(pce_plan_t p, int64_t batch, long long& per_b, long long& chunk) {
+    const long long nxh = p->nx / 2;
+    const long long H = (long long)p->ny * nxh;
+    per_b = 2 * H + p->ny + (long long)p->m * p->nrmax * nxh + (long long)p->m * H;
+    chunk = std::max<long long>(1, std::min<long long>(batch, kBackwardBudget / (per_b * 8)));
+}
+
+}  // namespace
+
+extern "C" int64_t pce_backward_workspace_bytes(pce_plan_t p, int64_t batch) {
+    if (!p || batch < 0) return 0;
+    if (p->ndims == 1) {
+        // stand-in outputs for a skipped dw or dhhat
+        return (int64_t)p->m * ((p->nx / 2 + 1) * 8 + p->nx * 4);
+    }
+    if (batch == 0) return 0;
+    long long per_b, chunk;
+    backward_layout(p, batch, per_b, chunk);
+    return chunk * per_b * 8;
+}
+
+extern "C" pce_status pce_backward(pce_plan_t p, const float* u, const float* r, float* du, float* dw,
+                                   float* dhhat, int64_t batch, void* workspace,
+                                   int64_t workspace_bytes, void* stream) {
+    pce_status st = check_plan(p);
+    if (st) return st;
+    if (batch < 0) return fail(PCE_ERR_INVALID, "batch must be >= 0");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int ny = p->ny, nx = p->nx, m = p->m, nxh = nx / 2;
+    const long long P = (long long)ny * nx;
+    const long long H = (long long)ny * nxh;
+    const size_t dh_bytes = sizeof(float2) * (size_t)m * (p->ndims == 1 ? (nxh + 1) : ny * (nxh + 1));
+    const size_t dw_bytes = sizeof(float) * (size_t)m * P;
+    for (const void* q : {(const void*)du, (const void*)dw, (const void*)dhhat})
+        if (q && !is_device_ptr(q)) return fail(PCE_ERR_INVALID, "gradient outputs must be device pointers");
+    if (batch == 0) {
+        if (dw) PCE_CK(cudaMemsetAsync(dw, 0, dw_bytes, s));
+        if (dhhat) PCE_CK(cudaMemsetAsync(dhhat, 0, dh_bytes, s));
+        return PCE_OK;
+    }
+    if (!is_device_ptr(u) || !is_device_ptr(r)) return fail(PCE_ERR_INVALID, "u and r must be device pointers");
+    const int64_t need = pce_backward_workspace_bytes(p, batch);
+    if (need > 0 && (!workspace || workspace_bytes < need || !is_device_ptr(workspace)))
+        return fail(PCE_ERR_INVALID, "workspace must be a device buffer of at least %lld bytes",
+                    (long long)need);
+    if (du) {
+        if ((st = check_io(p, r, du, batch))) return st;
+        if ((st = apply_impl(p, r, du, batch, true, s))) return st;
+    }
+    if (!dw && !dhhat) return PCE_OK;
+    const float scale = 1.0f / (float)P;
+    cudaError_t e = cudaSuccess;
+    if (p->ndims == 1) {
+        char* ws = static_cast<char*>(workspace);
+        float2* dh_out = dhhat ? reinterpret_cast<float2*>(dhhat) : reinterpret_cast<float2*>(ws);
+        float* dw_out = dw ? dw : reinterpret_cast<float*>(ws + (size_t)m * (nxh + 1) * 8);
+        e = pce::launch_grad_1d(nx, m, s, u, r, p->wbox, p->hh, (int)batch, dh_out, dw_out, scale, 0, p->twx);
+        if (e) return fail(PCE_ERR_CUDA, "1D backward launch: %s", cudaGetErrorString(e));
+        return PCE_OK;
+    }
+    long long per_b, chunk;
+    backward_layout(p, batch, per_b, chunk);
+    const int fpc = pce::rows_pairs_per_cta(nx);
+    const int cpc = pce::cols_columns_per_cta(ny);
+    const int npairs = (ny + 1) / 2;
+    const int tiles = (nxh + cpc - 1) / cpc;
+    const long long zk = (long long)p->nrmax * nxh;
+    const long long zb = (long long)m * zk;
+    for (long long b0 = 0; b0 < batch && e == cudaSuccess; b0 += chunk) {
+        const int nb = (int)std::min<long long>(chunk, batch - b0);
+        float2* S = static_cast<float2*>(workspace);
+        float2* Rh = S + nb * H;
+        float2* RhN = Rh + nb * H;
+        float2* Zg = RhN + (long long)nb * ny;
+        float2* Qf = Zg + nb * zb;
+        const float* ub = u + b0 * P;
+        const float* rb = r + b0 * P;
+        const int acc = b0 > 0 ? 1 : 0;
+        e = pce::launch_rows_r2c(nx, false, dim3(r2c_blocks(npairs, nx), nb), s, rb, P, ny, nullptr,
+                                 nullptr, nullptr, npairs, S, H, 0, p->twx);
+        if (dhhat && e == cudaSuccess) {
+            e = pce::launch_cols_spec(ny, dim3(nb, tiles), s, S, nxh, Rh, RhN, p->twy);
+            if (e == cudaSuccess && p->nitems > 0)
+                e = pce::launch_rows_r2c(nx, true, dim3(r2c_blocks(p->nitems, nx), nb), s, ub, P, ny,
+                                         p->wbox, p->d_box, p->items, p->nitems, Zg, zb, zk, p->twx);
+            if (e == cudaSuccess)
+                e = pce::launch_cols_grad_h(ny, dim3(m, tiles), s, Zg, zb, zk, nb, Rh, RhN, p->d_box, nxh,
+                                            reinterpret_cast<float2*>(dhhat), scale, acc, p->twy);
+        }
+        if (dw && e == cudaSuccess) {
+            e = pce::launch_cols_adj_full(ny, dim3(nb, tiles), s, S, H, p->hh, p->hN, m, p->d_box, nxh, Qf,
+                                          (long long)m * H, H, p->twy);
+            if (e == cudaSuccess)
+                e = pce::launch_rows_grad_w(nx, dim3((npairs + fpc - 1) / fpc, m), s, Qf, (long long)m * H, H,
+                                            ny, nb, ub, P, dw, scale, acc, p->twx);
+        }
+    }
+    if (e) return fail(PCE_ERR_CUDA, "2D backward launch: %s", cudaGetErrorString(e));
+    return PCE_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Forward apply without any allocation (no counterpart in the paper).
 //
 // pce_apply runs the 2D passes on intermediates that the plan allocated with
@@ -974,7 +1088,7 @@ extern "C" pce_status pce_apply_noalloc(pce_plan_t plan, const float* u, float* 
     for (long long b0 = 0; b0 < batch && e == cudaSuccess; b0 += chunk) {
         const int nb = (int)std::min<long long>(chunk, batch - b0);
         if (plan->nitems > 0)
-            e = pce::launch_rows_r2c(nx, true, dim3((plan->nitems + fpc - 1) / fpc, nb), s, u + b0 * P, P,
+            e = pce::launch_rows_r2c(nx, true, dim3(r2c_blocks(plan->nitems, nx), nb), s, u + b0 * P, P,
                                      ny, plan->wbox, plan->d_box, plan->items, plan->nitems, scrZ, zb, zk,
                                      plan->twx);
         if (e == cudaSuccess)

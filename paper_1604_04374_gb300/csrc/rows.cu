@@ -5,6 +5,7 @@
 namespace pce {
 
 int rows_pairs_per_cta(int nx) { return 256 / (nx / kR); }
+int rows_r2c_items_per_cta(int nx) { return kRowIters * (256 / (nx / kR)); }
 
 #define PCE_ROW_SIZES(X) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048)
 
@@ -57,6 +58,24 @@ cudaError_t launch_rows_adj(int nx, dim3 grid, cudaStream_t s, const float2* Q, 
     case N:                                                                                    \
         k_rows_adj<N><<<grid, 256, 0, s>>>(Q, q_bstride, q_kstride, nrows, wbox, box, kptr,     \
                                            klist, dst, dst_bstride, scale, tw);                \
+        break;
+        PCE_ROW_SIZES(X)
+#undef X
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rows_grad_w(int nx, dim3 grid, cudaStream_t s, const float2* Qf, long long q_bstride,
+                               long long q_kstride, int nrows, int nb, const float* u,
+                               long long u_bstride, float* dw, float scale, int accumulate,
+                               const float2* tw) {
+    switch (nx) {
+#define X(N)                                                                                   \
+    case N:                                                                                    \
+        k_rows_grad_w<N><<<grid, 256, 0, s>>>(Qf, q_bstride, q_kstride, nrows, nb, u, u_bstride, \
+                                              dw, scale, accumulate, tw);                      \
         break;
         PCE_ROW_SIZES(X)
 #undef X

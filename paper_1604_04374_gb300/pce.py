@@ -51,6 +51,10 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.pce_last_error_string.argtypes = []
     lib.pce_launch_count.argtypes = [P, ctypes.c_int, i64]
     lib.pce_launch_count.restype = i64
+    lib.pce_backward_workspace_bytes.argtypes = [P, i64]
+    lib.pce_backward_workspace_bytes.restype = i64
+    lib.pce_backward.argtypes = [P, P, P, P, P, P, i64, P, i64, P]
+    lib.pce_backward.restype = ctypes.c_int
     lib.pce_apply_noalloc.argtypes = [P, P, P, i64, P]
     lib.pce_apply_noalloc.restype = ctypes.c_int
     lib.pce_plan_set_timing.argtypes = [P, ctypes.c_int]
@@ -102,6 +106,18 @@ def pce_apply_adjoint(plan: int, v_ptr: int, x_ptr: int, batch: int, stream: int
 def pce_apply_noalloc(plan: int, u_ptr: int, y_ptr: int, batch: int, stream: int = 0) -> None:
     """y = H_m u on a 2D plan with the intermediates in the library's static device scratch."""
     _check(load_library().pce_apply_noalloc(plan, u_ptr, y_ptr, batch, stream))
+
+
+def pce_backward_workspace_bytes(plan: int, batch: int) -> int:
+    return int(load_library().pce_backward_workspace_bytes(plan, batch))
+
+
+def pce_backward(plan: int, u_ptr: int, r_ptr: int, du_ptr: int, dw_ptr: int, dhhat_ptr: int,
+                 batch: int, workspace_ptr: int, workspace_bytes: int, stream: int = 0) -> None:
+    """Gradients of L(y), y = H_m u, given r = dL/dy (any output pointer may be 0 to skip it)."""
+    _check(load_library().pce_backward(plan, u_ptr, r_ptr, du_ptr or None, dw_ptr or None,
+                                       dhhat_ptr or None, batch, workspace_ptr or None,
+                                       workspace_bytes, stream))
 
 
 def pce_plan_info(plan: int, m: int):
@@ -231,6 +247,24 @@ class Plan:
 
     def launch_count(self, adjoint: bool, batch: int) -> int:
         return pce_launch_count(self.handle, adjoint, batch)
+
+    def backward(self, u, r, need_u=True, need_w=True, need_hhat=True, stream=None):
+        """(du, dw, dhhat) of L(y), y = H_m u, given r = dL/dy; skipped ones are None."""
+        import torch
+        batch, _ = self._io(u, u, "u")
+        _need_cuda_f32(r, "r")
+        if r.shape != u.shape:
+            raise ValueError("r must have the shape of u")
+        du = torch.empty_like(u) if need_u else None
+        dw = torch.empty((self.m,) + self.shape, dtype=torch.float32, device=self.device) if need_w else None
+        dh = (torch.empty((self.m,) + self.shape[:-1] + (self.shape[-1] // 2 + 1,), dtype=torch.complex64,
+                          device=self.device) if need_hhat else None)
+        nbytes = pce_backward_workspace_bytes(self.handle, batch)
+        ws = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=self.device)
+        pce_backward(self.handle, u.data_ptr(), r.data_ptr(), du.data_ptr() if du is not None else 0,
+                     dw.data_ptr() if dw is not None else 0, dh.data_ptr() if dh is not None else 0,
+                     batch, ws.data_ptr(), nbytes, _stream_handle(stream))
+        return du, dw, dh
 
     def set_timing(self, enable: bool) -> None:
         pce_plan_set_timing(self.handle, enable)
