@@ -27,8 +27,11 @@
  * - Spectra are R2C half spectra along x: [Ny][Nx/2+1] complex64 (interleaved
  *   re, im), forward DFT X[f] = sum_j x[j] exp(-2 i pi j f / N) (the sign of
  *   the Fourier atoms of Section 2), unnormalised; inverses carry 1/N.
- * - Sizes are powers of two: N in [16, 8192] in 1D, Ny and Nx in [16, 2048]
- *   in 2D.  m >= 1.  Other sizes return PCE_ERR_UNSUPPORTED.
+ * - Sizes are powers of two: N in [16, 262144] in 1D, Ny and Nx in [16, 2048]
+ *   in 2D.  m >= 1.  Other sizes return PCE_ERR_UNSUPPORTED.  1D sizes above
+ *   8192 run a four-step FFT (column FFTs, twiddles, row FFTs over an
+ *   NY x NX view of the sequence); on those plans PCE_FLAG_LOWP_STORAGE and
+ *   pce_backward return PCE_ERR_UNSUPPORTED.
  * - Pointers named "device" must be CUDA device (or managed) memory of the
  *   current device; a host pointer returns PCE_ERR_INVALID.
  * - Calls are stream-ordered on `stream` (a cudaStream_t; NULL is the legacy
@@ -72,6 +75,16 @@ typedef struct pce_plan* pce_plan_t;
  * core and exists as the baseline the fused path is measured against.
  */
 #define PCE_FLAG_UNFUSED 1u
+/*
+ * PCE_FLAG_LOWP_STORAGE: the applies read the windows as bfloat16 and the
+ * spectra as FP16 complex, each term's spectrum divided by a power of two
+ * s_k = 2^ceil(log2 max |Re hhat_k|, |Im hhat_k|), which halves the bytes of
+ * w and hhat an apply reads.  FFTs, products and accumulations stay FP32.
+ * The plan's operator is the one with the rounded w_k and hhat_k
+ * (pce_plan_hhat returns the rounded spectra).  Not combinable with
+ * PCE_FLAG_UNFUSED; pce_backward returns PCE_ERR_UNSUPPORTED on such plans.
+ */
+#define PCE_FLAG_LOWP_STORAGE 2u
 
 /*
  * pce_plan_create -- precompute everything an operator needs (Eq. 1.4).
@@ -82,7 +95,8 @@ typedef struct pce_plan* pce_plan_t;
  *   m      : number of terms.
  *   w      : device, [m][shape] float32 windows w_k.
  *   h      : device, [m][shape] float32 impulse responses h_k, origin at index 0.
- *   flags  : PCE_FLAG_NONE or PCE_FLAG_UNFUSED; other bits return PCE_ERR_INVALID.
+ *   flags  : PCE_FLAG_NONE, PCE_FLAG_UNFUSED or PCE_FLAG_LOWP_STORAGE; other bits
+ *            return PCE_ERR_INVALID.
  *   stream : cudaStream_t used for the set-up work.
  *
  * The plan finds the support box of every w_k (the smallest periodic
@@ -181,6 +195,22 @@ enum {
 };
 pce_status pce_plan_set_timing(pce_plan_t plan, int enable);
 pce_status pce_plan_timing(pce_plan_t plan, int kind, double* total_ms, int64_t* launches);
+
+/*
+ * Failure detection.  Kernels that wait for an asynchronous copy (an
+ * mbarrier wait) give up after a bounded time (about a second) instead of
+ * hanging, skip the work that needed the copy and record the timeout in the
+ * plan's device status word.
+ *
+ * pce_plan_status: synchronise `stream`, return PCE_ERR_TIMEOUT if a kernel
+ *   recorded a timeout since the last call (and clear it), else PCE_OK.
+ * pce_plan_inject_wait_timeout (test support): with wait_cycles > 0, later
+ *   applies arm their barriers without starting the copies, so each wait runs
+ *   out after wait_cycles clock cycles and the results are wrong; 0 restores
+ *   normal operation.  No copy is left in flight either way.
+ */
+pce_status pce_plan_status(pce_plan_t plan, void* stream);
+pce_status pce_plan_inject_wait_timeout(pce_plan_t plan, int64_t wait_cycles);
 
 /*
  * Gradients (autograd support).

@@ -46,6 +46,22 @@ def rdft(x: np.ndarray) -> np.ndarray:
     return dft(x, axis=-1)[..., : n // 2 + 1]
 
 
+def dft_at(x: np.ndarray, freqs) -> np.ndarray:
+    """Forward DFT of the last axis at selected frequencies only (same definition as ``dft``).
+
+    X[..., s] = sum_j x[..., j] exp(-2 i pi (j f_s mod n) / n); one O(n) sum per
+    frequency, for lengths whose full DFT matrix would not fit in memory.
+    """
+    x = np.asarray(x)
+    n = x.shape[-1]
+    j = np.arange(n, dtype=np.int64)
+    out = np.empty(x.shape[:-1] + (len(freqs),), dtype=np.complex128)
+    for s, f in enumerate(freqs):
+        atom = np.exp(-2j * np.pi * ((j * int(f)) % n) / n)
+        out[..., s] = x.astype(np.complex128) @ atom
+    return out
+
+
 def irdft(X: np.ndarray, n: int) -> np.ndarray:
     """Complex-to-real inverse of the last axis from the half spectrum (C2R).
 

@@ -1,5 +1,6 @@
 // cols.cu -- instances of the column-pass kernels for NY = 16 .. 2048.
 #include "kernels.cuh"
+#include "wkernels.cuh"
 #include "launch.h"
 
 namespace pce {
@@ -32,16 +33,33 @@ int cols_smem(int ny) {
 }
 
 cudaError_t prepare_cols() {
-    cudaError_t e = cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(kw_cols_fwd<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWColSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kw_cols_fwd<__half2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWColSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kw_cols_adj<false, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kWColSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kw_cols_adj<false, __half2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kWColSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kw_cols_adj<true, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kWColSmem);
 #define X(N)                                                                                   \
     if (e == cudaSuccess)                                                                      \
-        e = cudaFuncSetAttribute(k_cols_fwd<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
-                                 ColCfg<N>::SMEM);                                             \
-    if (e == cudaSuccess)                                                                      \
-        e = cudaFuncSetAttribute(k_cols_adj<N, false>,                                         \
+        e = cudaFuncSetAttribute(k_cols_fwd<N, float2>,                                        \
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, ColCfg<N>::SMEM); \
     if (e == cudaSuccess)                                                                      \
-        e = cudaFuncSetAttribute(k_cols_adj<N, true>,                                          \
+        e = cudaFuncSetAttribute(k_cols_fwd<N, __half2>,                                       \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, ColCfg<N>::SMEM); \
+    if (e == cudaSuccess)                                                                      \
+        e = cudaFuncSetAttribute(k_cols_adj<N, false, float2>,                                 \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, ColCfg<N>::SMEM); \
+    if (e == cudaSuccess)                                                                      \
+        e = cudaFuncSetAttribute(k_cols_adj<N, false, __half2>,                                \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, ColCfg<N>::SMEM); \
+    if (e == cudaSuccess)                                                                      \
+        e = cudaFuncSetAttribute(k_cols_adj<N, true, float2>,                                  \
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, ColCfg<N>::SMEM); \
     if (e == cudaSuccess)                                                                      \
         e = cudaFuncSetAttribute(k_cols_grad_h<N>,                                             \
@@ -58,15 +76,33 @@ cudaError_t prepare_cols() {
 }
 
 cudaError_t launch_cols_fwd(int ny, dim3 grid, cudaStream_t s, const float2* Z, long long z_bstride,
-                            long long z_kstride, const float2* hh, const float2* hN, int m,
+                            long long z_kstride, const void* hh, const void* hN, const float* hscale,
+                            bool lowp, int m,
                             const Box* box, int nxh, float2* A, long long a_bstride,
-                            const float2* tw) {
+                            const float2* tw, const void* hhT, const float2* tw1024, int* status,
+                            long long wait_limit, int skip_copy) {
+    if (ny == kWarpN) {
+        if (lowp)
+            kw_cols_fwd<__half2><<<grid, kWColWarps * 32, kWColSmem, s>>>(
+                Z, z_bstride, z_kstride, static_cast<const __half2*>(hhT), static_cast<const __half2*>(hN),
+                hscale, m, box, nxh, A, a_bstride, tw1024, status, wait_limit, skip_copy);
+        else
+            kw_cols_fwd<float2><<<grid, kWColWarps * 32, kWColSmem, s>>>(
+                Z, z_bstride, z_kstride, static_cast<const float2*>(hhT), static_cast<const float2*>(hN),
+                hscale, m, box, nxh, A, a_bstride, tw1024, status, wait_limit, skip_copy);
+        return cudaGetLastError();
+    }
     switch (ny) {
-#define X(N)                                                                                  \
-    case N:                                                                                   \
-        k_cols_fwd<N><<<grid, ColCfg<N>::NT, ColCfg<N>::SMEM, s>>>(Z, z_bstride, z_kstride, hh, \
-                                                                   hN, m, box, nxh, A,         \
-                                                                   a_bstride, tw);             \
+#define X(N)                                                                                   \
+    case N:                                                                                    \
+        if (lowp)                                                                              \
+            k_cols_fwd<N, __half2><<<grid, ColCfg<N>::NT, ColCfg<N>::SMEM, s>>>(                 \
+                Z, z_bstride, z_kstride, static_cast<const __half2*>(hh),                      \
+                static_cast<const __half2*>(hN), hscale, m, box, nxh, A, a_bstride, tw);        \
+        else                                                                                   \
+            k_cols_fwd<N, float2><<<grid, ColCfg<N>::NT, ColCfg<N>::SMEM, s>>>(                  \
+                Z, z_bstride, z_kstride, static_cast<const float2*>(hh),                       \
+                static_cast<const float2*>(hN), hscale, m, box, nxh, A, a_bstride, tw);         \
         break;
         PCE_COL_SIZES(X)
 #undef X
@@ -77,14 +113,32 @@ cudaError_t launch_cols_fwd(int ny, dim3 grid, cudaStream_t s, const float2* Z, 
 }
 
 cudaError_t launch_cols_adj(int ny, dim3 grid, cudaStream_t s, const float2* V, long long v_bstride,
-                            const float2* hh, const float2* hN, int m, const Box* box, int nxh,
-                            float2* Q, long long q_bstride, long long q_kstride, const float2* tw) {
+                            const void* hh, const void* hN, const float* hscale, bool lowp, int m,
+                            const Box* box, int nxh, float2* Q, long long q_bstride, long long q_kstride,
+                            const float2* tw, const void* hhT, const float2* tw1024, int* status,
+                            long long wait_limit, int skip_copy) {
+    if (ny == kWarpN) {
+        if (lowp)
+            kw_cols_adj<false, __half2><<<grid, kWColWarps * 32, kWColSmem, s>>>(
+                V, v_bstride, static_cast<const __half2*>(hhT), static_cast<const __half2*>(hN), hscale, m,
+                box, nxh, Q, q_bstride, q_kstride, tw1024, status, wait_limit, skip_copy);
+        else
+            kw_cols_adj<false, float2><<<grid, kWColWarps * 32, kWColSmem, s>>>(
+                V, v_bstride, static_cast<const float2*>(hhT), static_cast<const float2*>(hN), hscale, m,
+                box, nxh, Q, q_bstride, q_kstride, tw1024, status, wait_limit, skip_copy);
+        return cudaGetLastError();
+    }
     switch (ny) {
-#define X(N)                                                                                  \
-    case N:                                                                                   \
-        k_cols_adj<N, false><<<grid, ColCfg<N>::NT, ColCfg<N>::SMEM, s>>>(V, v_bstride, hh, hN, m, box, \
-                                                                   nxh, Q, q_bstride,          \
-                                                                   q_kstride, tw);             \
+#define X(N)                                                                                   \
+    case N:                                                                                    \
+        if (lowp)                                                                              \
+            k_cols_adj<N, false, __half2><<<grid, ColCfg<N>::NT, ColCfg<N>::SMEM, s>>>(          \
+                V, v_bstride, static_cast<const __half2*>(hh), static_cast<const __half2*>(hN),  \
+                hscale, m, box, nxh, Q, q_bstride, q_kstride, tw);                             \
+        else                                                                                   \
+            k_cols_adj<N, false, float2><<<grid, ColCfg<N>::NT, ColCfg<N>::SMEM, s>>>(           \
+                V, v_bstride, static_cast<const float2*>(hh), static_cast<const float2*>(hN),    \
+                hscale, m, box, nxh, Q, q_bstride, q_kstride, tw);                             \
         break;
         PCE_COL_SIZES(X)
 #undef X
@@ -127,13 +181,19 @@ cudaError_t launch_plain_cols_inv(int ny, dim3 grid, cudaStream_t s, const float
 cudaError_t launch_cols_adj_full(int ny, dim3 grid, cudaStream_t s, const float2* V, long long v_bstride,
                                  const float2* hh, const float2* hN, int m, const Box* box, int nxh,
                                  float2* Q, long long q_bstride, long long q_kstride,
-                                 const float2* tw) {
+                                 const float2* tw, const float2* hhT, const float2* tw1024, int* status,
+                                 long long wait_limit, int skip_copy) {
+    if (ny == kWarpN) {
+        kw_cols_adj<true, float2><<<grid, kWColWarps * 32, kWColSmem, s>>>(
+            V, v_bstride, hhT, hN, nullptr, m, box, nxh, Q, q_bstride, q_kstride, tw1024, status, wait_limit,
+            skip_copy);
+        return cudaGetLastError();
+    }
     switch (ny) {
 #define X(N)                                                                                   \
     case N:                                                                                    \
-        k_cols_adj<N, true><<<grid, ColCfg<N>::NT, ColCfg<N>::SMEM, s>>>(V, v_bstride, hh, hN, m, \
-                                                                         box, nxh, Q, q_bstride, \
-                                                                         q_kstride, tw);       \
+        k_cols_adj<N, true, float2><<<grid, ColCfg<N>::NT, ColCfg<N>::SMEM, s>>>(                \
+            V, v_bstride, hh, hN, nullptr, m, box, nxh, Q, q_bstride, q_kstride, tw);         \
         break;
         PCE_COL_SIZES(X)
 #undef X

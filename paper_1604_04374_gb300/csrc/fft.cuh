@@ -30,10 +30,34 @@
 // the conjugate twiddles and is unnormalised.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace pce {
+
+// ---- storage precision of windows (W) and spectra (H)
+// FP32 storage: float windows, float2 spectra.  Reduced storage: bfloat16
+// windows, half2 spectra scaled per term by a power of two.  Loads convert
+// to FP32; all arithmetic is FP32.
+__device__ __forceinline__ float ldw(const float* p) { return __ldg(p); }
+__device__ __forceinline__ float ldw(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+__device__ __forceinline__ float2 ldh(const float2* p, float) { return __ldg(p); }
+__device__ __forceinline__ float2 ldh(const __half2* p, float s) {
+    const float2 f = __half22float2(__ldg(p));
+    return make_float2(f.x * s, f.y * s);
+}
+// the same from shared memory
+__device__ __forceinline__ float2 lds_h(const float2* p, float) { return *p; }
+__device__ __forceinline__ float2 lds_h(const __half2* p, float s) {
+    const float2 f = __half22float2(*p);
+    return make_float2(f.x * s, f.y * s);
+}
+template <typename HT>
+__device__ __forceinline__ float hscale_of(const float* hscale, int k) {
+    return sizeof(HT) == sizeof(float2) ? 1.f : __ldg(&hscale[k]);
+}
 
 constexpr int kR = 8;   // elements per thread
 

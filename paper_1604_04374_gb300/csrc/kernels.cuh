@@ -47,21 +47,22 @@ __device__ __forceinline__ int wrap(int i, int n) { return i & (n - 1); }
 // next item are loaded before the FFT of the current one.
 constexpr int kRowIters = 1;
 
+template <typename WT>
 struct RowItem {
     int k, la, lb;
     bool va, vb;
     const float* sa;
     const float* sb;
-    const float* wa;   // window row of la (WINDOW), nullptr otherwise
-    const float* wb;
+    const WT* wa;   // window row of la (WINDOW), nullptr otherwise
+    const WT* wb;
     int c0, nc;
 };
 
-template <int NX, bool WINDOW>
-__device__ __forceinline__ RowItem row_item(int item, int nitems, const float* __restrict__ src, int nrows,
-                                            const float* __restrict__ wbox, const Box* __restrict__ box,
-                                            const int2* __restrict__ items) {
-    RowItem it;
+template <int NX, bool WINDOW, typename WT>
+__device__ __forceinline__ RowItem<WT> row_item(int item, int nitems, const float* __restrict__ src, int nrows,
+                                                const WT* __restrict__ wbox, const Box* __restrict__ box,
+                                                const int2* __restrict__ items) {
+    RowItem<WT> it;
     const bool active = item < nitems;
     if (WINDOW) {
         const int2 kp = active ? items[item] : make_int2(0, 0);
@@ -92,8 +93,8 @@ __device__ __forceinline__ RowItem row_item(int item, int nitems, const float* _
     return it;
 }
 
-template <int NX, bool WINDOW>
-__device__ __forceinline__ void row_load(float2 (&v)[kR], const RowItem& it, int j) {
+template <int NX, bool WINDOW, typename WT>
+__device__ __forceinline__ void row_load(float2 (&v)[kR], const RowItem<WT>& it, int j) {
     constexpr int T = NX / kR;
 #pragma unroll
     for (int r = 0; r < kR; ++r) {
@@ -102,8 +103,8 @@ __device__ __forceinline__ void row_load(float2 (&v)[kR], const RowItem& it, int
         if (WINDOW) {
             const int cc = wrap(n - it.c0, NX);
             if (cc < it.nc) {
-                if (it.va) xa = __ldg(it.wa + cc) * __ldg(it.sa + n);
-                if (it.vb) xb = __ldg(it.wb + cc) * __ldg(it.sb + n);
+                if (it.va) xa = ldw(it.wa + cc) * __ldg(it.sa + n);
+                if (it.vb) xb = ldw(it.wb + cc) * __ldg(it.sb + n);
             }
         } else {
             if (it.va) xa = __ldg(it.sa + n);
@@ -113,10 +114,10 @@ __device__ __forceinline__ void row_load(float2 (&v)[kR], const RowItem& it, int
     }
 }
 
-template <int NX, bool WINDOW>
+template <int NX, bool WINDOW, typename WT = float>
 __global__ void __launch_bounds__(256)
 k_rows_r2c(const float* __restrict__ src, long long src_bstride, int nrows,
-           const float* __restrict__ wbox, const Box* __restrict__ box,
+           const WT* __restrict__ wbox, const Box* __restrict__ box,
            const int2* __restrict__ items, int nitems,
            float2* __restrict__ dst, long long dst_bstride, long long dst_kstride,
            const float2* __restrict__ tw) {
@@ -132,16 +133,16 @@ k_rows_r2c(const float* __restrict__ src, long long src_bstride, int nrows,
     const float* srcb = src + b * src_bstride;
     const int first = blockIdx.x * kRowIters * FPC + slot;
 
-    RowItem cur = row_item<NX, WINDOW>(first, nitems, srcb, nrows, wbox, box, items);
+    RowItem<WT> cur = row_item<NX, WINDOW, WT>(first, nitems, srcb, nrows, wbox, box, items);
     float2 v[kR];
-    row_load<NX, WINDOW>(v, cur, j);
+    row_load<NX, WINDOW, WT>(v, cur, j);
     for (int it = 0; it < kRowIters; ++it) {
-        RowItem nxt;
+        RowItem<WT> nxt;
         float2 vn[kR];
         const bool more = it + 1 < kRowIters;
         if (more) {
-            nxt = row_item<NX, WINDOW>(first + (it + 1) * FPC, nitems, srcb, nrows, wbox, box, items);
-            row_load<NX, WINDOW>(vn, nxt, j);
+            nxt = row_item<NX, WINDOW, WT>(first + (it + 1) * FPC, nitems, srcb, nrows, wbox, box, items);
+            row_load<NX, WINDOW, WT>(vn, nxt, j);
         }
         fft<NX, false>(v, j, b0, b1, tw);
 
@@ -189,6 +190,15 @@ __device__ __forceinline__ float2 load_half(const float2* p, int f) {
     if (f < NXh) return p[f];
     return cconj(p[NX - f]);
 }
+// The same from a stored spectrum (FP32, or FP16 times the term's scale s).
+template <int NX, typename HT>
+__device__ __forceinline__ float2 load_half_h(const HT* p, int f, float s) {
+    constexpr int NXh = NX / 2;
+    if (f == 0) return make_float2(ldh(&p[0], s).x, 0.f);
+    if (f == NXh) return make_float2(ldh(&p[0], s).y, 0.f);
+    if (f < NXh) return ldh(&p[f], s);
+    return cconj(ldh(&p[NX - f], s));
+}
 
 template <int NX>
 __global__ void __launch_bounds__(256)
@@ -233,18 +243,19 @@ k_rows_c2r(const float2* __restrict__ src, long long src_bstride, int nrows,
 // w_k . C2R(Q_{b,k}[row]), times scale.  Q rows are indexed inside the box.
 // The next term's Q rows and window values are loaded before the inverse
 // FFT of the current term.
+template <typename WT>
 struct AdjTerm {
     const float2* pa;
     const float2* pb;
-    const float* wa;
-    const float* wb;
+    const WT* wa;
+    const WT* wb;
     bool va, vb;
     int c0, nc;
 };
 
-template <int NX>
+template <int NX, typename WT>
 __device__ __forceinline__ void adj_load(float2 (&v)[kR], float (&wa)[kR], float (&wb)[kR],
-                                         const AdjTerm& q, int j) {
+                                         const AdjTerm<WT>& q, int j) {
     constexpr int T = NX / kR;
 #pragma unroll
     for (int r = 0; r < kR; ++r) {
@@ -254,15 +265,15 @@ __device__ __forceinline__ void adj_load(float2 (&v)[kR], float (&wa)[kR], float
         v[r] = make_float2(xa.x - xb.y, xa.y + xb.x);
         const int cc = wrap(f - q.c0, NX);     // f doubles as the output column n = j + r*T
         const bool in = cc < q.nc;
-        wa[r] = (q.va && in) ? __ldg(q.wa + cc) : 0.f;
-        wb[r] = (q.vb && in) ? __ldg(q.wb + cc) : 0.f;
+        wa[r] = (q.va && in) ? ldw(q.wa + cc) : 0.f;
+        wb[r] = (q.vb && in) ? ldw(q.wb + cc) : 0.f;
     }
 }
 
-template <int NX>
+template <int NX, typename WT = float>
 __global__ void __launch_bounds__(256)
 k_rows_adj(const float2* __restrict__ Q, long long q_bstride, long long q_kstride, int nrows,
-           const float* __restrict__ wbox, const Box* __restrict__ box,
+           const WT* __restrict__ wbox, const Box* __restrict__ box,
            const int* __restrict__ kptr, const int* __restrict__ klist,
            float* __restrict__ dst, long long dst_bstride, float scale,
            const float2* __restrict__ tw) {
@@ -290,7 +301,7 @@ k_rows_adj(const float2* __restrict__ Q, long long q_bstride, long long q_kstrid
     const int kcnt = pv ? __ldg(&kptr[p + 1]) - kbeg : 0;
 
     auto term = [&](int t) {
-        AdjTerm q;
+        AdjTerm<WT> q;
         const bool act = t < kcnt;
         const int k = act ? __ldg(&klist[kbeg + t]) : 0;
         const Box bx = box[k];
@@ -313,12 +324,12 @@ k_rows_adj(const float2* __restrict__ Q, long long q_bstride, long long q_kstrid
 
     float2 v[kR];
     float wa[kR], wb[kR];
-    if (nk > 0) adj_load<NX>(v, wa, wb, term(0), j);
+    if (nk > 0) adj_load<NX, WT>(v, wa, wb, term(0), j);
     for (int t = 0; t < nk; ++t) {
         float2 vn[kR];
         float wan[kR], wbn[kR];
         const bool more = t + 1 < nk;
-        if (more) adj_load<NX>(vn, wan, wbn, term(t + 1), j);
+        if (more) adj_load<NX, WT>(vn, wan, wbn, term(t + 1), j);
         fft<NX, true>(v, j, b0, b1, tw);
 #pragma unroll
         for (int r = 0; r < kR; ++r) {
@@ -381,10 +392,10 @@ __device__ __forceinline__ void load_col(float2 (&v)[kR], const float2* __restri
 // hh: [m][NY][NXh] (column 0 = DC column spectrum), hN: [m][NY] (Nyquist).
 // The next term's Z column and this term's spectrum are loaded before the
 // FFT so that their latency overlaps it.
-template <int NY>
+template <int NY, typename HT = float2>
 __global__ void __launch_bounds__(ColCfg<NY>::NT)
 k_cols_fwd(const float2* __restrict__ Z, long long z_bstride, long long z_kstride,
-           const float2* __restrict__ hh, const float2* __restrict__ hN, int m,
+           const HT* __restrict__ hh, const HT* __restrict__ hN, const float* __restrict__ hscale, int m,
            const Box* __restrict__ box, int NXh,
            float2* __restrict__ A, long long a_bstride, const float2* __restrict__ tw) {
     using CC = ColCfg<NY>;
@@ -430,11 +441,12 @@ k_cols_fwd(const float2* __restrict__ Z, long long z_bstride, long long z_kstrid
         int kn = k + 1;
         while (kn < m && box[kn].nr == 0) ++kn;
         // spectrum of term k at this thread's frequencies
-        const float2* hk = hh + (long long)k * NY * NXh;
+        const HT* hk = hh + (long long)k * NY * NXh;
+        const float sk = hscale_of<HT>(hscale, k);
         float2 hv[kR];
 #pragma unroll
         for (int r = 0; r < kR; ++r)
-            hv[r] = cv ? __ldg(&hk[(long long)(j + r * T) * NXh + col]) : make_float2(0.f, 0.f);
+            hv[r] = cv ? ldh(&hk[(long long)(j + r * T) * NXh + col], sk) : make_float2(0.f, 0.f);
         // Z column of the next term
         float2 zn[kR];
         Box bn = bx;
@@ -457,7 +469,7 @@ k_cols_fwd(const float2* __restrict__ Z, long long z_bstride, long long z_kstrid
                 float2 a, bb;
                 split_dc_nyq(v[r], xbuf[padi((NY - f) & (NY - 1))], a, bb);
                 acc[r] = cfma(hv[r], a, acc[r]);
-                const float2 t = cmul(__ldg(&hN[(long long)k * NY + f]), bb);
+                const float2 t = cmul(ldh(&hN[(long long)k * NY + f], sk), bb);
                 acc[r].x -= t.y;
                 acc[r].y += t.x;
             }
@@ -485,10 +497,10 @@ k_cols_fwd(const float2* __restrict__ Z, long long z_bstride, long long z_kstrid
 // (FULL: of every row, Q[b][k][NY][NXh], for the window gradient).
 // Grid (batch, NXh / C).  The next term's spectrum is loaded before the
 // current inverse FFT.
-template <int NY, bool FULL>
+template <int NY, bool FULL, typename HT = float2>
 __global__ void __launch_bounds__(ColCfg<NY>::NT)
 k_cols_adj(const float2* __restrict__ V, long long v_bstride,
-           const float2* __restrict__ hh, const float2* __restrict__ hN, int m,
+           const HT* __restrict__ hh, const HT* __restrict__ hN, const float* __restrict__ hscale, int m,
            const Box* __restrict__ box, int NXh,
            float2* __restrict__ Q, long long q_bstride, long long q_kstride,
            const float2* __restrict__ tw) {
@@ -517,10 +529,11 @@ k_cols_adj(const float2* __restrict__ V, long long v_bstride,
     while (k < m && !FULL && box[k].nr == 0) ++k;
     float2 hv[kR];
     if (k < m) {
-        const float2* hk = hh + (long long)k * NY * NXh;
+        const HT* hk = hh + (long long)k * NY * NXh;
+        const float sk = hscale_of<HT>(hscale, k);
 #pragma unroll
         for (int r = 0; r < kR; ++r)
-            hv[r] = cv ? __ldg(&hk[(long long)(j + r * T) * NXh + col]) : make_float2(0.f, 0.f);
+            hv[r] = cv ? ldh(&hk[(long long)(j + r * T) * NXh + col], sk) : make_float2(0.f, 0.f);
     }
     fft<NY, false, kColLayout>(vv, j, b0, b1, tw);
     if (tile0) {
@@ -542,7 +555,7 @@ k_cols_adj(const float2* __restrict__ V, long long v_bstride,
                 float2 a, bb;
                 split_dc_nyq(vv[r], xbuf[padi((NY - f) & (NY - 1))], a, bb);
                 float2 t = cmulc(a, hv[r]);
-                const float2 s = cmulc(bb, __ldg(&hN[(long long)k * NY + f]));
+                const float2 s = cmulc(bb, ldh(&hN[(long long)k * NY + f], hscale_of<HT>(hscale, k)));
                 t.x -= s.y;
                 t.y += s.x;
                 p[r] = t;
@@ -551,10 +564,11 @@ k_cols_adj(const float2* __restrict__ V, long long v_bstride,
             }
         }
         if (kn < m) {
-            const float2* hk = hh + (long long)kn * NY * NXh;
+            const HT* hk = hh + (long long)kn * NY * NXh;
+            const float sk = hscale_of<HT>(hscale, kn);
 #pragma unroll
             for (int r = 0; r < kR; ++r)
-                hv[r] = cv ? __ldg(&hk[(long long)(j + r * T) * NXh + col]) : make_float2(0.f, 0.f);
+                hv[r] = cv ? ldh(&hk[(long long)(j + r * T) * NXh + col], sk) : make_float2(0.f, 0.f);
         }
         fft<NY, true, kColLayout>(p, j, b0, b1, tw);
         if (cv) {
@@ -844,10 +858,10 @@ struct Cfg1d {
 // slot takes pairs of terms (w_k u + i w_{k+1} u in one complex FFT) and
 // accumulates the half spectrum in registers; the slots' sums are reduced in
 // shared memory and one inverse FFT follows.  hp: [m][N/2] packed spectra.
-template <int N>
+template <int N, typename WT = float, typename HT = float2>
 __global__ void __launch_bounds__(Cfg1d<N>::NT)
-k_fwd_1d(const float* __restrict__ u, const float* __restrict__ w,
-         const float2* __restrict__ hp, int m, float* __restrict__ y, float scale,
+k_fwd_1d(const float* __restrict__ u, const WT* __restrict__ w,
+         const HT* __restrict__ hp, const float* __restrict__ hscale, int m, float* __restrict__ y, float scale,
          const float2* __restrict__ tw) {
     using CF = Cfg1d<N>;
     constexpr int T = CF::T;
@@ -878,8 +892,8 @@ k_fwd_1d(const float* __restrict__ u, const float* __restrict__ w,
 #pragma unroll
         for (int r = 0; r < kR; ++r) {
             const int n = j + r * T;
-            v[r] = make_float2(a0 ? __ldg(w + (long long)k0 * N + n) * ureg[r] : 0.f,
-                               a1 ? __ldg(w + (long long)k1 * N + n) * ureg[r] : 0.f);
+            v[r] = make_float2(a0 ? ldw(w + (long long)k0 * N + n) * ureg[r] : 0.f,
+                               a1 ? ldw(w + (long long)k1 * N + n) * ureg[r] : 0.f);
         }
         fft<N, false>(v, j, b0, b1, tw);
         __syncthreads();
@@ -887,26 +901,28 @@ k_fwd_1d(const float* __restrict__ u, const float* __restrict__ w,
         for (int r = 0; r < kR; ++r) b0[padi(j + r * T)] = v[r];
         __syncthreads();
         if (a0) {
-            const float2* h0 = hp + (long long)k0 * Nh;
-            const float2* h1 = hp + (long long)(a1 ? k1 : k0) * Nh;
+            const HT* h0 = hp + (long long)k0 * Nh;
+            const HT* h1 = hp + (long long)(a1 ? k1 : k0) * Nh;
+            const float s0 = hscale_of<HT>(hscale, k0);
+            const float s1 = hscale_of<HT>(hscale, a1 ? k1 : k0);
 #pragma unroll
             for (int r = 0; r < kR / 2; ++r) {
                 const int f = j + r * T;
                 if (f == 0) {
                     // the DC and Nyquist terms are real: acc[0] of thread 0 packs (DC, Nyquist)
-                    const float2 p0 = __ldg(&h0[0]);
+                    const float2 p0 = ldh(&h0[0], s0);
                     acc[0].x = fmaf(p0.x, v[0].x, acc[0].x);
                     acc[0].y = fmaf(p0.y, v[kR / 2].x, acc[0].y);
                     if (a1) {
-                        const float2 p1 = __ldg(&h1[0]);
+                        const float2 p1 = ldh(&h1[0], s1);
                         acc[0].x = fmaf(p1.x, v[0].y, acc[0].x);
                         acc[0].y = fmaf(p1.y, v[kR / 2].y, acc[0].y);
                     }
                 } else {
                     float2 A, B;
                     split_dc_nyq(v[r], b0[padi(N - f)], A, B);
-                    acc[r] = cfma(__ldg(&h0[f]), A, acc[r]);
-                    if (a1) acc[r] = cfma(__ldg(&h1[f]), B, acc[r]);
+                    acc[r] = cfma(ldh(&h0[f], s0), A, acc[r]);
+                    if (a1) acc[r] = cfma(ldh(&h1[f], s1), B, acc[r]);
                 }
             }
         }
@@ -941,10 +957,10 @@ k_fwd_1d(const float* __restrict__ u, const float* __restrict__ w,
 // x_b = (1/N) sum_k w_k . IFFT( conj(hhat_k) . FFT(v_b) ).  One CTA per b;
 // every slot forms FFT(v_b) and takes pairs of terms: the two inverse FFTs
 // of a pair are real, so they share one complex inverse FFT.
-template <int N>
+template <int N, typename WT = float, typename HT = float2>
 __global__ void __launch_bounds__(Cfg1d<N>::NT)
-k_adj_1d(const float* __restrict__ vin, const float* __restrict__ w,
-         const float2* __restrict__ hp, int m, float* __restrict__ x, float scale,
+k_adj_1d(const float* __restrict__ vin, const WT* __restrict__ w,
+         const HT* __restrict__ hp, const float* __restrict__ hscale, int m, float* __restrict__ x, float scale,
          const float2* __restrict__ tw) {
     using CF = Cfg1d<N>;
     constexpr int T = CF::T;
@@ -972,16 +988,18 @@ k_adj_1d(const float* __restrict__ vin, const float* __restrict__ w,
         const bool a0 = pr < npairs;
         const int k0 = 2 * pr, k1 = k0 + 1;
         const bool a1 = a0 && k1 < m;
-        const float2* h0 = hp + (long long)(a0 ? k0 : 0) * Nh;
-        const float2* h1 = hp + (long long)(a1 ? k1 : 0) * Nh;
+        const HT* h0 = hp + (long long)(a0 ? k0 : 0) * Nh;
+        const HT* h1 = hp + (long long)(a1 ? k1 : 0) * Nh;
+        const float s0 = hscale_of<HT>(hscale, a0 ? k0 : 0);
+        const float s1 = hscale_of<HT>(hscale, a1 ? k1 : 0);
         float2 p[kR];
 #pragma unroll
         for (int r = 0; r < kR; ++r) {
             const int f = j + r * T;
             float2 t = make_float2(0.f, 0.f);
-            if (a0) t = cmulc(V[r], load_half<N>(h0, f));
+            if (a0) t = cmulc(V[r], load_half_h<N, HT>(h0, f, s0));
             if (a1) {
-                const float2 s = cmulc(V[r], load_half<N>(h1, f));
+                const float2 s = cmulc(V[r], load_half_h<N, HT>(h1, f, s1));
                 t.x -= s.y;
                 t.y += s.x;
             }
@@ -991,8 +1009,8 @@ k_adj_1d(const float* __restrict__ vin, const float* __restrict__ w,
 #pragma unroll
         for (int r = 0; r < kR; ++r) {
             const int n = j + r * T;
-            if (a0) ax[r] = fmaf(__ldg(w + (long long)k0 * N + n), p[r].x, ax[r]);
-            if (a1) ax[r] = fmaf(__ldg(w + (long long)k1 * N + n), p[r].y, ax[r]);
+            if (a0) ax[r] = fmaf(ldw(w + (long long)k0 * N + n), p[r].x, ax[r]);
+            if (a1) ax[r] = fmaf(ldw(w + (long long)k1 * N + n), p[r].y, ax[r]);
         }
     }
     __syncthreads();

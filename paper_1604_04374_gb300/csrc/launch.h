@@ -15,6 +15,8 @@ int cols_columns_per_cta(int ny);
 int cols_smem(int ny);
 // Rows handled per CTA of the row kernels (two rows per FFT).
 int rows_pairs_per_cta(int nx);
+// Row pairs per CTA of the window-gradient row kernel.
+int rows_grad_pairs_per_cta(int nx);
 // Items (row pairs) handled per CTA of the R2C row kernel.
 int rows_r2c_items_per_cta(int nx);
 // 1D kernels.
@@ -24,29 +26,35 @@ int fft1d_smem(int n);
 // Raise the dynamic shared-memory limit of every kernel that needs it (once per device).
 cudaError_t prepare_kernels();
 
+// Storage-precision arguments: `lowp` selects bfloat16 windows (wbox) and
+// half2 spectra scaled by hscale[k]; otherwise float windows and float2 spectra.
 cudaError_t launch_rows_r2c(int nx, bool window, dim3 grid, cudaStream_t s,
                             const float* src, long long src_bstride, int nrows,
-                            const float* wbox, const Box* box, const int2* items, int nitems,
+                            const void* wbox, bool lowp, const Box* box, const int2* items, int nitems,
                             float2* dst, long long dst_bstride, long long dst_kstride,
-                            const float2* tw);
+                            const float2* tw, const float2* tw1024);
 
 cudaError_t launch_rows_c2r(int nx, dim3 grid, cudaStream_t s, const float2* src,
                             long long src_bstride, int nrows, float* dst, long long dst_bstride,
-                            float scale, const float2* tw);
+                            float scale, const float2* tw, const float2* tw1024);
 
 cudaError_t launch_rows_adj(int nx, dim3 grid, cudaStream_t s, const float2* Q, long long q_bstride,
-                            long long q_kstride, int nrows, const float* wbox, const Box* box,
+                            long long q_kstride, int nrows, const void* wbox, bool lowp, const Box* box,
                             const int* kptr, const int* klist, float* dst, long long dst_bstride,
-                            float scale, const float2* tw);
+                            float scale, const float2* tw, const float2* tw1024);
 
 cudaError_t launch_cols_fwd(int ny, dim3 grid, cudaStream_t s, const float2* Z, long long z_bstride,
-                            long long z_kstride, const float2* hh, const float2* hN, int m,
+                            long long z_kstride, const void* hh, const void* hN, const float* hscale,
+                            bool lowp, int m,
                             const Box* box, int nxh, float2* A, long long a_bstride,
-                            const float2* tw);
+                            const float2* tw, const void* hhT, const float2* tw1024, int* status,
+                            long long wait_limit, int skip_copy);
 
 cudaError_t launch_cols_adj(int ny, dim3 grid, cudaStream_t s, const float2* V, long long v_bstride,
-                            const float2* hh, const float2* hN, int m, const Box* box, int nxh,
-                            float2* Q, long long q_bstride, long long q_kstride, const float2* tw);
+                            const void* hh, const void* hN, const float* hscale, bool lowp, int m,
+                            const Box* box, int nxh, float2* Q, long long q_bstride, long long q_kstride,
+                            const float2* tw, const void* hhT, const float2* tw1024, int* status,
+                            long long wait_limit, int skip_copy);
 
 cudaError_t launch_cols_spec(int ny, dim3 grid, cudaStream_t s, const float2* S, int nxh,
                              float2* hh, float2* hN, const float2* tw);
@@ -57,7 +65,8 @@ cudaError_t launch_plain_cols_inv(int ny, dim3 grid, cudaStream_t s, const float
 cudaError_t launch_cols_adj_full(int ny, dim3 grid, cudaStream_t s, const float2* V, long long v_bstride,
                                  const float2* hh, const float2* hN, int m, const Box* box, int nxh,
                                  float2* Q, long long q_bstride, long long q_kstride,
-                                 const float2* tw);
+                                 const float2* tw, const float2* hhT, const float2* tw1024, int* status,
+                                 long long wait_limit, int skip_copy);
 
 cudaError_t launch_cols_grad_h(int ny, dim3 grid, cudaStream_t s, const float2* Z, long long z_bstride,
                                long long z_kstride, int nb, const float2* Rh, const float2* RhN,
@@ -73,13 +82,34 @@ cudaError_t launch_grad_1d(int n, int m, cudaStream_t s, const float* u, const f
                            const float* w, const float2* hp, int nb, float2* dh, float* dw,
                            float scale, int accumulate, const float2* tw);
 
-cudaError_t launch_fwd_1d(int n, int batch, cudaStream_t s, const float* u, const float* w,
-                          const float2* hp, int m, float* y, float scale, const float2* tw);
+cudaError_t launch_fwd_1d(int n, int batch, cudaStream_t s, const float* u, const void* w,
+                          const void* hp, const float* hscale, bool lowp, int m, float* y, float scale,
+                          const float2* tw);
 
-cudaError_t launch_adj_1d(int n, int batch, cudaStream_t s, const float* v, const float* w,
-                          const float2* hp, int m, float* x, float scale, const float2* tw);
+cudaError_t launch_adj_1d(int n, int batch, cudaStream_t s, const float* v, const void* w,
+                          const void* hp, const float* hscale, bool lowp, int m, float* x, float scale,
+                          const float2* tw);
 
 cudaError_t launch_spec_1d(int n, int m, cudaStream_t s, const float* h, float2* hp,
                            const float2* tw);
+
+// 1D transforms of N = ny * nx > 8192 points (four-step, k1d_large.cuh).
+int l1_cols_per_cta(int ny);
+int l1_row_items(int nx);
+cudaError_t launch_l1_cols(int ny, int mode, dim3 grid, cudaStream_t s, const float* src,
+                           long long src_bstride, const float* w, int m, int nx, const float2* twN,
+                           float2* G, const float2* tw);
+cudaError_t launch_l1_rows_fwd(int nx, dim3 grid, cudaStream_t s, const float2* G, int npairs,
+                               const float2* hh4, int m, int ny, const float2* twN, float2* A,
+                               const float2* tw);
+cudaError_t launch_l1_cols_inv(int ny, dim3 grid, cudaStream_t s, const float2* A, int nx, float* y,
+                               float scale, const float2* tw);
+cudaError_t launch_l1_rows_adj(int nx, dim3 grid, cudaStream_t s, const float2* V, int npairs,
+                               const float2* hh4, int m, int ny, const float2* twN, float2* Q,
+                               const float2* tw);
+cudaError_t launch_l1_cols_adj(int ny, dim3 grid, cudaStream_t s, const float2* Q, int npairs,
+                               const float* w, int m, int nx, float* x, float scale, const float2* tw);
+cudaError_t launch_l1_rows_spec(int nx, dim3 grid, cudaStream_t s, const float2* G, int npairs, int m,
+                                int ny, float2* hh4, const float2* tw);
 
 }  // namespace pce

@@ -5,9 +5,12 @@
 // FP64, the work lists of the row passes, and the scratch intermediates of
 // the 2D passes (Z/Q: per-term row spectra restricted to the box rows; A/V:
 // per-right-hand-side spectra).  Applies only launch kernels.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -81,6 +84,70 @@ __global__ void k_twiddles(float2* tw, int n) {
             return;
         }
         off += cnt;
+    }
+}
+
+// Four-step twiddles of the one-warp 1024-point FFT: tw[p * 32 + l] = W1024^{l p} (FP64 sincospi).
+__global__ void k_twiddles_1024(float2* tw) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 1024) return;
+    const int p = idx >> 5, l = idx & 31;
+    double sn, cs;
+    sincospi(-2.0 * (double)(l * p) / 1024.0, &sn, &cs);
+    tw[idx] = make_float2((float)cs, (float)sn);
+}
+
+// twN[j] = W_N^j for j < N (FP64 sincospi).
+__global__ void k_twiddles_N(float2* tw, long long n) {
+    const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double sn, cs;
+    sincospi(-2.0 * (double)j / (double)n, &sn, &cs);
+    tw[j] = make_float2((float)cs, (float)sn);
+}
+
+// hhat [m][N/2+1] (natural half spectrum) -> hh4 [m][ny][nx] in the four-step
+// order (f = a + ny b at (a, b)), Hermitian extension, real DC and Nyquist.
+__global__ void k_from_half_l1(const float2* __restrict__ hhat, int m, int ny, int nx, float2* hh4) {
+    const long long N = (long long)ny * nx;
+    const long long total = (long long)m * N;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long k = i / N;
+        const long long e = i % N;
+        const long long a = e / nx, b = e % nx;
+        const long long f = a + ny * b;
+        const float2* src = hhat + k * (N / 2 + 1);
+        float2 v;
+        if (f == 0) v = make_float2(src[0].x, 0.f);
+        else if (f == N / 2) v = make_float2(src[N / 2].x, 0.f);
+        else if (f < N / 2) v = src[f];
+        else v = make_float2(src[N - f].x, -src[N - f].y);
+        hh4[i] = v;
+    }
+}
+
+__global__ void k_to_half_l1(const float2* __restrict__ hh4, int m, int ny, int nx, float2* hhat) {
+    const long long N = (long long)ny * nx;
+    const long long total = (long long)m * (N / 2 + 1);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long k = i / (N / 2 + 1);
+        const long long f = i % (N / 2 + 1);
+        hhat[i] = hh4[k * N + (f % ny) * nx + f / ny];
+    }
+}
+
+// hhT[k][c][f] = hh[k][f][c] (ny x nxh per term).
+__global__ void k_transpose_hh(const float2* __restrict__ hh, int m, int ny, int nxh, float2* hhT) {
+    const long long total = (long long)m * ny * nxh;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int f = (int)(i % ny);
+        const long long kc = i / ny;
+        const int c = (int)(kc % nxh);
+        const long long k = kc / nxh;
+        hhT[i] = hh[(k * ny + f) * nxh + c];
     }
 }
 
@@ -253,6 +320,42 @@ unsigned r2c_blocks(int items, int nx) {
     return (unsigned)((items + ipc - 1) / ipc);
 }
 
+// ----- reduced storage: per-term scale, half2 spectra, bfloat16 windows
+// out[k] (float bits) = max over term k's entries of max(|Re|, |Im|).
+__global__ void k_term_maxabs(const float2* __restrict__ a, long long per, int m, unsigned* out) {
+    const long long total = per * m;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float2 v = a[i];
+        const float x = fmaxf(fabsf(v.x), fabsf(v.y));
+        atomicMax(&out[i / per], __float_as_uint(x));   // non-negative floats order as their bits
+    }
+}
+
+// dst[i] = half2(src[i] / s_k); src[i] is replaced by the value dst[i] stands for.
+__global__ void k_quantize_h(float2* src, long long per, int m, const float* __restrict__ scale,
+                             __half2* dst) {
+    const long long total = per * m;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float sk = scale[i / per];
+        const float2 v = src[i];
+        const __half2 h = __floats2half2_rn(v.x / sk, v.y / sk);
+        dst[i] = h;
+        const float2 f = __half22float2(h);
+        src[i] = make_float2(f.x * sk, f.y * sk);
+    }
+}
+
+__global__ void k_quantize_w(float* src, long long n, __nv_bfloat16* dst) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const __nv_bfloat16 b = __float2bfloat16_rn(src[i]);
+        dst[i] = b;
+        src[i] = __bfloat162float(b);
+    }
+}
+
 unsigned grid_for(long long total, int threads = 256) {
     long long g = (total + threads - 1) / threads;
     return (unsigned)std::max<long long>(1, std::min<long long>(g, 1 << 20));
@@ -299,6 +402,23 @@ struct pce_plan {
     // spectra
     float2* hh = nullptr;       // 2D [m][ny][nx/2]; 1D packed [m][n/2]
     float2* hN = nullptr;       // 2D [m][ny]
+    float2* hhT = nullptr;      // 2D, ny = 1024: [m][nx/2][ny] (each column's spectrum contiguous)
+    float2* tw1024 = nullptr;   // four-step twiddles when a transform length is 1024
+    int* d_status = nullptr;    // device status word (bit 0: a bounded wait gave up)
+    // 1D of more than 8192 points: four-step over an l1ny x l1nx view
+    bool l1 = false;
+    int l1ny = 0, l1nx = 0;
+    float2* twN = nullptr;      // W_N^j, j < N
+    float2* hh4 = nullptr;      // [m][l1ny][l1nx]: hhat_k[a + l1ny * b] at (a, b)
+    // reduced storage (PCE_FLAG_LOWP_STORAGE): bfloat16 window copies, half2 spectra / hscale[k]
+    bool lowp = false;
+    void* wbox16 = nullptr;
+    void* hh16 = nullptr;
+    void* hN16 = nullptr;
+    void* hhT16 = nullptr;
+    float* hscale = nullptr;
+    long long wait_limit = 2000000000ll;   // clock cycles a kernel waits on an mbarrier
+    int skip_copy = 0;          // test support: arm barriers without copying
     // twiddles
     float2* twx = nullptr;
     float2* twy = nullptr;
@@ -329,8 +449,9 @@ struct pce_plan {
 
     ~pce_plan() {
         drop_events();
-        void* ptrs[] = {d_box, wbox, hh, hN, twx, twy == twx ? nullptr : twy, items, kptr, klist,
-                        scrZ, scrA};
+        void* ptrs[] = {d_box,  wbox,  hh,     hN,   hhT,   tw1024, d_status, twx, twy == twx ? nullptr : twy,
+                        items,  kptr,  klist,  scrZ, scrA,  wbox16, hh16,     hN16, hhT16, hscale,
+                        twN,    hh4};
         for (void* p : ptrs)
             if (p) cudaFree(p);
     }
@@ -338,13 +459,19 @@ struct pce_plan {
 
 namespace {
 
+// Window and spectrum storage the fused kernels read.
+const void* wstore(pce_plan_t p) { return p->lowp ? p->wbox16 : (const void*)p->wbox; }
+const void* hstore(pce_plan_t p) { return p->lowp ? p->hh16 : (const void*)p->hh; }
+const void* hNstore(pce_plan_t p) { return p->lowp ? p->hN16 : (const void*)p->hN; }
+const void* hTstore(pce_plan_t p) { return p->lowp ? p->hhT16 : (const void*)p->hhT; }
+
 pce_status validate_shape(int ndims, const int64_t* shape, int& ny, int& nx) {
     if (ndims != 1 && ndims != 2) return fail(PCE_ERR_INVALID, "ndims must be 1 or 2 (got %d)", ndims);
     if (!shape) return fail(PCE_ERR_INVALID, "shape is NULL");
     if (ndims == 1) {
         ny = 1;
-        if (!is_pow2(shape[0]) || shape[0] < 16 || shape[0] > 8192)
-            return fail(PCE_ERR_UNSUPPORTED, "1D size must be a power of two in [16, 8192] (got %lld)",
+        if (!is_pow2(shape[0]) || shape[0] < 16 || shape[0] > (1 << 18))
+            return fail(PCE_ERR_UNSUPPORTED, "1D size must be a power of two in [16, 262144] (got %lld)",
                         (long long)shape[0]);
         nx = (int)shape[0];
     } else {
@@ -359,7 +486,33 @@ pce_status validate_shape(int ndims, const int64_t* shape, int& ny, int& nx) {
     return PCE_OK;
 }
 
+pce_status make_twiddles_l1(pce_plan* p, cudaStream_t s) {
+    const long long N = p->nx;
+    pce_status st = dev_alloc(&p->twN, (size_t)N);
+    if (st) return st;
+    k_twiddles_N<<<grid_for(N), 256, 0, s>>>(p->twN, N);
+    PCE_CK(cudaGetLastError());
+    if ((st = dev_alloc(&p->twx, (size_t)twiddle_len(p->l1nx)))) return st;
+    k_twiddles<<<grid_for(twiddle_len(p->l1nx)), 256, 0, s>>>(p->twx, p->l1nx);
+    PCE_CK(cudaGetLastError());
+    if (p->l1ny == p->l1nx) {
+        p->twy = p->twx;
+    } else {
+        if ((st = dev_alloc(&p->twy, (size_t)twiddle_len(p->l1ny)))) return st;
+        k_twiddles<<<grid_for(twiddle_len(p->l1ny)), 256, 0, s>>>(p->twy, p->l1ny);
+        PCE_CK(cudaGetLastError());
+    }
+    return PCE_OK;
+}
+
 pce_status make_twiddles(pce_plan* p, cudaStream_t s) {
+    if (p->l1) return make_twiddles_l1(p, s);
+    if (p->nx == 1024 || (p->ndims == 2 && p->ny == 1024)) {
+        pce_status st0 = dev_alloc(&p->tw1024, 1024);
+        if (st0) return st0;
+        k_twiddles_1024<<<4, 256, 0, s>>>(p->tw1024);
+        PCE_CK(cudaGetLastError());
+    }
     pce_status st = dev_alloc(&p->twx, (size_t)std::max(1, twiddle_len(p->nx)));
     if (st) return st;
     k_twiddles<<<grid_for(twiddle_len(p->nx)), 256, 0, s>>>(p->twx, p->nx);
@@ -479,6 +632,73 @@ pce_status setup_windows(pce_plan* p, const float* w, cudaStream_t s) {
     return PCE_OK;
 }
 
+// Reduced storage of a plan whose FP32 windows and spectra are ready: bfloat16
+// box copies of w_k, half2 spectra with per-term scale s_k = 2^ceil(log2 max |Re, Im|).
+// The FP32 copies are replaced by the values the reduced ones stand for.
+pce_status quantize_plan(pce_plan* p, cudaStream_t s) {
+    const int m = p->m, ny = p->ny, nxh = p->nx / 2;
+    const bool two_d = p->ndims == 2;
+    const long long per = two_d ? (long long)ny * nxh : nxh;
+    unsigned* mx = nullptr;
+    pce_status st;
+    if ((st = dev_alloc(&mx, (size_t)m))) return st;
+    cudaError_t e = cudaMemsetAsync(mx, 0, sizeof(unsigned) * m, s);
+    if (e == cudaSuccess) {
+        k_term_maxabs<<<grid_for(per * m), 256, 0, s>>>(p->hh, per, m, mx);
+        if (two_d) k_term_maxabs<<<grid_for((long long)ny * m), 256, 0, s>>>(p->hN, ny, m, mx);
+        e = cudaGetLastError();
+    }
+    std::vector<unsigned> hmx(m);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hmx.data(), mx, sizeof(unsigned) * m, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(mx);
+    PCE_CK(e);
+    std::vector<float> sc(m);
+    for (int k = 0; k < m; ++k) {
+        float v;
+        std::memcpy(&v, &hmx[k], sizeof v);
+        int ex = 0;
+        const float fr = std::frexp(v, &ex);   // v = fr * 2^ex, fr in [0.5, 1)
+        sc[k] = (v > 0.f && std::isfinite(v)) ? std::ldexp(1.0f, fr == 0.5f ? ex - 1 : ex) : 1.0f;
+    }
+    if ((st = dev_alloc(&p->hscale, (size_t)m))) return st;
+    PCE_CK(cudaMemcpyAsync(p->hscale, sc.data(), sizeof(float) * m, cudaMemcpyHostToDevice, s));
+    __half2* h16 = nullptr;
+    if ((st = dev_alloc(&h16, (size_t)(per * m)))) return st;
+    p->hh16 = h16;
+    k_quantize_h<<<grid_for(per * m), 256, 0, s>>>(p->hh, per, m, p->hscale, h16);
+    PCE_CK(cudaGetLastError());
+    if (two_d) {
+        __half2* n16 = nullptr;
+        if ((st = dev_alloc(&n16, (size_t)ny * m))) return st;
+        p->hN16 = n16;
+        k_quantize_h<<<grid_for((long long)ny * m), 256, 0, s>>>(p->hN, ny, m, p->hscale, n16);
+        PCE_CK(cudaGetLastError());
+        if (p->hhT) {
+            __half2* t16 = nullptr;
+            if ((st = dev_alloc(&t16, (size_t)(per * m)))) return st;
+            p->hhT16 = t16;
+            k_quantize_h<<<grid_for(per * m), 256, 0, s>>>(p->hhT, per, m, p->hscale, t16);
+            PCE_CK(cudaGetLastError());
+        }
+    }
+    long long nw = 0;
+    if (two_d) {
+        for (const Box& b : p->box) nw = std::max(nw, b.woff + (long long)b.nr * b.ldw);
+    } else {
+        nw = (long long)m * p->nx;
+    }
+    __nv_bfloat16* w16 = nullptr;
+    if ((st = dev_alloc(&w16, (size_t)std::max<long long>(nw, 1)))) return st;
+    p->wbox16 = w16;
+    if (nw > 0) {
+        k_quantize_w<<<grid_for(nw), 256, 0, s>>>(p->wbox, nw, w16);
+        PCE_CK(cudaGetLastError());
+    }
+    p->lowp = true;
+    return PCE_OK;
+}
+
 pce_status check_plan(pce_plan_t p) {
     if (!p) return fail(PCE_ERR_INVALID, "plan is NULL");
     return PCE_OK;
@@ -492,7 +712,10 @@ pce_status create_common(pce_plan_t* out, int ndims, const int64_t* shape, int m
     pce_status st = validate_shape(ndims, shape, ny, nx);
     if (st) return st;
     if (m < 1) return fail(PCE_ERR_INVALID, "m must be >= 1 (got %d)", m);
-    if (flags & ~(uint32_t)PCE_FLAG_UNFUSED) return fail(PCE_ERR_INVALID, "unknown flag bits 0x%x", flags);
+    if (flags & ~(uint32_t)(PCE_FLAG_UNFUSED | PCE_FLAG_LOWP_STORAGE))
+        return fail(PCE_ERR_INVALID, "unknown flag bits 0x%x", flags);
+    if ((flags & PCE_FLAG_UNFUSED) && (flags & PCE_FLAG_LOWP_STORAGE))
+        return fail(PCE_ERR_INVALID, "PCE_FLAG_UNFUSED runs FP32 storage only");
     if (!is_device_ptr(w)) return fail(PCE_ERR_INVALID, "w must be a device pointer");
     if (!is_device_ptr(h)) return fail(PCE_ERR_INVALID, spectra ? "hhat must be a device pointer"
                                                                 : "h must be a device pointer");
@@ -516,10 +739,54 @@ pce_status create_common(pce_plan_t* out, int ndims, const int64_t* shape, int m
         delete p;
         return e;
     };
+    if (ndims == 1 && nx > 8192) {
+        if (flags & PCE_FLAG_LOWP_STORAGE) {
+            delete p;
+            return fail(PCE_ERR_UNSUPPORTED, "reduced storage serves 1D sizes up to 8192");
+        }
+        p->l1 = true;
+        int L = 0;
+        while ((1 << L) < nx) ++L;
+        p->l1ny = 1 << (L / 2);
+        p->l1nx = nx / p->l1ny;
+    }
     if ((st = make_twiddles(p, s))) return bail(st);
+    if ((st = dev_alloc(&p->d_status, 1))) return bail(st);
+    if (cudaMemsetAsync(p->d_status, 0, sizeof(int), s) != cudaSuccess)
+        return bail(fail(PCE_ERR_CUDA, "status word initialisation failed"));
     if ((st = setup_windows(p, w, s))) return bail(st);
     const int nxh = nx / 2;
-    if (ndims == 1) {
+    if (p->l1) {
+        const int npairs = (m + 1) / 2;
+        const long long N = nx;
+        if ((st = dev_alloc(&p->hh4, (size_t)(m * N)))) return bail(st);
+        if (spectra) {
+            k_from_half_l1<<<grid_for(m * N), 256, 0, s>>>(reinterpret_cast<const float2*>(h), m, p->l1ny,
+                                                          p->l1nx, p->hh4);
+            cudaError_t e = cudaGetLastError();
+            if (e) return bail(fail(PCE_ERR_CUDA, "spectrum conversion: %s", cudaGetErrorString(e)));
+        } else {
+            float2* G = nullptr;
+            if ((st = dev_alloc(&G, (size_t)(npairs * N)))) return bail(st);
+            const int cpc = pce::l1_cols_per_cta(p->l1ny);
+            cudaError_t e = pce::launch_l1_cols(p->l1ny, 1 /*pair*/, dim3(npairs, 1, (p->l1nx + cpc - 1) / cpc), s,
+                                                h, 0, nullptr, m, p->l1nx, p->twN, G, p->twy);
+            const int it = pce::l1_row_items(p->l1nx);
+            if (e == cudaSuccess)
+                e = pce::launch_l1_rows_spec(p->l1nx, dim3((p->l1ny / 2 + 1 + it - 1) / it, npairs), s, G, npairs,
+                                             m, p->l1ny, p->hh4, p->twx);
+            cudaError_t e2 = cudaStreamSynchronize(s);
+            cudaFree(G);
+            if (e == cudaSuccess) e = e2;
+            if (e) return bail(fail(PCE_ERR_CUDA, "spectrum of h: %s", cudaGetErrorString(e)));
+        }
+        // scratch: per right-hand side npairs * N (G or Q) + N (A or V) complex
+        const long long per_b = ((long long)npairs * N + N) * (long long)sizeof(float2);
+        p->bchunk = (int)std::max<long long>(1, std::min<long long>(kMaxChunk, kScratchBudget / per_b));
+        if ((st = dev_alloc(&p->scrZ, (size_t)(npairs * N * p->bchunk)))) return bail(st);
+        if ((st = dev_alloc(&p->scrA, (size_t)(N * p->bchunk)))) return bail(st);
+        p->scratch_bytes = per_b * p->bchunk;
+    } else if (ndims == 1) {
         if ((st = dev_alloc(&p->hh, (size_t)m * nxh))) return bail(st);
         if (spectra) {
             k_from_half1d<<<grid_for((long long)m * nxh), 256, 0, s>>>(
@@ -545,8 +812,8 @@ pce_status create_common(pce_plan_t* out, int ndims, const int64_t* shape, int m
             const int fpc = pce::rows_pairs_per_cta(nx);
             const int npairs = (ny + 1) / 2;
             cudaError_t e = pce::launch_rows_r2c(nx, false, dim3(r2c_blocks(npairs, nx), m), s, h,
-                                                 (long long)ny * nx, ny, nullptr, nullptr, nullptr,
-                                                 npairs, S, (long long)ny * nxh, 0, p->twx);
+                                                 (long long)ny * nx, ny, nullptr, false, nullptr, nullptr,
+                                                 npairs, S, (long long)ny * nxh, 0, p->twx, p->tw1024);
             const int cpc = pce::cols_columns_per_cta(ny);
             if (e == cudaSuccess)
                 e = pce::launch_cols_spec(ny, dim3(m, (nxh + cpc - 1) / cpc), s, S, nxh, p->hh, p->hN,
@@ -557,6 +824,13 @@ pce_status create_common(pce_plan_t* out, int ndims, const int64_t* shape, int m
             if (e) return bail(fail(PCE_ERR_CUDA, "spectrum of h: %s", cudaGetErrorString(e)));
         }
     }
+    if (ndims == 2 && ny == 1024) {
+        if ((st = dev_alloc(&p->hhT, (size_t)m * ny * nxh))) return bail(st);
+        k_transpose_hh<<<grid_for((long long)m * ny * nxh), 256, 0, s>>>(p->hh, m, ny, nxh, p->hhT);
+        cudaError_t e1 = cudaGetLastError();
+        if (e1) return bail(fail(PCE_ERR_CUDA, "spectrum transpose: %s", cudaGetErrorString(e1)));
+    }
+    if ((flags & PCE_FLAG_LOWP_STORAGE) && (st = quantize_plan(p, s))) return bail(st);
     cudaError_t e = cudaStreamSynchronize(s);
     if (e) return bail(fail(PCE_ERR_CUDA, "plan set-up: %s", cudaGetErrorString(e)));
     *out = p;
@@ -641,8 +915,8 @@ pce_status apply_plain(pce_plan_t p, const float* in, float* out, int64_t batch,
                 if (e == cudaSuccess)
                     e = timed(p, PCE_KERNEL_PLAIN, s, [&] {
                         return pce::launch_rows_r2c(nx, false, dim3(r2c_blocks(npairs, nx), nb), s, tmp,
-                                                    P, ny, nullptr, nullptr, nullptr, npairs, S, H, 0,
-                                                    p->twx);
+                                                    P, ny, nullptr, false, nullptr, nullptr, npairs, S, H, 0,
+                                                    p->twx, p->tw1024);
                     });
                 if (e == cudaSuccess)
                     e = timed(p, PCE_KERNEL_PLAIN, s, [&] {
@@ -664,12 +938,12 @@ pce_status apply_plain(pce_plan_t p, const float* in, float* out, int64_t batch,
             if (e == cudaSuccess)
                 e = timed(p, PCE_KERNEL_PLAIN, s, [&] {
                     return pce::launch_rows_c2r(nx, dim3((npairs + fpc - 1) / fpc, nb), s, p->scrA, H, ny,
-                                                dst, P, scale, p->twx);
+                                                dst, P, scale, p->twx, p->tw1024);
                 });
         } else {
             e = timed(p, PCE_KERNEL_PLAIN, s, [&] {
                 return pce::launch_rows_r2c(nx, false, dim3(r2c_blocks(npairs, nx), nb), s, src, P, ny,
-                                            nullptr, nullptr, nullptr, npairs, S, H, 0, p->twx);
+                                            nullptr, false, nullptr, nullptr, npairs, S, H, 0, p->twx, p->tw1024);
             });
             if (e == cudaSuccess)
                 e = timed(p, PCE_KERNEL_PLAIN, s, [&] {
@@ -693,7 +967,7 @@ pce_status apply_plain(pce_plan_t p, const float* in, float* out, int64_t batch,
                 if (e == cudaSuccess)
                     e = timed(p, PCE_KERNEL_PLAIN, s, [&] {
                         return pce::launch_rows_c2r(nx, dim3((npairs + fpc - 1) / fpc, nb), s, p->scrA, H,
-                                                    ny, tmp, P, scale, p->twx);
+                                                    ny, tmp, P, scale, p->twx, p->tw1024);
                     });
                 if (e == cudaSuccess)
                     e = timed(p, PCE_KERNEL_PLAIN, s, [&] {
@@ -716,11 +990,56 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
     const long long P = (long long)ny * nx;
     const float scale = 1.0f / (float)P;
     cudaError_t e = cudaSuccess;
+    if (p->l1) {
+        const int NY = p->l1ny, NX = p->l1nx;
+        const int npairs = (m + 1) / 2;
+        const int cpc = pce::l1_cols_per_cta(NY);
+        const int tiles = (NX + cpc - 1) / cpc;
+        const int it = pce::l1_row_items(NX);
+        const int kind = adjoint ? PCE_KERNEL_ADJ_1D : PCE_KERNEL_FWD_1D;
+        for (long long b0 = 0; b0 < batch && e == cudaSuccess; b0 += p->bchunk) {
+            const int nb = (int)std::min<long long>(p->bchunk, batch - b0);
+            const float* src = in + b0 * P;
+            float* dst = out + b0 * P;
+            if (!adjoint) {
+                e = timed(p, kind, s, [&] {
+                    return pce::launch_l1_cols(NY, 0 /*window*/, dim3(npairs, nb, tiles), s, src, P, p->wbox, m, NX,
+                                               p->twN, p->scrZ, p->twy);
+                });
+                if (e == cudaSuccess)
+                    e = timed(p, kind, s, [&] {
+                        return pce::launch_l1_rows_fwd(NX, dim3((NY / 2 + 1 + it - 1) / it, nb), s, p->scrZ, npairs,
+                                                       p->hh4, m, NY, p->twN, p->scrA, p->twx);
+                    });
+                if (e == cudaSuccess)
+                    e = timed(p, kind, s, [&] {
+                        return pce::launch_l1_cols_inv(NY, dim3(nb, tiles), s, p->scrA, NX, dst, scale, p->twy);
+                    });
+            } else {
+                e = timed(p, kind, s, [&] {
+                    return pce::launch_l1_cols(NY, 2 /*one*/, dim3(1, nb, tiles), s, src, P, nullptr, m, NX, p->twN,
+                                               p->scrA, p->twy);
+                });
+                if (e == cudaSuccess)
+                    e = timed(p, kind, s, [&] {
+                        return pce::launch_l1_rows_adj(NX, dim3((NY + 2 * it - 1) / (2 * it), nb), s, p->scrA,
+                                                       npairs, p->hh4, m, NY, p->twN, p->scrZ, p->twx);
+                    });
+                if (e == cudaSuccess)
+                    e = timed(p, kind, s, [&] {
+                        return pce::launch_l1_cols_adj(NY, dim3(nb, tiles), s, p->scrZ, npairs, p->wbox, m, NX, dst,
+                                                       scale, p->twy);
+                    });
+            }
+        }
+        if (e) return fail(PCE_ERR_CUDA, "1D apply launch: %s", cudaGetErrorString(e));
+        return PCE_OK;
+    }
     if (p->ndims == 1) {
         e = timed(p, adjoint ? PCE_KERNEL_ADJ_1D : PCE_KERNEL_FWD_1D, s, [&] {
             return adjoint
-                ? pce::launch_adj_1d(nx, (int)batch, s, in, p->wbox, p->hh, m, out, scale, p->twx)
-                : pce::launch_fwd_1d(nx, (int)batch, s, in, p->wbox, p->hh, m, out, scale, p->twx);
+                ? pce::launch_adj_1d(nx, (int)batch, s, in, wstore(p), hstore(p), p->hscale, p->lowp, m, out, scale, p->twx)
+                : pce::launch_fwd_1d(nx, (int)batch, s, in, wstore(p), hstore(p), p->hscale, p->lowp, m, out, scale, p->twx);
         });
         if (e) return fail(PCE_ERR_CUDA, "1D apply launch: %s", cudaGetErrorString(e));
         return PCE_OK;
@@ -740,35 +1059,35 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
             if (p->nitems > 0)
                 e = timed(p, PCE_KERNEL_ROWS_R2C_WINDOW, s, [&] {
                     return pce::launch_rows_r2c(nx, true, dim3(r2c_blocks(p->nitems, nx), nb), s, src,
-                                                P, ny, p->wbox, p->d_box, p->items, p->nitems, p->scrZ,
-                                                zb, zk, p->twx);
+                                                P, ny, wstore(p), p->lowp, p->d_box, p->items, p->nitems, p->scrZ,
+                                                zb, zk, p->twx, p->tw1024);
                 });
             if (e == cudaSuccess)
                 e = timed(p, PCE_KERNEL_COLS_FWD, s, [&] {
                     return pce::launch_cols_fwd(ny, dim3(nb, (nxh + cpc - 1) / cpc), s, p->scrZ, zb, zk,
-                                                p->hh, p->hN, m, p->d_box, nxh, p->scrA, ab, p->twy);
+                                                hstore(p), hNstore(p), p->hscale, p->lowp, m, p->d_box, nxh, p->scrA, ab, p->twy, hTstore(p), p->tw1024, p->d_status, p->wait_limit, p->skip_copy);
                 });
             if (e == cudaSuccess)
                 e = timed(p, PCE_KERNEL_ROWS_C2R, s, [&] {
                     return pce::launch_rows_c2r(nx, dim3((npairs + fpc - 1) / fpc, nb), s, p->scrA, ab,
-                                                ny, dst, P, scale, p->twx);
+                                                ny, dst, P, scale, p->twx, p->tw1024);
                 });
         } else {
             e = timed(p, PCE_KERNEL_ROWS_R2C, s, [&] {
                 return pce::launch_rows_r2c(nx, false, dim3(r2c_blocks(npairs, nx), nb), s, src, P,
-                                            ny, nullptr, nullptr, nullptr, npairs, p->scrA, ab, 0,
-                                            p->twx);
+                                            ny, nullptr, false, nullptr, nullptr, npairs, p->scrA, ab, 0,
+                                            p->twx, p->tw1024);
             });
             if (e == cudaSuccess)
                 e = timed(p, PCE_KERNEL_COLS_ADJ, s, [&] {
                     return pce::launch_cols_adj(ny, dim3(nb, (nxh + cpc - 1) / cpc), s, p->scrA, ab,
-                                                p->hh, p->hN, m, p->d_box, nxh, p->scrZ, zb, zk, p->twy);
+                                                hstore(p), hNstore(p), p->hscale, p->lowp, m, p->d_box, nxh, p->scrZ, zb, zk, p->twy, hTstore(p), p->tw1024, p->d_status, p->wait_limit, p->skip_copy);
                 });
             if (e == cudaSuccess)
                 e = timed(p, PCE_KERNEL_ROWS_ADJ, s, [&] {
                     return pce::launch_rows_adj(nx, dim3((npairs + fpc - 1) / fpc, nb), s, p->scrZ, zb,
-                                                zk, ny, p->wbox, p->d_box, p->kptr, p->klist, dst, P,
-                                                scale, p->twx);
+                                                zk, ny, wstore(p), p->lowp, p->d_box, p->kptr, p->klist, dst, P,
+                                                scale, p->twx, p->tw1024);
                 });
         }
     }
@@ -829,7 +1148,10 @@ pce_status pce_plan_hhat(pce_plan_t plan, float* hhat, void* stream) {
     if (!is_device_ptr(hhat)) return fail(PCE_ERR_INVALID, "hhat must be a device pointer");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int nxh = plan->nx / 2;
-    if (plan->ndims == 1)
+    if (plan->l1)
+        k_to_half_l1<<<grid_for((long long)plan->m * (nxh + 1)), 256, 0, s>>>(
+            plan->hh4, plan->m, plan->l1ny, plan->l1nx, reinterpret_cast<float2*>(hhat));
+    else if (plan->ndims == 1)
         k_to_half1d<<<grid_for((long long)plan->m * (nxh + 1)), 256, 0, s>>>(
             plan->hh, plan->m, nxh, reinterpret_cast<float2*>(hhat));
     else
@@ -848,6 +1170,30 @@ pce_status pce_plan_destroy(pce_plan_t plan) {
 }
 
 const char* pce_last_error_string(void) { return g_err.c_str(); }
+
+pce_status pce_plan_status(pce_plan_t plan, void* stream) {
+    pce_status st = check_plan(plan);
+    if (st) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int h = 0;
+    PCE_CK(cudaMemcpyAsync(&h, plan->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PCE_CK(cudaStreamSynchronize(s));
+    if (h) {
+        PCE_CK(cudaMemsetAsync(plan->d_status, 0, sizeof(int), s));
+        PCE_CK(cudaStreamSynchronize(s));
+        return fail(PCE_ERR_TIMEOUT, "a kernel gave up a bounded wait on an asynchronous copy");
+    }
+    return PCE_OK;
+}
+
+pce_status pce_plan_inject_wait_timeout(pce_plan_t plan, int64_t wait_cycles) {
+    pce_status st = check_plan(plan);
+    if (st) return st;
+    if (wait_cycles < 0) return fail(PCE_ERR_INVALID, "wait_cycles must be >= 0");
+    plan->skip_copy = wait_cycles > 0 ? 1 : 0;
+    plan->wait_limit = wait_cycles > 0 ? (long long)wait_cycles : 2000000000ll;
+    return PCE_OK;
+}
 
 pce_status pce_plan_set_timing(pce_plan_t plan, int enable) {
     pce_status st = check_plan(plan);
@@ -883,8 +1229,9 @@ pce_status pce_plan_timing(pce_plan_t plan, int kind, double* total_ms, int64_t*
 int64_t pce_launch_count(pce_plan_t plan, int adjoint, int64_t batch) {
     (void)adjoint;
     if (!plan || batch <= 0) return 0;
-    if (plan->ndims == 1) return 1;
     const int64_t chunks = (batch + plan->bchunk - 1) / plan->bchunk;
+    if (plan->l1) return chunks * 3;
+    if (plan->ndims == 1) return 1;
     if (plan->flags & PCE_FLAG_UNFUSED) {
         int64_t mk = 0;
         for (const Box& b : plan->box) mk += b.nr > 0;
@@ -930,6 +1277,8 @@ extern "C" pce_status pce_backward(pce_plan_t p, const float* u, const float* r,
     pce_status st = check_plan(p);
     if (st) return st;
     if (batch < 0) return fail(PCE_ERR_INVALID, "batch must be >= 0");
+    if (p->lowp) return fail(PCE_ERR_UNSUPPORTED, "pce_backward runs on plans with FP32 storage only");
+    if (p->l1) return fail(PCE_ERR_UNSUPPORTED, "pce_backward serves 1D sizes up to 8192");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int ny = p->ny, nx = p->nx, m = p->m, nxh = nx / 2;
     const long long P = (long long)ny * nx;
@@ -965,7 +1314,7 @@ extern "C" pce_status pce_backward(pce_plan_t p, const float* u, const float* r,
     }
     long long per_b, chunk;
     backward_layout(p, batch, per_b, chunk);
-    const int fpc = pce::rows_pairs_per_cta(nx);
+    const int gpc = pce::rows_grad_pairs_per_cta(nx);
     const int cpc = pce::cols_columns_per_cta(ny);
     const int npairs = (ny + 1) / 2;
     const int tiles = (nxh + cpc - 1) / cpc;
@@ -981,22 +1330,22 @@ extern "C" pce_status pce_backward(pce_plan_t p, const float* u, const float* r,
         const float* ub = u + b0 * P;
         const float* rb = r + b0 * P;
         const int acc = b0 > 0 ? 1 : 0;
-        e = pce::launch_rows_r2c(nx, false, dim3(r2c_blocks(npairs, nx), nb), s, rb, P, ny, nullptr,
-                                 nullptr, nullptr, npairs, S, H, 0, p->twx);
+        e = pce::launch_rows_r2c(nx, false, dim3(r2c_blocks(npairs, nx), nb), s, rb, P, ny, nullptr, false,
+                                 nullptr, nullptr, npairs, S, H, 0, p->twx, p->tw1024);
         if (dhhat && e == cudaSuccess) {
             e = pce::launch_cols_spec(ny, dim3(nb, tiles), s, S, nxh, Rh, RhN, p->twy);
             if (e == cudaSuccess && p->nitems > 0)
                 e = pce::launch_rows_r2c(nx, true, dim3(r2c_blocks(p->nitems, nx), nb), s, ub, P, ny,
-                                         p->wbox, p->d_box, p->items, p->nitems, Zg, zb, zk, p->twx);
+                                         p->wbox, false, p->d_box, p->items, p->nitems, Zg, zb, zk, p->twx, p->tw1024);
             if (e == cudaSuccess)
                 e = pce::launch_cols_grad_h(ny, dim3(m, tiles), s, Zg, zb, zk, nb, Rh, RhN, p->d_box, nxh,
                                             reinterpret_cast<float2*>(dhhat), scale, acc, p->twy);
         }
         if (dw && e == cudaSuccess) {
             e = pce::launch_cols_adj_full(ny, dim3(nb, tiles), s, S, H, p->hh, p->hN, m, p->d_box, nxh, Qf,
-                                          (long long)m * H, H, p->twy);
+                                          (long long)m * H, H, p->twy, p->hhT, p->tw1024, p->d_status, p->wait_limit, p->skip_copy);
             if (e == cudaSuccess)
-                e = pce::launch_rows_grad_w(nx, dim3((npairs + fpc - 1) / fpc, m), s, Qf, (long long)m * H, H,
+                e = pce::launch_rows_grad_w(nx, dim3((npairs + gpc - 1) / gpc, m), s, Qf, (long long)m * H, H,
                                             ny, nb, ub, P, dw, scale, acc, p->twx);
         }
     }
@@ -1089,14 +1438,16 @@ extern "C" pce_status pce_apply_noalloc(pce_plan_t plan, const float* u, float* 
         const int nb = (int)std::min<long long>(chunk, batch - b0);
         if (plan->nitems > 0)
             e = pce::launch_rows_r2c(nx, true, dim3(r2c_blocks(plan->nitems, nx), nb), s, u + b0 * P, P,
-                                     ny, plan->wbox, plan->d_box, plan->items, plan->nitems, scrZ, zb, zk,
-                                     plan->twx);
+                                     ny, wstore(plan), plan->lowp, plan->d_box, plan->items, plan->nitems, scrZ, zb, zk,
+                                     plan->twx, plan->tw1024);
         if (e == cudaSuccess)
-            e = pce::launch_cols_fwd(ny, dim3(nb, (nxh + cpc - 1) / cpc), s, scrZ, zb, zk, plan->hh,
-                                     plan->hN, m, plan->d_box, nxh, scrA, ab, plan->twy);
+            e = pce::launch_cols_fwd(ny, dim3(nb, (nxh + cpc - 1) / cpc), s, scrZ, zb, zk, hstore(plan),
+                                     hNstore(plan), plan->hscale, plan->lowp, m, plan->d_box, nxh, scrA, ab,
+                                     plan->twy, hTstore(plan), plan->tw1024, plan->d_status, plan->wait_limit,
+                                     plan->skip_copy);
         if (e == cudaSuccess)
             e = pce::launch_rows_c2r(nx, dim3((npairs + fpc - 1) / fpc, nb), s, scrA, ab, ny, y + b0 * P, P,
-                                     scale, plan->twx);
+                                     scale, plan->twx, plan->tw1024);
     }
     if (e) return fail(PCE_ERR_CUDA, "pce_apply_noalloc launch: %s", cudaGetErrorString(e));
     return PCE_OK;

@@ -5,25 +5,34 @@
 namespace pce {
 
 int rows_pairs_per_cta(int nx) { return 256 / (nx / kR); }
+int rows_grad_pairs_per_cta(int nx) { return 256 / (nx / kR); }
 int rows_r2c_items_per_cta(int nx) { return kRowIters * (256 / (nx / kR)); }
 
 #define PCE_ROW_SIZES(X) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048)
 
 cudaError_t launch_rows_r2c(int nx, bool window, dim3 grid, cudaStream_t s,
                             const float* src, long long src_bstride, int nrows,
-                            const float* wbox, const Box* box, const int2* items, int nitems,
+                            const void* wbox, bool lowp, const Box* box, const int2* items, int nitems,
                             float2* dst, long long dst_bstride, long long dst_kstride,
-                            const float2* tw) {
+                            const float2* tw, const float2* /*tw1024*/) {
+    using bf16 = __nv_bfloat16;
     switch (nx) {
 #define X(N)                                                                                   \
     case N:                                                                                    \
-        if (window)                                                                            \
-            k_rows_r2c<N, true><<<grid, 256, 0, s>>>(src, src_bstride, nrows, wbox, box, items, \
-                                                     nitems, dst, dst_bstride, dst_kstride, tw); \
+        if (window && lowp)                                                                    \
+            k_rows_r2c<N, true, bf16><<<grid, 256, 0, s>>>(src, src_bstride, nrows,            \
+                                                          static_cast<const bf16*>(wbox), box,  \
+                                                          items, nitems, dst, dst_bstride,     \
+                                                          dst_kstride, tw);                    \
+        else if (window)                                                                       \
+            k_rows_r2c<N, true, float><<<grid, 256, 0, s>>>(src, src_bstride, nrows,           \
+                                                           static_cast<const float*>(wbox), box, \
+                                                           items, nitems, dst, dst_bstride,    \
+                                                           dst_kstride, tw);                   \
         else                                                                                   \
-            k_rows_r2c<N, false><<<grid, 256, 0, s>>>(src, src_bstride, nrows, wbox, box,       \
-                                                      items, nitems, dst, dst_bstride,         \
-                                                      dst_kstride, tw);                        \
+            k_rows_r2c<N, false, float><<<grid, 256, 0, s>>>(src, src_bstride, nrows, nullptr,  \
+                                                            box, items, nitems, dst,           \
+                                                            dst_bstride, dst_kstride, tw);     \
         break;
         PCE_ROW_SIZES(X)
 #undef X
@@ -35,7 +44,7 @@ cudaError_t launch_rows_r2c(int nx, bool window, dim3 grid, cudaStream_t s,
 
 cudaError_t launch_rows_c2r(int nx, dim3 grid, cudaStream_t s, const float2* src,
                             long long src_bstride, int nrows, float* dst, long long dst_bstride,
-                            float scale, const float2* tw) {
+                            float scale, const float2* tw, const float2* /*tw1024*/) {
     switch (nx) {
 #define X(N)                                                                                  \
     case N:                                                                                   \
@@ -50,14 +59,21 @@ cudaError_t launch_rows_c2r(int nx, dim3 grid, cudaStream_t s, const float2* src
 }
 
 cudaError_t launch_rows_adj(int nx, dim3 grid, cudaStream_t s, const float2* Q, long long q_bstride,
-                            long long q_kstride, int nrows, const float* wbox, const Box* box,
+                            long long q_kstride, int nrows, const void* wbox, bool lowp, const Box* box,
                             const int* kptr, const int* klist, float* dst, long long dst_bstride,
-                            float scale, const float2* tw) {
+                            float scale, const float2* tw, const float2* /*tw1024*/) {
+    using bf16 = __nv_bfloat16;
     switch (nx) {
 #define X(N)                                                                                   \
     case N:                                                                                    \
-        k_rows_adj<N><<<grid, 256, 0, s>>>(Q, q_bstride, q_kstride, nrows, wbox, box, kptr,     \
-                                           klist, dst, dst_bstride, scale, tw);                \
+        if (lowp)                                                                              \
+            k_rows_adj<N, bf16><<<grid, 256, 0, s>>>(Q, q_bstride, q_kstride, nrows,            \
+                                                    static_cast<const bf16*>(wbox), box, kptr, \
+                                                    klist, dst, dst_bstride, scale, tw);       \
+        else                                                                                   \
+            k_rows_adj<N, float><<<grid, 256, 0, s>>>(Q, q_bstride, q_kstride, nrows,           \
+                                                     static_cast<const float*>(wbox), box,     \
+                                                     kptr, klist, dst, dst_bstride, scale, tw); \
         break;
         PCE_ROW_SIZES(X)
 #undef X

@@ -1,0 +1,125 @@
+// warpfft.cuh -- one-warp 1024-point FFT (four-step, 32 x 32) for sm_103a.
+//
+// Lane l holds v[q] = x[l + 32 q] (q = 0..31).  With n = l + 32 q and
+// k = p + 32 m (l, q, p, m < 32):
+//   X[p + 32 m] = sum_l W32^{l m} W1024^{l p} sum_q x[l + 32 q] W32^{q p},
+// so the FFT is
+//   1. a 32-point DFT over q in each lane's registers,
+//   2. the twiddles W1024^{l p} (table, FP32 rounded from FP64),
+//   3. a transpose of the 32 x 32 block through a warp-private shared tile
+//      (XOR-swizzled: element (l, p) at l*32 + (p ^ l), conflict-free both
+//      for the column writes and the row reads of a half-warp),
+//   4. a 32-point DFT over l in each lane.
+// On exit lane p holds v[m] = X[p + 32 m]: the same layout as on entry, so a
+// forward FFT, a pointwise product and an inverse FFT chain in registers.
+// Only __syncwarp is used: warps never wait for one another.
+// The inverse uses the conjugate twiddles and is unnormalised.
+#pragma once
+
+#include "fft.cuh"
+
+namespace pce {
+
+// cos(2 pi j / 32) on [0, 8] (FP32, correctly rounded; exact at 0 and 8)
+__host__ __device__ constexpr float cos32q(int j) {
+    return j == 0 ? 1.0f
+         : j == 1 ? 0.980785251f
+         : j == 2 ? 0.923879504f
+         : j == 3 ? 0.831469595f
+         : j == 4 ? 0.707106769f
+         : j == 5 ? 0.555570245f
+         : j == 6 ? 0.382683426f
+         : j == 7 ? 0.195090324f
+         : 0.0f;
+}
+__host__ __device__ constexpr float cos32(int j) {
+    return (j & 31) <= 8 ? cos32q(j & 31)
+         : (j & 31) <= 16 ? -cos32q(16 - (j & 31))
+         : (j & 31) <= 24 ? -cos32q((j & 31) - 16)
+         : cos32q(32 - (j & 31));
+}
+// sin(2 pi j / 32) = cos(2 pi (j - 8) / 32)
+__host__ __device__ constexpr float sin32(int j) { return cos32((j + 24) & 31); }
+
+// x * W32^j (forward: exp(-2 pi i j / 32); inverse: conjugate); j a compile-time constant
+template <bool INV>
+__device__ __forceinline__ float2 tw32(float2 x, int j) {
+    if (j == 0) return x;
+    if (j == 8) return mul_mi<INV>(x);
+    const float c = cos32(j);
+    const float s = INV ? sin32(j) : -sin32(j);
+    return cmul(x, make_float2(c, s));
+}
+
+// In-register 32-point DFT, natural order in and out: n = 4 n1 + n2,
+// k = k1 + 8 k2, X[k1 + 8 k2] = sum_n2 W4^{n2 k2} W32^{n2 k1} sum_n1 x[4 n1 + n2] W8^{n1 k1}.
+template <bool INV>
+__device__ __forceinline__ void dft32(float2 (&a)[32]) {
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+        float2 x[8];
+#pragma unroll
+        for (int n1 = 0; n1 < 8; ++n1) x[n1] = a[4 * n1 + n2];
+        Dft<8, INV>::run(x);
+#pragma unroll
+        for (int k1 = 0; k1 < 8; ++k1) a[4 * k1 + n2] = tw32<INV>(x[k1], n2 * k1);
+    }
+    float2 out[32];
+#pragma unroll
+    for (int k1 = 0; k1 < 8; ++k1) {
+        float2 y[4] = {a[4 * k1], a[4 * k1 + 1], a[4 * k1 + 2], a[4 * k1 + 3]};
+        Dft<4, INV>::run(y);
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) out[k1 + 8 * k2] = y[k2];
+    }
+#pragma unroll
+    for (int i = 0; i < 32; ++i) a[i] = out[i];
+}
+
+// Twiddle table of the four-step 1024-point FFT: tw[p * 32 + l] = W1024^{l p}.
+constexpr int kWarpTwLen = 1024;
+
+struct NoHook {
+    __device__ __forceinline__ void operator()() const {}
+};
+
+// One-warp 1024-point FFT (see the file comment).  tile: 1024 float2 of
+// shared memory private to the calling warp.  All 32 lanes must call it.
+// hook() runs once the transpose has been read back, i.e. when the tile is
+// free again (it may start an asynchronous copy into the tile).
+template <bool INV, typename Hook = NoHook>
+__device__ __forceinline__ void warp_fft1024(float2 (&v)[32], float2* tile, const float2* __restrict__ tw,
+                                             Hook hook = Hook()) {
+    const int lane = threadIdx.x & 31;
+    dft32<INV>(v);
+    // keep the twiddle loads after the first DFT: hoisted above it they would
+    // hold 62 more registers through it
+    __syncwarp();
+#pragma unroll
+    for (int p = 1; p < 32; ++p) {
+        const float2 t = __ldg(&tw[p * 32 + lane]);
+        v[p] = INV ? cmulc(v[p], t) : cmul(v[p], t);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int p = 0; p < 32; ++p) tile[lane * 32 + (p ^ lane)] = v[p];
+    __syncwarp();
+#pragma unroll
+    for (int l = 0; l < 32; ++l) v[l] = tile[l * 32 + (lane ^ l)];
+    __syncwarp();
+    hook();
+    dft32<INV>(v);
+}
+
+// Value X[1024 - f] for f = lane + 32 m, from the lane holding it: lane
+// (32 - lane) & 31, register 31 - m; lane 0 holds its own partner in
+// register (32 - m) & 31.
+__device__ __forceinline__ float2 warp_partner(const float2 (&v)[32], int lane, int M) {
+    float2 z;
+    z.x = __shfl_sync(0xffffffffu, v[31 - M].x, (32 - lane) & 31);
+    z.y = __shfl_sync(0xffffffffu, v[31 - M].y, (32 - lane) & 31);
+    if (lane == 0) z = v[(32 - M) & 31];
+    return z;
+}
+
+}  // namespace pce

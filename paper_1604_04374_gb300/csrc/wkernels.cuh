@@ -1,0 +1,289 @@
+// wkernels.cuh -- warp-FFT column kernels for columns of length Ny = 1024.
+// They compute exactly what the generic column kernels of kernels.cuh
+// compute, with the same global layouts (the spectra also in a transposed
+// copy), but every 1024-point column FFT is done by one warp (warpfft.cuh):
+// no CTA barrier inside an FFT and one shared-memory transpose per FFT,
+// where the generic kernel needs three barrier-separated exchanges.
+// (For the row passes the generic kernels stay faster: they keep 48 warps
+// per SM resident, the one-warp FFT's 32 elements per lane allow about 12.)
+//
+// One warp per half-spectrum column, 4 columns per CTA.  The
+// column data are moved between global memory and the warps through a
+// shared tile [row][kTileStride] (odd stride: a warp reading one column of
+// 16 consecutive rows hits 16 distinct bank pairs), filled with cp.async
+// 8-byte copies of 32-byte row segments; the copy of the next term's tile
+// overlaps the current term's FFT.
+#pragma once
+
+#include "kernels.cuh"
+#include "warpfft.cuh"
+
+namespace pce {
+
+constexpr int kWarpN = 1024;
+constexpr int kWColWarps = 4;          // columns per CTA of the column kernels
+constexpr int kTileStride = kWColWarps + 1;
+constexpr int kWColSmem = (kWarpN * kTileStride + kWColWarps * kWarpN) * (int)sizeof(float2);
+
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool pred) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    const int sz = pred ? 8 : 0;   // src-size 0: write zeros, read nothing
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "r"(sz) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// ---- bulk asynchronous copies (TMA engine) tracked by an mbarrier
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+
+// Arm the barrier for `bytes` and, unless skip_copy, copy `bytes` from global
+// memory to shared memory on the TMA engine.  Called by one lane.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar,
+                                          bool skip_copy) {
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+    if (!skip_copy)
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                smem_addr(dst)),
+            "l"(src), "r"(bytes), "r"(smem_addr(bar))
+            : "memory");
+}
+
+// Wait for phase `parity` of the barrier, for at most kWaitCycles clock
+// cycles (about a second).  Returns false when the wait gave up.
+constexpr long long kWaitCycles = 2000000000ll;
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, long long limit) {
+    const long long t0 = clock64();
+    while (true) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(smem_addr(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > limit) return false;
+    }
+}
+
+// Device status word of a plan: bit 0 = a bounded wait gave up.
+constexpr int kStatusTimeout = 1;
+
+// ----------------------------------------------------------- column kernels
+// Cooperative async copy of rows [0, nrows) of a [rows][nxh] column tile
+// (columns col0 .. col0+3) into the shared tile, row i -> tile row i.
+__device__ __forceinline__ void tile_load(float2* tile, const float2* __restrict__ src, int nrows_tile,
+                                          int nxh, int col0) {
+    for (int e = threadIdx.x; e < nrows_tile * kWColWarps; e += kWColWarps * 32) {
+        const int i = e >> 2, c = e & 3;
+        const bool ok = col0 + c < nxh;
+        cp_async8(tile + i * kTileStride + c, src + (long long)i * nxh + (ok ? col0 + c : 0), ok);
+    }
+    cp_async_commit();
+}
+
+// The DC/Nyquist column (column 0 of tile 0): separate the FFT of
+// DC + i Nyquist at f = lane + 32 m into A (DC) and B (Nyquist).
+__device__ __forceinline__ void warp_split(const float2 (&v)[32], int lane, int m, float2& A, float2& B) {
+    split_dc_nyq(v[m], warp_partner(v, lane, m), A, B);
+}
+
+// F2 for Ny = 1024.  Grid (batch, NXh / 4), 128 threads, kWColSmem bytes.
+// hhT: [m][NXh][1024] (column c's spectrum contiguous; c = 0: DC column),
+// hN: [m][1024] (Nyquist column).
+template <typename HT = float2>
+__global__ void __launch_bounds__(kWColWarps * 32, 3)
+kw_cols_fwd(const float2* __restrict__ Z, long long z_bstride, long long z_kstride,
+            const HT* __restrict__ hhT, const HT* __restrict__ hN, const float* __restrict__ hscale, int m,
+            const Box* __restrict__ box, int NXh, float2* __restrict__ A, long long a_bstride,
+            const float2* __restrict__ tw, int* __restrict__ status, long long wait_limit, int skip_copy) {
+    constexpr int NY = kWarpN;
+    extern __shared__ float2 smem[];
+    float2* tile = smem;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float2* tr = smem + NY * kTileStride + warp * kWarpN;
+    const int b = blockIdx.x;
+    const int col0 = blockIdx.y * kWColWarps;
+    const int col = col0 + warp;
+    const bool cv = col < NXh;
+    const bool dcn = blockIdx.y == 0 && warp == 0;
+    const float2* Zb = Z + b * z_bstride;
+    __shared__ unsigned long long bars[kWColWarps];
+    unsigned long long* bar = &bars[warp];
+    if (lane == 0) mbar_init(bar);
+    __syncwarp();
+    unsigned parity = 0;
+    bool failed = false;
+
+    float2 acc[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) acc[i] = make_float2(0.f, 0.f);
+    int k = 0;
+    while (k < m && box[k].nr == 0) ++k;
+    if (k < m) tile_load(tile, Zb + k * z_kstride, box[k].nr, NXh, col0);
+    while (k < m) {
+        int kn = k + 1;
+        while (kn < m && box[kn].nr == 0) ++kn;
+        const Box bx = box[k];
+        cp_async_wait_all();
+        __syncthreads();
+        float2 v[32];
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+            const int i = wrap(lane + 32 * q - bx.r0, NY);
+            v[q] = (i < bx.nr) ? tile[i * kTileStride + warp] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        if (kn < m) tile_load(tile, Zb + kn * z_kstride, box[kn].nr, NXh, col0);
+        // this column's spectrum of term k arrives in the warp's transpose
+        // tile while the FFT finishes
+        const bool bulk = !dcn && cv && !failed;
+        const float sk = hscale_of<HT>(hscale, k);
+        warp_fft1024<false>(v, tr, tw, [&] {
+            if (bulk && lane == 0)
+                bulk_load(tr, hhT + ((long long)k * NXh + col) * NY, NY * sizeof(HT), bar, skip_copy);
+        });
+        if (bulk) {
+            if (!mbar_wait(bar, parity, wait_limit)) {
+                failed = true;
+                if (lane == 0) atomicOr(status, kStatusTimeout);
+            }
+            parity ^= 1;
+        }
+        if (dcn) {
+            const HT* h0 = hhT + (long long)k * NXh * NY;
+            const HT* hn = hN + (long long)k * NY;
+#pragma unroll
+            for (int mm = 0; mm < 32; ++mm) {
+                const int f = lane + 32 * mm;
+                float2 a, bb;
+                warp_split(v, lane, mm, a, bb);
+                acc[mm] = cfma(ldh(&h0[f], sk), a, acc[mm]);
+                const float2 t = cmul(ldh(&hn[f], sk), bb);
+                acc[mm].x -= t.y;
+                acc[mm].y += t.x;
+            }
+        } else if (cv && !failed) {
+            const HT* th = reinterpret_cast<const HT*>(tr);
+#pragma unroll
+            for (int mm = 0; mm < 32; ++mm) acc[mm] = cfma(lds_h(&th[lane + 32 * mm], sk), v[mm], acc[mm]);
+        }
+        k = kn;
+    }
+    warp_fft1024<true>(acc, tr, tw);
+    __syncthreads();
+#pragma unroll
+    for (int mm = 0; mm < 32; ++mm) tile[(lane + 32 * mm) * kTileStride + warp] = acc[mm];
+    __syncthreads();
+    float2* Ab = A + b * a_bstride;
+    for (int e = threadIdx.x; e < NY * kWColWarps; e += kWColWarps * 32) {
+        const int i = e >> 2, c = e & 3;
+        if (col0 + c < NXh) Ab[(long long)i * NXh + col0 + c] = tile[i * kTileStride + c];
+    }
+}
+
+// G1b + G2 for Ny = 1024 (FULL: every row of Q, for the window gradient).
+// Grid (batch, NXh / 4).
+template <bool FULL, typename HT = float2>
+__global__ void __launch_bounds__(kWColWarps * 32, 3)
+kw_cols_adj(const float2* __restrict__ V, long long v_bstride,
+            const HT* __restrict__ hhT, const HT* __restrict__ hN, const float* __restrict__ hscale, int m,
+            const Box* __restrict__ box, int NXh,
+            float2* __restrict__ Q, long long q_bstride, long long q_kstride,
+            const float2* __restrict__ tw, int* __restrict__ status, long long wait_limit, int skip_copy) {
+    constexpr int NY = kWarpN;
+    extern __shared__ float2 smem[];
+    float2* tile = smem;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float2* tr = smem + NY * kTileStride + warp * kWarpN;
+    const int b = blockIdx.x;
+    const int col0 = blockIdx.y * kWColWarps;
+    const int col = col0 + warp;
+    const bool cv = col < NXh;
+    const bool dcn = blockIdx.y == 0 && warp == 0;
+    __shared__ unsigned long long bars[kWColWarps];
+    unsigned long long* bar = &bars[warp];
+    if (lane == 0) mbar_init(bar);
+    __syncwarp();
+    unsigned parity = 0;
+    bool failed = false;
+    const bool use_bulk = !dcn && cv;
+    auto next_term = [&](int k) {
+        while (k < m && !FULL && box[k].nr == 0) ++k;
+        return k;
+    };
+
+    tile_load(tile, V + b * v_bstride, NY, NXh, col0);
+    cp_async_wait_all();
+    __syncthreads();
+    float2 vv[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) vv[q] = tile[(lane + 32 * q) * kTileStride + warp];
+    int k = next_term(0);
+    // the spectrum of the first term arrives while the FFT of V finishes
+    warp_fft1024<false>(vv, tr, tw, [&] {
+        if (use_bulk && k < m && lane == 0)
+            bulk_load(tr, hhT + ((long long)k * NXh + col) * NY, NY * sizeof(HT), bar, skip_copy);
+    });
+    while (k < m) {
+        const Box bx = box[k];
+        const int kn = next_term(k + 1);
+        if (use_bulk && !failed) {
+            if (!mbar_wait(bar, parity, wait_limit)) {
+                failed = true;
+                if (lane == 0) atomicOr(status, kStatusTimeout);
+            }
+            parity ^= 1;
+        }
+        float2 p[32];
+        const float sk = hscale_of<HT>(hscale, k);
+        if (dcn) {
+            const HT* h0 = hhT + (long long)k * NXh * NY;
+            const HT* hn = hN + (long long)k * NY;
+#pragma unroll
+            for (int mm = 0; mm < 32; ++mm) {
+                const int f = lane + 32 * mm;
+                float2 a, bb;
+                warp_split(vv, lane, mm, a, bb);
+                float2 t = cmulc(a, ldh(&h0[f], sk));
+                const float2 s = cmulc(bb, ldh(&hn[f], sk));
+                t.x -= s.y;
+                t.y += s.x;
+                p[mm] = t;
+            }
+        } else {
+            const HT* th = reinterpret_cast<const HT*>(tr);
+#pragma unroll
+            for (int mm = 0; mm < 32; ++mm)
+                p[mm] = (use_bulk && !failed) ? cmulc(vv[mm], lds_h(&th[lane + 32 * mm], sk))
+                                              : make_float2(0.f, 0.f);
+        }
+        // the next term's spectrum arrives while this inverse FFT finishes
+        const bool issue = use_bulk && !failed && kn < m;
+        warp_fft1024<true>(p, tr, tw, [&] {
+            if (issue && lane == 0)
+                bulk_load(tr, hhT + ((long long)kn * NXh + col) * NY, NY * sizeof(HT), bar, skip_copy);
+        });
+        __syncthreads();
+#pragma unroll
+        for (int mm = 0; mm < 32; ++mm) tile[(lane + 32 * mm) * kTileStride + warp] = p[mm];
+        __syncthreads();
+        float2* Qk = Q + b * q_bstride + k * q_kstride;
+        const int rows = FULL ? NY : bx.nr;
+        for (int e = threadIdx.x; e < rows * kWColWarps; e += kWColWarps * 32) {
+            const int i = e >> 2, c = e & 3;
+            const int g = FULL ? i : wrap(bx.r0 + i, NY);
+            if (col0 + c < NXh) Qk[(long long)i * NXh + col0 + c] = tile[g * kTileStride + c];
+        }
+        k = kn;
+    }
+}
+
+}  // namespace pce

@@ -15,6 +15,7 @@ from . import build as _build
 PCE_OK, PCE_ERR_INVALID, PCE_ERR_UNSUPPORTED, PCE_ERR_OOM, PCE_ERR_CUDA, PCE_ERR_TIMEOUT = range(6)
 PCE_FLAG_NONE = 0
 PCE_FLAG_UNFUSED = 1
+PCE_FLAG_LOWP_STORAGE = 2
 STATUS_NAMES = {0: "PCE_OK", 1: "PCE_ERR_INVALID", 2: "PCE_ERR_UNSUPPORTED", 3: "PCE_ERR_OOM",
                 4: "PCE_ERR_CUDA", 5: "PCE_ERR_TIMEOUT"}
 
@@ -55,6 +56,10 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.pce_backward_workspace_bytes.restype = i64
     lib.pce_backward.argtypes = [P, P, P, P, P, P, i64, P, i64, P]
     lib.pce_backward.restype = ctypes.c_int
+    lib.pce_plan_status.argtypes = [P, P]
+    lib.pce_plan_status.restype = ctypes.c_int
+    lib.pce_plan_inject_wait_timeout.argtypes = [P, i64]
+    lib.pce_plan_inject_wait_timeout.restype = ctypes.c_int
     lib.pce_apply_noalloc.argtypes = [P, P, P, i64, P]
     lib.pce_apply_noalloc.restype = ctypes.c_int
     lib.pce_plan_set_timing.argtypes = [P, ctypes.c_int]
@@ -106,6 +111,15 @@ def pce_apply_adjoint(plan: int, v_ptr: int, x_ptr: int, batch: int, stream: int
 def pce_apply_noalloc(plan: int, u_ptr: int, y_ptr: int, batch: int, stream: int = 0) -> None:
     """y = H_m u on a 2D plan with the intermediates in the library's static device scratch."""
     _check(load_library().pce_apply_noalloc(plan, u_ptr, y_ptr, batch, stream))
+
+
+def pce_plan_status(plan: int, stream: int = 0) -> None:
+    """Raise PceError(PCE_ERR_TIMEOUT) if a kernel gave up a bounded wait since the last check."""
+    _check(load_library().pce_plan_status(plan, stream))
+
+
+def pce_plan_inject_wait_timeout(plan: int, wait_cycles: int) -> None:
+    _check(load_library().pce_plan_inject_wait_timeout(plan, wait_cycles))
 
 
 def pce_backward_workspace_bytes(plan: int, batch: int) -> int:

@@ -57,7 +57,7 @@ def test_argument_errors_are_status_codes(lib):
     assert lib.pce_plan_create(ctypes.byref(out), 3, shp, 4, None, None, 0, None) == pce.PCE_ERR_INVALID
     shp_bad = (ctypes.c_int64 * 2)(1000, 1024)
     assert lib.pce_plan_create(ctypes.byref(out), 2, shp_bad, 4, None, None, 0, None) == pce.PCE_ERR_UNSUPPORTED
-    shp_big = (ctypes.c_int64 * 1)(1 << 16)
+    shp_big = (ctypes.c_int64 * 1)(1 << 19)
     assert lib.pce_plan_create(ctypes.byref(out), 1, shp_big, 4, None, None, 0, None) == pce.PCE_ERR_UNSUPPORTED
     assert lib.pce_plan_create(ctypes.byref(out), 2, shp, 0, None, None, 0, None) == pce.PCE_ERR_INVALID
     assert lib.pce_plan_create(None, 2, shp, 4, None, None, 0, None) == pce.PCE_ERR_INVALID

@@ -1,0 +1,45 @@
+"""Failure detection without a GPU fault: a bounded wait that runs out.
+
+The one-warp column kernels (columns of length 1024) wait on an mbarrier for
+a bulk copy of a spectrum column.  With the copies suppressed
+(pce_plan_inject_wait_timeout), every wait gives up after a short bounded
+time, the kernels skip the dependent work, and the plan's status word turns
+the event into PCE_ERR_TIMEOUT on the host.  Nothing hangs and the context
+stays usable: after restoring normal operation the results are correct again.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import expansion as E
+
+pytestmark = pytest.mark.gpu
+
+
+def test_bounded_wait_times_out_and_recovers():
+    import torch
+    from paper_1604_04374_gb300 import Plan, PceError, build, pce
+    build.build()
+    pr = synth.problem_2d(1024, 64, 4, 1, 41, "normal")
+    dev = torch.device("cuda", 0)
+    plan = Plan(torch.from_numpy(pr.w).to(dev), h=torch.from_numpy(pr.h).to(dev))
+    u = torch.from_numpy(pr.u).to(dev)
+    pce.pce_plan_status(plan.handle)                       # clean start
+    pce.pce_plan_inject_wait_timeout(plan.handle, 200000)  # about 0.1 ms per wait
+    plan.apply(u)
+    plan.apply_adjoint(u)
+    with pytest.raises(PceError) as e:
+        pce.pce_plan_status(plan.handle)
+    assert e.value.status == pce.PCE_ERR_TIMEOUT
+    pce.pce_plan_status(plan.handle)                       # cleared by the previous read
+    pce.pce_plan_inject_wait_timeout(plan.handle, 0)
+    y = plan.apply(u).cpu().numpy().astype(np.float64)
+    x = plan.apply_adjoint(u).cpu().numpy().astype(np.float64)
+    pce.pce_plan_status(plan.handle)
+    pts = np.stack([np.random.default_rng(1).integers(0, n, 200) for n in pr.shape], axis=-1)
+    sel = (slice(None),) + tuple(pts.T)
+    yr = E.apply_at(pr.u, pr.w, pr.h, pts)
+    xr = E.apply_adjoint_at(pr.u, pr.w, pr.h, pts)
+    assert np.linalg.norm(y[sel] - yr) / np.linalg.norm(yr) < 1e-5
+    assert np.linalg.norm(x[sel] - xr) / np.linalg.norm(xr) < 1e-5
+    plan.close()

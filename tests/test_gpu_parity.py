@@ -89,6 +89,8 @@ def test_plan_spectra_match_naive_dft(torch_cuda, shape):
 
 SMALL_2D = [
     (16, 16, 4, 2), (64, 64, 4, 3), (32, 128, 8, 2), (128, 32, 8, 1), (64, 64, 16, 2),
+    # a side of 1024 runs the one-warp FFT kernels (rows and columns)
+    (16, 1024, 4, 2), (1024, 16, 4, 3), (32, 1024, 8, 1),
 ]
 
 
@@ -124,6 +126,30 @@ def test_dense_random_windows_and_responses(torch_cuda, shape):
     m = 5
     w = rng.standard_normal((m,) + shape)
     h = rng.standard_normal((m,) + shape)
+    u = rng.standard_normal((2,) + shape)
+    pr = custom(shape, w, h, u)
+    y, x = run_both(torch_cuda, pr)
+    assert rel_l2(y, E.apply(pr.u, pr.w, pr.h)) < TOL
+    assert rel_l2(x, E.apply_adjoint(pr.u, pr.w, pr.h)) < TOL
+
+
+@pytest.mark.parametrize("shape", [(1024, 32), (16, 1024)])
+def test_sparse_arbitrary_operator_at_1024(torch_cuda, shape):
+    """Random windows on random boxes and random sparse impulse responses, one side 1024."""
+    rng = np.random.default_rng(17)
+    m = 3
+    ny, nx = shape
+    w = np.zeros((m,) + shape)
+    for k in range(m):
+        r0, c0 = rng.integers(0, ny), rng.integers(0, nx)
+        nr, nc = rng.integers(1, ny + 1), rng.integers(1, nx + 1)
+        rows = (r0 + np.arange(nr)) % ny
+        cols = (c0 + np.arange(nc)) % nx
+        w[k][np.ix_(rows, cols)] = rng.standard_normal((nr, nc))
+    h = np.zeros((m,) + shape)
+    idx = rng.integers(0, ny * nx, size=(m, 150))
+    for k in range(m):
+        h[k].reshape(-1)[idx[k]] = rng.standard_normal(150)
     u = rng.standard_normal((2,) + shape)
     pr = custom(shape, w, h, u)
     y, x = run_both(torch_cuda, pr)

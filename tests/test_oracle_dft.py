@@ -54,3 +54,18 @@ def test_convolution_identity_by_brute_force():
     w = D.idft(D.dft(h) * D.dft(u))
     assert np.max(np.abs(w.real - np.array(v))) < 1e-13
     assert np.max(np.abs(w.imag)) < 1e-13
+
+
+def test_dft_at_delta_atom_and_full_transform():
+    """dft_at: a delta at j0 gives exp(-2 i pi j0 f / n); a pure atom gives n at its frequency."""
+    n = 64
+    x = np.zeros(n)
+    x[5] = 1.0
+    f = np.array([0, 1, 7, 32, 63])
+    np.testing.assert_allclose(D.dft_at(x, f)[0:], np.exp(-2j * np.pi * 5 * f / n), atol=1e-13)
+    atom = np.exp(2j * np.pi * 9 * np.arange(n) / n)
+    got = D.dft_at(atom, [9, 10])
+    np.testing.assert_allclose(got, [n, 0], atol=1e-11)
+    rng = np.random.default_rng(4)
+    y = rng.standard_normal((2, n))
+    np.testing.assert_allclose(D.dft_at(y, range(n)), D.dft(y), atol=1e-11)
