@@ -107,6 +107,8 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.rows: list[list[str]] = []
+        self.stamps: list[float] = []
+        self.t_start = 0.0
         self.proc = None
 
     def __enter__(self):
@@ -117,6 +119,10 @@ class ClockSampler:
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            # let nvidia-smi start sampling before the timed region begins
+            t0 = time.perf_counter()
+            while not self.rows and time.perf_counter() - t0 < 3.0 and self.proc.poll() is None:
+                time.sleep(0.02)
         except (OSError, FileNotFoundError):
             self.proc = None
         return self
@@ -125,7 +131,12 @@ class ClockSampler:
         for line in self.proc.stdout:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) >= 8:
+                self.stamps.append(time.perf_counter())
                 self.rows.append(parts)
+
+    def mark(self):
+        """Start of the timed region: samples before it (idle clocks) are not summarised."""
+        self.t_start = time.perf_counter()
 
     def __exit__(self, *exc):
         if self.proc is not None:
@@ -137,8 +148,10 @@ class ClockSampler:
         return False
 
     def summary(self) -> dict:
-        if not self.rows:
+        rows = [r for r, t in zip(self.rows, self.stamps) if t >= self.t_start]
+        if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.rows = rows
         sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
         mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -224,6 +237,28 @@ def reference_arm(args, pr: synth.Problem, rank: int) -> None:
     print(json.dumps(line), flush=True)
 
 
+def reference_mix_arm(args) -> None:
+    """The oracle on the uneven batch: each step a bounded sample over all operators."""
+    mx = synth.batch_mix(256, 4)
+    steps = []
+    last = None
+    per_step = max(1.0, min(args.ref_seconds, 150.0 / max(1, args.steps)))
+    for s in range(args.steps):
+        last = oracle_mix_rate(mx, target_s=per_step, seed=100 + s)
+        steps.append(last["value"])
+    value = statistics.median(steps)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * len(mx.op_of) / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": mx.name},
+        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1,
+                         "sample": last["sample"] if last else ""},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
 # ------------------------------------------------------------ rank combining
 
 def max_over_ranks(value_ms: float, dist=None, device=None) -> float:
@@ -260,6 +295,11 @@ def gpu_arm(args, pr: synth.Problem, rank: int, world: int) -> None:
     h = torch.from_numpy(pr.h).to(dev)
     u = torch.from_numpy(pr.u).to(dev)
     plan = Plan(w, h=h)
+    tuning = None
+    if args.autotune:
+        chunk, variant, ms = plan.autotune(pr.batch)
+        tuning = {"chunk": chunk, "column_variant": variant, "ms_per_apply": ms,
+                  "candidates": plan.tuning_log()}
     m, boxes, scratch = plan.info()
     del w, h
     y = torch.empty_like(u)
@@ -287,6 +327,7 @@ def gpu_arm(args, pr: synth.Problem, rank: int, world: int) -> None:
     sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     if sampler:
         sampler.__enter__()
+        sampler.mark()
     wall0 = time.perf_counter()
     for i in range(args.steps):
         flush.zero_()
@@ -331,6 +372,25 @@ def gpu_arm(args, pr: synth.Problem, rank: int, world: int) -> None:
                       "ms_per_step": cms / args.steps,
                       "launches_per_step": plain.launch_count(False, B) + plain.launch_count(True, B)}
         plain.close()
+
+    # the same step as one CUDA-graph launch of a two-lane batch (forward and
+    # adjoint concurrently, each lane with its own scratch)
+    from paper_1604_04374_gb300 import Batch
+    x2 = torch.empty_like(u)
+    y2 = torch.empty_like(u)
+    pair = Batch([(plan, u, y2, False), (plan, u, x2, True)], lanes=2)
+    for _ in range(args.warmup):
+        pair.launch()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.zero_()
+        starts[i].record(stream)
+        pair.launch()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    pair_ms = max_over_ranks(sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)), dist, dev)
+    pair.close()
+    del x2, y2
 
     # end to end: pinned host input -> device -> forward + adjoint -> host outputs
     u_host = torch.from_numpy(pr.u).pin_memory()
@@ -406,6 +466,10 @@ def gpu_arm(args, pr: synth.Problem, rank: int, world: int) -> None:
                          "frac": pbytes * args.steps / (dev_ms / 1000.0) / 1e9 / hbm_peak},
             "kernels": kernels,
             "comparator": dict(comparator, speedup=value / comparator["value"]) if comparator else None,
+            "fwd_adj_graph": {"value": weak_scaling_value(B, args.steps, world, pair_ms), "unit": UNIT,
+                              "ms_per_step": pair_ms / args.steps,
+                              "how": "forward and adjoint as one graph launch of a 2-lane pce_batch"},
+            "tuning": tuning,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": B * P * 4,
                     "d2h_bytes_per_step": 2 * B * P * 4},
             "gpu_launches": launches_per_step * args.steps,
@@ -422,10 +486,207 @@ def gpu_arm(args, pr: synth.Problem, rank: int, world: int) -> None:
         dist.destroy_process_group()
 
 
+# ------------------------------------------------------------ uneven batches
+
+BATCH_WORKLOAD = "batch256_mixed"
+
+
+def task_flops(shape, m, boxes) -> float:
+    """Algorithmic FP32 flops of one apply of one right-hand side (the work model above)."""
+    if len(shape) == 1:
+        n = shape[0]
+        fft_r = 2.5 * n * math.log2(n)
+        return m * (fft_r + n + 8 * (n // 2 + 1)) + fft_r
+    ny, nx = shape
+    rows = sum(b[1] for b in boxes)
+    box_px = sum(b[1] * b[3] for b in boxes)
+    nxh1 = nx // 2 + 1
+    return (rows * 2.5 * nx * math.log2(nx) + box_px + (m + 1) * nxh1 * 5.0 * ny * math.log2(ny)
+            + 8.0 * m * ny * nxh1 + ny * 2.5 * nx * math.log2(nx))
+
+
+def task_bytes(shape, m, boxes) -> float:
+    """Algorithmic HBM bytes of one apply of one right-hand side: in, out, hhat, w on its box."""
+    P = int(np.prod(shape))
+    if len(shape) == 1:
+        return 2 * P * 4 + m * (shape[0] // 2 + 1) * 8 + m * P * 4
+    ny, nx = shape
+    return 2 * P * 4 + m * ny * (nx // 2 + 1) * 8 + sum(b[1] * b[3] for b in boxes) * 4
+
+
+def oracle_mix_rate(mx, target_s: float = 12.0, seed: int = 5) -> dict:
+    """FP64 oracle (gather form) timed on sampled outputs of every operator of the mix
+    in both directions; the whole mix's CPU time is extrapolated from the seconds
+    per output of each (operator, direction)."""
+    from oracle import expansion as E
+    rng = np.random.default_rng(seed)
+    per_op = max(0.05, target_s / (2 * len(mx.ops)))
+    sec_per_out = {}
+    sampled = 0
+    spent = 0.0
+    for oi, (shape, m, w, h) in enumerate(mx.ops):
+        u0 = mx.inputs[mx.op_of.index(oi)]
+        for adj in (False, True):
+            fn = E.apply_adjoint_at if adj else E.apply_at
+            count, dt = 8, 0.0
+            while True:
+                pts = np.stack([rng.integers(0, n, count) for n in shape], axis=-1)
+                t0 = time.perf_counter()
+                fn(u0, w, h, pts)
+                dt = time.perf_counter() - t0
+                if dt >= per_op or count >= int(np.prod(shape)):
+                    break
+                count = min(int(np.prod(shape)), count * 4)
+            sec_per_out[(oi, adj)] = dt / count
+            sampled += count
+            spent += dt
+    total = sum(int(np.prod(mx.ops[o][0])) * sec_per_out[(o, a)] for o, a in zip(mx.op_of, mx.adjoint))
+    return {"value": len(mx.op_of) / total, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{sampled} sampled outputs over the {len(mx.ops)} operators x 2 directions of "
+                      f"{mx.name}, FP64 gather form, {spent:.1f} s; whole mix extrapolated per task",
+            "seconds": spent}
+
+
+def batch_arm(args, rank: int, world: int) -> None:
+    """256 uneven tasks (1D 4096/16384/65536, 2D 256^2/512^2/1024^2; m in 4..32;
+    forward or adjoint) per step: one CUDA-graph launch of a lane-scheduled batch."""
+    import torch
+    from paper_1604_04374_gb300 import Batch, Plan, build
+    build.build()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    mx = synth.batch_mix(256, 4)
+    plans = [Plan(torch.from_numpy(w).to(dev), h=torch.from_numpy(h).to(dev)) for _, _, w, h in mx.ops]
+    tuned = []
+    if args.autotune:
+        for p in plans:
+            tuned.append(p.autotune(1))
+    ins = [torch.from_numpy(u).to(dev) for u in mx.inputs]
+    outs = [torch.empty_like(x) for x in ins]
+    tasks = [(plans[mx.op_of[i]], ins[i], outs[i], mx.adjoint[i]) for i in range(len(ins))]
+    batch = Batch(tasks, lanes=args.lanes)
+    lanes, scratch, launches, makespan, _ = batch.info()
+    n_tasks = len(tasks)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    boxes = [p.info()[1] for p in plans]
+    flops = sum(task_flops(mx.ops[o][0], mx.ops[o][1], boxes[o]) for o in mx.op_of)
+    nbytes = sum(task_bytes(mx.ops[o][0], mx.ops[o][1], boxes[o]) for o in mx.op_of)
+
+    def timed(fn, steps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        st = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        en = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for i in range(steps):
+            flush.zero_()
+            st[i].record(stream)
+            fn()
+            en[i].record(stream)
+        torch.cuda.synchronize()
+        return max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(st, en)), dist, dev)
+
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.__enter__()
+        sampler.mark()
+    graph_ms = timed(batch.launch, args.steps)
+    if sampler:
+        sampler.__exit__(None, None, None)
+    eager_ms = timed(batch.run, args.steps)
+
+    def sequential():
+        for p, x, y, adj in tasks:
+            if adj:
+                p.apply_adjoint(x, out=y)
+            else:
+                p.apply(x, out=y)
+
+    seq_ms = timed(sequential, args.steps) if args.comparator else None
+
+    # end to end: every task's input from pinned host memory, the graph, every output back
+    hin = [torch.from_numpy(u).pin_memory() for u in mx.inputs]
+    hout = [torch.empty_like(x).pin_memory() for x in hin]
+
+    def e2e():
+        for a, b in zip(ins, hin):
+            a.copy_(b, non_blocking=True)
+        batch.launch()
+        for a, b in zip(hout, outs):
+            a.copy_(b, non_blocking=True)
+
+    e2e_ms = timed(e2e, max(10, args.steps // 4))
+    e2e_steps = max(10, args.steps // 4)
+    if rank == 0:
+        clocks = sampler.summary() if sampler else {}
+        sm_max = clocks.get("sm_max_mhz") or 2070.0
+        props = torch.cuda.get_device_properties(dev)
+        sms = getattr(props, "multi_processor_count", SM_COUNT_NOMINAL)
+        fp32_peak = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+        peaks = measured_peaks()
+        hbm_peak = peaks.get("hbm_gbs")
+        hbm_src = "measured" if hbm_peak else "fallback"
+        hbm_peak = hbm_peak or 6800.0
+        step_s = graph_ms / args.steps / 1000.0
+        achieved = flops / step_s / 1e12
+        io_bytes = sum(x.numel() * 4 for x in hin)
+        line = {
+            "metric": METRIC, "value": weak_scaling_value(n_tasks / 2, args.steps, world, graph_ms),
+            "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": graph_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": mx.name, "tasks": n_tasks, "operators": len(mx.ops),
+                       "shapes": [list(s) for s in synth.BATCH_SHAPES], "m": list(synth.BATCH_M),
+                       "batch_per_task": 1, "lanes": lanes, "autotuned": bool(args.autotune),
+                       "parallelism": f"replicas x{world}",
+                       "l2": "flushed between timed steps (256 MB write, outside the step events)",
+                       "step": "all tasks (forward or adjoint each) as one CUDA-graph launch"},
+            "roofline": {"kernel": "whole batch", "bound": "alu", "achieved": achieved, "peak": fp32_peak,
+                         "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                         "peak_source": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",
+                         "traffic": None},
+            "path_hbm": {"algorithmic_bytes_per_step": nbytes, "gbs": nbytes / step_s / 1e9,
+                         "peak_gbs": hbm_peak, "peak_source": hbm_src,
+                         "frac": nbytes / step_s / 1e9 / hbm_peak},
+            "eager_lanes": {"value": weak_scaling_value(n_tasks / 2, args.steps, world, eager_ms),
+                            "ms_per_step": eager_ms / args.steps},
+            "comparator": ({"impl": "the same tasks issued one by one (pce_apply / pce_apply_adjoint) "
+                                    "on one stream, no lanes, no graph",
+                            "value": weak_scaling_value(n_tasks / 2, args.steps, world, seq_ms),
+                            "unit": UNIT, "ms_per_step": seq_ms / args.steps,
+                            "speedup": seq_ms / graph_ms} if seq_ms else None),
+            "e2e": {"value": weak_scaling_value(n_tasks / 2, e2e_steps, world, e2e_ms), "unit": UNIT,
+                    "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes},
+            "gpu_launches": launches * args.steps,
+            "clocks": clocks,
+            "scratch_bytes": scratch,
+            "model_makespan_ms": makespan,
+            "tuning": tuned or None,
+        }
+        if args.cpu_baseline:
+            line["cpu_baseline"] = {k: v for k, v in oracle_mix_rate(mx, args.ref_seconds).items()
+                                    if k != "seconds"}
+        print(json.dumps(line), flush=True)
+    batch.close()
+    for p in plans:
+        p.close()
+    if dist:
+        dist.destroy_process_group()
+
+
 def plan_chunk(plan, batch: int) -> int:
     """Right-hand sides per launch: batch / launches-per-direction (2D), batch (1D)."""
     n = plan.launch_count(False, batch)
-    per = 3 if len(plan.shape) == 2 else 1
+    per = 3 if (len(plan.shape) == 2 or plan.shape[0] > 8192) else 1
     chunks = max(1, n // per)
     return math.ceil(batch / chunks)
 
@@ -433,9 +694,11 @@ def plan_chunk(plan, batch: int) -> int:
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="2d_1024_m16_b8", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--workload", default="2d_1024_m16_b8", choices=sorted(synth.WORKLOADS) + [BATCH_WORKLOAD])
+    ap.add_argument("--lanes", type=int, default=16, help="streams of the uneven batch")
+    ap.add_argument("--autotune", action="store_true", help="autotune every plan of the uneven batch")
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--ref-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
@@ -443,12 +706,19 @@ def main():
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.workload == BATCH_WORKLOAD:
+        if args.impl == "reference":
+            if rank == 0:
+                reference_mix_arm(args)
+            return
+        batch_arm(args, rank, world)
+        return
     pr = synth.workload(args.workload)
     if args.impl == "reference":
         reference_arm(args, pr, rank)
         return
-    if args.warmup < 3:
-        args.warmup = 3
     gpu_arm(args, pr, rank, world)
 
 

@@ -277,6 +277,97 @@ pce_status pce_backward(pce_plan_t plan, const float* u, const float* r, float* 
  */
 pce_status pce_apply_noalloc(pce_plan_t plan, const float* u, float* y, int64_t batch, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Batches of applies, CUDA-graph replay and the autotuner.
+ *
+ * The paper applies one operator at a time; serving many small or uneven
+ * operators (other sizes, other m, both directions) at once is this
+ * library's addition.  A task is one pce_apply or pce_apply_adjoint call.
+ * ---------------------------------------------------------------------- */
+typedef struct pce_task {
+    pce_plan_t plan;     /* plan of the operator (not PCE_FLAG_UNFUSED)          */
+    const float* in;     /* device, [batch][shape] float32                       */
+    float* out;          /* device, [batch][shape] float32                       */
+    int64_t batch;       /* right-hand sides, >= 0                               */
+    int adjoint;         /* 0: out = H_m in;  1: out = H_m^* in                  */
+    int reserved;        /* set to 0                                             */
+} pce_task;
+
+typedef struct pce_batch* pce_batch_t;
+
+/*
+ * pce_apply_batch -- run n independent tasks, stream-ordered after the work
+ * already queued on `stream`; work queued on `stream` afterwards runs after
+ * all of them.  Tasks on one plan share its scratch and run in order on one
+ * lane (an internal stream); tasks on different plans run concurrently on up
+ * to 16 lanes, plans assigned longest-first to the least loaded lane (cost =
+ * the autotuned time, else the flop model).  Allocates nothing; the lane
+ * streams are created at the first call on a device (make it outside any
+ * stream capture).  Capturable into a CUDA graph (ThreadLocal or Relaxed
+ * mode).  Errors: PCE_ERR_INVALID for a bad task (NULL plan, host or
+ * overlapping in/out, plans of another device, a task writing memory another
+ * task reads or writes), PCE_ERR_UNSUPPORTED for PCE_FLAG_UNFUSED plans.
+ * Concurrent calls from several host threads are serialised internally.
+ */
+pce_status pce_apply_batch(const pce_task* tasks, int n, void* stream);
+
+/*
+ * pce_batch_create -- a reusable batch of n tasks (copied; the pointers they
+ * hold are bound until pce_batch_destroy).  The tasks are spread over
+ * `lanes` (1..64) streams by the same longest-first rule, task by task, and
+ * every lane owns scratch for its largest task, so tasks of one plan also
+ * run concurrently.  Allocates the lane scratch (pce_batch_info reports it).
+ *   pce_batch_run    -- issue the batch on `stream` (fork onto the lanes,
+ *                       join back), like pce_apply_batch.
+ *   pce_batch_launch -- the same work as one CUDA graph launch on `stream`;
+ *                       the first call captures and instantiates the graph
+ *                       (on an internal stream; it must not be made while
+ *                       `stream` is capturing in global mode).
+ * Results are bitwise those of pce_apply / pce_apply_adjoint run with the
+ * same right-hand sides per launch.  Runs of one batch must not overlap.
+ */
+pce_status pce_batch_create(pce_batch_t* out, const pce_task* tasks, int n, int lanes);
+pce_status pce_batch_run(pce_batch_t batch, void* stream);
+pce_status pce_batch_launch(pce_batch_t batch, void* stream);
+/* lanes, scratch bytes, kernel launches per run, modelled makespan (ms) and,
+ * if lane_of is not NULL, the lane of every task ([n] ints).  Any pointer may
+ * be NULL. */
+pce_status pce_batch_info(pce_batch_t batch, int* lanes, int64_t* scratch_bytes, int64_t* launches,
+                          double* model_makespan_ms, int* lane_of);
+pce_status pce_batch_destroy(pce_batch_t batch);
+
+/*
+ * pce_schedule_lpt -- the lane rule, exposed for tests: tasks by decreasing
+ * cost (ties by index), each to the lane with the least load so far (ties:
+ * lowest lane).  Host only.  lane_of: [n] output; makespan may be NULL.
+ */
+pce_status pce_schedule_lpt(const double* cost, int n, int lanes, int* lane_of, double* makespan);
+
+/*
+ * pce_plan_autotune -- time the plan's applies (forward + adjoint of `batch`
+ * right-hand sides of a fixed pattern, L2 flushed between repetitions, best
+ * of three) for every candidate and keep the fastest:
+ *   - column FFT variant for Ny = 1024: 0 = one-warp 32 x 32 four-step
+ *     (radix 32), 1 = block Stockham (radix 8);
+ *   - right-hand sides per launch: powers of two up to the plan's scratch
+ *     chunk (2D plans and 1D plans above 8192 points).
+ * 1D plans up to 8192 points have nothing to choose and are only timed.  The
+ * result changes no value an apply computes beyond rounding order (the
+ * variants' FFTs round differently).  cache_path (may be NULL): a JSON-lines
+ * file; a line whose key (device, shape, m, flags, support boxes, batch)
+ * matches is used without timing, otherwise the measured choice is
+ * appended.  Allocates and frees temporary buffers and synchronises the
+ * stream.  pce_plan_tuning reads the choice back (ms_per_apply: measured
+ * milliseconds per right-hand side per direction; 0 if never tuned).
+ */
+pce_status pce_plan_autotune(pce_plan_t plan, int64_t batch, const char* cache_path, void* stream);
+pce_status pce_plan_tuning(pce_plan_t plan, int* chunk, int* col_variant, double* ms_per_apply);
+/* Every candidate the last timed pce_plan_autotune measured: writes up to
+ * max_entries (chunk, variant, ms per apply) triples into the arrays (any may
+ * be NULL) and returns how many there were (0 after a cache hit or for NULL). */
+int pce_plan_tuning_log(pce_plan_t plan, int max_entries, int* chunk, int* col_variant,
+                        double* ms_per_apply);
+
 #ifdef __cplusplus
 }
 #endif

@@ -80,8 +80,8 @@ cudaError_t launch_cols_fwd(int ny, dim3 grid, cudaStream_t s, const float2* Z, 
                             bool lowp, int m,
                             const Box* box, int nxh, float2* A, long long a_bstride,
                             const float2* tw, const void* hhT, const float2* tw1024, int* status,
-                            long long wait_limit, int skip_copy) {
-    if (ny == kWarpN) {
+                            long long wait_limit, int skip_copy, bool warp) {
+    if (ny == kWarpN && warp) {
         if (lowp)
             kw_cols_fwd<__half2><<<grid, kWColWarps * 32, kWColSmem, s>>>(
                 Z, z_bstride, z_kstride, static_cast<const __half2*>(hhT), static_cast<const __half2*>(hN),
@@ -116,8 +116,8 @@ cudaError_t launch_cols_adj(int ny, dim3 grid, cudaStream_t s, const float2* V, 
                             const void* hh, const void* hN, const float* hscale, bool lowp, int m,
                             const Box* box, int nxh, float2* Q, long long q_bstride, long long q_kstride,
                             const float2* tw, const void* hhT, const float2* tw1024, int* status,
-                            long long wait_limit, int skip_copy) {
-    if (ny == kWarpN) {
+                            long long wait_limit, int skip_copy, bool warp) {
+    if (ny == kWarpN && warp) {
         if (lowp)
             kw_cols_adj<false, __half2><<<grid, kWColWarps * 32, kWColSmem, s>>>(
                 V, v_bstride, static_cast<const __half2*>(hhT), static_cast<const __half2*>(hN), hscale, m,

@@ -21,12 +21,13 @@
 #include "kernels.cuh"
 #include "launch.h"
 #include "pce.h"
-
-using pce::Box;
+#include "plan.h"
 
 namespace {
-
 thread_local std::string g_err;
+}  // namespace
+
+namespace pce_rt {
 
 pce_status fail(pce_status s, const char* fmt, ...) {
     char buf[512];
@@ -37,6 +38,23 @@ pce_status fail(pce_status s, const char* fmt, ...) {
     g_err = buf;
     return s;
 }
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace pce_rt
+
+namespace {
+
+using pce_rt::fail;
+using pce_rt::is_device_ptr;
 
 #define PCE_CK(call)                                                                       \
     do {                                                                                   \
@@ -50,16 +68,6 @@ constexpr long long kScratchBudget = 1ll << 30;   // bytes of 2D scratch a plan 
 constexpr int kMaxChunk = 64;
 
 bool is_pow2(long long n) { return n > 0 && (n & (n - 1)) == 0; }
-
-bool is_device_ptr(const void* p) {
-    if (!p) return false;
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
 
 // ------------------------------------------------------------ plan kernels
 // Twiddle table of an N-point FFT (layout of pce::FftPlan), from FP64 sincospi.
@@ -390,72 +398,6 @@ pce_status dev_alloc(T** p, size_t count) {
 }
 
 }  // namespace
-
-struct pce_plan {
-    int ndims = 0, ny = 1, nx = 0, m = 0;
-    uint32_t flags = 0;
-    int device = 0;
-    // windows
-    std::vector<Box> box;
-    Box* d_box = nullptr;
-    float* wbox = nullptr;      // 2D: box copies; 1D: dense [m][N]
-    // spectra
-    float2* hh = nullptr;       // 2D [m][ny][nx/2]; 1D packed [m][n/2]
-    float2* hN = nullptr;       // 2D [m][ny]
-    float2* hhT = nullptr;      // 2D, ny = 1024: [m][nx/2][ny] (each column's spectrum contiguous)
-    float2* tw1024 = nullptr;   // four-step twiddles when a transform length is 1024
-    int* d_status = nullptr;    // device status word (bit 0: a bounded wait gave up)
-    // 1D of more than 8192 points: four-step over an l1ny x l1nx view
-    bool l1 = false;
-    int l1ny = 0, l1nx = 0;
-    float2* twN = nullptr;      // W_N^j, j < N
-    float2* hh4 = nullptr;      // [m][l1ny][l1nx]: hhat_k[a + l1ny * b] at (a, b)
-    // reduced storage (PCE_FLAG_LOWP_STORAGE): bfloat16 window copies, half2 spectra / hscale[k]
-    bool lowp = false;
-    void* wbox16 = nullptr;
-    void* hh16 = nullptr;
-    void* hN16 = nullptr;
-    void* hhT16 = nullptr;
-    float* hscale = nullptr;
-    long long wait_limit = 2000000000ll;   // clock cycles a kernel waits on an mbarrier
-    int skip_copy = 0;          // test support: arm barriers without copying
-    // twiddles
-    float2* twx = nullptr;
-    float2* twy = nullptr;
-    // work lists
-    int2* items = nullptr;
-    int nitems = 0;
-    int* kptr = nullptr;
-    int* klist = nullptr;
-    // scratch
-    float2* scrZ = nullptr;
-    float2* scrA = nullptr;
-    int nrmax = 0;
-    int bchunk = 1;
-    long long zalloc = 0;   // Z scratch per right-hand side (float2)
-    long long scratch_bytes = 0;
-    // per-kernel timing
-    bool timing = false;
-    std::vector<cudaEvent_t> ev;          // pairs (start, stop)
-    std::vector<int> ev_kind;
-    size_t ev_used = 0;
-
-    void drop_events() {
-        for (cudaEvent_t e : ev) cudaEventDestroy(e);
-        ev.clear();
-        ev_kind.clear();
-        ev_used = 0;
-    }
-
-    ~pce_plan() {
-        drop_events();
-        void* ptrs[] = {d_box,  wbox,  hh,     hN,   hhT,   tw1024, d_status, twx, twy == twx ? nullptr : twy,
-                        items,  kptr,  klist,  scrZ, scrA,  wbox16, hh16,     hN16, hhT16, hscale,
-                        twN,    hh4};
-        for (void* p : ptrs)
-            if (p) cudaFree(p);
-    }
-};
 
 namespace {
 
@@ -855,12 +797,53 @@ pce_status check_io(pce_plan_t p, const float* in, const float* out, int64_t bat
     return PCE_OK;
 }
 
+// Z/Q and A/V float2 per right-hand side of the plan's apply.
+void scratch_strides(const pce_plan* p, long long& zs, long long& as) {
+    if (p->l1) {
+        zs = (long long)((p->m + 1) / 2) * p->nx;
+        as = p->nx;
+    } else if (p->ndims == 1) {
+        zs = 0;
+        as = 0;
+    } else {
+        zs = p->zalloc;
+        as = (long long)p->ny * (p->nx / 2);
+    }
+}
+
+pce_rt::Scratch own_scratch(const pce_plan* p) {
+    pce_rt::Scratch r;
+    r.Z = p->scrZ;
+    r.A = p->scrA;
+    scratch_strides(p, r.zstride, r.astride);
+    r.chunk = p->run_chunk > 0 ? std::min(p->run_chunk, p->bchunk) : p->bchunk;
+    return r;
+}
+
 constexpr size_t kMaxTimed = 65536;
+
+// Timing events are recorded only while an apply allows them (not under
+// stream capture, not for the batch scheduler's lanes).
+thread_local bool g_timing_ok = true;
+struct TimingScope {
+    bool saved;
+    explicit TimingScope(bool ok) : saved(g_timing_ok) { g_timing_ok = ok; }
+    ~TimingScope() { g_timing_ok = saved; }
+};
+
+bool stream_capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return cs != cudaStreamCaptureStatusNone;
+}
 
 // Run one launch, bracketed by events when the plan records timings.
 template <class F>
 cudaError_t timed(pce_plan_t p, int kind, cudaStream_t s, F&& launch) {
-    if (!p->timing || p->ev_used >= 2 * kMaxTimed) return launch();
+    if (!p->timing || !g_timing_ok || p->ev_used >= 2 * kMaxTimed) return launch();
     if (p->ev_used + 2 > p->ev.size()) {
         for (int i = 0; i < 64; ++i) {
             cudaEvent_t e;
@@ -985,7 +968,8 @@ pce_status apply_plain(pce_plan_t p, const float* in, float* out, int64_t batch,
 }
 
 pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, bool adjoint,
-                      cudaStream_t s) {
+                      cudaStream_t s, const pce_rt::Scratch& scr, bool allow_timing = true) {
+    TimingScope ts(allow_timing && !stream_capturing(s));
     const int ny = p->ny, nx = p->nx, m = p->m, nxh = nx / 2;
     const long long P = (long long)ny * nx;
     const float scale = 1.0f / (float)P;
@@ -997,37 +981,37 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
         const int tiles = (NX + cpc - 1) / cpc;
         const int it = pce::l1_row_items(NX);
         const int kind = adjoint ? PCE_KERNEL_ADJ_1D : PCE_KERNEL_FWD_1D;
-        for (long long b0 = 0; b0 < batch && e == cudaSuccess; b0 += p->bchunk) {
-            const int nb = (int)std::min<long long>(p->bchunk, batch - b0);
+        for (long long b0 = 0; b0 < batch && e == cudaSuccess; b0 += scr.chunk) {
+            const int nb = (int)std::min<long long>(scr.chunk, batch - b0);
             const float* src = in + b0 * P;
             float* dst = out + b0 * P;
             if (!adjoint) {
                 e = timed(p, kind, s, [&] {
                     return pce::launch_l1_cols(NY, 0 /*window*/, dim3(npairs, nb, tiles), s, src, P, p->wbox, m, NX,
-                                               p->twN, p->scrZ, p->twy);
+                                               p->twN, scr.Z, p->twy);
                 });
                 if (e == cudaSuccess)
                     e = timed(p, kind, s, [&] {
-                        return pce::launch_l1_rows_fwd(NX, dim3((NY / 2 + 1 + it - 1) / it, nb), s, p->scrZ, npairs,
-                                                       p->hh4, m, NY, p->twN, p->scrA, p->twx);
+                        return pce::launch_l1_rows_fwd(NX, dim3((NY / 2 + 1 + it - 1) / it, nb), s, scr.Z, npairs,
+                                                       p->hh4, m, NY, p->twN, scr.A, p->twx);
                     });
                 if (e == cudaSuccess)
                     e = timed(p, kind, s, [&] {
-                        return pce::launch_l1_cols_inv(NY, dim3(nb, tiles), s, p->scrA, NX, dst, scale, p->twy);
+                        return pce::launch_l1_cols_inv(NY, dim3(nb, tiles), s, scr.A, NX, dst, scale, p->twy);
                     });
             } else {
                 e = timed(p, kind, s, [&] {
                     return pce::launch_l1_cols(NY, 2 /*one*/, dim3(1, nb, tiles), s, src, P, nullptr, m, NX, p->twN,
-                                               p->scrA, p->twy);
+                                               scr.A, p->twy);
                 });
                 if (e == cudaSuccess)
                     e = timed(p, kind, s, [&] {
-                        return pce::launch_l1_rows_adj(NX, dim3((NY + 2 * it - 1) / (2 * it), nb), s, p->scrA,
-                                                       npairs, p->hh4, m, NY, p->twN, p->scrZ, p->twx);
+                        return pce::launch_l1_rows_adj(NX, dim3((NY + 2 * it - 1) / (2 * it), nb), s, scr.A,
+                                                       npairs, p->hh4, m, NY, p->twN, scr.Z, p->twx);
                     });
                 if (e == cudaSuccess)
                     e = timed(p, kind, s, [&] {
-                        return pce::launch_l1_cols_adj(NY, dim3(nb, tiles), s, p->scrZ, npairs, p->wbox, m, NX, dst,
+                        return pce::launch_l1_cols_adj(NY, dim3(nb, tiles), s, scr.Z, npairs, p->wbox, m, NX, dst,
                                                        scale, p->twy);
                     });
             }
@@ -1045,47 +1029,48 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
         return PCE_OK;
     }
     if (p->flags & PCE_FLAG_UNFUSED) return apply_plain(p, in, out, batch, adjoint, s);
+    const bool warp = p->col_variant == 0;
     const long long zk = (long long)p->nrmax * nxh;
-    const long long zb = (long long)p->zalloc;
-    const long long ab = (long long)ny * nxh;
+    const long long zb = scr.zstride;
+    const long long ab = scr.astride;
     const int fpc = pce::rows_pairs_per_cta(nx);
-    const int cpc = pce::cols_columns_per_cta(ny);
+    const int cpc = pce::cols_columns_per_cta(ny);  // same for both variants
     const int npairs = (ny + 1) / 2;
-    for (long long b0 = 0; b0 < batch && e == cudaSuccess; b0 += p->bchunk) {
-        const int nb = (int)std::min<long long>(p->bchunk, batch - b0);
+    for (long long b0 = 0; b0 < batch && e == cudaSuccess; b0 += scr.chunk) {
+        const int nb = (int)std::min<long long>(scr.chunk, batch - b0);
         const float* src = in + b0 * P;
         float* dst = out + b0 * P;
         if (!adjoint) {
             if (p->nitems > 0)
                 e = timed(p, PCE_KERNEL_ROWS_R2C_WINDOW, s, [&] {
                     return pce::launch_rows_r2c(nx, true, dim3(r2c_blocks(p->nitems, nx), nb), s, src,
-                                                P, ny, wstore(p), p->lowp, p->d_box, p->items, p->nitems, p->scrZ,
+                                                P, ny, wstore(p), p->lowp, p->d_box, p->items, p->nitems, scr.Z,
                                                 zb, zk, p->twx, p->tw1024);
                 });
             if (e == cudaSuccess)
                 e = timed(p, PCE_KERNEL_COLS_FWD, s, [&] {
-                    return pce::launch_cols_fwd(ny, dim3(nb, (nxh + cpc - 1) / cpc), s, p->scrZ, zb, zk,
-                                                hstore(p), hNstore(p), p->hscale, p->lowp, m, p->d_box, nxh, p->scrA, ab, p->twy, hTstore(p), p->tw1024, p->d_status, p->wait_limit, p->skip_copy);
+                    return pce::launch_cols_fwd(ny, dim3(nb, (nxh + cpc - 1) / cpc), s, scr.Z, zb, zk,
+                                                hstore(p), hNstore(p), p->hscale, p->lowp, m, p->d_box, nxh, scr.A, ab, p->twy, hTstore(p), p->tw1024, p->d_status, p->wait_limit, p->skip_copy, warp);
                 });
             if (e == cudaSuccess)
                 e = timed(p, PCE_KERNEL_ROWS_C2R, s, [&] {
-                    return pce::launch_rows_c2r(nx, dim3((npairs + fpc - 1) / fpc, nb), s, p->scrA, ab,
+                    return pce::launch_rows_c2r(nx, dim3((npairs + fpc - 1) / fpc, nb), s, scr.A, ab,
                                                 ny, dst, P, scale, p->twx, p->tw1024);
                 });
         } else {
             e = timed(p, PCE_KERNEL_ROWS_R2C, s, [&] {
                 return pce::launch_rows_r2c(nx, false, dim3(r2c_blocks(npairs, nx), nb), s, src, P,
-                                            ny, nullptr, false, nullptr, nullptr, npairs, p->scrA, ab, 0,
+                                            ny, nullptr, false, nullptr, nullptr, npairs, scr.A, ab, 0,
                                             p->twx, p->tw1024);
             });
             if (e == cudaSuccess)
                 e = timed(p, PCE_KERNEL_COLS_ADJ, s, [&] {
-                    return pce::launch_cols_adj(ny, dim3(nb, (nxh + cpc - 1) / cpc), s, p->scrA, ab,
-                                                hstore(p), hNstore(p), p->hscale, p->lowp, m, p->d_box, nxh, p->scrZ, zb, zk, p->twy, hTstore(p), p->tw1024, p->d_status, p->wait_limit, p->skip_copy);
+                    return pce::launch_cols_adj(ny, dim3(nb, (nxh + cpc - 1) / cpc), s, scr.A, ab,
+                                                hstore(p), hNstore(p), p->hscale, p->lowp, m, p->d_box, nxh, scr.Z, zb, zk, p->twy, hTstore(p), p->tw1024, p->d_status, p->wait_limit, p->skip_copy, warp);
                 });
             if (e == cudaSuccess)
                 e = timed(p, PCE_KERNEL_ROWS_ADJ, s, [&] {
-                    return pce::launch_rows_adj(nx, dim3((npairs + fpc - 1) / fpc, nb), s, p->scrZ, zb,
+                    return pce::launch_rows_adj(nx, dim3((npairs + fpc - 1) / fpc, nb), s, scr.Z, zb,
                                                 zk, ny, wstore(p), p->lowp, p->d_box, p->kptr, p->klist, dst, P,
                                                 scale, p->twx, p->tw1024);
                 });
@@ -1115,7 +1100,7 @@ pce_status pce_apply(pce_plan_t plan, const float* u, float* y, int64_t batch, v
     if (st) return st;
     if ((st = check_io(plan, u, y, batch))) return st;
     if (batch == 0) return PCE_OK;
-    return apply_impl(plan, u, y, batch, false, static_cast<cudaStream_t>(stream));
+    return apply_impl(plan, u, y, batch, false, static_cast<cudaStream_t>(stream), own_scratch(plan));
 }
 
 pce_status pce_apply_adjoint(pce_plan_t plan, const float* v, float* x, int64_t batch,
@@ -1124,7 +1109,7 @@ pce_status pce_apply_adjoint(pce_plan_t plan, const float* v, float* x, int64_t 
     if (st) return st;
     if ((st = check_io(plan, v, x, batch))) return st;
     if (batch == 0) return PCE_OK;
-    return apply_impl(plan, v, x, batch, true, static_cast<cudaStream_t>(stream));
+    return apply_impl(plan, v, x, batch, true, static_cast<cudaStream_t>(stream), own_scratch(plan));
 }
 
 pce_status pce_plan_info(pce_plan_t plan, int* m_out, int* box_out, int64_t* scratch_bytes_out) {
@@ -1299,7 +1284,7 @@ extern "C" pce_status pce_backward(pce_plan_t p, const float* u, const float* r,
                     (long long)need);
     if (du) {
         if ((st = check_io(p, r, du, batch))) return st;
-        if ((st = apply_impl(p, r, du, batch, true, s))) return st;
+        if ((st = apply_impl(p, r, du, batch, true, s, own_scratch(p)))) return st;
     }
     if (!dw && !dhhat) return PCE_OK;
     const float scale = 1.0f / (float)P;
@@ -1444,7 +1429,7 @@ extern "C" pce_status pce_apply_noalloc(pce_plan_t plan, const float* u, float* 
             e = pce::launch_cols_fwd(ny, dim3(nb, (nxh + cpc - 1) / cpc), s, scrZ, zb, zk, hstore(plan),
                                      hNstore(plan), plan->hscale, plan->lowp, m, plan->d_box, nxh, scrA, ab,
                                      plan->twy, hTstore(plan), plan->tw1024, plan->d_status, plan->wait_limit,
-                                     plan->skip_copy);
+                                     plan->skip_copy, plan->col_variant == 0);
         if (e == cudaSuccess)
             e = pce::launch_rows_c2r(nx, dim3((npairs + fpc - 1) / fpc, nb), s, scrA, ab, ny, y + b0 * P, P,
                                      scale, plan->twx, plan->tw1024);
@@ -1452,3 +1437,45 @@ extern "C" pce_status pce_apply_noalloc(pce_plan_t plan, const float* u, float* 
     if (e) return fail(PCE_ERR_CUDA, "pce_apply_noalloc launch: %s", cudaGetErrorString(e));
     return PCE_OK;
 }
+
+// ----- runtime calls shared with the batch scheduler and the autotuner
+namespace pce_rt {
+
+pce_status check_io(pce_plan_t p, const float* in, const float* out, int64_t batch) {
+    return ::check_io(p, in, out, batch);
+}
+
+Scratch plan_scratch(const pce_plan* p) { return own_scratch(p); }
+
+void scratch_per_rhs(const pce_plan* p, long long& zstride, long long& astride) {
+    scratch_strides(p, zstride, astride);
+}
+
+pce_status apply_with(pce_plan_t p, const float* in, float* out, int64_t batch, bool adjoint,
+                      cudaStream_t s, const Scratch& scr, bool allow_timing) {
+    return apply_impl(p, in, out, batch, adjoint, s, scr, allow_timing);
+}
+
+// Algorithmic FP32 flops of one apply: 5 n log2 n per complex FFT of n points
+// (2.5 n log2 n for a real one), 8 flops per complex product-accumulate, one
+// multiply per window sample.
+double model_flops(const pce_plan* p, int64_t batch) {
+    auto lg = [](double n) { return std::log2(n); };
+    const double m = p->m;
+    if (p->ndims == 1) {
+        const double n = p->nx;
+        return (double)batch * ((m + 1.0) * 2.5 * n * lg(n) + 8.0 * m * (n / 2 + 1) + m * n);
+    }
+    const double ny = p->ny, nx = p->nx, nxh1 = nx / 2 + 1;
+    double rows = 0.0, win = 0.0;
+    for (const Box& b : p->box) {
+        rows += (double)b.nr * 2.5 * nx * lg(nx);
+        win += (double)b.nr * b.nc;
+    }
+    const double cols = (m + 1.0) * nxh1 * 5.0 * ny * lg(ny);
+    const double mac = 8.0 * m * ny * nxh1;
+    const double inv = ny * 2.5 * nx * lg(nx);
+    return (double)batch * (rows + win + cols + mac + inv);
+}
+
+}  // namespace pce_rt

@@ -1,0 +1,113 @@
+// plan.h -- the plan object and the runtime calls shared by the C ABI
+// (pce_api.cu) and the batch scheduler / autotuner (batch.cu).  Internal:
+// not part of include/pce.h.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "kernels.cuh"
+#include "pce.h"
+
+using pce::Box;
+
+struct pce_plan {
+    int ndims = 0, ny = 1, nx = 0, m = 0;
+    uint32_t flags = 0;
+    int device = 0;
+    // windows
+    std::vector<Box> box;
+    Box* d_box = nullptr;
+    float* wbox = nullptr;      // 2D: box copies; 1D: dense [m][N]
+    // spectra
+    float2* hh = nullptr;       // 2D [m][ny][nx/2]; 1D packed [m][n/2]
+    float2* hN = nullptr;       // 2D [m][ny]
+    float2* hhT = nullptr;      // 2D, ny = 1024: [m][nx/2][ny] (each column's spectrum contiguous)
+    float2* tw1024 = nullptr;   // four-step twiddles when a transform length is 1024
+    int* d_status = nullptr;    // device status word (bit 0: a bounded wait gave up)
+    // 1D of more than 8192 points: four-step over an l1ny x l1nx view
+    bool l1 = false;
+    int l1ny = 0, l1nx = 0;
+    float2* twN = nullptr;      // W_N^j, j < N
+    float2* hh4 = nullptr;      // [m][l1ny][l1nx]: hhat_k[a + l1ny * b] at (a, b)
+    // reduced storage (PCE_FLAG_LOWP_STORAGE): bfloat16 window copies, half2 spectra / hscale[k]
+    bool lowp = false;
+    void* wbox16 = nullptr;
+    void* hh16 = nullptr;
+    void* hN16 = nullptr;
+    void* hhT16 = nullptr;
+    float* hscale = nullptr;
+    long long wait_limit = 2000000000ll;   // clock cycles a kernel waits on an mbarrier
+    int skip_copy = 0;          // test support: arm barriers without copying
+    // twiddles
+    float2* twx = nullptr;
+    float2* twy = nullptr;
+    // work lists
+    int2* items = nullptr;
+    int nitems = 0;
+    int* kptr = nullptr;
+    int* klist = nullptr;
+    // scratch
+    float2* scrZ = nullptr;
+    float2* scrA = nullptr;
+    int nrmax = 0;
+    int bchunk = 1;             // right-hand sides the plan's scratch holds
+    // autotuned choices (pce_plan_autotune): 0 = default
+    int run_chunk = 0;          // right-hand sides per launch, <= bchunk
+    int col_variant = 0;        // columns of 1024: 0 one-warp four-step, 1 radix-8 Stockham
+    double tuned_ms = 0.0;      // measured ms per right-hand side (forward + adjoint) / 2
+    std::vector<double> tune_log;   // (chunk, variant, ms per apply) of every timed candidate
+    long long zalloc = 0;   // Z scratch per right-hand side (float2)
+    long long scratch_bytes = 0;
+    // per-kernel timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;          // pairs (start, stop)
+    std::vector<int> ev_kind;
+    size_t ev_used = 0;
+
+    void drop_events() {
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        ev.clear();
+        ev_kind.clear();
+        ev_used = 0;
+    }
+
+    ~pce_plan() {
+        drop_events();
+        void* ptrs[] = {d_box,  wbox,  hh,     hN,   hhT,   tw1024, d_status, twx, twy == twx ? nullptr : twy,
+                        items,  kptr,  klist,  scrZ, scrA,  wbox16, hh16,     hN16, hhT16, hscale,
+                        twN,    hh4};
+        for (void* q : ptrs)
+            if (q) cudaFree(q);
+    }
+};
+
+namespace pce_rt {
+
+// Scratch an apply runs on: Z/Q (per right-hand side zstride float2) and A/V
+// (astride float2), room for `chunk` right-hand sides.
+struct Scratch {
+    float2* Z = nullptr;
+    float2* A = nullptr;
+    long long zstride = 0;
+    long long astride = 0;
+    int chunk = 1;
+};
+
+pce_status fail(pce_status s, const char* fmt, ...);
+bool is_device_ptr(const void* p);
+pce_status check_io(pce_plan_t p, const float* in, const float* out, int64_t batch);
+// The plan's own scratch (with the tuned chunk).
+Scratch plan_scratch(const pce_plan* p);
+// float2 of Z/Q and A/V one right-hand side needs (0, 0 for 1D sizes <= 8192).
+void scratch_per_rhs(const pce_plan* p, long long& zstride, long long& astride);
+// Launch one apply (all chunks) on s with the given scratch; timing events
+// only when allowed and s is not capturing.
+pce_status apply_with(pce_plan_t p, const float* in, float* out, int64_t batch, bool adjoint,
+                      cudaStream_t s, const Scratch& scr, bool allow_timing);
+// Algorithmic FP32 flops of one apply of `batch` right-hand sides.
+double model_flops(const pce_plan* p, int64_t batch);
+
+}  // namespace pce_rt

@@ -154,6 +154,10 @@ kw_cols_fwd(const float2* __restrict__ Z, long long z_bstride, long long z_kstri
             if (!mbar_wait(bar, parity, wait_limit)) {
                 failed = true;
                 if (lane == 0) atomicOr(status, kStatusTimeout);
+                // a copy may still be in flight into the tile: wait for it once
+                // more (bounded) before the tile is reused; no further copies
+                // are issued and the products are skipped from here on
+                mbar_wait(bar, parity, wait_limit);
             }
             parity ^= 1;
         }
@@ -239,6 +243,10 @@ kw_cols_adj(const float2* __restrict__ V, long long v_bstride,
             if (!mbar_wait(bar, parity, wait_limit)) {
                 failed = true;
                 if (lane == 0) atomicOr(status, kStatusTimeout);
+                // a copy may still be in flight into the tile: wait for it once
+                // more (bounded) before the tile is reused; no further copies
+                // are issued and the products are skipped from here on
+                mbar_wait(bar, parity, wait_limit);
             }
             parity ^= 1;
         }

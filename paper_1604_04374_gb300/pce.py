@@ -22,6 +22,21 @@ STATUS_NAMES = {0: "PCE_OK", 1: "PCE_ERR_INVALID", 2: "PCE_ERR_UNSUPPORTED", 3: 
 _lib = None
 
 
+class PceTask(ctypes.Structure):
+    """struct pce_task of include/pce.h."""
+    _fields_ = [("plan", ctypes.c_void_p), ("in_", ctypes.c_void_p), ("out", ctypes.c_void_p),
+                ("batch", ctypes.c_int64), ("adjoint", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+
+def _task_array(tasks):
+    """tasks: iterable of (plan handle, in ptr, out ptr, batch, adjoint)."""
+    tasks = list(tasks)
+    arr = (PceTask * max(1, len(tasks)))()
+    for i, (plan, ip, op, b, adj) in enumerate(tasks):
+        arr[i] = PceTask(plan, ip, op, b, 1 if adj else 0, 0)
+    return arr, len(tasks)
+
+
 class PceError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -65,9 +80,27 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.pce_plan_set_timing.argtypes = [P, ctypes.c_int]
     lib.pce_plan_timing.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                     ctypes.POINTER(i64)]
+    TP = ctypes.POINTER(PceTask)
+    lib.pce_apply_batch.argtypes = [TP, ctypes.c_int, P]
+    lib.pce_batch_create.argtypes = [ctypes.POINTER(P), TP, ctypes.c_int, ctypes.c_int]
+    lib.pce_batch_run.argtypes = [P, P]
+    lib.pce_batch_launch.argtypes = [P, P]
+    lib.pce_batch_info.argtypes = [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                   ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
+    lib.pce_batch_destroy.argtypes = [P]
+    lib.pce_schedule_lpt.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_int,
+                                     ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+    lib.pce_plan_autotune.argtypes = [P, i64, ctypes.c_char_p, P]
+    lib.pce_plan_tuning.argtypes = [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_double)]
+    lib.pce_plan_tuning_log.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+    lib.pce_plan_tuning_log.restype = ctypes.c_int
     for name in ("pce_plan_create", "pce_plan_create_from_spectra", "pce_apply", "pce_apply_adjoint",
                  "pce_plan_info", "pce_plan_hhat", "pce_plan_destroy", "pce_plan_set_timing",
-                 "pce_plan_timing"):
+                 "pce_plan_timing", "pce_apply_batch", "pce_batch_create", "pce_batch_run",
+                 "pce_batch_launch", "pce_batch_info", "pce_batch_destroy", "pce_schedule_lpt",
+                 "pce_plan_autotune", "pce_plan_tuning"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -152,6 +185,77 @@ def pce_plan_destroy(plan: int) -> None:
 
 def pce_launch_count(plan: int, adjoint: bool, batch: int) -> int:
     return int(load_library().pce_launch_count(plan, 1 if adjoint else 0, batch))
+
+
+def pce_apply_batch(tasks, stream: int = 0) -> None:
+    arr, n = _task_array(tasks)
+    _check(load_library().pce_apply_batch(arr, n, stream))
+
+
+def pce_batch_create(tasks, lanes: int) -> int:
+    arr, n = _task_array(tasks)
+    handle = ctypes.c_void_p()
+    _check(load_library().pce_batch_create(ctypes.byref(handle), arr, n, lanes))
+    return handle.value
+
+
+def pce_batch_run(batch: int, stream: int = 0) -> None:
+    _check(load_library().pce_batch_run(batch, stream))
+
+
+def pce_batch_launch(batch: int, stream: int = 0) -> None:
+    _check(load_library().pce_batch_launch(batch, stream))
+
+
+def pce_batch_info(batch: int, n: int):
+    """(lanes, scratch bytes, launches per run, modelled makespan ms, [lane of each task])."""
+    lanes = ctypes.c_int()
+    scratch = ctypes.c_int64()
+    launches = ctypes.c_int64()
+    ms = ctypes.c_double()
+    lane_of = (ctypes.c_int * max(1, n))()
+    _check(load_library().pce_batch_info(batch, ctypes.byref(lanes), ctypes.byref(scratch),
+                                         ctypes.byref(launches), ctypes.byref(ms), lane_of))
+    return lanes.value, scratch.value, launches.value, ms.value, list(lane_of)[:n]
+
+
+def pce_batch_destroy(batch: int) -> None:
+    _check(load_library().pce_batch_destroy(batch))
+
+
+def pce_schedule_lpt(cost, lanes: int):
+    """(lane of every task, makespan) under the longest-processing-time-first rule."""
+    n = len(cost)
+    c = (ctypes.c_double * max(1, n))(*cost)
+    out = (ctypes.c_int * max(1, n))()
+    ms = ctypes.c_double()
+    _check(load_library().pce_schedule_lpt(c, n, lanes, out, ctypes.byref(ms)))
+    return list(out)[:n], ms.value
+
+
+def pce_plan_autotune(plan: int, batch: int, cache_path: str | None = None, stream: int = 0) -> None:
+    path = cache_path.encode() if cache_path else None
+    _check(load_library().pce_plan_autotune(plan, batch, path, stream))
+
+
+def pce_plan_tuning(plan: int):
+    """(right-hand sides per launch, column variant, measured ms per apply)."""
+    c = ctypes.c_int()
+    v = ctypes.c_int()
+    ms = ctypes.c_double()
+    _check(load_library().pce_plan_tuning(plan, ctypes.byref(c), ctypes.byref(v), ctypes.byref(ms)))
+    return c.value, v.value, ms.value
+
+
+def pce_plan_tuning_log(plan: int):
+    """[(chunk, variant, ms per apply)] of every candidate the last autotune timed."""
+    lib = load_library()
+    n = lib.pce_plan_tuning_log(plan, 0, None, None, None)
+    c = (ctypes.c_int * max(1, n))()
+    v = (ctypes.c_int * max(1, n))()
+    ms = (ctypes.c_double * max(1, n))()
+    lib.pce_plan_tuning_log(plan, n, c, v, ms)
+    return [(c[i], v[i], ms[i]) for i in range(n)]
 
 
 KERNEL_KINDS = ("rows_r2c_window", "cols_fwd", "rows_c2r", "rows_r2c", "cols_adj", "rows_adj",
@@ -280,6 +384,19 @@ class Plan:
                      batch, ws.data_ptr(), nbytes, _stream_handle(stream))
         return du, dw, dh
 
+    def autotune(self, batch: int, cache: str | None = None, stream=None):
+        """Pick the column variant and right-hand sides per launch by timing; returns tuning()."""
+        pce_plan_autotune(self.handle, batch, cache, _stream_handle(stream))
+        return self.tuning()
+
+    def tuning(self):
+        """(right-hand sides per launch, column variant, measured ms per apply)."""
+        return pce_plan_tuning(self.handle)
+
+    def tuning_log(self):
+        """[(chunk, variant, ms per apply)] of every candidate the last autotune timed."""
+        return pce_plan_tuning_log(self.handle)
+
     def set_timing(self, enable: bool) -> None:
         pce_plan_set_timing(self.handle, enable)
 
@@ -302,3 +419,52 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class Batch:
+    """A reusable batch of independent applies (pce_batch_*).
+
+    ``tasks``: list of (Plan, input tensor, output tensor, adjoint flag); the
+    tensors are held so that their memory stays valid while the batch lives.
+    """
+
+    def __init__(self, tasks, lanes: int = 16):
+        self._keep = []
+        raw = []
+        for plan, x, y, adj in tasks:
+            batch, y = plan._io(x, y, "in")
+            self._keep.append((plan, x, y))
+            raw.append((plan.handle, x.data_ptr(), y.data_ptr(), batch, adj))
+        self.n = len(raw)
+        self.handle = pce_batch_create(raw, lanes)
+
+    def run(self, stream=None):
+        pce_batch_run(self.handle, _stream_handle(stream))
+
+    def launch(self, stream=None):
+        """Replay the batch as one CUDA graph launch (captured at the first call)."""
+        pce_batch_launch(self.handle, _stream_handle(stream))
+
+    def info(self):
+        return pce_batch_info(self.handle, self.n)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            pce_batch_destroy(self.handle)
+            self.handle = None
+        self._keep = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def apply_batch(tasks, stream=None) -> None:
+    """One-shot batch: tasks = [(Plan, input, output, adjoint flag)] (pce_apply_batch)."""
+    raw = []
+    for plan, x, y, adj in tasks:
+        batch, y = plan._io(x, y, "in")
+        raw.append((plan.handle, x.data_ptr(), y.data_ptr(), batch, adj))
+    pce_apply_batch(raw, _stream_handle(stream))

@@ -194,3 +194,54 @@ WORKLOADS = {
 
 def workload(name: str) -> Problem:
     return WORKLOADS[name]()
+
+
+# ------------------------------------------------------------ uneven batches
+
+BATCH_SHAPES = ((4096,), (16384,), (65536,), (256, 256), (512, 512), (1024, 1024))
+BATCH_M = (4, 8, 16, 32)
+
+
+@dataclass
+class BatchMix:
+    """Uneven tasks: task i applies operator ops[op_of[i]] (forward or adjoint) to inputs[i] (B = 1)."""
+    name: str
+    ops: list            # [(shape, m, w [m,*shape] f32, h [m,*shape] f32)]
+    op_of: list          # [n_tasks] operator index
+    adjoint: list        # [n_tasks] bool
+    inputs: list         # [n_tasks] arrays [1, *shape] f32
+
+
+def batch_operator(shape: tuple, m: int):
+    """(w, h) of one operator of the mix: 1D hats + periodised Gaussians as in the
+    1D workload, 2D tensor hats on node_grid(m) + the anisotropic PSF family."""
+    if len(shape) == 1:
+        pr = problem_1d(shape[0], m, 1, 0)
+        return pr.w, pr.h
+    gy, gx = node_grid(m)
+    w = hat_windows_2d(shape[0], shape[1], gy, gx)
+    h = np.empty((m,) + tuple(shape), dtype=np.float32)
+    for a in range(gy):
+        for c in range(gx):
+            sx, sy, th = psf_params_2d(c / gx, a / gy)
+            h[a * gx + c] = aniso_psf_2d(shape[0], shape[1], sx, sy, th).astype(np.float32)
+    return w, h
+
+
+def batch_mix(n_tasks: int = 256, seed_index: int = 4, shapes=BATCH_SHAPES, ms=BATCH_M) -> BatchMix:
+    """n_tasks tasks with shape, m and direction drawn uniformly from a seed;
+    inputs u ~ N(0,1) in 1D and U[0,1) in 2D, one right-hand side each."""
+    rng = rng_for(seed_index)
+    picks = [(int(rng.integers(len(shapes))), int(rng.integers(len(ms))), bool(rng.integers(2)))
+             for _ in range(n_tasks)]
+    keys = sorted({(s, k) for s, k, _ in picks})
+    index = {key: i for i, key in enumerate(keys)}
+    ops = []
+    for s, k in keys:
+        w, h = batch_operator(shapes[s], ms[k])
+        ops.append((tuple(shapes[s]), ms[k], w, h))
+    op_of = [index[(s, k)] for s, k, _ in picks]
+    adjoint = [a for _, _, a in picks]
+    inputs = [draw(rng, (1,) + tuple(shapes[s]), "normal" if len(shapes[s]) == 1 else "uniform")
+              for s, _, _ in picks]
+    return BatchMix(f"batch{n_tasks}_mixed", ops, op_of, adjoint, inputs)
