@@ -1,4 +1,4 @@
-"""O1/O2/O3/O5: the convolution-product expansion by definition (test infrastructure, FP64).
+"""O1/O2/O3/O5/O6: the convolution-product expansion by definition (test infrastructure, FP64).
 
 Readings (the paper leaves these implicit):
 * Indices are 0-based and periodic: the discrete convolution of Section 3.5,
@@ -69,6 +69,46 @@ def apply_adjoint(v, w, h) -> np.ndarray:
         for d, hv in zip(offs, vals):
             t += hv * np.roll(v, tuple(-int(s) for s in d), axis=axes)
         x += w[k] * t
+    return x
+
+
+def product_convolution(u, w, h) -> np.ndarray:
+    """O6: the product-convolution form P_m u = sum_k w_k . (h_k * u) (Section 1,
+    the kernel K(x, y) = sum_k w_k(x) h_k(x - y): windows on the output side).
+
+    y[b, i] = sum_k w_k[i] sum_d h_k[d] u[b, i - d].
+    """
+    u = np.asarray(u, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    h = np.asarray(h, dtype=np.float64)
+    nd = w.ndim - 1
+    axes = tuple(range(-nd, 0))
+    y = np.zeros_like(u)
+    for k in range(w.shape[0]):
+        t = np.zeros_like(u)
+        offs, vals = _taps(h[k])
+        for d, hv in zip(offs, vals):
+            t += hv * np.roll(u, tuple(int(s) for s in d), axis=axes)
+        y += w[k] * t
+    return y
+
+
+def product_convolution_adjoint(v, w, h) -> np.ndarray:
+    """O6*: P_m^* v = sum_k h~_k * (w_k . v), the transpose of O6.
+
+    x[b, j] = sum_k sum_d h_k[d] w_k[j + d] v[b, j + d].
+    """
+    v = np.asarray(v, dtype=np.float64)
+    w = np.asarray(w, dtype=np.float64)
+    h = np.asarray(h, dtype=np.float64)
+    nd = w.ndim - 1
+    axes = tuple(range(-nd, 0))
+    x = np.zeros_like(v)
+    for k in range(w.shape[0]):
+        z = w[k] * v
+        offs, vals = _taps(h[k])
+        for d, hv in zip(offs, vals):
+            x += hv * np.roll(z, tuple(-int(s) for s in d), axis=axes)
     return x
 
 

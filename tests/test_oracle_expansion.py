@@ -205,3 +205,55 @@ def test_gradients_central_fd(shape):
         scale = np.max(np.abs(dhh))
         assert np.max(np.abs(dhh[..., 0].imag)) < 1e-14 * scale
         assert np.max(np.abs(dhh[..., nx // 2].imag)) < 1e-14 * scale
+
+
+def _dense_product_convolution(w, h):
+    """Matrix of u -> sum_k w_k(x) h_k(x - y) u(y) built entry by entry from the kernel
+    formula of the product-convolution form (Section 1), not from the shift sum."""
+    shape = w.shape[1:]
+    P = int(np.prod(shape))
+    idx = [np.unravel_index(i, shape) for i in range(P)]
+    K = np.zeros((P, P))
+    for a, xi in enumerate(idx):
+        for b, yi in enumerate(idx):
+            d = tuple((xi[t] - yi[t]) % shape[t] for t in range(len(shape)))
+            K[a, b] = sum(w[k][xi] * h[k][d] for k in range(w.shape[0]))
+    return K
+
+
+@pytest.mark.parametrize("shape", [(12,), (4, 6)])
+def test_product_convolution_matches_kernel_matrix(shape):
+    """O6 and its adjoint against the dense kernel K(x, y) = sum_k w_k(x) h_k(x - y) and its transpose."""
+    rng = np.random.default_rng(31)
+    m = 3
+    w = rng.standard_normal((m,) + shape)
+    h = rng.standard_normal((m,) + shape)
+    u = rng.standard_normal((2,) + shape)
+    K = _dense_product_convolution(w, h)
+    P = int(np.prod(shape))
+    got = E.product_convolution(u, w, h).reshape(2, P)
+    np.testing.assert_allclose(got, u.reshape(2, P) @ K.T, rtol=1e-12, atol=1e-12)
+    got = E.product_convolution_adjoint(u, w, h).reshape(2, P)
+    np.testing.assert_allclose(got, u.reshape(2, P) @ K, rtol=1e-12, atol=1e-12)
+
+
+def test_product_convolution_special_cases():
+    """Constant windows commute with the convolution (both forms agree); a single
+    delta h_k = delta_0 gives the pointwise product (sum_k w_k) . u."""
+    rng = np.random.default_rng(32)
+    shape = (16, 8)
+    m = 4
+    c = rng.standard_normal(m)
+    w = np.ones((m,) + shape) * c[:, None, None]
+    h = rng.standard_normal((m,) + shape)
+    u = rng.standard_normal((2,) + shape)
+    np.testing.assert_allclose(E.product_convolution(u, w, h), E.apply(u, w, h), rtol=1e-12, atol=1e-12)
+    w = rng.standard_normal((m,) + shape)
+    h = np.zeros((m,) + shape)
+    h[:, 0, 0] = 1.0
+    np.testing.assert_allclose(E.product_convolution(u, w, h), w.sum(axis=0) * u, rtol=1e-13, atol=1e-13)
+    v = rng.standard_normal((2,) + shape)
+    h = rng.standard_normal((m,) + shape)
+    lhs = np.sum(E.product_convolution(u, w, h) * v)
+    rhs = np.sum(u * E.product_convolution_adjoint(v, w, h))
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
