@@ -297,8 +297,8 @@ def gpu_arm(args, pr: synth.Problem, rank: int, world: int) -> None:
     plan = Plan(w, h=h)
     tuning = None
     if args.autotune:
-        chunk, variant, ms = plan.autotune(pr.batch)
-        tuning = {"chunk": chunk, "column_variant": variant, "ms_per_apply": ms,
+        chunk, variant, rvariant, ms = plan.autotune(pr.batch, args.tuning_cache)
+        tuning = {"chunk": chunk, "column_variant": variant, "row_variant": rvariant, "ms_per_apply": ms,
                   "candidates": plan.tuning_log()}
     m, boxes, scratch = plan.info()
     del w, h
@@ -310,38 +310,51 @@ def gpu_arm(args, pr: synth.Problem, rank: int, world: int) -> None:
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
+    from paper_1604_04374_gb300 import Batch
+
+    def timed_steps(fn, sample_clocks=False, on_start=None):
+        """W untimed steps, then K steps each bracketed by CUDA events on the launching
+        stream (L2 flushed before each, outside the events); max over ranks of the sum."""
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        if on_start:
+            on_start()
+        st = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        en = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        smp = ClockSampler(torch.cuda.current_device()) if (sample_clocks and rank == 0) else None
+        if smp:
+            smp.__enter__()
+            smp.mark()
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.zero_()
+            st[i].record(stream)
+            fn()
+            en[i].record(stream)
+        torch.cuda.synchronize()
+        wall_s = time.perf_counter() - t0
+        if smp:
+            smp.__exit__(None, None, None)
+        ms = max_over_ranks(sum(a_.elapsed_time(b_) for a_, b_ in zip(st, en)), dist, dev)
+        return ms, wall_s, smp
+
+    # headline step: forward and adjoint of the batch as one CUDA-graph launch of a
+    # two-lane pce_batch (the two directions run concurrently, each on its own scratch)
+    pair = Batch([(plan, u, y, False), (plan, u, x, True)], lanes=2)
+    dev_ms, wall, sampler = timed_steps(pair.launch, sample_clocks=True)
+
+    # the same step as two plain calls, with the library's per-kernel events
     def step():
         plan.apply(u, out=y)
         plan.apply_adjoint(u, out=x)
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    plan.set_timing(True)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
-    if sampler:
-        sampler.__enter__()
-        sampler.mark()
-    wall0 = time.perf_counter()
-    for i in range(args.steps):
-        flush.zero_()
-        starts[i].record(stream)
-        step()
-        ends[i].record(stream)
-    torch.cuda.synchronize()
-    wall = time.perf_counter() - wall0
-    if sampler:
-        sampler.__exit__(None, None, None)
+    seq_ms, _, _ = timed_steps(step, on_start=lambda: plan.set_timing(True))
     kern = plan.timing()
     plan.set_timing(False)
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    dev_ms = max_over_ranks(sum(step_ms), dist, dev)
     if dist:
         dist.barrier()
     launches_per_step = plan.launch_count(False, B) + plan.launch_count(True, B)
@@ -356,52 +369,22 @@ def gpu_arm(args, pr: synth.Problem, rank: int, world: int) -> None:
             plain.apply(u, out=y)
             plain.apply_adjoint(u, out=x)
 
-        for _ in range(args.warmup):
-            plain_step()
-        torch.cuda.synchronize()
-        cms = 0.0
-        for i in range(args.steps):
-            flush.zero_()
-            starts[i].record(stream)
-            plain_step()
-            ends[i].record(stream)
-        torch.cuda.synchronize()
-        cms = max_over_ranks(sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)), dist, dev)
+        cms, _, _ = timed_steps(plain_step)
         comparator = {"impl": "plain unfused FP32 per-term pipeline (PCE_FLAG_UNFUSED), same FFT core",
                       "value": weak_scaling_value(B, args.steps, world, cms), "unit": UNIT,
                       "ms_per_step": cms / args.steps,
                       "launches_per_step": plain.launch_count(False, B) + plain.launch_count(True, B)}
         plain.close()
 
-    # the same step as one CUDA-graph launch of a two-lane batch (forward and
-    # adjoint concurrently, each lane with its own scratch)
-    from paper_1604_04374_gb300 import Batch
-    x2 = torch.empty_like(u)
-    y2 = torch.empty_like(u)
-    pair = Batch([(plan, u, y2, False), (plan, u, x2, True)], lanes=2)
-    for _ in range(args.warmup):
-        pair.launch()
-    torch.cuda.synchronize()
-    for i in range(args.steps):
-        flush.zero_()
-        starts[i].record(stream)
-        pair.launch()
-        ends[i].record(stream)
-    torch.cuda.synchronize()
-    pair_ms = max_over_ranks(sum(s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)), dist, dev)
-    pair.close()
-    del x2, y2
-
-    # end to end: pinned host input -> device -> forward + adjoint -> host outputs
+    # end to end through the same batch: pinned host input -> its bound device input,
+    # the graph launch, both outputs back to pinned host memory
     u_host = torch.from_numpy(pr.u).pin_memory()
     y_host = torch.empty_like(u_host).pin_memory()
     x_host = torch.empty_like(u_host).pin_memory()
-    u_dev = torch.empty_like(u)
 
     def e2e_step():
-        u_dev.copy_(u_host, non_blocking=True)
-        plan.apply(u_dev, out=y)
-        plan.apply_adjoint(u_dev, out=x)
+        u.copy_(u_host, non_blocking=True)
+        pair.launch()
         y_host.copy_(y, non_blocking=True)
         x_host.copy_(x, non_blocking=True)
 
@@ -416,6 +399,7 @@ def gpu_arm(args, pr: synth.Problem, rank: int, world: int) -> None:
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+    pair.close()
 
     if rank == 0:
         value = weak_scaling_value(B, args.steps, world, dev_ms)
@@ -458,7 +442,8 @@ def gpu_arm(args, pr: synth.Problem, rank: int, world: int) -> None:
             "config": {"workload": pr.name, "shape": list(pr.shape), "m": pr.m, "batch_per_gpu": B,
                        "global_batch": B * world, "parallelism": f"replicas x{world}",
                        "l2": "flushed between timed steps (256 MB write, outside the step events)",
-                       "step": "forward + adjoint apply of the batch"},
+                       "step": "forward + adjoint apply of the batch, as one CUDA-graph launch "
+                               "of a two-lane pce_batch"},
             "roofline": roof,
             "path_hbm": {"algorithmic_bytes_per_step": pbytes,
                          "gbs": pbytes * args.steps / (dev_ms / 1000.0) / 1e9,
@@ -466,9 +451,10 @@ def gpu_arm(args, pr: synth.Problem, rank: int, world: int) -> None:
                          "frac": pbytes * args.steps / (dev_ms / 1000.0) / 1e9 / hbm_peak},
             "kernels": kernels,
             "comparator": dict(comparator, speedup=value / comparator["value"]) if comparator else None,
-            "fwd_adj_graph": {"value": weak_scaling_value(B, args.steps, world, pair_ms), "unit": UNIT,
-                              "ms_per_step": pair_ms / args.steps,
-                              "how": "forward and adjoint as one graph launch of a 2-lane pce_batch"},
+            "sequential": {"value": weak_scaling_value(B, args.steps, world, seq_ms), "unit": UNIT,
+                           "ms_per_step": seq_ms / args.steps,
+                           "how": "pce_apply then pce_apply_adjoint on one stream; the per-kernel "
+                                  "times and the roofline come from this pass"},
             "tuning": tuning,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": B * P * 4,
                     "d2h_bytes_per_step": 2 * B * P * 4},
@@ -563,13 +549,19 @@ def batch_arm(args, rank: int, world: int) -> None:
     mx = synth.batch_mix(256, 4)
     plans = [Plan(torch.from_numpy(w).to(dev), h=torch.from_numpy(h).to(dev)) for _, _, w, h in mx.ops]
     tuned = []
-    if args.autotune:
+    if args.tune_plans:
         for p in plans:
             tuned.append(p.autotune(1))
     ins = [torch.from_numpy(u).to(dev) for u in mx.inputs]
     outs = [torch.empty_like(x) for x in ins]
     tasks = [(plans[mx.op_of[i]], ins[i], outs[i], mx.adjoint[i]) for i in range(len(ins))]
     batch = Batch(tasks, lanes=args.lanes)
+    batch_tuning = None
+    if args.autotune:
+        (cp, rp), log = batch.autotune()
+        batch_tuning = {"column_policy": cp, "row_policy": rp,
+                        "policies_ms_per_run": [list(t) for t in log],
+                        "policy_meaning": "-1: every plan's own variant; 0/1: that variant for all tasks"}
     lanes, scratch, launches, makespan, _ = batch.info()
     n_tasks = len(tasks)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
@@ -646,7 +638,7 @@ def batch_arm(args, rank: int, world: int) -> None:
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": mx.name, "tasks": n_tasks, "operators": len(mx.ops),
                        "shapes": [list(s) for s in synth.BATCH_SHAPES], "m": list(synth.BATCH_M),
-                       "batch_per_task": 1, "lanes": lanes, "autotuned": bool(args.autotune),
+                       "batch_per_task": 1, "lanes": lanes, "plans_autotuned": bool(args.tune_plans),
                        "parallelism": f"replicas x{world}",
                        "l2": "flushed between timed steps (256 MB write, outside the step events)",
                        "step": "all tasks (forward or adjoint each) as one CUDA-graph launch"},
@@ -671,6 +663,7 @@ def batch_arm(args, rank: int, world: int) -> None:
             "scratch_bytes": scratch,
             "model_makespan_ms": makespan,
             "tuning": tuned or None,
+            "batch_tuning": batch_tuning,
         }
         if args.cpu_baseline:
             line["cpu_baseline"] = {k: v for k, v in oracle_mix_rate(mx, args.ref_seconds).items()
@@ -698,7 +691,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--workload", default="2d_1024_m16_b8", choices=sorted(synth.WORKLOADS) + [BATCH_WORKLOAD])
     ap.add_argument("--lanes", type=int, default=16, help="streams of the uneven batch")
-    ap.add_argument("--autotune", action="store_true", help="autotune every plan of the uneven batch")
+    ap.add_argument("--autotune", dest="autotune", action="store_true", default=True,
+                    help="autotune the plan(s) before timing (default)")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false")
+    ap.add_argument("--tuning-cache", default=None,
+                    help="JSON-lines autotuner cache: reuse earlier choices instead of timing again")
+    ap.add_argument("--tune-plans", action="store_true",
+                    help="uneven batch: autotune every plan in isolation first")
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--ref-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")

@@ -85,6 +85,18 @@ typedef struct pce_plan* pce_plan_t;
  * PCE_FLAG_UNFUSED; pce_backward returns PCE_ERR_UNSUPPORTED on such plans.
  */
 #define PCE_FLAG_LOWP_STORAGE 2u
+/*
+ * PCE_FLAG_PRODUCT_CONVOLUTION: the plan's operator is the product-convolution
+ * form P_m u = sum_k w_k . (h_k * u) (windows on the output side; Section 1)
+ * instead of H_m u = sum_k h_k * (w_k . u).  pce_apply computes P_m u and
+ * pce_apply_adjoint P_m^* v = sum_k h~_k * (w_k . v).  The plan stores the
+ * spectra of h~_k = conj(hhat_k) and runs the other direction's kernels (one
+ * forward FFT of u, per term a product and an inverse FFT, windowed
+ * accumulation).  pce_plan_hhat still returns hhat_k; plans from spectra take
+ * hhat_k.  Combines with the other flags; pce_backward and pce_apply_noalloc
+ * return PCE_ERR_UNSUPPORTED on such plans.
+ */
+#define PCE_FLAG_PRODUCT_CONVOLUTION 4u
 
 /*
  * pce_plan_create -- precompute everything an operator needs (Eq. 1.4).
@@ -95,8 +107,9 @@ typedef struct pce_plan* pce_plan_t;
  *   m      : number of terms.
  *   w      : device, [m][shape] float32 windows w_k.
  *   h      : device, [m][shape] float32 impulse responses h_k, origin at index 0.
- *   flags  : PCE_FLAG_NONE, PCE_FLAG_UNFUSED or PCE_FLAG_LOWP_STORAGE; other bits
- *            return PCE_ERR_INVALID.
+ *   flags  : PCE_FLAG_NONE or a combination of PCE_FLAG_UNFUSED,
+ *            PCE_FLAG_LOWP_STORAGE (not with PCE_FLAG_UNFUSED) and
+ *            PCE_FLAG_PRODUCT_CONVOLUTION; other bits return PCE_ERR_INVALID.
  *   stream : cudaStream_t used for the set-up work.
  *
  * The plan finds the support box of every w_k (the smallest periodic
@@ -337,6 +350,24 @@ pce_status pce_batch_info(pce_batch_t batch, int* lanes, int64_t* scratch_bytes,
 pce_status pce_batch_destroy(pce_batch_t batch);
 
 /*
+ * pce_batch_autotune -- choose, for the whole batch, the column-variant and
+ * row-variant policy (each: -1 = every plan's own choice, 0 or 1 = that
+ * variant for every task; see pce_plan_autotune) by timing the batch's graph
+ * launch under all nine policies (L2 flushed, best of three) and keeping the
+ * fastest.  Variants chosen per plan in isolation can lose inside a
+ * concurrent batch, which is why the batch is timed as a whole.  Runs the
+ * batch (outputs are overwritten), allocates and frees temporary buffers,
+ * synchronises `stream`, and drops the captured graph (the next
+ * pce_batch_launch captures again).  pce_batch_tuning reads the policies
+ * back; pce_batch_tuning_log lists every timed policy (col, row, ms per run)
+ * and returns their number.
+ */
+pce_status pce_batch_autotune(pce_batch_t batch, void* stream);
+pce_status pce_batch_tuning(pce_batch_t batch, int* col_policy, int* row_policy);
+int pce_batch_tuning_log(pce_batch_t batch, int max_entries, int* col_policy, int* row_policy,
+                         double* ms_per_run);
+
+/*
  * pce_schedule_lpt -- the lane rule, exposed for tests: tasks by decreasing
  * cost (ties by index), each to the lane with the least load so far (ties:
  * lowest lane).  Host only.  lane_of: [n] output; makespan may be NULL.
@@ -349,24 +380,28 @@ pce_status pce_schedule_lpt(const double* cost, int n, int lanes, int* lane_of, 
  * of three) for every candidate and keep the fastest:
  *   - column FFT variant for Ny = 1024: 0 = one-warp 32 x 32 four-step
  *     (radix 32), 1 = block Stockham (radix 8);
+ *   - adjoint row-pass variant (2D): 0 = next term's data prefetched into
+ *     registers (2 CTAs per SM), 1 = no prefetch (3 CTAs per SM);
  *   - right-hand sides per launch: powers of two up to the plan's scratch
  *     chunk (2D plans and 1D plans above 8192 points).
  * 1D plans up to 8192 points have nothing to choose and are only timed.  The
- * result changes no value an apply computes beyond rounding order (the
- * variants' FFTs round differently).  cache_path (may be NULL): a JSON-lines
- * file; a line whose key (device, shape, m, flags, support boxes, batch)
- * matches is used without timing, otherwise the measured choice is
+ * choice changes no value an apply computes beyond rounding order (the
+ * column variants' FFTs round differently).  cache_path (may be NULL): a
+ * JSON-lines file; a line whose key (device, shape, m, flags, support boxes,
+ * batch) matches is used without timing, otherwise the measured choice is
  * appended.  Allocates and frees temporary buffers and synchronises the
  * stream.  pce_plan_tuning reads the choice back (ms_per_apply: measured
  * milliseconds per right-hand side per direction; 0 if never tuned).
  */
 pce_status pce_plan_autotune(pce_plan_t plan, int64_t batch, const char* cache_path, void* stream);
-pce_status pce_plan_tuning(pce_plan_t plan, int* chunk, int* col_variant, double* ms_per_apply);
+pce_status pce_plan_tuning(pce_plan_t plan, int* chunk, int* col_variant, int* row_variant,
+                           double* ms_per_apply);
 /* Every candidate the last timed pce_plan_autotune measured: writes up to
- * max_entries (chunk, variant, ms per apply) triples into the arrays (any may
- * be NULL) and returns how many there were (0 after a cache hit or for NULL). */
+ * max_entries (chunk, column variant, row variant, ms per apply) entries into
+ * the arrays (any may be NULL) and returns how many there were (0 after a
+ * cache hit or for NULL). */
 int pce_plan_tuning_log(pce_plan_t plan, int max_entries, int* chunk, int* col_variant,
-                        double* ms_per_apply);
+                        int* row_variant, double* ms_per_apply);
 
 #ifdef __cplusplus
 }

@@ -159,6 +159,15 @@ struct pce_batch {
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    int col_policy = -1, row_policy = -1;   // -1: every plan's own variants
+    std::vector<double> tune_log;           // (col policy, row policy, ms per run)
+
+    void drop_graph() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        exec = nullptr;
+        graph = nullptr;
+    }
 
     ~pce_batch() {
         if (exec) cudaGraphExecDestroy(exec);
@@ -423,7 +432,8 @@ std::string tune_key(const pce_plan* p, int64_t batch) {
     return buf;
 }
 
-bool cache_lookup(const char* path, const std::string& key, int& chunk, int& variant, double& ms) {
+bool cache_lookup(const char* path, const std::string& key, int& chunk, int& variant, int& rvariant,
+                  double& ms) {
     FILE* f = std::fopen(path, "r");
     if (!f) return false;
     const std::string pat = "\"key\": \"" + key + "\"";
@@ -434,12 +444,16 @@ bool cache_lookup(const char* path, const std::string& key, int& chunk, int& var
         const char* c = std::strstr(line, "\"chunk\": ");
         const char* v = std::strstr(line, "\"variant\": ");
         const char* t = std::strstr(line, "\"ms_per_apply\": ");
+        const char* rv = std::strstr(line, "\"row_variant\": ");
+        int rr = 0;
+        if (rv && (std::sscanf(rv + 15, "%d", &rr) != 1 || (rr != 0 && rr != 1))) continue;
         int cc = 0, vv = 0;
         double tt = 0.0;
         if (c && v && t && std::sscanf(c + 9, "%d", &cc) == 1 && std::sscanf(v + 11, "%d", &vv) == 1 &&
             std::sscanf(t + 16, "%lf", &tt) == 1 && cc >= 1 && (vv == 0 || vv == 1)) {
             chunk = cc;
             variant = vv;
+            rvariant = rr;
             ms = tt;
             found = true;   // the last matching line wins
         }
@@ -448,11 +462,12 @@ bool cache_lookup(const char* path, const std::string& key, int& chunk, int& var
     return found;
 }
 
-pce_status cache_store(const char* path, const std::string& key, int chunk, int variant, double ms) {
+pce_status cache_store(const char* path, const std::string& key, int chunk, int variant, int rvariant,
+                       double ms) {
     FILE* f = std::fopen(path, "a");
     if (!f) return fail(PCE_ERR_INVALID, "cannot open the tuning cache %s for appending", path);
-    std::fprintf(f, "{\"key\": \"%s\", \"chunk\": %d, \"variant\": %d, \"ms_per_apply\": %.6g}\n", key.c_str(),
-                 chunk, variant, ms);
+    std::fprintf(f, "{\"key\": \"%s\", \"chunk\": %d, \"variant\": %d, \"row_variant\": %d, \"ms_per_apply\": %.6g}\n",
+                 key.c_str(), chunk, variant, rvariant, ms);
     std::fclose(f);
     return PCE_OK;
 }
@@ -469,11 +484,13 @@ extern "C" pce_status pce_plan_autotune(pce_plan_t p, int64_t batch, const char*
     const std::string key = tune_key(p, batch);
     const int cmax = (int)std::max<long long>(1, std::min<long long>(p->bchunk, batch));
     if (cache_path) {
-        int c = 0, v = 0;
+        int c = 0, v = 0, rv = 0;
         double ms = 0.0;
-        if (cache_lookup(cache_path, key, c, v, ms)) {
+        if (cache_lookup(cache_path, key, c, v, rv, ms)) {
+            p->tune_log.clear();
             p->run_chunk = std::min(c, cmax);
             p->col_variant = (p->ndims == 2 && p->ny == 1024) ? v : 0;
+            p->row_variant = (p->ndims == 2) ? rv : 0;
             p->tuned_ms = ms;
             return PCE_OK;
         }
@@ -481,6 +498,8 @@ extern "C" pce_status pce_plan_autotune(pce_plan_t p, int64_t batch, const char*
     // candidates
     std::vector<int> variants = {0};
     if (p->ndims == 2 && p->ny == 1024) variants.push_back(1);
+    std::vector<int> rvariants = {0};
+    if (p->ndims == 2) rvariants.push_back(1);
     std::vector<int> chunks;
     if (p->ndims == 2 || p->l1) {
         for (int c = 1; c < cmax; c *= 2) chunks.push_back(c);
@@ -514,14 +533,16 @@ extern "C" pce_status pce_plan_autotune(pce_plan_t p, int64_t batch, const char*
         return fail(e == cudaErrorMemoryAllocation ? PCE_ERR_OOM : PCE_ERR_CUDA, "autotune set-up: %s",
                     cudaGetErrorString(e));
     }
-    const int saved_chunk = p->run_chunk, saved_variant = p->col_variant;
+    const int saved_chunk = p->run_chunk, saved_variant = p->col_variant, saved_rv = p->row_variant;
     p->tune_log.clear();
     double best = 1e300;
-    int best_c = cmax, best_v = 0;
+    int best_c = cmax, best_v = 0, best_r = 0;
     pce_status st = PCE_OK;
     for (int v : variants) {
+      for (int rv : rvariants) {
         for (int c : chunks) {
             p->col_variant = v;
+            p->row_variant = rv;
             p->run_chunk = c;
             const pce_rt::Scratch scr = pce_rt::plan_scratch(p);
             float tmin = 1e30f;
@@ -543,44 +564,144 @@ extern "C" pce_status pce_plan_autotune(pce_plan_t p, int64_t batch, const char*
                 st = fail(PCE_ERR_CUDA, "autotune timing: %s", cudaGetErrorString(e));
             if (st) break;
             const double per_apply = (double)tmin / (2.0 * (double)batch);
-            p->tune_log.insert(p->tune_log.end(), {(double)c, (double)v, per_apply});
+            p->tune_log.insert(p->tune_log.end(), {(double)c, (double)v, (double)rv, per_apply});
             if (per_apply < best) {
                 best = per_apply;
                 best_c = c;
                 best_v = v;
+                best_r = rv;
+            }
+        }
+        if (st) break;
+      }
+      if (st) break;
+    }
+    cleanup();
+    if (st) {
+        p->run_chunk = saved_chunk;
+        p->col_variant = saved_variant;
+        p->row_variant = saved_rv;
+        return st;
+    }
+    p->run_chunk = best_c;
+    p->col_variant = best_v;
+    p->row_variant = best_r;
+    p->tuned_ms = best;
+    if (cache_path) return cache_store(cache_path, key, best_c, best_v, best_r, best);
+    return PCE_OK;
+}
+
+extern "C" pce_status pce_plan_tuning(pce_plan_t p, int* chunk, int* col_variant, int* row_variant,
+                                      double* ms_per_apply) {
+    if (!p) return fail(PCE_ERR_INVALID, "plan is NULL");
+    if (chunk) *chunk = p->run_chunk > 0 ? std::min(p->run_chunk, p->bchunk) : p->bchunk;
+    if (col_variant) *col_variant = p->col_variant;
+    if (row_variant) *row_variant = p->row_variant;
+    if (ms_per_apply) *ms_per_apply = p->tuned_ms;
+    return PCE_OK;
+}
+
+extern "C" int pce_plan_tuning_log(pce_plan_t p, int max_entries, int* chunk, int* col_variant,
+                                   int* row_variant, double* ms_per_apply) {
+    if (!p) return 0;
+    const int n = (int)(p->tune_log.size() / 4);
+    for (int i = 0; i < std::min(n, max_entries); ++i) {
+        if (chunk) chunk[i] = (int)p->tune_log[4 * i];
+        if (col_variant) col_variant[i] = (int)p->tune_log[4 * i + 1];
+        if (row_variant) row_variant[i] = (int)p->tune_log[4 * i + 2];
+        if (ms_per_apply) ms_per_apply[i] = p->tune_log[4 * i + 3];
+    }
+    return n;
+}
+
+// ------------------------------------------------------ batch-level tuning
+
+extern "C" pce_status pce_batch_autotune(pce_batch_t b, void* stream) {
+    if (!b) return fail(PCE_ERR_INVALID, "batch is NULL");
+    int dev = 0;
+    PCE_BCK(cudaGetDevice(&dev));
+    if (dev != b->device) return fail(PCE_ERR_INVALID, "batch belongs to device %d, current is %d", b->device, dev);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    void* flush = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const size_t flush_bytes = 192ull << 20;
+    auto cleanup = [&]() {
+        if (flush) cudaFree(flush);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    cudaError_t e = cudaMalloc(&flush, flush_bytes);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) {
+        cleanup();
+        return fail(PCE_ERR_CUDA, "batch autotune set-up: %s", cudaGetErrorString(e));
+    }
+    const int pol[] = {-1, 0, 1};
+    double best = 1e300;
+    int best_c = -1, best_r = -1;
+    b->tune_log.clear();
+    pce_status st = PCE_OK;
+    for (int cp : pol) {
+        for (int rp : pol) {
+            for (size_t i = 0; i < b->scr.size(); ++i) {
+                b->scr[i].col_variant = cp;
+                b->scr[i].row_variant = rp;
+            }
+            b->drop_graph();
+            float tmin = 1e30f;
+            for (int rep = 0; rep < 4 && st == PCE_OK; ++rep) {   // rep 0 captures and warms up
+                e = cudaMemsetAsync(flush, rep, flush_bytes, s);
+                if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+                if (e != cudaSuccess) break;
+                if ((st = pce_batch_launch(b, stream))) break;
+                e = cudaEventRecord(e1, s);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e != cudaSuccess) break;
+                if (rep > 0) tmin = std::min(tmin, ms);
+            }
+            if (st == PCE_OK && e != cudaSuccess) st = fail(PCE_ERR_CUDA, "batch autotune timing: %s", cudaGetErrorString(e));
+            if (st) break;
+            b->tune_log.insert(b->tune_log.end(), {(double)cp, (double)rp, (double)tmin});
+            if (tmin < best) {
+                best = tmin;
+                best_c = cp;
+                best_r = rp;
             }
         }
         if (st) break;
     }
     cleanup();
     if (st) {
-        p->run_chunk = saved_chunk;
-        p->col_variant = saved_variant;
-        return st;
+        best_c = best_r = -1;
     }
-    p->run_chunk = best_c;
-    p->col_variant = best_v;
-    p->tuned_ms = best;
-    if (cache_path) return cache_store(cache_path, key, best_c, best_v, best);
-    return PCE_OK;
+    for (size_t i = 0; i < b->scr.size(); ++i) {
+        b->scr[i].col_variant = best_c;
+        b->scr[i].row_variant = best_r;
+    }
+    b->col_policy = best_c;
+    b->row_policy = best_r;
+    b->drop_graph();
+    return st;
 }
 
-extern "C" pce_status pce_plan_tuning(pce_plan_t p, int* chunk, int* col_variant, double* ms_per_apply) {
-    if (!p) return fail(PCE_ERR_INVALID, "plan is NULL");
-    if (chunk) *chunk = p->run_chunk > 0 ? std::min(p->run_chunk, p->bchunk) : p->bchunk;
-    if (col_variant) *col_variant = p->col_variant;
-    if (ms_per_apply) *ms_per_apply = p->tuned_ms;
-    return PCE_OK;
-}
-
-extern "C" int pce_plan_tuning_log(pce_plan_t p, int max_entries, int* chunk, int* col_variant,
-                                   double* ms_per_apply) {
-    if (!p) return 0;
-    const int n = (int)(p->tune_log.size() / 3);
+extern "C" int pce_batch_tuning_log(pce_batch_t b, int max_entries, int* col_policy, int* row_policy,
+                                    double* ms_per_run) {
+    if (!b) return 0;
+    const int n = (int)(b->tune_log.size() / 3);
     for (int i = 0; i < std::min(n, max_entries); ++i) {
-        if (chunk) chunk[i] = (int)p->tune_log[3 * i];
-        if (col_variant) col_variant[i] = (int)p->tune_log[3 * i + 1];
-        if (ms_per_apply) ms_per_apply[i] = p->tune_log[3 * i + 2];
+        if (col_policy) col_policy[i] = (int)b->tune_log[3 * i];
+        if (row_policy) row_policy[i] = (int)b->tune_log[3 * i + 1];
+        if (ms_per_run) ms_per_run[i] = b->tune_log[3 * i + 2];
     }
     return n;
+}
+
+extern "C" pce_status pce_batch_tuning(pce_batch_t b, int* col_policy, int* row_policy) {
+    if (!b) return fail(PCE_ERR_INVALID, "batch is NULL");
+    if (col_policy) *col_policy = b->col_policy;
+    if (row_policy) *row_policy = b->row_policy;
+    return PCE_OK;
 }

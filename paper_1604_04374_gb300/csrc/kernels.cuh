@@ -270,8 +270,12 @@ __device__ __forceinline__ void adj_load(float2 (&v)[kR], float (&wa)[kR], float
     }
 }
 
-template <int NX, typename WT = float>
-__global__ void __launch_bounds__(256)
+// RV = 0: the next term's Q rows and window values are prefetched into
+// registers during the current term's FFT (128 registers, 2 CTAs per SM);
+// RV = 1: no prefetch, 80 registers, 3 CTAs per SM (more warps hide the
+// loads instead).  The autotuner picks one per plan.
+template <int NX, typename WT = float, int RV = 0>
+__global__ void __launch_bounds__(256, RV == 1 ? 3 : 1)
 k_rows_adj(const float2* __restrict__ Q, long long q_bstride, long long q_kstride, int nrows,
            const WT* __restrict__ wbox, const Box* __restrict__ box,
            const int* __restrict__ kptr, const int* __restrict__ klist,
@@ -324,24 +328,36 @@ k_rows_adj(const float2* __restrict__ Q, long long q_bstride, long long q_kstrid
 
     float2 v[kR];
     float wa[kR], wb[kR];
-    if (nk > 0) adj_load<NX, WT>(v, wa, wb, term(0), j);
-    for (int t = 0; t < nk; ++t) {
-        float2 vn[kR];
-        float wan[kR], wbn[kR];
-        const bool more = t + 1 < nk;
-        if (more) adj_load<NX, WT>(vn, wan, wbn, term(t + 1), j);
-        fft<NX, true>(v, j, b0, b1, tw);
-#pragma unroll
-        for (int r = 0; r < kR; ++r) {
-            acc[r].x = fmaf(wa[r], v[r].x, acc[r].x);
-            acc[r].y = fmaf(wb[r], v[r].y, acc[r].y);
-        }
-        if (more) {
+    if constexpr (RV == 1) {
+        for (int t = 0; t < nk; ++t) {
+            adj_load<NX, WT>(v, wa, wb, term(t), j);
+            fft<NX, true>(v, j, b0, b1, tw);
 #pragma unroll
             for (int r = 0; r < kR; ++r) {
-                v[r] = vn[r];
-                wa[r] = wan[r];
-                wb[r] = wbn[r];
+                acc[r].x = fmaf(wa[r], v[r].x, acc[r].x);
+                acc[r].y = fmaf(wb[r], v[r].y, acc[r].y);
+            }
+        }
+    } else {
+        if (nk > 0) adj_load<NX, WT>(v, wa, wb, term(0), j);
+        for (int t = 0; t < nk; ++t) {
+            float2 vn[kR];
+            float wan[kR], wbn[kR];
+            const bool more = t + 1 < nk;
+            if (more) adj_load<NX, WT>(vn, wan, wbn, term(t + 1), j);
+            fft<NX, true>(v, j, b0, b1, tw);
+#pragma unroll
+            for (int r = 0; r < kR; ++r) {
+                acc[r].x = fmaf(wa[r], v[r].x, acc[r].x);
+                acc[r].y = fmaf(wb[r], v[r].y, acc[r].y);
+            }
+            if (more) {
+#pragma unroll
+                for (int r = 0; r < kR; ++r) {
+                    v[r] = vn[r];
+                    wa[r] = wan[r];
+                    wb[r] = wbn[r];
+                }
             }
         }
     }

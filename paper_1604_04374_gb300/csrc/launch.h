@@ -41,7 +41,7 @@ cudaError_t launch_rows_c2r(int nx, dim3 grid, cudaStream_t s, const float2* src
 cudaError_t launch_rows_adj(int nx, dim3 grid, cudaStream_t s, const float2* Q, long long q_bstride,
                             long long q_kstride, int nrows, const void* wbox, bool lowp, const Box* box,
                             const int* kptr, const int* klist, float* dst, long long dst_bstride,
-                            float scale, const float2* tw, const float2* tw1024);
+                            float scale, const float2* tw, const float2* tw1024, int rv = 0);
 
 cudaError_t launch_cols_fwd(int ny, dim3 grid, cudaStream_t s, const float2* Z, long long z_bstride,
                             long long z_kstride, const void* hh, const void* hN, const float* hscale,

@@ -114,6 +114,16 @@ __global__ void k_twiddles_N(float2* tw, long long n) {
     tw[j] = make_float2((float)cs, (float)sn);
 }
 
+// x[i] = conj(x[i]) for i < n, except every per-th element from 0 when skip0
+// (slot 0 of a packed 1D half spectrum holds the real pair (X[0], X[N/2])).
+__global__ void k_conj(float2* x, long long n, long long per, int skip0) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (skip0 && i % per == 0) continue;
+        x[i].y = -x[i].y;
+    }
+}
+
 // hhat [m][N/2+1] (natural half spectrum) -> hh4 [m][ny][nx] in the four-step
 // order (f = a + ny b at (a, b)), Hermitian extension, real DC and Nyquist.
 __global__ void k_from_half_l1(const float2* __restrict__ hhat, int m, int ny, int nx, float2* hh4) {
@@ -654,7 +664,7 @@ pce_status create_common(pce_plan_t* out, int ndims, const int64_t* shape, int m
     pce_status st = validate_shape(ndims, shape, ny, nx);
     if (st) return st;
     if (m < 1) return fail(PCE_ERR_INVALID, "m must be >= 1 (got %d)", m);
-    if (flags & ~(uint32_t)(PCE_FLAG_UNFUSED | PCE_FLAG_LOWP_STORAGE))
+    if (flags & ~(uint32_t)(PCE_FLAG_UNFUSED | PCE_FLAG_LOWP_STORAGE | PCE_FLAG_PRODUCT_CONVOLUTION))
         return fail(PCE_ERR_INVALID, "unknown flag bits 0x%x", flags);
     if ((flags & PCE_FLAG_UNFUSED) && (flags & PCE_FLAG_LOWP_STORAGE))
         return fail(PCE_ERR_INVALID, "PCE_FLAG_UNFUSED runs FP32 storage only");
@@ -765,6 +775,19 @@ pce_status create_common(pce_plan_t* out, int ndims, const int64_t* shape, int m
             if (e == cudaSuccess) e = e2;
             if (e) return bail(fail(PCE_ERR_CUDA, "spectrum of h: %s", cudaGetErrorString(e)));
         }
+    }
+    if (flags & PCE_FLAG_PRODUCT_CONVOLUTION) {
+        // sum_k w_k . (h_k * u) is the adjoint structure with the spectra of h~_k = conj(hhat_k)
+        if (p->l1) {
+            k_conj<<<grid_for((long long)m * nx), 256, 0, s>>>(p->hh4, (long long)m * nx, 1, 0);
+        } else if (ndims == 1) {
+            k_conj<<<grid_for((long long)m * nxh), 256, 0, s>>>(p->hh, (long long)m * nxh, nxh, 1);
+        } else {
+            k_conj<<<grid_for((long long)m * ny * nxh), 256, 0, s>>>(p->hh, (long long)m * ny * nxh, 1, 0);
+            k_conj<<<grid_for((long long)m * ny), 256, 0, s>>>(p->hN, (long long)m * ny, 1, 0);
+        }
+        cudaError_t e1 = cudaGetLastError();
+        if (e1) return bail(fail(PCE_ERR_CUDA, "spectrum conjugation: %s", cudaGetErrorString(e1)));
     }
     if (ndims == 2 && ny == 1024) {
         if ((st = dev_alloc(&p->hhT, (size_t)m * ny * nxh))) return bail(st);
@@ -970,6 +993,8 @@ pce_status apply_plain(pce_plan_t p, const float* in, float* out, int64_t batch,
 pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, bool adjoint,
                       cudaStream_t s, const pce_rt::Scratch& scr, bool allow_timing = true) {
     TimingScope ts(allow_timing && !stream_capturing(s));
+    // a product-convolution plan holds conj(hhat_k): its operator is the adjoint structure
+    if (p->flags & PCE_FLAG_PRODUCT_CONVOLUTION) adjoint = !adjoint;
     const int ny = p->ny, nx = p->nx, m = p->m, nxh = nx / 2;
     const long long P = (long long)ny * nx;
     const float scale = 1.0f / (float)P;
@@ -1029,7 +1054,8 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
         return PCE_OK;
     }
     if (p->flags & PCE_FLAG_UNFUSED) return apply_plain(p, in, out, batch, adjoint, s);
-    const bool warp = p->col_variant == 0;
+    const bool warp = (scr.col_variant >= 0 ? scr.col_variant : p->col_variant) == 0;
+    const int rowv = scr.row_variant >= 0 ? scr.row_variant : p->row_variant;
     const long long zk = (long long)p->nrmax * nxh;
     const long long zb = scr.zstride;
     const long long ab = scr.astride;
@@ -1072,7 +1098,7 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
                 e = timed(p, PCE_KERNEL_ROWS_ADJ, s, [&] {
                     return pce::launch_rows_adj(nx, dim3((npairs + fpc - 1) / fpc, nb), s, scr.Z, zb,
                                                 zk, ny, wstore(p), p->lowp, p->d_box, p->kptr, p->klist, dst, P,
-                                                scale, p->twx, p->tw1024);
+                                                scale, p->twx, p->tw1024, rowv);
                 });
         }
     }
@@ -1142,6 +1168,10 @@ pce_status pce_plan_hhat(pce_plan_t plan, float* hhat, void* stream) {
     else
         k_to_half2d<<<grid_for((long long)plan->m * plan->ny * (nxh + 1)), 256, 0, s>>>(
             plan->hh, plan->hN, plan->m, plan->ny, nxh, reinterpret_cast<float2*>(hhat));
+    if (plan->flags & PCE_FLAG_PRODUCT_CONVOLUTION) {
+        const long long n = (long long)plan->m * plan->ny * (nxh + 1);
+        k_conj<<<grid_for(n), 256, 0, s>>>(reinterpret_cast<float2*>(hhat), n, 1, 0);
+    }
     PCE_CK(cudaGetLastError());
     return PCE_OK;
 }
@@ -1212,9 +1242,10 @@ pce_status pce_plan_timing(pce_plan_t plan, int kind, double* total_ms, int64_t*
 }
 
 int64_t pce_launch_count(pce_plan_t plan, int adjoint, int64_t batch) {
-    (void)adjoint;
     if (!plan || batch <= 0) return 0;
-    const int64_t chunks = (batch + plan->bchunk - 1) / plan->bchunk;
+    if (plan->flags & PCE_FLAG_PRODUCT_CONVOLUTION) adjoint = !adjoint;
+    const int64_t c = own_scratch(plan).chunk;
+    const int64_t chunks = (batch + c - 1) / c;
     if (plan->l1) return chunks * 3;
     if (plan->ndims == 1) return 1;
     if (plan->flags & PCE_FLAG_UNFUSED) {
@@ -1263,6 +1294,8 @@ extern "C" pce_status pce_backward(pce_plan_t p, const float* u, const float* r,
     if (st) return st;
     if (batch < 0) return fail(PCE_ERR_INVALID, "batch must be >= 0");
     if (p->lowp) return fail(PCE_ERR_UNSUPPORTED, "pce_backward runs on plans with FP32 storage only");
+    if (p->flags & PCE_FLAG_PRODUCT_CONVOLUTION)
+        return fail(PCE_ERR_UNSUPPORTED, "pce_backward serves convolution-product plans only");
     if (p->l1) return fail(PCE_ERR_UNSUPPORTED, "pce_backward serves 1D sizes up to 8192");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int ny = p->ny, nx = p->nx, m = p->m, nxh = nx / 2;
@@ -1390,6 +1423,8 @@ extern "C" pce_status pce_apply_noalloc(pce_plan_t plan, const float* u, float* 
                                         void* stream) {
     pce_status st = check_plan(plan);
     if (st) return st;
+    if (plan->flags & PCE_FLAG_PRODUCT_CONVOLUTION)
+        return fail(PCE_ERR_UNSUPPORTED, "pce_apply_noalloc serves convolution-product plans only");
     if (plan->ndims != 2)
         return fail(PCE_ERR_UNSUPPORTED, "pce_apply_noalloc serves 2D plans only (the 1D apply uses no scratch)");
     if ((st = check_io(plan, u, y, batch))) return st;

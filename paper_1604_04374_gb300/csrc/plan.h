@@ -57,8 +57,9 @@ struct pce_plan {
     // autotuned choices (pce_plan_autotune): 0 = default
     int run_chunk = 0;          // right-hand sides per launch, <= bchunk
     int col_variant = 0;        // columns of 1024: 0 one-warp four-step, 1 radix-8 Stockham
+    int row_variant = 0;        // adjoint row pass: 0 register prefetch, 1 none (3 CTAs per SM)
     double tuned_ms = 0.0;      // measured ms per right-hand side (forward + adjoint) / 2
-    std::vector<double> tune_log;   // (chunk, variant, ms per apply) of every timed candidate
+    std::vector<double> tune_log;   // (chunk, col variant, row variant, ms per apply) per timed candidate
     long long zalloc = 0;   // Z scratch per right-hand side (float2)
     long long scratch_bytes = 0;
     // per-kernel timing
@@ -94,6 +95,8 @@ struct Scratch {
     long long zstride = 0;
     long long astride = 0;
     int chunk = 1;
+    int col_variant = -1;   // >= 0: overrides the plan's column variant for this apply
+    int row_variant = -1;   // >= 0: overrides the plan's row variant for this apply
 };
 
 pce_status fail(pce_status s, const char* fmt, ...);

@@ -16,6 +16,7 @@ PCE_OK, PCE_ERR_INVALID, PCE_ERR_UNSUPPORTED, PCE_ERR_OOM, PCE_ERR_CUDA, PCE_ERR
 PCE_FLAG_NONE = 0
 PCE_FLAG_UNFUSED = 1
 PCE_FLAG_LOWP_STORAGE = 2
+PCE_FLAG_PRODUCT_CONVOLUTION = 4
 STATUS_NAMES = {0: "PCE_OK", 1: "PCE_ERR_INVALID", 2: "PCE_ERR_UNSUPPORTED", 3: "PCE_ERR_OOM",
                 4: "PCE_ERR_CUDA", 5: "PCE_ERR_TIMEOUT"}
 
@@ -88,19 +89,23 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.pce_batch_info.argtypes = [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(i64), ctypes.POINTER(i64),
                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
     lib.pce_batch_destroy.argtypes = [P]
+    lib.pce_batch_autotune.argtypes = [P, P]
+    lib.pce_batch_tuning.argtypes = [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    lib.pce_batch_tuning_log.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+    lib.pce_batch_tuning_log.restype = ctypes.c_int
     lib.pce_schedule_lpt.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.c_int, ctypes.c_int,
                                      ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
     lib.pce_plan_autotune.argtypes = [P, i64, ctypes.c_char_p, P]
-    lib.pce_plan_tuning.argtypes = [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
-                                    ctypes.POINTER(ctypes.c_double)]
-    lib.pce_plan_tuning_log.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
-                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+    IP = ctypes.POINTER(ctypes.c_int)
+    lib.pce_plan_tuning.argtypes = [P, IP, IP, IP, ctypes.POINTER(ctypes.c_double)]
+    lib.pce_plan_tuning_log.argtypes = [P, ctypes.c_int, IP, IP, IP, ctypes.POINTER(ctypes.c_double)]
     lib.pce_plan_tuning_log.restype = ctypes.c_int
     for name in ("pce_plan_create", "pce_plan_create_from_spectra", "pce_apply", "pce_apply_adjoint",
                  "pce_plan_info", "pce_plan_hhat", "pce_plan_destroy", "pce_plan_set_timing",
                  "pce_plan_timing", "pce_apply_batch", "pce_batch_create", "pce_batch_run",
                  "pce_batch_launch", "pce_batch_info", "pce_batch_destroy", "pce_schedule_lpt",
-                 "pce_plan_autotune", "pce_plan_tuning"):
+                 "pce_plan_autotune", "pce_plan_tuning", "pce_batch_autotune", "pce_batch_tuning"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -223,6 +228,29 @@ def pce_batch_destroy(batch: int) -> None:
     _check(load_library().pce_batch_destroy(batch))
 
 
+def pce_batch_autotune(batch: int, stream: int = 0) -> None:
+    _check(load_library().pce_batch_autotune(batch, stream))
+
+
+def pce_batch_tuning(batch: int):
+    """(column-variant policy, row-variant policy); -1 = every plan's own choice."""
+    c = ctypes.c_int()
+    r = ctypes.c_int()
+    _check(load_library().pce_batch_tuning(batch, ctypes.byref(c), ctypes.byref(r)))
+    return c.value, r.value
+
+
+def pce_batch_tuning_log(batch: int):
+    """[(column policy, row policy, ms per run)] of every policy the last batch autotune timed."""
+    lib = load_library()
+    n = lib.pce_batch_tuning_log(batch, 0, None, None, None)
+    c = (ctypes.c_int * max(1, n))()
+    r = (ctypes.c_int * max(1, n))()
+    ms = (ctypes.c_double * max(1, n))()
+    lib.pce_batch_tuning_log(batch, n, c, r, ms)
+    return [(c[i], r[i], ms[i]) for i in range(n)]
+
+
 def pce_schedule_lpt(cost, lanes: int):
     """(lane of every task, makespan) under the longest-processing-time-first rule."""
     n = len(cost)
@@ -239,23 +267,26 @@ def pce_plan_autotune(plan: int, batch: int, cache_path: str | None = None, stre
 
 
 def pce_plan_tuning(plan: int):
-    """(right-hand sides per launch, column variant, measured ms per apply)."""
+    """(right-hand sides per launch, column variant, row variant, measured ms per apply)."""
     c = ctypes.c_int()
     v = ctypes.c_int()
+    r = ctypes.c_int()
     ms = ctypes.c_double()
-    _check(load_library().pce_plan_tuning(plan, ctypes.byref(c), ctypes.byref(v), ctypes.byref(ms)))
-    return c.value, v.value, ms.value
+    _check(load_library().pce_plan_tuning(plan, ctypes.byref(c), ctypes.byref(v), ctypes.byref(r),
+                                          ctypes.byref(ms)))
+    return c.value, v.value, r.value, ms.value
 
 
 def pce_plan_tuning_log(plan: int):
-    """[(chunk, variant, ms per apply)] of every candidate the last autotune timed."""
+    """[(chunk, column variant, row variant, ms per apply)] of every candidate the last autotune timed."""
     lib = load_library()
-    n = lib.pce_plan_tuning_log(plan, 0, None, None, None)
+    n = lib.pce_plan_tuning_log(plan, 0, None, None, None, None)
     c = (ctypes.c_int * max(1, n))()
     v = (ctypes.c_int * max(1, n))()
+    r = (ctypes.c_int * max(1, n))()
     ms = (ctypes.c_double * max(1, n))()
-    lib.pce_plan_tuning_log(plan, n, c, v, ms)
-    return [(c[i], v[i], ms[i]) for i in range(n)]
+    lib.pce_plan_tuning_log(plan, n, c, v, r, ms)
+    return [(c[i], v[i], r[i], ms[i]) for i in range(n)]
 
 
 KERNEL_KINDS = ("rows_r2c_window", "cols_fwd", "rows_c2r", "rows_r2c", "cols_adj", "rows_adj",
@@ -390,11 +421,11 @@ class Plan:
         return self.tuning()
 
     def tuning(self):
-        """(right-hand sides per launch, column variant, measured ms per apply)."""
+        """(right-hand sides per launch, column variant, row variant, measured ms per apply)."""
         return pce_plan_tuning(self.handle)
 
     def tuning_log(self):
-        """[(chunk, variant, ms per apply)] of every candidate the last autotune timed."""
+        """[(chunk, column variant, row variant, ms per apply)] of every candidate the last autotune timed."""
         return pce_plan_tuning_log(self.handle)
 
     def set_timing(self, enable: bool) -> None:
@@ -447,6 +478,11 @@ class Batch:
 
     def info(self):
         return pce_batch_info(self.handle, self.n)
+
+    def autotune(self, stream=None):
+        """Pick the variant policies by timing the whole batch; returns (policies, log)."""
+        pce_batch_autotune(self.handle, _stream_handle(stream))
+        return pce_batch_tuning(self.handle), pce_batch_tuning_log(self.handle)
 
     def close(self):
         if getattr(self, "handle", None):

@@ -245,3 +245,97 @@ def batch_mix(n_tasks: int = 256, seed_index: int = 4, shapes=BATCH_SHAPES, ms=B
     inputs = [draw(rng, (1,) + tuple(shapes[s]), "normal" if len(shapes[s]) == 1 else "uniform")
               for s, _, _ in picks]
     return BatchMix(f"batch{n_tasks}_mixed", ops, op_of, adjoint, inputs)
+
+
+# ----------------------------------------------- wavelet windows (Section 4.3)
+
+# Daubechies' orthonormal scaling filter with two vanishing moments (D4), closed form.
+_S3 = math.sqrt(3.0)
+D4_FILTER = np.array([1 + _S3, 3 + _S3, 3 - _S3, 1 - _S3]) / (4 * math.sqrt(2.0))
+
+
+def _synthesis_step(a: np.ndarray, d: np.ndarray, hfil: np.ndarray) -> np.ndarray:
+    """One periodic inverse DWT step: length L coefficients -> length 2L signal,
+    x[t] = sum_k a[k] h[t - 2k] + d[k] g[t - 2k] (indices mod 2L), g[i] = (-1)^i h[M-1-i]."""
+    L = a.shape[0]
+    M = hfil.shape[0]
+    g = np.array([(-1) ** i * hfil[M - 1 - i] for i in range(M)])
+    x = np.zeros(2 * L)
+    for k in range(L):
+        for i in range(M):
+            t = (2 * k + i) % (2 * L)
+            x[t] += a[k] * hfil[i] + d[k] * g[i]
+    return x
+
+
+def periodic_wavelet(n: int, j: int, k: int, kind: str, hfil: np.ndarray = D4_FILTER) -> np.ndarray:
+    """Periodic orthonormal scaling function ('phi') or wavelet ('psi') at scale j,
+    position k < 2^j, sampled on n = 2^L points (float64): the inverse periodic DWT
+    of a unit coefficient, synthesised up to length n."""
+    L = int(round(math.log2(n)))
+    if 2 ** L != n or not 0 <= j < L or not 0 <= k < 2 ** j:
+        raise ValueError("need n = 2^L, 0 <= j < L, 0 <= k < 2^j")
+    a = np.zeros(2 ** j)
+    d = np.zeros(2 ** j)
+    (a if kind == "phi" else d)[k] = 1.0
+    x = _synthesis_step(a, d, hfil)
+    while x.shape[0] < n:
+        x = _synthesis_step(x, np.zeros_like(x), hfil)
+    return x
+
+
+def wavelet_windows_1d(n: int, j0: int, levels: int) -> tuple[np.ndarray, list]:
+    """Windows of the wavelet form (Section 4.3): the 2^j0 scaling functions at scale j0
+    and the wavelets of scales j0 .. j0+levels-1 (2^j each), periodic D4.
+    Returns ([m][n] float32, [(kind, j, k)])."""
+    funcs, labels = [], []
+    for k in range(2 ** j0):
+        funcs.append(periodic_wavelet(n, j0, k, "phi"))
+        labels.append(("phi", j0, k))
+    for j in range(j0, j0 + levels):
+        for k in range(2 ** j):
+            funcs.append(periodic_wavelet(n, j, k, "psi"))
+            labels.append(("psi", j, k))
+    return np.stack(funcs).astype(np.float32), labels
+
+
+def wavelet_windows_2d(ny: int, nx: int, j0: int, levels: int) -> tuple[np.ndarray, list]:
+    """Tensor-product windows phi_{j0,a}(row) phi_{j0,c}(col) and psi_{j,a}(row) psi_{j,c}(col),
+    j = j0 .. j0+levels-1: supports from most of the grid down to 3/2^j of each side."""
+    funcs, labels = [], []
+    for a in range(2 ** j0):
+        fa = periodic_wavelet(ny, j0, a, "phi")
+        for c in range(2 ** j0):
+            funcs.append(np.outer(fa, periodic_wavelet(nx, j0, c, "phi")))
+            labels.append(("phi", j0, a, c))
+    for j in range(j0, j0 + levels):
+        for a in range(2 ** j):
+            fa = periodic_wavelet(ny, j, a, "psi")
+            for c in range(2 ** j):
+                funcs.append(np.outer(fa, periodic_wavelet(nx, j, c, "psi")))
+                labels.append(("psi", j, a, c))
+    return np.stack(funcs).astype(np.float32), labels
+
+
+def wavelet_problem(shape: tuple, j0: int, levels: int, batch: int, seed_index: int,
+                    radius: int | None = None) -> Problem:
+    """Wavelet windows of varying support with random impulse responses supported on
+    |offset| <= radius per axis (default 12 in 1D, 5 in 2D); u ~ N(0,1)."""
+    if radius is None:
+        radius = 12 if len(shape) == 1 else 5
+    if len(shape) == 1:
+        w, labels = wavelet_windows_1d(shape[0], j0, levels)
+    else:
+        w, labels = wavelet_windows_2d(shape[0], shape[1], j0, levels)
+    m = w.shape[0]
+    rng = rng_for(seed_index)
+    h = np.zeros((m,) + tuple(shape), np.float32)
+    offs = [np.arange(-radius, radius + 1) % n for n in shape]
+    if len(shape) == 1:
+        h[:, offs[0]] = rng.standard_normal((m, offs[0].size)).astype(np.float32)
+    else:
+        h[:, offs[0][:, None], offs[1][None, :]] = rng.standard_normal(
+            (m, offs[0].size, offs[1].size)).astype(np.float32)
+    u = draw(rng, (batch,) + tuple(shape), "normal")
+    return Problem(f"wavelet_{'x'.join(map(str, shape))}_j{j0}_l{levels}", tuple(shape), m, w, h, u,
+                   {"labels": labels})

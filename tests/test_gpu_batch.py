@@ -106,6 +106,28 @@ def test_batch_object_run_and_graph_launch(torch_cuda, mix, lanes):
     b.close()
 
 
+def test_batch_autotune_keeps_results(torch_cuda, mix):
+    """Every policy runs the same operators: after tuning the outputs still equal the
+    single applies up to rounding (column variants round differently)."""
+    torch = torch_cuda
+    from paper_1604_04374_gb300 import Batch
+    mx, plans, ins = mix
+    ref = singles(torch, mx, plans, ins)
+    tasks, outs = tasks_of(torch, mx, plans, ins)
+    b = Batch(tasks, lanes=6)
+    (cp, rp), log = b.autotune()
+    assert len(log) == 9 and {(c, r) for c, r, _ in log} == {(c, r) for c in (-1, 0, 1) for r in (-1, 0, 1)}
+    assert all(ms > 0 for _, _, ms in log)
+    assert (cp, rp, min(ms for _, _, ms in log)) in {(c, r, ms) for c, r, ms in log}
+    for o in outs:
+        o.fill_(float("nan"))
+    b.launch()
+    torch.cuda.synchronize()
+    for i in range(len(ins)):
+        assert rel(host(outs[i])[None], ref[i][None]) < 1e-6, i
+    b.close()
+
+
 def test_batch_tasks_match_oracle(torch_cuda, mix):
     torch = torch_cuda
     from paper_1604_04374_gb300 import Batch
@@ -158,22 +180,24 @@ def test_autotune_variants_and_cache(torch_cuda, tmp_path):
     pr = synth.problem_2d(1024, 32, 4, 3, 61, "normal")
     cache = str(tmp_path / "tune.jsonl")
     plan = Plan(dev(torch, pr.w), h=dev(torch, pr.h))
-    chunk, variant, ms = plan.autotune(3, cache)
-    assert 1 <= chunk <= 3 and variant in (0, 1) and ms > 0
+    chunk, variant, rvariant, ms = plan.autotune(3, cache)
+    assert 1 <= chunk <= 3 and variant in (0, 1) and rvariant in (0, 1) and ms > 0
+    assert len(plan.tuning_log()) == 3 * 2 * 2
     lines = open(cache).read().splitlines()
     assert len(lines) == 1
     rec = json.loads(lines[0])
-    assert rec["chunk"] == chunk and rec["variant"] == variant
+    assert rec["chunk"] == chunk and rec["variant"] == variant and rec["row_variant"] == rvariant
     u = dev(torch, pr.u)
     assert rel(host(plan.apply(u)), E.apply(pr.u, pr.w, pr.h)) < TOL
     assert rel(host(plan.apply_adjoint(u)), E.apply_adjoint(pr.u, pr.w, pr.h)) < TOL
     # a second plan of the same operator reads the cache; force the other variant through it
-    rec2 = dict(rec, variant=1 - variant, chunk=1)
+    rec2 = dict(rec, variant=1 - variant, row_variant=1 - rvariant, chunk=1)
     with open(cache, "a") as f:
         f.write(json.dumps(rec2) + "\n")
     p2 = Plan(dev(torch, pr.w), h=dev(torch, pr.h))
-    c2, v2, _ = p2.autotune(3, cache)
-    assert (c2, v2) == (1, 1 - variant)
+    c2, v2, r2, _ = p2.autotune(3, cache)
+    assert (c2, v2, r2) == (1, 1 - variant, 1 - rvariant)
+    assert p2.tuning_log() == []
     assert len(open(cache).read().splitlines()) == 2      # nothing appended
     assert rel(host(p2.apply(u)), E.apply(pr.u, pr.w, pr.h)) < TOL
     assert rel(host(p2.apply_adjoint(u)), E.apply_adjoint(pr.u, pr.w, pr.h)) < TOL
@@ -188,8 +212,9 @@ def test_autotune_other_plans(torch_cuda, shape, m):
     else:
         pr = synth.problem_2d(shape[0], shape[1], m, 4, 62, "normal")
     plan = Plan(dev(torch, pr.w), h=dev(torch, pr.h))
-    chunk, variant, ms = plan.autotune(4)
+    chunk, variant, rvariant, ms = plan.autotune(4)
     assert variant == 0 and ms > 0 and chunk >= 1
+    assert rvariant in ((0, 1) if len(shape) == 2 else (0,))
     u = dev(torch, pr.u)
     assert rel(host(plan.apply(u)), E.apply(pr.u, pr.w, pr.h)) < TOL
     assert rel(host(plan.apply_adjoint(u)), E.apply_adjoint(pr.u, pr.w, pr.h)) < TOL

@@ -84,7 +84,8 @@ def test_batch_entry_points_reject_bad_arguments_without_a_gpu(lib):
     assert L.pce_batch_launch(None, None) == lib.PCE_ERR_INVALID
     assert L.pce_batch_destroy(None) == lib.PCE_OK
     assert L.pce_plan_autotune(None, 4, None, None) == lib.PCE_ERR_INVALID
-    assert L.pce_plan_tuning(None, None, None, None) == lib.PCE_ERR_INVALID
+    assert L.pce_plan_tuning(None, None, None, None, None) == lib.PCE_ERR_INVALID
+    assert L.pce_plan_tuning_log(None, 0, None, None, None, None) == 0
 
 
 def test_batch_mix_is_seeded_and_uneven():

@@ -71,3 +71,38 @@ def test_workload_shapes_and_determinism():
     assert p.u.dtype == np.float32
     r = synth.problem_1d(128, 8, 3, 0)
     assert r.w.shape == (8, 128) and r.u.shape == (3, 128)
+
+
+def test_d4_filter_closed_form_properties():
+    """Daubechies D4: sum sqrt(2), unit norm, orthogonal to its even shifts, two vanishing moments."""
+    h = synth.D4_FILTER
+    assert abs(h.sum() - np.sqrt(2.0)) < 1e-15
+    assert abs((h * h).sum() - 1.0) < 1e-15
+    assert abs(h[0] * h[2] + h[1] * h[3]) < 1e-15
+    g = np.array([(-1) ** i * h[3 - i] for i in range(4)])
+    t = np.arange(4)
+    assert abs(g.sum()) < 1e-15 and abs((t * g).sum()) < 1e-14
+
+
+@pytest.mark.parametrize("n", [32, 128])
+def test_periodic_wavelet_basis_is_orthonormal_and_complete(n):
+    L = int(np.log2(n))
+    funcs = [synth.periodic_wavelet(n, 2, k, "phi") for k in range(4)]
+    for j in range(2, L):
+        funcs += [synth.periodic_wavelet(n, j, k, "psi") for k in range(2 ** j)]
+    B = np.stack(funcs)
+    assert B.shape == (n, n)
+    np.testing.assert_allclose(B @ B.T, np.eye(n), atol=1e-12)
+
+
+def test_wavelet_window_supports_shrink_with_scale():
+    """psi_{j,k} on n points is supported on 3 n / 2^j - 2 consecutive (periodic) samples."""
+    n = 256
+    for j in range(3, 8):
+        for k in (0, 2 ** j - 1):
+            f = synth.periodic_wavelet(n, j, k, "psi")
+            assert np.count_nonzero(np.abs(f) > 1e-14) == 3 * n // 2 ** j - 2
+    w, labels = synth.wavelet_windows_2d(32, 64, 2, 2)
+    assert w.shape == (16 + 16 + 64, 32, 64) and len(labels) == w.shape[0]
+    pr = synth.wavelet_problem((64,), 2, 3, 2, 9)
+    assert pr.w.shape == (4 + 4 + 8 + 16, 64) and pr.u.shape == (2, 64)
