@@ -44,13 +44,49 @@ FP32_LANES_PER_SM = 128
 
 # ------------------------------------------------------------- algorithmic work
 
-def work_model(pr: synth.Problem, boxes, nb: int) -> dict:
+def cyclic_extent(flags) -> tuple[int, int]:
+    """(start, length) of the shortest periodic interval holding every set flag."""
+    n = len(flags)
+    if not np.any(flags):
+        return 0, 0
+    if np.all(flags):
+        return 0, n
+    best = run = 0
+    best_end = 0
+    for t in range(2 * n):
+        if not flags[t % n]:
+            run += 1
+            if run > best and run <= n:
+                best, best_end = run, t
+        else:
+            run = 0
+    return (best_end + 1) % n, n - best
+
+
+def slot_boxes(wy: np.ndarray, wx: np.ndarray) -> list:
+    """Boxes (r0, nr, c0, nc) of the row-transform slots of a separable plan: one
+    per distinct column factor, rows = union of its terms' row supports."""
+    slots = {}
+    for k in range(wy.shape[0]):
+        slots.setdefault(wx[k].tobytes(), []).append(k)
+    out = []
+    for key, ks in slots.items():
+        rows = np.any(wy[ks] != 0, axis=0)
+        r0, nr = cyclic_extent(rows)
+        c0, nc = cyclic_extent(wx[ks[0]] != 0)
+        out.append((r0, nr, c0, nc))
+    return out
+
+
+def work_model(pr: synth.Problem, boxes, nb: int, slots=None) -> dict:
     """Algorithmic flops and bytes per launch of each kernel kind for a chunk of nb right-hand sides.
 
     Flops are the nominal FFT counts (5 N log2 N per complex N-point FFT,
     2.5 N log2 N per real one), 8 per complex multiply-add, 1 per window
     multiply.  Bytes are the compulsory global traffic of the kernel: its
-    inputs read once and its outputs written once.
+    inputs read once and its outputs written once.  With `slots` (separable
+    windows) the row passes transform one row set per slot instead of one per
+    term, the column passes multiply by the row factors.
     """
     if len(pr.shape) == 1:
         n = pr.shape[0]
@@ -71,6 +107,20 @@ def work_model(pr: synth.Problem, boxes, nb: int) -> dict:
     zbytes = nb * rows * nxh * 8
     abytes = nb * ny * nxh * 8
     ubytes = nb * ny * nx * 4
+    if slots:
+        srows = sum(b[1] for b in slots)
+        spx = sum(b[1] * b[3] for b in slots)
+        sbytes = nb * srows * nxh * 8
+        wcols = sum(b[3] for b in slots) * 4
+        cfl = nb * ((m + 1) * (nxh + 1) * f_col + m * 8 * ny * (nxh + 1) + rows * (nxh + 1) * 2)
+        return {
+            "rows_r2c_window": (nb * (srows * f_row_r2c + spx), ubytes + wcols + sbytes),
+            "cols_fwd": (cfl, sbytes + hbytes + abytes + m * ny * 4),
+            "rows_c2r": (nb * ny * f_row_r2c, abytes + ubytes),
+            "rows_r2c": (nb * ny * f_row_r2c, ubytes + abytes),
+            "cols_adj": (cfl, abytes + hbytes + sbytes + m * ny * 4),
+            "rows_adj": (nb * (srows * f_row_r2c + spx), sbytes + wcols + ubytes),
+        }
     return {
         "rows_r2c_window": (nb * (rows * f_row_r2c + box_px), ubytes + box_px * 4 + zbytes),
         "cols_fwd": (nb * ((m + 1) * (nxh + 1) * f_col + m * 8 * ny * (nxh + 1)),
@@ -294,7 +344,19 @@ def gpu_arm(args, pr: synth.Problem, rank: int, world: int) -> None:
     w = torch.from_numpy(pr.w).to(dev)
     h = torch.from_numpy(pr.h).to(dev)
     u = torch.from_numpy(pr.u).to(dev)
-    plan = Plan(w, h=h)
+    windows = "dense (pce_plan_create)"
+    plan = None
+    slots = None
+    if len(pr.shape) == 2 and "grid" in pr.meta:
+        # the node-grid hats are tensor products: give the plan their factors
+        wy_np, wx_np = synth.hat_factors_2d(pr.shape[0], pr.shape[1], *pr.meta["grid"])
+        if np.array_equal(np.einsum("kr,kc->krc", wy_np, wx_np), pr.w):
+            plan = Plan(wy=torch.from_numpy(wy_np).to(dev), wx=torch.from_numpy(wx_np).to(dev), h=h)
+            windows = f"tensor-product hats (pce_plan_create_separable, {plan.slots()} column-factor slots)"
+            if plan.slots():
+                slots = slot_boxes(wy_np, wx_np)
+    if plan is None:
+        plan = Plan(w, h=h)
     tuning = None
     if args.autotune:
         chunk, variant, rvariant, ms = plan.autotune(pr.batch, args.tuning_cache)
@@ -415,7 +477,7 @@ def gpu_arm(args, pr: synth.Problem, rank: int, world: int) -> None:
         hbm_src = "measured" if hbm_peak else "fallback"
         hbm_peak = hbm_peak or 6800.0
         chunk = plan_chunk(plan, B)
-        model = work_model(pr, boxes, chunk)
+        model = work_model(pr, boxes, chunk, slots)
         kernels = {}
         for name, (ms, n) in kern.items():
             fl, by = model.get(name, (0.0, 0.0))
@@ -440,6 +502,7 @@ def gpu_arm(args, pr: synth.Problem, rank: int, world: int) -> None:
             "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": pr.name, "shape": list(pr.shape), "m": pr.m, "batch_per_gpu": B,
+                       "windows": windows,
                        "global_batch": B * world, "parallelism": f"replicas x{world}",
                        "l2": "flushed between timed steps (256 MB write, outside the step events)",
                        "step": "forward + adjoint apply of the batch, as one CUDA-graph launch "

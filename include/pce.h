@@ -141,6 +141,35 @@ pce_status pce_plan_create_from_spectra(pce_plan_t* out, int ndims, const int64_
                                         void* stream);
 
 /*
+ * pce_plan_create_separable -- a 2D plan whose windows are tensor products,
+ * w_k[r][c] = wy[k][r] * wx[k][c] (the tensor-product B-spline windows of the
+ * paper's 2D examples, e.g. bilinear hats on a node grid).
+ *
+ *   shape : [2] = (Ny, Nx).
+ *   wy    : device, [m][Ny] float32 row factors.
+ *   wx    : device, [m][Nx] float32 column factors.
+ *   h, flags, stream : as for pce_plan_create (hhat for the _from_spectra form).
+ *
+ * The operator is exactly that of pce_plan_create with w_k = wy_k (x) wx_k
+ * (the plan also builds everything the general path needs).  For Ny = 1024
+ * with FP32 storage and the fused kernels, applies take a faster path: terms
+ * whose column factors are bitwise equal share one set of row transforms,
+ * since R2C_x(wy_k(y) wx_j(x) u) = wy_k(y) R2C_x(wx_j u): the forward row
+ * pass transforms one row set per distinct column factor instead of one per
+ * term, the column pass applies wy_k on load, and the adjoint column pass
+ * sums wy_k . Q_k per column factor before the single row pass over those
+ * sums.  Results agree with the general path up to rounding order.
+ * pce_plan_slots returns the number of distinct column factors when the fast
+ * path is on, 0 otherwise.  The inputs may be freed after the call returns.
+ */
+pce_status pce_plan_create_separable(pce_plan_t* out, const int64_t* shape, int m, const float* wy,
+                                     const float* wx, const float* h, uint32_t flags, void* stream);
+pce_status pce_plan_create_separable_from_spectra(pce_plan_t* out, const int64_t* shape, int m,
+                                                  const float* wy, const float* wx, const float* hhat,
+                                                  uint32_t flags, void* stream);
+int pce_plan_slots(pce_plan_t plan);
+
+/*
  * pce_apply -- y = H_m u for `batch` right-hand sides (Eq. 1.4).
  *
  *   u : device, [batch][shape] float32 input.

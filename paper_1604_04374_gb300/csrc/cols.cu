@@ -43,6 +43,12 @@ cudaError_t prepare_cols() {
         e = cudaFuncSetAttribute(kw_cols_adj<false, __half2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  kWColSmem);
     if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kw_cols_fwd<float2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kWColSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kw_cols_adj<false, float2, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kWColSmem);
+    if (e == cudaSuccess)
         e = cudaFuncSetAttribute(kw_cols_adj<true, float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  kWColSmem);
 #define X(N)                                                                                   \
@@ -175,6 +181,28 @@ cudaError_t launch_plain_cols_inv(int ny, dim3 grid, cudaStream_t s, const float
         default:
             return cudaErrorInvalidValue;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cols_fwd_sep(dim3 grid, cudaStream_t s, const float2* Z, long long z_bstride,
+                                long long z_kstride, const float2* hhT, const float2* hN, int m,
+                                const Box* box, int nxh, float2* A, long long a_bstride,
+                                const float2* tw1024, int* status, long long wait_limit, int skip_copy,
+                                const SepTerms& sep) {
+    kw_cols_fwd<float2, true><<<grid, kWColWarps * 32, kWColSmem, s>>>(
+        Z, z_bstride, z_kstride, hhT, hN, nullptr, m, box, nxh, A, a_bstride, tw1024, status, wait_limit,
+        skip_copy, sep);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cols_adj_sep(dim3 grid, cudaStream_t s, const float2* V, long long v_bstride,
+                                const float2* hhT, const float2* hN, int m, const Box* box, int nxh,
+                                float2* Q, long long q_bstride, long long q_kstride,
+                                const float2* tw1024, int* status, long long wait_limit, int skip_copy,
+                                const SepTerms& sep) {
+    kw_cols_adj<false, float2, true><<<grid, kWColWarps * 32, kWColSmem, s>>>(
+        V, v_bstride, hhT, hN, nullptr, m, box, nxh, Q, q_bstride, q_kstride, tw1024, status, wait_limit,
+        skip_copy, sep);
     return cudaGetLastError();
 }
 

@@ -35,6 +35,15 @@ struct Box {          // periodic support box of w_k and its compacted copy
     int pad_;
 };
 
+// Separable windows w_k = wy_k (x) wx_k: terms sharing the column factor wx
+// share one slot of row spectra R_j = R2C_x(wx_j . u) (rows of the slot box).
+struct SepTerms {
+    const float* wrow = nullptr;   // [m][Ny] row factors wy_k
+    const int* kslot = nullptr;    // [m] slot of every term
+    const int* korder = nullptr;   // [nterms] the terms to run, grouped by slot
+    int nterms = 0;
+};
+
 // i mod n for a power of two n (two's complement: also for negative i)
 __device__ __forceinline__ int wrap(int i, int n) { return i & (n - 1); }
 

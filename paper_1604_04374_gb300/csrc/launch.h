@@ -8,6 +8,7 @@
 namespace pce {
 
 struct Box;
+struct SepTerms;
 
 // Shared-memory bytes and threads of the column kernels for a column length.
 int cols_threads(int ny);
@@ -61,6 +62,19 @@ cudaError_t launch_cols_spec(int ny, dim3 grid, cudaStream_t s, const float2* S,
 
 cudaError_t launch_plain_cols_inv(int ny, dim3 grid, cudaStream_t s, const float2* acc,
                                   const float2* accN, int nxh, float2* A, const float2* tw);
+
+// Separable windows, Ny = 1024 (one-warp column kernels): Z / Q hold one slot
+// per column factor, box[] is indexed by slot.
+cudaError_t launch_cols_fwd_sep(dim3 grid, cudaStream_t s, const float2* Z, long long z_bstride,
+                                long long z_kstride, const float2* hhT, const float2* hN, int m,
+                                const Box* box, int nxh, float2* A, long long a_bstride,
+                                const float2* tw1024, int* status, long long wait_limit, int skip_copy,
+                                const SepTerms& sep);
+cudaError_t launch_cols_adj_sep(dim3 grid, cudaStream_t s, const float2* V, long long v_bstride,
+                                const float2* hhT, const float2* hN, int m, const Box* box, int nxh,
+                                float2* Q, long long q_bstride, long long q_kstride,
+                                const float2* tw1024, int* status, long long wait_limit, int skip_copy,
+                                const SepTerms& sep);
 
 cudaError_t launch_cols_adj_full(int ny, dim3 grid, cudaStream_t s, const float2* V, long long v_bstride,
                                  const float2* hh, const float2* hN, int m, const Box* box, int nxh,

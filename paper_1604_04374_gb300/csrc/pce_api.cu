@@ -802,6 +802,118 @@ pce_status create_common(pce_plan_t* out, int ndims, const int64_t* shape, int m
     return PCE_OK;
 }
 
+// w[k][r][c] = wy[k][r] * wx[k][c]
+__global__ void k_outer(const float* __restrict__ wy, const float* __restrict__ wx, int m, int ny, int nx,
+                        float* w) {
+    const long long total = (long long)m * ny * nx;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long k = i / ((long long)ny * nx);
+        const long long e = i % ((long long)ny * nx);
+        w[i] = wy[k * ny + e / nx] * wx[k * nx + e % nx];
+    }
+}
+
+// Slots of the separable fast path: one per distinct column factor (bitwise),
+// its column box, the union of its terms' row supports, the work lists of the
+// row passes over the slots, and the term order grouped by slot.  Only for
+// Ny = 1024 with FP32 storage; otherwise the plan keeps the general path.
+pce_status setup_separable(pce_plan* p, const float* wy, const float* wx, cudaStream_t s) {
+    const int m = p->m, ny = p->ny, nx = p->nx;
+    if (p->ndims != 2 || ny != 1024 || p->lowp || (p->flags & PCE_FLAG_UNFUSED)) return PCE_OK;
+    std::vector<float> hy((size_t)m * ny), hx((size_t)m * nx);
+    PCE_CK(cudaMemcpyAsync(hy.data(), wy, sizeof(float) * hy.size(), cudaMemcpyDeviceToHost, s));
+    PCE_CK(cudaMemcpyAsync(hx.data(), wx, sizeof(float) * hx.size(), cudaMemcpyDeviceToHost, s));
+    PCE_CK(cudaStreamSynchronize(s));
+    std::vector<int> kslot(m, -1), rep;   // rep[j]: first term of slot j
+    for (int k = 0; k < m; ++k) {
+        for (size_t j = 0; j < rep.size(); ++j)
+            if (std::memcmp(&hx[(size_t)k * nx], &hx[(size_t)rep[j] * nx], sizeof(float) * nx) == 0) {
+                kslot[k] = (int)j;
+                break;
+            }
+        if (kslot[k] < 0) {
+            kslot[k] = (int)rep.size();
+            rep.push_back(k);
+        }
+    }
+    const int ns = (int)rep.size();
+    std::vector<int> korder;
+    for (int j = 0; j < ns; ++j)
+        for (int k = 0; k < m; ++k)
+            if (kslot[k] == j && p->box[k].nr > 0) korder.push_back(k);
+    std::vector<Box> vbox(ns);
+    std::vector<float> wxb;
+    int nrmax = 0;
+    for (int j = 0; j < ns; ++j) {
+        std::vector<unsigned char> rf(ny, 0), cf(nx, 0);
+        for (int k : korder)
+            if (kslot[k] == j)
+                for (int r = 0; r < ny; ++r) rf[r] |= hy[(size_t)k * ny + r] != 0.f;
+        for (int c = 0; c < nx; ++c) cf[c] = hx[(size_t)rep[j] * nx + c] != 0.f;
+        Box b{};
+        cyclic_support(rf.data(), ny, b.r0, b.nr);
+        cyclic_support(cf.data(), nx, b.c0, b.nc);
+        if (b.nr == 0 || b.nc == 0) { b.nr = 0; b.nc = 0; }
+        b.ldw = 0;   // every row reads the same column factor
+        b.woff = (long long)wxb.size();
+        for (int i = 0; i < b.nc; ++i) wxb.push_back(hx[(size_t)rep[j] * nx + (b.c0 + i) % nx]);
+        while (wxb.size() % 4) wxb.push_back(0.f);
+        vbox[j] = b;
+        nrmax = std::max(nrmax, b.nr);
+    }
+    const long long nxh = nx / 2;
+    const long long zk = (long long)nrmax * nxh;
+    if ((long long)ns * zk > p->zalloc) return PCE_OK;   // the general scratch does not hold the slots
+    std::vector<int2> items;
+    for (int j = 0; j < ns; ++j)
+        for (int q = 0; q < (vbox[j].nr + 1) / 2; ++q) items.push_back(make_int2(j, q));
+    const int npairs = (ny + 1) / 2;
+    std::vector<int> kptr(npairs + 1, 0), klist;
+    for (int q = 0; q < npairs; ++q) {
+        for (int j = 0; j < ns; ++j) {
+            const Box& b = vbox[j];
+            if (b.nr == 0) continue;
+            bool hit = false;
+            for (int g = 2 * q; g < std::min(2 * q + 2, ny); ++g) {
+                int i = g - b.r0;
+                if (i < 0) i += ny;
+                if (i < b.nr) hit = true;
+            }
+            if (hit) klist.push_back(j);
+        }
+        kptr[q + 1] = (int)klist.size();
+    }
+    pce_status st;
+    if ((st = dev_alloc(&p->wrow, hy.size()))) return st;
+    if ((st = dev_alloc(&p->wxbox, std::max<size_t>(wxb.size(), 4)))) return st;
+    if ((st = dev_alloc(&p->d_vbox, (size_t)ns))) return st;
+    if ((st = dev_alloc(&p->d_kslot, (size_t)m))) return st;
+    if ((st = dev_alloc(&p->d_korder, std::max<size_t>(korder.size(), 1)))) return st;
+    if ((st = dev_alloc(&p->sitems, std::max<size_t>(items.size(), 1)))) return st;
+    if ((st = dev_alloc(&p->skptr, kptr.size()))) return st;
+    if ((st = dev_alloc(&p->sklist, std::max<size_t>(klist.size(), 1)))) return st;
+    PCE_CK(cudaMemcpyAsync(p->wrow, hy.data(), sizeof(float) * hy.size(), cudaMemcpyHostToDevice, s));
+    if (!wxb.empty())
+        PCE_CK(cudaMemcpyAsync(p->wxbox, wxb.data(), sizeof(float) * wxb.size(), cudaMemcpyHostToDevice, s));
+    PCE_CK(cudaMemcpyAsync(p->d_vbox, vbox.data(), sizeof(Box) * ns, cudaMemcpyHostToDevice, s));
+    PCE_CK(cudaMemcpyAsync(p->d_kslot, kslot.data(), sizeof(int) * m, cudaMemcpyHostToDevice, s));
+    if (!korder.empty())
+        PCE_CK(cudaMemcpyAsync(p->d_korder, korder.data(), sizeof(int) * korder.size(), cudaMemcpyHostToDevice, s));
+    if (!items.empty())
+        PCE_CK(cudaMemcpyAsync(p->sitems, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice, s));
+    PCE_CK(cudaMemcpyAsync(p->skptr, kptr.data(), sizeof(int) * kptr.size(), cudaMemcpyHostToDevice, s));
+    if (!klist.empty())
+        PCE_CK(cudaMemcpyAsync(p->sklist, klist.data(), sizeof(int) * klist.size(), cudaMemcpyHostToDevice, s));
+    PCE_CK(cudaStreamSynchronize(s));   // the host vectors die at return
+    p->nslots = ns;
+    p->nterms = (int)korder.size();
+    p->nsitems = (int)items.size();
+    p->zk_s = zk;
+    p->sep = true;
+    return PCE_OK;
+}
+
 pce_status check_io(pce_plan_t p, const float* in, const float* out, int64_t batch) {
     if (batch < 0) return fail(PCE_ERR_INVALID, "batch must be >= 0");
     if (batch == 0) return PCE_OK;
@@ -1056,6 +1168,13 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
     if (p->flags & PCE_FLAG_UNFUSED) return apply_plain(p, in, out, batch, adjoint, s);
     const bool warp = (scr.col_variant >= 0 ? scr.col_variant : p->col_variant) == 0;
     const int rowv = scr.row_variant >= 0 ? scr.row_variant : p->row_variant;
+    // separable fast path: one-warp column kernels only
+    const bool sepx = p->sep && warp;
+    pce::SepTerms sept;
+    sept.wrow = p->wrow;
+    sept.kslot = p->d_kslot;
+    sept.korder = p->d_korder;
+    sept.nterms = p->nterms;
     const long long zk = (long long)p->nrmax * nxh;
     const long long zb = scr.zstride;
     const long long ab = scr.astride;
@@ -1066,7 +1185,43 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
         const int nb = (int)std::min<long long>(scr.chunk, batch - b0);
         const float* src = in + b0 * P;
         float* dst = out + b0 * P;
-        if (!adjoint) {
+        if (sepx && !adjoint) {
+            if (p->nsitems > 0)
+                e = timed(p, PCE_KERNEL_ROWS_R2C_WINDOW, s, [&] {
+                    return pce::launch_rows_r2c(nx, true, dim3(r2c_blocks(p->nsitems, nx), nb), s, src, P, ny,
+                                                p->wxbox, false, p->d_vbox, p->sitems, p->nsitems, scr.Z, zb,
+                                                p->zk_s, p->twx, p->tw1024);
+                });
+            if (e == cudaSuccess)
+                e = timed(p, PCE_KERNEL_COLS_FWD, s, [&] {
+                    return pce::launch_cols_fwd_sep(dim3(nb, (nxh + cpc - 1) / cpc), s, scr.Z, zb, p->zk_s,
+                                                    p->hhT, p->hN, m, p->d_vbox, nxh, scr.A, ab, p->tw1024,
+                                                    p->d_status, p->wait_limit, p->skip_copy, sept);
+                });
+            if (e == cudaSuccess)
+                e = timed(p, PCE_KERNEL_ROWS_C2R, s, [&] {
+                    return pce::launch_rows_c2r(nx, dim3((npairs + fpc - 1) / fpc, nb), s, scr.A, ab,
+                                                ny, dst, P, scale, p->twx, p->tw1024);
+                });
+        } else if (sepx) {
+            e = timed(p, PCE_KERNEL_ROWS_R2C, s, [&] {
+                return pce::launch_rows_r2c(nx, false, dim3(r2c_blocks(npairs, nx), nb), s, src, P,
+                                            ny, nullptr, false, nullptr, nullptr, npairs, scr.A, ab, 0,
+                                            p->twx, p->tw1024);
+            });
+            if (e == cudaSuccess)
+                e = timed(p, PCE_KERNEL_COLS_ADJ, s, [&] {
+                    return pce::launch_cols_adj_sep(dim3(nb, (nxh + cpc - 1) / cpc), s, scr.A, ab, p->hhT, p->hN,
+                                                    m, p->d_vbox, nxh, scr.Z, zb, p->zk_s, p->tw1024,
+                                                    p->d_status, p->wait_limit, p->skip_copy, sept);
+                });
+            if (e == cudaSuccess)
+                e = timed(p, PCE_KERNEL_ROWS_ADJ, s, [&] {
+                    return pce::launch_rows_adj(nx, dim3((npairs + fpc - 1) / fpc, nb), s, scr.Z, zb,
+                                                p->zk_s, ny, p->wxbox, false, p->d_vbox, p->skptr, p->sklist,
+                                                dst, P, scale, p->twx, p->tw1024, rowv);
+                });
+        } else if (!adjoint) {
             if (p->nitems > 0)
                 e = timed(p, PCE_KERNEL_ROWS_R2C_WINDOW, s, [&] {
                     return pce::launch_rows_r2c(nx, true, dim3(r2c_blocks(p->nitems, nx), nb), s, src,
@@ -1120,6 +1275,57 @@ pce_status pce_plan_create_from_spectra(pce_plan_t* out, int ndims, const int64_
                                         void* stream) {
     return create_common(out, ndims, shape, m, w, hhat, true, flags, stream);
 }
+
+}  // extern "C"
+
+namespace {
+
+pce_status create_separable(pce_plan_t* out, const int64_t* shape, int m, const float* wy, const float* wx,
+                            const float* h, bool spectra, uint32_t flags, void* stream) {
+    if (!out) return fail(PCE_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    int ny = 1, nx = 0;
+    pce_status st = validate_shape(2, shape, ny, nx);
+    if (st) return st;
+    if (m < 1) return fail(PCE_ERR_INVALID, "m must be >= 1 (got %d)", m);
+    if (!is_device_ptr(wy) || !is_device_ptr(wx))
+        return fail(PCE_ERR_INVALID, "wy and wx must be device pointers");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    float* w = nullptr;
+    if ((st = dev_alloc(&w, (size_t)m * ny * nx))) return st;
+    k_outer<<<grid_for((long long)m * ny * nx), 256, 0, s>>>(wy, wx, m, ny, nx, w);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        cudaFree(w);
+        return fail(PCE_ERR_CUDA, "window outer products: %s", cudaGetErrorString(e));
+    }
+    st = create_common(out, 2, shape, m, w, h, spectra, flags, stream);
+    cudaFree(w);
+    if (st) return st;
+    if ((st = setup_separable(*out, wy, wx, s))) {
+        delete *out;
+        *out = nullptr;
+        return st;
+    }
+    return PCE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pce_status pce_plan_create_separable(pce_plan_t* out, const int64_t* shape, int m, const float* wy,
+                                     const float* wx, const float* h, uint32_t flags, void* stream) {
+    return create_separable(out, shape, m, wy, wx, h, false, flags, stream);
+}
+
+pce_status pce_plan_create_separable_from_spectra(pce_plan_t* out, const int64_t* shape, int m,
+                                                  const float* wy, const float* wx, const float* hhat,
+                                                  uint32_t flags, void* stream) {
+    return create_separable(out, shape, m, wy, wx, hhat, true, flags, stream);
+}
+
+int pce_plan_slots(pce_plan_t plan) { return (plan && plan->sep) ? plan->nslots : 0; }
 
 pce_status pce_apply(pce_plan_t plan, const float* u, float* y, int64_t batch, void* stream) {
     pce_status st = check_plan(plan);

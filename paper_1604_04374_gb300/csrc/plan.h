@@ -62,6 +62,21 @@ struct pce_plan {
     std::vector<double> tune_log;   // (chunk, col variant, row variant, ms per apply) per timed candidate
     long long zalloc = 0;   // Z scratch per right-hand side (float2)
     long long scratch_bytes = 0;
+    // separable windows w_k = wy_k (x) wx_k (pce_plan_create_separable), Ny = 1024:
+    // one slot of row spectra per distinct column factor
+    bool sep = false;
+    int nslots = 0;
+    float* wrow = nullptr;      // [m][ny] row factors
+    float* wxbox = nullptr;     // column factors of the slots on their column boxes
+    Box* d_vbox = nullptr;      // [nslots] slot boxes (rows: union of the slot's row supports; ldw 0)
+    int* d_kslot = nullptr;     // [m]
+    int* d_korder = nullptr;    // [nterms] active terms grouped by slot
+    int nterms = 0;
+    int2* sitems = nullptr;     // F1 items of the slots
+    int nsitems = 0;
+    int* skptr = nullptr;       // G3 lists of the slots
+    int* sklist = nullptr;
+    long long zk_s = 0;         // float2 per slot (rows of the largest slot box x nx/2)
     // per-kernel timing
     bool timing = false;
     std::vector<cudaEvent_t> ev;          // pairs (start, stop)
@@ -79,7 +94,7 @@ struct pce_plan {
         drop_events();
         void* ptrs[] = {d_box,  wbox,  hh,     hN,   hhT,   tw1024, d_status, twx, twy == twx ? nullptr : twy,
                         items,  kptr,  klist,  scrZ, scrA,  wbox16, hh16,     hN16, hhT16, hscale,
-                        twN,    hh4};
+                        twN,    hh4,   wrow, wxbox, d_vbox, d_kslot, d_korder, sitems, skptr, sklist};
         for (void* q : ptrs)
             if (q) cudaFree(q);
     }

@@ -87,7 +87,10 @@ struct NoHook {
 // shared memory private to the calling warp.  All 32 lanes must call it.
 // hook() runs once the transpose has been read back, i.e. when the tile is
 // free again (it may start an asynchronous copy into the tile).
-template <bool INV, typename Hook = NoHook>
+// SPLIT: the twiddles W1024^{l p} come from ten table loads and products (fewer
+// loads in flight, more multiplies); otherwise from 31 table loads.  Which one
+// is faster depends on the register pressure of the calling kernel.
+template <bool INV, bool SPLIT = true, typename Hook = NoHook>
 __device__ __forceinline__ void warp_fft1024(float2 (&v)[32], float2* tile, const float2* __restrict__ tw,
                                              Hook hook = Hook()) {
     const int lane = threadIdx.x & 31;
@@ -95,10 +98,26 @@ __device__ __forceinline__ void warp_fft1024(float2 (&v)[32], float2* tile, cons
     // keep the twiddle loads after the first DFT: hoisted above it they would
     // hold 62 more registers through it
     __syncwarp();
+    if constexpr (SPLIT) {
+        // W1024^{l p} with p = 8 a + b is W1024^{8 l a} W1024^{l b}: ten table
+        // loads issued together, then products (two roundings at most)
+        float2 wb[8], wa[4];
 #pragma unroll
-    for (int p = 1; p < 32; ++p) {
-        const float2 t = __ldg(&tw[p * 32 + lane]);
-        v[p] = INV ? cmulc(v[p], t) : cmul(v[p], t);
+        for (int q = 1; q < 8; ++q) wb[q] = __ldg(&tw[q * 32 + lane]);
+#pragma unroll
+        for (int q = 1; q < 4; ++q) wa[q] = __ldg(&tw[8 * q * 32 + lane]);
+#pragma unroll
+        for (int p = 1; p < 32; ++p) {
+            const int a = p >> 3, bq = p & 7;
+            const float2 t = a == 0 ? wb[bq] : (bq == 0 ? wa[a] : cmul(wa[a], wb[bq]));
+            v[p] = INV ? cmulc(v[p], t) : cmul(v[p], t);
+        }
+    } else {
+#pragma unroll
+        for (int p = 1; p < 32; ++p) {
+            const float2 t = __ldg(&tw[p * 32 + lane]);
+            v[p] = INV ? cmulc(v[p], t) : cmul(v[p], t);
+        }
     }
     __syncwarp();
 #pragma unroll

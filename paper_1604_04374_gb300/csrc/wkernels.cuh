@@ -98,12 +98,17 @@ __device__ __forceinline__ void warp_split(const float2 (&v)[32], int lane, int 
 // F2 for Ny = 1024.  Grid (batch, NXh / 4), 128 threads, kWColSmem bytes.
 // hhT: [m][NXh][1024] (column c's spectrum contiguous; c = 0: DC column),
 // hN: [m][1024] (Nyquist column).
-template <typename HT = float2>
+// SEP = false: Z holds one slot per term (box[k] rows of w_k . u's row spectra).
+// SEP = true: Z holds one slot per column factor (box[] indexed by slot), each
+// term's column is its slot's column times wy_k (row factor) on load, and a
+// slot's tile is loaded once for all of its terms.
+template <typename HT = float2, bool SEP = false>
 __global__ void __launch_bounds__(kWColWarps * 32, 3)
 kw_cols_fwd(const float2* __restrict__ Z, long long z_bstride, long long z_kstride,
             const HT* __restrict__ hhT, const HT* __restrict__ hN, const float* __restrict__ hscale, int m,
             const Box* __restrict__ box, int NXh, float2* __restrict__ A, long long a_bstride,
-            const float2* __restrict__ tw, int* __restrict__ status, long long wait_limit, int skip_copy) {
+            const float2* __restrict__ tw, int* __restrict__ status, long long wait_limit, int skip_copy,
+            SepTerms sep = SepTerms{}) {
     constexpr int NY = kWarpN;
     extern __shared__ float2 smem[];
     float2* tile = smem;
@@ -125,23 +130,54 @@ kw_cols_fwd(const float2* __restrict__ Z, long long z_bstride, long long z_kstri
     float2 acc[32];
 #pragma unroll
     for (int i = 0; i < 32; ++i) acc[i] = make_float2(0.f, 0.f);
-    int k = 0;
-    while (k < m && box[k].nr == 0) ++k;
-    if (k < m) tile_load(tile, Zb + k * z_kstride, box[k].nr, NXh, col0);
-    while (k < m) {
-        int kn = k + 1;
-        while (kn < m && box[kn].nr == 0) ++kn;
-        const Box bx = box[k];
-        cp_async_wait_all();
-        __syncthreads();
-        float2 v[32];
-#pragma unroll
-        for (int q = 0; q < 32; ++q) {
-            const int i = wrap(lane + 32 * q - bx.r0, NY);
-            v[q] = (i < bx.nr) ? tile[i * kTileStride + warp] : make_float2(0.f, 0.f);
+    // the sequence of terms: general, every term with a nonempty box in index
+    // order (slot = term); separable, sep.korder (slot = sep.kslot[term])
+    const int tend = SEP ? sep.nterms : m;
+    auto next_t = [&](int t) {
+        if constexpr (!SEP) {
+            while (t < m && box[t].nr == 0) ++t;
         }
-        __syncthreads();
-        if (kn < m) tile_load(tile, Zb + kn * z_kstride, box[kn].nr, NXh, col0);
+        return t;
+    };
+    auto kof = [&](int t) { return SEP ? __ldg(&sep.korder[t]) : t; };
+    auto slot_of = [&](int kk) { return SEP ? __ldg(&sep.kslot[kk]) : kk; };
+    int t = next_t(0);
+    int cur_slot = -1;
+    if (t < tend) {
+        const int s0 = slot_of(kof(t));
+        tile_load(tile, Zb + s0 * z_kstride, box[s0].nr, NXh, col0);
+    }
+    while (t < tend) {
+        const int k = kof(t);
+        const int sl = slot_of(k);
+        const int tn = next_t(t + 1);
+        const int sn = tn < tend ? slot_of(kof(tn)) : -1;
+        const Box bx = box[sl];
+        if (sl != cur_slot) {   // uniform over the CTA
+            cp_async_wait_all();
+            __syncthreads();
+            cur_slot = sl;
+        }
+        float2 v[32];
+        if constexpr (SEP) {
+            const float* wr = sep.wrow + (long long)k * NY;
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+                const int i = wrap(lane + 32 * q - bx.r0, NY);
+                v[q] = (i < bx.nr) ? cscale(tile[i * kTileStride + warp], __ldg(&wr[lane + 32 * q]))
+                                   : make_float2(0.f, 0.f);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+                const int i = wrap(lane + 32 * q - bx.r0, NY);
+                v[q] = (i < bx.nr) ? tile[i * kTileStride + warp] : make_float2(0.f, 0.f);
+            }
+        }
+        if (tn < tend && sn != sl) {   // the next term needs another slot: reload the tile
+            __syncthreads();
+            tile_load(tile, Zb + sn * z_kstride, box[sn].nr, NXh, col0);
+        }
         // this column's spectrum of term k arrives in the warp's transpose
         // tile while the FFT finishes
         const bool bulk = !dcn && cv && !failed;
@@ -179,7 +215,7 @@ kw_cols_fwd(const float2* __restrict__ Z, long long z_bstride, long long z_kstri
 #pragma unroll
             for (int mm = 0; mm < 32; ++mm) acc[mm] = cfma(lds_h(&th[lane + 32 * mm], sk), v[mm], acc[mm]);
         }
-        k = kn;
+        t = tn;
     }
     warp_fft1024<true>(acc, tr, tw);
     __syncthreads();
@@ -195,13 +231,17 @@ kw_cols_fwd(const float2* __restrict__ Z, long long z_bstride, long long z_kstri
 
 // G1b + G2 for Ny = 1024 (FULL: every row of Q, for the window gradient).
 // Grid (batch, NXh / 4).
-template <bool FULL, typename HT = float2>
+// SEP: Q receives one slot per column factor: S_j = sum over the slot's terms of
+// wy_k . IFFT_y(conj(hhat_k) V), on the slot box rows (box[] indexed by slot),
+// accumulated in the shared tile and stored once per slot.
+template <bool FULL, typename HT = float2, bool SEP = false>
 __global__ void __launch_bounds__(kWColWarps * 32, 3)
 kw_cols_adj(const float2* __restrict__ V, long long v_bstride,
             const HT* __restrict__ hhT, const HT* __restrict__ hN, const float* __restrict__ hscale, int m,
             const Box* __restrict__ box, int NXh,
             float2* __restrict__ Q, long long q_bstride, long long q_kstride,
-            const float2* __restrict__ tw, int* __restrict__ status, long long wait_limit, int skip_copy) {
+            const float2* __restrict__ tw, int* __restrict__ status, long long wait_limit, int skip_copy,
+            SepTerms sep = SepTerms{}) {
     constexpr int NY = kWarpN;
     extern __shared__ float2 smem[];
     float2* tile = smem;
@@ -219,10 +259,16 @@ kw_cols_adj(const float2* __restrict__ V, long long v_bstride,
     unsigned parity = 0;
     bool failed = false;
     const bool use_bulk = !dcn && cv;
-    auto next_term = [&](int k) {
-        while (k < m && !FULL && box[k].nr == 0) ++k;
-        return k;
+    // the sequence of terms (see kw_cols_fwd)
+    const int tend = SEP ? sep.nterms : m;
+    auto next_t = [&](int t) {
+        if constexpr (!SEP) {
+            while (t < m && !FULL && box[t].nr == 0) ++t;
+        }
+        return t;
     };
+    auto kof = [&](int t) { return SEP ? __ldg(&sep.korder[t]) : t; };
+    auto slot_of = [&](int kk) { return SEP ? __ldg(&sep.kslot[kk]) : kk; };
 
     tile_load(tile, V + b * v_bstride, NY, NXh, col0);
     cp_async_wait_all();
@@ -230,15 +276,22 @@ kw_cols_adj(const float2* __restrict__ V, long long v_bstride,
     float2 vv[32];
 #pragma unroll
     for (int q = 0; q < 32; ++q) vv[q] = tile[(lane + 32 * q) * kTileStride + warp];
-    int k = next_term(0);
+    int t = next_t(0);
+    int prev_slot = -1;
     // the spectrum of the first term arrives while the FFT of V finishes
-    warp_fft1024<false>(vv, tr, tw, [&] {
-        if (use_bulk && k < m && lane == 0)
-            bulk_load(tr, hhT + ((long long)k * NXh + col) * NY, NY * sizeof(HT), bar, skip_copy);
+    warp_fft1024<false, false>(vv, tr, tw, [&] {
+        if (use_bulk && t < tend && lane == 0)
+            bulk_load(tr, hhT + ((long long)kof(t) * NXh + col) * NY, NY * sizeof(HT), bar, skip_copy);
     });
-    while (k < m) {
-        const Box bx = box[k];
-        const int kn = next_term(k + 1);
+    while (t < tend) {
+        const int k = kof(t);
+        const int sl = slot_of(k);
+        const Box bx = box[sl];
+        const int tn = next_t(t + 1);
+        const int kn = tn < tend ? kof(tn) : m;
+        const bool first = sl != prev_slot;
+        const bool last = tn >= tend || slot_of(kn) != sl;
+        prev_slot = sl;
         if (use_bulk && !failed) {
             if (!mbar_wait(bar, parity, wait_limit)) {
                 failed = true;
@@ -274,23 +327,46 @@ kw_cols_adj(const float2* __restrict__ V, long long v_bstride,
                                               : make_float2(0.f, 0.f);
         }
         // the next term's spectrum arrives while this inverse FFT finishes
-        const bool issue = use_bulk && !failed && kn < m;
-        warp_fft1024<true>(p, tr, tw, [&] {
+        const bool issue = use_bulk && !failed && tn < tend;
+        warp_fft1024<true, false>(p, tr, tw, [&] {
             if (issue && lane == 0)
                 bulk_load(tr, hhT + ((long long)kn * NXh + col) * NY, NY * sizeof(HT), bar, skip_copy);
         });
-        __syncthreads();
+        if constexpr (SEP) {
+            // accumulate wy_k . p into this warp's column of the tile; the previous
+            // slot's store must have finished reading the tile first
+            if (first) __syncthreads();
+            const float* wr = sep.wrow + (long long)k * NY;
 #pragma unroll
-        for (int mm = 0; mm < 32; ++mm) tile[(lane + 32 * mm) * kTileStride + warp] = p[mm];
-        __syncthreads();
-        float2* Qk = Q + b * q_bstride + k * q_kstride;
-        const int rows = FULL ? NY : bx.nr;
-        for (int e = threadIdx.x; e < rows * kWColWarps; e += kWColWarps * 32) {
-            const int i = e >> 2, c = e & 3;
-            const int g = FULL ? i : wrap(bx.r0 + i, NY);
-            if (col0 + c < NXh) Qk[(long long)i * NXh + col0 + c] = tile[g * kTileStride + c];
+            for (int mm = 0; mm < 32; ++mm) {
+                const int y = lane + 32 * mm;
+                const float2 val = cscale(p[mm], __ldg(&wr[y]));
+                float2* cell = &tile[y * kTileStride + warp];
+                *cell = first ? val : cadd(*cell, val);
+            }
+            if (last) {
+                __syncthreads();
+                float2* Qs = Q + b * q_bstride + sl * q_kstride;
+                for (int e = threadIdx.x; e < bx.nr * kWColWarps; e += kWColWarps * 32) {
+                    const int i = e >> 2, c = e & 3;
+                    const int g = wrap(bx.r0 + i, NY);
+                    if (col0 + c < NXh) Qs[(long long)i * NXh + col0 + c] = tile[g * kTileStride + c];
+                }
+            }
+        } else {
+            __syncthreads();
+#pragma unroll
+            for (int mm = 0; mm < 32; ++mm) tile[(lane + 32 * mm) * kTileStride + warp] = p[mm];
+            __syncthreads();
+            float2* Qk = Q + b * q_bstride + k * q_kstride;
+            const int rows = FULL ? NY : bx.nr;
+            for (int e = threadIdx.x; e < rows * kWColWarps; e += kWColWarps * 32) {
+                const int i = e >> 2, c = e & 3;
+                const int g = FULL ? i : wrap(bx.r0 + i, NY);
+                if (col0 + c < NXh) Qk[(long long)i * NXh + col0 + c] = tile[g * kTileStride + c];
+            }
         }
-        k = kn;
+        t = tn;
     }
 }
 

@@ -58,6 +58,11 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.pce_plan_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, ctypes.POINTER(i64), ctypes.c_int,
                                     P, P, ctypes.c_uint32, P]
     lib.pce_plan_create_from_spectra.argtypes = lib.pce_plan_create.argtypes
+    lib.pce_plan_create_separable.argtypes = [ctypes.POINTER(P), ctypes.POINTER(i64), ctypes.c_int, P, P, P,
+                                              ctypes.c_uint32, P]
+    lib.pce_plan_create_separable_from_spectra.argtypes = lib.pce_plan_create_separable.argtypes
+    lib.pce_plan_slots.argtypes = [P]
+    lib.pce_plan_slots.restype = ctypes.c_int
     lib.pce_apply.argtypes = [P, P, P, i64, P]
     lib.pce_apply_adjoint.argtypes = [P, P, P, i64, P]
     lib.pce_plan_info.argtypes = [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -103,7 +108,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.pce_plan_tuning_log.restype = ctypes.c_int
     for name in ("pce_plan_create", "pce_plan_create_from_spectra", "pce_apply", "pce_apply_adjoint",
                  "pce_plan_info", "pce_plan_hhat", "pce_plan_destroy", "pce_plan_set_timing",
-                 "pce_plan_timing", "pce_apply_batch", "pce_batch_create", "pce_batch_run",
+                 "pce_plan_timing", "pce_plan_create_separable", "pce_plan_create_separable_from_spectra",
+                 "pce_apply_batch", "pce_batch_create", "pce_batch_run",
                  "pce_batch_launch", "pce_batch_info", "pce_batch_destroy", "pce_schedule_lpt",
                  "pce_plan_autotune", "pce_plan_tuning", "pce_batch_autotune", "pce_batch_tuning"):
         getattr(lib, name).restype = ctypes.c_int
@@ -127,6 +133,20 @@ def pce_plan_create(ndims: int, shape, m: int, w_ptr: int, h_ptr: int, flags: in
     _check(load_library().pce_plan_create(ctypes.byref(handle), ndims, shp, m, w_ptr, h_ptr,
                                           flags, stream))
     return handle.value
+
+
+def pce_plan_create_separable(shape, m: int, wy_ptr: int, wx_ptr: int, h_ptr: int, flags: int = 0,
+                              stream: int = 0, spectra: bool = False) -> int:
+    handle = ctypes.c_void_p()
+    shp = (ctypes.c_int64 * 2)(*shape)
+    lib = load_library()
+    fn = lib.pce_plan_create_separable_from_spectra if spectra else lib.pce_plan_create_separable
+    _check(fn(ctypes.byref(handle), shp, m, wy_ptr, wx_ptr, h_ptr, flags, stream))
+    return handle.value
+
+
+def pce_plan_slots(plan: int) -> int:
+    return int(load_library().pce_plan_slots(plan))
 
 
 def pce_plan_create_from_spectra(ndims: int, shape, m: int, w_ptr: int, hhat_ptr: int,
@@ -331,8 +351,34 @@ class Plan:
     [m, N/2+1]).  ``shape`` is (N,) or (Ny, Nx).
     """
 
-    def __init__(self, w, h=None, hhat=None, stream=None, flags: int = 0):
+    def __init__(self, w=None, h=None, hhat=None, stream=None, flags: int = 0, wy=None, wx=None):
         import torch
+        if w is None:
+            # separable windows w_k = wy_k (x) wx_k
+            _need_cuda_f32(wy, "wy")
+            _need_cuda_f32(wx, "wx")
+            if wy.dim() != 2 or wx.dim() != 2 or wy.shape[0] != wx.shape[0]:
+                raise ValueError("wy must be [m, Ny] and wx [m, Nx]")
+            self.m = int(wy.shape[0])
+            self.shape = (int(wy.shape[1]), int(wx.shape[1]))
+            self.ndims = 2
+            self.device = wy.device
+            if (h is None) == (hhat is None):
+                raise ValueError("give exactly one of h and hhat")
+            src = h if h is not None else hhat
+            if h is not None:
+                _need_cuda_f32(h, "h")
+                if tuple(h.shape) != (self.m,) + self.shape:
+                    raise ValueError("h must be [m, Ny, Nx]")
+            else:
+                want = (self.m, self.shape[0], self.shape[1] // 2 + 1)
+                if hhat.dtype != torch.complex64 or tuple(hhat.shape) != want or not hhat.is_contiguous():
+                    raise ValueError(f"hhat must be a contiguous complex64 tensor of shape {want}")
+            with torch.cuda.device(self.device):
+                self.handle = pce_plan_create_separable(self.shape, self.m, wy.data_ptr(), wx.data_ptr(),
+                                                        src.data_ptr(), flags, _stream_handle(stream),
+                                                        spectra=hhat is not None)
+            return
         _need_cuda_f32(w, "w")
         self.m = int(w.shape[0])
         self.shape = tuple(int(s) for s in w.shape[1:])
@@ -386,6 +432,10 @@ class Plan:
     def info(self):
         """(m, support boxes [(r0, nr, c0, nc)], scratch bytes)."""
         return pce_plan_info(self.handle, self.m)
+
+    def slots(self) -> int:
+        """Distinct column factors when the separable fast path is on, else 0."""
+        return pce_plan_slots(self.handle)
 
     def hhat(self, stream=None):
         import torch

@@ -75,6 +75,20 @@ def hat_windows_2d(ny: int, nx: int, gy: int, gx: int) -> np.ndarray:
     return out.astype(np.float32)
 
 
+def hat_factors_2d(ny: int, nx: int, gy: int, gx: int) -> tuple[np.ndarray, np.ndarray]:
+    """Factors of the tensor-product hats: wy [m][ny], wx [m][nx] float32 with
+    hat_windows_2d(...)[k] == outer(wy[k], wx[k]) exactly (the hat values are
+    dyadic rationals, so the products are exact in float32)."""
+    m = gy * gx
+    wy = np.empty((m, ny), dtype=np.float32)
+    wx = np.empty((m, nx), dtype=np.float32)
+    for a in range(gy):
+        for c in range(gx):
+            wy[a * gx + c] = hat_1d(ny, gy, a)
+            wx[a * gx + c] = hat_1d(nx, gx, c)
+    return wy, wx
+
+
 # ------------------------------------------------------ impulse responses
 
 def sigma_1d(y: float) -> float:

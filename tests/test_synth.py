@@ -106,3 +106,11 @@ def test_wavelet_window_supports_shrink_with_scale():
     assert w.shape == (16 + 16 + 64, 32, 64) and len(labels) == w.shape[0]
     pr = synth.wavelet_problem((64,), 2, 3, 2, 9)
     assert pr.w.shape == (4 + 4 + 8 + 16, 64) and pr.u.shape == (2, 64)
+
+
+@pytest.mark.parametrize("ny,nx,gy,gx", [(1024, 1024, 4, 4), (1024, 256, 2, 4), (64, 128, 8, 4)])
+def test_hat_factors_reproduce_tensor_hats_exactly(ny, nx, gy, gx):
+    wy, wx = synth.hat_factors_2d(ny, nx, gy, gx)
+    w = synth.hat_windows_2d(ny, nx, gy, gx)
+    assert np.array_equal(np.einsum("kr,kc->krc", wy, wx), w)
+    assert np.array_equal((wy[:, :, None] * wx[:, None, :]).astype(np.float32), w)
