@@ -9,10 +9,11 @@
 //
 // One warp per half-spectrum column, 4 columns per CTA.  The
 // column data are moved between global memory and the warps through a
-// shared tile [row][kTileStride] (odd stride: a warp reading one column of
-// 16 consecutive rows hits 16 distinct bank pairs), filled with cp.async
-// 8-byte copies of 32-byte row segments; the copy of the next term's tile
-// overlaps the current term's FFT.
+// shared tile [row][4] whose column index is XOR-swizzled by (row >> 2) & 3
+// (tix): a half-warp reading one column of 16 consecutive rows, or writing
+// 4 columns of 4 rows, hits 16 distinct 8-byte bank slots.  The tile is
+// filled with cp.async 8-byte copies of 32-byte row segments; the copy of the
+// next term's tile overlaps the current term's FFT.
 #pragma once
 
 #include "kernels.cuh"
@@ -22,13 +23,25 @@ namespace pce {
 
 constexpr int kWarpN = 1024;
 constexpr int kWColWarps = 4;          // columns per CTA of the column kernels
-constexpr int kTileStride = kWColWarps + 1;
-constexpr int kWColSmem = (kWarpN * kTileStride + kWColWarps * kWarpN) * (int)sizeof(float2);
+// shared memory: the column tile, one 1024-point transpose tile per warp, and
+// two 1024-float buffers of row factors (separable windows)
+constexpr int kWColSmem = (kWarpN * kWColWarps + kWColWarps * kWarpN) * (int)sizeof(float2) +
+                          2 * kWarpN * (int)sizeof(float);
+
+// element (row, column c < 4) of the swizzled column tile
+__device__ __forceinline__ int tix(int row, int c) { return row * kWColWarps + (c ^ ((row >> 2) & 3)); }
+// A lane touches rows r0 + 32 q: (row >> 2) & 3 is the same for all of them,
+// so tix(r0 + 32 q, c) = 4 (r0 + 32 q) + sw with sw = c ^ ((r0 >> 2) & 3).
+__device__ __forceinline__ int tix_sw(int r0, int c) { return c ^ ((r0 >> 2) & 3); }
 
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool pred) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     const int sz = pred ? 8 : 0;   // src-size 0: write zeros, read nothing
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "r"(sz) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
@@ -84,9 +97,16 @@ __device__ __forceinline__ void tile_load(float2* tile, const float2* __restrict
     for (int e = threadIdx.x; e < nrows_tile * kWColWarps; e += kWColWarps * 32) {
         const int i = e >> 2, c = e & 3;
         const bool ok = col0 + c < nxh;
-        cp_async8(tile + i * kTileStride + c, src + (long long)i * nxh + (ok ? col0 + c : 0), ok);
+        cp_async8(tile + tix(i, c), src + (long long)i * nxh + (ok ? col0 + c : 0), ok);
     }
     cp_async_commit();
+}
+
+// Separable windows: cooperative async copy of row factor wy_k (1024 floats)
+// into one of the two row-factor buffers (committed with the next group).
+__device__ __forceinline__ void wy_load(float* dst, const float* __restrict__ wrow, int k) {
+    const float* src = wrow + (long long)k * kWarpN;
+    for (int e = threadIdx.x; e < kWarpN / 4; e += kWColWarps * 32) cp_async16(dst + 4 * e, src + 4 * e);
 }
 
 // The DC/Nyquist column (column 0 of tile 0): separate the FFT of
@@ -113,7 +133,7 @@ kw_cols_fwd(const float2* __restrict__ Z, long long z_bstride, long long z_kstri
     extern __shared__ float2 smem[];
     float2* tile = smem;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float2* tr = smem + NY * kTileStride + warp * kWarpN;
+    float2* tr = smem + NY * kWColWarps + warp * kWarpN;
     const int b = blockIdx.x;
     const int col0 = blockIdx.y * kWColWarps;
     const int col = col0 + warp;
@@ -141,10 +161,13 @@ kw_cols_fwd(const float2* __restrict__ Z, long long z_bstride, long long z_kstri
     };
     auto kof = [&](int t) { return SEP ? __ldg(&sep.korder[t]) : t; };
     auto slot_of = [&](int kk) { return SEP ? __ldg(&sep.kslot[kk]) : kk; };
+    // SEP: row factors of term t in buffer (t & 1), prefetched one term ahead
+    float* wys = reinterpret_cast<float*>(smem + 2 * NY * kWColWarps);
     int t = next_t(0);
     int cur_slot = -1;
     if (t < tend) {
         const int s0 = slot_of(kof(t));
+        if constexpr (SEP) wy_load(wys, sep.wrow, kof(t));
         tile_load(tile, Zb + s0 * z_kstride, box[s0].nr, NXh, col0);
     }
     while (t < tend) {
@@ -153,25 +176,24 @@ kw_cols_fwd(const float2* __restrict__ Z, long long z_bstride, long long z_kstri
         const int tn = next_t(t + 1);
         const int sn = tn < tend ? slot_of(kof(tn)) : -1;
         const Box bx = box[sl];
-        if (sl != cur_slot) {   // uniform over the CTA
+        if (SEP || sl != cur_slot) {   // uniform over the CTA
             cp_async_wait_all();
             __syncthreads();
             cur_slot = sl;
         }
         float2 v[32];
         if constexpr (SEP) {
-            const float* wr = sep.wrow + (long long)k * NY;
+            const float* wr = wys + (t & 1) * NY;
 #pragma unroll
             for (int q = 0; q < 32; ++q) {
                 const int i = wrap(lane + 32 * q - bx.r0, NY);
-                v[q] = (i < bx.nr) ? cscale(tile[i * kTileStride + warp], __ldg(&wr[lane + 32 * q]))
-                                   : make_float2(0.f, 0.f);
+                v[q] = (i < bx.nr) ? cscale(tile[tix(i, warp)], wr[lane + 32 * q]) : make_float2(0.f, 0.f);
             }
         } else {
 #pragma unroll
             for (int q = 0; q < 32; ++q) {
                 const int i = wrap(lane + 32 * q - bx.r0, NY);
-                v[q] = (i < bx.nr) ? tile[i * kTileStride + warp] : make_float2(0.f, 0.f);
+                v[q] = (i < bx.nr) ? tile[tix(i, warp)] : make_float2(0.f, 0.f);
             }
         }
         if (tn < tend && sn != sl) {   // the next term needs another slot: reload the tile
@@ -215,17 +237,27 @@ kw_cols_fwd(const float2* __restrict__ Z, long long z_bstride, long long z_kstri
 #pragma unroll
             for (int mm = 0; mm < 32; ++mm) acc[mm] = cfma(lds_h(&th[lane + 32 * mm], sk), v[mm], acc[mm]);
         }
+        if constexpr (SEP) {
+            // next term's row factors into the other buffer, last read in the
+            // previous term (before this term's barrier)
+            if (tn < tend) {
+                wy_load(wys + ((t + 1) & 1) * NY, sep.wrow, kof(tn));
+                cp_async_commit();
+            }
+        }
         t = tn;
     }
     warp_fft1024<true>(acc, tr, tw);
     __syncthreads();
 #pragma unroll
-    for (int mm = 0; mm < 32; ++mm) tile[(lane + 32 * mm) * kTileStride + warp] = acc[mm];
+    const int swl = tix_sw(lane, warp);
+#pragma unroll
+    for (int mm = 0; mm < 32; ++mm) tile[4 * (lane + 32 * mm) + swl] = acc[mm];
     __syncthreads();
     float2* Ab = A + b * a_bstride;
     for (int e = threadIdx.x; e < NY * kWColWarps; e += kWColWarps * 32) {
         const int i = e >> 2, c = e & 3;
-        if (col0 + c < NXh) Ab[(long long)i * NXh + col0 + c] = tile[i * kTileStride + c];
+        if (col0 + c < NXh) Ab[(long long)i * NXh + col0 + c] = tile[tix(i, c)];
     }
 }
 
@@ -246,7 +278,7 @@ kw_cols_adj(const float2* __restrict__ V, long long v_bstride,
     extern __shared__ float2 smem[];
     float2* tile = smem;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float2* tr = smem + NY * kTileStride + warp * kWarpN;
+    float2* tr = smem + NY * kWColWarps + warp * kWarpN;
     const int b = blockIdx.x;
     const int col0 = blockIdx.y * kWColWarps;
     const int col = col0 + warp;
@@ -270,16 +302,21 @@ kw_cols_adj(const float2* __restrict__ V, long long v_bstride,
     auto kof = [&](int t) { return SEP ? __ldg(&sep.korder[t]) : t; };
     auto slot_of = [&](int kk) { return SEP ? __ldg(&sep.kslot[kk]) : kk; };
 
+    // SEP: row factors of the t-th term in buffer (t & 1), prefetched one term ahead
+    float* wys = reinterpret_cast<float*>(smem + 2 * NY * kWColWarps);
+    if constexpr (SEP) {
+        if (sep.nterms > 0) wy_load(wys, sep.wrow, __ldg(&sep.korder[0]));
+    }
     tile_load(tile, V + b * v_bstride, NY, NXh, col0);
     cp_async_wait_all();
     __syncthreads();
     float2 vv[32];
 #pragma unroll
-    for (int q = 0; q < 32; ++q) vv[q] = tile[(lane + 32 * q) * kTileStride + warp];
+    for (int q = 0; q < 32; ++q) vv[q] = tile[4 * (lane + 32 * q) + tix_sw(lane, warp)];
     int t = next_t(0);
     int prev_slot = -1;
     // the spectrum of the first term arrives while the FFT of V finishes
-    warp_fft1024<false, false>(vv, tr, tw, [&] {
+    warp_fft1024<false, SEP>(vv, tr, tw, [&] {
         if (use_bulk && t < tend && lane == 0)
             bulk_load(tr, hhT + ((long long)kof(t) * NXh + col) * NY, NY * sizeof(HT), bar, skip_copy);
     });
@@ -328,21 +365,28 @@ kw_cols_adj(const float2* __restrict__ V, long long v_bstride,
         }
         // the next term's spectrum arrives while this inverse FFT finishes
         const bool issue = use_bulk && !failed && tn < tend;
-        warp_fft1024<true, false>(p, tr, tw, [&] {
+        warp_fft1024<true, SEP>(p, tr, tw, [&] {
             if (issue && lane == 0)
                 bulk_load(tr, hhT + ((long long)kn * NXh + col) * NY, NY * sizeof(HT), bar, skip_copy);
         });
         if constexpr (SEP) {
             // accumulate wy_k . p into this warp's column of the tile; the previous
-            // slot's store must have finished reading the tile first
-            if (first) __syncthreads();
-            const float* wr = sep.wrow + (long long)k * NY;
+            // slot's store must have finished reading the tile, and this term's
+            // row factors must have landed
+            cp_async_wait_all();
+            __syncthreads();
+            if (tn < tend) {   // the other buffer was last read in the previous term
+                wy_load(wys + ((t + 1) & 1) * NY, sep.wrow, kn);
+                cp_async_commit();
+            }
+            const float* wr = wys + (t & 1) * NY;
+            float2* col = tile + tix_sw(lane, warp) + 4 * lane;
+            if (first) {
 #pragma unroll
-            for (int mm = 0; mm < 32; ++mm) {
-                const int y = lane + 32 * mm;
-                const float2 val = cscale(p[mm], __ldg(&wr[y]));
-                float2* cell = &tile[y * kTileStride + warp];
-                *cell = first ? val : cadd(*cell, val);
+                for (int mm = 0; mm < 32; ++mm) col[128 * mm] = cscale(p[mm], wr[lane + 32 * mm]);
+            } else {
+#pragma unroll
+                for (int mm = 0; mm < 32; ++mm) col[128 * mm] = cadd(col[128 * mm], cscale(p[mm], wr[lane + 32 * mm]));
             }
             if (last) {
                 __syncthreads();
@@ -350,20 +394,20 @@ kw_cols_adj(const float2* __restrict__ V, long long v_bstride,
                 for (int e = threadIdx.x; e < bx.nr * kWColWarps; e += kWColWarps * 32) {
                     const int i = e >> 2, c = e & 3;
                     const int g = wrap(bx.r0 + i, NY);
-                    if (col0 + c < NXh) Qs[(long long)i * NXh + col0 + c] = tile[g * kTileStride + c];
+                    if (col0 + c < NXh) Qs[(long long)i * NXh + col0 + c] = tile[tix(g, c)];
                 }
             }
         } else {
             __syncthreads();
 #pragma unroll
-            for (int mm = 0; mm < 32; ++mm) tile[(lane + 32 * mm) * kTileStride + warp] = p[mm];
+            for (int mm = 0; mm < 32; ++mm) tile[4 * (lane + 32 * mm) + tix_sw(lane, warp)] = p[mm];
             __syncthreads();
             float2* Qk = Q + b * q_bstride + k * q_kstride;
             const int rows = FULL ? NY : bx.nr;
             for (int e = threadIdx.x; e < rows * kWColWarps; e += kWColWarps * 32) {
                 const int i = e >> 2, c = e & 3;
                 const int g = FULL ? i : wrap(bx.r0 + i, NY);
-                if (col0 + c < NXh) Qk[(long long)i * NXh + col0 + c] = tile[g * kTileStride + c];
+                if (col0 + c < NXh) Qk[(long long)i * NXh + col0 + c] = tile[tix(g, c)];
             }
         }
         t = tn;
