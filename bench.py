@@ -42,6 +42,13 @@ SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
 
 
+# DRAM bytes (read + write) per launch measured by ncu for the dominant kernels
+# of the 1024 x 1024, m = 16, B = 8 workload with tensor-product windows (one
+# launch = 8 right-hand sides); see profiles/kw_cols_2d_1024_m16_b8.md.  Valid
+# only for that workload and the kernels as captured.
+MEASURED_TRAFFIC = {("2d_1024x1024_m16_b8", "separable", "cols_fwd"): 207.906304e6 + 18.656512e6,
+                    ("2d_1024x1024_m16_b8", "separable", "cols_adj"): 102.050816e6 + 89.044224e6}
+
 # ------------------------------------------------------------- algorithmic work
 
 def cyclic_extent(flags) -> tuple[int, int]:
@@ -236,13 +243,18 @@ def oracle_sample_rate(pr: synth.Problem, target_s: float = 12.0, seed: int = 5)
     rng = np.random.default_rng(seed)
     u0 = pr.u[:1]
 
+    kept = {}
+
     def run(count):
         pts = np.stack([rng.integers(0, n, count) for n in pr.shape], axis=-1)
+        ys, xs = [], []
         t0 = time.perf_counter()
         for i in range(0, count, 1024):          # bounded gather arrays
-            E.apply_at(u0, pr.w, pr.h, pts[i:i + 1024])
-            E.apply_adjoint_at(u0, pr.w, pr.h, pts[i:i + 1024])
-        return time.perf_counter() - t0
+            ys.append(E.apply_at(u0, pr.w, pr.h, pts[i:i + 1024]))
+            xs.append(E.apply_adjoint_at(u0, pr.w, pr.h, pts[i:i + 1024]))
+        dt = time.perf_counter() - t0
+        kept.update(pts=pts, y=np.concatenate(ys, axis=1)[0], x=np.concatenate(xs, axis=1)[0])
+        return dt
 
     count = 16
     dt = run(count)
@@ -259,7 +271,7 @@ def oracle_sample_rate(pr: synth.Problem, target_s: float = 12.0, seed: int = 5)
     return {"value": applies / total_t, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"{total_pts} sampled output pixels x (forward + adjoint) of right-hand side 0 "
                       f"of {pr.name}, FP64 gather form, {total_t:.1f} s",
-            "seconds": total_t}
+            "seconds": total_t, "points": kept.get("pts"), "oracle_y": kept.get("y"), "oracle_x": kept.get("x")}
 
 
 def reference_arm(args, pr: synth.Problem, rank: int) -> None:
@@ -347,16 +359,19 @@ def gpu_arm(args, pr: synth.Problem, rank: int, world: int) -> None:
     windows = "dense (pce_plan_create)"
     plan = None
     slots = None
+    from paper_1604_04374_gb300.pce import PCE_FLAG_LOWP_STORAGE
+    pflags = PCE_FLAG_LOWP_STORAGE if args.lowp else 0
     if len(pr.shape) == 2 and "grid" in pr.meta:
         # the node-grid hats are tensor products: give the plan their factors
         wy_np, wx_np = synth.hat_factors_2d(pr.shape[0], pr.shape[1], *pr.meta["grid"])
         if np.array_equal(np.einsum("kr,kc->krc", wy_np, wx_np), pr.w):
-            plan = Plan(wy=torch.from_numpy(wy_np).to(dev), wx=torch.from_numpy(wx_np).to(dev), h=h)
+            plan = Plan(wy=torch.from_numpy(wy_np).to(dev), wx=torch.from_numpy(wx_np).to(dev), h=h,
+                        flags=pflags)
             windows = f"tensor-product hats (pce_plan_create_separable, {plan.slots()} column-factor slots)"
             if plan.slots():
                 slots = slot_boxes(wy_np, wx_np)
     if plan is None:
-        plan = Plan(w, h=h)
+        plan = Plan(w, h=h, flags=pflags)
     tuning = None
     if args.autotune:
         chunk, variant, rvariant, ms = plan.autotune(pr.batch, args.tuning_cache)
@@ -438,6 +453,15 @@ def gpu_arm(args, pr: synth.Problem, rank: int, world: int) -> None:
                       "ms_per_step": cms / args.steps,
                       "launches_per_step": plain.launch_count(False, B) + plain.launch_count(True, B)}
         plain.close()
+
+    # gradients (pce_backward: dL/du, dL/dw, dL/dhhat of L = <H_m u, r>) per step
+    backward = None
+    if args.backward:
+        r_t = torch.from_numpy(synth.draw(synth.rng_for(99), pr.u.shape, "normal")).to(dev)
+        bms, _, _ = timed_steps(lambda: plan.backward(u, r_t))
+        backward = {"value": weak_scaling_value(B / 2, args.steps, world, bms), "unit": "right-hand sides/s",
+                    "ms_per_step": bms / args.steps,
+                    "what": "pce_backward: dL/du (adjoint apply), dL/dw and dL/dhhat for the batch"}
 
     # end to end through the public API, pipelined like a serving loop: two buffer
     # sets, each bound to its own two-lane batch; step i copies its input from
@@ -526,12 +550,17 @@ def gpu_arm(args, pr: synth.Problem, rank: int, world: int) -> None:
             roof = {"kernel": dom, "bound": "alu", "achieved": d["tflops"], "peak": fp32_peak_tflops,
                     "unit": "TFLOP/s", "frac": d["tflops"] / fp32_peak_tflops,
                     "peak_source": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",
-                    "traffic": None, "hbm_gbs": d["gbs"], "hbm_frac_of_" + hbm_src: d["gbs"] / hbm_peak}
+                    "traffic": MEASURED_TRAFFIC.get((pr.name, "separable" if slots else "dense", dom))
+                    if (chunk == 8 and not args.lowp) else None,
+                    "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch "
+                                      "(profiles/kw_cols_2d_1024_m16_b8.md)",
+                    "hbm_gbs": d["gbs"], "hbm_frac_of_" + hbm_src: d["gbs"] / hbm_peak}
         pbytes = path_bytes(pr, boxes)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "storage": "bf16 windows, fp16 spectra with per-term scale" if args.lowp else "f32",
             "config": {"workload": pr.name, "shape": list(pr.shape), "m": pr.m, "batch_per_gpu": B,
                        "windows": windows,
                        "global_batch": B * world, "parallelism": f"replicas x{world}",
@@ -550,6 +579,7 @@ def gpu_arm(args, pr: synth.Problem, rank: int, world: int) -> None:
                            "how": "pce_apply then pce_apply_adjoint on one stream; the per-kernel "
                                   "times and the roofline come from this pass"},
             "tuning": tuning,
+            "backward": backward,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": B * P * 4,
                     "d2h_bytes_per_step": 2 * B * P * 4,
                     "how": "pinned host u -> device, graph (forward + adjoint), both results -> pinned host, "
@@ -562,8 +592,21 @@ def gpu_arm(args, pr: synth.Problem, rank: int, world: int) -> None:
             "scratch_bytes": scratch,
         }
         if args.cpu_baseline and world >= 1:
-            line["cpu_baseline"] = {k: v for k, v in oracle_sample_rate(pr, args.ref_seconds).items()
-                                    if k != "seconds"}
+            cb = oracle_sample_rate(pr, args.ref_seconds)
+            line["cpu_baseline"] = {k: v for k, v in cb.items()
+                                    if k not in ("seconds", "points", "oracle_y", "oracle_x")}
+            # the same oracle outputs give the accuracy of this run (right-hand side 0)
+            if cb.get("points") is not None:
+                pts = cb["points"]
+                flat = np.ravel_multi_index(tuple(pts.T), pr.shape)
+                gy = y_ref[0].reshape(-1)[torch.from_numpy(flat).to(dev)].double().cpu().numpy()
+                gx = x_ref[0].reshape(-1)[torch.from_numpy(flat).to(dev)].double().cpu().numpy()
+                line["accuracy"] = {
+                    "rel_l2_forward": float(np.linalg.norm(gy - cb["oracle_y"]) / np.linalg.norm(cb["oracle_y"])),
+                    "rel_l2_adjoint": float(np.linalg.norm(gx - cb["oracle_x"]) / np.linalg.norm(cb["oracle_x"])),
+                    "points": int(len(flat)), "bar": 3e-3 if args.lowp else 1e-5,
+                    "against": "FP64 oracle (gather form) at the cpu_baseline leg's sampled outputs, "
+                               "right-hand side 0"}
         print(json.dumps(line), flush=True)
     plan.close()
     if dist:
@@ -792,6 +835,9 @@ def main():
     ap.add_argument("--autotune", dest="autotune", action="store_true", default=True,
                     help="autotune the plan(s) before timing (default)")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
+    ap.add_argument("--backward", action="store_true", help="also time pce_backward (gradients)")
+    ap.add_argument("--lowp", action="store_true",
+                    help="reduced storage (PCE_FLAG_LOWP_STORAGE: bf16 windows, fp16 spectra)")
     ap.add_argument("--tuning-cache", default=None,
                     help="JSON-lines autotuner cache: reuse earlier choices instead of timing again")
     ap.add_argument("--tune-plans", action="store_true",

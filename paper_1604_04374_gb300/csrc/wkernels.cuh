@@ -184,10 +184,16 @@ kw_cols_fwd(const float2* __restrict__ Z, long long z_bstride, long long z_kstri
         float2 v[32];
         if constexpr (SEP) {
             const float* wr = wys + (t & 1) * NY;
+            if (bx.r0 == 0 && bx.nr == NY) {   // uniform: the slot holds every row in place
+                const float2* tb = tile + 4 * lane + tix_sw(lane, warp);
 #pragma unroll
-            for (int q = 0; q < 32; ++q) {
-                const int i = wrap(lane + 32 * q - bx.r0, NY);
-                v[q] = (i < bx.nr) ? cscale(tile[tix(i, warp)], wr[lane + 32 * q]) : make_float2(0.f, 0.f);
+                for (int q = 0; q < 32; ++q) v[q] = cscale(tb[128 * q], wr[lane + 32 * q]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    const int i = wrap(lane + 32 * q - bx.r0, NY);
+                    v[q] = (i < bx.nr) ? cscale(tile[tix(i, warp)], wr[lane + 32 * q]) : make_float2(0.f, 0.f);
+                }
             }
         } else {
 #pragma unroll
