@@ -176,6 +176,18 @@ cudaError_t prepare_kernels() {
     if (e == cudaSuccess) e = prepare_l1();
 #define X(N)                                                                                   \
     if (e == cudaSuccess)                                                                      \
+        e = cudaFuncSetAttribute(k_fwd_1d<N, float, float2, 1>,                                \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg1d<N, 1>::SMEM); \
+    if (e == cudaSuccess)                                                                      \
+        e = cudaFuncSetAttribute(k_adj_1d<N, float, float2, 1>,                                \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg1d<N, 1>::SMEM); \
+    if (e == cudaSuccess)                                                                      \
+        e = cudaFuncSetAttribute(k_fwd_1d<N, __nv_bfloat16, __half2, 1>,                       \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg1d<N, 1>::SMEM); \
+    if (e == cudaSuccess)                                                                      \
+        e = cudaFuncSetAttribute(k_adj_1d<N, __nv_bfloat16, __half2, 1>,                       \
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg1d<N, 1>::SMEM); \
+    if (e == cudaSuccess)                                                                      \
         e = cudaFuncSetAttribute(k_fwd_1d<N, float, float2>,                                   \
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg1d<N>::SMEM); \
     if (e == cudaSuccess)                                                                      \
@@ -198,6 +210,14 @@ cudaError_t prepare_kernels() {
     return e;
 }
 
+// Wide CTAs (more slots per right-hand side) when the batch leaves most SMs
+// idle and the terms need more than one round of the narrow CTA's slots.
+template <int N>
+bool wide_1d(int batch, int m) {
+    const int npairs = (m + 1) / 2;
+    return Cfg1d<N, 1>::G > Cfg1d<N>::G && npairs > Cfg1d<N>::G && batch < 2 * 152;
+}
+
 cudaError_t launch_fwd_1d(int n, int batch, cudaStream_t s, const float* u, const void* w,
                           const void* hp, const float* hscale, bool lowp, int m, float* y, float scale,
                           const float2* tw) {
@@ -205,7 +225,16 @@ cudaError_t launch_fwd_1d(int n, int batch, cudaStream_t s, const float* u, cons
     switch (n) {
 #define X(N)                                                                                   \
     case N:                                                                                    \
-        if (lowp)                                                                              \
+        if (wide_1d<N>(batch, m)) {                                                            \
+            if (lowp)                                                                          \
+                k_fwd_1d<N, bf16, __half2, 1><<<batch, Cfg1d<N, 1>::NT, Cfg1d<N, 1>::SMEM, s>>>(  \
+                    u, static_cast<const bf16*>(w), static_cast<const __half2*>(hp), hscale, m, y, \
+                    scale, tw);                                                                \
+            else                                                                               \
+                k_fwd_1d<N, float, float2, 1><<<batch, Cfg1d<N, 1>::NT, Cfg1d<N, 1>::SMEM, s>>>(  \
+                    u, static_cast<const float*>(w), static_cast<const float2*>(hp), hscale, m, y, \
+                    scale, tw);                                                                \
+        } else if (lowp)                                                                       \
             k_fwd_1d<N, bf16, __half2><<<batch, Cfg1d<N>::NT, Cfg1d<N>::SMEM, s>>>(              \
                 u, static_cast<const bf16*>(w), static_cast<const __half2*>(hp), hscale, m, y,  \
                 scale, tw);                                                                    \
@@ -229,7 +258,16 @@ cudaError_t launch_adj_1d(int n, int batch, cudaStream_t s, const float* v, cons
     switch (n) {
 #define X(N)                                                                                   \
     case N:                                                                                    \
-        if (lowp)                                                                              \
+        if (wide_1d<N>(batch, m)) {                                                            \
+            if (lowp)                                                                          \
+                k_adj_1d<N, bf16, __half2, 1><<<batch, Cfg1d<N, 1>::NT, Cfg1d<N, 1>::SMEM, s>>>(  \
+                    v, static_cast<const bf16*>(w), static_cast<const __half2*>(hp), hscale, m, x, \
+                    scale, tw);                                                                \
+            else                                                                               \
+                k_adj_1d<N, float, float2, 1><<<batch, Cfg1d<N, 1>::NT, Cfg1d<N, 1>::SMEM, s>>>(  \
+                    v, static_cast<const float*>(w), static_cast<const float2*>(hp), hscale, m, x, \
+                    scale, tw);                                                                \
+        } else if (lowp)                                                                       \
             k_adj_1d<N, bf16, __half2><<<batch, Cfg1d<N>::NT, Cfg1d<N>::SMEM, s>>>(              \
                 v, static_cast<const bf16*>(w), static_cast<const __half2*>(hp), hscale, m, x,  \
                 scale, tw);                                                                    \

@@ -871,10 +871,14 @@ k_rows_grad_w(const float2* __restrict__ Qf, long long q_bstride, long long q_ks
 }
 
 // ------------------------------------------------------------------- 1D
-template <int N>
+template <int N, int WIDE = 0>
 struct Cfg1d {
     static constexpr int T = N / kR;
-    static constexpr int G = (256 / T) > 0 ? (256 / T) : 1;   // FFT slots per CTA
+    // FFT slots per CTA: 256 threads (throughput), or with WIDE up to 8 slots
+    // in up to 1024 threads, so that a few right-hand sides finish sooner (the
+    // slots work on different term pairs of the same right-hand side)
+    static constexpr int G = WIDE ? ((1024 / T) < 8 ? ((1024 / T) > 0 ? 1024 / T : 1) : 8)
+                                  : ((256 / T) > 0 ? (256 / T) : 1);
     static constexpr int NT = T * G;
     static constexpr int SMEM = G * fft_region(N) * (int)sizeof(float2);
 };
@@ -883,12 +887,12 @@ struct Cfg1d {
 // slot takes pairs of terms (w_k u + i w_{k+1} u in one complex FFT) and
 // accumulates the half spectrum in registers; the slots' sums are reduced in
 // shared memory and one inverse FFT follows.  hp: [m][N/2] packed spectra.
-template <int N, typename WT = float, typename HT = float2>
-__global__ void __launch_bounds__(Cfg1d<N>::NT)
+template <int N, typename WT = float, typename HT = float2, int WIDE = 0>
+__global__ void __launch_bounds__(Cfg1d<N, WIDE>::NT)
 k_fwd_1d(const float* __restrict__ u, const WT* __restrict__ w,
          const HT* __restrict__ hp, const float* __restrict__ hscale, int m, float* __restrict__ y, float scale,
          const float2* __restrict__ tw) {
-    using CF = Cfg1d<N>;
+    using CF = Cfg1d<N, WIDE>;
     constexpr int T = CF::T;
     constexpr int G = CF::G;
     constexpr int Nh = N / 2;
@@ -982,12 +986,12 @@ k_fwd_1d(const float* __restrict__ u, const WT* __restrict__ w,
 // x_b = (1/N) sum_k w_k . IFFT( conj(hhat_k) . FFT(v_b) ).  One CTA per b;
 // every slot forms FFT(v_b) and takes pairs of terms: the two inverse FFTs
 // of a pair are real, so they share one complex inverse FFT.
-template <int N, typename WT = float, typename HT = float2>
-__global__ void __launch_bounds__(Cfg1d<N>::NT)
+template <int N, typename WT = float, typename HT = float2, int WIDE = 0>
+__global__ void __launch_bounds__(Cfg1d<N, WIDE>::NT)
 k_adj_1d(const float* __restrict__ vin, const WT* __restrict__ w,
          const HT* __restrict__ hp, const float* __restrict__ hscale, int m, float* __restrict__ x, float scale,
          const float2* __restrict__ tw) {
-    using CF = Cfg1d<N>;
+    using CF = Cfg1d<N, WIDE>;
     constexpr int T = CF::T;
     constexpr int G = CF::G;
     constexpr int Nh = N / 2;

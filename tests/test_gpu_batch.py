@@ -218,3 +218,33 @@ def test_autotune_other_plans(torch_cuda, shape, m):
     u = dev(torch, pr.u)
     assert rel(host(plan.apply(u)), E.apply(pr.u, pr.w, pr.h)) < TOL
     assert rel(host(plan.apply_adjoint(u)), E.apply_adjoint(pr.u, pr.w, pr.h)) < TOL
+
+
+def test_full_uneven_batch_as_benchmarked(torch_cuda):
+    """The 256-task mix (1D 4096/16384/65536, 2D 256^2/512^2/1024^2, m 4..32, both
+    directions) as one graph launch after batch-level tuning: every task equals its
+    single apply up to rounding order, and sampled outputs of 1D tasks match the oracle."""
+    torch = torch_cuda
+    from paper_1604_04374_gb300 import Batch, Plan
+    mx = synth.batch_mix(256, 4)
+    plans = [Plan(dev(torch, w), h=dev(torch, h)) for _, _, w, h in mx.ops]
+    ins = [dev(torch, u) for u in mx.inputs]
+    ref = singles(torch, mx, plans, ins)
+    tasks, outs = tasks_of(torch, mx, plans, ins)
+    b = Batch(tasks, lanes=16)
+    b.autotune()
+    b.launch()
+    torch.cuda.synchronize()
+    for i in range(len(ins)):
+        assert rel(host(outs[i])[None], ref[i][None]) < 1e-6, i
+    rng = np.random.default_rng(2)
+    checked = 0
+    for i in range(len(ins)):
+        shape, m, w, h = mx.ops[mx.op_of[i]]
+        if len(shape) != 1 or checked >= 12:
+            continue
+        pts = rng.integers(0, shape[0], 32)[:, None]
+        fn = E.apply_adjoint_at if mx.adjoint[i] else E.apply_at
+        assert rel(host(outs[i]).reshape(1, -1)[:, pts[:, 0]], fn(mx.inputs[i], w, h, pts)) < TOL, i
+        checked += 1
+    b.close()

@@ -147,3 +147,33 @@ def test_separable_with_stockham_columns_and_in_batches(torch_cuda, tmp_path):
     for o, r in zip(outs, (ref_y, ref_x, ref_y, ref_x)):
         assert rel(host(o), r) < 2e-6
     b.close()
+
+
+def test_bench_launch_configuration_full_size(torch_cuda):
+    """The headline step exactly as timed: 1024 x 1024, m = 16, B = 8, separable plan,
+    forward and adjoint as one graph launch of a two-lane batch.  Outputs equal the
+    plain applies bit for bit and match the oracle at sampled outputs of every
+    right-hand side."""
+    torch = torch_cuda
+    from paper_1604_04374_gb300 import Batch, Plan
+    pr = synth.workload("2d_1024_m16_b8")
+    wy, wx = synth.hat_factors_2d(1024, 1024, 4, 4)
+    assert np.array_equal(np.einsum("kr,kc->krc", wy, wx), pr.w)
+    plan = Plan(wy=dev(torch, wy), wx=dev(torch, wx), h=dev(torch, pr.h))
+    plan.autotune(pr.batch)
+    u = dev(torch, pr.u)
+    y0, x0 = host(plan.apply(u)), host(plan.apply_adjoint(u))
+    y, x = torch.empty_like(u), torch.empty_like(u)
+    b = Batch([(plan, u, y, False), (plan, u, x, True)], lanes=2)
+    b.launch()
+    b.launch()
+    torch.cuda.synchronize()
+    assert np.array_equal(host(y), y0) and np.array_equal(host(x), x0)
+    b.close()
+    rng = np.random.default_rng(11)
+    pts = np.stack([rng.integers(0, 1024, 64), rng.integers(0, 1024, 64)], axis=-1)
+    flat = pts[:, 0] * 1024 + pts[:, 1]
+    ys = E.apply_at(pr.u, pr.w, pr.h, pts)
+    xs = E.apply_adjoint_at(pr.u, pr.w, pr.h, pts)
+    assert rel(y0.reshape(8, -1)[:, flat], ys) < TOL
+    assert rel(x0.reshape(8, -1)[:, flat], xs) < TOL
