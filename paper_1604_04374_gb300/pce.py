@@ -8,6 +8,7 @@ raises PceError carrying the status and pce_last_error_string().
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 
 from . import build as _build
@@ -408,7 +409,7 @@ class Plan:
         _need_cuda_f32(x, name)
         if tuple(x.shape[-self.ndims:]) != self.shape:
             raise ValueError(f"{name} must end with shape {self.shape}")
-        batch = x.numel() // max(1, int(torch.tensor(self.shape).prod()))
+        batch = x.numel() // max(1, math.prod(self.shape))
         if out is None:
             out = torch.empty_like(x)
         else:
