@@ -489,7 +489,7 @@ extern "C" pce_status pce_plan_autotune(pce_plan_t p, int64_t batch, const char*
         if (cache_lookup(cache_path, key, c, v, rv, ms)) {
             p->tune_log.clear();
             p->run_chunk = std::min(c, cmax);
-            p->col_variant = (p->ndims == 2 && p->ny == 1024) ? v : 0;
+            p->col_variant = (p->ndims == 2 && (p->ny == 1024 || p->ny == 2048)) ? v : 0;
             p->row_variant = (p->ndims == 2) ? rv : 0;
             p->tuned_ms = ms;
             return PCE_OK;
@@ -497,7 +497,7 @@ extern "C" pce_status pce_plan_autotune(pce_plan_t p, int64_t batch, const char*
     }
     // candidates
     std::vector<int> variants = {0};
-    if (p->ndims == 2 && p->ny == 1024) variants.push_back(1);
+    if (p->ndims == 2 && (p->ny == 1024 || p->ny == 2048)) variants.push_back(1);
     std::vector<int> rvariants = {0};
     if (p->ndims == 2) rvariants.push_back(1);
     std::vector<int> chunks;

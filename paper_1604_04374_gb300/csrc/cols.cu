@@ -1,6 +1,7 @@
 // cols.cu -- instances of the column-pass kernels for NY = 16 .. 2048.
 #include "kernels.cuh"
 #include "wkernels.cuh"
+#include "wkernels2.cuh"
 #include "launch.h"
 
 namespace pce {
@@ -34,6 +35,14 @@ int cols_smem(int ny) {
 
 cudaError_t prepare_cols() {
     cudaError_t e = cudaFuncSetAttribute(kw_cols_fwd<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWColSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kw2_cols_fwd<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kW2Smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kw2_cols_fwd<__half2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kW2Smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kw2_cols_adj<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kW2Smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kw2_cols_adj<__half2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kW2Smem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(kw_cols_fwd<__half2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWColSmem);
     if (e == cudaSuccess)
@@ -86,7 +95,23 @@ cudaError_t launch_cols_fwd(int ny, dim3 grid, cudaStream_t s, const float2* Z, 
                             bool lowp, int m,
                             const Box* box, int nxh, float2* A, long long a_bstride,
                             const float2* tw, const void* hhT, const float2* tw1024, int* status,
-                            long long wait_limit, int skip_copy, bool warp) {
+                            long long wait_limit, int skip_copy, bool warp,
+                            const void* hN2, const float2* tw2048l) {
+    // the warp-FFT column kernels index these tables: refuse to launch without them
+    if ((ny == kWarpN || ny == kW2N) && warp && (!tw1024 || !hhT)) return cudaErrorInvalidValue;
+    if (ny == kW2N && warp && (!tw2048l || !hN2)) return cudaErrorInvalidValue;
+    if (ny == kW2N && warp) {
+        dim3 g2 = grid;
+        if (lowp)
+            kw2_cols_fwd<__half2><<<g2, 128, kW2Smem, s>>>(
+                Z, z_bstride, z_kstride, static_cast<const __half2*>(hhT), static_cast<const __half2*>(hN2),
+                hscale, m, box, nxh, A, a_bstride, tw1024, tw2048l, status, wait_limit, skip_copy);
+        else
+            kw2_cols_fwd<float2><<<g2, 128, kW2Smem, s>>>(
+                Z, z_bstride, z_kstride, static_cast<const float2*>(hhT), static_cast<const float2*>(hN2),
+                hscale, m, box, nxh, A, a_bstride, tw1024, tw2048l, status, wait_limit, skip_copy);
+        return cudaGetLastError();
+    }
     if (ny == kWarpN && warp) {
         if (lowp)
             kw_cols_fwd<__half2><<<grid, kWColWarps * 32, kWColSmem, s>>>(
@@ -122,7 +147,21 @@ cudaError_t launch_cols_adj(int ny, dim3 grid, cudaStream_t s, const float2* V, 
                             const void* hh, const void* hN, const float* hscale, bool lowp, int m,
                             const Box* box, int nxh, float2* Q, long long q_bstride, long long q_kstride,
                             const float2* tw, const void* hhT, const float2* tw1024, int* status,
-                            long long wait_limit, int skip_copy, bool warp) {
+                            long long wait_limit, int skip_copy, bool warp,
+                            const void* hN2, const float2* tw2048l) {
+    if ((ny == kWarpN || ny == kW2N) && warp && (!tw1024 || !hhT)) return cudaErrorInvalidValue;
+    if (ny == kW2N && warp && (!tw2048l || !hN2)) return cudaErrorInvalidValue;
+    if (ny == kW2N && warp) {
+        if (lowp)
+            kw2_cols_adj<__half2><<<grid, 128, kW2Smem, s>>>(
+                V, v_bstride, static_cast<const __half2*>(hhT), static_cast<const __half2*>(hN2), hscale, m,
+                box, nxh, Q, q_bstride, q_kstride, tw1024, tw2048l, status, wait_limit, skip_copy);
+        else
+            kw2_cols_adj<float2><<<grid, 128, kW2Smem, s>>>(
+                V, v_bstride, static_cast<const float2*>(hhT), static_cast<const float2*>(hN2), hscale, m,
+                box, nxh, Q, q_bstride, q_kstride, tw1024, tw2048l, status, wait_limit, skip_copy);
+        return cudaGetLastError();
+    }
     if (ny == kWarpN && warp) {
         if (lowp)
             kw_cols_adj<false, __half2><<<grid, kWColWarps * 32, kWColSmem, s>>>(

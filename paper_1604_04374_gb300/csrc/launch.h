@@ -49,13 +49,15 @@ cudaError_t launch_cols_fwd(int ny, dim3 grid, cudaStream_t s, const float2* Z, 
                             bool lowp, int m,
                             const Box* box, int nxh, float2* A, long long a_bstride,
                             const float2* tw, const void* hhT, const float2* tw1024, int* status,
-                            long long wait_limit, int skip_copy, bool warp = true);
+                            long long wait_limit, int skip_copy, bool warp = true,
+                            const void* hN2 = nullptr, const float2* tw2048l = nullptr);
 
 cudaError_t launch_cols_adj(int ny, dim3 grid, cudaStream_t s, const float2* V, long long v_bstride,
                             const void* hh, const void* hN, const float* hscale, bool lowp, int m,
                             const Box* box, int nxh, float2* Q, long long q_bstride, long long q_kstride,
                             const float2* tw, const void* hhT, const float2* tw1024, int* status,
-                            long long wait_limit, int skip_copy, bool warp = true);
+                            long long wait_limit, int skip_copy, bool warp = true,
+                            const void* hN2 = nullptr, const float2* tw2048l = nullptr);
 
 cudaError_t launch_cols_spec(int ny, dim3 grid, cudaStream_t s, const float2* S, int nxh,
                              float2* hh, float2* hN, const float2* tw);

@@ -169,6 +169,31 @@ __global__ void k_transpose_hh(const float2* __restrict__ hh, int m, int ny, int
     }
 }
 
+// ny = 2048: hhT[k][c][par][f'] = hh[k][2 f' + par][c], hN2[k][par][f'] = hN[k][2 f' + par]
+__global__ void k_split_hh2(const float2* __restrict__ hh, const float2* __restrict__ hN, int m, int nxh,
+                            float2* hhT, float2* hN2) {
+    const long long total = (long long)m * nxh * 2048;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int fp = (int)(i & 1023);
+        const int par = (int)((i >> 10) & 1);
+        const long long kc = i >> 11;
+        const int c = (int)(kc % nxh);
+        const long long k = kc / nxh;
+        hhT[i] = hh[(k * 2048 + 2 * fp + par) * nxh + c];
+        if (c == 0) hN2[(k * 2 + par) * 1024 + fp] = hN[k * 2048 + 2 * fp + par];
+    }
+}
+
+// W2048^l for l < 32 (FP64 sincospi)
+__global__ void k_tw2048l(float2* tw) {
+    const int l = threadIdx.x;
+    if (l >= 32) return;
+    double sn, cs;
+    sincospi(-2.0 * l / 2048.0, &sn, &cs);
+    tw[l] = make_float2((float)cs, (float)sn);
+}
+
 int twiddle_len(int n) {
     const int L = pce::ilog2(n);
     const int nfull = L / 3, rem = L % 3;
@@ -416,6 +441,7 @@ const void* wstore(pce_plan_t p) { return p->lowp ? p->wbox16 : (const void*)p->
 const void* hstore(pce_plan_t p) { return p->lowp ? p->hh16 : (const void*)p->hh; }
 const void* hNstore(pce_plan_t p) { return p->lowp ? p->hN16 : (const void*)p->hN; }
 const void* hTstore(pce_plan_t p) { return p->lowp ? p->hhT16 : (const void*)p->hhT; }
+const void* hN2store(pce_plan_t p) { return p->lowp ? p->hN2_16 : (const void*)p->hN2; }
 
 pce_status validate_shape(int ndims, const int64_t* shape, int& ny, int& nx) {
     if (ndims != 1 && ndims != 2) return fail(PCE_ERR_INVALID, "ndims must be 1 or 2 (got %d)", ndims);
@@ -459,7 +485,9 @@ pce_status make_twiddles_l1(pce_plan* p, cudaStream_t s) {
 
 pce_status make_twiddles(pce_plan* p, cudaStream_t s) {
     if (p->l1) return make_twiddles_l1(p, s);
-    if (p->nx == 1024 || (p->ndims == 2 && p->ny == 1024)) {
+    // the one-warp 1024-point FFT serves transforms of 1024 and, two warps per
+    // column, columns of 2048
+    if (p->nx == 1024 || (p->ndims == 2 && (p->ny == 1024 || p->ny == 2048))) {
         pce_status st0 = dev_alloc(&p->tw1024, 1024);
         if (st0) return st0;
         k_twiddles_1024<<<4, 256, 0, s>>>(p->tw1024);
@@ -626,6 +654,13 @@ pce_status quantize_plan(pce_plan* p, cudaStream_t s) {
         p->hN16 = n16;
         k_quantize_h<<<grid_for((long long)ny * m), 256, 0, s>>>(p->hN, ny, m, p->hscale, n16);
         PCE_CK(cudaGetLastError());
+        if (p->hN2) {
+            __half2* n2 = nullptr;
+            if ((st = dev_alloc(&n2, (size_t)ny * m))) return st;
+            p->hN2_16 = n2;
+            k_quantize_h<<<grid_for((long long)ny * m), 256, 0, s>>>(p->hN2, ny, m, p->hscale, n2);
+            PCE_CK(cudaGetLastError());
+        }
         if (p->hhT) {
             __half2* t16 = nullptr;
             if ((st = dev_alloc(&t16, (size_t)(per * m)))) return st;
@@ -794,6 +829,16 @@ pce_status create_common(pce_plan_t* out, int ndims, const int64_t* shape, int m
         k_transpose_hh<<<grid_for((long long)m * ny * nxh), 256, 0, s>>>(p->hh, m, ny, nxh, p->hhT);
         cudaError_t e1 = cudaGetLastError();
         if (e1) return bail(fail(PCE_ERR_CUDA, "spectrum transpose: %s", cudaGetErrorString(e1)));
+    }
+    if (ndims == 2 && ny == 2048) {
+        // spectra of each column split by frequency parity for the two-warp column FFT
+        if ((st = dev_alloc(&p->hhT, (size_t)m * ny * nxh))) return bail(st);
+        if ((st = dev_alloc(&p->hN2, (size_t)m * ny))) return bail(st);
+        if ((st = dev_alloc(&p->tw2048l, 32))) return bail(st);
+        k_split_hh2<<<grid_for((long long)m * ny * nxh), 256, 0, s>>>(p->hh, p->hN, m, nxh, p->hhT, p->hN2);
+        k_tw2048l<<<1, 32, 0, s>>>(p->tw2048l);
+        cudaError_t e1 = cudaGetLastError();
+        if (e1) return bail(fail(PCE_ERR_CUDA, "spectrum split: %s", cudaGetErrorString(e1)));
     }
     if ((flags & PCE_FLAG_LOWP_STORAGE) && (st = quantize_plan(p, s))) return bail(st);
     cudaError_t e = cudaStreamSynchronize(s);
@@ -1107,6 +1152,10 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
     TimingScope ts(allow_timing && !stream_capturing(s));
     // a product-convolution plan holds conj(hhat_k): its operator is the adjoint structure
     if (p->flags & PCE_FLAG_PRODUCT_CONVOLUTION) adjoint = !adjoint;
+    // right-hand sides per launch: as many launches as the scratch chunk needs,
+    // with equal shares (3 + 1 would leave the last launch with too few CTAs)
+    const long long nch = (batch + scr.chunk - 1) / std::max(1, scr.chunk);
+    const long long bal = nch > 0 ? (batch + nch - 1) / nch : 1;
     const int ny = p->ny, nx = p->nx, m = p->m, nxh = nx / 2;
     const long long P = (long long)ny * nx;
     const float scale = 1.0f / (float)P;
@@ -1118,8 +1167,8 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
         const int tiles = (NX + cpc - 1) / cpc;
         const int it = pce::l1_row_items(NX);
         const int kind = adjoint ? PCE_KERNEL_ADJ_1D : PCE_KERNEL_FWD_1D;
-        for (long long b0 = 0; b0 < batch && e == cudaSuccess; b0 += scr.chunk) {
-            const int nb = (int)std::min<long long>(scr.chunk, batch - b0);
+        for (long long b0 = 0; b0 < batch && e == cudaSuccess; b0 += bal) {
+            const int nb = (int)std::min<long long>(bal, batch - b0);
             const float* src = in + b0 * P;
             float* dst = out + b0 * P;
             if (!adjoint) {
@@ -1181,8 +1230,8 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
     const int fpc = pce::rows_pairs_per_cta(nx);
     const int cpc = pce::cols_columns_per_cta(ny);  // same for both variants
     const int npairs = (ny + 1) / 2;
-    for (long long b0 = 0; b0 < batch && e == cudaSuccess; b0 += scr.chunk) {
-        const int nb = (int)std::min<long long>(scr.chunk, batch - b0);
+    for (long long b0 = 0; b0 < batch && e == cudaSuccess; b0 += bal) {
+        const int nb = (int)std::min<long long>(bal, batch - b0);
         const float* src = in + b0 * P;
         float* dst = out + b0 * P;
         if (sepx && !adjoint) {
@@ -1231,7 +1280,8 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
             if (e == cudaSuccess)
                 e = timed(p, PCE_KERNEL_COLS_FWD, s, [&] {
                     return pce::launch_cols_fwd(ny, dim3(nb, (nxh + cpc - 1) / cpc), s, scr.Z, zb, zk,
-                                                hstore(p), hNstore(p), p->hscale, p->lowp, m, p->d_box, nxh, scr.A, ab, p->twy, hTstore(p), p->tw1024, p->d_status, p->wait_limit, p->skip_copy, warp);
+                                                hstore(p), hNstore(p), p->hscale, p->lowp, m, p->d_box, nxh, scr.A, ab, p->twy, hTstore(p), p->tw1024, p->d_status, p->wait_limit, p->skip_copy, warp,
+                                                hN2store(p), p->tw2048l);
                 });
             if (e == cudaSuccess)
                 e = timed(p, PCE_KERNEL_ROWS_C2R, s, [&] {
@@ -1247,7 +1297,8 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
             if (e == cudaSuccess)
                 e = timed(p, PCE_KERNEL_COLS_ADJ, s, [&] {
                     return pce::launch_cols_adj(ny, dim3(nb, (nxh + cpc - 1) / cpc), s, scr.A, ab,
-                                                hstore(p), hNstore(p), p->hscale, p->lowp, m, p->d_box, nxh, scr.Z, zb, zk, p->twy, hTstore(p), p->tw1024, p->d_status, p->wait_limit, p->skip_copy, warp);
+                                                hstore(p), hNstore(p), p->hscale, p->lowp, m, p->d_box, nxh, scr.Z, zb, zk, p->twy, hTstore(p), p->tw1024, p->d_status, p->wait_limit, p->skip_copy, warp,
+                                                hN2store(p), p->tw2048l);
                 });
             if (e == cudaSuccess)
                 e = timed(p, PCE_KERNEL_ROWS_ADJ, s, [&] {
@@ -1670,7 +1721,7 @@ extern "C" pce_status pce_apply_noalloc(pce_plan_t plan, const float* u, float* 
             e = pce::launch_cols_fwd(ny, dim3(nb, (nxh + cpc - 1) / cpc), s, scrZ, zb, zk, hstore(plan),
                                      hNstore(plan), plan->hscale, plan->lowp, m, plan->d_box, nxh, scrA, ab,
                                      plan->twy, hTstore(plan), plan->tw1024, plan->d_status, plan->wait_limit,
-                                     plan->skip_copy, plan->col_variant == 0);
+                                     plan->skip_copy, plan->col_variant == 0, hN2store(plan), plan->tw2048l);
         if (e == cudaSuccess)
             e = pce::launch_rows_c2r(nx, dim3((npairs + fpc - 1) / fpc, nb), s, scrA, ab, ny, y + b0 * P, P,
                                      scale, plan->twx, plan->tw1024);

@@ -24,8 +24,12 @@ struct pce_plan {
     // spectra
     float2* hh = nullptr;       // 2D [m][ny][nx/2]; 1D packed [m][n/2]
     float2* hN = nullptr;       // 2D [m][ny]
-    float2* hhT = nullptr;      // 2D, ny = 1024: [m][nx/2][ny] (each column's spectrum contiguous)
-    float2* tw1024 = nullptr;   // four-step twiddles when a transform length is 1024
+    float2* hhT = nullptr;      // 2D, ny = 1024: [m][nx/2][ny] (each column's spectrum contiguous);
+                                // ny = 2048: [m][nx/2][2][1024] (even, odd frequencies of each column)
+    float2* tw1024 = nullptr;   // four-step twiddles when a transform length is 1024 (or 2048)
+    float2* hN2 = nullptr;      // 2D, ny = 2048: Nyquist-column spectra split by parity [m][2][1024]
+    void* hN2_16 = nullptr;
+    float2* tw2048l = nullptr;  // W2048^l, l < 32
     int* d_status = nullptr;    // device status word (bit 0: a bounded wait gave up)
     // 1D of more than 8192 points: four-step over an l1ny x l1nx view
     bool l1 = false;
@@ -94,7 +98,8 @@ struct pce_plan {
         drop_events();
         void* ptrs[] = {d_box,  wbox,  hh,     hN,   hhT,   tw1024, d_status, twx, twy == twx ? nullptr : twy,
                         items,  kptr,  klist,  scrZ, scrA,  wbox16, hh16,     hN16, hhT16, hscale,
-                        twN,    hh4,   wrow, wxbox, d_vbox, d_kslot, d_korder, sitems, skptr, sklist};
+                        twN,    hh4,   wrow, wxbox, d_vbox, d_kslot, d_korder, sitems, skptr, sklist,
+                        hN2,    hN2_16, tw2048l};
         for (void* q : ptrs)
             if (q) cudaFree(q);
     }

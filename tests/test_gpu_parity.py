@@ -343,3 +343,44 @@ def test_non_default_stream(torch_cuda):
         y = plan.apply(u, stream=s)
     s.synchronize()
     assert np.array_equal(host(y), ref)
+
+
+@pytest.mark.parametrize("ny,nx,m,batch", [(2048, 16, 4, 2), (2048, 64, 8, 1), (2048, 32, 16, 3)])
+def test_2048_point_columns_two_warp_fft(torch_cuda, ny, nx, m, batch):
+    """Columns of 2048: two warps per column (even / odd frequencies by decimation in
+    frequency), forward and adjoint, FP32 and reduced storage, against the oracle."""
+    torch = torch_cuda
+    from paper_1604_04374_gb300 import Plan, pce
+    pr = synth.problem_2d(ny, nx, m, batch, 300 + m, "normal")
+    y, x = run_both(torch, pr)
+    assert rel_l2(y, E.apply(pr.u, pr.w, pr.h)) < TOL
+    assert rel_l2(x, E.apply_adjoint(pr.u, pr.w, pr.h)) < TOL
+    lp = Plan(dev(torch, pr.w), h=dev(torch, pr.h), flags=pce.PCE_FLAG_LOWP_STORAGE)
+    u = dev(torch, pr.u)
+    assert rel_l2(host(lp.apply(u)), E.apply(pr.u, pr.w, pr.h)) < 3e-3
+    assert rel_l2(host(lp.apply_adjoint(u)), E.apply_adjoint(pr.u, pr.w, pr.h)) < 3e-3
+
+
+def test_2048_point_columns_variants_agree(torch_cuda, tmp_path):
+    """The block-Stockham column variant (forced through the tuning cache) and the
+    product-convolution form on 2048-point columns."""
+    torch = torch_cuda
+    import json
+    from paper_1604_04374_gb300 import Plan, pce
+    pr = synth.problem_2d(2048, 32, 4, 2, 321, "normal")
+    u = dev(torch, pr.u)
+    p1 = Plan(dev(torch, pr.w), h=dev(torch, pr.h))
+    cache = str(tmp_path / "t.jsonl")
+    p1.autotune(2, cache)
+    rec = json.loads(open(cache).read().splitlines()[0])
+    with open(cache, "a") as f:
+        f.write(json.dumps(dict(rec, variant=1 - rec["variant"])) + "\n")
+    p2 = Plan(dev(torch, pr.w), h=dev(torch, pr.h))
+    p2.autotune(2, cache)
+    for fn, ref in (("apply", E.apply), ("apply_adjoint", E.apply_adjoint)):
+        r = ref(pr.u, pr.w, pr.h)
+        assert rel_l2(host(getattr(p1, fn)(u)), r) < TOL
+        assert rel_l2(host(getattr(p2, fn)(u)), r) < TOL
+    q = Plan(dev(torch, pr.w), h=dev(torch, pr.h), flags=pce.PCE_FLAG_PRODUCT_CONVOLUTION)
+    assert rel_l2(host(q.apply(u)), E.product_convolution(pr.u, pr.w, pr.h)) < TOL
+    assert rel_l2(host(q.apply_adjoint(u)), E.product_convolution_adjoint(pr.u, pr.w, pr.h)) < TOL
