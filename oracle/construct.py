@@ -66,15 +66,18 @@ def hat_basis(n: int, m: int) -> np.ndarray:
     return np.maximum(0.0, 1.0 - m * np.abs(t))
 
 
-def project_on_hats(T: np.ndarray, m: int) -> np.ndarray:
-    """L2 projection of every row T(x_i, .) onto span{B_{1,m}(. - k/m)} (Corollary 4.3).
-
-    Coefficients c(x_i) = argmin_c || T(x_i, .) - B c ||_2 on the sample grid,
-    i.e. c = (B^T B)^{-1} B^T T(x_i, .); returns T_m = c B^T.
-    """
+def projection_coefficients(T: np.ndarray, m: int) -> np.ndarray:
+    """Coefficients of the L2 projection of every row T(x_i, .) onto the periodic hats
+    (Corollary 4.3): c(x_i) = argmin_c || T(x_i, .) - B c ||_2 on the sample grid,
+    c = (B^T B)^{-1} B^T T(x_i, .).  Returns C [n][m] (h_k = C[:, k], w_k = B[:, k])."""
     B = hat_basis(T.shape[1], m)
-    C = np.linalg.solve(B.T @ B, B.T @ T.T).T          # [n][m]
-    return C @ B.T
+    return np.linalg.solve(B.T @ B, B.T @ np.asarray(T, dtype=np.float64).T).T
+
+
+def project_on_hats(T: np.ndarray, m: int) -> np.ndarray:
+    """L2 projection of every row T(x_i, .) onto span{B_{1,m}(. - k/m)} (Corollary 4.3):
+    T_m = C B^T with C from projection_coefficients."""
+    return projection_coefficients(T, m) @ hat_basis(T.shape[1], m).T
 
 
 def interpolate_on_hats(T: np.ndarray, m: int) -> np.ndarray:

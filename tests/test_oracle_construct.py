@@ -107,3 +107,16 @@ def test_interpolated_expansion_error_decreases_with_m():
     assert all(b < a for a, b in zip(errs, errs[1:])), errs
     slope = np.log(errs[-1] / errs[-2]) / np.log(2)
     assert -2.4 < slope < -1.6, (errs, slope)
+
+
+def test_projection_coefficients_reproduce_rows_in_the_hat_span():
+    """Idempotence: rows that already are combinations of the hats come back exactly,
+    and the residual of a general T is orthogonal to every hat (normal equations)."""
+    rng = np.random.default_rng(8)
+    n, m = 96, 12
+    B = C.hat_basis(n, m)
+    C0 = rng.standard_normal((n, m))
+    np.testing.assert_allclose(C.projection_coefficients(C0 @ B.T, m), C0, atol=1e-10)
+    T = rng.standard_normal((n, n))
+    R = T - C.projection_coefficients(T, m) @ B.T
+    assert np.abs(R @ B).max() < 1e-10 * np.abs(T).max() * n
