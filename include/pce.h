@@ -432,6 +432,31 @@ pce_status pce_plan_tuning(pce_plan_t plan, int* chunk, int* col_variant, int* r
 int pce_plan_tuning_log(pce_plan_t plan, int max_entries, int* chunk, int* col_variant,
                         int* row_variant, double* ms_per_apply);
 
+/* ------------------------------------------------------------------------
+ * Construction of (h_k, w_k) (plan-time, not part of the apply).
+ * ---------------------------------------------------------------------- */
+
+/*
+ * pce_construct_projection_1d -- the L2 projection of a sampled time-varying
+ * impulse response onto m periodic hats (Corollary 4.3; hats of Definition
+ * 2.2 with alpha = 1 at the nodes k/m).
+ *
+ *   T     : device, [n][n] float32, T[d][j] = T(x_d, y_j): the impulse
+ *           response at shift d (origin at index 0, periodic) for the input
+ *           position j; the kernel is K(x_i, y_j) = T[(i - j) mod n][j].
+ *   n     : samples per axis, in [16, 262144]; m in [3, min(n, 512)].
+ *   h_out : device, [m][n] float32: h_k[d], the projection coefficients of
+ *           the rows of T (computed with FP64 sums and an FP64 Gram inverse).
+ *   w_out : device, [m][n] float32: w_k[j] = B_{1,m}(j/n - k/m), periodic.
+ *
+ * T(x_d, y_j) ~ sum_k h_k[d] w_k[j] with the residual of every row orthogonal
+ * to the hats, so that pce_plan_create(1, {n}, m, w_out, h_out, ...) applies
+ * the projected operator.  Allocates and frees temporary device memory and
+ * synchronises `stream`.  PCE_ERR_INVALID for bad sizes or host pointers.
+ */
+pce_status pce_construct_projection_1d(const float* T, int n, int m, float* h_out, float* w_out,
+                                       void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -255,7 +255,6 @@ kw_cols_fwd(const float2* __restrict__ Z, long long z_bstride, long long z_kstri
     }
     warp_fft1024<true>(acc, tr, tw);
     __syncthreads();
-#pragma unroll
     const int swl = tix_sw(lane, warp);
 #pragma unroll
     for (int mm = 0; mm < 32; ++mm) tile[4 * (lane + 32 * mm) + swl] = acc[mm];

@@ -96,6 +96,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
     lib.pce_batch_destroy.argtypes = [P]
     lib.pce_batch_autotune.argtypes = [P, P]
+    lib.pce_construct_projection_1d.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P, P]
+    lib.pce_construct_projection_1d.restype = ctypes.c_int
     lib.pce_batch_tuning.argtypes = [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.pce_batch_tuning_log.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
@@ -270,6 +272,24 @@ def pce_batch_tuning_log(batch: int):
     ms = (ctypes.c_double * max(1, n))()
     lib.pce_batch_tuning_log(batch, n, c, r, ms)
     return [(c[i], r[i], ms[i]) for i in range(n)]
+
+
+def pce_construct_projection_1d(T_ptr: int, n: int, m: int, h_ptr: int, w_ptr: int, stream: int = 0) -> None:
+    _check(load_library().pce_construct_projection_1d(T_ptr, n, m, h_ptr, w_ptr, stream))
+
+
+def construct_projection_1d(T, m: int, stream=None):
+    """(h [m, n], w [m, n]) of the L2 projection of the TVIR T [n, n] (T[d, j]: shift d,
+    input position j) onto m periodic hats (pce_construct_projection_1d)."""
+    import torch
+    _need_cuda_f32(T, "T")
+    n = int(T.shape[0])
+    if T.dim() != 2 or T.shape[1] != n:
+        raise ValueError("T must be [n, n]")
+    h = torch.empty((m, n), dtype=torch.float32, device=T.device)
+    w = torch.empty((m, n), dtype=torch.float32, device=T.device)
+    pce_construct_projection_1d(T.data_ptr(), n, m, h.data_ptr(), w.data_ptr(), _stream_handle(stream))
+    return h, w
 
 
 def pce_schedule_lpt(cost, lanes: int):

@@ -1,0 +1,86 @@
+"""GPU construction of (h_k, w_k) by L2 projection onto periodic hats
+(pce_construct_projection_1d, Corollary 4.3) against the FP64 oracle, and the
+constructed expansion fed to a plan.
+
+The TVIR is the 1D workload's kernel: T[d][j] = g_sigma(y_j)(d / n) / n, the
+periodised Gaussian with sigma(y) = 0.01 + 0.005 sin(2 pi y).
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import construct as C
+from oracle import expansion as E
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    from paper_1604_04374_gb300 import build
+    build.build()
+    torch.cuda.init()
+    return torch
+
+
+def dev(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def tvir(n):
+    """[n][n] float32: column j is the impulse response at y_j = j / n."""
+    return np.stack([synth.gaussian_psf_1d(n, synth.sigma_1d(j / n)) for j in range(n)], axis=1).astype(np.float32)
+
+
+@pytest.mark.parametrize("n,m", [(256, 8), (512, 16), (512, 5), (1024, 32)])
+def test_projection_matches_oracle(torch_cuda, n, m):
+    torch = torch_cuda
+    from paper_1604_04374_gb300 import construct_projection_1d
+    T = tvir(n)
+    h, w = construct_projection_1d(dev(torch, T), m)
+    h = h.cpu().numpy().astype(np.float64)
+    w = w.cpu().numpy().astype(np.float64)
+    B = C.hat_basis(n, m)
+    assert np.abs(w - B.T).max() < 1e-6
+    ref = C.projection_coefficients(T.astype(np.float64), m).T      # [m][n]
+    assert np.linalg.norm(h - ref) / np.linalg.norm(ref) < 1e-5
+
+
+def test_constructed_expansion_feeds_a_plan(torch_cuda):
+    """Plan(w, h) from the construction applies sum_k h_k * (w_k . u); the error to the
+    true operator u -> sum_j T[(i - j) mod n][j] u[j] does not grow over nested hat spaces."""
+    torch = torch_cuda
+    from paper_1604_04374_gb300 import Plan, construct_projection_1d
+    n = 512
+    T = tvir(n)
+    rng = np.random.default_rng(12)
+    u = rng.standard_normal((2, n)).astype(np.float32)
+    idx = (np.arange(n)[:, None] - np.arange(n)[None, :]) % n
+    K = T.astype(np.float64)[idx, np.arange(n)[None, :]]                # K[i][j] = T[(i - j) mod n][j]
+    y_true = u.astype(np.float64) @ K.T
+    errs = []
+    for m in (4, 8, 16, 32, 64):
+        h, w = construct_projection_1d(dev(torch, T), m)
+        plan = Plan(w.contiguous(), h=h.contiguous())
+        y = plan.apply(dev(torch, u)).cpu().numpy().astype(np.float64)
+        ref = E.apply(u, w.cpu().numpy(), h.cpu().numpy())
+        assert np.linalg.norm(y - ref) / np.linalg.norm(ref) < 1e-5
+        errs.append(np.linalg.norm(y - y_true) / np.linalg.norm(y_true))
+    assert all(b <= a * (1 + 1e-3) for a, b in zip(errs, errs[1:])), errs
+    assert errs[-1] < 0.2 * errs[0], errs
+
+
+def test_projection_argument_errors(torch_cuda):
+    torch = torch_cuda
+    from paper_1604_04374_gb300 import pce
+    from paper_1604_04374_gb300.pce import PceError
+    T = torch.zeros((64, 64), device="cuda")
+    h = torch.empty((4, 64), device="cuda")
+    with pytest.raises(PceError) as e:
+        pce.pce_construct_projection_1d(T.data_ptr(), 64, 2, h.data_ptr(), h.data_ptr())
+    assert e.value.status == pce.PCE_ERR_INVALID
+    Tc = torch.zeros((64, 64))
+    with pytest.raises(PceError) as e:
+        pce.pce_construct_projection_1d(Tc.data_ptr(), 64, 4, h.data_ptr(), h.data_ptr())
+    assert e.value.status == pce.PCE_ERR_INVALID
