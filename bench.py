@@ -454,6 +454,32 @@ def gpu_arm(args, pr: synth.Problem, rank: int, world: int) -> None:
                       "launches_per_step": plain.launch_count(False, B) + plain.launch_count(True, B)}
         plain.close()
 
+    # sectioned applies (Lemma 3.2): the same operator on per-term sections, same step
+    sectioned = None
+    if args.sectioned and len(pr.shape) == 2:
+        from paper_1604_04374_gb300.pce import PCE_FLAG_SECTIONED, PceError
+        try:
+            sp = Plan(torch.from_numpy(pr.w).to(dev), h=torch.from_numpy(pr.h).to(dev), flags=PCE_FLAG_SECTIONED)
+        except PceError as exc:
+            sectioned = {"unsupported": str(exc)}
+        else:
+            ys, xs = torch.empty_like(u), torch.empty_like(u)
+            spair = Batch([(sp, u, ys, False), (sp, u, xs, True)], lanes=2)
+            sms, _, _ = timed_steps(spair.launch)
+            spair.close()
+
+            def rel_t(a, b):
+                a, b = a.reshape(B, -1).double(), b.reshape(B, -1).double()
+                return float(((a - b).norm(dim=1) / b.norm(dim=1)).max())
+
+            sectioned = {"impl": "PCE_FLAG_SECTIONED: every term on a 1024-row section, overlap-add",
+                         "value": weak_scaling_value(B, args.steps, world, sms), "unit": UNIT,
+                         "ms_per_step": sms / args.steps,
+                         "launches_per_step": sp.launch_count(False, B) + sp.launch_count(True, B),
+                         "max_rel_diff_vs_headline_plan": max(rel_t(ys, y_ref), rel_t(xs, x_ref))}
+            sp.close()
+            del ys, xs
+
     # gradients (pce_backward: dL/du, dL/dw, dL/dhhat of L = <H_m u, r>) per step
     backward = None
     if args.backward:
@@ -580,6 +606,7 @@ def gpu_arm(args, pr: synth.Problem, rank: int, world: int) -> None:
                                   "times and the roofline come from this pass"},
             "tuning": tuning,
             "backward": backward,
+            "sectioned": sectioned,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": B * P * 4,
                     "d2h_bytes_per_step": 2 * B * P * 4,
                     "how": "pinned host u -> device, graph (forward + adjoint), both results -> pinned host, "
@@ -836,6 +863,8 @@ def main():
                     help="autotune the plan(s) before timing (default)")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--backward", action="store_true", help="also time pce_backward (gradients)")
+    ap.add_argument("--sectioned", action="store_true",
+                    help="also time the same step with a sectioned plan (PCE_FLAG_SECTIONED)")
     ap.add_argument("--lowp", action="store_true",
                     help="reduced storage (PCE_FLAG_LOWP_STORAGE: bf16 windows, fp16 spectra)")
     ap.add_argument("--tuning-cache", default=None,

@@ -97,6 +97,21 @@ typedef struct pce_plan* pce_plan_t;
  * return PCE_ERR_UNSUPPORTED on such plans.
  */
 #define PCE_FLAG_PRODUCT_CONVOLUTION 4u
+/*
+ * PCE_FLAG_SECTIONED: applies convolve every term on a section (Lemma 3.2)
+ * of 1024 rows x L columns, L the smallest power of two holding the width of
+ * w_k's support box plus the width of h_k's support (h_k's exact nonzeros,
+ * found at plan time), and add the sections into the output (overlap-add;
+ * atomic adds, so the rounding order varies from run to run).  Pays when the
+ * grid is much larger than box + support (e.g. 2048 x 2048 with boxes of 511
+ * and 73-pixel PSFs: two 1024-point column FFTs per term instead of one
+ * 2048-point one shared with the other terms).  2D plans from pce_plan_create
+ * only, FP32 storage, convolution-product form; box rows + support rows - 1
+ * <= 1024 and box columns + support columns - 1 <= 2048 for every term.
+ * Otherwise PCE_ERR_UNSUPPORTED.  Gradients and pce_apply_noalloc use the
+ * plan's whole-grid structures.
+ */
+#define PCE_FLAG_SECTIONED 8u
 
 /*
  * pce_plan_create -- precompute everything an operator needs (Eq. 1.4).

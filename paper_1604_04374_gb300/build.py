@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libpce.so")
-SOURCES = ["pce_api.cu", "batch.cu", "construct.cu", "rows.cu", "cols.cu", "k1d.cu"]
+SOURCES = ["pce_api.cu", "batch.cu", "construct.cu", "sect.cu", "rows.cu", "cols.cu", "k1d.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -50,8 +50,7 @@ double task_cost(const pce_task& t) {
 
 // Right-hand sides per launch a task runs with.
 int task_chunk(const pce_task& t) {
-    const pce_plan* p = t.plan;
-    const int c = p->run_chunk > 0 ? std::min(p->run_chunk, p->bchunk) : p->bchunk;
+    const int c = pce_rt::plan_scratch(t.plan).chunk;
     return (int)std::max<long long>(1, std::min<long long>(c, t.batch));
 }
 
@@ -496,12 +495,13 @@ extern "C" pce_status pce_plan_autotune(pce_plan_t p, int64_t batch, const char*
         }
     }
     // candidates
+    // a sectioned plan runs its own kernels and chunks: one candidate, timed
     std::vector<int> variants = {0};
-    if (p->ndims == 2 && (p->ny == 1024 || p->ny == 2048)) variants.push_back(1);
+    if (p->ndims == 2 && !p->sect && (p->ny == 1024 || p->ny == 2048)) variants.push_back(1);
     std::vector<int> rvariants = {0};
-    if (p->ndims == 2) rvariants.push_back(1);
+    if (p->ndims == 2 && !p->sect) rvariants.push_back(1);
     std::vector<int> chunks;
-    if (p->ndims == 2 || p->l1) {
+    if ((p->ndims == 2 && !p->sect) || p->l1) {
         for (int c = 1; c < cmax; c *= 2) chunks.push_back(c);
     }
     chunks.push_back(cmax);

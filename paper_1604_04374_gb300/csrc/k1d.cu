@@ -174,6 +174,7 @@ cudaError_t launch_l1_rows_spec(int nx, dim3 grid, cudaStream_t s, const float2*
 cudaError_t prepare_kernels() {
     cudaError_t e = prepare_cols();
     if (e == cudaSuccess) e = prepare_l1();
+    if (e == cudaSuccess) e = prepare_sec();
 #define X(N)                                                                                   \
     if (e == cudaSuccess)                                                                      \
         e = cudaFuncSetAttribute(k_fwd_1d<N, float, float2, 1>,                                \

@@ -35,6 +35,18 @@ struct Box {          // periodic support box of w_k and its compacted copy
     int pad_;
 };
 
+// Sectioned apply (section.cuh): a term's input and output windows, as box
+// offsets relative to the box origin (r0, c0).
+struct SecGeom {
+    int r0, c0;             // box origin in the grid
+    int in_lo_r, in_rows;   // input rows: box offsets in_lo_r .. in_lo_r + in_rows - 1
+    int in_lo_c, in_hi_c;   // input columns: box offsets in_lo_c .. in_hi_c
+    int out_lo_r, out_rows;
+    int out_lo_c, out_hi_c;
+    long long woff;         // window box copy [nr][ldw] (the box of w_k)
+    int ldw, pad_;
+};
+
 // Separable windows w_k = wy_k (x) wx_k: terms sharing the column factor wx
 // share one slot of row spectra R_j = R2C_x(wx_j . u) (rows of the slot box).
 struct SepTerms {

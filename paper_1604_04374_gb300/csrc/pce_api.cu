@@ -691,6 +691,8 @@ pce_status check_plan(pce_plan_t p) {
     return PCE_OK;
 }
 
+pce_status setup_sectioned(pce_plan* p, const float* h, cudaStream_t s);
+
 pce_status create_common(pce_plan_t* out, int ndims, const int64_t* shape, int m, const float* w,
                          const float* h, bool spectra, uint32_t flags, void* stream) {
     if (!out) return fail(PCE_ERR_INVALID, "out is NULL");
@@ -699,7 +701,12 @@ pce_status create_common(pce_plan_t* out, int ndims, const int64_t* shape, int m
     pce_status st = validate_shape(ndims, shape, ny, nx);
     if (st) return st;
     if (m < 1) return fail(PCE_ERR_INVALID, "m must be >= 1 (got %d)", m);
-    if (flags & ~(uint32_t)(PCE_FLAG_UNFUSED | PCE_FLAG_LOWP_STORAGE | PCE_FLAG_PRODUCT_CONVOLUTION))
+    if ((flags & PCE_FLAG_SECTIONED) &&
+        (ndims != 2 || spectra || (flags & (PCE_FLAG_UNFUSED | PCE_FLAG_LOWP_STORAGE | PCE_FLAG_PRODUCT_CONVOLUTION))))
+        return fail(PCE_ERR_UNSUPPORTED, "PCE_FLAG_SECTIONED serves 2D convolution-product plans from h with "
+                                         "FP32 storage");
+    if (flags & ~(uint32_t)(PCE_FLAG_UNFUSED | PCE_FLAG_LOWP_STORAGE | PCE_FLAG_PRODUCT_CONVOLUTION |
+                            PCE_FLAG_SECTIONED))
         return fail(PCE_ERR_INVALID, "unknown flag bits 0x%x", flags);
     if ((flags & PCE_FLAG_UNFUSED) && (flags & PCE_FLAG_LOWP_STORAGE))
         return fail(PCE_ERR_INVALID, "PCE_FLAG_UNFUSED runs FP32 storage only");
@@ -841,6 +848,7 @@ pce_status create_common(pce_plan_t* out, int ndims, const int64_t* shape, int m
         if (e1) return bail(fail(PCE_ERR_CUDA, "spectrum split: %s", cudaGetErrorString(e1)));
     }
     if ((flags & PCE_FLAG_LOWP_STORAGE) && (st = quantize_plan(p, s))) return bail(st);
+    if ((flags & PCE_FLAG_SECTIONED) && (st = setup_sectioned(p, h, s))) return bail(st);
     cudaError_t e = cudaStreamSynchronize(s);
     if (e) return bail(fail(PCE_ERR_CUDA, "plan set-up: %s", cudaGetErrorString(e)));
     *out = p;
@@ -959,6 +967,188 @@ pce_status setup_separable(pce_plan* p, const float* wy, const float* wx, cudaSt
     return PCE_OK;
 }
 
+// h_k's support placed into a 1024 x lc section at its signed offsets:
+// sec[k][(dr0 + i) mod 1024][(dc0 + j) mod lc] = h_k[(sr0 + i) mod ny][(sc0 + j) mod nx]
+struct HSupport {
+    int sr0, snr, sc0, snc;   // cyclic support of h_k in the grid
+    int dr0, dc0;             // its first offsets, signed
+};
+
+__global__ void k_place_h(const float* __restrict__ h, int ny, int nx, const HSupport* __restrict__ sup, int m,
+                          int lc, float* sec) {
+    const long long total = (long long)m * 1024 * lc;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(i / (1024LL * lc));
+        const int e = (int)(i % (1024LL * lc));
+        const int pr = e / lc, pc = e % lc;
+        const HSupport sp = sup[k];
+        // section position (pr, pc) holds offset (dr0 + i, dc0 + j) with i = (pr - dr0) mod 1024
+        const int ii = ((pr - sp.dr0) % 1024 + 1024) % 1024;
+        const int jj = ((pc - sp.dc0) % lc + lc) % lc;
+        float v = 0.f;
+        if (ii < sp.snr && jj < sp.snc)
+            v = h[((long long)k * ny + (sp.sr0 + ii) % ny) * nx + (sp.sc0 + jj) % nx];
+        sec[i] = v;
+    }
+}
+
+// Sections of PCE_FLAG_SECTIONED: support of every h_k, section size, the
+// section spectra of h_k, the windows of both directions, work lists, scratch.
+pce_status setup_sectioned(pce_plan* p, const float* h, cudaStream_t s) {
+    const int m = p->m, ny = p->ny, nx = p->nx;
+    // exact support of every h_k (rows, columns)
+    unsigned char* flags = nullptr;
+    const size_t nflags = (size_t)m * (ny + nx);
+    PCE_CK(cudaMalloc(&flags, nflags));
+    cudaError_t e = cudaMemsetAsync(flags, 0, nflags, s);
+    if (e == cudaSuccess) {
+        k_support<<<grid_for((long long)m * ny * nx), 256, 0, s>>>(h, m, ny, nx, flags, flags + (size_t)m * ny);
+        e = cudaGetLastError();
+    }
+    std::vector<unsigned char> hf(nflags);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hf.data(), flags, nflags, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(flags);
+    PCE_CK(e);
+    std::vector<HSupport> sup(m);
+    int need_c = 1;
+    for (int k = 0; k < m; ++k) {
+        HSupport& sp = sup[k];
+        cyclic_support(&hf[(size_t)k * ny], ny, sp.sr0, sp.snr);
+        cyclic_support(&hf[(size_t)m * ny + (size_t)k * nx], nx, sp.sc0, sp.snc);
+        if (sp.snr == 0 || sp.snc == 0) { sp.snr = 0; sp.snc = 0; }
+        sp.dr0 = sp.sr0 >= ny / 2 ? sp.sr0 - ny : sp.sr0;
+        sp.dc0 = sp.sc0 >= nx / 2 ? sp.sc0 - nx : sp.sc0;
+        const Box& b = p->box[k];
+        if (b.nr == 0 || sp.snr == 0) continue;
+        if (b.nr + sp.snr - 1 > 1024)
+            return fail(PCE_ERR_UNSUPPORTED, "term %d: box rows %d + support rows %d - 1 exceed a 1024-row section",
+                        k, b.nr, sp.snr);
+        need_c = std::max(need_c, b.nc + sp.snc - 1);
+    }
+    int lc = 16;
+    while (lc < need_c) lc *= 2;
+    if (lc > 2048)
+        return fail(PCE_ERR_UNSUPPORTED, "box columns + support columns - 1 = %d exceed a 2048-column section", need_c);
+    // windows
+    std::vector<SecGeom> gf(m), ga(m);
+    std::vector<int2> ibox, iwin;
+    int rows_max = 1;
+    for (int k = 0; k < m; ++k) {
+        const Box& b = p->box[k];
+        const HSupport& sp = sup[k];
+        SecGeom f{};
+        f.r0 = b.r0;
+        f.c0 = b.c0;
+        f.woff = b.woff;
+        f.ldw = b.ldw;
+        const bool live = b.nr > 0 && sp.snr > 0;
+        const int wr = live ? b.nr + sp.snr - 1 : 0;
+        f.in_lo_r = 0;
+        f.in_rows = live ? b.nr : 0;
+        f.in_lo_c = 0;
+        f.in_hi_c = b.nc - 1;
+        f.out_lo_r = sp.dr0;
+        f.out_rows = wr;
+        f.out_lo_c = sp.dc0;
+        f.out_hi_c = b.nc - 1 + sp.dc0 + sp.snc - 1;
+        SecGeom a = f;
+        a.in_lo_r = f.out_lo_r;
+        a.in_rows = f.out_rows;
+        a.in_lo_c = f.out_lo_c;
+        a.in_hi_c = f.out_hi_c;
+        a.out_lo_r = 0;
+        a.out_rows = f.in_rows;
+        a.out_lo_c = 0;
+        a.out_hi_c = b.nc - 1;
+        gf[k] = f;
+        ga[k] = a;
+        for (int q = 0; q < (f.in_rows + 1) / 2; ++q) ibox.push_back(make_int2(k, q));
+        for (int q = 0; q < (wr + 1) / 2; ++q) iwin.push_back(make_int2(k, q));
+        rows_max = std::max(rows_max, wr);
+    }
+    pce_status st;
+    // twiddles: one-warp 1024-point columns, Stockham rows of lc
+    if (!p->tw1024) {
+        if ((st = dev_alloc(&p->tw1024, 1024))) return st;
+        k_twiddles_1024<<<4, 256, 0, s>>>(p->tw1024);
+        PCE_CK(cudaGetLastError());
+    }
+    if ((st = dev_alloc(&p->sec_twc, (size_t)std::max(1, twiddle_len(lc))))) return st;
+    k_twiddles<<<grid_for(twiddle_len(lc)), 256, 0, s>>>(p->sec_twc, lc);
+    float2* twr = nullptr;   // Stockham twiddles of 1024 (the column pass of the section spectra)
+    if ((st = dev_alloc(&twr, (size_t)twiddle_len(1024)))) return st;
+    k_twiddles<<<grid_for(twiddle_len(1024)), 256, 0, s>>>(twr, 1024);
+    PCE_CK(cudaGetLastError());
+    // section spectra of h_k: place, row R2C, column FFT, transpose
+    const int lch = lc / 2;
+    HSupport* dsup = nullptr;
+    float* sec = nullptr;
+    float2* S = nullptr;
+    float2* hs = nullptr;
+    auto cleanup = [&]() {
+        if (dsup) cudaFree(dsup);
+        if (sec) cudaFree(sec);
+        if (S) cudaFree(S);
+        if (hs) cudaFree(hs);
+        cudaFree(twr);
+    };
+    e = cudaMalloc(&dsup, sizeof(HSupport) * m);
+    if (e == cudaSuccess) e = cudaMalloc(&sec, sizeof(float) * (size_t)m * 1024 * lc);
+    if (e == cudaSuccess) e = cudaMalloc(&S, sizeof(float2) * (size_t)m * 1024 * lch);
+    if (e == cudaSuccess) e = cudaMalloc(&hs, sizeof(float2) * (size_t)m * 1024 * lch);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dsup, sup.data(), sizeof(HSupport) * m, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        k_place_h<<<grid_for((long long)m * 1024 * lc), 256, 0, s>>>(h, ny, nx, dsup, m, lc, sec);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = pce::launch_rows_r2c(lc, false, dim3(r2c_blocks(512, lc), m), s, sec, 1024LL * lc, 1024, nullptr, false,
+                                 nullptr, nullptr, 512, S, 1024LL * lch, 0, p->sec_twc, p->tw1024);
+    if (e == cudaSuccess && (st = dev_alloc(&p->hsN, (size_t)m * 1024)) != PCE_OK) {
+        cleanup();
+        return st;
+    }
+    const int cpc = pce::cols_columns_per_cta(1024);
+    if (e == cudaSuccess)
+        e = pce::launch_cols_spec(1024, dim3(m, (lch + cpc - 1) / cpc), s, S, lch, hs, p->hsN, twr);
+    if (e == cudaSuccess && (st = dev_alloc(&p->hsT, (size_t)m * 1024 * lch)) != PCE_OK) {
+        cleanup();
+        return st;
+    }
+    if (e == cudaSuccess) {
+        k_transpose_hh<<<grid_for((long long)m * 1024 * lch), 256, 0, s>>>(hs, m, 1024, lch, p->hsT);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cleanup();
+    if (e != cudaSuccess) return fail(PCE_ERR_CUDA, "section spectra: %s", cudaGetErrorString(e));
+    // windows, work lists, scratch
+    if ((st = dev_alloc(&p->d_geo_f, (size_t)m))) return st;
+    if ((st = dev_alloc(&p->d_geo_a, (size_t)m))) return st;
+    if ((st = dev_alloc(&p->sec_items_box, std::max<size_t>(ibox.size(), 1)))) return st;
+    if ((st = dev_alloc(&p->sec_items_win, std::max<size_t>(iwin.size(), 1)))) return st;
+    PCE_CK(cudaMemcpyAsync(p->d_geo_f, gf.data(), sizeof(SecGeom) * m, cudaMemcpyHostToDevice, s));
+    PCE_CK(cudaMemcpyAsync(p->d_geo_a, ga.data(), sizeof(SecGeom) * m, cudaMemcpyHostToDevice, s));
+    if (!ibox.empty())
+        PCE_CK(cudaMemcpyAsync(p->sec_items_box, ibox.data(), sizeof(int2) * ibox.size(), cudaMemcpyHostToDevice, s));
+    if (!iwin.empty())
+        PCE_CK(cudaMemcpyAsync(p->sec_items_win, iwin.data(), sizeof(int2) * iwin.size(), cudaMemcpyHostToDevice, s));
+    PCE_CK(cudaStreamSynchronize(s));
+    p->n_items_box = (int)ibox.size();
+    p->n_items_win = (int)iwin.size();
+    p->sec_lc = lc;
+    p->sec_k = (long long)rows_max * lch;
+    p->sec_b = (long long)m * p->sec_k;
+    const long long per_b = 2 * p->sec_b * (long long)sizeof(float2);
+    p->sec_chunk = (int)std::max<long long>(1, std::min<long long>(kMaxChunk, kScratchBudget / per_b));
+    if ((st = dev_alloc(&p->scrZs, (size_t)(p->sec_b * p->sec_chunk)))) return st;
+    if ((st = dev_alloc(&p->scrAs, (size_t)(p->sec_b * p->sec_chunk)))) return st;
+    p->sect = true;
+    return PCE_OK;
+}
+
 pce_status check_io(pce_plan_t p, const float* in, const float* out, int64_t batch) {
     if (batch < 0) return fail(PCE_ERR_INVALID, "batch must be >= 0");
     if (batch == 0) return PCE_OK;
@@ -979,7 +1169,10 @@ pce_status check_io(pce_plan_t p, const float* in, const float* out, int64_t bat
 
 // Z/Q and A/V float2 per right-hand side of the plan's apply.
 void scratch_strides(const pce_plan* p, long long& zs, long long& as) {
-    if (p->l1) {
+    if (p->sect) {
+        zs = p->sec_b;
+        as = p->sec_b;
+    } else if (p->l1) {
         zs = (long long)((p->m + 1) / 2) * p->nx;
         as = p->nx;
     } else if (p->ndims == 1) {
@@ -993,10 +1186,13 @@ void scratch_strides(const pce_plan* p, long long& zs, long long& as) {
 
 pce_rt::Scratch own_scratch(const pce_plan* p) {
     pce_rt::Scratch r;
-    r.Z = p->scrZ;
-    r.A = p->scrA;
+    r.Z = p->sect ? p->scrZs : p->scrZ;
+    r.A = p->sect ? p->scrAs : p->scrA;
     scratch_strides(p, r.zstride, r.astride);
-    r.chunk = p->run_chunk > 0 ? std::min(p->run_chunk, p->bchunk) : p->bchunk;
+    if (p->sect)
+        r.chunk = p->sec_chunk;
+    else
+        r.chunk = p->run_chunk > 0 ? std::min(p->run_chunk, p->bchunk) : p->bchunk;
     return r;
 }
 
@@ -1215,6 +1411,45 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
         return PCE_OK;
     }
     if (p->flags & PCE_FLAG_UNFUSED) return apply_plain(p, in, out, batch, adjoint, s);
+    if (p->sect) {
+        // sections (Lemma 3.2): every term on 1024 x sec_lc points, added into the output
+        const int lc = p->sec_lc, lch = lc / 2;
+        const int fpc = pce::sec_rows_per_cta(lc);
+        const int cpc = pce::cols_columns_per_cta(1024);
+        const float sscale = 1.0f / (1024.0f * (float)lc);
+        const long long nchs = (batch + scr.chunk - 1) / scr.chunk;
+        const long long sbal = (batch + nchs - 1) / nchs;
+        const pce::SecGeom* geo = adjoint ? p->d_geo_a : p->d_geo_f;
+        const int2* it_in = adjoint ? p->sec_items_win : p->sec_items_box;
+        const int n_in = adjoint ? p->n_items_win : p->n_items_box;
+        const int2* it_out = adjoint ? p->sec_items_box : p->sec_items_win;
+        const int n_out = adjoint ? p->n_items_box : p->n_items_win;
+        for (long long b0 = 0; b0 < batch && e == cudaSuccess; b0 += sbal) {
+            const int nb = (int)std::min<long long>(sbal, batch - b0);
+            float* dst = out + b0 * P;
+            e = cudaMemsetAsync(dst, 0, sizeof(float) * P * nb, s);
+            if (e == cudaSuccess && n_in > 0)
+                e = timed(p, adjoint ? PCE_KERNEL_ROWS_R2C : PCE_KERNEL_ROWS_R2C_WINDOW, s, [&] {
+                    return pce::launch_sec_r2c(lc, !adjoint, dim3((n_in + fpc - 1) / fpc, nb), s, in + b0 * P, P, ny,
+                                               nx, p->wbox, geo, it_in, n_in, scr.Z, scr.zstride, p->sec_k,
+                                               p->sec_twc);
+                });
+            if (e == cudaSuccess)
+                e = timed(p, adjoint ? PCE_KERNEL_COLS_ADJ : PCE_KERNEL_COLS_FWD, s, [&] {
+                    return pce::launch_sec_cols(adjoint, dim3(m, (lch + cpc - 1) / cpc), s, scr.Z, scr.zstride,
+                                                p->sec_k, nb, p->hsT, p->hsN, geo, lch, scr.A, scr.astride, p->sec_k,
+                                                p->tw1024);
+                });
+            if (e == cudaSuccess && n_out > 0)
+                e = timed(p, adjoint ? PCE_KERNEL_ROWS_ADJ : PCE_KERNEL_ROWS_C2R, s, [&] {
+                    return pce::launch_sec_c2r(lc, adjoint, dim3((n_out + fpc - 1) / fpc, nb), s, scr.A, scr.astride,
+                                               p->sec_k, geo, it_out, n_out, p->wbox, dst, P, ny, nx, sscale,
+                                               p->sec_twc);
+                });
+        }
+        if (e) return fail(PCE_ERR_CUDA, "sectioned apply launch: %s", cudaGetErrorString(e));
+        return PCE_OK;
+    }
     const bool warp = (scr.col_variant >= 0 ? scr.col_variant : p->col_variant) == 0;
     const int rowv = scr.row_variant >= 0 ? scr.row_variant : p->row_variant;
     // separable fast path: one-warp column kernels only
@@ -1504,6 +1739,7 @@ int64_t pce_launch_count(pce_plan_t plan, int adjoint, int64_t batch) {
     const int64_t c = own_scratch(plan).chunk;
     const int64_t chunks = (batch + c - 1) / c;
     if (plan->l1) return chunks * 3;
+    if (plan->sect) return chunks * 3;
     if (plan->ndims == 1) return 1;
     if (plan->flags & PCE_FLAG_UNFUSED) {
         int64_t mk = 0;

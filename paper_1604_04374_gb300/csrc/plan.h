@@ -12,6 +12,7 @@
 #include "pce.h"
 
 using pce::Box;
+using pce::SecGeom;
 
 struct pce_plan {
     int ndims = 0, ny = 1, nx = 0, m = 0;
@@ -81,6 +82,21 @@ struct pce_plan {
     int* skptr = nullptr;       // G3 lists of the slots
     int* sklist = nullptr;
     long long zk_s = 0;         // float2 per slot (rows of the largest slot box x nx/2)
+    // sectioned apply (PCE_FLAG_SECTIONED): per term a 1024 x sec_lc section
+    bool sect = false;
+    int sec_lc = 0;
+    SecGeom* d_geo_f = nullptr;   // [m] forward windows
+    SecGeom* d_geo_a = nullptr;   // [m] adjoint windows
+    int2* sec_items_box = nullptr;   // (k, pair) over the box rows
+    int2* sec_items_win = nullptr;   // (k, pair) over the forward output window rows
+    int n_items_box = 0, n_items_win = 0;
+    float2* hsT = nullptr;        // [m][sec_lc/2][1024] section spectra of h_k (c = 0: DC column)
+    float2* hsN = nullptr;        // [m][1024] Nyquist column
+    float2* sec_twc = nullptr;    // Stockham twiddles of sec_lc
+    float2* scrZs = nullptr;      // [chunk][m][rows][sec_lc/2]
+    float2* scrAs = nullptr;
+    long long sec_k = 0, sec_b = 0;   // float2 per term, per right-hand side
+    int sec_chunk = 1;
     // per-kernel timing
     bool timing = false;
     std::vector<cudaEvent_t> ev;          // pairs (start, stop)
@@ -99,7 +115,8 @@ struct pce_plan {
         void* ptrs[] = {d_box,  wbox,  hh,     hN,   hhT,   tw1024, d_status, twx, twy == twx ? nullptr : twy,
                         items,  kptr,  klist,  scrZ, scrA,  wbox16, hh16,     hN16, hhT16, hscale,
                         twN,    hh4,   wrow, wxbox, d_vbox, d_kslot, d_korder, sitems, skptr, sklist,
-                        hN2,    hN2_16, tw2048l};
+                        hN2,    hN2_16, tw2048l, d_geo_f, d_geo_a, sec_items_box, sec_items_win, hsT, hsN,
+                        sec_twc, scrZs, scrAs};
         for (void* q : ptrs)
             if (q) cudaFree(q);
     }

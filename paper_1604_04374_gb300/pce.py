@@ -18,6 +18,7 @@ PCE_FLAG_NONE = 0
 PCE_FLAG_UNFUSED = 1
 PCE_FLAG_LOWP_STORAGE = 2
 PCE_FLAG_PRODUCT_CONVOLUTION = 4
+PCE_FLAG_SECTIONED = 8
 STATUS_NAMES = {0: "PCE_OK", 1: "PCE_ERR_INVALID", 2: "PCE_ERR_UNSUPPORTED", 3: "PCE_ERR_OOM",
                 4: "PCE_ERR_CUDA", 5: "PCE_ERR_TIMEOUT"}
 

@@ -1,0 +1,125 @@
+"""GPU: sectioned applies (PCE_FLAG_SECTIONED, Lemma 3.2) against the FP64 oracle.
+
+Every term is convolved on a 1024-row section sized to its window box plus
+the support of h_k and added into the output; the operator is the same as the
+whole-grid path's (the rounding order differs, and the atomic adds make it
+vary from run to run), so both are checked against the oracle.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import expansion as E
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    from paper_1604_04374_gb300 import build
+    build.build()
+    torch.cuda.init()
+    return torch
+
+
+def dev(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def rel(got, ref):
+    got = got.reshape(got.shape[0], -1)
+    ref = ref.reshape(ref.shape[0], -1)
+    return float(np.max(np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)))
+
+
+def short_h(pr, seed, ra=5, rb=3):
+    """Random impulse responses supported on offsets [-ra, rb] x [-rb, ra] (asymmetric)."""
+    rng = np.random.default_rng(seed)
+    ny, nx = pr.shape
+    h = np.zeros_like(pr.h)
+    rows = np.arange(-ra, rb + 1) % ny
+    cols = np.arange(-rb, ra + 1) % nx
+    h[:, rows[:, None], cols[None, :]] = rng.standard_normal((pr.m, rows.size, cols.size)).astype(np.float32)
+    return h
+
+
+@pytest.mark.parametrize("ny,nx,m,batch", [(2048, 64, 64, 2), (1024, 128, 16, 1), (2048, 256, 64, 1)])
+def test_sectioned_matches_oracle(torch_cuda, ny, nx, m, batch):
+    torch = torch_cuda
+    from paper_1604_04374_gb300 import Plan, pce
+    pr = synth.problem_2d(ny, nx, m, batch, 400 + m, "normal")
+    h = short_h(pr, 7 + m)
+    plan = Plan(dev(torch, pr.w), h=dev(torch, h), flags=pce.PCE_FLAG_SECTIONED)
+    u = dev(torch, pr.u)
+    assert rel(host(plan.apply(u)), E.apply(pr.u, pr.w, h)) < TOL
+    assert rel(host(plan.apply_adjoint(u)), E.apply_adjoint(pr.u, pr.w, h)) < TOL
+    assert plan.launch_count(False, batch) == 3 and plan.launch_count(True, batch) == 3
+
+
+def test_sectioned_with_psf_family_and_gradients(torch_cuda):
+    """The anisotropic PSFs of the 2D workloads (their exact support is found at plan
+    time); the gradients of a sectioned plan use its whole-grid structures."""
+    torch = torch_cuda
+    from paper_1604_04374_gb300 import Plan, pce
+    pr = synth.problem_2d(1024, 64, 16, 2, 431, "normal")
+    plan = Plan(dev(torch, pr.w), h=dev(torch, pr.h), flags=pce.PCE_FLAG_SECTIONED)
+    u = dev(torch, pr.u)
+    assert rel(host(plan.apply(u)), E.apply(pr.u, pr.w, pr.h)) < TOL
+    assert rel(host(plan.apply_adjoint(u)), E.apply_adjoint(pr.u, pr.w, pr.h)) < TOL
+    r = np.random.default_rng(3).standard_normal(pr.u.shape).astype(np.float32)
+    du, dw, dh = plan.backward(u, dev(torch, r))
+    rdu, rdw, _, rdh = E.grad(pr.u, pr.w, pr.h.astype(np.float64), r)
+    assert rel(host(du), rdu) < TOL and rel(host(dw)[None], rdw[None]) < TOL
+
+
+def test_sectioned_full_size_workload_sampled(torch_cuda):
+    """2048 x 2048, m = 64, B = 4 (the reduced-storage workload's operator in FP32):
+    sampled outputs against the oracle and agreement with the whole-grid path."""
+    torch = torch_cuda
+    from paper_1604_04374_gb300 import Plan, pce
+    pr = synth.workload("2d_2048_m64_b4")
+    u = dev(torch, pr.u)
+    sec = Plan(dev(torch, pr.w), h=dev(torch, pr.h), flags=pce.PCE_FLAG_SECTIONED)
+    gen = Plan(dev(torch, pr.w), h=dev(torch, pr.h))
+    ys, xs = host(sec.apply(u)), host(sec.apply_adjoint(u))
+    assert rel(ys, host(gen.apply(u))) < 2e-6
+    assert rel(xs, host(gen.apply_adjoint(u))) < 2e-6
+    rng = np.random.default_rng(4)
+    pts = np.stack([rng.integers(0, 2048, 24), rng.integers(0, 2048, 24)], axis=-1)
+    flat = pts[:, 0] * 2048 + pts[:, 1]
+    assert rel(ys.reshape(4, -1)[:, flat], E.apply_at(pr.u, pr.w, pr.h, pts)) < TOL
+    assert rel(xs.reshape(4, -1)[:, flat], E.apply_adjoint_at(pr.u, pr.w, pr.h, pts)) < TOL
+
+
+def test_sectioned_restrictions(torch_cuda):
+    torch = torch_cuda
+    from paper_1604_04374_gb300 import Plan, pce
+    from paper_1604_04374_gb300.pce import PceError
+    pr = synth.problem_2d(1024, 64, 16, 1, 440, "normal")
+    w, h = dev(torch, pr.w), dev(torch, pr.h)
+    for flags in (pce.PCE_FLAG_SECTIONED | pce.PCE_FLAG_LOWP_STORAGE,
+                  pce.PCE_FLAG_SECTIONED | pce.PCE_FLAG_PRODUCT_CONVOLUTION,
+                  pce.PCE_FLAG_SECTIONED | pce.PCE_FLAG_UNFUSED):
+        with pytest.raises(PceError) as e:
+            Plan(w, h=h, flags=flags)
+        assert e.value.status == pce.PCE_ERR_UNSUPPORTED
+    hhat = torch.zeros((16, 1024, 33), dtype=torch.complex64, device="cuda")
+    with pytest.raises(PceError) as e:
+        Plan(w, hhat=hhat, flags=pce.PCE_FLAG_SECTIONED)
+    assert e.value.status == pce.PCE_ERR_UNSUPPORTED
+    # boxes of 1023 rows plus the PSF support do not fit a 1024-row section
+    big = synth.problem_2d(2048, 32, 16, 1, 441, "normal")
+    with pytest.raises(PceError) as e:
+        Plan(dev(torch, big.w), h=dev(torch, big.h), flags=pce.PCE_FLAG_SECTIONED)
+    assert e.value.status == pce.PCE_ERR_UNSUPPORTED
+    w1 = dev(torch, np.ones((2, 256), np.float32))
+    with pytest.raises(PceError) as e:
+        Plan(w1, h=w1, flags=pce.PCE_FLAG_SECTIONED)
+    assert e.value.status == pce.PCE_ERR_UNSUPPORTED
