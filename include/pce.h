@@ -472,6 +472,39 @@ int pce_plan_tuning_log(pce_plan_t plan, int max_entries, int* chunk, int* col_v
 pce_status pce_construct_projection_1d(const float* T, int n, int m, float* h_out, float* w_out,
                                        void* stream);
 
+/*
+ * pce_construct_svd_1d -- the truncated singular value decomposition of a
+ * sampled time-varying impulse response (Section 5.1): T(x, y) ~ sum_k
+ * sigma_k f_k(x) e_k(y) with h_k = sigma_k f_k and w_k = e_k, the best rank-m
+ * approximation of T (and of the operator, in the Hilbert-Schmidt norm).
+ *
+ *   T          : device, [n][n] float32, T[d][j] as for
+ *                pce_construct_projection_1d; n in [16, 8192].
+ *   m          : terms, in [1, min(n, 256)].
+ *   oversample : extra directions of the randomised range finder (Halko,
+ *                Martinsson and Tropp, 2011), in [0, 256]; the subspace has
+ *                l = min(n, m + oversample) columns.  10 is typical.
+ *   power_iters: power iterations of the range finder, in [0, 16]; each
+ *                sharpens the subspace by the ratio sigma_{l+1} / sigma_k
+ *                squared.  2 is typical.
+ *   seed       : seed of the Gaussian test matrix (SplitMix64 counters,
+ *                Box-Muller).
+ *   h_out      : device, [m][n] float32: h_k = sigma_k f_k.
+ *   w_out      : device, [m][n] float32: w_k = e_k, orthonormal, signed so
+ *                that sum_j w_k[j] >= 0.
+ *   sigma_out  : device, [m] float32, or NULL: sigma_1 >= ... >= sigma_m.
+ *
+ * Products with T run on the device with FP64 sums; the factorisations of
+ * the n x l iterates (Householder QRs) and the one-sided Jacobi SVD of the
+ * l x l triangular factor run on the host in FP64.  Terms beyond the numerical
+ * rank of T (sigma_k <= 1e-12 sigma_1) are returned as zeros.  Allocates and
+ * frees temporary memory and synchronises `stream`.  PCE_ERR_INVALID for bad
+ * sizes or host pointers.
+ */
+pce_status pce_construct_svd_1d(const float* T, int n, int m, int oversample, int power_iters,
+                                unsigned long long seed, float* h_out, float* w_out, float* sigma_out,
+                                void* stream);
+
 #ifdef __cplusplus
 }
 #endif

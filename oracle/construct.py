@@ -97,3 +97,25 @@ def svd_truncate(T: np.ndarray, m: int) -> np.ndarray:
     """Best rank-m approximation (Section 5.1: h_k = sigma_k f_k, w_k = e_k)."""
     U, s, Vt = np.linalg.svd(T)
     return (U[:, :m] * s[:m]) @ Vt[:m]
+
+
+def svd_terms(T: np.ndarray, m: int, rank_tol: float = 1e-12):
+    """The m leading terms of the SVD of T (Section 5.1), as an expansion:
+    h [m][n] with h_k = sigma_k f_k (f_k the left singular vectors, over the
+    shift d), w [m][n] with w_k = e_k (right singular vectors, over the input
+    position j), and sigma [m], so that T[d][j] ~ sum_k h_k[d] w_k[j].  Each
+    pair's sign is fixed by sum_j w_k[j] >= 0; terms with sigma_k <=
+    rank_tol * sigma_1 (beyond the numerical rank) are zero."""
+    U, s, Vt = np.linalg.svd(np.asarray(T, dtype=np.float64))
+    n = T.shape[1]
+    h = np.zeros((m, T.shape[0]))
+    w = np.zeros((m, n))
+    sig = np.zeros(m)
+    for k in range(min(m, s.size)):
+        if not s[k] > rank_tol * s[0]:
+            continue
+        sgn = -1.0 if Vt[k].sum() < 0 else 1.0
+        sig[k] = s[k]
+        h[k] = sgn * s[k] * U[:, k]
+        w[k] = sgn * Vt[k]
+    return h, w, sig

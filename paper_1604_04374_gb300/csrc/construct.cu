@@ -170,3 +170,307 @@ extern "C" pce_status pce_construct_projection_1d(const float* T, int n, int m, 
     if (e != cudaSuccess) return fail(PCE_ERR_CUDA, "projection: %s", cudaGetErrorString(e));
     return PCE_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Truncated SVD of the TVIR (Section 5.1): T(x, y) ~ sum_k sigma_k f_k(x) e_k(y)
+// with h_k = sigma_k f_k and w_k = e_k, the best rank-m approximation.  The
+// leading singular subspace is found by the randomised range finder with
+// power iterations of Halko, Martinsson and Tropp (2011), the method the
+// paper's operation count refers to:
+//
+//   Y = T Omega                     (Omega: n x l Gaussian, l = m + oversampling)
+//   Q = orth(Y);  q times: Q = orth(T orth(T^t Q))
+//   B^t = T^t Q                     (n x l; B = Q^t T)
+//   B^t = Q2 R                      (host, FP64 Householder QR)
+//   R = U_R diag(sigma) V_R^t       (host, FP64 one-sided Jacobi)
+//   f_k = (Q V_R)_k,  e_k = (Q2 U_R)_k
+//
+// (no Gram matrix of B is formed, so small singular values keep their
+// relative accuracy and the e_k are orthonormal to rounding)
+//
+// orth() is the Q factor of a Householder QR (host, FP64): it keeps all l
+// directions, so singular values down to the rounding level of T survive.
+// The products with T are FP64 sums of the float32 T on the device.
+// ---------------------------------------------------------------------------
+namespace {
+
+// SplitMix64 (Steele, Lea and Flood, 2014): the counter-based generator of
+// the test matrix; its output for counter c is mix(seed + (c + 1) * gamma).
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// X[i][c] ~ N(0, 1) by the Box-Muller transform of two SplitMix64 draws
+__global__ void k_gaussian(long long total, unsigned long long seed, double* __restrict__ X) {
+    const unsigned long long gamma = 0x9E3779B97F4A7C15ull;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long a = splitmix64(seed + (2ull * i + 1ull) * gamma);
+        const unsigned long long b = splitmix64(seed + (2ull * i + 2ull) * gamma);
+        const double u1 = ((double)(a >> 11) + 1.0) * 0x1.0p-53;   // (0, 1]
+        const double u2 = (double)(b >> 11) * 0x1.0p-53;           // [0, 1)
+        X[i] = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+    }
+}
+
+// Y = T X (TRANS = false) or Y = T^t X (TRANS = true); T [n][n] float32,
+// X, Y [n][l] FP64.  One thread per output element; the l threads of a row
+// share the T element (broadcast) and read X coalesced.
+template <bool TRANS>
+__global__ void k_tvir_mul(const float* __restrict__ T, const double* __restrict__ X, int n, int l,
+                           double* __restrict__ Y) {
+    const long long total = (long long)n * l;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e / l), c = (int)(e % l);
+        double s = 0.0;
+        if (TRANS) {
+            for (int i = 0; i < n; ++i) s += (double)__ldg(&T[(long long)i * n + r]) * X[(long long)i * l + c];
+        } else {
+            const float* Tr = T + (long long)r * n;
+            for (int j = 0; j < n; ++j) s += (double)__ldg(&Tr[j]) * X[(long long)j * l + c];
+        }
+        Y[e] = s;
+    }
+}
+
+// Z = Y M, Y [n][l], M [l][l2], Z [n][l2]
+__global__ void k_right_mul(const double* __restrict__ Y, const double* __restrict__ M, int n, int l, int l2,
+                            double* __restrict__ Z) {
+    const long long total = (long long)n * l2;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / l2), c = (int)(e % l2);
+        double s = 0.0;
+        for (int a = 0; a < l; ++a) s += Y[(long long)i * l + a] * M[a * l2 + c];
+        Z[e] = s;
+    }
+}
+
+// out[k][i] = scale[k] * Z[i][k] (float32), Z [n][m]
+__global__ void k_terms_out(const double* __restrict__ Z, const double* __restrict__ scale, int n, int m,
+                            float* __restrict__ out) {
+    const long long total = (long long)n * m;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(e / n), i = (int)(e % n);
+        out[e] = (float)(scale[k] * Z[(long long)i * m + k]);
+    }
+}
+
+}  // namespace
+
+namespace {
+
+// Householder QR of A (n x l, n >= l, row-major, destroyed) (Golub and Van
+// Loan, Section 5.2): A = Q2 R with Q2 (n x l) orthonormal columns, R (l x l)
+// upper triangular.
+void householder_qr(std::vector<double>& A, int n, int l, std::vector<double>& Q2, std::vector<double>& R) {
+    std::vector<std::vector<double>> vs(l);
+    std::vector<double> beta(l, 0.0);
+    for (int j = 0; j < l; ++j) {
+        double nrm = 0.0;
+        for (int i = j; i < n; ++i) nrm += A[(size_t)i * l + j] * A[(size_t)i * l + j];
+        nrm = std::sqrt(nrm);
+        std::vector<double>& v = vs[j];
+        v.assign(n - j, 0.0);
+        for (int i = j; i < n; ++i) v[i - j] = A[(size_t)i * l + j];
+        if (nrm == 0.0) continue;   // zero column: no reflection
+        const double x0 = v[0];
+        v[0] = x0 + (x0 >= 0.0 ? nrm : -nrm);
+        double vv = 0.0;
+        for (double x : v) vv += x * x;
+        beta[j] = 2.0 / vv;
+        for (int c = j; c < l; ++c) {   // A[j:, c] -= beta v (v . A[j:, c])
+            double d = 0.0;
+            for (int i = j; i < n; ++i) d += v[i - j] * A[(size_t)i * l + c];
+            d *= beta[j];
+            for (int i = j; i < n; ++i) A[(size_t)i * l + c] -= d * v[i - j];
+        }
+    }
+    R.assign((size_t)l * l, 0.0);
+    for (int i = 0; i < l; ++i)
+        for (int c = i; c < l; ++c) R[(size_t)i * l + c] = A[(size_t)i * l + c];
+    // Q2 = H_0 H_1 ... H_{l-1} [I; 0], accumulated from the last reflection
+    Q2.assign((size_t)n * l, 0.0);
+    for (int i = 0; i < l; ++i) Q2[(size_t)i * l + i] = 1.0;
+    for (int j = l - 1; j >= 0; --j) {
+        if (beta[j] == 0.0) continue;
+        const std::vector<double>& v = vs[j];
+        for (int c = 0; c < l; ++c) {
+            double d = 0.0;
+            for (int i = j; i < n; ++i) d += v[i - j] * Q2[(size_t)i * l + c];
+            d *= beta[j];
+            for (int i = j; i < n; ++i) Q2[(size_t)i * l + c] -= d * v[i - j];
+        }
+    }
+}
+
+// One-sided Jacobi SVD of a square R (l x l) (Hestenes; Demmel and Veselic,
+// 1992): plane rotations from the right make the columns of R V mutually
+// orthogonal; sigma_c = |(R V)_c|, U_R = (R V) diag(1/sigma), V_R = V.
+// Sweeps until every pair is orthogonal to 1e-15 relative, at most 60.
+void one_sided_jacobi(std::vector<double> R, int l, std::vector<double>& sv, std::vector<double>& U,
+                      std::vector<double>& V) {
+    V.assign((size_t)l * l, 0.0);
+    for (int i = 0; i < l; ++i) V[(size_t)i * l + i] = 1.0;
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        bool rotated = false;
+        for (int p = 0; p < l; ++p)
+            for (int q = p + 1; q < l; ++q) {
+                double al = 0.0, be = 0.0, ga = 0.0;
+                for (int i = 0; i < l; ++i) {
+                    const double rp = R[(size_t)i * l + p], rq = R[(size_t)i * l + q];
+                    al += rp * rp;
+                    be += rq * rq;
+                    ga += rp * rq;
+                }
+                if (ga == 0.0 || std::fabs(ga) <= 1e-15 * std::sqrt(al * be)) continue;
+                rotated = true;
+                const double zeta = (be - al) / (2.0 * ga);
+                const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (std::fabs(zeta) + std::sqrt(1.0 + zeta * zeta));
+                const double c = 1.0 / std::sqrt(1.0 + t * t), s = t * c;
+                for (int i = 0; i < l; ++i) {
+                    const double rp = R[(size_t)i * l + p], rq = R[(size_t)i * l + q];
+                    R[(size_t)i * l + p] = c * rp - s * rq;
+                    R[(size_t)i * l + q] = s * rp + c * rq;
+                    const double vp = V[(size_t)i * l + p], vq = V[(size_t)i * l + q];
+                    V[(size_t)i * l + p] = c * vp - s * vq;
+                    V[(size_t)i * l + q] = s * vp + c * vq;
+                }
+            }
+        if (!rotated) break;
+    }
+    sv.assign(l, 0.0);
+    U.assign((size_t)l * l, 0.0);
+    for (int c = 0; c < l; ++c) {
+        double nrm = 0.0;
+        for (int i = 0; i < l; ++i) nrm += R[(size_t)i * l + c] * R[(size_t)i * l + c];
+        sv[c] = std::sqrt(nrm);
+        if (sv[c] > 0.0)
+            for (int i = 0; i < l; ++i) U[(size_t)i * l + c] = R[(size_t)i * l + c] / sv[c];
+    }
+}
+
+}  // namespace
+
+namespace {
+
+// Y [n][l] (device) <- the Q factor of its Householder QR, computed on the
+// host in FP64; returns false on a CUDA error (in e).
+bool orth(double* Y, int n, int l, cudaStream_t s, cudaError_t& e) {
+    std::vector<double> a((size_t)n * l), q, r;
+    e = cudaMemcpyAsync(a.data(), Y, sizeof(double) * a.size(), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return false;
+    householder_qr(a, n, l, q, r);
+    e = cudaMemcpyAsync(Y, q.data(), sizeof(double) * q.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // q must outlive the copy
+    return e == cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" pce_status pce_construct_svd_1d(const float* T, int n, int m, int oversample, int power_iters,
+                                           unsigned long long seed, float* h_out, float* w_out, float* sigma_out,
+                                           void* stream) {
+    if (n < 16 || n > 8192) return fail(PCE_ERR_INVALID, "n must be in [16, 8192] (got %d)", n);
+    if (m < 1 || m > std::min(n, 256)) return fail(PCE_ERR_INVALID, "m must be in [1, min(n, 256)] (got %d)", m);
+    if (oversample < 0 || oversample > 256 || power_iters < 0 || power_iters > 16)
+        return fail(PCE_ERR_INVALID, "oversample must be in [0, 256] and power_iters in [0, 16]");
+    if (!pce_rt::is_device_ptr(T) || !pce_rt::is_device_ptr(h_out) || !pce_rt::is_device_ptr(w_out) ||
+        (sigma_out && !pce_rt::is_device_ptr(sigma_out)))
+        return fail(PCE_ERR_INVALID, "T, h_out, w_out and sigma_out must be device pointers");
+    const int l = std::min(n, m + oversample);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    double *Y = nullptr, *Z = nullptr, *tmp = nullptr, *M = nullptr, *sc = nullptr;
+    auto cleanup = [&]() {
+        for (double* q : {Y, Z, tmp, M, sc})
+            if (q) cudaFree(q);
+    };
+    const size_t nl = (size_t)n * l;
+    cudaError_t e = cudaMalloc(&Y, sizeof(double) * nl);
+    if (e == cudaSuccess) e = cudaMalloc(&Z, sizeof(double) * nl);
+    if (e == cudaSuccess) e = cudaMalloc(&tmp, sizeof(double) * nl);
+    if (e == cudaSuccess) e = cudaMalloc(&M, sizeof(double) * (size_t)l * l);
+    if (e == cudaSuccess) e = cudaMalloc(&sc, sizeof(double) * (size_t)std::max(l, m));
+    if (e != cudaSuccess) {
+        cleanup();
+        return fail(e == cudaErrorMemoryAllocation ? PCE_ERR_OOM : PCE_ERR_CUDA, "svd set-up: %s",
+                    cudaGetErrorString(e));
+    }
+    // range finder: Y = T Omega, then power iterations
+    k_gaussian<<<grid_of((long long)nl), 256, 0, s>>>((long long)nl, seed, Z);
+    k_tvir_mul<false><<<grid_of((long long)nl), 256, 0, s>>>(T, Z, n, l, Y);
+    e = cudaGetLastError();
+    bool ok = e == cudaSuccess && orth(Y, n, l, s, e);
+    for (int it = 0; it < power_iters && ok; ++it) {
+        k_tvir_mul<true><<<grid_of((long long)nl), 256, 0, s>>>(T, Y, n, l, Z);
+        e = cudaGetLastError();
+        ok = e == cudaSuccess && orth(Z, n, l, s, e);
+        if (!ok) break;
+        k_tvir_mul<false><<<grid_of((long long)nl), 256, 0, s>>>(T, Z, n, l, Y);
+        e = cudaGetLastError();
+        ok = e == cudaSuccess && orth(Y, n, l, s, e);
+    }
+    // B^t = T^t Q (into Z), brought to the host for its SVD
+    std::vector<double> bt(nl);
+    if (ok) {
+        k_tvir_mul<true><<<grid_of((long long)nl), 256, 0, s>>>(T, Y, n, l, Z);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(bt.data(), Z, sizeof(double) * nl, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    if (!ok || e != cudaSuccess) {
+        cleanup();
+        return fail(PCE_ERR_CUDA, "svd range finder: %s", cudaGetErrorString(e));
+    }
+    // B^t = Q2 R (Householder), R = U_R diag(sigma) V_R^t (one-sided Jacobi), so
+    // that T ~ Q B = (Q V_R) diag(sigma) (Q2 U_R)^t: f_k = (Q V_R)_k, e_k = (Q2 U_R)_k
+    std::vector<double> q2, R;
+    householder_qr(bt, n, l, q2, R);
+    std::vector<double> sv, UR, VR;
+    one_sided_jacobi(R, l, sv, UR, VR);
+    std::vector<int> order(l);
+    for (int i = 0; i < l; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return sv[a] > sv[b]; });
+    const double smax = sv[order[0]];
+    std::vector<double> vm((size_t)l * m, 0.0), sig(m, 0.0);
+    std::vector<float> wf((size_t)m * n, 0.f);
+    std::vector<double> q2sum(l, 0.0);
+    for (int i = 0; i < n; ++i)
+        for (int a = 0; a < l; ++a) q2sum[a] += q2[(size_t)i * l + a];
+    for (int k = 0; k < m && k < l; ++k) {
+        const int c = order[k];
+        if (!(sv[c] > 1e-12 * smax)) continue;   // no range left: a zero term
+        // sign: sum_j e_k[j] >= 0
+        double t = 0.0;
+        for (int a = 0; a < l; ++a) t += q2sum[a] * UR[(size_t)a * l + c];
+        const double sgn = t < 0.0 ? -1.0 : 1.0;
+        sig[k] = sv[c];
+        for (int a = 0; a < l; ++a) vm[(size_t)a * m + k] = sgn * VR[(size_t)a * l + c];
+        for (int i = 0; i < n; ++i) {
+            double x = 0.0;
+            for (int a = 0; a < l; ++a) x += q2[(size_t)i * l + a] * UR[(size_t)a * l + c];
+            wf[(size_t)k * n + i] = (float)(sgn * x);
+        }
+    }
+    std::vector<float> sigf(sig.begin(), sig.end());
+    // h_k = sigma_k (Q V_R)_k on the device; w_k from the host
+    e = cudaMemcpyAsync(M, vm.data(), sizeof(double) * vm.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sc, sig.data(), sizeof(double) * m, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        k_right_mul<<<grid_of((long long)n * m), 256, 0, s>>>(Y, M, n, l, m, tmp);
+        k_terms_out<<<grid_of((long long)n * m), 256, 0, s>>>(tmp, sc, n, m, h_out);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(w_out, wf.data(), sizeof(float) * wf.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && sigma_out)
+        e = cudaMemcpyAsync(sigma_out, sigf.data(), sizeof(float) * m, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cleanup();
+    if (e != cudaSuccess) return fail(PCE_ERR_CUDA, "svd: %s", cudaGetErrorString(e));
+    return PCE_OK;
+}

@@ -99,6 +99,9 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.pce_batch_autotune.argtypes = [P, P]
     lib.pce_construct_projection_1d.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P, P]
     lib.pce_construct_projection_1d.restype = ctypes.c_int
+    lib.pce_construct_svd_1d.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_ulonglong, P, P, P, P]
+    lib.pce_construct_svd_1d.restype = ctypes.c_int
     lib.pce_batch_tuning.argtypes = [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     lib.pce_batch_tuning_log.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
@@ -277,6 +280,29 @@ def pce_batch_tuning_log(batch: int):
 
 def pce_construct_projection_1d(T_ptr: int, n: int, m: int, h_ptr: int, w_ptr: int, stream: int = 0) -> None:
     _check(load_library().pce_construct_projection_1d(T_ptr, n, m, h_ptr, w_ptr, stream))
+
+
+def pce_construct_svd_1d(T_ptr: int, n: int, m: int, oversample: int, power_iters: int, seed: int,
+                         h_ptr: int, w_ptr: int, sigma_ptr: int = 0, stream: int = 0) -> None:
+    _check(load_library().pce_construct_svd_1d(T_ptr, n, m, oversample, power_iters, seed, h_ptr, w_ptr,
+                                               sigma_ptr or None, stream))
+
+
+def construct_svd_1d(T, m: int, oversample: int = 10, power_iters: int = 2, seed: int = 0, stream=None):
+    """(h [m, n], w [m, n], sigma [m]) of the truncated SVD of the TVIR T [n, n]
+    (T[d, j]: shift d, input position j): h_k = sigma_k f_k, w_k = e_k
+    (pce_construct_svd_1d, randomised range finder)."""
+    import torch
+    _need_cuda_f32(T, "T")
+    n = int(T.shape[0])
+    if T.dim() != 2 or T.shape[1] != n:
+        raise ValueError("T must be [n, n]")
+    h = torch.empty((m, n), dtype=torch.float32, device=T.device)
+    w = torch.empty((m, n), dtype=torch.float32, device=T.device)
+    sig = torch.empty((m,), dtype=torch.float32, device=T.device)
+    pce_construct_svd_1d(T.data_ptr(), n, m, oversample, power_iters, seed, h.data_ptr(), w.data_ptr(),
+                         sig.data_ptr(), _stream_handle(stream))
+    return h, w, sig
 
 
 def construct_projection_1d(T, m: int, stream=None):

@@ -84,3 +84,86 @@ def test_projection_argument_errors(torch_cuda):
     with pytest.raises(PceError) as e:
         pce.pce_construct_projection_1d(Tc.data_ptr(), 64, 4, h.data_ptr(), h.data_ptr())
     assert e.value.status == pce.PCE_ERR_INVALID
+
+
+# ---------------------------------------------------------------- SVD (Section 5.1)
+
+def fro_rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("n,m", [(256, 4), (256, 8), (1024, 12), (1024, 32)])
+def test_svd_matches_oracle(torch_cuda, n, m):
+    """Randomised SVD on the GPU against the oracle's exact SVD of the same float32
+    TVIR: singular values, the rank-m approximation, the significant terms one by
+    one (same sign rule), and orthonormal windows."""
+    torch = torch_cuda
+    from paper_1604_04374_gb300 import construct_svd_1d
+    T = tvir(n)
+    h, w, s = construct_svd_1d(dev(torch, T), m)
+    h, w, s = (t.cpu().numpy().astype(np.float64) for t in (h, w, s))
+    rh, rw, rs = C.svd_terms(T.astype(np.float64), m)
+    big = rs > 1e-4 * rs[0]
+    assert np.abs(s[big] / rs[big] - 1).max() < 1e-5
+    assert np.abs(s - rs).max() < 1e-6 * rs[0]
+    assert fro_rel(h.T @ w, rh.T @ rw) < 1e-5
+    for k in np.flatnonzero(big):
+        assert fro_rel(w[k], rw[k]) < 1e-3 and fro_rel(h[k], rh[k]) < 1e-3
+    assert np.abs(w @ w.T - np.eye(m)).max() < 1e-5
+    # Eckart-Young: the residual is the tail of the spectrum
+    tail = np.sqrt(np.sum(np.linalg.svd(T.astype(np.float64), compute_uv=False)[m:] ** 2))
+    res = np.linalg.norm(T - h.T @ w)
+    assert res <= tail + 1e-6 * np.linalg.norm(T)
+
+
+def test_svd_rank_deficient_tvir(torch_cuda):
+    """Example 3.3 (rank 2): the third and later terms come back as zeros."""
+    torch = torch_cuda
+    from paper_1604_04374_gb300 import construct_svd_1d
+    T = C.fig1_matrix(3).astype(np.float32)
+    h, w, s = construct_svd_1d(dev(torch, T), 5)
+    h, w, s = (t.cpu().numpy().astype(np.float64) for t in (h, w, s))
+    rh, rw, rs = C.svd_terms(T.astype(np.float64), 2)
+    assert np.abs(s[:2] / rs - 1).max() < 1e-5
+    assert np.all(s[2:] == 0) and np.all(h[2:] == 0) and np.all(w[2:] == 0)
+    assert fro_rel(h[:2].T @ w[:2], rh.T @ rw) < 1e-5
+
+
+def test_svd_expansion_feeds_a_plan(torch_cuda):
+    """Plan(w, h) from the SVD (full-support windows) applies sum_k h_k * (w_k . u); its
+    error to the true operator does not grow with m and reaches the float32 level."""
+    torch = torch_cuda
+    from paper_1604_04374_gb300 import Plan, construct_svd_1d
+    n = 512
+    T = tvir(n)
+    rng = np.random.default_rng(13)
+    u = rng.standard_normal((2, n)).astype(np.float32)
+    idx = (np.arange(n)[:, None] - np.arange(n)[None, :]) % n
+    K = T.astype(np.float64)[idx, np.arange(n)[None, :]]
+    y_true = u.astype(np.float64) @ K.T
+    errs = []
+    for m in (1, 2, 4, 8):
+        h, w, _ = construct_svd_1d(dev(torch, T), m)
+        plan = Plan(w.contiguous(), h=h.contiguous())
+        y = plan.apply(dev(torch, u)).cpu().numpy().astype(np.float64)
+        ref = E.apply(u, w.cpu().numpy(), h.cpu().numpy())
+        assert np.linalg.norm(y - ref) / np.linalg.norm(ref) < 1e-5
+        errs.append(np.linalg.norm(y - y_true) / np.linalg.norm(y_true))
+    assert all(b <= a * (1 + 1e-3) for a, b in zip(errs, errs[1:])), errs
+    assert errs[-1] < 1e-4, errs
+
+
+def test_svd_argument_errors(torch_cuda):
+    torch = torch_cuda
+    from paper_1604_04374_gb300 import pce
+    from paper_1604_04374_gb300.pce import PceError
+    T = torch.zeros((64, 64), device="cuda")
+    h = torch.empty((4, 64), device="cuda")
+    for n, m, p, q in ((64, 0, 10, 2), (64, 65, 0, 2), (64, 4, -1, 2), (64, 4, 10, 17), (8, 4, 0, 0)):
+        with pytest.raises(PceError) as e:
+            pce.pce_construct_svd_1d(T.data_ptr(), n, m, p, q, 0, h.data_ptr(), h.data_ptr())
+        assert e.value.status == pce.PCE_ERR_INVALID
+    Tc = torch.zeros((64, 64))
+    with pytest.raises(PceError) as e:
+        pce.pce_construct_svd_1d(Tc.data_ptr(), 64, 4, 10, 2, 0, h.data_ptr(), h.data_ptr())
+    assert e.value.status == pce.PCE_ERR_INVALID

@@ -120,3 +120,45 @@ def test_projection_coefficients_reproduce_rows_in_the_hat_span():
     T = rng.standard_normal((n, n))
     R = T - C.projection_coefficients(T, m) @ B.T
     assert np.abs(R @ B).max() < 1e-10 * np.abs(T).max() * n
+
+
+def test_svd_terms_reproduce_the_printed_spectra_and_are_orthonormal():
+    """The singular values of svd_terms on the Fig. 1 matrices are the printed
+    ones (first values, with the global factors of the Fig. 1 readings); the
+    windows are orthonormal and the responses orthogonal with norms sigma_k."""
+    for ex in (1, 2):
+        gold = _golden(ex)
+        h, w, s = C.svd_terms(C.fig1_matrix(ex), 8)
+        assert np.allclose(s * C.FIG1_SCALE[ex], gold[:8], rtol=1e-9, atol=0)
+        assert np.allclose(w @ w.T, np.eye(8), atol=1e-12)
+        assert np.allclose(h @ h.T, np.diag(s ** 2), atol=1e-12 * s[0] ** 2)
+        assert np.all(w.sum(axis=1) >= 0)
+
+
+def test_svd_terms_closed_forms():
+    """A rank-one TVIR a b^t gives h_0 = |b| a, w_0 = b / |b| (sum of b positive);
+    Example 3.3 has rank 2, so every further term is zero (Section 3)."""
+    rng = np.random.default_rng(5)
+    a = rng.standard_normal(32)
+    b = rng.random(32) + 0.1
+    h, w, s = C.svd_terms(np.outer(a, b), 3)
+    assert np.allclose(h[0], np.linalg.norm(b) * a, atol=1e-12)
+    assert np.allclose(w[0], b / np.linalg.norm(b), atol=1e-14)
+    assert np.all(h[1:] == 0) and np.all(w[1:] == 0)
+    h, w, s = C.svd_terms(C.fig1_matrix(3), 5)
+    assert s[1] > 0.1 and np.all(s[2:] == 0) and np.all(h[2:] == 0)
+
+
+def test_svd_expansion_is_exact_for_a_rank_m_kernel():
+    """Lemma 3.1: a kernel K(x, y) = sum_k h_k(x - y) w_k(y) of rank m is
+    reproduced exactly by the m SVD terms of its TVIR, applied as Eq. 1.4
+    (expansion.apply against the dense matrix built entry by entry)."""
+    n, m = 48, 3
+    rng = np.random.default_rng(8)
+    h0 = rng.standard_normal((m, n))
+    w0 = rng.standard_normal((m, n))
+    T = h0.T @ w0                                   # T[d][j] = sum_k h_k[d] w_k[j]
+    h, w, s = C.svd_terms(T, m)
+    K = np.array([[T[(i - j) % n, j] for j in range(n)] for i in range(n)])
+    u = rng.standard_normal((2, n))
+    assert np.allclose(E.apply(u, w, h), u @ K.T, atol=1e-11)
