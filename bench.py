@@ -140,6 +140,48 @@ def work_model(pr: synth.Problem, boxes, nb: int, slots=None) -> dict:
     }
 
 
+def sectioned_work_model(pr: synth.Problem, boxes, nb: int) -> dict:
+    """Algorithmic flops and bytes per launch of the sectioned kernels (PCE_FLAG_SECTIONED)
+    for a chunk of nb right-hand sides, from the support boxes of w_k and the exact
+    support of every h_k (as the plan finds them).  Per term: forward input window =
+    box (nr x nc), output window = box dilated by the support (nr + snr - 1 rows,
+    nc + snc - 1 columns); sections of 1024 x LC points, LC the smallest power of two
+    (at least 16) holding every output window's columns.  Bytes: window inputs read
+    once, section spectra of h read once per launch, intermediates written once and
+    read once, the output window added once."""
+    ny, nx = pr.shape
+    terms = []
+    need_c = 1
+    for k, (r0, nr, c0, nc) in enumerate(boxes):
+        _, snr = cyclic_extent(np.any(pr.h[k] != 0, axis=1))
+        _, snc = cyclic_extent(np.any(pr.h[k] != 0, axis=0))
+        if nr == 0 or snr == 0:
+            continue
+        terms.append((nr, nc, nr + snr - 1, nc + snc - 1))
+        need_c = max(need_c, nc + snc - 1)
+    lc = 16
+    while lc < need_c:
+        lc *= 2
+    lch = lc // 2
+    f_row = 2.5 * lc * math.log2(lc)
+    f_col = 2 * 5.0 * 1024 * 10 + 6.0 * 1024        # FFT, product, inverse FFT per column
+    in_rows = sum(t[0] for t in terms)
+    out_rows = sum(t[2] for t in terms)
+    in_px = sum(t[0] * t[1] for t in terms)
+    out_px = sum(t[2] * t[3] for t in terms)
+    hs = len(terms) * (lch * 1024 + 1024) * 8
+    cols = len(terms) * lch
+    return {
+        "lc": lc,
+        "rows_r2c_window": (nb * (in_rows * f_row + in_px), nb * in_px * 4 + in_px * 4 + nb * in_rows * lch * 8),
+        "cols_fwd": (nb * cols * f_col, nb * (in_rows + out_rows) * lch * 8 + hs),
+        "rows_c2r": (nb * out_rows * f_row, nb * out_rows * lch * 8 + nb * out_px * 4),
+        "rows_r2c": (nb * out_rows * f_row, nb * out_px * 4 + nb * out_rows * lch * 8),
+        "cols_adj": (nb * cols * f_col, nb * (in_rows + out_rows) * lch * 8 + hs),
+        "rows_adj": (nb * (in_rows * f_row + in_px), nb * in_rows * lch * 8 + in_px * 4 + nb * in_px * 4),
+    }
+
+
 def path_bytes(pr: synth.Problem, boxes) -> float:
     """Algorithmic HBM bytes of one forward + one adjoint apply of the batch:
     u and y (x and v) once, hhat once, w on its support box once, per direction."""
@@ -468,6 +510,14 @@ def gpu_arm(args, pr: synth.Problem, rank: int, world: int) -> None:
             sms, _, _ = timed_steps(spair.launch)
             spair.close()
 
+            def sstep():
+                sp.apply(u, out=ys)
+                sp.apply_adjoint(u, out=xs)
+
+            sseq, _, _ = timed_steps(sstep, on_start=lambda: sp.set_timing(True))
+            skern = sp.timing()
+            sp.set_timing(False)
+
             def rel_t(a, b):
                 a, b = a.reshape(B, -1).double(), b.reshape(B, -1).double()
                 return float(((a - b).norm(dim=1) / b.norm(dim=1)).max())
@@ -476,7 +526,9 @@ def gpu_arm(args, pr: synth.Problem, rank: int, world: int) -> None:
                          "value": weak_scaling_value(B, args.steps, world, sms), "unit": UNIT,
                          "ms_per_step": sms / args.steps,
                          "launches_per_step": sp.launch_count(False, B) + sp.launch_count(True, B),
-                         "max_rel_diff_vs_headline_plan": max(rel_t(ys, y_ref), rel_t(xs, x_ref))}
+                         "max_rel_diff_vs_headline_plan": max(rel_t(ys, y_ref), rel_t(xs, x_ref)),
+                         "sequential_ms_per_step": sseq / args.steps,
+                         "kernel_times": skern, "chunk": plan_chunk(sp, B), "boxes": sp.info()[1]}
             sp.close()
             del ys, xs
 
@@ -559,17 +611,17 @@ def gpu_arm(args, pr: synth.Problem, rank: int, world: int) -> None:
         hbm_peak = hbm_peak or 6800.0
         chunk = plan_chunk(plan, B)
         model = work_model(pr, boxes, chunk, slots)
-        kernels = {}
-        for name, (ms, n) in kern.items():
-            fl, by = model.get(name, (0.0, 0.0))
-            avg = ms / n
-            kernels[name] = {"launches": n, "avg_us": 1000.0 * avg, "share": None,
-                             "tflops": fl / (avg / 1000.0) / 1e12 if fl else None,
-                             "gbs": by / (avg / 1000.0) / 1e9 if by else None}
-        tot = sum(v["avg_us"] * v["launches"] for v in kernels.values()) or 1.0
-        for v in kernels.values():
-            v["share"] = v["avg_us"] * v["launches"] / tot
-        dom = max(kernels, key=lambda k: kernels[k]["share"]) if kernels else None
+        kernels, dom = kernel_table(kern, model)
+        if sectioned and "kernel_times" in sectioned:
+            smodel = sectioned_work_model(pr, sectioned.pop("boxes"), sectioned["chunk"])
+            sectioned["lc"] = smodel["lc"]
+            sk, sdom = kernel_table(sectioned.pop("kernel_times"), smodel)
+            sectioned["kernels"] = sk
+            if sdom:
+                sectioned["roofline"] = {
+                    "kernel": sdom, "bound": "alu", "achieved": sk[sdom]["tflops"], "peak": fp32_peak_tflops,
+                    "unit": "TFLOP/s", "frac": sk[sdom]["tflops"] / fp32_peak_tflops,
+                    "hbm_gbs": sk[sdom]["gbs"], "hbm_frac_of_" + hbm_src: sk[sdom]["gbs"] / hbm_peak}
         roof = None
         if dom:
             d = kernels[dom]
@@ -842,6 +894,23 @@ def batch_arm(args, rank: int, world: int) -> None:
         p.close()
     if dist:
         dist.destroy_process_group()
+
+
+def kernel_table(kern: dict, model: dict):
+    """Per kernel kind: launches, average time, share of the summed kernel time, and the
+    work model's FP32 rate and HBM rate; with the kind of the largest share."""
+    kernels = {}
+    for name, (ms, n) in kern.items():
+        fl, by = model.get(name, (0.0, 0.0))
+        avg = ms / n
+        kernels[name] = {"launches": n, "avg_us": 1000.0 * avg, "share": None,
+                         "tflops": fl / (avg / 1000.0) / 1e12 if fl else None,
+                         "gbs": by / (avg / 1000.0) / 1e9 if by else None}
+    tot = sum(v["avg_us"] * v["launches"] for v in kernels.values()) or 1.0
+    for v in kernels.values():
+        v["share"] = v["avg_us"] * v["launches"] / tot
+    dom = max(kernels, key=lambda k: kernels[k]["share"]) if kernels else None
+    return kernels, dom
 
 
 def plan_chunk(plan, batch: int) -> int:

@@ -74,7 +74,8 @@ cudaError_t launch_sec_r2c(int lc, bool win, dim3 grid, cudaStream_t s, const fl
                            float2* dst, long long dst_bstride, long long dst_kstride, const float2* tw);
 cudaError_t launch_sec_cols(bool conj, dim3 grid, cudaStream_t s, const float2* Z, long long z_bstride,
                             long long z_kstride, int nb, const float2* hsT, const float2* hsN, const SecGeom* geo,
-                            int nxh, float2* A, long long a_bstride, long long a_kstride, const float2* tw1024);
+                            int nxh, float2* A, long long a_bstride, long long a_kstride, const float2* tw1024,
+                            int* status, long long wait_limit, int skip_copy);
 cudaError_t launch_sec_c2r(int lc, bool win, dim3 grid, cudaStream_t s, const float2* src, long long src_bstride,
                            long long src_kstride, const SecGeom* geo, const int2* items, int nitems,
                            const float* wbox, float* dst, long long dst_bstride, int nyg, int nxg, float scale,

@@ -1438,7 +1438,7 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
                 e = timed(p, adjoint ? PCE_KERNEL_COLS_ADJ : PCE_KERNEL_COLS_FWD, s, [&] {
                     return pce::launch_sec_cols(adjoint, dim3(m, (lch + cpc - 1) / cpc), s, scr.Z, scr.zstride,
                                                 p->sec_k, nb, p->hsT, p->hsN, geo, lch, scr.A, scr.astride, p->sec_k,
-                                                p->tw1024);
+                                                p->tw1024, p->d_status, p->wait_limit, p->skip_copy);
                 });
             if (e == cudaSuccess && n_out > 0)
                 e = timed(p, adjoint ? PCE_KERNEL_ROWS_ADJ : PCE_KERNEL_ROWS_C2R, s, [&] {

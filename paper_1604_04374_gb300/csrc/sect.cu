@@ -45,14 +45,15 @@ cudaError_t launch_sec_r2c(int lc, bool win, dim3 grid, cudaStream_t s, const fl
 
 cudaError_t launch_sec_cols(bool conj, dim3 grid, cudaStream_t s, const float2* Z, long long z_bstride,
                             long long z_kstride, int nb, const float2* hsT, const float2* hsN, const SecGeom* geo,
-                            int nxh, float2* A, long long a_bstride, long long a_kstride, const float2* tw1024) {
+                            int nxh, float2* A, long long a_bstride, long long a_kstride, const float2* tw1024,
+                            int* status, long long wait_limit, int skip_copy) {
     if (!tw1024 || !hsT || !hsN) return cudaErrorInvalidValue;
     if (conj)
         kw_sec_cols<true><<<grid, kWColWarps * 32, kWColSmem, s>>>(Z, z_bstride, z_kstride, nb, hsT, hsN, geo, nxh,
-                                                                   A, a_bstride, a_kstride, tw1024);
+                                                                   A, a_bstride, a_kstride, tw1024, status, wait_limit, skip_copy);
     else
         kw_sec_cols<false><<<grid, kWColWarps * 32, kWColSmem, s>>>(Z, z_bstride, z_kstride, nb, hsT, hsN, geo, nxh,
-                                                                    A, a_bstride, a_kstride, tw1024);
+                                                                    A, a_bstride, a_kstride, tw1024, status, wait_limit, skip_copy);
     return cudaGetLastError();
 }
 

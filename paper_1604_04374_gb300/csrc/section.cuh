@@ -18,8 +18,9 @@
 //   k_sec_r2c:  rows of the input window gathered from the grid (w_k applied
 //               in the forward), R2C, packed half spectra [b][k][row][LC/2]
 //   kw_sec_cols: per term and column, FFT_y, times the section spectrum of
-//               h_k (conjugated for the adjoint; read through the L1 cache,
-//               once per right-hand side), IFFT_y, output rows
+//               h_k (conjugated for the adjoint; copied into shared memory
+//               by the TMA engine during the FFT, once per right-hand side),
+//               IFFT_y, output rows
 //   k_sec_c2r:  C2R of the output rows, times 1 / (LR LC) (and w_k in the
 //               adjoint), added into the grid with atomicAdd (terms overlap)
 #pragma once
@@ -102,14 +103,17 @@ k_sec_r2c(const float* __restrict__ src, long long src_bstride, int NYg, int NXg
 
 // Columns of the sections (LR = 1024).  Grid (m, ceil(NXh / 4)), 128
 // threads, kWColSmem bytes; each CTA takes one term and four columns and runs
-// all nb right-hand sides through them.  hsT: the section
-// spectra of h_k, [m][NXh][1024] (c = 0: DC column), hsN: [m][1024] (Nyquist).
+// all nb right-hand sides through them.  hsT: the section spectra of h_k,
+// [m][NXh][1024] (c = 0: DC column), hsN: [m][1024] (Nyquist).  A warp's
+// spectrum column (8 KB) is copied into its transpose tile by the TMA engine
+// while the second half of its FFT runs, once per right-hand side; the wait
+// for it is bounded (status bit kStatusTimeout, products skipped after it).
 template <bool CONJ>
 __global__ void __launch_bounds__(kWColWarps * 32, 3)
 kw_sec_cols(const float2* __restrict__ Z, long long z_bstride, long long z_kstride, int nb,
             const float2* __restrict__ hsT, const float2* __restrict__ hsN, const SecGeom* __restrict__ geo,
             int NXh, float2* __restrict__ A, long long a_bstride, long long a_kstride,
-            const float2* __restrict__ tw) {
+            const float2* __restrict__ tw, int* __restrict__ status, long long wait_limit, int skip_copy) {
     constexpr int NY = kSecLR;
     extern __shared__ float2 smem[];
     float2* tile = smem;
@@ -121,23 +125,46 @@ kw_sec_cols(const float2* __restrict__ Z, long long z_bstride, long long z_kstri
     const bool cv = col < NXh;
     const bool dcn = blockIdx.y == 0 && warp == 0;
     const SecGeom g = geo[k];
-    // this column's section spectrum of h_k: read through the L1 cache for every
-    // right-hand side (8 KB per column, shared by nothing else)
+    __shared__ unsigned long long bars[kWColWarps];
+    unsigned long long* bar = &bars[warp];
+    if (lane == 0) mbar_init(bar);
+    __syncwarp();
+    unsigned parity = 0;
+    bool failed = false;
     const float2* hcol = hsT + ((long long)k * NXh + (cv ? col : 0)) * NY;
     const float2* h0 = hsT + (long long)k * NXh * NY;   // DC column (dcn warp only)
     const float2* hn = hsN + (long long)k * NY;
     const int swl = tix_sw(lane, warp);
     for (int b = 0; b < nb; ++b) {
+        // the twiddles and the row indices are the same for every right-hand
+        // side; opaque copies keep the compiler from holding them in registers
+        // across the loop (which spills)
+        const float2* twb = tw;
+        int lo_r = g.in_lo_r, rows = g.in_rows;
+        asm volatile("" : "+l"(twb), "+r"(lo_r), "+r"(rows));
         tile_load(tile, Z + b * z_bstride + k * z_kstride, g.in_rows, NXh, col0);
         cp_async_wait_all();
         __syncthreads();
         float2 v[32];
 #pragma unroll
         for (int q = 0; q < 32; ++q) {
-            const int i = wrap(lane + 32 * q - g.in_lo_r, NY);
-            v[q] = (i < g.in_rows) ? tile[tix(i, warp)] : make_float2(0.f, 0.f);
+            const int i = wrap(lane + 32 * q - lo_r, NY);
+            v[q] = (i < rows) ? tile[tix(i, warp)] : make_float2(0.f, 0.f);
         }
-        warp_fft1024<false>(v, tr, tw);
+        const bool bulk = !dcn && cv && !failed;
+        warp_fft1024<false>(v, tr, twb, [&] {
+            if (bulk && lane == 0) bulk_load(tr, hcol, NY * sizeof(float2), bar, skip_copy);
+        });
+        if (bulk) {
+            if (!mbar_wait(bar, parity, wait_limit)) {
+                failed = true;
+                if (lane == 0) atomicOr(status, kStatusTimeout);
+                // a copy may still be in flight into the tile: wait once more
+                // (bounded) before the tile is reused; no further copies are issued
+                mbar_wait(bar, parity, wait_limit);
+            }
+            parity ^= 1;
+        }
         if (dcn) {
             // the partner values Z[-f] come from the transpose tile (free after the
             // FFT), so the products can overwrite v in place
@@ -158,14 +185,17 @@ kw_sec_cols(const float2* __restrict__ Z, long long z_bstride, long long z_kstri
                 v[mm] = t;
             }
             __syncwarp();
-        } else if (cv) {
+        } else if (cv && !failed) {
 #pragma unroll
             for (int mm = 0; mm < 32; ++mm) {
-                const float2 hv = __ldg(&hcol[lane + 32 * mm]);
-                v[mm] = cmul(v[mm], CONJ ? cconj(hv) : hv);
+                const float2 hv = tr[lane + 32 * mm];
+                v[mm] = CONJ ? cmulc(v[mm], hv) : cmul(v[mm], hv);
             }
+        } else {
+#pragma unroll
+            for (int mm = 0; mm < 32; ++mm) v[mm] = make_float2(0.f, 0.f);
         }
-        warp_fft1024<true>(v, tr, tw);
+        warp_fft1024<true>(v, tr, twb);
         __syncthreads();   // every warp has read its input rows from the tile
 #pragma unroll
         for (int q = 0; q < 32; ++q) tile[4 * (lane + 32 * q) + swl] = v[q];

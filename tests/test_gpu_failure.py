@@ -1,7 +1,7 @@
 """Failure detection without a GPU fault: a bounded wait that runs out.
 
-The one-warp column kernels (columns of length 1024) wait on an mbarrier for
-a bulk copy of a spectrum column.  With the copies suppressed
+The one-warp column kernels (columns of length 1024, whole-grid and
+sectioned) wait on an mbarrier for a bulk copy of a spectrum column.  With the copies suppressed
 (pce_plan_inject_wait_timeout), every wait gives up after a short bounded
 time, the kernels skip the dependent work, and the plan's status word turns
 the event into PCE_ERR_TIMEOUT on the host.  Nothing hangs and the context
@@ -16,13 +16,18 @@ from oracle import expansion as E
 pytestmark = pytest.mark.gpu
 
 
-def test_bounded_wait_times_out_and_recovers():
+@pytest.mark.parametrize("sectioned", [False, True])
+def test_bounded_wait_times_out_and_recovers(sectioned):
+    """Both the whole-grid column kernels and the sectioned column kernel
+    (PCE_FLAG_SECTIONED, whose spectrum columns also arrive by bulk copy)."""
     import torch
     from paper_1604_04374_gb300 import Plan, PceError, build, pce
     build.build()
-    pr = synth.problem_2d(1024, 64, 4, 1, 41, "normal")
+    # 4 x 4 hats (m = 16): boxes of 511 rows, which a 1024-row section holds
+    pr = synth.problem_2d(1024, 64, 16 if sectioned else 4, 1, 41, "normal")
     dev = torch.device("cuda", 0)
-    plan = Plan(torch.from_numpy(pr.w).to(dev), h=torch.from_numpy(pr.h).to(dev))
+    plan = Plan(torch.from_numpy(pr.w).to(dev), h=torch.from_numpy(pr.h).to(dev),
+                flags=pce.PCE_FLAG_SECTIONED if sectioned else 0)
     u = torch.from_numpy(pr.u).to(dev)
     pce.pce_plan_status(plan.handle)                       # clean start
     pce.pce_plan_inject_wait_timeout(plan.handle, 200000)  # about 0.1 ms per wait
