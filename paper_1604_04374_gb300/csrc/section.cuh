@@ -244,8 +244,22 @@ k_sec_c2r(const float2* __restrict__ src, long long src_bstride, long long src_k
         const float2 xb = vb ? load_half<NX>(pb, f) : make_float2(0.f, 0.f);
         v[r] = make_float2(xa.x - xb.y, xa.y + xb.x);
     }
-    fft<NX, true>(v, j, b0, b1, tw);
     const int ra = g.out_lo_r + ia, rb = g.out_lo_r + ib;   // box row offsets
+    // window values (adjoint), loaded before the FFT so that their latency
+    // overlaps it
+    float wa[kR], wb[kR];
+#pragma unroll
+    for (int r = 0; r < kR; ++r) {
+        wa[r] = 1.f;
+        wb[r] = 1.f;
+        if (WIN) {
+            const int rc = sec_offset(j + r * T, g.out_lo_c, g.out_hi_c, NX);
+            const bool in = rc >= g.out_lo_c && rc <= g.out_hi_c;
+            wa[r] = (in && va) ? __ldg(wbox + g.woff + (long long)ra * g.ldw + rc) : 0.f;
+            wb[r] = (in && vb) ? __ldg(wbox + g.woff + (long long)rb * g.ldw + rc) : 0.f;
+        }
+    }
+    fft<NX, true>(v, j, b0, b1, tw);
     float* db = dst + b * dst_bstride;
     float* ya = db + (long long)(((g.r0 + ra) % NYg + NYg) % NYg) * NXg;
     float* yb = db + (long long)(((g.r0 + rb) % NYg + NYg) % NYg) * NXg;
@@ -255,11 +269,7 @@ k_sec_c2r(const float2* __restrict__ src, long long src_bstride, long long src_k
         const int rc = sec_offset(n, g.out_lo_c, g.out_hi_c, NX);
         if (rc < g.out_lo_c || rc > g.out_hi_c) continue;
         const int col = ((g.c0 + rc) % NXg + NXg) % NXg;
-        float xa = v[r].x * scale, xb = v[r].y * scale;
-        if (WIN) {
-            xa *= __ldg(wbox + g.woff + (long long)(va ? ra : 0) * g.ldw + rc);
-            xb *= __ldg(wbox + g.woff + (long long)(vb ? rb : 0) * g.ldw + rc);
-        }
+        const float xa = v[r].x * scale * wa[r], xb = v[r].y * scale * wb[r];
         if (va) atomicAdd(ya + col, xa);
         if (vb) atomicAdd(yb + col, xb);
     }
