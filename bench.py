@@ -501,7 +501,8 @@ def gpu_arm(args, pr: synth.Problem, rank: int, world: int) -> None:
     if args.sectioned and len(pr.shape) == 2:
         from paper_1604_04374_gb300.pce import PCE_FLAG_SECTIONED, PceError
         try:
-            sp = Plan(torch.from_numpy(pr.w).to(dev), h=torch.from_numpy(pr.h).to(dev), flags=PCE_FLAG_SECTIONED)
+            sp = Plan(torch.from_numpy(pr.w).to(dev), h=torch.from_numpy(pr.h).to(dev),
+                      flags=PCE_FLAG_SECTIONED | pflags)
         except PceError as exc:
             sectioned = {"unsupported": str(exc)}
         else:
@@ -523,6 +524,8 @@ def gpu_arm(args, pr: synth.Problem, rank: int, world: int) -> None:
                 return float(((a - b).norm(dim=1) / b.norm(dim=1)).max())
 
             sectioned = {"impl": "PCE_FLAG_SECTIONED: every term on a 1024-row section, overlap-add",
+                         "storage": ("half2 section spectra with per-term scale, bf16 windows" if args.lowp
+                                     else "f32"),
                          "value": weak_scaling_value(B, args.steps, world, sms), "unit": UNIT,
                          "ms_per_step": sms / args.steps,
                          "launches_per_step": sp.launch_count(False, B) + sp.launch_count(True, B),

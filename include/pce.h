@@ -106,8 +106,10 @@ typedef struct pce_plan* pce_plan_t;
  * grid is much larger than box + support (e.g. 2048 x 2048 with boxes of 511
  * and 73-pixel PSFs: two 1024-point column FFTs per term instead of one
  * 2048-point one shared with the other terms).  2D plans from pce_plan_create
- * only, FP32 storage, convolution-product form; box rows + support rows - 1
- * <= 1024 and box columns + support columns - 1 <= 2048 for every term.
+ * only, fused, convolution-product form; with PCE_FLAG_LOWP_STORAGE the
+ * section spectra are stored as half2 with their own per-term power-of-two
+ * scales and the windows as bfloat16.  Box rows + support rows - 1 <= 1024
+ * and box columns + support columns - 1 <= 2048 for every term.
  * Otherwise PCE_ERR_UNSUPPORTED.  Gradients and pce_apply_noalloc use the
  * plan's whole-grid structures.
  */
@@ -123,8 +125,9 @@ typedef struct pce_plan* pce_plan_t;
  *   w      : device, [m][shape] float32 windows w_k.
  *   h      : device, [m][shape] float32 impulse responses h_k, origin at index 0.
  *   flags  : PCE_FLAG_NONE or a combination of PCE_FLAG_UNFUSED,
- *            PCE_FLAG_LOWP_STORAGE (not with PCE_FLAG_UNFUSED) and
- *            PCE_FLAG_PRODUCT_CONVOLUTION; other bits return PCE_ERR_INVALID.
+ *            PCE_FLAG_LOWP_STORAGE (not with PCE_FLAG_UNFUSED),
+ *            PCE_FLAG_PRODUCT_CONVOLUTION and PCE_FLAG_SECTIONED (see each
+ *            flag for the combinations); other bits return PCE_ERR_INVALID.
  *   stream : cudaStream_t used for the set-up work.
  *
  * The plan finds the support box of every w_k (the smallest periodic

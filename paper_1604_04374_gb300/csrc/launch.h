@@ -69,17 +69,20 @@ cudaError_t launch_plain_cols_inv(int ny, dim3 grid, cudaStream_t s, const float
 // Sectioned apply (section.cuh)
 int sec_rows_per_cta(int lc);
 cudaError_t prepare_sec();
+// wbox: float or bfloat16 (lowp) box copies; hsT / hsN: float2 or half2 (lowp)
+// section spectra with per-term scales hscale (lowp only).
 cudaError_t launch_sec_r2c(int lc, bool win, dim3 grid, cudaStream_t s, const float* src, long long src_bstride,
-                           int nyg, int nxg, const float* wbox, const SecGeom* geo, const int2* items, int nitems,
-                           float2* dst, long long dst_bstride, long long dst_kstride, const float2* tw);
+                           int nyg, int nxg, const void* wbox, bool lowp, const SecGeom* geo, const int2* items,
+                           int nitems, float2* dst, long long dst_bstride, long long dst_kstride, const float2* tw);
 cudaError_t launch_sec_cols(bool conj, dim3 grid, cudaStream_t s, const float2* Z, long long z_bstride,
-                            long long z_kstride, int nb, const float2* hsT, const float2* hsN, const SecGeom* geo,
-                            int nxh, float2* A, long long a_bstride, long long a_kstride, const float2* tw1024,
-                            int* status, long long wait_limit, int skip_copy);
+                            long long z_kstride, int nb, const void* hsT, const void* hsN, const float* hscale,
+                            bool lowp, const SecGeom* geo, int nxh, float2* A, long long a_bstride,
+                            long long a_kstride, const float2* tw1024, int* status, long long wait_limit,
+                            int skip_copy);
 cudaError_t launch_sec_c2r(int lc, bool win, dim3 grid, cudaStream_t s, const float2* src, long long src_bstride,
                            long long src_kstride, const SecGeom* geo, const int2* items, int nitems,
-                           const float* wbox, float* dst, long long dst_bstride, int nyg, int nxg, float scale,
-                           const float2* tw);
+                           const void* wbox, bool lowp, float* dst, long long dst_bstride, int nyg, int nxg,
+                           float scale, const float2* tw);
 
 // Separable windows, Ny = 1024 (one-warp column kernels): Z / Q hold one slot
 // per column factor, box[] is indexed by slot.

@@ -612,20 +612,18 @@ pce_status setup_windows(pce_plan* p, const float* w, cudaStream_t s) {
     return PCE_OK;
 }
 
-// Reduced storage of a plan whose FP32 windows and spectra are ready: bfloat16
-// box copies of w_k, half2 spectra with per-term scale s_k = 2^ceil(log2 max |Re, Im|).
-// The FP32 copies are replaced by the values the reduced ones stand for.
-pce_status quantize_plan(pce_plan* p, cudaStream_t s) {
-    const int m = p->m, ny = p->ny, nxh = p->nx / 2;
-    const bool two_d = p->ndims == 2;
-    const long long per = two_d ? (long long)ny * nxh : nxh;
+// Per-term power-of-two scales s_k = 2^ceil(log2 max |Re, Im|) over the
+// spectra a ([m][per]) and b ([m][perb], may be NULL), into sc_dev ([m],
+// allocated here).
+pce_status term_scales(const float2* a, long long per, const float2* b, long long perb, int m, cudaStream_t s,
+                       float** sc_dev) {
     unsigned* mx = nullptr;
     pce_status st;
     if ((st = dev_alloc(&mx, (size_t)m))) return st;
     cudaError_t e = cudaMemsetAsync(mx, 0, sizeof(unsigned) * m, s);
     if (e == cudaSuccess) {
-        k_term_maxabs<<<grid_for(per * m), 256, 0, s>>>(p->hh, per, m, mx);
-        if (two_d) k_term_maxabs<<<grid_for((long long)ny * m), 256, 0, s>>>(p->hN, ny, m, mx);
+        k_term_maxabs<<<grid_for(per * m), 256, 0, s>>>(a, per, m, mx);
+        if (b) k_term_maxabs<<<grid_for(perb * m), 256, 0, s>>>(b, perb, m, mx);
         e = cudaGetLastError();
     }
     std::vector<unsigned> hmx(m);
@@ -641,8 +639,21 @@ pce_status quantize_plan(pce_plan* p, cudaStream_t s) {
         const float fr = std::frexp(v, &ex);   // v = fr * 2^ex, fr in [0.5, 1)
         sc[k] = (v > 0.f && std::isfinite(v)) ? std::ldexp(1.0f, fr == 0.5f ? ex - 1 : ex) : 1.0f;
     }
-    if ((st = dev_alloc(&p->hscale, (size_t)m))) return st;
-    PCE_CK(cudaMemcpyAsync(p->hscale, sc.data(), sizeof(float) * m, cudaMemcpyHostToDevice, s));
+    if ((st = dev_alloc(sc_dev, (size_t)m))) return st;
+    PCE_CK(cudaMemcpyAsync(*sc_dev, sc.data(), sizeof(float) * m, cudaMemcpyHostToDevice, s));
+    PCE_CK(cudaStreamSynchronize(s));   // sc must outlive the copy
+    return PCE_OK;
+}
+
+// Reduced storage of a plan whose FP32 windows and spectra are ready: bfloat16
+// box copies of w_k, half2 spectra with per-term scale s_k = 2^ceil(log2 max |Re, Im|).
+// The FP32 copies are replaced by the values the reduced ones stand for.
+pce_status quantize_plan(pce_plan* p, cudaStream_t s) {
+    const int m = p->m, ny = p->ny, nxh = p->nx / 2;
+    const bool two_d = p->ndims == 2;
+    const long long per = two_d ? (long long)ny * nxh : nxh;
+    pce_status st;
+    if ((st = term_scales(p->hh, per, two_d ? p->hN : nullptr, ny, m, s, &p->hscale))) return st;
     __half2* h16 = nullptr;
     if ((st = dev_alloc(&h16, (size_t)(per * m)))) return st;
     p->hh16 = h16;
@@ -702,9 +713,9 @@ pce_status create_common(pce_plan_t* out, int ndims, const int64_t* shape, int m
     if (st) return st;
     if (m < 1) return fail(PCE_ERR_INVALID, "m must be >= 1 (got %d)", m);
     if ((flags & PCE_FLAG_SECTIONED) &&
-        (ndims != 2 || spectra || (flags & (PCE_FLAG_UNFUSED | PCE_FLAG_LOWP_STORAGE | PCE_FLAG_PRODUCT_CONVOLUTION))))
-        return fail(PCE_ERR_UNSUPPORTED, "PCE_FLAG_SECTIONED serves 2D convolution-product plans from h with "
-                                         "FP32 storage");
+        (ndims != 2 || spectra || (flags & (PCE_FLAG_UNFUSED | PCE_FLAG_PRODUCT_CONVOLUTION))))
+        return fail(PCE_ERR_UNSUPPORTED, "PCE_FLAG_SECTIONED serves 2D convolution-product plans from h, "
+                                         "fused");
     if (flags & ~(uint32_t)(PCE_FLAG_UNFUSED | PCE_FLAG_LOWP_STORAGE | PCE_FLAG_PRODUCT_CONVOLUTION |
                             PCE_FLAG_SECTIONED))
         return fail(PCE_ERR_INVALID, "unknown flag bits 0x%x", flags);
@@ -1145,6 +1156,21 @@ pce_status setup_sectioned(pce_plan* p, const float* h, cudaStream_t s) {
     p->sec_chunk = (int)std::max<long long>(1, std::min<long long>(kMaxChunk, kScratchBudget / per_b));
     if ((st = dev_alloc(&p->scrZs, (size_t)(p->sec_b * p->sec_chunk)))) return st;
     if ((st = dev_alloc(&p->scrAs, (size_t)(p->sec_b * p->sec_chunk)))) return st;
+    if (p->lowp) {
+        // reduced storage: half2 section spectra with their own per-term scales
+        const long long per = 1024LL * lch;
+        if ((st = term_scales(p->hsT, per, p->hsN, 1024, m, s, &p->sec_hscale))) return st;
+        if ((st = dev_alloc(&p->hsT16, (size_t)(per * m)))) return st;
+        if ((st = dev_alloc(&p->hsN16, (size_t)m * 1024))) return st;
+        k_quantize_h<<<grid_for(per * m), 256, 0, s>>>(p->hsT, per, m, p->sec_hscale, p->hsT16);
+        k_quantize_h<<<grid_for(1024LL * m), 256, 0, s>>>(p->hsN, 1024, m, p->sec_hscale, p->hsN16);
+        PCE_CK(cudaGetLastError());
+        PCE_CK(cudaStreamSynchronize(s));
+        cudaFree(p->hsT);
+        cudaFree(p->hsN);
+        p->hsT = nullptr;
+        p->hsN = nullptr;
+    }
     p->sect = true;
     return PCE_OK;
 }
@@ -1428,22 +1454,26 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
             const int nb = (int)std::min<long long>(sbal, batch - b0);
             float* dst = out + b0 * P;
             e = cudaMemsetAsync(dst, 0, sizeof(float) * P * nb, s);
+            const void* wst = wstore(p);
+            const void* hst = p->lowp ? (const void*)p->hsT16 : (const void*)p->hsT;
+            const void* hsn = p->lowp ? (const void*)p->hsN16 : (const void*)p->hsN;
             if (e == cudaSuccess && n_in > 0)
                 e = timed(p, adjoint ? PCE_KERNEL_ROWS_R2C : PCE_KERNEL_ROWS_R2C_WINDOW, s, [&] {
                     return pce::launch_sec_r2c(lc, !adjoint, dim3((n_in + fpc - 1) / fpc, nb), s, in + b0 * P, P, ny,
-                                               nx, p->wbox, geo, it_in, n_in, scr.Z, scr.zstride, p->sec_k,
+                                               nx, wst, p->lowp, geo, it_in, n_in, scr.Z, scr.zstride, p->sec_k,
                                                p->sec_twc);
                 });
             if (e == cudaSuccess)
                 e = timed(p, adjoint ? PCE_KERNEL_COLS_ADJ : PCE_KERNEL_COLS_FWD, s, [&] {
                     return pce::launch_sec_cols(adjoint, dim3(m, (lch + cpc - 1) / cpc), s, scr.Z, scr.zstride,
-                                                p->sec_k, nb, p->hsT, p->hsN, geo, lch, scr.A, scr.astride, p->sec_k,
-                                                p->tw1024, p->d_status, p->wait_limit, p->skip_copy);
+                                                p->sec_k, nb, hst, hsn, p->sec_hscale, p->lowp, geo, lch, scr.A,
+                                                scr.astride, p->sec_k, p->tw1024, p->d_status, p->wait_limit,
+                                                p->skip_copy);
                 });
             if (e == cudaSuccess && n_out > 0)
                 e = timed(p, adjoint ? PCE_KERNEL_ROWS_ADJ : PCE_KERNEL_ROWS_C2R, s, [&] {
                     return pce::launch_sec_c2r(lc, adjoint, dim3((n_out + fpc - 1) / fpc, nb), s, scr.A, scr.astride,
-                                               p->sec_k, geo, it_out, n_out, p->wbox, dst, P, ny, nx, sscale,
+                                               p->sec_k, geo, it_out, n_out, wst, p->lowp, dst, P, ny, nx, sscale,
                                                p->sec_twc);
                 });
         }

@@ -92,6 +92,10 @@ struct pce_plan {
     int n_items_box = 0, n_items_win = 0;
     float2* hsT = nullptr;        // [m][sec_lc/2][1024] section spectra of h_k (c = 0: DC column)
     float2* hsN = nullptr;        // [m][1024] Nyquist column
+    // reduced storage: half2 section spectra / sec_hscale[k] (FP32 copies freed)
+    __half2* hsT16 = nullptr;
+    __half2* hsN16 = nullptr;
+    float* sec_hscale = nullptr;
     float2* sec_twc = nullptr;    // Stockham twiddles of sec_lc
     float2* scrZs = nullptr;      // [chunk][m][rows][sec_lc/2]
     float2* scrAs = nullptr;
@@ -116,7 +120,7 @@ struct pce_plan {
                         items,  kptr,  klist,  scrZ, scrA,  wbox16, hh16,     hN16, hhT16, hscale,
                         twN,    hh4,   wrow, wxbox, d_vbox, d_kslot, d_korder, sitems, skptr, sklist,
                         hN2,    hN2_16, tw2048l, d_geo_f, d_geo_a, sec_items_box, sec_items_win, hsT, hsN,
-                        sec_twc, scrZs, scrAs};
+                        sec_twc, scrZs, scrAs, hsT16, hsN16, sec_hscale};
         for (void* q : ptrs)
             if (q) cudaFree(q);
     }

@@ -16,24 +16,65 @@ int sec_rows_per_cta(int lc) {
 }
 
 cudaError_t prepare_sec() {
-    cudaError_t e = cudaFuncSetAttribute(kw_sec_cols<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWColSmem);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(kw_sec_cols<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWColSmem);
-    return e;
+    const void* fns[] = {(const void*)kw_sec_cols<false, float2>, (const void*)kw_sec_cols<true, float2>,
+                         (const void*)kw_sec_cols<false, __half2>, (const void*)kw_sec_cols<true, __half2>};
+    for (const void* f : fns) {
+        const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kWColSmem);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
+namespace {
+
+template <int N, typename WT>
+void sec_r2c(bool win, dim3 grid, cudaStream_t s, const float* src, long long src_bstride, int nyg, int nxg,
+             const WT* wbox, const SecGeom* geo, const int2* items, int nitems, float2* dst, long long dst_bstride,
+             long long dst_kstride, const float2* tw) {
+    if (win)
+        k_sec_r2c<N, true, WT><<<grid, 256, 0, s>>>(src, src_bstride, nyg, nxg, wbox, geo, items, nitems, dst,
+                                                    dst_bstride, dst_kstride, tw);
+    else
+        k_sec_r2c<N, false, WT><<<grid, 256, 0, s>>>(src, src_bstride, nyg, nxg, wbox, geo, items, nitems, dst,
+                                                     dst_bstride, dst_kstride, tw);
+}
+
+template <int N, typename WT>
+void sec_c2r(bool win, dim3 grid, cudaStream_t s, const float2* src, long long src_bstride, long long src_kstride,
+             const SecGeom* geo, const int2* items, int nitems, const WT* wbox, float* dst, long long dst_bstride,
+             int nyg, int nxg, float scale, const float2* tw) {
+    if (win)
+        k_sec_c2r<N, true, WT><<<grid, 256, 0, s>>>(src, src_bstride, src_kstride, geo, items, nitems, wbox, dst,
+                                                    dst_bstride, nyg, nxg, scale, tw);
+    else
+        k_sec_c2r<N, false, WT><<<grid, 256, 0, s>>>(src, src_bstride, src_kstride, geo, items, nitems, wbox, dst,
+                                                     dst_bstride, nyg, nxg, scale, tw);
+}
+
+template <bool CONJ, typename HT>
+void sec_cols(dim3 grid, cudaStream_t s, const float2* Z, long long z_bstride, long long z_kstride, int nb,
+              const void* hsT, const void* hsN, const float* hscale, const SecGeom* geo, int nxh, float2* A,
+              long long a_bstride, long long a_kstride, const float2* tw1024, int* status, long long wait_limit,
+              int skip_copy) {
+    kw_sec_cols<CONJ, HT><<<grid, kWColWarps * 32, kWColSmem, s>>>(
+        Z, z_bstride, z_kstride, nb, static_cast<const HT*>(hsT), static_cast<const HT*>(hsN), hscale, geo, nxh, A,
+        a_bstride, a_kstride, tw1024, status, wait_limit, skip_copy);
+}
+
+}  // namespace
+
 cudaError_t launch_sec_r2c(int lc, bool win, dim3 grid, cudaStream_t s, const float* src, long long src_bstride,
-                           int nyg, int nxg, const float* wbox, const SecGeom* geo, const int2* items, int nitems,
-                           float2* dst, long long dst_bstride, long long dst_kstride, const float2* tw) {
+                           int nyg, int nxg, const void* wbox, bool lowp, const SecGeom* geo, const int2* items,
+                           int nitems, float2* dst, long long dst_bstride, long long dst_kstride, const float2* tw) {
     switch (lc) {
-#define X(N)                                                                                   \
-    case N:                                                                                    \
-        if (win)                                                                               \
-            k_sec_r2c<N, true><<<grid, 256, 0, s>>>(src, src_bstride, nyg, nxg, wbox, geo, items, nitems, \
-                                                    dst, dst_bstride, dst_kstride, tw);        \
-        else                                                                                   \
-            k_sec_r2c<N, false><<<grid, 256, 0, s>>>(src, src_bstride, nyg, nxg, wbox, geo, items, nitems, \
-                                                     dst, dst_bstride, dst_kstride, tw);       \
+#define X(N)                                                                                                   \
+    case N:                                                                                                    \
+        if (lowp)                                                                                              \
+            sec_r2c<N>(win, grid, s, src, src_bstride, nyg, nxg, static_cast<const __nv_bfloat16*>(wbox), geo, \
+                       items, nitems, dst, dst_bstride, dst_kstride, tw);                                      \
+        else                                                                                                   \
+            sec_r2c<N>(win, grid, s, src, src_bstride, nyg, nxg, static_cast<const float*>(wbox), geo, items,  \
+                       nitems, dst, dst_bstride, dst_kstride, tw);                                             \
         break;
         PCE_SEC_SIZES(X)
 #undef X
@@ -44,32 +85,42 @@ cudaError_t launch_sec_r2c(int lc, bool win, dim3 grid, cudaStream_t s, const fl
 }
 
 cudaError_t launch_sec_cols(bool conj, dim3 grid, cudaStream_t s, const float2* Z, long long z_bstride,
-                            long long z_kstride, int nb, const float2* hsT, const float2* hsN, const SecGeom* geo,
-                            int nxh, float2* A, long long a_bstride, long long a_kstride, const float2* tw1024,
-                            int* status, long long wait_limit, int skip_copy) {
-    if (!tw1024 || !hsT || !hsN) return cudaErrorInvalidValue;
-    if (conj)
-        kw_sec_cols<true><<<grid, kWColWarps * 32, kWColSmem, s>>>(Z, z_bstride, z_kstride, nb, hsT, hsN, geo, nxh,
-                                                                   A, a_bstride, a_kstride, tw1024, status, wait_limit, skip_copy);
-    else
-        kw_sec_cols<false><<<grid, kWColWarps * 32, kWColSmem, s>>>(Z, z_bstride, z_kstride, nb, hsT, hsN, geo, nxh,
-                                                                    A, a_bstride, a_kstride, tw1024, status, wait_limit, skip_copy);
+                            long long z_kstride, int nb, const void* hsT, const void* hsN, const float* hscale,
+                            bool lowp, const SecGeom* geo, int nxh, float2* A, long long a_bstride,
+                            long long a_kstride, const float2* tw1024, int* status, long long wait_limit,
+                            int skip_copy) {
+    if (!tw1024 || !hsT || !hsN || (lowp && !hscale)) return cudaErrorInvalidValue;
+    if (lowp) {
+        if (conj)
+            sec_cols<true, __half2>(grid, s, Z, z_bstride, z_kstride, nb, hsT, hsN, hscale, geo, nxh, A, a_bstride,
+                                    a_kstride, tw1024, status, wait_limit, skip_copy);
+        else
+            sec_cols<false, __half2>(grid, s, Z, z_bstride, z_kstride, nb, hsT, hsN, hscale, geo, nxh, A, a_bstride,
+                                     a_kstride, tw1024, status, wait_limit, skip_copy);
+    } else {
+        if (conj)
+            sec_cols<true, float2>(grid, s, Z, z_bstride, z_kstride, nb, hsT, hsN, hscale, geo, nxh, A, a_bstride,
+                                   a_kstride, tw1024, status, wait_limit, skip_copy);
+        else
+            sec_cols<false, float2>(grid, s, Z, z_bstride, z_kstride, nb, hsT, hsN, hscale, geo, nxh, A, a_bstride,
+                                    a_kstride, tw1024, status, wait_limit, skip_copy);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_sec_c2r(int lc, bool win, dim3 grid, cudaStream_t s, const float2* src, long long src_bstride,
                            long long src_kstride, const SecGeom* geo, const int2* items, int nitems,
-                           const float* wbox, float* dst, long long dst_bstride, int nyg, int nxg, float scale,
-                           const float2* tw) {
+                           const void* wbox, bool lowp, float* dst, long long dst_bstride, int nyg, int nxg,
+                           float scale, const float2* tw) {
     switch (lc) {
-#define X(N)                                                                                   \
-    case N:                                                                                    \
-        if (win)                                                                               \
-            k_sec_c2r<N, true><<<grid, 256, 0, s>>>(src, src_bstride, src_kstride, geo, items, nitems, wbox, \
-                                                    dst, dst_bstride, nyg, nxg, scale, tw);    \
-        else                                                                                   \
-            k_sec_c2r<N, false><<<grid, 256, 0, s>>>(src, src_bstride, src_kstride, geo, items, nitems, wbox, \
-                                                     dst, dst_bstride, nyg, nxg, scale, tw);   \
+#define X(N)                                                                                                   \
+    case N:                                                                                                    \
+        if (lowp)                                                                                              \
+            sec_c2r<N>(win, grid, s, src, src_bstride, src_kstride, geo, items, nitems,                        \
+                       static_cast<const __nv_bfloat16*>(wbox), dst, dst_bstride, nyg, nxg, scale, tw);        \
+        else                                                                                                   \
+            sec_c2r<N>(win, grid, s, src, src_bstride, src_kstride, geo, items, nitems,                        \
+                       static_cast<const float*>(wbox), dst, dst_bstride, nyg, nxg, scale, tw);                \
         break;
         PCE_SEC_SIZES(X)
 #undef X

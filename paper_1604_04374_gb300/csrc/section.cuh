@@ -37,10 +37,10 @@ constexpr int kSecLR = 1024;
 __device__ __forceinline__ int sec_offset(int n, int lo, int hi, int L) { return n <= hi ? n : n - L; }
 
 // Input rows: items (k, q) take window rows 2q, 2q+1 of term k.
-template <int NX, bool WIN>
+template <int NX, bool WIN, typename WT = float>
 __global__ void __launch_bounds__(256)
 k_sec_r2c(const float* __restrict__ src, long long src_bstride, int NYg, int NXg,
-          const float* __restrict__ wbox, const SecGeom* __restrict__ geo, const int2* __restrict__ items,
+          const WT* __restrict__ wbox, const SecGeom* __restrict__ geo, const int2* __restrict__ items,
           int nitems, float2* __restrict__ dst, long long dst_bstride, long long dst_kstride,
           const float2* __restrict__ tw) {
     constexpr int T = NX / kR;
@@ -73,8 +73,8 @@ k_sec_r2c(const float* __restrict__ src, long long src_bstride, int NYg, int NXg
             if (va) xa = __ldg(sa + col);
             if (vb) xb = __ldg(sb + col);
             if (WIN) {
-                if (va) xa *= __ldg(wbox + g.woff + (long long)ra * g.ldw + rc);
-                if (vb) xb *= __ldg(wbox + g.woff + (long long)rb * g.ldw + rc);
+                if (va) xa *= ldw(wbox + g.woff + (long long)ra * g.ldw + rc);
+                if (vb) xb *= ldw(wbox + g.woff + (long long)rb * g.ldw + rc);
             }
         }
         v[r] = make_float2(xa, xb);
@@ -104,14 +104,16 @@ k_sec_r2c(const float* __restrict__ src, long long src_bstride, int NYg, int NXg
 // Columns of the sections (LR = 1024).  Grid (m, ceil(NXh / 4)), 128
 // threads, kWColSmem bytes; each CTA takes one term and four columns and runs
 // all nb right-hand sides through them.  hsT: the section spectra of h_k,
-// [m][NXh][1024] (c = 0: DC column), hsN: [m][1024] (Nyquist).  A warp's
+// [m][NXh][1024] (c = 0: DC column), hsN: [m][1024] (Nyquist); float2, or
+// half2 times hscale[k] (reduced storage).  A warp's
 // spectrum column (8 KB) is copied into its transpose tile by the TMA engine
 // while the second half of its FFT runs, once per right-hand side; the wait
 // for it is bounded (status bit kStatusTimeout, products skipped after it).
-template <bool CONJ>
+template <bool CONJ, typename HT = float2>
 __global__ void __launch_bounds__(kWColWarps * 32, 3)
 kw_sec_cols(const float2* __restrict__ Z, long long z_bstride, long long z_kstride, int nb,
-            const float2* __restrict__ hsT, const float2* __restrict__ hsN, const SecGeom* __restrict__ geo,
+            const HT* __restrict__ hsT, const HT* __restrict__ hsN, const float* __restrict__ hscale,
+            const SecGeom* __restrict__ geo,
             int NXh, float2* __restrict__ A, long long a_bstride, long long a_kstride,
             const float2* __restrict__ tw, int* __restrict__ status, long long wait_limit, int skip_copy) {
     constexpr int NY = kSecLR;
@@ -131,9 +133,10 @@ kw_sec_cols(const float2* __restrict__ Z, long long z_bstride, long long z_kstri
     __syncwarp();
     unsigned parity = 0;
     bool failed = false;
-    const float2* hcol = hsT + ((long long)k * NXh + (cv ? col : 0)) * NY;
-    const float2* h0 = hsT + (long long)k * NXh * NY;   // DC column (dcn warp only)
-    const float2* hn = hsN + (long long)k * NY;
+    const HT* hcol = hsT + ((long long)k * NXh + (cv ? col : 0)) * NY;
+    const HT* h0 = hsT + (long long)k * NXh * NY;   // DC column (dcn warp only)
+    const HT* hn = hsN + (long long)k * NY;
+    const float sk = hscale_of<HT>(hscale, k);
     const int swl = tix_sw(lane, warp);
     for (int b = 0; b < nb; ++b) {
         // the twiddles and the row indices are the same for every right-hand
@@ -153,7 +156,7 @@ kw_sec_cols(const float2* __restrict__ Z, long long z_bstride, long long z_kstri
         }
         const bool bulk = !dcn && cv && !failed;
         warp_fft1024<false>(v, tr, twb, [&] {
-            if (bulk && lane == 0) bulk_load(tr, hcol, NY * sizeof(float2), bar, skip_copy);
+            if (bulk && lane == 0) bulk_load(tr, hcol, NY * sizeof(HT), bar, skip_copy);
         });
         if (bulk) {
             if (!mbar_wait(bar, parity, wait_limit)) {
@@ -176,8 +179,8 @@ kw_sec_cols(const float2* __restrict__ Z, long long z_bstride, long long z_kstri
                 const int f = lane + 32 * mm;
                 float2 a, bb;
                 split_dc_nyq(v[mm], tr[(NY - f) & (NY - 1)], a, bb);
-                const float2 hd = CONJ ? cconj(__ldg(&h0[f])) : __ldg(&h0[f]);
-                const float2 hN = CONJ ? cconj(__ldg(&hn[f])) : __ldg(&hn[f]);
+                const float2 hd = CONJ ? cconj(ldh(&h0[f], sk)) : ldh(&h0[f], sk);
+                const float2 hN = CONJ ? cconj(ldh(&hn[f], sk)) : ldh(&hn[f], sk);
                 float2 t = cmul(hd, a);
                 const float2 sN = cmul(hN, bb);
                 t.x -= sN.y;
@@ -186,9 +189,10 @@ kw_sec_cols(const float2* __restrict__ Z, long long z_bstride, long long z_kstri
             }
             __syncwarp();
         } else if (cv && !failed) {
+            const HT* th = reinterpret_cast<const HT*>(tr);
 #pragma unroll
             for (int mm = 0; mm < 32; ++mm) {
-                const float2 hv = tr[lane + 32 * mm];
+                const float2 hv = lds_h(&th[lane + 32 * mm], sk);
                 v[mm] = CONJ ? cmulc(v[mm], hv) : cmul(v[mm], hv);
             }
         } else {
@@ -212,11 +216,11 @@ kw_sec_cols(const float2* __restrict__ Z, long long z_bstride, long long z_kstri
 
 // Output rows: items (k, q) take output-window rows 2q, 2q+1 of term k; C2R,
 // times scale (and the window in the adjoint), added into the grid.
-template <int NX, bool WIN>
+template <int NX, bool WIN, typename WT = float>
 __global__ void __launch_bounds__(256)
 k_sec_c2r(const float2* __restrict__ src, long long src_bstride, long long src_kstride,
           const SecGeom* __restrict__ geo, const int2* __restrict__ items, int nitems,
-          const float* __restrict__ wbox, float* __restrict__ dst, long long dst_bstride, int NYg, int NXg,
+          const WT* __restrict__ wbox, float* __restrict__ dst, long long dst_bstride, int NYg, int NXg,
           float scale, const float2* __restrict__ tw) {
     constexpr int T = NX / kR;
     constexpr int FPC = 256 / T;
@@ -255,8 +259,8 @@ k_sec_c2r(const float2* __restrict__ src, long long src_bstride, long long src_k
         if (WIN) {
             const int rc = sec_offset(j + r * T, g.out_lo_c, g.out_hi_c, NX);
             const bool in = rc >= g.out_lo_c && rc <= g.out_hi_c;
-            wa[r] = (in && va) ? __ldg(wbox + g.woff + (long long)ra * g.ldw + rc) : 0.f;
-            wb[r] = (in && vb) ? __ldg(wbox + g.woff + (long long)rb * g.ldw + rc) : 0.f;
+            wa[r] = (in && va) ? ldw(wbox + g.woff + (long long)ra * g.ldw + rc) : 0.f;
+            wb[r] = (in && vb) ? ldw(wbox + g.woff + (long long)rb * g.ldw + rc) : 0.f;
         }
     }
     fft<NX, true>(v, j, b0, b1, tw);
