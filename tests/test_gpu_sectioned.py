@@ -50,8 +50,10 @@ def short_h(pr, seed, ra=5, rb=3):
     return h
 
 
-@pytest.mark.parametrize("ny,nx,m,batch", [(2048, 64, 64, 2), (1024, 128, 16, 1), (2048, 256, 64, 1)])
+@pytest.mark.parametrize("ny,nx,m,batch", [(2048, 64, 64, 2), (1024, 128, 16, 1), (2048, 256, 64, 1),
+                                            (1024, 1024, 16, 1)])
 def test_sectioned_matches_oracle(torch_cuda, ny, nx, m, batch):
+    """Section widths 32, 32, 128 and 1024."""
     torch = torch_cuda
     from paper_1604_04374_gb300 import Plan, pce
     pr = synth.problem_2d(ny, nx, m, batch, 400 + m, "normal")
