@@ -828,19 +828,66 @@ def batch_arm(args, rank: int, world: int) -> None:
 
     seq_ms = timed(sequential, args.steps) if args.comparator else None
 
-    # end to end: every task's input from pinned host memory, the graph, every output back
+    # end to end: every task's input from pinned host memory, the graph, every output
+    # back, pipelined like a serving loop: two buffer sets, each bound to its own batch;
+    # step i copies its inputs in (copy-in stream), runs its graph (compute stream) and
+    # copies its outputs back (copy-out stream), overlapping steps i-1 and i+1
+    ref_outs = [o.clone() for o in outs]
     hin = [torch.from_numpy(u).pin_memory() for u in mx.inputs]
-    hout = [torch.empty_like(x).pin_memory() for x in hin]
+    hout = [[torch.empty_like(x).pin_memory() for x in hin] for _ in range(2)]
+    sets = [(ins, outs, batch)]
+    ins2 = [torch.empty_like(x) for x in ins]
+    outs2 = [torch.empty_like(x) for x in outs]
+    tasks2 = [(plans[mx.op_of[i]], ins2[i], outs2[i], mx.adjoint[i]) for i in range(len(ins))]
+    batch2 = Batch(tasks2, lanes=args.lanes)
+    if args.autotune:
+        batch2.autotune()
+    sets.append((ins2, outs2, batch2))
+    s_in, s_comp, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    ev = {key: [torch.cuda.Event() for _ in range(2)] for key in ("in", "comp", "out")}
+    started = [False, False]
 
-    def e2e():
-        for a, b in zip(ins, hin):
-            a.copy_(b, non_blocking=True)
-        batch.launch()
-        for a, b in zip(hout, outs):
-            a.copy_(b, non_blocking=True)
+    def e2e_step(i):
+        k = i % 2
+        din, dout, bt = sets[k]
+        with torch.cuda.stream(s_in):
+            if started[k]:
+                s_in.wait_event(ev["comp"][k])      # step i-2 has consumed these inputs
+            for a, b in zip(din, hin):
+                a.copy_(b, non_blocking=True)
+            ev["in"][k].record(s_in)
+        with torch.cuda.stream(s_comp):
+            s_comp.wait_event(ev["in"][k])
+            if started[k]:
+                s_comp.wait_event(ev["out"][k])     # step i-2's outputs have been read back
+            bt.launch(s_comp)
+            ev["comp"][k].record(s_comp)
+        with torch.cuda.stream(s_out):
+            s_out.wait_event(ev["comp"][k])
+            for a, b in zip(hout[k], dout):
+                a.copy_(b, non_blocking=True)
+            ev["out"][k].record(s_out)
+        started[k] = True
 
-    e2e_ms = timed(e2e, max(10, args.steps // 4))
     e2e_steps = max(10, args.steps // 4)
+    for i in range(max(2, args.warmup)):
+        e2e_step(i)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s_in.wait_stream(stream)
+    for i in range(e2e_steps):
+        e2e_step(i)
+    stream.wait_stream(s_out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+    last = hout[(e2e_steps - 1) % 2]
+    e2e_ok = all(torch.equal(a, b.cpu()) for a, b in zip(last, ref_outs))
+    batch2.close()
     if rank == 0:
         clocks = sampler.summary() if sampler else {}
         sm_max = clocks.get("sm_max_mhz") or 2070.0
@@ -880,7 +927,10 @@ def batch_arm(args, rank: int, world: int) -> None:
                             "unit": UNIT, "ms_per_step": seq_ms / args.steps,
                             "speedup": seq_ms / graph_ms} if seq_ms else None),
             "e2e": {"value": weak_scaling_value(n_tasks / 2, e2e_steps, world, e2e_ms), "unit": UNIT,
-                    "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes},
+                    "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes,
+                    "how": "pinned host inputs -> device, graph, every output -> pinned host, every step; "
+                           "two buffer sets on copy-in / compute / copy-out streams",
+                    "results_match_device_run": e2e_ok},
             "gpu_launches": launches * args.steps,
             "clocks": clocks,
             "scratch_bytes": scratch,
