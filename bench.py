@@ -143,36 +143,50 @@ def work_model(pr: synth.Problem, boxes, nb: int, slots=None) -> dict:
 def sectioned_work_model(pr: synth.Problem, boxes, nb: int) -> dict:
     """Algorithmic flops and bytes per launch of the sectioned kernels (PCE_FLAG_SECTIONED)
     for a chunk of nb right-hand sides, from the support boxes of w_k and the exact
-    support of every h_k (as the plan finds them).  Per term: forward input window =
-    box (nr x nc), output window = box dilated by the support (nr + snr - 1 rows,
-    nc + snc - 1 columns); sections of 1024 x LC points, LC the smallest power of two
-    (at least 16) holding every output window's columns.  Bytes: window inputs read
+    support of every h_k, with the plan's choice of sections: each term's box is cut
+    into column tiles of LC - snc + 1 columns (one section each), LC the power of two
+    in 16..2048 of least modelled work.  Per section: forward input window = tile
+    (nr x nct), output window = tile dilated by the support (nr + snr - 1 rows,
+    nct + snc - 1 columns), sections of 1024 x LC points.  Bytes: window inputs read
     once, section spectra of h read once per launch, intermediates written once and
     read once, the output window added once."""
-    ny, nx = pr.shape
     terms = []
-    need_c = 1
     for k, (r0, nr, c0, nc) in enumerate(boxes):
         _, snr = cyclic_extent(np.any(pr.h[k] != 0, axis=1))
         _, snc = cyclic_extent(np.any(pr.h[k] != 0, axis=0))
         if nr == 0 or snr == 0:
             continue
-        terms.append((nr, nc, nr + snr - 1, nc + snc - 1))
-        need_c = max(need_c, nc + snc - 1)
+        terms.append((nr, nc, snr, snc))
     lc = 16
-    while lc < need_c:
+    while lc < max([t[3] for t in terms] + [1]):
         lc *= 2
+    best = None
+    w = lc
+    while w <= 2048:
+        cost = sum(((nc + w - snc) // (w - snc + 1)) * ((2 * nr + snr - 1) * 2.5 * w * math.log2(w)
+                                                       + (w // 2) * 2.0 * 5.0 * 1024 * 10)
+                   for nr, nc, snr, snc in terms)
+        if best is None or cost < best[0]:
+            best = (cost, w)
+        w *= 2
+    lc = best[1]
     lch = lc // 2
+    secs = []                                   # (in rows, in cols, out rows, out cols, term)
+    for t, (nr, nc, snr, snc) in enumerate(terms):
+        tw = lc - snc + 1
+        for cs in range(0, nc, tw):
+            nct = min(tw, nc - cs)
+            secs.append((nr, nct, nr + snr - 1, nct + snc - 1, t))
     f_row = 2.5 * lc * math.log2(lc)
     f_col = 2 * 5.0 * 1024 * 10 + 6.0 * 1024        # FFT, product, inverse FFT per column
-    in_rows = sum(t[0] for t in terms)
-    out_rows = sum(t[2] for t in terms)
-    in_px = sum(t[0] * t[1] for t in terms)
-    out_px = sum(t[2] * t[3] for t in terms)
+    in_rows = sum(x[0] for x in secs)
+    out_rows = sum(x[2] for x in secs)
+    in_px = sum(x[0] * x[1] for x in secs)
+    out_px = sum(x[2] * x[3] for x in secs)
     hs = len(terms) * (lch * 1024 + 1024) * 8
-    cols = len(terms) * lch
+    cols = len(secs) * lch
     return {
-        "lc": lc,
+        "lc": lc, "sections": len(secs),
         "rows_r2c_window": (nb * (in_rows * f_row + in_px), nb * in_px * 4 + in_px * 4 + nb * in_rows * lch * 8),
         "cols_fwd": (nb * cols * f_col, nb * (in_rows + out_rows) * lch * 8 + hs),
         "rows_c2r": (nb * out_rows * f_row, nb * out_rows * lch * 8 + nb * out_px * 4),
@@ -618,6 +632,7 @@ def gpu_arm(args, pr: synth.Problem, rank: int, world: int) -> None:
         if sectioned and "kernel_times" in sectioned:
             smodel = sectioned_work_model(pr, sectioned.pop("boxes"), sectioned["chunk"])
             sectioned["lc"] = smodel["lc"]
+            sectioned["sections"] = smodel["sections"]
             sk, sdom = kernel_table(sectioned.pop("kernel_times"), smodel)
             sectioned["kernels"] = sk
             if sdom:

@@ -98,18 +98,20 @@ typedef struct pce_plan* pce_plan_t;
  */
 #define PCE_FLAG_PRODUCT_CONVOLUTION 4u
 /*
- * PCE_FLAG_SECTIONED: applies convolve every term on a section (Lemma 3.2)
- * of 1024 rows x L columns, L the smallest power of two holding the width of
- * w_k's support box plus the width of h_k's support (h_k's exact nonzeros,
- * found at plan time), and add the sections into the output (overlap-add;
- * atomic adds, so the rounding order varies from run to run).  Pays when the
+ * PCE_FLAG_SECTIONED: applies convolve every term on sections (Lemma 3.2) of
+ * 1024 rows x L columns and add the sections into the output (overlap-add;
+ * atomic adds, so the rounding order varies from run to run).  Each term's
+ * support box is cut into column tiles of L - (width of h_k's support) + 1
+ * columns, one section per tile (h_k's exact nonzeros are found at plan
+ * time); L, a power of two from 16 to 2048, is the width of least modelled
+ * FFT work.  Pays when the
  * grid is much larger than box + support (e.g. 2048 x 2048 with boxes of 511
  * and 73-pixel PSFs: two 1024-point column FFTs per term instead of one
  * 2048-point one shared with the other terms).  2D plans from pce_plan_create
  * only, fused, convolution-product form; with PCE_FLAG_LOWP_STORAGE the
  * section spectra are stored as half2 with their own per-term power-of-two
  * scales and the windows as bfloat16.  Box rows + support rows - 1 <= 1024
- * and box columns + support columns - 1 <= 2048 for every term.
+ * and support columns <= 2048 for every term.
  * Otherwise PCE_ERR_UNSUPPORTED.  Gradients and pce_apply_noalloc use the
  * plan's whole-grid structures.
  */

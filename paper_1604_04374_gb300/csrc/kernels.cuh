@@ -43,8 +43,8 @@ struct SecGeom {
     int in_lo_c, in_hi_c;   // input columns: box offsets in_lo_c .. in_hi_c
     int out_lo_r, out_rows;
     int out_lo_c, out_hi_c;
-    long long woff;         // window box copy [nr][ldw] (the box of w_k)
-    int ldw, pad_;
+    long long woff;         // window box copy [nr][ldw] (the box of w_k), at the section's first column
+    int ldw, k;             // k: the term whose section spectrum the section uses
 };
 
 // Separable windows w_k = wy_k (x) wx_k: terms sharing the column factor wx

@@ -1023,7 +1023,7 @@ pce_status setup_sectioned(pce_plan* p, const float* h, cudaStream_t s) {
     cudaFree(flags);
     PCE_CK(e);
     std::vector<HSupport> sup(m);
-    int need_c = 1;
+    int max_snc = 1;
     for (int k = 0; k < m; ++k) {
         HSupport& sp = sup[k];
         cyclic_support(&hf[(size_t)k * ny], ny, sp.sr0, sp.snr);
@@ -1036,49 +1036,79 @@ pce_status setup_sectioned(pce_plan* p, const float* h, cudaStream_t s) {
         if (b.nr + sp.snr - 1 > 1024)
             return fail(PCE_ERR_UNSUPPORTED, "term %d: box rows %d + support rows %d - 1 exceed a 1024-row section",
                         k, b.nr, sp.snr);
-        need_c = std::max(need_c, b.nc + sp.snc - 1);
+        max_snc = std::max(max_snc, sp.snc);
     }
+    if (max_snc > 2048)
+        return fail(PCE_ERR_UNSUPPORTED, "support columns %d exceed a 2048-column section", max_snc);
+    // Section width LC (a power of two, 16 .. 2048, at least every support's
+    // width): each term's box columns are cut into tiles of LC - snc + 1
+    // columns, one section each, and the LC of least modelled work is kept
+    // (R2C / C2R of the input and output rows of every section, LC/2 pairs
+    // of 1024-point column FFTs per section).
+    auto live = [&](int k) { return p->box[k].nr > 0 && sup[k].snr > 0; };
+    auto tiles = [&](int k, int w) { return (p->box[k].nc + (w - sup[k].snc)) / (w - sup[k].snc + 1); };
     int lc = 16;
-    while (lc < need_c) lc *= 2;
-    if (lc > 2048)
-        return fail(PCE_ERR_UNSUPPORTED, "box columns + support columns - 1 = %d exceed a 2048-column section", need_c);
-    // windows
-    std::vector<SecGeom> gf(m), ga(m);
+    while (lc < max_snc) lc *= 2;
+    double best = -1.0;
+    int best_lc = lc;
+    for (int w = lc; w <= 2048; w *= 2) {
+        double cost = 0.0;
+        for (int k = 0; k < m; ++k) {
+            if (!live(k)) continue;
+            const Box& b = p->box[k];
+            const double rows = 2.0 * b.nr + sup[k].snr - 1;
+            cost += tiles(k, w) * (rows * 2.5 * w * std::log2((double)w) + (w / 2) * 2.0 * 5.0 * 1024 * 10);
+        }
+        if (best < 0.0 || cost < best) {
+            best = cost;
+            best_lc = w;
+        }
+    }
+    lc = best_lc;
+    // windows: one section per (term, column tile)
+    std::vector<SecGeom> gf, ga;
     std::vector<int2> ibox, iwin;
     int rows_max = 1;
     for (int k = 0; k < m; ++k) {
+        if (!live(k)) continue;
         const Box& b = p->box[k];
         const HSupport& sp = sup[k];
-        SecGeom f{};
-        f.r0 = b.r0;
-        f.c0 = b.c0;
-        f.woff = b.woff;
-        f.ldw = b.ldw;
-        const bool live = b.nr > 0 && sp.snr > 0;
-        const int wr = live ? b.nr + sp.snr - 1 : 0;
-        f.in_lo_r = 0;
-        f.in_rows = live ? b.nr : 0;
-        f.in_lo_c = 0;
-        f.in_hi_c = b.nc - 1;
-        f.out_lo_r = sp.dr0;
-        f.out_rows = wr;
-        f.out_lo_c = sp.dc0;
-        f.out_hi_c = b.nc - 1 + sp.dc0 + sp.snc - 1;
-        SecGeom a = f;
-        a.in_lo_r = f.out_lo_r;
-        a.in_rows = f.out_rows;
-        a.in_lo_c = f.out_lo_c;
-        a.in_hi_c = f.out_hi_c;
-        a.out_lo_r = 0;
-        a.out_rows = f.in_rows;
-        a.out_lo_c = 0;
-        a.out_hi_c = b.nc - 1;
-        gf[k] = f;
-        ga[k] = a;
-        for (int q = 0; q < (f.in_rows + 1) / 2; ++q) ibox.push_back(make_int2(k, q));
-        for (int q = 0; q < (wr + 1) / 2; ++q) iwin.push_back(make_int2(k, q));
+        const int tw_c = lc - sp.snc + 1;   // box columns per tile
+        const int wr = b.nr + sp.snr - 1;
+        for (int t = 0, cs = 0; cs < b.nc; ++t, cs += tw_c) {
+            const int nct = std::min(tw_c, b.nc - cs);
+            SecGeom f{};
+            f.r0 = b.r0;
+            f.c0 = b.c0 + cs;
+            f.woff = b.woff + cs;
+            f.ldw = b.ldw;
+            f.k = k;
+            f.in_lo_r = 0;
+            f.in_rows = b.nr;
+            f.in_lo_c = 0;
+            f.in_hi_c = nct - 1;
+            f.out_lo_r = sp.dr0;
+            f.out_rows = wr;
+            f.out_lo_c = sp.dc0;
+            f.out_hi_c = nct - 1 + sp.dc0 + sp.snc - 1;
+            SecGeom a = f;
+            a.in_lo_r = f.out_lo_r;
+            a.in_rows = f.out_rows;
+            a.in_lo_c = f.out_lo_c;
+            a.in_hi_c = f.out_hi_c;
+            a.out_lo_r = 0;
+            a.out_rows = f.in_rows;
+            a.out_lo_c = 0;
+            a.out_hi_c = nct - 1;
+            const int sidx = (int)gf.size();
+            gf.push_back(f);
+            ga.push_back(a);
+            for (int q = 0; q < (f.in_rows + 1) / 2; ++q) ibox.push_back(make_int2(sidx, q));
+            for (int q = 0; q < (wr + 1) / 2; ++q) iwin.push_back(make_int2(sidx, q));
+        }
         rows_max = std::max(rows_max, wr);
     }
+    const int nsec = (int)gf.size();
     pce_status st;
     // twiddles: one-warp 1024-point columns, Stockham rows of lc
     if (!p->tw1024) {
@@ -1136,12 +1166,14 @@ pce_status setup_sectioned(pce_plan* p, const float* h, cudaStream_t s) {
     cleanup();
     if (e != cudaSuccess) return fail(PCE_ERR_CUDA, "section spectra: %s", cudaGetErrorString(e));
     // windows, work lists, scratch
-    if ((st = dev_alloc(&p->d_geo_f, (size_t)m))) return st;
-    if ((st = dev_alloc(&p->d_geo_a, (size_t)m))) return st;
+    if ((st = dev_alloc(&p->d_geo_f, (size_t)std::max(nsec, 1)))) return st;
+    if ((st = dev_alloc(&p->d_geo_a, (size_t)std::max(nsec, 1)))) return st;
     if ((st = dev_alloc(&p->sec_items_box, std::max<size_t>(ibox.size(), 1)))) return st;
     if ((st = dev_alloc(&p->sec_items_win, std::max<size_t>(iwin.size(), 1)))) return st;
-    PCE_CK(cudaMemcpyAsync(p->d_geo_f, gf.data(), sizeof(SecGeom) * m, cudaMemcpyHostToDevice, s));
-    PCE_CK(cudaMemcpyAsync(p->d_geo_a, ga.data(), sizeof(SecGeom) * m, cudaMemcpyHostToDevice, s));
+    if (nsec > 0) {
+        PCE_CK(cudaMemcpyAsync(p->d_geo_f, gf.data(), sizeof(SecGeom) * nsec, cudaMemcpyHostToDevice, s));
+        PCE_CK(cudaMemcpyAsync(p->d_geo_a, ga.data(), sizeof(SecGeom) * nsec, cudaMemcpyHostToDevice, s));
+    }
     if (!ibox.empty())
         PCE_CK(cudaMemcpyAsync(p->sec_items_box, ibox.data(), sizeof(int2) * ibox.size(), cudaMemcpyHostToDevice, s));
     if (!iwin.empty())
@@ -1150,8 +1182,9 @@ pce_status setup_sectioned(pce_plan* p, const float* h, cudaStream_t s) {
     p->n_items_box = (int)ibox.size();
     p->n_items_win = (int)iwin.size();
     p->sec_lc = lc;
+    p->nsec = nsec;
     p->sec_k = (long long)rows_max * lch;
-    p->sec_b = (long long)m * p->sec_k;
+    p->sec_b = (long long)std::max(nsec, 1) * p->sec_k;
     const long long per_b = 2 * p->sec_b * (long long)sizeof(float2);
     p->sec_chunk = (int)std::max<long long>(1, std::min<long long>(kMaxChunk, kScratchBudget / per_b));
     if ((st = dev_alloc(&p->scrZs, (size_t)(p->sec_b * p->sec_chunk)))) return st;
@@ -1465,7 +1498,7 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
                 });
             if (e == cudaSuccess)
                 e = timed(p, adjoint ? PCE_KERNEL_COLS_ADJ : PCE_KERNEL_COLS_FWD, s, [&] {
-                    return pce::launch_sec_cols(adjoint, dim3(m, (lch + cpc - 1) / cpc), s, scr.Z, scr.zstride,
+                    return pce::launch_sec_cols(adjoint, dim3(p->nsec, (lch + cpc - 1) / cpc), s, scr.Z, scr.zstride,
                                                 p->sec_k, nb, hst, hsn, p->sec_hscale, p->lowp, geo, lch, scr.A,
                                                 scr.astride, p->sec_k, p->tw1024, p->d_status, p->wait_limit,
                                                 p->skip_copy);

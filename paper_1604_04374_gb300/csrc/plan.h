@@ -85,8 +85,8 @@ struct pce_plan {
     // sectioned apply (PCE_FLAG_SECTIONED): per term a 1024 x sec_lc section
     bool sect = false;
     int sec_lc = 0;
-    SecGeom* d_geo_f = nullptr;   // [m] forward windows
-    SecGeom* d_geo_a = nullptr;   // [m] adjoint windows
+    SecGeom* d_geo_f = nullptr;   // [nsec] forward windows
+    SecGeom* d_geo_a = nullptr;   // [nsec] adjoint windows
     int2* sec_items_box = nullptr;   // (k, pair) over the box rows
     int2* sec_items_win = nullptr;   // (k, pair) over the forward output window rows
     int n_items_box = 0, n_items_win = 0;
@@ -97,9 +97,10 @@ struct pce_plan {
     __half2* hsN16 = nullptr;
     float* sec_hscale = nullptr;
     float2* sec_twc = nullptr;    // Stockham twiddles of sec_lc
-    float2* scrZs = nullptr;      // [chunk][m][rows][sec_lc/2]
+    float2* scrZs = nullptr;      // [chunk][nsec][rows][sec_lc/2]
     float2* scrAs = nullptr;
-    long long sec_k = 0, sec_b = 0;   // float2 per term, per right-hand side
+    int nsec = 0;                 // sections: one per (term, column tile of its box)
+    long long sec_k = 0, sec_b = 0;   // float2 per section, per right-hand side
     int sec_chunk = 1;
     // per-kernel timing
     bool timing = false;

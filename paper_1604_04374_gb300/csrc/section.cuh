@@ -1,11 +1,13 @@
-// section.cuh -- sectioned apply (Lemma 3.2): every term is convolved on a
-// section of LR x LC points (LR = 1024 rows, LC a power of two) just large
-// enough for the window box of w_k plus the support of h_k, and the results
-// are added into the output (overlap-add), instead of transforming the whole
-// grid once per term.
+// section.cuh -- sectioned apply (Lemma 3.2): every term is convolved on
+// sections of LR x LC points (LR = 1024 rows, LC a power of two chosen at plan
+// time), each holding a column tile of the window box of w_k plus the support
+// of h_k, and the results are added into the output (overlap-add), instead of
+// transforming the whole grid once per term.  Sections are indexed by s; the
+// geometry of section s (SecGeom) names its term k.
 //
-// Coordinates.  A term's box starts at grid (r0, c0); section offsets rho are
-// relative to it.  h_k's support, as signed offsets, is [dr0, dr0 + snr) x
+// Coordinates.  A section's tile of the box starts at grid (r0, c0) (its
+// columns [c0, c0 + nc) are box columns of the term; tiles of one term take
+// consecutive column ranges); section offsets rho are relative to it.  h_k's support, as signed offsets, is [dr0, dr0 + snr) x
 // [dc0, dc0 + snc).  h_k is placed at section position (d mod LR, d mod LC);
 // a section position holds box offset rho at rho mod LR (LC).
 //   forward:  input rows rho in [0, nr),   columns [0, nc)   (times w_k)
@@ -16,8 +18,8 @@
 //
 // Kernels (one warp per 1024-point column, Stockham FFTs for the rows):
 //   k_sec_r2c:  rows of the input window gathered from the grid (w_k applied
-//               in the forward), R2C, packed half spectra [b][k][row][LC/2]
-//   kw_sec_cols: per term and column, FFT_y, times the section spectrum of
+//               in the forward), R2C, packed half spectra [b][s][row][LC/2]
+//   kw_sec_cols: per section and column, FFT_y, times the section spectrum of
 //               h_k (conjugated for the adjoint; copied into shared memory
 //               by the TMA engine during the FFT, once per right-hand side),
 //               IFFT_y, output rows
@@ -101,9 +103,9 @@ k_sec_r2c(const float* __restrict__ src, long long src_bstride, int NYg, int NXg
     }
 }
 
-// Columns of the sections (LR = 1024).  Grid (m, ceil(NXh / 4)), 128
-// threads, kWColSmem bytes; each CTA takes one term and four columns and runs
-// all nb right-hand sides through them.  hsT: the section spectra of h_k,
+// Columns of the sections (LR = 1024).  Grid (sections, ceil(NXh / 4)), 128
+// threads, kWColSmem bytes; each CTA takes one section and four columns and
+// runs all nb right-hand sides through them.  hsT: the section spectra of h_k,
 // [m][NXh][1024] (c = 0: DC column), hsN: [m][1024] (Nyquist); float2, or
 // half2 times hscale[k] (reduced storage).  A warp's
 // spectrum column (8 KB) is copied into its transpose tile by the TMA engine
@@ -121,12 +123,13 @@ kw_sec_cols(const float2* __restrict__ Z, long long z_bstride, long long z_kstri
     float2* tile = smem;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float2* tr = smem + NY * kWColWarps + warp * kWarpN;
-    const int k = blockIdx.x;
+    const int sec = blockIdx.x;   // section; its term is g.k
     const int col0 = blockIdx.y * kWColWarps;
     const int col = col0 + warp;
     const bool cv = col < NXh;
     const bool dcn = blockIdx.y == 0 && warp == 0;
-    const SecGeom g = geo[k];
+    const SecGeom g = geo[sec];
+    const int k = g.k;
     __shared__ unsigned long long bars[kWColWarps];
     unsigned long long* bar = &bars[warp];
     if (lane == 0) mbar_init(bar);
@@ -145,7 +148,7 @@ kw_sec_cols(const float2* __restrict__ Z, long long z_bstride, long long z_kstri
         const float2* twb = tw;
         int lo_r = g.in_lo_r, rows = g.in_rows;
         asm volatile("" : "+l"(twb), "+r"(lo_r), "+r"(rows));
-        tile_load(tile, Z + b * z_bstride + k * z_kstride, g.in_rows, NXh, col0);
+        tile_load(tile, Z + b * z_bstride + sec * z_kstride, g.in_rows, NXh, col0);
         cp_async_wait_all();
         __syncthreads();
         float2 v[32];
@@ -204,7 +207,7 @@ kw_sec_cols(const float2* __restrict__ Z, long long z_bstride, long long z_kstri
 #pragma unroll
         for (int q = 0; q < 32; ++q) tile[4 * (lane + 32 * q) + swl] = v[q];
         __syncthreads();
-        float2* Ab = A + b * a_bstride + k * a_kstride;
+        float2* Ab = A + b * a_bstride + sec * a_kstride;
         for (int e = threadIdx.x; e < g.out_rows * kWColWarps; e += kWColWarps * 32) {
             const int i = e >> 2, c = e & 3;
             const int s = wrap(g.out_lo_r + i, NY);
