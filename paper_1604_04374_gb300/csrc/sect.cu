@@ -19,7 +19,7 @@ cudaError_t prepare_sec() {
     const void* fns[] = {(const void*)kw_sec_cols<false, float2>, (const void*)kw_sec_cols<true, float2>,
                          (const void*)kw_sec_cols<false, __half2>, (const void*)kw_sec_cols<true, __half2>};
     for (const void* f : fns) {
-        const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kWColSmem);
+        const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kSecColSmem);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -56,7 +56,7 @@ void sec_cols(dim3 grid, cudaStream_t s, const float2* Z, long long z_bstride, l
               const void* hsT, const void* hsN, const float* hscale, const SecGeom* geo, int nxh, float2* A,
               long long a_bstride, long long a_kstride, const float2* tw1024, int* status, long long wait_limit,
               int skip_copy) {
-    kw_sec_cols<CONJ, HT><<<grid, kWColWarps * 32, kWColSmem, s>>>(
+    kw_sec_cols<CONJ, HT><<<grid, kWColWarps * 32, kSecColSmem, s>>>(
         Z, z_bstride, z_kstride, nb, static_cast<const HT*>(hsT), static_cast<const HT*>(hsN), hscale, geo, nxh, A,
         a_bstride, a_kstride, tw1024, status, wait_limit, skip_copy);
 }

@@ -21,8 +21,7 @@
 //               in the forward), R2C, packed half spectra [b][s][row][LC/2]
 //   kw_sec_cols: per section and column, FFT_y, times the section spectrum of
 //               h_k (conjugated for the adjoint; copied into shared memory
-//               by the TMA engine during the FFT, once per right-hand side),
-//               IFFT_y, output rows
+//               by the TMA engine once per CTA), IFFT_y, output rows
 //   k_sec_c2r:  C2R of the output rows, times 1 / (LR LC) (and w_k in the
 //               adjoint), added into the grid with atomicAdd (terms overlap)
 #pragma once
@@ -107,12 +106,16 @@ k_sec_r2c(const float* __restrict__ src, long long src_bstride, int NYg, int NXg
 // threads, kWColSmem bytes; each CTA takes one section and four columns and
 // runs all nb right-hand sides through them.  hsT: the section spectra of h_k,
 // [m][NXh][1024] (c = 0: DC column), hsN: [m][1024] (Nyquist); float2, or
-// half2 times hscale[k] (reduced storage).  A warp's
-// spectrum column (8 KB) is copied into its transpose tile by the TMA engine
-// while the second half of its FFT runs, once per right-hand side; the wait
-// for it is bounded (status bit kStatusTimeout, products skipped after it).
+// half2 times hscale[k] (reduced storage).  A warp's spectrum column (8 KB)
+// is copied once per CTA into a buffer of its own by the TMA engine, at the
+// start, and serves every right-hand side (several sections of a term read
+// the same columns, so per-right-hand-side copies multiplied the traffic);
+// the one wait for it is bounded (status bit kStatusTimeout, products skipped
+// after it).  Shared memory: tile, transpose tiles, spectrum buffers (96 KB,
+// two CTAs per SM).
+constexpr int kSecColSmem = 2 * kSecLR * kWColWarps * 8 + kWColWarps * kSecLR * 8;
 template <bool CONJ, typename HT = float2>
-__global__ void __launch_bounds__(kWColWarps * 32, 3)
+__global__ void __launch_bounds__(kWColWarps * 32, 2)
 kw_sec_cols(const float2* __restrict__ Z, long long z_bstride, long long z_kstride, int nb,
             const HT* __restrict__ hsT, const HT* __restrict__ hsN, const float* __restrict__ hscale,
             const SecGeom* __restrict__ geo,
@@ -141,6 +144,9 @@ kw_sec_cols(const float2* __restrict__ Z, long long z_bstride, long long z_kstri
     const HT* hn = hsN + (long long)k * NY;
     const float sk = hscale_of<HT>(hscale, k);
     const int swl = tix_sw(lane, warp);
+    HT* hb = reinterpret_cast<HT*>(smem + 2 * NY * kWColWarps) + warp * NY;
+    const bool bulk = !dcn && cv;
+    if (bulk && lane == 0) bulk_load(hb, hcol, NY * sizeof(HT), bar, skip_copy);
     for (int b = 0; b < nb; ++b) {
         // the twiddles and the row indices are the same for every right-hand
         // side; opaque copies keep the compiler from holding them in registers
@@ -157,16 +163,13 @@ kw_sec_cols(const float2* __restrict__ Z, long long z_bstride, long long z_kstri
             const int i = wrap(lane + 32 * q - lo_r, NY);
             v[q] = (i < rows) ? tile[tix(i, warp)] : make_float2(0.f, 0.f);
         }
-        const bool bulk = !dcn && cv && !failed;
-        warp_fft1024<false>(v, tr, twb, [&] {
-            if (bulk && lane == 0) bulk_load(tr, hcol, NY * sizeof(HT), bar, skip_copy);
-        });
-        if (bulk) {
+        warp_fft1024<false>(v, tr, twb);
+        if (bulk && b == 0) {
             if (!mbar_wait(bar, parity, wait_limit)) {
                 failed = true;
                 if (lane == 0) atomicOr(status, kStatusTimeout);
-                // a copy may still be in flight into the tile: wait once more
-                // (bounded) before the tile is reused; no further copies are issued
+                // the copy may still be in flight into the buffer: wait once more
+                // (bounded) before the kernel goes on; the products are skipped
                 mbar_wait(bar, parity, wait_limit);
             }
             parity ^= 1;
@@ -192,10 +195,9 @@ kw_sec_cols(const float2* __restrict__ Z, long long z_bstride, long long z_kstri
             }
             __syncwarp();
         } else if (cv && !failed) {
-            const HT* th = reinterpret_cast<const HT*>(tr);
 #pragma unroll
             for (int mm = 0; mm < 32; ++mm) {
-                const float2 hv = lds_h(&th[lane + 32 * mm], sk);
+                const float2 hv = lds_h(&hb[lane + 32 * mm], sk);
                 v[mm] = CONJ ? cmulc(v[mm], hv) : cmul(v[mm], hv);
             }
         } else {
