@@ -1079,7 +1079,7 @@ pce_status setup_sectioned(pce_plan* p, const float* h, cudaStream_t s) {
             const int nct = std::min(tw_c, b.nc - cs);
             SecGeom f{};
             f.r0 = b.r0;
-            f.c0 = b.c0 + cs;
+            f.c0 = (b.c0 + cs) % nx;   // grid column of the tile's first box column
             f.woff = b.woff + cs;
             f.ldw = b.ldw;
             f.k = k;

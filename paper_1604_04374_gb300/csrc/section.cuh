@@ -37,6 +37,19 @@ constexpr int kSecLR = 1024;
 // a value outside the window
 __device__ __forceinline__ int sec_offset(int n, int lo, int hi, int L) { return n <= hi ? n : n - L; }
 
+// Grid column of section column offset rc: c0 is in [0, n) and |rc| < L, so
+// for sections no wider than the grid (L <= n) one conditional add or
+// subtract wraps it; wider sections (small grids) take the remainder.
+__device__ __forceinline__ int sec_col(int c0, int rc, int n, bool narrow) {
+    int c = c0 + rc;
+    if (narrow) {
+        c += c < 0 ? n : 0;
+        c -= c >= n ? n : 0;
+        return c;
+    }
+    return (c % n + n) % n;
+}
+
 // Input rows: items (k, q) take window rows 2q, 2q+1 of term k.
 template <int NX, bool WIN, typename WT = float>
 __global__ void __launch_bounds__(256)
@@ -57,6 +70,7 @@ k_sec_r2c(const float* __restrict__ src, long long src_bstride, int NYg, int NXg
     const bool active = item < nitems;
     const int2 kq = active ? items[item] : make_int2(0, 0);
     const SecGeom g = geo[kq.x];
+    const bool narrow = NX <= NXg;
     const int ia = 2 * kq.y, ib = ia + 1;
     const bool va = active && ia < g.in_rows, vb = active && ib < g.in_rows;
     const int ra = g.in_lo_r + ia, rb = g.in_lo_r + ib;   // box row offsets
@@ -70,7 +84,7 @@ k_sec_r2c(const float* __restrict__ src, long long src_bstride, int NYg, int NXg
         const int rc = sec_offset(n, g.in_lo_c, g.in_hi_c, NX);
         float xa = 0.f, xb = 0.f;
         if (rc >= g.in_lo_c && rc <= g.in_hi_c) {
-            const int col = ((g.c0 + rc) % NXg + NXg) % NXg;
+            const int col = sec_col(g.c0, rc, NXg, narrow);
             if (va) xa = __ldg(sa + col);
             if (vb) xb = __ldg(sb + col);
             if (WIN) {
@@ -240,6 +254,7 @@ k_sec_c2r(const float2* __restrict__ src, long long src_bstride, long long src_k
     const bool active = item < nitems;
     const int2 kq = active ? items[item] : make_int2(0, 0);
     const SecGeom g = geo[kq.x];
+    const bool narrow = NX <= NXg;
     const int ia = 2 * kq.y, ib = ia + 1;
     const bool va = active && ia < g.out_rows, vb = active && ib < g.out_rows;
     const float2* base = src + b * src_bstride + kq.x * src_kstride;
@@ -277,7 +292,7 @@ k_sec_c2r(const float2* __restrict__ src, long long src_bstride, long long src_k
         const int n = j + r * T;
         const int rc = sec_offset(n, g.out_lo_c, g.out_hi_c, NX);
         if (rc < g.out_lo_c || rc > g.out_hi_c) continue;
-        const int col = ((g.c0 + rc) % NXg + NXg) % NXg;
+        const int col = sec_col(g.c0, rc, NXg, narrow);
         const float xa = v[r].x * scale * wa[r], xb = v[r].y * scale * wb[r];
         if (va) atomicAdd(ya + col, xa);
         if (vb) atomicAdd(yb + col, xb);
