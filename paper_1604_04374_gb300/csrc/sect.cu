@@ -4,6 +4,9 @@
 
 namespace pce {
 
+// the host sizes the sectioned column grid with cols_columns_per_cta(1024)
+static_assert(ColCfg<1024>::C == kWColWarps, "columns per CTA of the 1024-point column kernels");
+
 #define PCE_SEC_SIZES(X) X(16) X(32) X(64) X(128) X(256) X(512) X(1024) X(2048)
 
 int sec_rows_per_cta(int lc) {
