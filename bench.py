@@ -415,9 +415,13 @@ def gpu_arm(args, pr: synth.Problem, rank: int, world: int) -> None:
     windows = "dense (pce_plan_create)"
     plan = None
     slots = None
-    from paper_1604_04374_gb300.pce import PCE_FLAG_LOWP_STORAGE
+    from paper_1604_04374_gb300.pce import PCE_FLAG_LOWP_STORAGE, PCE_FLAG_SECTIONED
     pflags = PCE_FLAG_LOWP_STORAGE if args.lowp else 0
-    if len(pr.shape) == 2 and "grid" in pr.meta:
+    sectioned_plan = args.plan == "sectioned" and len(pr.shape) == 2
+    if sectioned_plan:
+        plan = Plan(w, h=h, flags=PCE_FLAG_SECTIONED | pflags)
+        windows = "dense, sectioned (PCE_FLAG_SECTIONED: 1024-row sections per column tile of every box)"
+    if plan is None and len(pr.shape) == 2 and "grid" in pr.meta:
         # the node-grid hats are tensor products: give the plan their factors
         wy_np, wx_np = synth.hat_factors_2d(pr.shape[0], pr.shape[1], *pr.meta["grid"])
         if np.array_equal(np.einsum("kr,kc->krc", wy_np, wx_np), pr.w):
@@ -608,8 +612,14 @@ def gpu_arm(args, pr: synth.Problem, rank: int, world: int) -> None:
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
-    ok = bool(torch.equal(y_host[(args.steps - 1) % 2], y_ref.cpu())
-              and torch.equal(x_host[(args.steps - 1) % 2], x_ref.cpu()))
+    ey, ex = y_host[(args.steps - 1) % 2], x_host[(args.steps - 1) % 2]
+    if sectioned_plan:
+        # sections are added with atomics: the last bits vary from run to run
+        e2e_diff = max(float((ey - y_ref.cpu()).norm() / y_ref.cpu().norm()),
+                       float((ex - x_ref.cpu()).norm() / x_ref.cpu().norm()))
+        ok = e2e_diff < 1e-6
+    else:
+        ok = bool(torch.equal(ey, y_ref.cpu()) and torch.equal(ex, x_ref.cpu()))
     for st_ in sets:
         st_[3].close()
 
@@ -627,7 +637,7 @@ def gpu_arm(args, pr: synth.Problem, rank: int, world: int) -> None:
         hbm_src = "measured" if hbm_peak else "fallback"
         hbm_peak = hbm_peak or 6800.0
         chunk = plan_chunk(plan, B)
-        model = work_model(pr, boxes, chunk, slots)
+        model = sectioned_work_model(pr, boxes, chunk) if sectioned_plan else work_model(pr, boxes, chunk, slots)
         kernels, dom = kernel_table(kern, model)
         if sectioned and "kernel_times" in sectioned:
             smodel = sectioned_work_model(pr, sectioned.pop("boxes"), sectioned["chunk"])
@@ -682,7 +692,9 @@ def gpu_arm(args, pr: synth.Problem, rank: int, world: int) -> None:
                     "how": "pinned host u -> device, graph (forward + adjoint), both results -> pinned host, "
                            "every step; two buffer sets on copy-in / compute / copy-out streams, so copies "
                            "overlap the neighbouring steps' compute",
-                    "results_match_device_run": ok},
+                    "results_match_device_run": ok,
+                    "match": ("relative l2 < 1e-6 (atomic adds of the sections)" if sectioned_plan
+                              else "bitwise")},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
             "wall_s": wall,
@@ -1000,6 +1012,8 @@ def main():
                     help="autotune the plan(s) before timing (default)")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--backward", action="store_true", help="also time pce_backward (gradients)")
+    ap.add_argument("--plan", default="auto", choices=["auto", "sectioned"],
+                    help="headline plan: auto (separable for node-grid hats, else dense) or sectioned")
     ap.add_argument("--sectioned", action="store_true",
                     help="also time the same step with a sectioned plan (PCE_FLAG_SECTIONED)")
     ap.add_argument("--lowp", action="store_true",
