@@ -1496,7 +1496,7 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
                                                nx, wst, p->lowp, geo, it_in, n_in, scr.Z, scr.zstride, p->sec_k,
                                                p->sec_twc);
                 });
-            if (e == cudaSuccess)
+            if (e == cudaSuccess && p->nsec > 0)   // no sections (every h_k or w_k zero): y = 0
                 e = timed(p, adjoint ? PCE_KERNEL_COLS_ADJ : PCE_KERNEL_COLS_FWD, s, [&] {
                     return pce::launch_sec_cols(adjoint, dim3(p->nsec, (lch + cpc - 1) / cpc), s, scr.Z, scr.zstride,
                                                 p->sec_k, nb, hst, hsn, p->sec_hscale, p->lowp, geo, lch, scr.A,
@@ -1802,7 +1802,7 @@ int64_t pce_launch_count(pce_plan_t plan, int adjoint, int64_t batch) {
     const int64_t c = own_scratch(plan).chunk;
     const int64_t chunks = (batch + c - 1) / c;
     if (plan->l1) return chunks * 3;
-    if (plan->sect) return chunks * 3;
+    if (plan->sect) return plan->nsec > 0 ? chunks * 3 : 0;
     if (plan->ndims == 1) return 1;
     if (plan->flags & PCE_FLAG_UNFUSED) {
         int64_t mk = 0;

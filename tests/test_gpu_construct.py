@@ -129,6 +129,14 @@ def test_svd_rank_deficient_tvir(torch_cuda):
     assert fro_rel(h[:2].T @ w[:2], rh.T @ rw) < 1e-5
 
 
+def test_svd_of_a_zero_tvir(torch_cuda):
+    """T = 0 has no range: every term comes back as zeros, without an error."""
+    torch = torch_cuda
+    from paper_1604_04374_gb300 import construct_svd_1d
+    h, w, s = construct_svd_1d(torch.zeros((128, 128), device="cuda"), 6)
+    assert float(h.abs().max()) == 0.0 and float(w.abs().max()) == 0.0 and float(s.abs().max()) == 0.0
+
+
 def test_svd_expansion_feeds_a_plan(torch_cuda):
     """Plan(w, h) from the SVD (full-support windows) applies sum_k h_k * (w_k . u); its
     error to the true operator does not grow with m and reaches the float32 level."""

@@ -121,6 +121,25 @@ def test_sectioned_reduced_storage_matches_oracle(torch_cuda, ny, nx, m, batch):
     assert rel(y, host(full.apply(u))) > 1e-6   # the storage really is reduced
 
 
+def test_sectioned_without_sections(torch_cuda):
+    """Every h_k zero, or every w_k zero but one: no section for the dead terms; an
+    operator without any section applies as zero."""
+    torch = torch_cuda
+    from paper_1604_04374_gb300 import Plan, pce
+    pr = synth.problem_2d(256, 64, 16, 2, 460, "normal")
+    u = dev(torch, pr.u)
+    zero = Plan(dev(torch, pr.w), h=dev(torch, np.zeros_like(pr.h)), flags=pce.PCE_FLAG_SECTIONED)
+    assert float(zero.apply(u).abs().max()) == 0.0
+    assert float(zero.apply_adjoint(u).abs().max()) == 0.0
+    assert zero.launch_count(False, 2) == 0
+    w1 = np.zeros_like(pr.w)
+    w1[5] = pr.w[5]
+    h = short_h(pr, 17)
+    one = Plan(dev(torch, w1), h=dev(torch, h), flags=pce.PCE_FLAG_SECTIONED)
+    assert rel(host(one.apply(u)), E.apply(pr.u, w1, h)) < TOL
+    assert rel(host(one.apply_adjoint(u)), E.apply_adjoint(pr.u, w1, h)) < TOL
+
+
 def test_sectioned_restrictions(torch_cuda):
     torch = torch_cuda
     from paper_1604_04374_gb300 import Plan, pce
