@@ -117,7 +117,7 @@ k_sec_r2c(const float* __restrict__ src, long long src_bstride, int NYg, int NXg
 }
 
 // Columns of the sections (LR = 1024).  Grid (sections, ceil(NXh / 4)), 128
-// threads, kWColSmem bytes; each CTA takes one section and four columns and
+// threads, kSecColSmem bytes; each CTA takes one section and four columns and
 // runs all nb right-hand sides through them.  hsT: the section spectra of h_k,
 // [m][NXh][1024] (c = 0: DC column), hsN: [m][1024] (Nyquist); float2, or
 // half2 times hscale[k] (reduced storage).  A warp's spectrum column (8 KB)
