@@ -62,3 +62,25 @@ def test_argument_errors_are_status_codes(lib):
     assert lib.pce_plan_create(ctypes.byref(out), 2, shp, 0, None, None, 0, None) == pce.PCE_ERR_INVALID
     assert lib.pce_plan_create(None, 2, shp, 4, None, None, 0, None) == pce.PCE_ERR_INVALID
     assert lib.pce_launch_count(None, 0, 8) == 0
+
+
+def test_construction_and_flag_errors_without_a_gpu(lib):
+    """Size and flag errors of the constructions and of PCE_FLAG_SECTIONED are status
+    codes returned before any device pointer is looked at."""
+    from paper_1604_04374_gb300 import pce
+    svd = lib.pce_construct_svd_1d
+    for n, m, over, iters in ((8, 4, 10, 2), (1 << 14, 4, 10, 2), (64, 0, 10, 2), (64, 65, 0, 2),
+                              (64, 257, 0, 2), (64, 4, -1, 2), (64, 4, 257, 2), (64, 4, 10, 17)):
+        assert svd(None, n, m, over, iters, 0, None, None, None, None) == pce.PCE_ERR_INVALID, (n, m, over, iters)
+    proj = lib.pce_construct_projection_1d
+    for n, m in ((8, 4), (1 << 19, 4), (64, 2), (64, 65)):
+        assert proj(None, n, m, None, None, None) == pce.PCE_ERR_INVALID, (n, m)
+    out = ctypes.c_void_p()
+    shp1 = (ctypes.c_int64 * 1)(1024)
+    shp2 = (ctypes.c_int64 * 2)(256, 256)
+    sect = pce.PCE_FLAG_SECTIONED
+    assert lib.pce_plan_create(ctypes.byref(out), 1, shp1, 4, None, None, sect, None) == pce.PCE_ERR_UNSUPPORTED
+    for extra in (pce.PCE_FLAG_UNFUSED, pce.PCE_FLAG_PRODUCT_CONVOLUTION):
+        assert (lib.pce_plan_create(ctypes.byref(out), 2, shp2, 4, None, None, sect | extra, None)
+                == pce.PCE_ERR_UNSUPPORTED)
+    assert lib.pce_plan_create(ctypes.byref(out), 2, shp2, 4, None, None, 1 << 7, None) == pce.PCE_ERR_INVALID
