@@ -1004,7 +1004,7 @@ def plan_chunk(plan, batch: int) -> int:
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--workload", default="2d_1024_m16_b8", choices=sorted(synth.WORKLOADS) + [BATCH_WORKLOAD])
     ap.add_argument("--lanes", type=int, default=16, help="streams of the uneven batch")
