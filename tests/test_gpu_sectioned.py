@@ -164,3 +164,24 @@ def test_sectioned_restrictions(torch_cuda):
     with pytest.raises(PceError) as e:
         Plan(w1, h=w1, flags=pce.PCE_FLAG_SECTIONED)
     assert e.value.status == pce.PCE_ERR_UNSUPPORTED
+
+
+def test_sectioned_plan_in_a_batch_and_autotuned(torch_cuda):
+    """A sectioned plan's forward and adjoint as two concurrent tasks of one batch graph
+    (each lane has its own section scratch), and its autotune (one timed candidate)."""
+    torch = torch_cuda
+    from paper_1604_04374_gb300 import Batch, Plan, pce
+    pr = synth.problem_2d(1024, 128, 16, 3, 470, "normal")
+    h = short_h(pr, 19)
+    plan = Plan(dev(torch, pr.w), h=dev(torch, h), flags=pce.PCE_FLAG_SECTIONED)
+    chunk, variant, rvariant, ms = plan.autotune(3)
+    assert ms > 0 and len(plan.tuning_log()) == 1
+    u = dev(torch, pr.u)
+    y, x = torch.empty_like(u), torch.empty_like(u)
+    b = Batch([(plan, u, y, False), (plan, u, x, True)], lanes=2)
+    for _ in range(2):   # a replay starts from the previous run's outputs
+        b.launch()
+        torch.cuda.synchronize()
+        assert rel(host(y), E.apply(pr.u, pr.w, h)) < TOL
+        assert rel(host(x), E.apply_adjoint(pr.u, pr.w, h)) < TOL
+    b.close()
