@@ -185,3 +185,28 @@ def test_sectioned_plan_in_a_batch_and_autotuned(torch_cuda):
         assert rel(host(y), E.apply(pr.u, pr.w, h)) < TOL
         assert rel(host(x), E.apply_adjoint(pr.u, pr.w, h)) < TOL
     b.close()
+
+
+def test_sectioned_sections_wider_than_the_grid(torch_cuda):
+    """A 15-column support on a 16-column grid: the work model takes sections of 32
+    columns, wider than the grid, whose columns wrap by the remainder."""
+    torch = torch_cuda
+    from paper_1604_04374_gb300 import Plan, pce
+    pr = synth.problem_2d(256, 16, 4, 2, 480, "normal")
+    h = short_h(pr, 21, ra=7, rb=7)
+    plan = Plan(dev(torch, pr.w), h=dev(torch, h), flags=pce.PCE_FLAG_SECTIONED)
+    u = dev(torch, pr.u)
+    assert rel(host(plan.apply(u)), E.apply(pr.u, pr.w, h)) < TOL
+    assert rel(host(plan.apply_adjoint(u)), E.apply_adjoint(pr.u, pr.w, h)) < TOL
+
+
+def test_sectioned_wavelet_windows(torch_cuda):
+    """Wavelet windows (Section 4.3): boxes of several widths per plan and windows of
+    both signs, cut into column tiles."""
+    torch = torch_cuda
+    from paper_1604_04374_gb300 import Plan, pce
+    pr = synth.wavelet_problem((256, 128), 2, 2, 2, 490)
+    plan = Plan(dev(torch, pr.w), h=dev(torch, pr.h), flags=pce.PCE_FLAG_SECTIONED)
+    u = dev(torch, pr.u)
+    assert rel(host(plan.apply(u)), E.apply(pr.u, pr.w, pr.h)) < TOL
+    assert rel(host(plan.apply_adjoint(u)), E.apply_adjoint(pr.u, pr.w, pr.h)) < TOL
