@@ -210,3 +210,20 @@ def test_sectioned_wavelet_windows(torch_cuda):
     u = dev(torch, pr.u)
     assert rel(host(plan.apply(u)), E.apply(pr.u, pr.w, pr.h)) < TOL
     assert rel(host(plan.apply_adjoint(u)), E.apply_adjoint(pr.u, pr.w, pr.h)) < TOL
+
+
+def test_sectioned_separable_plan(torch_cuda):
+    """pce_plan_create_separable with PCE_FLAG_SECTIONED: the tensor-product windows are
+    expanded to w_k = wy_k (x) wx_k and applied by sections."""
+    torch = torch_cuda
+    from paper_1604_04374_gb300 import Plan, pce
+    wy, wx = synth.hat_factors_2d(1024, 128, 4, 4)
+    w = np.einsum("kr,kc->krc", wy, wx).astype(np.float32)
+    rng = np.random.default_rng(31)
+    u = rng.standard_normal((2, 1024, 128)).astype(np.float32)
+    pr = synth.Problem("sep", (1024, 128), 16, w, np.zeros_like(w), u)
+    h = short_h(pr, 23)
+    plan = Plan(wy=dev(torch, wy), wx=dev(torch, wx), h=dev(torch, h), flags=pce.PCE_FLAG_SECTIONED)
+    ud = dev(torch, u)
+    assert rel(host(plan.apply(ud)), E.apply(u, w, h)) < TOL
+    assert rel(host(plan.apply_adjoint(ud)), E.apply_adjoint(u, w, h)) < TOL
