@@ -502,9 +502,11 @@ pce_status pce_construct_projection_1d(const float* T, int n, int m, float* h_ou
  * Products with T run on the device with FP64 sums; the factorisations of
  * the n x l iterates (Householder QRs) and the one-sided Jacobi SVD of the
  * l x l triangular factor run on the host in FP64.  Terms beyond the numerical
- * rank of T (sigma_k <= 1e-12 sigma_1) are returned as zeros.  Allocates and
- * frees temporary memory and synchronises `stream`.  PCE_ERR_INVALID for bad
- * sizes or host pointers.
+ * rank of T (sigma_k <= 1e-12 sigma_1) are returned as zeros.  Cost: 2 q + 2
+ * products of T with n x l matrices, n^2 l (2 q + 2) FP64 multiply-adds on the
+ * device (GB300's FP64 rate is low: seconds for n = 4096), plus host QRs of
+ * O(n l^2) each.  Allocates and frees temporary memory and synchronises
+ * `stream`.  PCE_ERR_INVALID for bad sizes or host pointers.
  */
 pce_status pce_construct_svd_1d(const float* T, int n, int m, int oversample, int power_iters,
                                 unsigned long long seed, float* h_out, float* w_out, float* sigma_out,
