@@ -248,3 +248,44 @@ def test_full_uneven_batch_as_benchmarked(torch_cuda):
         assert rel(host(outs[i]).reshape(1, -1)[:, pts[:, 0]], fn(mx.inputs[i], w, h, pts)) < TOL, i
         checked += 1
     b.close()
+
+
+def test_full_mix_with_separable_plans(torch_cuda):
+    """The 256-task mix with its 2D node-grid hats as separable plans (as the benchmark
+    builds them): every task of the batch graph equals the dense plan's single apply to
+    1e-5 (the two forms round differently), and sampled outputs of 2D separable tasks
+    match the oracle."""
+    torch = torch_cuda
+    from paper_1604_04374_gb300 import Batch, Plan
+    mx = synth.batch_mix(256, 4)
+    dense = [Plan(dev(torch, w), h=dev(torch, h)) for _, _, w, h in mx.ops]
+    plans, separable = [], []
+    for (shape, m, w, h), pd in zip(mx.ops, dense):
+        sep = False
+        if len(shape) == 2:
+            wy, wx = synth.hat_factors_2d(shape[0], shape[1], *synth.node_grid(m))
+            sep = bool(np.array_equal(np.einsum("kr,kc->krc", wy, wx), w))
+        plans.append(Plan(wy=dev(torch, wy), wx=dev(torch, wx), h=dev(torch, h)) if sep else pd)
+        separable.append(sep)
+    assert sum(separable) > 0
+    ins = [dev(torch, u) for u in mx.inputs]
+    ref = singles(torch, mx, dense, ins)
+    tasks, outs = tasks_of(torch, mx, plans, ins)
+    b = Batch(tasks, lanes=16)
+    b.launch()
+    torch.cuda.synchronize()
+    for i in range(len(ins)):
+        assert rel(host(outs[i])[None], ref[i][None]) < 1e-5, i
+    rng = np.random.default_rng(3)
+    checked = 0
+    for i in range(len(ins)):
+        o = mx.op_of[i]
+        shape, m, w, h = mx.ops[o]
+        if not separable[o] or checked >= 6:
+            continue
+        pts = np.stack([rng.integers(0, n, 48) for n in shape], axis=-1)
+        fn = E.apply_adjoint_at if mx.adjoint[i] else E.apply_at
+        got = host(outs[i])[0][tuple(pts.T)][None]
+        assert rel(got, fn(mx.inputs[i], w, h, pts)) < TOL, i
+        checked += 1
+    b.close()
