@@ -5,23 +5,33 @@ whole batch of right-hand sides (every kernel of the hot path runs once per
 chunk of the batch).  Metric: applies per second, counting each right-hand
 side of each direction as one apply.
 
-Default workload: 2D periodic 1024 x 1024 float32 images, batch 8, m = 16
+Headline workload: 2D periodic 1024 x 1024 float32 images, batch 8, m = 16
 bilinear hat windows on a 4 x 4 node grid, anisotropic rotated Gaussian PSFs
 (sigma_x = 1.5 + y1, sigma_y = 1.5 + y2 px, theta = pi y1 y2), u ~ U[0,1).
+The default run then measures every other workload of the benchmark set under
+"configs": 1D N = 1024 (m = 8, B = 1); 2D 512^2 (m = 16, B = 16) with the
+gradients; 2D 2048^2 (m = 64, B = 4) whole-grid and sectioned, each with FP32
+and reduced (bf16 w / fp16 hhat) storage; and 256 uneven tasks in one graph.
+Each carries its own clock samples, accuracy against the FP64 oracle,
+roofline and end-to-end figures.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl reference]
 
 Under torchrun (N > 1) every rank runs its own batch (weak scaling: the
 right-hand sides are independent, no data-path collective), the step time is
 the max over ranks and rank 0 prints the JSON line.  ``--impl reference``
-times the FP64 CPU oracle on a bounded sample of the same workload.
+times the compiled FP64 CPU oracle on the host cores: each step is the
+forward and the adjoint apply of one right-hand side of the same workload,
+every output computed.
 """
 from __future__ import annotations
 
 import argparse
+import copy
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -40,60 +50,77 @@ METRIC = "H·u and H*·v applies/sec (fused FP32 path, rel-l2 <= 1e-5 vs FP64 or
 UNIT = "applies/s"
 SM_COUNT_NOMINAL = 152
 FP32_LANES_PER_SM = 128
+HEADLINE = "2d_1024_m16_b8"
+BATCH_WORKLOAD = "batch256_mixed"
+# the other workloads of the default run: (name, workload, option overrides)
+SUB_CONFIGS = (
+    ("1d_n1024_m8_b1", "1d_n1024_m8_b1", {}),
+    ("2d_512_m16_b16", "2d_512_m16_b16", {"backward": True}),
+    ("2d_2048_m64_b4_whole_f32", "2d_2048_m64_b4", {}),
+    ("2d_2048_m64_b4_whole_lowp", "2d_2048_m64_b4", {"lowp": True, "comparator": False}),
+    ("2d_2048_m64_b4_sectioned_f32", "2d_2048_m64_b4", {"plan": "sectioned", "comparator": False}),
+    ("2d_2048_m64_b4_sectioned_lowp", "2d_2048_m64_b4", {"plan": "sectioned", "lowp": True,
+                                                         "comparator": False}),
+    (BATCH_WORKLOAD, BATCH_WORKLOAD, {}),
+)
 
-
-# DRAM bytes (read + write) per launch measured by ncu for the dominant kernels
-# of the 1024 x 1024, m = 16, B = 8 workload with tensor-product windows (one
-# launch = 8 right-hand sides); see profiles/kw_cols_2d_1024_m16_b8.md.  Valid
-# only for that workload and the kernels as captured.
-MEASURED_TRAFFIC = {("2d_1024x1024_m16_b8", "separable", "cols_fwd"): 207.906304e6 + 18.656512e6,
-                    ("2d_1024x1024_m16_b8", "separable", "cols_adj"): 102.050816e6 + 89.044224e6}
+# DRAM bytes (read + write) per launch measured by ncu, keyed by (workload,
+# plan kind, kernel kind, column variant); valid only for the kernels as
+# captured, each entry naming its profile summary.
+MEASURED_TRAFFIC = {
+    ("2d_1024x1024_m16_b8", "separable", "cols_fwd", 0): (207.906304e6 + 18.656512e6,
+                                                          "profiles/kw_cols_2d_1024_m16_b8.md"),
+    ("2d_1024x1024_m16_b8", "separable", "cols_adj", 0): (102.050816e6 + 89.044224e6,
+                                                          "profiles/kw_cols_2d_1024_m16_b8.md"),
+}
 
 # ------------------------------------------------------------- algorithmic work
 
+
 def cyclic_extent(flags) -> tuple[int, int]:
-    """(start, length) of the shortest periodic interval holding every set flag."""
+    """Smallest periodic arc [start, start + n) holding every True entry: (start, n)."""
+    flags = np.asarray(flags, dtype=bool)
     n = len(flags)
-    if not np.any(flags):
+    if not flags.any():
         return 0, 0
-    if np.all(flags):
+    if flags.all():
         return 0, n
-    best = run = 0
-    best_end = 0
-    for t in range(2 * n):
-        if not flags[t % n]:
-            run += 1
-            if run > best and run <= n:
-                best, best_end = run, t
-        else:
-            run = 0
-    return (best_end + 1) % n, n - best
+    idx = np.nonzero(flags)[0]
+    gaps = np.diff(np.concatenate([idx, [idx[0] + n]]))
+    g = int(np.argmax(gaps))
+    start = int(idx[(g + 1) % len(idx)])
+    return start, n - int(gaps[g]) + 1
 
 
 def slot_boxes(wy: np.ndarray, wx: np.ndarray) -> list:
-    """Boxes (r0, nr, c0, nc) of the row-transform slots of a separable plan: one
-    per distinct column factor, rows = union of its terms' row supports."""
+    """Boxes (r0, nr, c0, nc) of the slots of tensor-product windows: one slot per distinct
+    column factor, rows = union of the slot's row supports, columns = the factor's support."""
     slots = {}
     for k in range(wy.shape[0]):
-        slots.setdefault(wx[k].tobytes(), []).append(k)
+        key = wx[k].tobytes()
+        rows = wy[k] != 0
+        slots[key] = (slots[key][0] | rows, wx[k]) if key in slots else (rows, wx[k])
     out = []
-    for key, ks in slots.items():
-        rows = np.any(wy[ks] != 0, axis=0)
+    for rows, f in slots.values():
         r0, nr = cyclic_extent(rows)
-        c0, nc = cyclic_extent(wx[ks[0]] != 0)
+        c0, nc = cyclic_extent(f != 0)
         out.append((r0, nr, c0, nc))
     return out
 
 
 def work_model(pr: synth.Problem, boxes, nb: int, slots=None) -> dict:
-    """Algorithmic flops and bytes per launch of each kernel kind for a chunk of nb right-hand sides.
+    """Per kernel kind, for a chunk of nb right-hand sides: (algorithmic FP32 flops,
+    algorithmic HBM bytes, scratch bytes).
 
     Flops are the nominal FFT counts (5 N log2 N per complex N-point FFT,
     2.5 N log2 N per real one), 8 per complex multiply-add, 1 per window
-    multiply.  Bytes are the compulsory global traffic of the kernel: its
-    inputs read once and its outputs written once.  With `slots` (separable
-    windows) the row passes transform one row set per slot instead of one per
-    term, the column passes multiply by the row factors.
+    multiply.  Algorithmic bytes are what the method must move: u and y once,
+    hhat once, w on its support box once (the row factors once for separable
+    windows).  Scratch bytes are the intermediates Z/Q and A/V, which the
+    design keeps out of the algorithmic count (they would stay on chip or in
+    L2 in an ideal schedule) and which are reported beside it.  With `slots`
+    (separable windows) the row passes transform one row set per slot instead
+    of one per term, the column passes multiply by the row factors.
     """
     if len(pr.shape) == 1:
         n = pr.shape[0]
@@ -101,7 +128,7 @@ def work_model(pr: synth.Problem, boxes, nb: int, slots=None) -> dict:
         fft_r = 2.5 * n * math.log2(n)
         fl = nb * (m * (fft_r + n + 8 * (n // 2 + 1)) + fft_r)
         by = nb * n * 8 + m * (n // 2 + 1) * 8 + m * n * 4
-        return {"fwd_1d": (fl, by), "adj_1d": (fl, by)}
+        return {"fwd_1d": (fl, by, 0.0), "adj_1d": (fl, by, 0.0)}
     ny, nx = pr.shape
     m = pr.m
     nxh = nx // 2
@@ -119,37 +146,36 @@ def work_model(pr: synth.Problem, boxes, nb: int, slots=None) -> dict:
         spx = sum(b[1] * b[3] for b in slots)
         sbytes = nb * srows * nxh * 8
         wcols = sum(b[3] for b in slots) * 4
+        wrows = m * ny * 4
         cfl = nb * ((m + 1) * (nxh + 1) * f_col + m * 8 * ny * (nxh + 1) + rows * (nxh + 1) * 2)
         return {
-            "rows_r2c_window": (nb * (srows * f_row_r2c + spx), ubytes + wcols + sbytes),
-            "cols_fwd": (cfl, sbytes + hbytes + abytes + m * ny * 4),
-            "rows_c2r": (nb * ny * f_row_r2c, abytes + ubytes),
-            "rows_r2c": (nb * ny * f_row_r2c, ubytes + abytes),
-            "cols_adj": (cfl, abytes + hbytes + sbytes + m * ny * 4),
-            "rows_adj": (nb * (srows * f_row_r2c + spx), sbytes + wcols + ubytes),
+            "rows_r2c_window": (nb * (srows * f_row_r2c + spx), ubytes + wcols, sbytes),
+            "cols_fwd": (cfl, hbytes + wrows, sbytes + abytes),
+            "rows_c2r": (nb * ny * f_row_r2c, ubytes, abytes),
+            "rows_r2c": (nb * ny * f_row_r2c, ubytes, abytes),
+            "cols_adj": (cfl, hbytes + wrows, abytes + sbytes),
+            "rows_adj": (nb * (srows * f_row_r2c + spx), wcols + ubytes, sbytes),
         }
     return {
-        "rows_r2c_window": (nb * (rows * f_row_r2c + box_px), ubytes + box_px * 4 + zbytes),
-        "cols_fwd": (nb * ((m + 1) * (nxh + 1) * f_col + m * 8 * ny * (nxh + 1)),
-                     zbytes + hbytes + abytes),
-        "rows_c2r": (nb * ny * f_row_r2c, abytes + ubytes),
-        "rows_r2c": (nb * ny * f_row_r2c, ubytes + abytes),
-        "cols_adj": (nb * ((m + 1) * (nxh + 1) * f_col + m * 8 * ny * (nxh + 1)),
-                     abytes + hbytes + zbytes),
-        "rows_adj": (nb * (rows * f_row_r2c + box_px), zbytes + box_px * 4 + ubytes),
+        "rows_r2c_window": (nb * (rows * f_row_r2c + box_px), ubytes + box_px * 4, zbytes),
+        "cols_fwd": (nb * ((m + 1) * (nxh + 1) * f_col + m * 8 * ny * (nxh + 1)), hbytes, zbytes + abytes),
+        "rows_c2r": (nb * ny * f_row_r2c, ubytes, abytes),
+        "rows_r2c": (nb * ny * f_row_r2c, ubytes, abytes),
+        "cols_adj": (nb * ((m + 1) * (nxh + 1) * f_col + m * 8 * ny * (nxh + 1)), hbytes, abytes + zbytes),
+        "rows_adj": (nb * (rows * f_row_r2c + box_px), box_px * 4 + ubytes, zbytes),
     }
 
 
 def sectioned_work_model(pr: synth.Problem, boxes, nb: int) -> dict:
-    """Algorithmic flops and bytes per launch of the sectioned kernels (PCE_FLAG_SECTIONED)
-    for a chunk of nb right-hand sides, from the support boxes of w_k and the exact
-    support of every h_k, with the plan's choice of sections: each term's box is cut
-    into column tiles of LC - snc + 1 columns (one section each), LC the power of two
-    in 16..2048 of least modelled work.  Per section: forward input window = tile
-    (nr x nct), output window = tile dilated by the support (nr + snr - 1 rows,
-    nct + snc - 1 columns), sections of 1024 x LC points.  Bytes: window inputs read
-    once, section spectra of h read once per launch, intermediates written once and
-    read once, the output window added once."""
+    """Per sectioned kernel kind (PCE_FLAG_SECTIONED) and chunk of nb right-hand sides:
+    (flops, algorithmic bytes, scratch bytes), from the support boxes of w_k and the
+    exact support of every h_k, with the plan's choice of sections: each term's box
+    is cut into column tiles of LC - snc + 1 columns (one section each), LC the power
+    of two in 16..2048 of least modelled work.  Per section: forward input window =
+    tile (nr x nct), output window = tile dilated by the support (nr + snr - 1 rows,
+    nct + snc - 1 columns), sections of 1024 x LC points.  Algorithmic bytes: window
+    inputs and outputs once, section spectra of h once, window box once; scratch:
+    the section intermediates written and read once each."""
     terms = []
     for k, (r0, nr, c0, nc) in enumerate(boxes):
         _, snr = cyclic_extent(np.any(pr.h[k] != 0, axis=1))
@@ -185,14 +211,16 @@ def sectioned_work_model(pr: synth.Problem, boxes, nb: int) -> dict:
     out_px = sum(x[2] * x[3] for x in secs)
     hs = len(terms) * (lch * 1024 + 1024) * 8
     cols = len(secs) * lch
+    zin = nb * in_rows * lch * 8
+    zout = nb * out_rows * lch * 8
     return {
         "lc": lc, "sections": len(secs),
-        "rows_r2c_window": (nb * (in_rows * f_row + in_px), nb * in_px * 4 + in_px * 4 + nb * in_rows * lch * 8),
-        "cols_fwd": (nb * cols * f_col, nb * (in_rows + out_rows) * lch * 8 + hs),
-        "rows_c2r": (nb * out_rows * f_row, nb * out_rows * lch * 8 + nb * out_px * 4),
-        "rows_r2c": (nb * out_rows * f_row, nb * out_px * 4 + nb * out_rows * lch * 8),
-        "cols_adj": (nb * cols * f_col, nb * (in_rows + out_rows) * lch * 8 + hs),
-        "rows_adj": (nb * (in_rows * f_row + in_px), nb * in_rows * lch * 8 + in_px * 4 + nb * in_px * 4),
+        "rows_r2c_window": (nb * (in_rows * f_row + in_px), nb * in_px * 4 + in_px * 4, zin),
+        "cols_fwd": (nb * cols * f_col, hs, zin + zout),
+        "rows_c2r": (nb * out_rows * f_row, nb * out_px * 4, zout),
+        "rows_r2c": (nb * out_rows * f_row, nb * out_px * 4, zout),
+        "cols_adj": (nb * cols * f_col, hs, zin + zout),
+        "rows_adj": (nb * (in_rows * f_row + in_px), in_px * 4 + nb * in_px * 4, zin),
     }
 
 
@@ -206,6 +234,29 @@ def path_bytes(pr: synth.Problem, boxes) -> float:
     ny, nx = pr.shape
     per = 2 * pr.batch * ny * nx * 4 + pr.m * ny * (nx // 2 + 1) * 8 + sum(b[1] * b[3] for b in boxes) * 4
     return 2 * per
+
+
+def task_flops(shape, m, boxes) -> float:
+    """Algorithmic FP32 flops of one apply of one right-hand side (the work model above)."""
+    if len(shape) == 1:
+        n = shape[0]
+        fft_r = 2.5 * n * math.log2(n)
+        return m * (fft_r + n + 8 * (n // 2 + 1)) + fft_r
+    ny, nx = shape
+    rows = sum(b[1] for b in boxes)
+    box_px = sum(b[1] * b[3] for b in boxes)
+    nxh1 = nx // 2 + 1
+    return (rows * 2.5 * nx * math.log2(nx) + box_px + (m + 1) * nxh1 * 5.0 * ny * math.log2(ny)
+            + 8.0 * m * ny * nxh1 + ny * 2.5 * nx * math.log2(nx))
+
+
+def task_bytes(shape, m, boxes) -> float:
+    """Algorithmic HBM bytes of one apply of one right-hand side: in, out, hhat, w on its box."""
+    P = int(np.prod(shape))
+    if len(shape) == 1:
+        return 2 * P * 4 + m * (shape[0] // 2 + 1) * 8 + m * P * 4
+    ny, nx = shape
+    return 2 * P * 4 + m * ny * (nx // 2 + 1) * 8 + sum(b[1] * b[3] for b in boxes) * 4
 
 
 # --------------------------------------------------------------------- clocks
@@ -222,6 +273,7 @@ class ClockSampler:
         self.rows: list[list[str]] = []
         self.stamps: list[float] = []
         self.t_start = 0.0
+        self.t_end = None
         self.proc = None
 
     def __enter__(self):
@@ -251,7 +303,15 @@ class ClockSampler:
         """Start of the timed region: samples before it (idle clocks) are not summarised."""
         self.t_start = time.perf_counter()
 
+    def end(self):
+        """End of the timed region: keep sampling one more period (the reading of the last
+        moments under load arrives after it)."""
+        self.t_end = time.perf_counter()
+        time.sleep(0.15)
+
     def __exit__(self, *exc):
+        if self.t_end is None:
+            self.t_end = time.perf_counter()
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -261,17 +321,17 @@ class ClockSampler:
         return False
 
     def summary(self) -> dict:
-        rows = [r for r, t in zip(self.rows, self.stamps) if t >= self.t_start]
+        hi = (self.t_end or time.perf_counter()) + 0.12
+        rows = [r for r, t in zip(self.rows, self.stamps) if self.t_start <= t <= hi]
         if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        self.rows = rows
-        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
-        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[4 + i] == "Active"})
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i] == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.rows)}
+                "reasons": reasons, "samples": len(rows)}
 
 
 def measured_peaks() -> dict:
@@ -285,93 +345,161 @@ def measured_peaks() -> dict:
     return {}
 
 
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.processor() or platform.machine()
+
+
 # ----------------------------------------------------------------- CPU oracle
 
-def oracle_sample_rate(pr: synth.Problem, target_s: float = 12.0, seed: int = 5) -> dict:
-    """Time the FP64 oracle (gather form) on sampled outputs of right-hand side 0.
+def oracle_threads_wanted() -> int:
+    """The host cores this process may run on (the affinity mask)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
 
-    Returns applies/s extrapolated from the fraction of outputs computed: one
-    forward and one adjoint output per sampled pixel; P sampled outputs of
-    one direction count as one apply.
-    """
-    from oracle import expansion as E
-    P = int(np.prod(pr.shape))
-    rng = np.random.default_rng(seed)
+
+def _oracle():
+    os.environ.setdefault("OMP_NUM_THREADS", str(oracle_threads_wanted()))
+    from oracle import direct
+    return direct
+
+
+def oracle_rhs0(pr: synth.Problem) -> dict:
+    """The compiled FP64 oracle on right-hand side 0, every output of both directions,
+    timed on the host cores.  Returns the outputs, the time and a cpu_baseline record."""
+    C = _oracle()
     u0 = pr.u[:1]
-
-    kept = {}
-
-    def run(count):
-        pts = np.stack([rng.integers(0, n, count) for n in pr.shape], axis=-1)
-        ys, xs = [], []
-        t0 = time.perf_counter()
-        for i in range(0, count, 1024):          # bounded gather arrays
-            ys.append(E.apply_at(u0, pr.w, pr.h, pts[i:i + 1024]))
-            xs.append(E.apply_adjoint_at(u0, pr.w, pr.h, pts[i:i + 1024]))
-        dt = time.perf_counter() - t0
-        kept.update(pts=pts, y=np.concatenate(ys, axis=1)[0], x=np.concatenate(xs, axis=1)[0])
-        return dt
-
-    count = 16
-    dt = run(count)
-    while dt < 0.5 and count < P:
-        count = min(P, count * 4)
-        dt = run(count)
-    total_pts, total_t = 0, 0.0
-    while total_t < target_s and total_pts < P:
-        c = int(min(P, max(count, count * (target_s - total_t) / max(dt, 1e-9) / 2)))
-        t = run(c)
-        total_pts += c
-        total_t += t
-    applies = 2.0 * total_pts / P
-    return {"value": applies / total_t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{total_pts} sampled output pixels x (forward + adjoint) of right-hand side 0 "
-                      f"of {pr.name}, FP64 gather form, {total_t:.1f} s",
-            "seconds": total_t, "points": kept.get("pts"), "oracle_y": kept.get("y"), "oracle_x": kept.get("x")}
+    t0 = time.perf_counter()
+    y = C.apply(u0, pr.w, pr.h)[0]
+    x = C.apply_adjoint(u0, pr.w, pr.h)[0]
+    dt = time.perf_counter() - t0
+    return {"y": y, "x": x, "seconds": dt,
+            "cpu_baseline": {"value": 2.0 / dt, "unit": UNIT, "cores": C.threads(), "kind": "oracle",
+                             "cpu_model": cpu_model(),
+                             "sample": f"forward + adjoint of right-hand side 0 of {pr.name}, every output, "
+                                       f"FP64 direct summation (oracle/direct.c, OpenMP), {dt:.2f} s"}}
 
 
-def reference_arm(args, pr: synth.Problem, rank: int) -> None:
+def oracle_mix_rate(mx, target_s: float = 12.0, seed: int = 5) -> dict:
+    """The compiled FP64 oracle on sampled outputs of every operator of the uneven mix
+    in both directions; the whole mix's CPU time is extrapolated from the seconds
+    per output of each (operator, direction)."""
+    C = _oracle()
+    rng = np.random.default_rng(seed)
+    per_op = max(0.05, target_s / (2 * len(mx.ops)))
+    sec_per_out = {}
+    sampled = 0
+    spent = 0.0
+    for oi, (shape, m, w, h) in enumerate(mx.ops):
+        u0 = mx.inputs[mx.op_of.index(oi)]
+        for adj in (False, True):
+            fn = C.apply_adjoint_at if adj else C.apply_at
+            count, dt = 64, 0.0
+            while True:
+                pts = np.stack([rng.integers(0, n, count) for n in shape], axis=-1)
+                t0 = time.perf_counter()
+                fn(u0, w, h, pts)
+                dt = time.perf_counter() - t0
+                if dt >= per_op or count >= int(np.prod(shape)):
+                    break
+                count = min(int(np.prod(shape)), count * 4)
+            sec_per_out[(oi, adj)] = dt / count
+            sampled += count
+            spent += dt
+    total = sum(int(np.prod(mx.ops[o][0])) * sec_per_out[(o, a)] for o, a in zip(mx.op_of, mx.adjoint))
+    return {"value": len(mx.op_of) / total, "unit": UNIT, "cores": C.threads(), "kind": "oracle",
+            "cpu_model": cpu_model(),
+            "sample": f"{sampled} sampled outputs over the {len(mx.ops)} operators x 2 directions of "
+                      f"{mx.name}, FP64 direct summation (oracle/direct.c, OpenMP), {spent:.1f} s; "
+                      "whole mix extrapolated per task",
+            "seconds": spent}
+
+
+def headline_config(pr: synth.Problem, world: int) -> dict:
+    """The config block of a plan workload, the same for the GPU and the reference arm."""
+    sep = len(pr.shape) == 2 and "grid" in pr.meta
+    return {"workload": pr.name, "shape": list(pr.shape), "m": pr.m, "batch_per_gpu": pr.batch,
+            "global_batch": pr.batch * world, "parallelism": f"replicas x{world}",
+            "windows": ("tensor-product hats on a node grid" if sep else "hats") + f", m = {pr.m}",
+            "l2": "flushed between timed steps (256 MB write, outside the step events)",
+            "step": "forward + adjoint apply of the batch"}
+
+
+def mix_config(mx, world: int) -> dict:
+    return {"workload": mx.name, "tasks": len(mx.op_of), "operators": len(mx.ops),
+            "shapes": [list(s) for s in synth.BATCH_SHAPES], "m": list(synth.BATCH_M), "batch_per_task": 1,
+            "parallelism": f"replicas x{world}",
+            "l2": "flushed between timed steps (256 MB write, outside the step events)",
+            "step": "all tasks (forward or adjoint each)"}
+
+
+def reference_arm(args, workload: str, rank: int, world: int) -> None:
+    """The FP64 oracle (oracle/direct.c) on the host cores.  Plan workloads: every
+    step is the forward and the adjoint apply of one right-hand side, every output
+    computed (2 applies per step).  The uneven mix: every step is a bounded sample
+    over all operators, extrapolated per task."""
     if rank != 0:
         return
-    steps = []
-    for _ in range(args.warmup):
-        oracle_sample_rate(pr, target_s=min(2.0, args.ref_seconds), seed=1)
-    last = None
-    per_step = max(1.0, min(args.ref_seconds, 150.0 / max(1, args.steps)))
-    for s in range(args.steps):
-        last = oracle_sample_rate(pr, target_s=per_step, seed=100 + s)
-        steps.append(last)
-    value = statistics.median([s["value"] for s in steps])
-    ms_per_step = 1000.0 * 2 * pr.batch / value
+    if workload == BATCH_WORKLOAD:
+        mx = synth.batch_mix(256, 4)
+        per_step = max(1.0, min(args.ref_seconds, 150.0 / max(1, args.steps)))
+        for s in range(args.warmup):
+            oracle_mix_rate(mx, target_s=0.5, seed=1 + s)
+        vals, last = [], None
+        for s in range(args.steps):
+            last = oracle_mix_rate(mx, target_s=per_step, seed=100 + s)
+            vals.append(last["value"])
+        value = statistics.median(vals)
+        ms_per_step = 1000.0 * statistics.median([per_step] * args.steps)
+        config = mix_config(mx, world)
+        sample = last["sample"] if last else ""
+        cores = last["cores"] if last else 1
+    else:
+        pr = synth.workload(workload)
+        C = _oracle()
+        u0 = pr.u[:1]
+
+        def step():
+            C.apply(u0, pr.w, pr.h)
+            C.apply_adjoint(u0, pr.w, pr.h)
+
+        for _ in range(args.warmup):
+            step()
+        times = []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            step()
+            times.append(time.perf_counter() - t0)
+        total = sum(times)
+        value = 2.0 * args.steps / total
+        ms_per_step = 1000.0 * total / args.steps
+        config = headline_config(pr, world)
+        cores = C.threads()
+        sample = (f"each step: forward + adjoint of right-hand side 0 of {pr.name}, every output, "
+                  "FP64 direct summation (oracle/direct.c, OpenMP)")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": pr.name},
-        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1,
-                         "sample": last["sample"] if last else ""},
-        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }
-    print(json.dumps(line), flush=True)
-
-
-def reference_mix_arm(args) -> None:
-    """The oracle on the uneven batch: each step a bounded sample over all operators."""
-    mx = synth.batch_mix(256, 4)
-    steps = []
-    last = None
-    per_step = max(1.0, min(args.ref_seconds, 150.0 / max(1, args.steps)))
-    for s in range(args.steps):
-        last = oracle_mix_rate(mx, target_s=per_step, seed=100 + s)
-        steps.append(last["value"])
-    value = statistics.median(steps)
-    line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * len(mx.op_of) / value,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": mx.name},
-        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1,
-                         "sample": last["sample"] if last else ""},
+        "data": "synthetic", "config": config,
+        "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": cores, "cpu_model": cpu_model(),
+                         "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -397,30 +525,140 @@ def weak_scaling_value(batch_per_rank: int, steps: int, world: int, max_ms: floa
 
 # ------------------------------------------------------------------- GPU arm
 
-def gpu_arm(args, pr: synth.Problem, rank: int, world: int) -> None:
-    import torch
-    from paper_1604_04374_gb300 import Plan, build
-    build.build()
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
+class Ctx:
+    """What every measurement shares: the device, the process group, the L2 flush."""
 
+    def __init__(self, rank: int, world: int):
+        import torch
+        from paper_1604_04374_gb300 import build
+        build.build()
+        self.torch = torch
+        self.rank, self.world = rank, world
+        local = int(os.environ.get("LOCAL_RANK", "0"))
+        torch.cuda.set_device(local)
+        self.dev = torch.device("cuda", local)
+        self.dist = None
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("nccl", device_id=self.dev)
+            self.dist = dist
+        # L2 flush buffer (larger than the 129 MB L2), written between timed steps
+        self.flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=self.dev)
+        props = torch.cuda.get_device_properties(self.dev)
+        self.sms = getattr(props, "multi_processor_count", SM_COUNT_NOMINAL)
+        peaks = measured_peaks()
+        self.hbm_peak = peaks.get("hbm_gbs") or 6800.0
+        self.hbm_src = "measured" if peaks.get("hbm_gbs") else "fallback"
+
+    def fp32_peak(self, sm_max_mhz) -> float:
+        """FP32 ALU peak from unit counts and clock: SMs x 128 lanes x 2 (FMA) x max SM clock."""
+        return self.sms * FP32_LANES_PER_SM * 2 * (sm_max_mhz or 2070.0) * 1e6 / 1e12
+
+    def peak_source(self, sm_max_mhz) -> str:
+        return f"derived: {self.sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max_mhz or 2070.0:.0f} MHz"
+
+    def timed(self, fn, steps: int, warmup: int, sample_clocks=False, on_start=None, min_seconds=0.0):
+        """W untimed steps, then K steps each bracketed by CUDA events on the launching
+        stream (L2 flushed before each, outside the events); max over ranks of the sum.
+        min_seconds > 0 raises K until the timed region lasts about that long (the
+        clock samples need a few tenths of a second).  Returns (ms, steps, wall_s, clocks)."""
+        torch = self.torch
+        stream = torch.cuda.current_stream()
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        if min_seconds > 0:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            per = max(e0.elapsed_time(e1), 1e-3) / 1000.0
+            steps = max(steps, min(100000, int(math.ceil(min_seconds / per))))
+        if on_start:
+            on_start()
+        st = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        en = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        if self.dist:
+            self.dist.barrier()
+        torch.cuda.synchronize()
+        smp = ClockSampler(torch.cuda.current_device()) if (sample_clocks and self.rank == 0) else None
+        if smp:
+            smp.__enter__()
+            smp.mark()
+        t0 = time.perf_counter()
+        for i in range(steps):
+            self.flush.zero_()
+            st[i].record(stream)
+            fn()
+            en[i].record(stream)
+        torch.cuda.synchronize()
+        wall_s = time.perf_counter() - t0
+        clocks = None
+        if smp:
+            smp.end()
+            smp.__exit__(None, None, None)
+            clocks = smp.summary()
+        ms = max_over_ranks(sum(a_.elapsed_time(b_) for a_, b_ in zip(st, en)), self.dist, self.dev)
+        return ms, steps, wall_s, clocks
+
+    def close(self):
+        if self.dist:
+            self.dist.destroy_process_group()
+
+
+def kernel_table(kern: dict, model: dict, hbm_peak: float):
+    """Per kernel kind: launches, average time, share of the summed kernel time, the work
+    model's FP32 rate, its HBM rate of algorithmic bytes (and the fraction of the HBM
+    peak), and the scratch bytes per launch; with the kind of the largest share."""
+    kernels = {}
+    for name, (ms, n) in kern.items():
+        fl, by, scr = model.get(name, (0.0, 0.0, 0.0))
+        avg = ms / n
+        gbs = by / (avg / 1000.0) / 1e9 if by else None
+        kernels[name] = {"launches": n, "avg_us": 1000.0 * avg, "share": None,
+                         "tflops": fl / (avg / 1000.0) / 1e12 if fl else None,
+                         "algorithmic_gbs": gbs, "hbm_frac": gbs / hbm_peak if gbs else None,
+                         "scratch_bytes_per_launch": scr}
+    tot = sum(v["avg_us"] * v["launches"] for v in kernels.values()) or 1.0
+    for v in kernels.values():
+        v["share"] = v["avg_us"] * v["launches"] / tot
+    dom = max(kernels, key=lambda k: kernels[k]["share"]) if kernels else None
+    return kernels, dom
+
+
+def plan_chunk(plan, batch: int) -> int:
+    """Right-hand sides per launch: batch / launches-per-direction (2D), batch (1D)."""
+    n = plan.launch_count(False, batch)
+    per = 3 if (len(plan.shape) == 2 or plan.shape[0] > 8192) else 1
+    chunks = max(1, n // per)
+    return math.ceil(batch / chunks)
+
+
+def rel_l2(got: np.ndarray, ref: np.ndarray) -> float:
+    return float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+
+
+def gpu_arm(args, pr: synth.Problem, ctx: Ctx, oracle_cache: dict, headline: bool) -> dict | None:
+    """Measure one plan workload; returns the JSON record on rank 0."""
+    torch = ctx.torch
+    dev = ctx.dev
+    from paper_1604_04374_gb300 import Batch, Plan
+    from paper_1604_04374_gb300.pce import PCE_FLAG_LOWP_STORAGE, PCE_FLAG_SECTIONED, PCE_FLAG_UNFUSED
+    world = ctx.world
     w = torch.from_numpy(pr.w).to(dev)
     h = torch.from_numpy(pr.h).to(dev)
     u = torch.from_numpy(pr.u).to(dev)
     windows = "dense (pce_plan_create)"
     plan = None
     slots = None
-    from paper_1604_04374_gb300.pce import PCE_FLAG_LOWP_STORAGE, PCE_FLAG_SECTIONED
+    kind = "dense"
     pflags = PCE_FLAG_LOWP_STORAGE if args.lowp else 0
     sectioned_plan = args.plan == "sectioned" and len(pr.shape) == 2
     if sectioned_plan:
         plan = Plan(w, h=h, flags=PCE_FLAG_SECTIONED | pflags)
         windows = "dense, sectioned (PCE_FLAG_SECTIONED: 1024-row sections per column tile of every box)"
+        kind = "sectioned"
     if plan is None and len(pr.shape) == 2 and "grid" in pr.meta:
         # the node-grid hats are tensor products: give the plan their factors
         wy_np, wx_np = synth.hat_factors_2d(pr.shape[0], pr.shape[1], *pr.meta["grid"])
@@ -430,136 +668,69 @@ def gpu_arm(args, pr: synth.Problem, rank: int, world: int) -> None:
             windows = f"tensor-product hats (pce_plan_create_separable, {plan.slots()} column-factor slots)"
             if plan.slots():
                 slots = slot_boxes(wy_np, wx_np)
+                kind = "separable"
     if plan is None:
         plan = Plan(w, h=h, flags=pflags)
     tuning = None
-    if args.autotune:
+    if args.col_variant is not None:
+        plan.set_tuning(0, args.col_variant, args.row_variant or 0)
+        tuning = {"forced": True, "column_variant": args.col_variant, "row_variant": args.row_variant or 0}
+    elif args.autotune:
         chunk, variant, rvariant, ms = plan.autotune(pr.batch, args.tuning_cache)
         tuning = {"chunk": chunk, "column_variant": variant, "row_variant": rvariant, "ms_per_apply": ms,
                   "candidates": plan.tuning_log()}
+    col_variant = plan.tuning()[1]
+    nb = plan_chunk(plan, pr.batch)
     m, boxes, scratch = plan.info()
     del w, h
     y = torch.empty_like(u)
     x = torch.empty_like(u)
     B = pr.batch
     P = int(np.prod(pr.shape))
-    # L2 flush buffer (larger than the 129 MB L2), written between timed steps
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream()
+    min_s = 0.0 if headline else 0.3
 
-    from paper_1604_04374_gb300 import Batch
-
-    def timed_steps(fn, sample_clocks=False, on_start=None):
-        """W untimed steps, then K steps each bracketed by CUDA events on the launching
-        stream (L2 flushed before each, outside the events); max over ranks of the sum."""
-        for _ in range(args.warmup):
-            fn()
-        torch.cuda.synchronize()
-        if on_start:
-            on_start()
-        st = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        en = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-        smp = ClockSampler(torch.cuda.current_device()) if (sample_clocks and rank == 0) else None
-        if smp:
-            smp.__enter__()
-            smp.mark()
-        t0 = time.perf_counter()
-        for i in range(args.steps):
-            flush.zero_()
-            st[i].record(stream)
-            fn()
-            en[i].record(stream)
-        torch.cuda.synchronize()
-        wall_s = time.perf_counter() - t0
-        if smp:
-            smp.__exit__(None, None, None)
-        ms = max_over_ranks(sum(a_.elapsed_time(b_) for a_, b_ in zip(st, en)), dist, dev)
-        return ms, wall_s, smp
-
-    # headline step: forward and adjoint of the batch as one CUDA-graph launch of a
+    # the step: forward and adjoint of the batch as one CUDA-graph launch of a
     # two-lane pce_batch (the two directions run concurrently, each on its own scratch)
     pair = Batch([(plan, u, y, False), (plan, u, x, True)], lanes=2)
-    dev_ms, wall, sampler = timed_steps(pair.launch, sample_clocks=True)
+    dev_ms, steps, wall, clocks = ctx.timed(pair.launch, args.steps, args.warmup, sample_clocks=True,
+                                            min_seconds=min_s)
 
     # the same step as two plain calls, with the library's per-kernel events
     def step():
         plan.apply(u, out=y)
         plan.apply_adjoint(u, out=x)
 
-    seq_ms, _, _ = timed_steps(step, on_start=lambda: plan.set_timing(True))
+    seq_ms, seq_steps, _, _ = ctx.timed(step, min(steps, max(args.steps, 20)), args.warmup,
+                                        on_start=lambda: plan.set_timing(True))
     kern = plan.timing()
     plan.set_timing(False)
     y_ref, x_ref = y.clone(), x.clone()
-    if dist:
-        dist.barrier()
     launches_per_step = plan.launch_count(False, B) + plan.launch_count(True, B)
 
     # comparator: the plain unfused FP32 per-term pipeline on the same inputs
     comparator = None
-    if args.comparator:
-        from paper_1604_04374_gb300.pce import PCE_FLAG_UNFUSED
+    if args.comparator and len(pr.shape) == 2:
         plain = Plan(torch.from_numpy(pr.w).to(dev), h=torch.from_numpy(pr.h).to(dev), flags=PCE_FLAG_UNFUSED)
 
         def plain_step():
             plain.apply(u, out=y)
             plain.apply_adjoint(u, out=x)
 
-        cms, _, _ = timed_steps(plain_step)
+        cms, csteps, _, _ = ctx.timed(plain_step, max(3, min(args.steps, 20)), args.warmup)
         comparator = {"impl": "plain unfused FP32 per-term pipeline (PCE_FLAG_UNFUSED), same FFT core",
-                      "value": weak_scaling_value(B, args.steps, world, cms), "unit": UNIT,
-                      "ms_per_step": cms / args.steps,
+                      "value": weak_scaling_value(B, csteps, world, cms), "unit": UNIT,
+                      "ms_per_step": cms / csteps,
                       "launches_per_step": plain.launch_count(False, B) + plain.launch_count(True, B)}
         plain.close()
-
-    # sectioned applies (Lemma 3.2): the same operator on per-term sections, same step
-    sectioned = None
-    if args.sectioned and len(pr.shape) == 2:
-        from paper_1604_04374_gb300.pce import PCE_FLAG_SECTIONED, PceError
-        try:
-            sp = Plan(torch.from_numpy(pr.w).to(dev), h=torch.from_numpy(pr.h).to(dev),
-                      flags=PCE_FLAG_SECTIONED | pflags)
-        except PceError as exc:
-            sectioned = {"unsupported": str(exc)}
-        else:
-            ys, xs = torch.empty_like(u), torch.empty_like(u)
-            spair = Batch([(sp, u, ys, False), (sp, u, xs, True)], lanes=2)
-            sms, _, _ = timed_steps(spair.launch)
-            spair.close()
-
-            def sstep():
-                sp.apply(u, out=ys)
-                sp.apply_adjoint(u, out=xs)
-
-            sseq, _, _ = timed_steps(sstep, on_start=lambda: sp.set_timing(True))
-            skern = sp.timing()
-            sp.set_timing(False)
-
-            def rel_t(a, b):
-                a, b = a.reshape(B, -1).double(), b.reshape(B, -1).double()
-                return float(((a - b).norm(dim=1) / b.norm(dim=1)).max())
-
-            sectioned = {"impl": "PCE_FLAG_SECTIONED: every term on a 1024-row section, overlap-add",
-                         "storage": ("half2 section spectra with per-term scale, bf16 windows" if args.lowp
-                                     else "f32"),
-                         "value": weak_scaling_value(B, args.steps, world, sms), "unit": UNIT,
-                         "ms_per_step": sms / args.steps,
-                         "launches_per_step": sp.launch_count(False, B) + sp.launch_count(True, B),
-                         "max_rel_diff_vs_headline_plan": max(rel_t(ys, y_ref), rel_t(xs, x_ref)),
-                         "sequential_ms_per_step": sseq / args.steps,
-                         "kernel_times": skern, "chunk": plan_chunk(sp, B), "boxes": sp.info()[1]}
-            sp.close()
-            del ys, xs
 
     # gradients (pce_backward: dL/du, dL/dw, dL/dhhat of L = <H_m u, r>) per step
     backward = None
     if args.backward:
         r_t = torch.from_numpy(synth.draw(synth.rng_for(99), pr.u.shape, "normal")).to(dev)
-        bms, _, _ = timed_steps(lambda: plan.backward(u, r_t))
-        backward = {"value": weak_scaling_value(B / 2, args.steps, world, bms), "unit": "right-hand sides/s",
-                    "ms_per_step": bms / args.steps,
+        bms, bsteps, _, bclocks = ctx.timed(lambda: plan.backward(u, r_t), args.steps, args.warmup,
+                                            sample_clocks=True, min_seconds=0.3)
+        backward = {"value": weak_scaling_value(B / 2, bsteps, world, bms), "unit": "right-hand sides/s",
+                    "ms_per_step": bms / bsteps, "steps": bsteps, "clocks": bclocks,
                     "what": "pce_backward: dL/du (adjoint apply), dL/dw and dL/dhhat for the batch"}
 
     # end to end through the public API, pipelined like a serving loop: two buffer
@@ -599,20 +770,23 @@ def gpu_arm(args, pr: synth.Problem, rank: int, world: int) -> None:
             ev["out"][k].record(s_out)
         started[k] = True
 
+    stream = torch.cuda.current_stream()
     for i in range(max(2, args.warmup)):
         e2e_step(i)
     torch.cuda.synchronize()
+    if ctx.dist:
+        ctx.dist.barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     s_in.wait_stream(stream)
-    for i in range(args.steps):
+    for i in range(steps):
         e2e_step(i)
     stream.wait_stream(s_out)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
-    ey, ex = y_host[(args.steps - 1) % 2], x_host[(args.steps - 1) % 2]
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), ctx.dist, dev)
+    ey, ex = y_host[(steps - 1) % 2], x_host[(steps - 1) % 2]
     if sectioned_plan:
         # sections are added with atomics: the last bits vary from run to run
         e2e_diff = max(float((ey - y_ref.cpu()).norm() / y_ref.cpu().norm()),
@@ -622,181 +796,85 @@ def gpu_arm(args, pr: synth.Problem, rank: int, world: int) -> None:
         ok = bool(torch.equal(ey, y_ref.cpu()) and torch.equal(ex, x_ref.cpu()))
     for st_ in sets:
         st_[3].close()
-
-    if rank == 0:
-        value = weak_scaling_value(B, args.steps, world, dev_ms)
-        e2e_value = weak_scaling_value(B, args.steps, world, e2e_ms)
-        clocks = sampler.summary() if sampler else {}
-        sm_max = clocks.get("sm_max_mhz") or 2070.0
-        # FP32 ALU peak from unit counts and clock: SMs x 128 lanes x 2 (FMA) x max SM clock
-        props = torch.cuda.get_device_properties(dev)
-        sms = getattr(props, "multi_processor_count", SM_COUNT_NOMINAL)
-        fp32_peak_tflops = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-        peaks = measured_peaks()
-        hbm_peak = peaks.get("hbm_gbs")
-        hbm_src = "measured" if hbm_peak else "fallback"
-        hbm_peak = hbm_peak or 6800.0
-        chunk = plan_chunk(plan, B)
-        model = sectioned_work_model(pr, boxes, chunk) if sectioned_plan else work_model(pr, boxes, chunk, slots)
-        kernels, dom = kernel_table(kern, model)
-        if sectioned and "kernel_times" in sectioned:
-            smodel = sectioned_work_model(pr, sectioned.pop("boxes"), sectioned["chunk"])
-            sectioned["lc"] = smodel["lc"]
-            sectioned["sections"] = smodel["sections"]
-            sk, sdom = kernel_table(sectioned.pop("kernel_times"), smodel)
-            sectioned["kernels"] = sk
-            if sdom:
-                sectioned["roofline"] = {
-                    "kernel": sdom, "bound": "alu", "achieved": sk[sdom]["tflops"], "peak": fp32_peak_tflops,
-                    "unit": "TFLOP/s", "frac": sk[sdom]["tflops"] / fp32_peak_tflops,
-                    "hbm_gbs": sk[sdom]["gbs"], "hbm_frac_of_" + hbm_src: sk[sdom]["gbs"] / hbm_peak}
-        roof = None
-        if dom:
-            d = kernels[dom]
-            roof = {"kernel": dom, "bound": "alu", "achieved": d["tflops"], "peak": fp32_peak_tflops,
-                    "unit": "TFLOP/s", "frac": d["tflops"] / fp32_peak_tflops,
-                    "peak_source": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",
-                    "traffic": MEASURED_TRAFFIC.get((pr.name, "separable" if slots else "dense", dom))
-                    if (chunk == 8 and not args.lowp) else None,
-                    "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch "
-                                      "(profiles/kw_cols_2d_1024_m16_b8.md)",
-                    "hbm_gbs": d["gbs"], "hbm_frac_of_" + hbm_src: d["gbs"] / hbm_peak}
-        pbytes = path_bytes(pr, boxes)
-        line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "storage": "bf16 windows, fp16 spectra with per-term scale" if args.lowp else "f32",
-            "config": {"workload": pr.name, "shape": list(pr.shape), "m": pr.m, "batch_per_gpu": B,
-                       "windows": windows,
-                       "global_batch": B * world, "parallelism": f"replicas x{world}",
-                       "l2": "flushed between timed steps (256 MB write, outside the step events)",
-                       "step": "forward + adjoint apply of the batch, as one CUDA-graph launch "
-                               "of a two-lane pce_batch"},
-            "roofline": roof,
-            "path_hbm": {"algorithmic_bytes_per_step": pbytes,
-                         "gbs": pbytes * args.steps / (dev_ms / 1000.0) / 1e9,
-                         "peak_gbs": hbm_peak, "peak_source": hbm_src,
-                         "frac": pbytes * args.steps / (dev_ms / 1000.0) / 1e9 / hbm_peak},
-            "kernels": kernels,
-            "comparator": dict(comparator, speedup=value / comparator["value"]) if comparator else None,
-            "sequential": {"value": weak_scaling_value(B, args.steps, world, seq_ms), "unit": UNIT,
-                           "ms_per_step": seq_ms / args.steps,
-                           "how": "pce_apply then pce_apply_adjoint on one stream; the per-kernel "
-                                  "times and the roofline come from this pass"},
-            "tuning": tuning,
-            "backward": backward,
-            "sectioned": sectioned,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": B * P * 4,
-                    "d2h_bytes_per_step": 2 * B * P * 4,
-                    "how": "pinned host u -> device, graph (forward + adjoint), both results -> pinned host, "
-                           "every step; two buffer sets on copy-in / compute / copy-out streams, so copies "
-                           "overlap the neighbouring steps' compute",
-                    "results_match_device_run": ok,
-                    "match": ("relative l2 < 1e-6 (atomic adds of the sections)" if sectioned_plan
-                              else "bitwise")},
-            "gpu_launches": launches_per_step * args.steps,
-            "clocks": clocks,
-            "wall_s": wall,
-            "scratch_bytes": scratch,
-        }
-        if args.cpu_baseline and world >= 1:
-            cb = oracle_sample_rate(pr, args.ref_seconds)
-            line["cpu_baseline"] = {k: v for k, v in cb.items()
-                                    if k not in ("seconds", "points", "oracle_y", "oracle_x")}
-            # the same oracle outputs give the accuracy of this run (right-hand side 0)
-            if cb.get("points") is not None:
-                pts = cb["points"]
-                flat = np.ravel_multi_index(tuple(pts.T), pr.shape)
-                gy = y_ref[0].reshape(-1)[torch.from_numpy(flat).to(dev)].double().cpu().numpy()
-                gx = x_ref[0].reshape(-1)[torch.from_numpy(flat).to(dev)].double().cpu().numpy()
-                line["accuracy"] = {
-                    "rel_l2_forward": float(np.linalg.norm(gy - cb["oracle_y"]) / np.linalg.norm(cb["oracle_y"])),
-                    "rel_l2_adjoint": float(np.linalg.norm(gx - cb["oracle_x"]) / np.linalg.norm(cb["oracle_x"])),
-                    "points": int(len(flat)), "bar": 3e-3 if args.lowp else 1e-5,
-                    "against": "FP64 oracle (gather form) at the cpu_baseline leg's sampled outputs, "
-                               "right-hand side 0"}
-        print(json.dumps(line), flush=True)
     plan.close()
-    if dist:
-        dist.destroy_process_group()
+    if ctx.rank != 0:
+        return None
+
+    value = weak_scaling_value(B, steps, world, dev_ms)
+    e2e_value = weak_scaling_value(B, steps, world, e2e_ms)
+    clocks = clocks or {}
+    sm_max = clocks.get("sm_max_mhz") or 2070.0
+    fp32_peak = ctx.fp32_peak(sm_max)
+    model = sectioned_work_model(pr, boxes, nb) if sectioned_plan else work_model(pr, boxes, nb, slots)
+    kernels, dom = kernel_table(kern, model, ctx.hbm_peak)
+    roof = None
+    if dom:
+        d = kernels[dom]
+        traffic = MEASURED_TRAFFIC.get((pr.name, kind, dom, col_variant)) if (nb == 8 and not args.lowp) else None
+        roof = {"kernel": dom, "bound": "alu", "achieved": d["tflops"], "peak": fp32_peak,
+                "unit": "TFLOP/s", "frac": d["tflops"] / fp32_peak if d["tflops"] else None,
+                "peak_source": ctx.peak_source(sm_max),
+                "traffic": traffic[0] if traffic else None,
+                "algorithmic_bytes_per_launch": model[dom][1],
+                "scratch_bytes_per_launch": model[dom][2],
+                "hbm_gbs": d["algorithmic_gbs"], "hbm_peak_gbs": ctx.hbm_peak, "hbm_peak_source": ctx.hbm_src,
+                "hbm_frac": d["hbm_frac"]}
+        if traffic:
+            roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch "
+                                      f"({traffic[1]})")
+    pbytes = path_bytes(pr, boxes)
+    rec = {
+        "value": value, "unit": UNIT, "steps": steps, "ms_per_step": dev_ms / steps,
+        "storage": "bf16 windows, fp16 spectra with per-term scale" if args.lowp else "f32",
+        "plan": {"kind": kind, "windows": windows, "column_variant": col_variant, "right_hand_sides_per_launch": nb,
+                 "boxes": len(boxes), "scratch_bytes": scratch},
+        "roofline": roof,
+        "path_hbm": {"algorithmic_bytes_per_step": pbytes,
+                     "gbs": pbytes * steps / (dev_ms / 1000.0) / 1e9,
+                     "peak_gbs": ctx.hbm_peak, "peak_source": ctx.hbm_src,
+                     "frac": pbytes * steps / (dev_ms / 1000.0) / 1e9 / ctx.hbm_peak},
+        "kernels": kernels,
+        "comparator": dict(comparator, speedup=value / comparator["value"]) if comparator else None,
+        "sequential": {"value": weak_scaling_value(B, seq_steps, world, seq_ms), "unit": UNIT,
+                       "ms_per_step": seq_ms / seq_steps,
+                       "how": "pce_apply then pce_apply_adjoint on one stream; the per-kernel "
+                              "times and the roofline come from this pass"},
+        "tuning": tuning,
+        "backward": backward,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": B * P * 4,
+                "d2h_bytes_per_step": 2 * B * P * 4,
+                "how": "pinned host u -> device, graph (forward + adjoint), both results -> pinned host, "
+                       "every step; two buffer sets on copy-in / compute / copy-out streams, so copies "
+                       "overlap the neighbouring steps' compute",
+                "results_match_device_run": ok,
+                "match": ("relative l2 < 1e-6 (atomic adds of the sections)" if sectioned_plan
+                          else "bitwise")},
+        "gpu_launches": launches_per_step * steps,
+        "clocks": clocks,
+        "wall_s": wall,
+    }
+    if args.cpu_baseline:
+        if pr.name not in oracle_cache:
+            oracle_cache[pr.name] = oracle_rhs0(pr)
+        orc = oracle_cache[pr.name]
+        rec["cpu_baseline"] = orc["cpu_baseline"]
+        gy = y_ref[0].double().cpu().numpy()
+        gx = x_ref[0].double().cpu().numpy()
+        rec["accuracy"] = {"rel_l2_forward": rel_l2(gy, orc["y"]), "rel_l2_adjoint": rel_l2(gx, orc["x"]),
+                           "outputs": int(P), "bar": 3e-3 if args.lowp else 1e-5,
+                           "against": "FP64 oracle (oracle/direct.c), every output of right-hand side 0"}
+    return rec
 
 
-# ------------------------------------------------------------ uneven batches
-
-BATCH_WORKLOAD = "batch256_mixed"
-
-
-def task_flops(shape, m, boxes) -> float:
-    """Algorithmic FP32 flops of one apply of one right-hand side (the work model above)."""
-    if len(shape) == 1:
-        n = shape[0]
-        fft_r = 2.5 * n * math.log2(n)
-        return m * (fft_r + n + 8 * (n // 2 + 1)) + fft_r
-    ny, nx = shape
-    rows = sum(b[1] for b in boxes)
-    box_px = sum(b[1] * b[3] for b in boxes)
-    nxh1 = nx // 2 + 1
-    return (rows * 2.5 * nx * math.log2(nx) + box_px + (m + 1) * nxh1 * 5.0 * ny * math.log2(ny)
-            + 8.0 * m * ny * nxh1 + ny * 2.5 * nx * math.log2(nx))
-
-
-def task_bytes(shape, m, boxes) -> float:
-    """Algorithmic HBM bytes of one apply of one right-hand side: in, out, hhat, w on its box."""
-    P = int(np.prod(shape))
-    if len(shape) == 1:
-        return 2 * P * 4 + m * (shape[0] // 2 + 1) * 8 + m * P * 4
-    ny, nx = shape
-    return 2 * P * 4 + m * ny * (nx // 2 + 1) * 8 + sum(b[1] * b[3] for b in boxes) * 4
-
-
-def oracle_mix_rate(mx, target_s: float = 12.0, seed: int = 5) -> dict:
-    """FP64 oracle (gather form) timed on sampled outputs of every operator of the mix
-    in both directions; the whole mix's CPU time is extrapolated from the seconds
-    per output of each (operator, direction)."""
-    from oracle import expansion as E
-    rng = np.random.default_rng(seed)
-    per_op = max(0.05, target_s / (2 * len(mx.ops)))
-    sec_per_out = {}
-    sampled = 0
-    spent = 0.0
-    for oi, (shape, m, w, h) in enumerate(mx.ops):
-        u0 = mx.inputs[mx.op_of.index(oi)]
-        for adj in (False, True):
-            fn = E.apply_adjoint_at if adj else E.apply_at
-            count, dt = 8, 0.0
-            while True:
-                pts = np.stack([rng.integers(0, n, count) for n in shape], axis=-1)
-                t0 = time.perf_counter()
-                fn(u0, w, h, pts)
-                dt = time.perf_counter() - t0
-                if dt >= per_op or count >= int(np.prod(shape)):
-                    break
-                count = min(int(np.prod(shape)), count * 4)
-            sec_per_out[(oi, adj)] = dt / count
-            sampled += count
-            spent += dt
-    total = sum(int(np.prod(mx.ops[o][0])) * sec_per_out[(o, a)] for o, a in zip(mx.op_of, mx.adjoint))
-    return {"value": len(mx.op_of) / total, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{sampled} sampled outputs over the {len(mx.ops)} operators x 2 directions of "
-                      f"{mx.name}, FP64 gather form, {spent:.1f} s; whole mix extrapolated per task",
-            "seconds": spent}
-
-
-def batch_arm(args, rank: int, world: int) -> None:
+def batch_arm(args, ctx: Ctx) -> dict | None:
     """256 uneven tasks (1D 4096/16384/65536, 2D 256^2/512^2/1024^2; m in 4..32;
     forward or adjoint) per step: one CUDA-graph launch of a lane-scheduled batch."""
-    import torch
-    from paper_1604_04374_gb300 import Batch, Plan, build
-    build.build()
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
+    torch = ctx.torch
+    dev = ctx.dev
+    world = ctx.world
+    from paper_1604_04374_gb300 import Batch, Plan
     mx = synth.batch_mix(256, 4)
+
     def make_plan(shape, m, w, h):
         """Node-grid hats are tensor products: a separable plan when the factors
         reproduce w exactly (the row transforms are shared per column factor)."""
@@ -826,51 +904,31 @@ def batch_arm(args, rank: int, world: int) -> None:
                         "policy_meaning": "-1: every plan's own variant; 0/1: that variant for all tasks"}
     lanes, scratch, launches, makespan, _ = batch.info()
     n_tasks = len(tasks)
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream()
     boxes = [p.info()[1] for p in plans]
     flops = sum(task_flops(mx.ops[o][0], mx.ops[o][1], boxes[o]) for o in mx.op_of)
     nbytes = sum(task_bytes(mx.ops[o][0], mx.ops[o][1], boxes[o]) for o in mx.op_of)
 
-    def timed(fn, steps):
-        for _ in range(args.warmup):
-            fn()
-        torch.cuda.synchronize()
-        st = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-        en = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-        for i in range(steps):
-            flush.zero_()
-            st[i].record(stream)
-            fn()
-            en[i].record(stream)
-        torch.cuda.synchronize()
-        return max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(st, en)), dist, dev)
-
-    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
-    if sampler:
-        sampler.__enter__()
-        sampler.mark()
-    graph_ms = timed(batch.launch, args.steps)
-    if sampler:
-        sampler.__exit__(None, None, None)
-    eager_ms = timed(batch.run, args.steps)
+    graph_ms, steps, wall, clocks = ctx.timed(batch.launch, args.steps, args.warmup, sample_clocks=True,
+                                              min_seconds=0.3)
+    eager_ms, esteps, _, _ = ctx.timed(batch.run, max(3, min(args.steps, 20)), args.warmup)
 
     def sequential():
-        for p, x, y, adj in tasks:
+        for p, x_, y_, adj in tasks:
             if adj:
-                p.apply_adjoint(x, out=y)
+                p.apply_adjoint(x_, out=y_)
             else:
-                p.apply(x, out=y)
+                p.apply(x_, out=y_)
 
-    seq_ms = timed(sequential, args.steps) if args.comparator else None
+    seq_ms, qsteps = (None, 0)
+    if args.comparator:
+        seq_ms, qsteps, _, _ = ctx.timed(sequential, max(3, min(args.steps, 20)), args.warmup)
 
     # end to end: every task's input from pinned host memory, the graph, every output
     # back, pipelined like a serving loop: two buffer sets, each bound to its own batch;
     # step i copies its inputs in (copy-in stream), runs its graph (compute stream) and
     # copies its outputs back (copy-out stream), overlapping steps i-1 and i+1
+    batch.launch()
+    torch.cuda.synchronize()
     ref_outs = [o.clone() for o in outs]
     hin = [torch.from_numpy(u).pin_memory() for u in mx.inputs]
     hout = [[torch.empty_like(x).pin_memory() for x in hin] for _ in range(2)]
@@ -908,12 +966,13 @@ def batch_arm(args, rank: int, world: int) -> None:
             ev["out"][k].record(s_out)
         started[k] = True
 
-    e2e_steps = max(10, args.steps // 4)
+    stream = torch.cuda.current_stream()
+    e2e_steps = max(10, min(steps, 200))
     for i in range(max(2, args.warmup)):
         e2e_step(i)
     torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
+    if ctx.dist:
+        ctx.dist.barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -923,96 +982,90 @@ def batch_arm(args, rank: int, world: int) -> None:
     stream.wait_stream(s_out)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), ctx.dist, dev)
     last = hout[(e2e_steps - 1) % 2]
     e2e_ok = all(torch.equal(a, b.cpu()) for a, b in zip(last, ref_outs))
     batch2.close()
-    if rank == 0:
-        clocks = sampler.summary() if sampler else {}
-        sm_max = clocks.get("sm_max_mhz") or 2070.0
-        props = torch.cuda.get_device_properties(dev)
-        sms = getattr(props, "multi_processor_count", SM_COUNT_NOMINAL)
-        fp32_peak = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-        peaks = measured_peaks()
-        hbm_peak = peaks.get("hbm_gbs")
-        hbm_src = "measured" if hbm_peak else "fallback"
-        hbm_peak = hbm_peak or 6800.0
-        step_s = graph_ms / args.steps / 1000.0
-        achieved = flops / step_s / 1e12
-        io_bytes = sum(x.numel() * 4 for x in hin)
-        line = {
-            "metric": METRIC, "value": weak_scaling_value(n_tasks / 2, args.steps, world, graph_ms),
-            "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": graph_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": mx.name, "tasks": n_tasks, "operators": len(mx.ops),
-                       "shapes": [list(s) for s in synth.BATCH_SHAPES], "m": list(synth.BATCH_M),
-                       "batch_per_task": 1, "lanes": lanes, "plans_autotuned": bool(args.tune_plans),
-                       "windows": f"{n_separable} of {len(plans)} operators as separable plans "
-                                  "(pce_plan_create_separable: 2D node-grid hats), the rest dense",
-                       "parallelism": f"replicas x{world}",
-                       "l2": "flushed between timed steps (256 MB write, outside the step events)",
-                       "step": "all tasks (forward or adjoint each) as one CUDA-graph launch"},
-            "roofline": {"kernel": "whole batch", "bound": "alu", "achieved": achieved, "peak": fp32_peak,
-                         "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                         "peak_source": f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",
-                         "traffic": None},
-            "path_hbm": {"algorithmic_bytes_per_step": nbytes, "gbs": nbytes / step_s / 1e9,
-                         "peak_gbs": hbm_peak, "peak_source": hbm_src,
-                         "frac": nbytes / step_s / 1e9 / hbm_peak},
-            "eager_lanes": {"value": weak_scaling_value(n_tasks / 2, args.steps, world, eager_ms),
-                            "ms_per_step": eager_ms / args.steps},
-            "comparator": ({"impl": "the same tasks issued one by one (pce_apply / pce_apply_adjoint) "
-                                    "on one stream, no lanes, no graph",
-                            "value": weak_scaling_value(n_tasks / 2, args.steps, world, seq_ms),
-                            "unit": UNIT, "ms_per_step": seq_ms / args.steps,
-                            "speedup": seq_ms / graph_ms} if seq_ms else None),
-            "e2e": {"value": weak_scaling_value(n_tasks / 2, e2e_steps, world, e2e_ms), "unit": UNIT,
-                    "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes,
-                    "how": "pinned host inputs -> device, graph, every output -> pinned host, every step; "
-                           "two buffer sets on copy-in / compute / copy-out streams",
-                    "results_match_device_run": e2e_ok},
-            "gpu_launches": launches * args.steps,
-            "clocks": clocks,
-            "scratch_bytes": scratch,
-            "model_makespan_ms": makespan,
-            "tuning": tuned or None,
-            "batch_tuning": batch_tuning,
-        }
-        if args.cpu_baseline:
-            line["cpu_baseline"] = {k: v for k, v in oracle_mix_rate(mx, args.ref_seconds).items()
-                                    if k != "seconds"}
-        print(json.dumps(line), flush=True)
+    # accuracy: every output of a few tasks of each kind against the oracle
+    acc = None
+    if args.cpu_baseline and ctx.rank == 0:
+        C = _oracle()
+        worst = {}
+        seen = set()
+        for i in range(n_tasks):
+            o = mx.op_of[i]
+            key = (mx.ops[o][0], mx.adjoint[i])
+            if key in seen or int(np.prod(mx.ops[o][0])) > 512 * 512:
+                continue
+            seen.add(key)
+            shape, m_, w_, h_ = mx.ops[o]
+            fn = C.apply_adjoint if mx.adjoint[i] else C.apply
+            ref = fn(mx.inputs[i], w_, h_)
+            got = ref_outs[i].double().cpu().numpy()
+            name = "x".join(str(s) for s in shape) + (" adjoint" if mx.adjoint[i] else " forward")
+            worst[name] = rel_l2(got, ref)
+        acc = {"rel_l2_max": max(worst.values()) if worst else None, "per_kind": worst, "bar": 1e-5,
+               "against": "FP64 oracle (oracle/direct.c), every output of the first task of each "
+                          "(shape, direction) up to 512 x 512"}
     batch.close()
     for p in plans:
         p.close()
-    if dist:
-        dist.destroy_process_group()
+    if ctx.rank != 0:
+        return None
+    clocks = clocks or {}
+    sm_max = clocks.get("sm_max_mhz") or 2070.0
+    fp32_peak = ctx.fp32_peak(sm_max)
+    step_s = graph_ms / steps / 1000.0
+    achieved = flops / step_s / 1e12
+    io_bytes = sum(x.numel() * 4 for x in hin)
+    rec = {
+        "value": weak_scaling_value(n_tasks / 2, steps, world, graph_ms),
+        "unit": UNIT, "steps": steps, "ms_per_step": graph_ms / steps,
+        "config": dict(mix_config(mx, world), lanes=lanes, plans_autotuned=bool(args.tune_plans),
+                       windows=f"{n_separable} of {len(plans)} operators as separable plans "
+                               "(pce_plan_create_separable: 2D node-grid hats), the rest dense",
+                       step="all tasks (forward or adjoint each) as one CUDA-graph launch"),
+        "roofline": {"kernel": "whole batch", "bound": "alu", "achieved": achieved, "peak": fp32_peak,
+                     "unit": "TFLOP/s", "frac": achieved / fp32_peak, "peak_source": ctx.peak_source(sm_max),
+                     "traffic": None},
+        "path_hbm": {"algorithmic_bytes_per_step": nbytes, "gbs": nbytes / step_s / 1e9,
+                     "peak_gbs": ctx.hbm_peak, "peak_source": ctx.hbm_src,
+                     "frac": nbytes / step_s / 1e9 / ctx.hbm_peak},
+        "eager_lanes": {"value": weak_scaling_value(n_tasks / 2, esteps, world, eager_ms),
+                        "ms_per_step": eager_ms / esteps},
+        "comparator": ({"impl": "the same tasks issued one by one (pce_apply / pce_apply_adjoint) "
+                                "on one stream, no lanes, no graph",
+                        "value": weak_scaling_value(n_tasks / 2, qsteps, world, seq_ms),
+                        "unit": UNIT, "ms_per_step": seq_ms / qsteps,
+                        "speedup": (seq_ms / qsteps) / (graph_ms / steps)} if seq_ms else None),
+        "e2e": {"value": weak_scaling_value(n_tasks / 2, e2e_steps, world, e2e_ms), "unit": UNIT,
+                "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes,
+                "how": "pinned host inputs -> device, graph, every output -> pinned host, every step; "
+                       "two buffer sets on copy-in / compute / copy-out streams",
+                "results_match_device_run": e2e_ok},
+        "gpu_launches": launches * steps,
+        "clocks": clocks,
+        "wall_s": wall,
+        "scratch_bytes": scratch,
+        "model_makespan_ms": makespan,
+        "tuning": tuned or None,
+        "batch_tuning": batch_tuning,
+        "accuracy": acc,
+    }
+    if args.cpu_baseline:
+        rec["cpu_baseline"] = {k: v for k, v in oracle_mix_rate(mx, args.ref_seconds).items() if k != "seconds"}
+    return rec
 
 
-def kernel_table(kern: dict, model: dict):
-    """Per kernel kind: launches, average time, share of the summed kernel time, and the
-    work model's FP32 rate and HBM rate; with the kind of the largest share."""
-    kernels = {}
-    for name, (ms, n) in kern.items():
-        fl, by = model.get(name, (0.0, 0.0))
-        avg = ms / n
-        kernels[name] = {"launches": n, "avg_us": 1000.0 * avg, "share": None,
-                         "tflops": fl / (avg / 1000.0) / 1e12 if fl else None,
-                         "gbs": by / (avg / 1000.0) / 1e9 if by else None}
-    tot = sum(v["avg_us"] * v["launches"] for v in kernels.values()) or 1.0
-    for v in kernels.values():
-        v["share"] = v["avg_us"] * v["launches"] / tot
-    dom = max(kernels, key=lambda k: kernels[k]["share"]) if kernels else None
-    return kernels, dom
-
-
-def plan_chunk(plan, batch: int) -> int:
-    """Right-hand sides per launch: batch / launches-per-direction (2D), batch (1D)."""
-    n = plan.launch_count(False, batch)
-    per = 3 if (len(plan.shape) == 2 or plan.shape[0] > 8192) else 1
-    chunks = max(1, n // per)
-    return math.ceil(batch / chunks)
+def top_line(args, rec: dict, world: int, config: dict) -> dict:
+    """The contract's JSON line around a measurement record."""
+    line = {"metric": METRIC, "value": rec["value"], "unit": UNIT, "n_gpus": world, "steps": rec["steps"],
+            "warmup": args.warmup, "ms_per_step": rec["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config}
+    for k, v in rec.items():
+        if k not in line and k not in ("config",):
+            line[k] = v
+    return line
 
 
 def main():
@@ -1020,16 +1073,21 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="2d_1024_m16_b8", choices=sorted(synth.WORKLOADS) + [BATCH_WORKLOAD])
+    ap.add_argument("--workload", default=HEADLINE, choices=sorted(synth.WORKLOADS) + [BATCH_WORKLOAD])
+    ap.add_argument("--headline-only", action="store_true",
+                    help="measure only the chosen workload (no sub-configs)")
+    ap.add_argument("--configs", default=None,
+                    help="comma-separated names of the sub-configs to measure (default: all)")
     ap.add_argument("--lanes", type=int, default=16, help="streams of the uneven batch")
     ap.add_argument("--autotune", dest="autotune", action="store_true", default=True,
                     help="autotune the plan(s) before timing (default)")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false")
+    ap.add_argument("--col-variant", type=int, default=None,
+                    help="force the column variant of the plan (0, 1, 2) instead of autotuning")
+    ap.add_argument("--row-variant", type=int, default=None, help="with --col-variant: the row variant")
     ap.add_argument("--backward", action="store_true", help="also time pce_backward (gradients)")
     ap.add_argument("--plan", default="auto", choices=["auto", "sectioned"],
-                    help="headline plan: auto (separable for node-grid hats, else dense) or sectioned")
-    ap.add_argument("--sectioned", action="store_true",
-                    help="also time the same step with a sectioned plan (PCE_FLAG_SECTIONED)")
+                    help="plan: auto (separable for node-grid hats, else dense) or sectioned")
     ap.add_argument("--lowp", action="store_true",
                     help="reduced storage (PCE_FLAG_LOWP_STORAGE: bf16 windows, fp16 spectra)")
     ap.add_argument("--tuning-cache", default=None,
@@ -1045,18 +1103,44 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.warmup < 3:
         args.warmup = 3
-    if args.workload == BATCH_WORKLOAD:
-        if args.impl == "reference":
-            if rank == 0:
-                reference_mix_arm(args)
-            return
-        batch_arm(args, rank, world)
-        return
-    pr = synth.workload(args.workload)
     if args.impl == "reference":
-        reference_arm(args, pr, rank)
+        reference_arm(args, args.workload, rank, world)
         return
-    gpu_arm(args, pr, rank, world)
+    ctx = Ctx(rank, world)
+    oracle_cache: dict = {}
+    if args.workload == BATCH_WORKLOAD:
+        rec = batch_arm(args, ctx)
+        config = rec["config"] if rec else None
+    else:
+        pr = synth.workload(args.workload)
+        rec = gpu_arm(args, pr, ctx, oracle_cache, headline=True)
+        config = headline_config(pr, world)
+        del pr
+    line = top_line(args, rec, world, config) if rec else None
+    if not args.headline_only and args.workload == HEADLINE:
+        wanted = set(args.configs.split(",")) if args.configs else None
+        subs = {}
+        for name, wl, over in SUB_CONFIGS:
+            if wanted is not None and name not in wanted:
+                continue
+            sargs = copy.copy(args)
+            for k, v in over.items():
+                setattr(sargs, k, v)
+            if wl == BATCH_WORKLOAD:
+                srec = batch_arm(sargs, ctx)
+            else:
+                spr = synth.workload(wl)
+                srec = gpu_arm(sargs, spr, ctx, oracle_cache, headline=False)
+                if srec is not None:
+                    srec["config"] = headline_config(spr, world)
+                del spr
+            if srec is not None:
+                subs[name] = srec
+        if line is not None:
+            line["configs"] = subs
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    ctx.close()
 
 
 if __name__ == "__main__":

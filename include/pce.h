@@ -329,13 +329,17 @@ pce_status pce_backward(pce_plan_t plan, const float* u, const float* r, float* 
  * required size in pce_last_error_string().  Larger batches are processed in
  * chunks that fit.
  *
- * The first call on a device looks up the device address of the static
- * block (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  Every call on a device shares the same
+ * Every call looks up the device address of the static block on the
+ * current device (cudaGetSymbolAddress, which allocates nothing), so a
+ * device reset between calls is handled.  The first lookup on a device may
+ * load the library's device code there: make the first call on a device
+ * before any stream capture.  Every call on a device shares the same
  * block, which keeps the previous call's contents (nothing needs to start at
  * zero: every element a kernel reads is written earlier in the same call).
  * Calls whose work overlaps on the GPU (other streams, other threads, other
  * plans) race on the block and give wrong results: serialise them.
+ * Separable and sectioned plans run here on their whole-grid structures
+ * (the general kernels), with the same result up to rounding.
  */
 pce_status pce_apply_noalloc(pce_plan_t plan, const float* u, float* y, int64_t batch, void* stream);
 
@@ -428,7 +432,9 @@ pce_status pce_schedule_lpt(const double* cost, int n, int lanes, int* lane_of, 
  * right-hand sides of a fixed pattern, L2 flushed between repetitions, best
  * of three) for every candidate and keep the fastest:
  *   - column FFT variant for Ny = 1024: 0 = one-warp 32 x 32 four-step
- *     (radix 32), 1 = block Stockham (radix 8);
+ *     (radix 32), 1 = block Stockham (radix 8), 2 (separable plans) = the
+ *     one-warp four-step with each warp's held column and accumulator in
+ *     tensor memory (more warps per SM);
  *   - adjoint row-pass variant (2D): 0 = next term's data prefetched into
  *     registers (2 CTAs per SM), 1 = no prefetch (3 CTAs per SM);
  *   - right-hand sides per launch: powers of two up to the plan's scratch
@@ -445,6 +451,14 @@ pce_status pce_schedule_lpt(const double* cost, int n, int lanes, int* lane_of, 
 pce_status pce_plan_autotune(pce_plan_t plan, int64_t batch, const char* cache_path, void* stream);
 pce_status pce_plan_tuning(pce_plan_t plan, int* chunk, int* col_variant, int* row_variant,
                            double* ms_per_apply);
+/* pce_plan_set_tuning -- set the choices pce_plan_autotune would make, by
+ * hand: chunk = right-hand sides per launch (0 = the plan's scratch chunk;
+ * larger values are clamped to it), col_variant and row_variant as above.
+ * A column variant the plan has no kernels for is PCE_ERR_UNSUPPORTED
+ * (1 needs a 2D plan with 1024 or 2048 rows, 2 a separable plan with 1024
+ * rows); a row variant other than 0 needs a 2D plan.  Changes no value an
+ * apply computes beyond rounding order.  Host only, no synchronisation. */
+pce_status pce_plan_set_tuning(pce_plan_t plan, int chunk, int col_variant, int row_variant);
 /* Every candidate the last timed pce_plan_autotune measured: writes up to
  * max_entries (chunk, column variant, row variant, ms per apply) entries into
  * the arrays (any may be NULL) and returns how many there were (0 after a

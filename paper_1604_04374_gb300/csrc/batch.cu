@@ -488,7 +488,7 @@ extern "C" pce_status pce_plan_autotune(pce_plan_t p, int64_t batch, const char*
         if (cache_lookup(cache_path, key, c, v, rv, ms)) {
             p->tune_log.clear();
             p->run_chunk = std::min(c, cmax);
-            p->col_variant = (p->ndims == 2 && (p->ny == 1024 || p->ny == 2048)) ? v : 0;
+            p->col_variant = (p->ndims == 2 && (p->ny == 1024 || p->ny == 2048) && (v != 2 || p->sep)) ? v : 0;
             p->row_variant = (p->ndims == 2) ? rv : 0;
             p->tuned_ms = ms;
             return PCE_OK;
@@ -498,6 +498,7 @@ extern "C" pce_status pce_plan_autotune(pce_plan_t p, int64_t batch, const char*
     // a sectioned plan runs its own kernels and chunks: one candidate, timed
     std::vector<int> variants = {0};
     if (p->ndims == 2 && !p->sect && (p->ny == 1024 || p->ny == 2048)) variants.push_back(1);
+    if (p->sep && !p->sect && p->ny == 1024) variants.push_back(2);
     std::vector<int> rvariants = {0};
     if (p->ndims == 2 && !p->sect) rvariants.push_back(1);
     std::vector<int> chunks;
@@ -588,6 +589,23 @@ extern "C" pce_status pce_plan_autotune(pce_plan_t p, int64_t batch, const char*
     p->row_variant = best_r;
     p->tuned_ms = best;
     if (cache_path) return cache_store(cache_path, key, best_c, best_v, best_r, best);
+    return PCE_OK;
+}
+
+extern "C" pce_status pce_plan_set_tuning(pce_plan_t p, int chunk, int col_variant, int row_variant) {
+    if (!p) return fail(PCE_ERR_INVALID, "plan is NULL");
+    if (chunk < 0) return fail(PCE_ERR_INVALID, "chunk must be >= 0 (got %d)", chunk);
+    if (col_variant < 0 || col_variant > 2 || row_variant < 0 || row_variant > 1)
+        return fail(PCE_ERR_INVALID, "column variant must be 0..2 and row variant 0..1 (got %d, %d)", col_variant,
+                    row_variant);
+    if (col_variant == 1 && !(p->ndims == 2 && (p->ny == 1024 || p->ny == 2048)))
+        return fail(PCE_ERR_UNSUPPORTED, "column variant 1 needs a 2D plan with 1024 or 2048 rows");
+    if (col_variant == 2 && !(p->sep && p->ny == 1024))
+        return fail(PCE_ERR_UNSUPPORTED, "column variant 2 needs a separable plan with 1024 rows");
+    if (row_variant != 0 && p->ndims != 2) return fail(PCE_ERR_UNSUPPORTED, "row variant 1 needs a 2D plan");
+    p->run_chunk = chunk == 0 ? 0 : std::min(chunk, p->bchunk);
+    p->col_variant = col_variant;
+    p->row_variant = row_variant;
     return PCE_OK;
 }
 

@@ -2,6 +2,7 @@
 #include "kernels.cuh"
 #include "wkernels.cuh"
 #include "wkernels2.cuh"
+#include "tkernels.cuh"
 #include "launch.h"
 
 namespace pce {
@@ -35,6 +36,10 @@ int cols_smem(int ny) {
 
 cudaError_t prepare_cols() {
     cudaError_t e = cudaFuncSetAttribute(kw_cols_fwd<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWColSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kt_cols_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, kTColSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kt_cols_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, kTColSmem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(kw2_cols_fwd<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kW2Smem);
     if (e == cudaSuccess)
@@ -242,6 +247,26 @@ cudaError_t launch_cols_adj_sep(dim3 grid, cudaStream_t s, const float2* V, long
     kw_cols_adj<false, float2, true><<<grid, kWColWarps * 32, kWColSmem, s>>>(
         V, v_bstride, hhT, hN, nullptr, m, box, nxh, Q, q_bstride, q_kstride, tw1024, status, wait_limit,
         skip_copy, sep);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cols_fwd_sep_tm(dim3 grid, cudaStream_t s, const float2* Z, long long z_bstride,
+                                   long long z_kstride, const float2* hhT, const float2* hN, const Box* box,
+                                   int nxh, float2* A, long long a_bstride, const float2* tw1024, int* status,
+                                   long long wait_limit, int skip_copy, const SepTerms& sep) {
+    if (!tw1024 || !hhT) return cudaErrorInvalidValue;
+    kt_cols_fwd<<<grid, kWColWarps * 32, kTColSmem, s>>>(Z, z_bstride, z_kstride, hhT, hN, box, nxh, A, a_bstride,
+                                                         tw1024, status, wait_limit, skip_copy, sep);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cols_adj_sep_tm(dim3 grid, cudaStream_t s, const float2* V, long long v_bstride,
+                                   const float2* hhT, const float2* hN, const Box* box, int nxh, float2* Q,
+                                   long long q_bstride, long long q_kstride, const float2* tw1024, int* status,
+                                   long long wait_limit, int skip_copy, const SepTerms& sep) {
+    if (!tw1024 || !hhT) return cudaErrorInvalidValue;
+    kt_cols_adj<<<grid, kWColWarps * 32, kTColSmem, s>>>(V, v_bstride, hhT, hN, box, nxh, Q, q_bstride, q_kstride,
+                                                         tw1024, status, wait_limit, skip_copy, sep);
     return cudaGetLastError();
 }
 

@@ -97,6 +97,16 @@ cudaError_t launch_cols_adj_sep(dim3 grid, cudaStream_t s, const float2* V, long
                                 const float2* tw1024, int* status, long long wait_limit, int skip_copy,
                                 const SepTerms& sep);
 
+// The same with the per-warp state in tensor memory (tkernels.cuh).
+cudaError_t launch_cols_fwd_sep_tm(dim3 grid, cudaStream_t s, const float2* Z, long long z_bstride,
+                                   long long z_kstride, const float2* hhT, const float2* hN, const Box* box,
+                                   int nxh, float2* A, long long a_bstride, const float2* tw1024, int* status,
+                                   long long wait_limit, int skip_copy, const SepTerms& sep);
+cudaError_t launch_cols_adj_sep_tm(dim3 grid, cudaStream_t s, const float2* V, long long v_bstride,
+                                   const float2* hhT, const float2* hN, const Box* box, int nxh, float2* Q,
+                                   long long q_bstride, long long q_kstride, const float2* tw1024, int* status,
+                                   long long wait_limit, int skip_copy, const SepTerms& sep);
+
 cudaError_t launch_cols_adj_full(int ny, dim3 grid, cudaStream_t s, const float2* V, long long v_bstride,
                                  const float2* hh, const float2* hN, int m, const Box* box, int nxh,
                                  float2* Q, long long q_bstride, long long q_kstride,

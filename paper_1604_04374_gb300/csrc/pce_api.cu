@@ -1513,10 +1513,13 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
         if (e) return fail(PCE_ERR_CUDA, "sectioned apply launch: %s", cudaGetErrorString(e));
         return PCE_OK;
     }
-    const bool warp = (scr.col_variant >= 0 ? scr.col_variant : p->col_variant) == 0;
+    const int colv = scr.col_variant >= 0 ? scr.col_variant : p->col_variant;
+    const bool warp = colv != 1;
     const int rowv = scr.row_variant >= 0 ? scr.row_variant : p->row_variant;
-    // separable fast path: one-warp column kernels only
+    // separable fast path: one-warp column kernels only; variant 2 keeps the
+    // per-warp column state in tensor memory
     const bool sepx = p->sep && warp;
+    const bool septm = sepx && colv == 2;
     pce::SepTerms sept;
     sept.wrow = p->wrow;
     sept.kslot = p->d_kslot;
@@ -1541,6 +1544,10 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
                 });
             if (e == cudaSuccess)
                 e = timed(p, PCE_KERNEL_COLS_FWD, s, [&] {
+                    if (septm)
+                        return pce::launch_cols_fwd_sep_tm(dim3(nb, (nxh + cpc - 1) / cpc), s, scr.Z, zb, p->zk_s,
+                                                           p->hhT, p->hN, p->d_vbox, nxh, scr.A, ab, p->tw1024,
+                                                           p->d_status, p->wait_limit, p->skip_copy, sept);
                     return pce::launch_cols_fwd_sep(dim3(nb, (nxh + cpc - 1) / cpc), s, scr.Z, zb, p->zk_s,
                                                     p->hhT, p->hN, m, p->d_vbox, nxh, scr.A, ab, p->tw1024,
                                                     p->d_status, p->wait_limit, p->skip_copy, sept);
@@ -1558,6 +1565,10 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
             });
             if (e == cudaSuccess)
                 e = timed(p, PCE_KERNEL_COLS_ADJ, s, [&] {
+                    if (septm)
+                        return pce::launch_cols_adj_sep_tm(dim3(nb, (nxh + cpc - 1) / cpc), s, scr.A, ab, p->hhT,
+                                                           p->hN, p->d_vbox, nxh, scr.Z, zb, p->zk_s, p->tw1024,
+                                                           p->d_status, p->wait_limit, p->skip_copy, sept);
                     return pce::launch_cols_adj_sep(dim3(nb, (nxh + cpc - 1) / cpc), s, scr.A, ab, p->hhT, p->hN,
                                                     m, p->d_vbox, nxh, scr.Z, zb, p->zk_s, p->tw1024,
                                                     p->d_status, p->wait_limit, p->skip_copy, sept);
@@ -1936,40 +1947,27 @@ extern "C" pce_status pce_backward(pce_plan_t p, const float* u, const float* r,
 // soon as the library is loaded on a device, so the call itself never
 // allocates.  Host code may not pass g_noalloc_scratch to a kernel directly:
 // in host code the name denotes a host-side shadow, not device memory.  Its
-// device address is looked up once per device with cudaGetSymbolAddress.
+// device address comes from cudaGetSymbolAddress on the current device.
 namespace {
 
 constexpr size_t kNoallocScratchBytes = 64ull << 20;   // 64 MiB per device
-constexpr int kNoallocMaxDevices = 64;
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
-struct NoallocSlot {
-    bool ready = false;
-    float2* ptr = nullptr;
-};
-NoallocSlot g_noalloc_slots[kNoallocMaxDevices];
-std::mutex g_noalloc_mutex;
-
-// Device address of the static scratch on the current device (first call per device).
+// Device address of the static scratch on the current device.  Looked up on
+// every call: the lookup allocates nothing and queues no work, and a device
+// reset between calls (which reloads the module, possibly elsewhere) then
+// cannot leave a stale address behind.  The first lookup on a device loads
+// the library's device code there if lazy loading has not done so yet.
 pce_status noalloc_scratch(float2** out) {
     int dev = 0;
     PCE_CK(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kNoallocMaxDevices)
-        return fail(PCE_ERR_UNSUPPORTED, "device %d is beyond the %d devices the static scratch tracks",
-                    dev, kNoallocMaxDevices);
-    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    NoallocSlot& slot = g_noalloc_slots[dev];
-    if (!slot.ready) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess)
-            return fail(PCE_ERR_CUDA, "cudaGetSymbolAddress of the static scratch on device %d: %s", dev,
-                        cudaGetErrorString(e));
-        slot.ptr = static_cast<float2*>(p);
-        slot.ready = true;
-    }
-    *out = slot.ptr;
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess)
+        return fail(PCE_ERR_CUDA, "cudaGetSymbolAddress of the static scratch on device %d: %s", dev,
+                    cudaGetErrorString(e));
+    *out = static_cast<float2*>(p);
     return PCE_OK;
 }
 
@@ -2020,7 +2018,7 @@ extern "C" pce_status pce_apply_noalloc(pce_plan_t plan, const float* u, float* 
             e = pce::launch_cols_fwd(ny, dim3(nb, (nxh + cpc - 1) / cpc), s, scrZ, zb, zk, hstore(plan),
                                      hNstore(plan), plan->hscale, plan->lowp, m, plan->d_box, nxh, scrA, ab,
                                      plan->twy, hTstore(plan), plan->tw1024, plan->d_status, plan->wait_limit,
-                                     plan->skip_copy, plan->col_variant == 0, hN2store(plan), plan->tw2048l);
+                                     plan->skip_copy, plan->col_variant != 1, hN2store(plan), plan->tw2048l);
         if (e == cudaSuccess)
             e = pce::launch_rows_c2r(nx, dim3((npairs + fpc - 1) / fpc, nb), s, scrA, ab, ny, y + b0 * P, P,
                                      scale, plan->twx, plan->tw1024);

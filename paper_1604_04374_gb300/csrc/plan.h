@@ -61,7 +61,8 @@ struct pce_plan {
     int bchunk = 1;             // right-hand sides the plan's scratch holds
     // autotuned choices (pce_plan_autotune): 0 = default
     int run_chunk = 0;          // right-hand sides per launch, <= bchunk
-    int col_variant = 0;        // columns of 1024: 0 one-warp four-step, 1 radix-8 Stockham
+    int col_variant = 0;        // columns of 1024: 0 one-warp four-step, 1 radix-8 Stockham,
+                                // 2 (separable plans) one-warp with the warp state in tensor memory
     int row_variant = 0;        // adjoint row pass: 0 register prefetch, 1 none (3 CTAs per SM)
     double tuned_ms = 0.0;      // measured ms per right-hand side (forward + adjoint) / 2
     std::vector<double> tune_log;   // (chunk, col variant, row variant, ms per apply) per timed candidate

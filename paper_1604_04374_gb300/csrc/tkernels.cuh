@@ -1,0 +1,364 @@
+// tkernels.cuh -- column kernels of separable plans for Ny = 1024 with the
+// per-warp state in tensor memory.
+//
+// They compute exactly what kw_cols_fwd<float2, true> / kw_cols_adj<false,
+// float2, true> (wkernels.cuh) compute, with the same global layouts, and run
+// the same one-warp 1024-point FFT (warpfft.cuh).  What moves is the state a
+// warp carries from term to term:
+//
+//   forward: the slot's column Z_j[:, c] (reused by every term of the slot)
+//            and the spectral accumulator sum_k hhat_k . FFT_y(wy_k . Z_j);
+//   adjoint: the column spectrum FFT_y(V[:, c]) (reused by every term) and
+//            the slot accumulator S_j = sum_k wy_k . IFFT_y(conj(hhat_k) V).
+//
+// In wkernels.cuh the accumulator takes 64 registers per thread beside the
+// 64 of the FFT, and the column lives in a 32 KB shared tile per CTA: 168
+// registers and 72 KB per 4-warp CTA, so 3 CTAs (12 warps) per SM.  Here both
+// live in tensor memory, 64 + 64 columns of the warp's lane quarter
+// (tmem.cuh), and the shared memory holds only the four warps' transpose tiles
+// (which double as the staging tile of the coalesced column loads and stores)
+// and the row factors: 40 KB and 4 CTAs (16 warps) per SM, bounded by the
+// 512 tensor-memory columns of an SM (4 x 128).  The shared-memory request is
+// padded so that a fifth CTA never fits: every resident CTA's allocation is
+// then satisfied at once.
+//
+// Layout of a warp's 128 columns: [0, 64) held column, [64, 128) accumulator;
+// thread l holds, like the registers of the one-warp FFT, the values of rows
+// (or frequencies) l + 32 q at columns 2q, 2q + 1.
+#pragma once
+
+#include "tmem.cuh"
+#include "wkernels.cuh"
+
+namespace pce {
+
+constexpr int kTmCols = 128;
+constexpr int kTmHold = 0;
+constexpr int kTmAcc = 64;
+constexpr int kTColSmemUsed = (kWColWarps * kWarpN) * (int)sizeof(float2) + 2 * kWarpN * (int)sizeof(float);
+// padded: 5 x (47 KB + the 1 KB per-CTA reserve) exceeds the SM's 228 KB, 4 x does not
+constexpr int kTColSmem = 47 * 1024;
+static_assert(kTColSmem >= kTColSmemUsed, "tensor-memory column kernels: shared memory");
+
+// Allocate the CTA's tensor memory (warp 0), publish its base address and
+// return this warp's lane-quarter base.
+__device__ __forceinline__ unsigned tm_begin(unsigned* slot) {
+    const int warp = threadIdx.x >> 5;
+    if (warp == 0) tm_alloc(slot, kTmCols);
+    tm_fence_before();
+    __syncthreads();
+    tm_fence_after();
+    return *slot + ((unsigned)(32 * warp) << 16);
+}
+// Every warp's tcgen05 loads and stores have completed (the loads wait in
+// place; stores are waited by the caller).  Release the allocation (warp 0).
+__device__ __forceinline__ void tm_end(const unsigned* slot) {
+    tm_fence_before();
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0) {
+        tm_fence_after();
+        tm_dealloc(*slot, kTmCols);
+    }
+}
+
+// acc[8 quarter .. 8 quarter + 7] of a 32-value accumulator in tensor memory
+template <typename F>
+__device__ __forceinline__ void tm_update8(unsigned tacc, int quarter, F&& f) {
+    float2 a[8];
+    tm_load8c(tacc + 16 * quarter, a);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = f(8 * quarter + j, a[j]);
+    tm_store8c(tacc + 16 * quarter, a);
+}
+
+// X[(1024 - f) mod 1024] from a warp's transpose tile holding X[f] at f.
+__device__ __forceinline__ float2 tr_partner(const float2* tr, int f) { return tr[(kWarpN - f) & (kWarpN - 1)]; }
+
+// F2 for separable plans, Ny = 1024.  Grid (batch, NXh / 4), 128 threads,
+// kTColSmem bytes.  Arguments as kw_cols_fwd<float2, true>.
+__global__ void __launch_bounds__(kWColWarps * 32, 4)
+kt_cols_fwd(const float2* __restrict__ Z, long long z_bstride, long long z_kstride,
+            const float2* __restrict__ hhT, const float2* __restrict__ hN, const Box* __restrict__ box,
+            int NXh, float2* __restrict__ A, long long a_bstride, const float2* __restrict__ tw,
+            int* __restrict__ status, long long wait_limit, int skip_copy, SepTerms sep) {
+    constexpr int NY = kWarpN;
+    extern __shared__ __align__(16) float2 smem[];
+    float2* tile = smem;                                     // staging tile [1024][4] (swizzled)
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float2* tr = smem + warp * kWarpN;                       // this warp's transpose tile
+    float* wys = reinterpret_cast<float*>(smem + NY * kWColWarps);
+    __shared__ unsigned long long bars[kWColWarps];
+    __shared__ unsigned tm_slot;
+    const int b = blockIdx.x;
+    const int col0 = blockIdx.y * kWColWarps;
+    const int col = col0 + warp;
+    const bool cv = col < NXh;
+    const bool dcn = blockIdx.y == 0 && warp == 0;
+    const float2* Zb = Z + b * z_bstride;
+    unsigned long long* bar = &bars[warp];
+    if (lane == 0) mbar_init(bar);
+    const unsigned tbase = tm_begin(&tm_slot);
+    const unsigned t_hold = tbase + kTmHold, t_acc = tbase + kTmAcc;
+    unsigned parity = 0;
+    bool failed = false;
+    {
+        float2 z[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) z[j] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq) tm_store8c(t_acc + 16 * qq, z);
+        tm_wait_st();
+    }
+    const int tend = sep.nterms;
+    if (tend > 0) {
+        wy_load(wys, sep.wrow, __ldg(&sep.korder[0]));
+        cp_async_commit();
+    }
+    int cur_slot = -1;
+    for (int t = 0; t < tend; ++t) {
+        const int k = __ldg(&sep.korder[t]);
+        const int sl = __ldg(&sep.kslot[k]);
+        cp_async_wait_all();
+        __syncthreads();   // this term's row factors have landed; every warp is past its previous FFT
+        if (sl != cur_slot) {   // uniform over the CTA: stage the slot's four columns, keep this warp's
+            const Box bx = box[sl];
+            tile_load(tile, Zb + sl * z_kstride, bx.nr, NXh, col0);
+            cp_async_wait_all();
+            __syncthreads();
+            float2 v[32];
+            if (bx.r0 == 0 && bx.nr == NY) {
+                const float2* tb = tile + 4 * lane + tix_sw(lane, warp);
+#pragma unroll
+                for (int q = 0; q < 32; ++q) v[q] = tb[128 * q];
+            } else {
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    const int i = wrap(lane + 32 * q - bx.r0, NY);
+                    v[q] = (i < bx.nr) ? tile[tix(i, warp)] : make_float2(0.f, 0.f);
+                }
+            }
+            tm_store32c(t_hold, v);
+            tm_wait_st();
+            __syncthreads();   // the staging tile is read: the transpose tiles are free again
+            cur_slot = sl;
+        }
+        // the next term's row factors into the other buffer (last read in the previous term)
+        if (t + 1 < tend) {
+            wy_load(wys + ((t + 1) & 1) * NY, sep.wrow, __ldg(&sep.korder[t + 1]));
+            cp_async_commit();
+        }
+        float2 v[32];
+        tm_load32c(t_hold, v);
+        {
+            const float* wr = wys + (t & 1) * NY;
+#pragma unroll
+            for (int q = 0; q < 32; ++q) v[q] = cscale(v[q], wr[lane + 32 * q]);
+        }
+        const bool bulk = !dcn && cv && !failed;
+        warp_fft1024<false>(v, tr, tw, [&] {
+            if (bulk && lane == 0) bulk_load(tr, hhT + ((long long)k * NXh + col) * NY, NY * sizeof(float2), bar, skip_copy);
+        });
+        if (bulk) {
+            if (!mbar_wait(bar, parity, wait_limit)) {
+                failed = true;
+                if (lane == 0) atomicOr(status, kStatusTimeout);
+                // a copy may still be in flight into the tile: wait for it once
+                // more (bounded) before the tile is reused; no further copies
+                // are issued and the products are skipped from here on
+                mbar_wait(bar, parity, wait_limit);
+            }
+            parity ^= 1;
+        }
+        if (dcn) {
+            // the DC/Nyquist column: separate DC and Nyquist with the partner
+            // frequencies, read back from the (unused) transpose tile
+            const float2* h0 = hhT + (long long)k * NXh * NY;
+            const float2* hn = hN + (long long)k * NY;
+            __syncwarp();
+#pragma unroll
+            for (int mm = 0; mm < 32; ++mm) tr[lane + 32 * mm] = v[mm];
+            __syncwarp();
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq)
+                tm_update8(t_acc, qq, [&](int mm, float2 a) {
+                    const int f = lane + 32 * mm;
+                    float2 x, y;
+                    split_dc_nyq(v[mm], tr_partner(tr, f), x, y);
+                    a = cfma(__ldg(&h0[f]), x, a);
+                    const float2 s = cmul(__ldg(&hn[f]), y);
+                    a.x -= s.y;
+                    a.y += s.x;
+                    return a;
+                });
+            tm_wait_st();
+            __syncwarp();
+        } else if (cv && !failed) {
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq)
+                tm_update8(t_acc, qq, [&](int mm, float2 a) { return cfma(tr[lane + 32 * mm], v[mm], a); });
+            tm_wait_st();
+        }
+    }
+    float2 acc[32];
+    tm_load32c(t_acc, acc);
+    warp_fft1024<true>(acc, tr, tw);
+    __syncthreads();   // every warp is done with its transpose tile: stage the four columns
+    const int swl = tix_sw(lane, warp);
+#pragma unroll
+    for (int mm = 0; mm < 32; ++mm) tile[4 * (lane + 32 * mm) + swl] = acc[mm];
+    __syncthreads();
+    float2* Ab = A + b * a_bstride;
+    for (int e = threadIdx.x; e < NY * kWColWarps; e += kWColWarps * 32) {
+        const int i = e >> 2, c = e & 3;
+        if (col0 + c < NXh) Ab[(long long)i * NXh + col0 + c] = tile[tix(i, c)];
+    }
+    tm_end(&tm_slot);
+}
+
+// G1b + G2 for separable plans, Ny = 1024.  Grid (batch, NXh / 4), 128
+// threads, kTColSmem bytes.  Arguments as kw_cols_adj<false, float2, true>:
+// Q receives, per slot, S_j on the slot box rows.
+__global__ void __launch_bounds__(kWColWarps * 32, 4)
+kt_cols_adj(const float2* __restrict__ V, long long v_bstride, const float2* __restrict__ hhT,
+            const float2* __restrict__ hN, const Box* __restrict__ box, int NXh, float2* __restrict__ Q,
+            long long q_bstride, long long q_kstride, const float2* __restrict__ tw, int* __restrict__ status,
+            long long wait_limit, int skip_copy, SepTerms sep) {
+    constexpr int NY = kWarpN;
+    extern __shared__ __align__(16) float2 smem[];
+    float2* tile = smem;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float2* tr = smem + warp * kWarpN;
+    float* wys = reinterpret_cast<float*>(smem + NY * kWColWarps);
+    __shared__ unsigned long long bars[kWColWarps];
+    __shared__ unsigned tm_slot;
+    const int b = blockIdx.x;
+    const int col0 = blockIdx.y * kWColWarps;
+    const int col = col0 + warp;
+    const bool cv = col < NXh;
+    const bool dcn = blockIdx.y == 0 && warp == 0;
+    const bool use_bulk = !dcn && cv;
+    unsigned long long* bar = &bars[warp];
+    if (lane == 0) mbar_init(bar);
+    const unsigned tbase = tm_begin(&tm_slot);
+    const unsigned t_hold = tbase + kTmHold, t_acc = tbase + kTmAcc;
+    unsigned parity = 0;
+    bool failed = false;
+    const int tend = sep.nterms;
+    const int swl = tix_sw(lane, warp);
+
+    if (tend > 0) wy_load(wys, sep.wrow, __ldg(&sep.korder[0]));
+    tile_load(tile, V + b * v_bstride, NY, NXh, col0);
+    cp_async_wait_all();
+    __syncthreads();
+    {
+        float2 vv[32];
+#pragma unroll
+        for (int q = 0; q < 32; ++q) vv[q] = tile[4 * (lane + 32 * q) + swl];
+        __syncthreads();   // the staging tile is read: the transpose tiles are free
+        // the spectrum of the first term arrives while the FFT of V finishes
+        warp_fft1024<false, true>(vv, tr, tw, [&] {
+            if (use_bulk && tend > 0 && lane == 0)
+                bulk_load(tr, hhT + ((long long)__ldg(&sep.korder[0]) * NXh + col) * NY, NY * sizeof(float2), bar,
+                          skip_copy);
+        });
+        tm_store32c(t_hold, vv);
+        tm_wait_st();
+    }
+    int prev_slot = -1;
+    for (int t = 0; t < tend; ++t) {
+        const int k = __ldg(&sep.korder[t]);
+        const int sl = __ldg(&sep.kslot[k]);
+        const int kn = t + 1 < tend ? __ldg(&sep.korder[t + 1]) : -1;
+        const bool first = sl != prev_slot;
+        const bool last = kn < 0 || __ldg(&sep.kslot[kn]) != sl;
+        prev_slot = sl;
+        if (use_bulk && !failed) {
+            if (!mbar_wait(bar, parity, wait_limit)) {
+                failed = true;
+                if (lane == 0) atomicOr(status, kStatusTimeout);
+                // a copy may still be in flight into the tile: wait for it once
+                // more (bounded) before the tile is reused; no further copies
+                // are issued and the products are skipped from here on
+                mbar_wait(bar, parity, wait_limit);
+            }
+            parity ^= 1;
+        }
+        float2 p[32];
+        tm_load32c(t_hold, p);
+        if (dcn) {
+            const float2* h0 = hhT + (long long)k * NXh * NY;
+            const float2* hn = hN + (long long)k * NY;
+            __syncwarp();
+#pragma unroll
+            for (int mm = 0; mm < 32; ++mm) tr[lane + 32 * mm] = p[mm];
+            __syncwarp();
+#pragma unroll
+            for (int mm = 0; mm < 32; ++mm) {
+                const int f = lane + 32 * mm;
+                float2 x, y;
+                split_dc_nyq(p[mm], tr_partner(tr, f), x, y);
+                float2 r = cmulc(x, __ldg(&h0[f]));
+                const float2 s = cmulc(y, __ldg(&hn[f]));
+                r.x -= s.y;
+                r.y += s.x;
+                p[mm] = r;
+            }
+            __syncwarp();
+        } else {
+#pragma unroll
+            for (int mm = 0; mm < 32; ++mm)
+                p[mm] = (use_bulk && !failed) ? cmulc(p[mm], tr[lane + 32 * mm]) : make_float2(0.f, 0.f);
+        }
+        // the next term's spectrum arrives while this inverse FFT finishes; at
+        // the end of a slot the transpose tiles stage the store first
+        const bool issue = use_bulk && !failed && kn >= 0;
+        warp_fft1024<true, true>(p, tr, tw, [&] {
+            if (issue && !last && lane == 0)
+                bulk_load(tr, hhT + ((long long)kn * NXh + col) * NY, NY * sizeof(float2), bar, skip_copy);
+        });
+        // this term's row factors have landed; the other buffer was last read
+        // in the previous term
+        cp_async_wait_all();
+        __syncthreads();
+        if (kn >= 0) {
+            wy_load(wys + ((t + 1) & 1) * NY, sep.wrow, kn);
+            cp_async_commit();
+        }
+        const float* wr = wys + (t & 1) * NY;
+        if (first) {
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq) {
+                float2 a[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) a[j] = cscale(p[8 * qq + j], wr[lane + 32 * (8 * qq + j)]);
+                tm_store8c(t_acc + 16 * qq, a);
+            }
+        } else {
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq)
+                tm_update8(t_acc, qq, [&](int mm, float2 a) { return cadd(a, cscale(p[mm], wr[lane + 32 * mm])); });
+        }
+        tm_wait_st();
+        if (last) {
+            // S_j of the slot: stage the four columns, store the slot box rows
+            float2 s[32];
+            tm_load32c(t_acc, s);
+#pragma unroll
+            for (int mm = 0; mm < 32; ++mm) tile[4 * (lane + 32 * mm) + swl] = s[mm];
+            __syncthreads();
+            const Box bx = box[sl];
+            float2* Qs = Q + b * q_bstride + sl * q_kstride;
+            for (int e = threadIdx.x; e < bx.nr * kWColWarps; e += kWColWarps * 32) {
+                const int i = e >> 2, c = e & 3;
+                const int g = wrap(bx.r0 + i, NY);
+                if (col0 + c < NXh) Qs[(long long)i * NXh + col0 + c] = tile[tix(g, c)];
+            }
+            __syncthreads();   // the transpose tiles are free again
+            if (issue && lane == 0)
+                bulk_load(tr, hhT + ((long long)kn * NXh + col) * NY, NY * sizeof(float2), bar, skip_copy);
+        }
+    }
+    tm_end(&tm_slot);
+}
+
+}  // namespace pce

@@ -113,6 +113,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.pce_plan_tuning.argtypes = [P, IP, IP, IP, ctypes.POINTER(ctypes.c_double)]
     lib.pce_plan_tuning_log.argtypes = [P, ctypes.c_int, IP, IP, IP, ctypes.POINTER(ctypes.c_double)]
     lib.pce_plan_tuning_log.restype = ctypes.c_int
+    lib.pce_plan_set_tuning.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.pce_plan_set_tuning.restype = ctypes.c_int
     for name in ("pce_plan_create", "pce_plan_create_from_spectra", "pce_apply", "pce_apply_adjoint",
                  "pce_plan_info", "pce_plan_hhat", "pce_plan_destroy", "pce_plan_set_timing",
                  "pce_plan_timing", "pce_plan_create_separable", "pce_plan_create_separable_from_spectra",
@@ -345,6 +347,10 @@ def pce_plan_tuning(plan: int):
     return c.value, v.value, r.value, ms.value
 
 
+def pce_plan_set_tuning(plan: int, chunk: int, col_variant: int, row_variant: int) -> None:
+    _check(load_library().pce_plan_set_tuning(plan, chunk, col_variant, row_variant))
+
+
 def pce_plan_tuning_log(plan: int):
     """[(chunk, column variant, row variant, ms per apply)] of every candidate the last autotune timed."""
     lib = load_library()
@@ -525,6 +531,10 @@ class Plan:
     def tuning_log(self):
         """[(chunk, column variant, row variant, ms per apply)] of every candidate the last autotune timed."""
         return pce_plan_tuning_log(self.handle)
+
+    def set_tuning(self, chunk: int = 0, col_variant: int = 0, row_variant: int = 0) -> None:
+        """Set the autotuner's choices by hand (chunk 0: the plan's scratch chunk)."""
+        pce_plan_set_tuning(self.handle, chunk, col_variant, row_variant)
 
     def set_timing(self, enable: bool) -> None:
         pce_plan_set_timing(self.handle, enable)

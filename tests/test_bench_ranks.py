@@ -61,5 +61,25 @@ def test_reference_arm_skips_other_ranks(capsys):
     import bench
     import synth
     args = argparse.Namespace(steps=1, warmup=0, ref_seconds=1.0, gpus=2)
-    bench.reference_arm(args, synth.problem_2d(64, 64, 4, 1, 0), rank=1)
+    bench.reference_arm(args, "2d_1024_m16_b8", rank=1, world=2)
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_line_matches_the_gpu_arm_config(capsys):
+    """Rank 0 times the compiled oracle for real steps and prints the contract's line
+    with the same config block the GPU arm prints for that workload."""
+    import argparse
+    import json
+
+    import bench
+    import synth
+    args = argparse.Namespace(steps=2, warmup=0, ref_seconds=1.0, gpus=1)
+    bench.reference_arm(args, "1d_n1024_m8_b1", rank=0, world=1)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["steps"] == 2 and line["value"] > 0
+    assert line["config"] == bench.headline_config(synth.workload("1d_n1024_m8_b1"), 1)
+    assert line["cpu_baseline"]["cores"] >= 1 and line["cpu_baseline"]["cpu_model"]
+    # each step is one forward and one adjoint apply: value = 2 steps x 2 applies / total time
+    assert line["value"] == __import__("pytest").approx(2 * 2 / (2 * line["ms_per_step"] / 1000.0))
+    assert line["e2e"] == {"value": line["value"], "unit": "applies/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}

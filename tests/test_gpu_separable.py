@@ -177,3 +177,98 @@ def test_bench_launch_configuration_full_size(torch_cuda):
     xs = E.apply_adjoint_at(pr.u, pr.w, pr.h, pts)
     assert rel(y0.reshape(8, -1)[:, flat], ys) < TOL
     assert rel(x0.reshape(8, -1)[:, flat], xs) < TOL
+
+
+def banded_factors(ny, nx, bands, seed):
+    """Separable windows with chosen row supports: term k has the row factor
+    nonzero (random, positive) on rows bands[k] = (r0, n) taken mod ny and a
+    column factor from two column hats, so slots hold one or more terms and
+    slot boxes can be partial or wrap the seam."""
+    rng = np.random.default_rng(seed)
+    m = len(bands)
+    wy = np.zeros((m, ny), dtype=np.float32)
+    for k, (r0, n) in enumerate(bands):
+        rows = (r0 + np.arange(n)) % ny
+        wy[k, rows] = rng.uniform(0.1, 1.0, n).astype(np.float32)
+    wx = np.stack([synth.hat_1d(nx, 4, k % 2) for k in range(m)]).astype(np.float32)
+    return wy, wx
+
+
+@pytest.mark.parametrize("case", ["hats_2x2", "hats_8x4", "partial", "wrapped"])
+def test_tensor_memory_columns_match_oracle(torch_cuda, case):
+    """Column variant 2 (per-warp column and accumulator in tensor memory)
+    against the FP64 oracle, forward and adjoint, on full, partial and
+    seam-wrapping slot boxes and several right-hand sides."""
+    torch = torch_cuda
+    from paper_1604_04374_gb300 import Plan
+    nx = 64
+    if case.startswith("hats"):
+        gy, gx = (2, 2) if case == "hats_2x2" else (8, 4)
+        wy, wx, w, h, u = sep_problem(1024, nx, gy, gx, 3, 90 + gy, random_h=True)
+    else:
+        # slots of terms {0, 2} and {1, 3}; the slot boxes (550 and 800 rows, or 294 and
+        # 150 rows across the seam) fit the general scratch of 4 x the largest term box
+        bands = ([(0, 300), (150, 400), (250, 300), (600, 350)] if case == "partial"
+                 else [(900, 200), (1000, 100), (120, 50), (950, 150)])
+        wy, wx = banded_factors(1024, nx, bands, 91)
+        w = np.einsum("kr,kc->krc", wy, wx)
+        pr = synth.problem_2d(1024, nx, 4, 3, 92, "normal")
+        h, u = pr.h, pr.u
+    plan = Plan(wy=dev(torch, wy), wx=dev(torch, wx), h=dev(torch, h))
+    assert plan.slots() == gx if case.startswith("hats") else plan.slots() == 2
+    plan.set_tuning(0, 2, 0)
+    assert plan.tuning()[1] == 2
+    ud = dev(torch, u)
+    assert rel(host(plan.apply(ud)), E.apply(u, w, h)) < TOL
+    assert rel(host(plan.apply_adjoint(ud)), E.apply_adjoint(u, w, h)) < TOL
+    # the same plan on the register variant: same operator up to rounding
+    y2, x2 = host(plan.apply(ud)), host(plan.apply_adjoint(ud))
+    plan.set_tuning(0, 0, 0)
+    assert rel(host(plan.apply(ud)), y2) < 2e-6
+    assert rel(host(plan.apply_adjoint(ud)), x2) < 2e-6
+    plan.close()
+
+
+def test_tensor_memory_columns_on_the_bench_workload(torch_cuda):
+    """1024 x 1024, m = 16 hats, B = 8 in one launch: variant 2 equals variant 0
+    to rounding on every output and matches the oracle at sampled outputs of
+    every right-hand side; a graph of the two-lane batch replays it bit for bit."""
+    torch = torch_cuda
+    from paper_1604_04374_gb300 import Batch, Plan
+    pr = synth.workload("2d_1024_m16_b8")
+    wy, wx = synth.hat_factors_2d(1024, 1024, 4, 4)
+    plan = Plan(wy=dev(torch, wy), wx=dev(torch, wx), h=dev(torch, pr.h))
+    u = dev(torch, pr.u)
+    plan.set_tuning(8, 0, 1)
+    ya, xa = host(plan.apply(u)), host(plan.apply_adjoint(u))
+    plan.set_tuning(8, 2, 1)
+    yb, xb = host(plan.apply(u)), host(plan.apply_adjoint(u))
+    assert rel(yb, ya) < 2e-6 and rel(xb, xa) < 2e-6
+    y, x = torch.empty_like(u), torch.empty_like(u)
+    b = Batch([(plan, u, y, False), (plan, u, x, True)], lanes=2)
+    b.launch()
+    b.launch()
+    torch.cuda.synchronize()
+    assert np.array_equal(host(y), yb) and np.array_equal(host(x), xb)
+    b.close()
+    rng = np.random.default_rng(12)
+    pts = np.stack([rng.integers(0, 1024, 64), rng.integers(0, 1024, 64)], axis=-1)
+    flat = pts[:, 0] * 1024 + pts[:, 1]
+    assert rel(yb.reshape(8, -1)[:, flat], E.apply_at(pr.u, pr.w, pr.h, pts)) < TOL
+    assert rel(xb.reshape(8, -1)[:, flat], E.apply_adjoint_at(pr.u, pr.w, pr.h, pts)) < TOL
+    plan.close()
+
+
+def test_set_tuning_rejects_missing_variants(torch_cuda):
+    torch = torch_cuda
+    from paper_1604_04374_gb300 import Plan, PceError, pce
+    wy, wx, w, h, u = sep_problem(128, 64, 2, 2, 1, 93, random_h=True)
+    p = Plan(wy=dev(torch, wy), wx=dev(torch, wx), h=dev(torch, h))   # 128 rows: general structures
+    for cv in (1, 2):
+        with pytest.raises(PceError) as e:
+            p.set_tuning(0, cv, 0)
+        assert e.value.status == pce.PCE_ERR_UNSUPPORTED
+    with pytest.raises(PceError) as e:
+        p.set_tuning(0, 3, 0)
+    assert e.value.status == pce.PCE_ERR_INVALID
+    p.close()
