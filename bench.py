@@ -901,7 +901,7 @@ def batch_arm(args, ctx: Ctx) -> dict | None:
         (cp, rp), log = batch.autotune()
         batch_tuning = {"column_policy": cp, "row_policy": rp,
                         "policies_ms_per_run": [list(t) for t in log],
-                        "policy_meaning": "-1: every plan's own variant; 0/1: that variant for all tasks"}
+                        "policy_meaning": "-1: every plan's own variant; 0/1/2: that variant for every task that has it"}
     lanes, scratch, launches, makespan, _ = batch.info()
     n_tasks = len(tasks)
     boxes = [p.info()[1] for p in plans]

@@ -404,10 +404,10 @@ pce_status pce_batch_destroy(pce_batch_t batch);
 
 /*
  * pce_batch_autotune -- choose, for the whole batch, the column-variant and
- * row-variant policy (each: -1 = every plan's own choice, 0 or 1 = that
- * variant for every task; see pce_plan_autotune) by timing the batch's graph
- * launch under all nine policies (L2 flushed, best of three) and keeping the
- * fastest.  Variants chosen per plan in isolation can lose inside a
+ * row-variant policy (each: -1 = every plan's own choice, 0, 1 or 2 = that
+ * variant for every task that has it, the others keeping their own; see
+ * pce_plan_autotune) by timing the batch's graph launch under all sixteen
+ * policies (L2 flushed, best of three) and keeping the fastest.  Variants chosen per plan in isolation can lose inside a
  * concurrent batch, which is why the batch is timed as a whole.  Runs the
  * batch (outputs are overwritten), allocates and frees temporary buffers,
  * synchronises `stream`, and drops the captured graph (the next
@@ -434,9 +434,15 @@ pce_status pce_schedule_lpt(const double* cost, int n, int lanes, int* lane_of, 
  *   - column FFT variant for Ny = 1024: 0 = one-warp 32 x 32 four-step
  *     (radix 32), 1 = block Stockham (radix 8), 2 (separable plans) = the
  *     one-warp four-step with each warp's held column and accumulator in
- *     tensor memory (more warps per SM);
- *   - adjoint row-pass variant (2D): 0 = next term's data prefetched into
- *     registers (2 CTAs per SM), 1 = no prefetch (3 CTAs per SM);
+ *     tensor memory (more warps per SM), 3 = variant 2 with pruned column
+ *     transforms (separable plans whose row factors each lie in 512 rows
+ *     starting on a multiple of 32: the forward FFT skips the zero half of
+ *     its input, the adjoint computes the needed half of its output);
+ *   - row-pass variant (2D): 0 = block Stockham rows, the adjoint with the
+ *     next term's data prefetched into registers (2 CTAs per SM), 1 = block
+ *     Stockham rows without prefetch (3 CTAs per SM), 2 = variant 1 with the
+ *     plain row transforms (the adjoint's input R2C and the forward's output
+ *     C2R) by one warp per row pair (rows of 1024 points);
  *   - right-hand sides per launch: powers of two up to the plan's scratch
  *     chunk (2D plans and 1D plans above 8192 points).
  * 1D plans up to 8192 points have nothing to choose and are only timed.  The
@@ -456,7 +462,8 @@ pce_status pce_plan_tuning(pce_plan_t plan, int* chunk, int* col_variant, int* r
  * larger values are clamped to it), col_variant and row_variant as above.
  * A column variant the plan has no kernels for is PCE_ERR_UNSUPPORTED
  * (1 needs a 2D plan with 1024 or 2048 rows, 2 a separable plan with 1024
- * rows); a row variant other than 0 needs a 2D plan.  Changes no value an
+ * rows, 3 such a plan whose row factors allow pruning); row variants 1
+ * and 2 need a 2D plan, 2 also rows of 1024 points.  Changes no value an
  * apply computes beyond rounding order.  Host only, no synchronisation. */
 pce_status pce_plan_set_tuning(pce_plan_t plan, int chunk, int col_variant, int row_variant);
 /* Every candidate the last timed pce_plan_autotune measured: writes up to
@@ -490,6 +497,24 @@ int pce_plan_tuning_log(pce_plan_t plan, int max_entries, int* chunk, int* col_v
  */
 pce_status pce_construct_projection_1d(const float* T, int n, int m, float* h_out, float* w_out,
                                        void* stream);
+
+/*
+ * pce_construct_projection_bspline_1d -- the same L2 projection onto the
+ * periodic cardinal B-splines of order alpha (Definition 2.2: B_{0,m} the
+ * indicator of [-1/(2m), 1/(2m)], B_{alpha,m} = m B_{0,m} * B_{alpha-1,m}) at the
+ * nodes k/m (Corollary 4.3: for T of class T^s the error falls like m^-s
+ * when alpha >= s; smooth T give m^-(alpha+1)).
+ *
+ *   alpha : 1 (hats, the same result as pce_construct_projection_1d), 2 or 3.
+ *   m     : in [alpha + 2, min(n, 512)].
+ *   w_out : device, [m][n] float32: w_k[j] = B_{alpha,m}(j/n - k/m), periodic;
+ *           support (alpha + 1) n / m samples.
+ *   T, n, h_out, stream: as for pce_construct_projection_1d.
+ *
+ * PCE_ERR_INVALID for bad sizes, orders or host pointers.
+ */
+pce_status pce_construct_projection_bspline_1d(const float* T, int n, int m, int alpha, float* h_out,
+                                               float* w_out, void* stream);
 
 /*
  * pce_construct_svd_1d -- the truncated singular value decomposition of a

@@ -4,7 +4,8 @@
   integral operator whose kernel is the TVIR T).
 * Two constructions of T_m(x, y) = sum_k c_k(x) B_{1,m}(y - k/m) on the hat
   space B_{1,m} of Definition 2.2:
-  - the L2 projection of T(x, .) (Corollary 4.3),
+  - the L2 projection of T(x, .) (Corollary 4.3), also onto the B-spline
+    spaces B_{alpha,m} of order alpha = 2, 3,
   - interpolation at the nodes y_k = k/m (Section 4, "Interpolation VS
     approximation"), for which c_k = T(., y_k) because the hats are
     cardinal (B_{1,m}(y_i - y_k) = delta_ik).
@@ -66,11 +67,39 @@ def hat_basis(n: int, m: int) -> np.ndarray:
     return np.maximum(0.0, 1.0 - m * np.abs(t))
 
 
-def projection_coefficients(T: np.ndarray, m: int) -> np.ndarray:
-    """Coefficients of the L2 projection of every row T(x_i, .) onto the periodic hats
-    (Corollary 4.3): c(x_i) = argmin_c || T(x_i, .) - B c ||_2 on the sample grid,
+def cardinal_bspline(alpha: int, u) -> np.ndarray:
+    """B_{alpha,1}(u), the centred cardinal B-spline of order alpha on unit knot spacing
+    (Definition 2.2 with m = 1: the (alpha + 1)-fold convolution of the indicator of
+    [-1/2, 1/2]), written out as its textbook piecewise polynomial for alpha = 1, 2, 3.
+    B_{alpha,m}(t) = B_{alpha,1}(m t)."""
+    a = np.abs(np.asarray(u, dtype=np.float64))
+    if alpha == 1:
+        return np.maximum(0.0, 1.0 - a)
+    if alpha == 2:
+        return np.where(a <= 0.5, 0.75 - a ** 2, np.where(a <= 1.5, 0.5 * (1.5 - a) ** 2, 0.0))
+    if alpha == 3:
+        return np.where(a <= 1.0, 2.0 / 3.0 - a ** 2 + 0.5 * a ** 3,
+                        np.where(a <= 2.0, (2.0 - a) ** 3 / 6.0, 0.0))
+    raise ValueError("alpha must be 1, 2 or 3")
+
+
+def bspline_basis(n: int, m: int, alpha: int = 1) -> np.ndarray:
+    """[n][m] matrix of periodic B-splines B_{alpha,m}(y_j - k/m) on y_j = j/n
+    (Definition 2.2, nodes k/m; m >= alpha + 2 keeps one bump per period)."""
+    if m < alpha + 2:
+        raise ValueError("Definition 2.2 needs m >= alpha + 2")
+    y = np.arange(n, dtype=np.float64) / n
+    t = y[:, None] - np.arange(m)[None, :] / m
+    t = t - np.round(t)
+    return cardinal_bspline(alpha, m * t)
+
+
+def projection_coefficients(T: np.ndarray, m: int, alpha: int = 1) -> np.ndarray:
+    """Coefficients of the L2 projection of every row T(x_i, .) onto the periodic
+    B-splines of order alpha (Corollary 4.3; hats for alpha = 1):
+    c(x_i) = argmin_c || T(x_i, .) - B c ||_2 on the sample grid,
     c = (B^T B)^{-1} B^T T(x_i, .).  Returns C [n][m] (h_k = C[:, k], w_k = B[:, k])."""
-    B = hat_basis(T.shape[1], m)
+    B = hat_basis(T.shape[1], m) if alpha == 1 else bspline_basis(T.shape[1], m, alpha)
     return np.linalg.solve(B.T @ B, B.T @ np.asarray(T, dtype=np.float64).T).T
 
 
@@ -78,6 +107,11 @@ def project_on_hats(T: np.ndarray, m: int) -> np.ndarray:
     """L2 projection of every row T(x_i, .) onto span{B_{1,m}(. - k/m)} (Corollary 4.3):
     T_m = C B^T with C from projection_coefficients."""
     return projection_coefficients(T, m) @ hat_basis(T.shape[1], m).T
+
+
+def project_on_bsplines(T: np.ndarray, m: int, alpha: int) -> np.ndarray:
+    """L2 projection of every row T(x_i, .) onto span{B_{alpha,m}(. - k/m)} (Corollary 4.3)."""
+    return projection_coefficients(T, m, alpha) @ bspline_basis(T.shape[1], m, alpha).T
 
 
 def interpolate_on_hats(T: np.ndarray, m: int) -> np.ndarray:

@@ -445,11 +445,11 @@ bool cache_lookup(const char* path, const std::string& key, int& chunk, int& var
         const char* t = std::strstr(line, "\"ms_per_apply\": ");
         const char* rv = std::strstr(line, "\"row_variant\": ");
         int rr = 0;
-        if (rv && (std::sscanf(rv + 15, "%d", &rr) != 1 || (rr != 0 && rr != 1))) continue;
+        if (rv && (std::sscanf(rv + 15, "%d", &rr) != 1 || rr < 0 || rr > 2)) continue;
         int cc = 0, vv = 0;
         double tt = 0.0;
         if (c && v && t && std::sscanf(c + 9, "%d", &cc) == 1 && std::sscanf(v + 11, "%d", &vv) == 1 &&
-            std::sscanf(t + 16, "%lf", &tt) == 1 && cc >= 1 && (vv == 0 || vv == 1)) {
+            std::sscanf(t + 16, "%lf", &tt) == 1 && cc >= 1 && vv >= 0 && vv <= 3) {
             chunk = cc;
             variant = vv;
             rvariant = rr;
@@ -488,8 +488,10 @@ extern "C" pce_status pce_plan_autotune(pce_plan_t p, int64_t batch, const char*
         if (cache_lookup(cache_path, key, c, v, rv, ms)) {
             p->tune_log.clear();
             p->run_chunk = std::min(c, cmax);
-            p->col_variant = (p->ndims == 2 && (p->ny == 1024 || p->ny == 2048) && (v != 2 || p->sep)) ? v : 0;
-            p->row_variant = (p->ndims == 2) ? rv : 0;
+            const bool ok = p->ndims == 2 && (p->ny == 1024 || p->ny == 2048) && (v < 2 || p->sep) &&
+                            (v != 3 || p->sep_prune);
+            p->col_variant = ok ? v : 0;
+            p->row_variant = (p->ndims == 2 && (rv < 2 || p->nx == 1024)) ? rv : 0;
             p->tuned_ms = ms;
             return PCE_OK;
         }
@@ -499,8 +501,10 @@ extern "C" pce_status pce_plan_autotune(pce_plan_t p, int64_t batch, const char*
     std::vector<int> variants = {0};
     if (p->ndims == 2 && !p->sect && (p->ny == 1024 || p->ny == 2048)) variants.push_back(1);
     if (p->sep && !p->sect && p->ny == 1024) variants.push_back(2);
+    if (p->sep && p->sep_prune && !p->sect && p->ny == 1024) variants.push_back(3);
     std::vector<int> rvariants = {0};
     if (p->ndims == 2 && !p->sect) rvariants.push_back(1);
+    if (p->ndims == 2 && !p->sect && p->nx == 1024 && !(p->flags & PCE_FLAG_UNFUSED)) rvariants.push_back(2);
     std::vector<int> chunks;
     if ((p->ndims == 2 && !p->sect) || p->l1) {
         for (int c = 1; c < cmax; c *= 2) chunks.push_back(c);
@@ -595,14 +599,20 @@ extern "C" pce_status pce_plan_autotune(pce_plan_t p, int64_t batch, const char*
 extern "C" pce_status pce_plan_set_tuning(pce_plan_t p, int chunk, int col_variant, int row_variant) {
     if (!p) return fail(PCE_ERR_INVALID, "plan is NULL");
     if (chunk < 0) return fail(PCE_ERR_INVALID, "chunk must be >= 0 (got %d)", chunk);
-    if (col_variant < 0 || col_variant > 2 || row_variant < 0 || row_variant > 1)
-        return fail(PCE_ERR_INVALID, "column variant must be 0..2 and row variant 0..1 (got %d, %d)", col_variant,
+    if (col_variant < 0 || col_variant > 3 || row_variant < 0 || row_variant > 2)
+        return fail(PCE_ERR_INVALID, "column variant must be 0..3 and row variant 0..2 (got %d, %d)", col_variant,
                     row_variant);
     if (col_variant == 1 && !(p->ndims == 2 && (p->ny == 1024 || p->ny == 2048)))
         return fail(PCE_ERR_UNSUPPORTED, "column variant 1 needs a 2D plan with 1024 or 2048 rows");
     if (col_variant == 2 && !(p->sep && p->ny == 1024))
         return fail(PCE_ERR_UNSUPPORTED, "column variant 2 needs a separable plan with 1024 rows");
-    if (row_variant != 0 && p->ndims != 2) return fail(PCE_ERR_UNSUPPORTED, "row variant 1 needs a 2D plan");
+    if (col_variant == 3 && !(p->sep && p->sep_prune))
+        return fail(PCE_ERR_UNSUPPORTED,
+                    "column variant 3 needs a separable plan with 1024 rows whose row factors each lie in "
+                    "512 rows starting on a multiple of 32");
+    if (row_variant != 0 && p->ndims != 2) return fail(PCE_ERR_UNSUPPORTED, "row variants 1, 2 need a 2D plan");
+    if (row_variant == 2 && p->nx != 1024)
+        return fail(PCE_ERR_UNSUPPORTED, "row variant 2 needs rows of 1024 points");
     p->run_chunk = chunk == 0 ? 0 : std::min(chunk, p->bchunk);
     p->col_variant = col_variant;
     p->row_variant = row_variant;
@@ -655,7 +665,7 @@ extern "C" pce_status pce_batch_autotune(pce_batch_t b, void* stream) {
         cleanup();
         return fail(PCE_ERR_CUDA, "batch autotune set-up: %s", cudaGetErrorString(e));
     }
-    const int pol[] = {-1, 0, 1};
+    const int pol[] = {-1, 0, 1, 2};
     double best = 1e300;
     int best_c = -1, best_r = -1;
     b->tune_log.clear();

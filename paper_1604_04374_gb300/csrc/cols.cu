@@ -37,9 +37,13 @@ int cols_smem(int ny) {
 cudaError_t prepare_cols() {
     cudaError_t e = cudaFuncSetAttribute(kw_cols_fwd<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWColSmem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(kt_cols_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, kTColSmem);
+        e = cudaFuncSetAttribute(kt_cols_fwd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTColSmem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(kt_cols_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, kTColSmem);
+        e = cudaFuncSetAttribute(kt_cols_adj<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTColSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kt_cols_fwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTColSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kt_cols_adj<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTColSmem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(kw2_cols_fwd<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kW2Smem);
     if (e == cudaSuccess)
@@ -255,8 +259,14 @@ cudaError_t launch_cols_fwd_sep_tm(dim3 grid, cudaStream_t s, const float2* Z, l
                                    int nxh, float2* A, long long a_bstride, const float2* tw1024, int* status,
                                    long long wait_limit, int skip_copy, const SepTerms& sep) {
     if (!tw1024 || !hhT) return cudaErrorInvalidValue;
-    kt_cols_fwd<<<grid, kWColWarps * 32, kTColSmem, s>>>(Z, z_bstride, z_kstride, hhT, hN, box, nxh, A, a_bstride,
-                                                         tw1024, status, wait_limit, skip_copy, sep);
+    if (sep.kq0)
+        kt_cols_fwd<true><<<grid, kWColWarps * 32, kTColSmem, s>>>(Z, z_bstride, z_kstride, hhT, hN, box, nxh, A,
+                                                                   a_bstride, tw1024, status, wait_limit, skip_copy,
+                                                                   sep);
+    else
+        kt_cols_fwd<false><<<grid, kWColWarps * 32, kTColSmem, s>>>(Z, z_bstride, z_kstride, hhT, hN, box, nxh, A,
+                                                                    a_bstride, tw1024, status, wait_limit,
+                                                                    skip_copy, sep);
     return cudaGetLastError();
 }
 
@@ -265,8 +275,14 @@ cudaError_t launch_cols_adj_sep_tm(dim3 grid, cudaStream_t s, const float2* V, l
                                    long long q_bstride, long long q_kstride, const float2* tw1024, int* status,
                                    long long wait_limit, int skip_copy, const SepTerms& sep) {
     if (!tw1024 || !hhT) return cudaErrorInvalidValue;
-    kt_cols_adj<<<grid, kWColWarps * 32, kTColSmem, s>>>(V, v_bstride, hhT, hN, box, nxh, Q, q_bstride, q_kstride,
-                                                         tw1024, status, wait_limit, skip_copy, sep);
+    if (sep.kq0)
+        kt_cols_adj<true><<<grid, kWColWarps * 32, kTColSmem, s>>>(V, v_bstride, hhT, hN, box, nxh, Q, q_bstride,
+                                                                   q_kstride, tw1024, status, wait_limit, skip_copy,
+                                                                   sep);
+    else
+        kt_cols_adj<false><<<grid, kWColWarps * 32, kTColSmem, s>>>(V, v_bstride, hhT, hN, box, nxh, Q, q_bstride,
+                                                                    q_kstride, tw1024, status, wait_limit,
+                                                                    skip_copy, sep);
     return cudaGetLastError();
 }
 

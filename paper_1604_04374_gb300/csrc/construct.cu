@@ -1,8 +1,9 @@
 // construct.cu -- plan-time construction of (h_k, w_k) from a sampled
 // time-varying impulse response (TVIR), on the GPU: the L2 projection of
-// every row T(x, .) onto the periodic hats B_{1,m}(. - k/m) (Corollary 4.3).
+// every row T(x, .) onto the periodic B-splines B_{alpha,m}(. - k/m) of order
+// alpha = 1 (hats), 2 or 3 (Definition 2.2, Corollary 4.3).
 //
-//   w_k[j]  = B_{1,m}(j/n - k/m)                      (periodic hats)
+//   w_k[j]  = B_{alpha,m}(j/n - k/m)                  (periodic B-splines)
 //   R[d][k] = sum_j T[d][j] w_k[j]                    (right-hand sides, FP64 sums)
 //   G[k][l] = sum_j w_k[j] w_l[j]                     (Gram matrix, host, FP64)
 //   h_k[d]  = sum_l (G^{-1})[k][l] R[d][l]            (FP64 sums)
@@ -24,23 +25,35 @@ using pce_rt::fail;
 
 namespace {
 
-// periodic hat of m nodes on n samples, as the plan receives it (float32)
-__global__ void k_hats(int n, int m, float* w) {
+// B_{alpha,1}(u): the centred cardinal B-spline of order alpha (Definition 2.2
+// on unit knot spacing: the (alpha + 1)-fold convolution of the indicator of
+// [-1/2, 1/2]), as its piecewise polynomial; B_{alpha,m}(t) = B_{alpha,1}(m t).
+__device__ double cardinal_bspline(int alpha, double u) {
+    const double a = fabs(u);
+    if (alpha == 1) return fmax(0.0, 1.0 - a);
+    if (alpha == 2) return a <= 0.5 ? 0.75 - a * a : (a <= 1.5 ? 0.5 * (1.5 - a) * (1.5 - a) : 0.0);
+    return a <= 1.0 ? 2.0 / 3.0 - a * a + 0.5 * a * a * a : (a <= 2.0 ? (2.0 - a) * (2.0 - a) * (2.0 - a) / 6.0 : 0.0);
+}
+
+// periodic B-splines of order alpha at the m nodes k/m on n samples, as the plan
+// receives them (float32): w[k][j] = B_{alpha,m}(j/n - k/m)
+__global__ void k_bsplines(int n, int m, int alpha, float* w) {
     const long long total = (long long)m * n;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
         const int k = (int)(i / n), j = (int)(i % n);
         double t = (double)j / n - (double)k / m;
         t -= rint(t);   // periodic distance in [-1/2, 1/2]
-        w[i] = (float)fmax(0.0, 1.0 - m * fabs(t));
+        w[i] = (float)cardinal_bspline(alpha, m * t);
     }
 }
 
-// R[d][k] = sum_j T[d][j] w_k[j] over the support of w_k (|j/n - k/m| < 1/m)
-__global__ void k_proj_rhs(const float* __restrict__ T, const float* __restrict__ w, int n, int m,
+// R[d][k] = sum_j T[d][j] w_k[j] over the support of w_k (|j/n - k/m| < (alpha + 1) / (2m))
+__global__ void k_proj_rhs(const float* __restrict__ T, const float* __restrict__ w, int n, int m, int alpha,
                            double* __restrict__ R) {
     const long long total = (long long)n * m;
-    const int half = (int)((long long)n / m) + 2;   // samples on each side of the node
+    // samples on each side of the node
+    const int half = (int)(((long long)(alpha + 1) * n + 2 * m - 1) / (2 * m)) + 2;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
          i += (long long)gridDim.x * blockDim.x) {
         const int d = (int)(i / m), k = (int)(i % m);
@@ -110,10 +123,12 @@ bool invert(std::vector<double>& a, int m, std::vector<double>& inv) {
 
 }  // namespace
 
-extern "C" pce_status pce_construct_projection_1d(const float* T, int n, int m, float* h_out, float* w_out,
-                                                  void* stream) {
+extern "C" pce_status pce_construct_projection_bspline_1d(const float* T, int n, int m, int alpha, float* h_out,
+                                                          float* w_out, void* stream) {
+    if (alpha < 1 || alpha > 3) return fail(PCE_ERR_INVALID, "alpha must be 1, 2 or 3 (got %d)", alpha);
     if (n < 16 || n > (1 << 18)) return fail(PCE_ERR_INVALID, "n must be in [16, 262144] (got %d)", n);
-    if (m < 3 || m > std::min(n, 512)) return fail(PCE_ERR_INVALID, "m must be in [3, min(n, 512)] (got %d)", m);
+    if (m < alpha + 2 || m > std::min(n, 512))
+        return fail(PCE_ERR_INVALID, "m must be in [alpha + 2, min(n, 512)] (got %d, alpha %d)", m, alpha);
     if (!pce_rt::is_device_ptr(T) || !pce_rt::is_device_ptr(h_out) || !pce_rt::is_device_ptr(w_out))
         return fail(PCE_ERR_INVALID, "T, h_out and w_out must be device pointers");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -126,8 +141,8 @@ extern "C" pce_status pce_construct_projection_1d(const float* T, int n, int m, 
     cudaError_t e = cudaMalloc(&R, sizeof(double) * (size_t)n * m);
     if (e == cudaSuccess) e = cudaMalloc(&Gi, sizeof(double) * (size_t)m * m);
     if (e == cudaSuccess) {
-        k_hats<<<grid_of((long long)m * n), 256, 0, s>>>(n, m, w_out);
-        k_proj_rhs<<<grid_of((long long)n * m), 256, 0, s>>>(T, w_out, n, m, R);
+        k_bsplines<<<grid_of((long long)m * n), 256, 0, s>>>(n, m, alpha, w_out);
+        k_proj_rhs<<<grid_of((long long)n * m), 256, 0, s>>>(T, w_out, n, m, alpha, R);
         e = cudaGetLastError();
     }
     // Gram matrix of the float32 hats the plan will use, in FP64 on the host
@@ -139,13 +154,14 @@ extern "C" pce_status pce_construct_projection_1d(const float* T, int n, int m, 
         return fail(e == cudaErrorMemoryAllocation ? PCE_ERR_OOM : PCE_ERR_CUDA, "projection set-up: %s",
                     cudaGetErrorString(e));
     }
-    // a sample j meets the hats whose nodes are within 1/m of j/n: k in
-    // floor(j m / n) - 1 .. + 2 (mod m) covers them all
+    // a sample j meets the B-splines whose nodes are within (alpha + 1) / (2m) of
+    // j/n: k in floor(j m / n) - r .. + r + 1 (mod m), r = (alpha + 2) / 2, covers them all
+    const int r = (alpha + 2) / 2;
     std::vector<double> G((size_t)m * m, 0.0);
     for (int j = 0; j < n; ++j) {
         const int k0 = (int)(((long long)j * m) / n);
-        int ks[4], nk = 0;
-        for (int dk = -1; dk <= 2; ++dk) {
+        int ks[8], nk = 0;
+        for (int dk = -r; dk <= r + 1; ++dk) {
             const int k = ((k0 + dk) % m + m) % m;
             bool seen = false;
             for (int t = 0; t < nk; ++t) seen |= ks[t] == k;
@@ -158,7 +174,7 @@ extern "C" pce_status pce_construct_projection_1d(const float* T, int n, int m, 
     std::vector<double> Ginv;
     if (!invert(G, m, Ginv)) {
         cleanup();
-        return fail(PCE_ERR_INVALID, "the Gram matrix of %d hats on %d samples is singular", m, n);
+        return fail(PCE_ERR_INVALID, "the Gram matrix of %d B-splines on %d samples is singular", m, n);
     }
     e = cudaMemcpyAsync(Gi, Ginv.data(), sizeof(double) * Ginv.size(), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) {
@@ -169,6 +185,11 @@ extern "C" pce_status pce_construct_projection_1d(const float* T, int n, int m, 
     cleanup();
     if (e != cudaSuccess) return fail(PCE_ERR_CUDA, "projection: %s", cudaGetErrorString(e));
     return PCE_OK;
+}
+
+extern "C" pce_status pce_construct_projection_1d(const float* T, int n, int m, float* h_out, float* w_out,
+                                                  void* stream) {
+    return pce_construct_projection_bspline_1d(T, n, m, 1, h_out, w_out, stream);
 }
 
 // ---------------------------------------------------------------------------

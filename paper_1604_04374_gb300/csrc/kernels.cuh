@@ -54,6 +54,7 @@ struct SepTerms {
     const int* kslot = nullptr;    // [m] slot of every term
     const int* korder = nullptr;   // [nterms] the terms to run, grouped by slot
     int nterms = 0;
+    const int* kq0 = nullptr;      // [m] pruned column kernels: wy_k's rows lie in [32 kq0, 32 kq0 + 512)
 };
 
 // i mod n for a power of two n (two's complement: also for negative i)

@@ -45,6 +45,14 @@ cudaError_t launch_rows_adj(int nx, dim3 grid, cudaStream_t s, const float2* Q, 
                             const int* kptr, const int* klist, float* dst, long long dst_bstride,
                             float scale, const float2* tw, const float2* tw1024, int rv = 0);
 
+// One-warp plain row transforms for Nx = 1024 (wrows.cuh): the same results
+// and layouts as launch_rows_r2c without a window (row pairs of every row) and
+// launch_rows_c2r; one warp per row pair, grids derived from nrows.
+cudaError_t launch_wrows_r2c(int nb, cudaStream_t s, const float* src, long long src_bstride, int nrows,
+                             float2* dst, long long dst_bstride, const float2* tw1024);
+cudaError_t launch_wrows_c2r(int nb, cudaStream_t s, const float2* src, long long src_bstride, int nrows, float* dst,
+                             long long dst_bstride, float scale, const float2* tw1024);
+
 cudaError_t launch_cols_fwd(int ny, dim3 grid, cudaStream_t s, const float2* Z, long long z_bstride,
                             long long z_kstride, const void* hh, const void* hN, const float* hscale,
                             bool lowp, int m,
@@ -97,7 +105,9 @@ cudaError_t launch_cols_adj_sep(dim3 grid, cudaStream_t s, const float2* V, long
                                 const float2* tw1024, int* status, long long wait_limit, int skip_copy,
                                 const SepTerms& sep);
 
-// The same with the per-warp state in tensor memory (tkernels.cuh).
+// The same with the per-warp state in tensor memory (tkernels.cuh).  With
+// sep.kq0 set, the pruned kernels run and hhT / hN must be the rotated spectra
+// hhat_k[f] W1024^{32 f kq0[k]}.
 cudaError_t launch_cols_fwd_sep_tm(dim3 grid, cudaStream_t s, const float2* Z, long long z_bstride,
                                    long long z_kstride, const float2* hhT, const float2* hN, const Box* box,
                                    int nxh, float2* A, long long a_bstride, const float2* tw1024, int* status,

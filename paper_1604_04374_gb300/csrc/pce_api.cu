@@ -169,6 +169,34 @@ __global__ void k_transpose_hh(const float2* __restrict__ hh, int m, int ny, int
     }
 }
 
+// Spectra of the pruned separable column kernels (Ny = 1024): a term whose row
+// factor lies in rows [s, s + 512), s = 32 kq0[k], is transformed rotated by s,
+// and FFT(x)[f] = W1024^{f s} FFT(x rotated)[f], so the spectra carry that
+// phase: out[k][c][f] = hhT[k][c][f] W1024^{(f s) mod 1024} (c < nxh) and
+// outN[k][f] = hN[k][f] W1024^{(f s) mod 1024}.  Phase and product in FP64.
+__global__ void k_rotate_cols(const float2* __restrict__ hhT, const float2* __restrict__ hN,
+                              const int* __restrict__ kq0, int m, int nxh, float2* __restrict__ out,
+                              float2* __restrict__ outN) {
+    const long long n = (long long)m * (nxh + 1) * 1024;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int f = (int)(i & 1023);
+        const long long kc = i >> 10;
+        const int k = (int)(kc / (nxh + 1));
+        const int c = (int)(kc % (nxh + 1));   // c == nxh: the Nyquist column
+        const int j = (int)(((long long)f * 32 * kq0[k]) & 1023);
+        double sn, cs;
+        sincospi(-2.0 * (double)j / 1024.0, &sn, &cs);
+        const float2 h = c < nxh ? hhT[((long long)k * nxh + c) * 1024 + f] : hN[(long long)k * 1024 + f];
+        const float2 r = make_float2((float)((double)h.x * cs - (double)h.y * sn),
+                                     (float)((double)h.x * sn + (double)h.y * cs));
+        if (c < nxh)
+            out[((long long)k * nxh + c) * 1024 + f] = r;
+        else
+            outN[(long long)k * 1024 + f] = r;
+    }
+}
+
 // ny = 2048: hhT[k][c][par][f'] = hh[k][2 f' + par][c], hN2[k][par][f'] = hN[k][2 f' + par]
 __global__ void k_split_hh2(const float2* __restrict__ hh, const float2* __restrict__ hN, int m, int nxh,
                             float2* hhT, float2* hN2) {
@@ -969,12 +997,34 @@ pce_status setup_separable(pce_plan* p, const float* wy, const float* wx, cudaSt
     PCE_CK(cudaMemcpyAsync(p->skptr, kptr.data(), sizeof(int) * kptr.size(), cudaMemcpyHostToDevice, s));
     if (!klist.empty())
         PCE_CK(cudaMemcpyAsync(p->sklist, klist.data(), sizeof(int) * klist.size(), cudaMemcpyHostToDevice, s));
+    // pruned column kernels: every active term's row factor inside 512 rows that
+    // start on a multiple of 32 (the hats of a node grid with 4 or more rows)
+    std::vector<int> kq0(m, 0);
+    bool prune = !korder.empty() && p->hhT != nullptr && p->hN != nullptr;
+    for (int k : korder) {
+        std::vector<unsigned char> rf(ny, 0);
+        for (int r = 0; r < ny; ++r) rf[r] = hy[(size_t)k * ny + r] != 0.f;
+        int r0 = 0, nr = 0;
+        cyclic_support(rf.data(), ny, r0, nr);
+        if (nr == 0 || (r0 & 31) + nr > 512) prune = false;
+        kq0[k] = r0 >> 5;
+    }
+    if (prune) {
+        if ((st = dev_alloc(&p->d_kq0, (size_t)m))) return st;
+        if ((st = dev_alloc(&p->hhTr, (size_t)m * nxh * ny))) return st;
+        if ((st = dev_alloc(&p->hNr, (size_t)m * ny))) return st;
+        PCE_CK(cudaMemcpyAsync(p->d_kq0, kq0.data(), sizeof(int) * m, cudaMemcpyHostToDevice, s));
+        k_rotate_cols<<<grid_for((long long)m * (nxh + 1) * ny), 256, 0, s>>>(p->hhT, p->hN, p->d_kq0, m,
+                                                                            (int)nxh, p->hhTr, p->hNr);
+        PCE_CK(cudaGetLastError());
+    }
     PCE_CK(cudaStreamSynchronize(s));   // the host vectors die at return
     p->nslots = ns;
     p->nterms = (int)korder.size();
     p->nsitems = (int)items.size();
     p->zk_s = zk;
     p->sep = true;
+    p->sep_prune = prune;
     return PCE_OK;
 }
 
@@ -1519,15 +1569,26 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
     // separable fast path: one-warp column kernels only; variant 2 keeps the
     // per-warp column state in tensor memory
     const bool sepx = p->sep && warp;
-    const bool septm = sepx && colv == 2;
+    const bool septm = sepx && (colv == 2 || colv == 3);
     pce::SepTerms sept;
     sept.wrow = p->wrow;
     sept.kslot = p->d_kslot;
     sept.korder = p->d_korder;
     sept.nterms = p->nterms;
+    // the tensor-memory kernels; variant 3 runs the pruned ones (rotated spectra),
+    // which the plan has when every term allows them
+    const bool prune = colv == 3 && p->sep_prune;
+    pce::SepTerms septp = sept;
+    septp.kq0 = prune ? p->d_kq0 : nullptr;
+    const float2* tm_hT = prune ? p->hhTr : p->hhT;
+    const float2* tm_hN = prune ? p->hNr : p->hN;
     const long long zk = (long long)p->nrmax * nxh;
     const long long zb = scr.zstride;
     const long long ab = scr.astride;
+    // row variant 2: the plain row transforms by the one-warp row kernels (rows of
+    // 1024 points), the windowed passes by the block kernels without prefetch
+    const bool wrows = rowv == 2 && nx == 1024 && p->tw1024 != nullptr;
+    const int brv = rowv == 0 ? 0 : 1;
     const int fpc = pce::rows_pairs_per_cta(nx);
     const int cpc = pce::cols_columns_per_cta(ny);  // same for both variants
     const int npairs = (ny + 1) / 2;
@@ -1546,19 +1607,21 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
                 e = timed(p, PCE_KERNEL_COLS_FWD, s, [&] {
                     if (septm)
                         return pce::launch_cols_fwd_sep_tm(dim3(nb, (nxh + cpc - 1) / cpc), s, scr.Z, zb, p->zk_s,
-                                                           p->hhT, p->hN, p->d_vbox, nxh, scr.A, ab, p->tw1024,
-                                                           p->d_status, p->wait_limit, p->skip_copy, sept);
+                                                           tm_hT, tm_hN, p->d_vbox, nxh, scr.A, ab, p->tw1024,
+                                                           p->d_status, p->wait_limit, p->skip_copy, septp);
                     return pce::launch_cols_fwd_sep(dim3(nb, (nxh + cpc - 1) / cpc), s, scr.Z, zb, p->zk_s,
                                                     p->hhT, p->hN, m, p->d_vbox, nxh, scr.A, ab, p->tw1024,
                                                     p->d_status, p->wait_limit, p->skip_copy, sept);
                 });
             if (e == cudaSuccess)
                 e = timed(p, PCE_KERNEL_ROWS_C2R, s, [&] {
+                    if (wrows) return pce::launch_wrows_c2r(nb, s, scr.A, ab, ny, dst, P, scale, p->tw1024);
                     return pce::launch_rows_c2r(nx, dim3((npairs + fpc - 1) / fpc, nb), s, scr.A, ab,
                                                 ny, dst, P, scale, p->twx, p->tw1024);
                 });
         } else if (sepx) {
             e = timed(p, PCE_KERNEL_ROWS_R2C, s, [&] {
+                if (wrows) return pce::launch_wrows_r2c(nb, s, src, P, ny, scr.A, ab, p->tw1024);
                 return pce::launch_rows_r2c(nx, false, dim3(r2c_blocks(npairs, nx), nb), s, src, P,
                                             ny, nullptr, false, nullptr, nullptr, npairs, scr.A, ab, 0,
                                             p->twx, p->tw1024);
@@ -1566,9 +1629,9 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
             if (e == cudaSuccess)
                 e = timed(p, PCE_KERNEL_COLS_ADJ, s, [&] {
                     if (septm)
-                        return pce::launch_cols_adj_sep_tm(dim3(nb, (nxh + cpc - 1) / cpc), s, scr.A, ab, p->hhT,
-                                                           p->hN, p->d_vbox, nxh, scr.Z, zb, p->zk_s, p->tw1024,
-                                                           p->d_status, p->wait_limit, p->skip_copy, sept);
+                        return pce::launch_cols_adj_sep_tm(dim3(nb, (nxh + cpc - 1) / cpc), s, scr.A, ab, tm_hT,
+                                                           tm_hN, p->d_vbox, nxh, scr.Z, zb, p->zk_s, p->tw1024,
+                                                           p->d_status, p->wait_limit, p->skip_copy, septp);
                     return pce::launch_cols_adj_sep(dim3(nb, (nxh + cpc - 1) / cpc), s, scr.A, ab, p->hhT, p->hN,
                                                     m, p->d_vbox, nxh, scr.Z, zb, p->zk_s, p->tw1024,
                                                     p->d_status, p->wait_limit, p->skip_copy, sept);
@@ -1577,7 +1640,7 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
                 e = timed(p, PCE_KERNEL_ROWS_ADJ, s, [&] {
                     return pce::launch_rows_adj(nx, dim3((npairs + fpc - 1) / fpc, nb), s, scr.Z, zb,
                                                 p->zk_s, ny, p->wxbox, false, p->d_vbox, p->skptr, p->sklist,
-                                                dst, P, scale, p->twx, p->tw1024, rowv);
+                                                dst, P, scale, p->twx, p->tw1024, brv);
                 });
         } else if (!adjoint) {
             if (p->nitems > 0)
@@ -1594,11 +1657,13 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
                 });
             if (e == cudaSuccess)
                 e = timed(p, PCE_KERNEL_ROWS_C2R, s, [&] {
+                    if (wrows) return pce::launch_wrows_c2r(nb, s, scr.A, ab, ny, dst, P, scale, p->tw1024);
                     return pce::launch_rows_c2r(nx, dim3((npairs + fpc - 1) / fpc, nb), s, scr.A, ab,
                                                 ny, dst, P, scale, p->twx, p->tw1024);
                 });
         } else {
             e = timed(p, PCE_KERNEL_ROWS_R2C, s, [&] {
+                if (wrows) return pce::launch_wrows_r2c(nb, s, src, P, ny, scr.A, ab, p->tw1024);
                 return pce::launch_rows_r2c(nx, false, dim3(r2c_blocks(npairs, nx), nb), s, src, P,
                                             ny, nullptr, false, nullptr, nullptr, npairs, scr.A, ab, 0,
                                             p->twx, p->tw1024);
@@ -1613,7 +1678,7 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
                 e = timed(p, PCE_KERNEL_ROWS_ADJ, s, [&] {
                     return pce::launch_rows_adj(nx, dim3((npairs + fpc - 1) / fpc, nb), s, scr.Z, zb,
                                                 zk, ny, wstore(p), p->lowp, p->d_box, p->kptr, p->klist, dst, P,
-                                                scale, p->twx, p->tw1024, rowv);
+                                                scale, p->twx, p->tw1024, brv);
                 });
         }
     }

@@ -62,7 +62,8 @@ struct pce_plan {
     // autotuned choices (pce_plan_autotune): 0 = default
     int run_chunk = 0;          // right-hand sides per launch, <= bchunk
     int col_variant = 0;        // columns of 1024: 0 one-warp four-step, 1 radix-8 Stockham,
-                                // 2 (separable plans) one-warp with the warp state in tensor memory
+                                // 2 (separable plans) one-warp with the warp state in tensor memory,
+                                // 3 the same with pruned column transforms (sep_prune)
     int row_variant = 0;        // adjoint row pass: 0 register prefetch, 1 none (3 CTAs per SM)
     double tuned_ms = 0.0;      // measured ms per right-hand side (forward + adjoint) / 2
     std::vector<double> tune_log;   // (chunk, col variant, row variant, ms per apply) per timed candidate
@@ -83,6 +84,12 @@ struct pce_plan {
     int* skptr = nullptr;       // G3 lists of the slots
     int* sklist = nullptr;
     long long zk_s = 0;         // float2 per slot (rows of the largest slot box x nx/2)
+    // pruned tensor-memory column kernels: every active term's row factor lies in
+    // rows [32 kq0[k], 32 kq0[k] + 512) mod 1024; spectra rotated by W1024^{32 f kq0[k]}
+    bool sep_prune = false;
+    int* d_kq0 = nullptr;       // [m]
+    float2* hhTr = nullptr;     // [m][nx/2][1024]
+    float2* hNr = nullptr;      // [m][1024]
     // sectioned apply (PCE_FLAG_SECTIONED): per term a 1024 x sec_lc section
     bool sect = false;
     int sec_lc = 0;
@@ -122,7 +129,7 @@ struct pce_plan {
                         items,  kptr,  klist,  scrZ, scrA,  wbox16, hh16,     hN16, hhT16, hscale,
                         twN,    hh4,   wrow, wxbox, d_vbox, d_kslot, d_korder, sitems, skptr, sklist,
                         hN2,    hN2_16, tw2048l, d_geo_f, d_geo_a, sec_items_box, sec_items_win, hsT, hsN,
-                        sec_twc, scrZs, scrAs, hsT16, hsN16, sec_hscale};
+                        sec_twc, scrZs, scrAs, hsT16, hsN16, sec_hscale, d_kq0, hhTr, hNr};
         for (void* q : ptrs)
             if (q) cudaFree(q);
     }

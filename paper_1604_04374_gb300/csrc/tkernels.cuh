@@ -25,6 +25,20 @@
 // Layout of a warp's 128 columns: [0, 64) held column, [64, 128) accumulator;
 // thread l holds, like the registers of the one-warp FFT, the values of rows
 // (or frequencies) l + 32 q at columns 2q, 2q + 1.
+//
+// PRUNE (every term's row factor wy_k nonzero only inside rows
+// [s_k, s_k + 512) mod 1024, s_k = 32 q0_k; the hats of a 4 x 4 node grid
+// cover 511 rows): the forward column input of a term is zero on half of the
+// column, the adjoint needs the term's inverse FFT on half of the rows only
+// (Lemma 3.2 applied to the column transforms).  With the input rotated by
+// s_k, the nonzeros land in q < 16 of every lane, and the first 32-point DFT
+// of the one-warp FFT skips its first butterflies (warpfft.cuh, IN_HALF); in
+// the adjoint the last 32-point DFT computes outputs m < 16 only (OUT_HALF).
+// The rotation costs nothing at apply time: FFT(x)[f] = W^{f s} FFT(x')[f]
+// for x'[n] = x[n + s], so the plan stores hhat_k[f] W1024^{f s_k} (the
+// forward then accumulates hhat'_k FFT(x'_k), and conj(hhat'_k) V shifts the
+// adjoint's inverse FFT output by s_k).  The held column is read rotated from
+// tensor memory at runtime column offsets (tm_load16_rot).
 #pragma once
 
 #include "tmem.cuh"
@@ -35,6 +49,7 @@ namespace pce {
 constexpr int kTmCols = 128;
 constexpr int kTmHold = 0;
 constexpr int kTmAcc = 64;
+// four transpose tiles and two row-factor buffers
 constexpr int kTColSmemUsed = (kWColWarps * kWarpN) * (int)sizeof(float2) + 2 * kWarpN * (int)sizeof(float);
 // padded: 5 x (47 KB + the 1 KB per-CTA reserve) exceeds the SM's 228 KB, 4 x does not
 constexpr int kTColSmem = 47 * 1024;
@@ -76,6 +91,7 @@ __device__ __forceinline__ float2 tr_partner(const float2* tr, int f) { return t
 
 // F2 for separable plans, Ny = 1024.  Grid (batch, NXh / 4), 128 threads,
 // kTColSmem bytes.  Arguments as kw_cols_fwd<float2, true>.
+template <bool PRUNE>
 __global__ void __launch_bounds__(kWColWarps * 32, 4)
 kt_cols_fwd(const float2* __restrict__ Z, long long z_bstride, long long z_kstride,
             const float2* __restrict__ hhT, const float2* __restrict__ hN, const Box* __restrict__ box,
@@ -148,16 +164,25 @@ kt_cols_fwd(const float2* __restrict__ Z, long long z_bstride, long long z_kstri
             cp_async_commit();
         }
         float2 v[32];
-        tm_load32c(t_hold, v);
         {
             const float* wr = wys + (t & 1) * NY;
+            if constexpr (PRUNE) {
+                // rows 32 q0 + l + 32 j, j < 16: the support of wy_k, rotated to q < 16
+                const int q0 = __ldg(&sep.kq0[k]);
+                tm_load16_rot(t_hold, q0, v);
 #pragma unroll
-            for (int q = 0; q < 32; ++q) v[q] = cscale(v[q], wr[lane + 32 * q]);
+                for (int j = 0; j < 16; ++j) v[j] = cscale(v[j], wr[lane + 32 * ((q0 + j) & 31)]);
+            } else {
+                tm_load32c(t_hold, v);
+#pragma unroll
+                for (int q = 0; q < 32; ++q) v[q] = cscale(v[q], wr[lane + 32 * q]);
+            }
         }
         const bool bulk = !dcn && cv && !failed;
-        warp_fft1024<false>(v, tr, tw, [&] {
+        auto hook = [&] {
             if (bulk && lane == 0) bulk_load(tr, hhT + ((long long)k * NXh + col) * NY, NY * sizeof(float2), bar, skip_copy);
-        });
+        };
+        warp_fft1024<false, true, decltype(hook), PRUNE>(v, tr, tw, hook);
         if (bulk) {
             if (!mbar_wait(bar, parity, wait_limit)) {
                 failed = true;
@@ -218,6 +243,7 @@ kt_cols_fwd(const float2* __restrict__ Z, long long z_bstride, long long z_kstri
 // G1b + G2 for separable plans, Ny = 1024.  Grid (batch, NXh / 4), 128
 // threads, kTColSmem bytes.  Arguments as kw_cols_adj<false, float2, true>:
 // Q receives, per slot, S_j on the slot box rows.
+template <bool PRUNE>
 __global__ void __launch_bounds__(kWColWarps * 32, 4)
 kt_cols_adj(const float2* __restrict__ V, long long v_bstride, const float2* __restrict__ hhT,
             const float2* __restrict__ hN, const Box* __restrict__ box, int NXh, float2* __restrict__ Q,
@@ -256,11 +282,12 @@ kt_cols_adj(const float2* __restrict__ V, long long v_bstride, const float2* __r
         for (int q = 0; q < 32; ++q) vv[q] = tile[4 * (lane + 32 * q) + swl];
         __syncthreads();   // the staging tile is read: the transpose tiles are free
         // the spectrum of the first term arrives while the FFT of V finishes
-        warp_fft1024<false, true>(vv, tr, tw, [&] {
+        auto hook0 = [&] {
             if (use_bulk && tend > 0 && lane == 0)
                 bulk_load(tr, hhT + ((long long)__ldg(&sep.korder[0]) * NXh + col) * NY, NY * sizeof(float2), bar,
                           skip_copy);
-        });
+        };
+        warp_fft1024<false, true, decltype(hook0)>(vv, tr, tw, hook0);
         tm_store32c(t_hold, vv);
         tm_wait_st();
     }
@@ -312,10 +339,12 @@ kt_cols_adj(const float2* __restrict__ V, long long v_bstride, const float2* __r
         // the next term's spectrum arrives while this inverse FFT finishes; at
         // the end of a slot the transpose tiles stage the store first
         const bool issue = use_bulk && !failed && kn >= 0;
-        warp_fft1024<true, true>(p, tr, tw, [&] {
+        auto hook = [&] {
             if (issue && !last && lane == 0)
                 bulk_load(tr, hhT + ((long long)kn * NXh + col) * NY, NY * sizeof(float2), bar, skip_copy);
-        });
+        };
+        // PRUNE: p[j], j < 16, are rows s_k + l + 32 j of the inverse FFT
+        warp_fft1024<true, true, decltype(hook), false, PRUNE>(p, tr, tw, hook);
         // this term's row factors have landed; the other buffer was last read
         // in the previous term
         cp_async_wait_all();
@@ -325,7 +354,22 @@ kt_cols_adj(const float2* __restrict__ V, long long v_bstride, const float2* __r
             cp_async_commit();
         }
         const float* wr = wys + (t & 1) * NY;
-        if (first) {
+        if constexpr (PRUNE) {
+            const int q0 = __ldg(&sep.kq0[k]);
+            if (first) {   // the slot accumulator starts at zero on every row
+                float2 z[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) z[j] = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int qq = 0; qq < 4; ++qq) tm_store8c(t_acc + 16 * qq, z);
+                tm_wait_st();
+            }
+            float2 a[32];
+            tm_load16_rot(t_acc, q0, a);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) a[j] = cadd(a[j], cscale(p[j], wr[lane + 32 * ((q0 + j) & 31)]));
+            tm_store16_rot(t_acc, q0, a);
+        } else if (first) {
 #pragma unroll
             for (int qq = 0; qq < 4; ++qq) {
                 float2 a[8];

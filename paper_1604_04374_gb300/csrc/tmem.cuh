@@ -101,4 +101,78 @@ __device__ __forceinline__ void tm_store8c(unsigned taddr, const float2 (&v)[8])
     tm_st16(taddr, r);
 }
 
+// 16 complex values from runtime columns: value j from columns a[j], a[j] + 1.
+__device__ __forceinline__ void tm_ld2x16(const unsigned (&a)[16], unsigned (&r)[32]) {
+    asm volatile(
+        "{\n"
+        " tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%32];\n"
+        " tcgen05.ld.sync.aligned.32x32b.x2.b32 {%2, %3}, [%33];\n"
+        " tcgen05.ld.sync.aligned.32x32b.x2.b32 {%4, %5}, [%34];\n"
+        " tcgen05.ld.sync.aligned.32x32b.x2.b32 {%6, %7}, [%35];\n"
+        " tcgen05.ld.sync.aligned.32x32b.x2.b32 {%8, %9}, [%36];\n"
+        " tcgen05.ld.sync.aligned.32x32b.x2.b32 {%10, %11}, [%37];\n"
+        " tcgen05.ld.sync.aligned.32x32b.x2.b32 {%12, %13}, [%38];\n"
+        " tcgen05.ld.sync.aligned.32x32b.x2.b32 {%14, %15}, [%39];\n"
+        " tcgen05.ld.sync.aligned.32x32b.x2.b32 {%16, %17}, [%40];\n"
+        " tcgen05.ld.sync.aligned.32x32b.x2.b32 {%18, %19}, [%41];\n"
+        " tcgen05.ld.sync.aligned.32x32b.x2.b32 {%20, %21}, [%42];\n"
+        " tcgen05.ld.sync.aligned.32x32b.x2.b32 {%22, %23}, [%43];\n"
+        " tcgen05.ld.sync.aligned.32x32b.x2.b32 {%24, %25}, [%44];\n"
+        " tcgen05.ld.sync.aligned.32x32b.x2.b32 {%26, %27}, [%45];\n"
+        " tcgen05.ld.sync.aligned.32x32b.x2.b32 {%28, %29}, [%46];\n"
+        " tcgen05.ld.sync.aligned.32x32b.x2.b32 {%30, %31}, [%47];\n"
+        " tcgen05.wait::ld.sync.aligned;\n}\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]), "r"(a[8]), "r"(a[9]), "r"(a[10]), "r"(a[11]), "r"(a[12]), "r"(a[13]), "r"(a[14]), "r"(a[15])
+        : "memory");
+}
+
+// 16 complex values to runtime columns (value j to columns a[j], a[j] + 1).
+__device__ __forceinline__ void tm_st2x16(const unsigned (&a)[16], const unsigned (&r)[32]) {
+    asm volatile(
+        "{\n"
+        " tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%16, %17};\n"
+        " tcgen05.st.sync.aligned.32x32b.x2.b32 [%1], {%18, %19};\n"
+        " tcgen05.st.sync.aligned.32x32b.x2.b32 [%2], {%20, %21};\n"
+        " tcgen05.st.sync.aligned.32x32b.x2.b32 [%3], {%22, %23};\n"
+        " tcgen05.st.sync.aligned.32x32b.x2.b32 [%4], {%24, %25};\n"
+        " tcgen05.st.sync.aligned.32x32b.x2.b32 [%5], {%26, %27};\n"
+        " tcgen05.st.sync.aligned.32x32b.x2.b32 [%6], {%28, %29};\n"
+        " tcgen05.st.sync.aligned.32x32b.x2.b32 [%7], {%30, %31};\n"
+        " tcgen05.st.sync.aligned.32x32b.x2.b32 [%8], {%32, %33};\n"
+        " tcgen05.st.sync.aligned.32x32b.x2.b32 [%9], {%34, %35};\n"
+        " tcgen05.st.sync.aligned.32x32b.x2.b32 [%10], {%36, %37};\n"
+        " tcgen05.st.sync.aligned.32x32b.x2.b32 [%11], {%38, %39};\n"
+        " tcgen05.st.sync.aligned.32x32b.x2.b32 [%12], {%40, %41};\n"
+        " tcgen05.st.sync.aligned.32x32b.x2.b32 [%13], {%42, %43};\n"
+        " tcgen05.st.sync.aligned.32x32b.x2.b32 [%14], {%44, %45};\n"
+        " tcgen05.st.sync.aligned.32x32b.x2.b32 [%15], {%46, %47};\n"
+        "}\n"
+        :
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(a[4]), "r"(a[5]), "r"(a[6]), "r"(a[7]), "r"(a[8]), "r"(a[9]), "r"(a[10]), "r"(a[11]), "r"(a[12]), "r"(a[13]), "r"(a[14]), "r"(a[15]), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+        : "memory");
+}
+
+// Rows (l + 32 q) of a 32-value column in tensor memory, q = (q0 + j) mod 32
+// for j < 16: the 16 registers a term whose support lies in rows
+// [32 q0, 32 q0 + 512) (mod 1024) needs, in that order.
+__device__ __forceinline__ void tm_load16_rot(unsigned taddr, int q0, float2 (&v)[32]) {
+    unsigned a[16], r[32];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) a[j] = taddr + 2u * (unsigned)((q0 + j) & 31);
+    tm_ld2x16(a, r);
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
+}
+__device__ __forceinline__ void tm_store16_rot(unsigned taddr, int q0, const float2 (&v)[32]) {
+    unsigned a[16], r[32];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        a[j] = taddr + 2u * (unsigned)((q0 + j) & 31);
+        r[2 * j] = __float_as_uint(v[j].x);
+        r[2 * j + 1] = __float_as_uint(v[j].y);
+    }
+    tm_st2x16(a, r);
+}
+
 }  // namespace pce

@@ -51,16 +51,56 @@ __device__ __forceinline__ float2 tw32(float2 x, int j) {
     return cmul(x, make_float2(c, s));
 }
 
+// 8-point DFT of x[0..3] with x[4..7] = 0 (the first decimation-in-frequency
+// butterflies of Dft<8> reduce to copies).
+template <bool INV>
+__device__ __forceinline__ void dft8_lower_half(float2 (&a)[8]) {
+    const float h = 0.70710678118654752440f;
+    float2 b[4], e[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) b[q] = e[q] = a[q];
+    {
+        float2 x = e[1];
+        e[1] = INV ? make_float2((x.x - x.y) * h, (x.x + x.y) * h) : make_float2((x.x + x.y) * h, (x.y - x.x) * h);
+        e[2] = mul_mi<INV>(e[2]);
+        x = e[3];
+        e[3] = INV ? make_float2((-x.x - x.y) * h, (x.x - x.y) * h) : make_float2((x.y - x.x) * h, (-x.x - x.y) * h);
+    }
+    Dft<4, INV>::run(b);
+    Dft<4, INV>::run(e);
+    a[0] = b[0]; a[2] = b[1]; a[4] = b[2]; a[6] = b[3];
+    a[1] = e[0]; a[3] = e[1]; a[5] = e[2]; a[7] = e[3];
+}
+
+// Outputs 0 and 1 of the 4-point DFT only.
+template <bool INV>
+__device__ __forceinline__ void dft4_first_two(float2 (&a)[4]) {
+    const float2 d0 = cadd(a[0], a[2]);
+    const float2 d1 = csub(a[0], a[2]);
+    const float2 d2 = cadd(a[1], a[3]);
+    const float2 d3 = mul_mi<INV>(csub(a[1], a[3]));
+    a[0] = cadd(d0, d2);
+    a[1] = cadd(d1, d3);
+}
+
 // In-register 32-point DFT, natural order in and out: n = 4 n1 + n2,
 // k = k1 + 8 k2, X[k1 + 8 k2] = sum_n2 W4^{n2 k2} W32^{n2 k1} sum_n1 x[4 n1 + n2] W8^{n1 k1}.
-template <bool INV>
+// IN_HALF: x[16..31] are zero (n1 >= 4) and are not read.
+// OUT_HALF: only X[0..15] (k2 < 2) are computed; a[16..31] are left undefined.
+template <bool INV, bool IN_HALF = false, bool OUT_HALF = false>
 __device__ __forceinline__ void dft32(float2 (&a)[32]) {
 #pragma unroll
     for (int n2 = 0; n2 < 4; ++n2) {
         float2 x[8];
+        if constexpr (IN_HALF) {
 #pragma unroll
-        for (int n1 = 0; n1 < 8; ++n1) x[n1] = a[4 * n1 + n2];
-        Dft<8, INV>::run(x);
+            for (int n1 = 0; n1 < 4; ++n1) x[n1] = a[4 * n1 + n2];
+            dft8_lower_half<INV>(x);
+        } else {
+#pragma unroll
+            for (int n1 = 0; n1 < 8; ++n1) x[n1] = a[4 * n1 + n2];
+            Dft<8, INV>::run(x);
+        }
 #pragma unroll
         for (int k1 = 0; k1 < 8; ++k1) a[4 * k1 + n2] = tw32<INV>(x[k1], n2 * k1);
     }
@@ -68,12 +108,18 @@ __device__ __forceinline__ void dft32(float2 (&a)[32]) {
 #pragma unroll
     for (int k1 = 0; k1 < 8; ++k1) {
         float2 y[4] = {a[4 * k1], a[4 * k1 + 1], a[4 * k1 + 2], a[4 * k1 + 3]};
-        Dft<4, INV>::run(y);
+        if constexpr (OUT_HALF) {
+            dft4_first_two<INV>(y);
 #pragma unroll
-        for (int k2 = 0; k2 < 4; ++k2) out[k1 + 8 * k2] = y[k2];
+            for (int k2 = 0; k2 < 2; ++k2) out[k1 + 8 * k2] = y[k2];
+        } else {
+            Dft<4, INV>::run(y);
+#pragma unroll
+            for (int k2 = 0; k2 < 4; ++k2) out[k1 + 8 * k2] = y[k2];
+        }
     }
 #pragma unroll
-    for (int i = 0; i < 32; ++i) a[i] = out[i];
+    for (int i = 0; i < (OUT_HALF ? 16 : 32); ++i) a[i] = out[i];
 }
 
 // Twiddle table of the four-step 1024-point FFT: tw[p * 32 + l] = W1024^{l p}.
@@ -90,11 +136,14 @@ struct NoHook {
 // SPLIT: the twiddles W1024^{l p} come from ten table loads and products (fewer
 // loads in flight, more multiplies); otherwise from 31 table loads.  Which one
 // is faster depends on the register pressure of the calling kernel.
-template <bool INV, bool SPLIT = true, typename Hook = NoHook>
+// IN_HALF: the inputs x[l + 32 q] with q >= 16 are zero (v[16..31] not read).
+// OUT_HALF: only the outputs X[p + 32 m] with m < 16 are computed (v[16..31]
+// undefined on exit).
+template <bool INV, bool SPLIT = true, typename Hook = NoHook, bool IN_HALF = false, bool OUT_HALF = false>
 __device__ __forceinline__ void warp_fft1024(float2 (&v)[32], float2* tile, const float2* __restrict__ tw,
                                              Hook hook = Hook()) {
     const int lane = threadIdx.x & 31;
-    dft32<INV>(v);
+    dft32<INV, IN_HALF>(v);
     // keep the twiddle loads after the first DFT: hoisted above it they would
     // hold 62 more registers through it
     __syncwarp();
@@ -127,7 +176,7 @@ __device__ __forceinline__ void warp_fft1024(float2 (&v)[32], float2* tile, cons
     for (int l = 0; l < 32; ++l) v[l] = tile[l * 32 + (lane ^ l)];
     __syncwarp();
     hook();
-    dft32<INV>(v);
+    dft32<INV, false, OUT_HALF>(v);
 }
 
 // Value X[1024 - f] for f = lane + 32 m, from the lane holding it: lane

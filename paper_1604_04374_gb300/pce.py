@@ -99,6 +99,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.pce_batch_autotune.argtypes = [P, P]
     lib.pce_construct_projection_1d.argtypes = [P, ctypes.c_int, ctypes.c_int, P, P, P]
     lib.pce_construct_projection_1d.restype = ctypes.c_int
+    lib.pce_construct_projection_bspline_1d.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, P]
+    lib.pce_construct_projection_bspline_1d.restype = ctypes.c_int
     lib.pce_construct_svd_1d.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_ulonglong, P, P, P, P]
     lib.pce_construct_svd_1d.restype = ctypes.c_int
@@ -284,6 +286,11 @@ def pce_construct_projection_1d(T_ptr: int, n: int, m: int, h_ptr: int, w_ptr: i
     _check(load_library().pce_construct_projection_1d(T_ptr, n, m, h_ptr, w_ptr, stream))
 
 
+def pce_construct_projection_bspline_1d(T_ptr: int, n: int, m: int, alpha: int, h_ptr: int, w_ptr: int,
+                                        stream: int = 0) -> None:
+    _check(load_library().pce_construct_projection_bspline_1d(T_ptr, n, m, alpha, h_ptr, w_ptr, stream))
+
+
 def pce_construct_svd_1d(T_ptr: int, n: int, m: int, oversample: int, power_iters: int, seed: int,
                          h_ptr: int, w_ptr: int, sigma_ptr: int = 0, stream: int = 0) -> None:
     _check(load_library().pce_construct_svd_1d(T_ptr, n, m, oversample, power_iters, seed, h_ptr, w_ptr,
@@ -307,9 +314,10 @@ def construct_svd_1d(T, m: int, oversample: int = 10, power_iters: int = 2, seed
     return h, w, sig
 
 
-def construct_projection_1d(T, m: int, stream=None):
+def construct_projection_1d(T, m: int, alpha: int = 1, stream=None):
     """(h [m, n], w [m, n]) of the L2 projection of the TVIR T [n, n] (T[d, j]: shift d,
-    input position j) onto m periodic hats (pce_construct_projection_1d)."""
+    input position j) onto m periodic B-splines of order alpha (1: hats,
+    pce_construct_projection_1d; 2, 3: pce_construct_projection_bspline_1d)."""
     import torch
     _need_cuda_f32(T, "T")
     n = int(T.shape[0])
@@ -317,7 +325,11 @@ def construct_projection_1d(T, m: int, stream=None):
         raise ValueError("T must be [n, n]")
     h = torch.empty((m, n), dtype=torch.float32, device=T.device)
     w = torch.empty((m, n), dtype=torch.float32, device=T.device)
-    pce_construct_projection_1d(T.data_ptr(), n, m, h.data_ptr(), w.data_ptr(), _stream_handle(stream))
+    if alpha == 1:
+        pce_construct_projection_1d(T.data_ptr(), n, m, h.data_ptr(), w.data_ptr(), _stream_handle(stream))
+    else:
+        pce_construct_projection_bspline_1d(T.data_ptr(), n, m, alpha, h.data_ptr(), w.data_ptr(),
+                                            _stream_handle(stream))
     return h, w
 
 

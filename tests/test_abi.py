@@ -75,6 +75,10 @@ def test_construction_and_flag_errors_without_a_gpu(lib):
     proj = lib.pce_construct_projection_1d
     for n, m in ((8, 4), (1 << 19, 4), (64, 2), (64, 65)):
         assert proj(None, n, m, None, None, None) == pce.PCE_ERR_INVALID, (n, m)
+    bproj = lib.pce_construct_projection_bspline_1d
+    for n, m, alpha in ((8, 5, 2), (64, 4, 3), (64, 3, 2), (64, 65, 2), (64, 8, 0), (64, 8, 4), (64, 8, 2)):
+        # the last one is valid in size and order but has NULL (host) pointers
+        assert bproj(None, n, m, alpha, None, None, None) == pce.PCE_ERR_INVALID, (n, m, alpha)
     out = ctypes.c_void_p()
     shp1 = (ctypes.c_int64 * 1)(1024)
     shp2 = (ctypes.c_int64 * 2)(256, 256)

@@ -116,7 +116,8 @@ def test_batch_autotune_keeps_results(torch_cuda, mix):
     tasks, outs = tasks_of(torch, mx, plans, ins)
     b = Batch(tasks, lanes=6)
     (cp, rp), log = b.autotune()
-    assert len(log) == 9 and {(c, r) for c, r, _ in log} == {(c, r) for c in (-1, 0, 1) for r in (-1, 0, 1)}
+    pols = (-1, 0, 1, 2)
+    assert len(log) == 16 and {(c, r) for c, r, _ in log} == {(c, r) for c in pols for r in pols}
     assert all(ms > 0 for _, _, ms in log)
     assert (cp, rp, min(ms for _, _, ms in log)) in {(c, r, ms) for c, r, ms in log}
     for o in outs:

@@ -47,6 +47,44 @@ def test_projection_matches_oracle(torch_cuda, n, m):
     assert np.linalg.norm(h - ref) / np.linalg.norm(ref) < 1e-5
 
 
+@pytest.mark.parametrize("n,m,alpha", [(256, 8, 2), (512, 16, 3), (512, 5, 3), (1024, 32, 2), (256, 8, 1)])
+def test_bspline_projection_matches_oracle(torch_cuda, n, m, alpha):
+    """pce_construct_projection_bspline_1d (Corollary 4.3 on B_{alpha,m}) against the oracle:
+    the B-spline windows and the projection coefficients."""
+    torch = torch_cuda
+    from paper_1604_04374_gb300 import construct_projection_1d
+    T = tvir(n)
+    h, w = construct_projection_1d(dev(torch, T), m, alpha)
+    h = h.cpu().numpy().astype(np.float64)
+    w = w.cpu().numpy().astype(np.float64)
+    assert np.abs(w - C.bspline_basis(n, m, alpha).T).max() < 1e-6
+    ref = C.projection_coefficients(T.astype(np.float64), m, alpha).T
+    assert np.linalg.norm(h - ref) / np.linalg.norm(ref) < 1e-5
+
+
+def test_bspline_expansion_feeds_a_plan_and_beats_hats(torch_cuda):
+    """The cubic-spline construction applied by a plan equals the oracle's expansion, and
+    approximates the true operator better than the hat construction at the same m."""
+    torch = torch_cuda
+    from paper_1604_04374_gb300 import Plan, construct_projection_1d
+    n = 512
+    T = tvir(n)
+    u = np.random.default_rng(13).standard_normal((2, n)).astype(np.float32)
+    idx = (np.arange(n)[:, None] - np.arange(n)[None, :]) % n
+    K = T.astype(np.float64)[idx, np.arange(n)[None, :]]
+    y_true = u.astype(np.float64) @ K.T
+    err = {}
+    for alpha in (1, 3):
+        h, w = construct_projection_1d(dev(torch, T), 16, alpha)
+        plan = Plan(w.contiguous(), h=h.contiguous())
+        y = plan.apply(dev(torch, u)).cpu().numpy().astype(np.float64)
+        ref = E.apply(u, w.cpu().numpy(), h.cpu().numpy())
+        assert np.linalg.norm(y - ref) / np.linalg.norm(ref) < 1e-5
+        err[alpha] = np.linalg.norm(y - y_true) / np.linalg.norm(y_true)
+        plan.close()
+    assert err[3] < err[1], err
+
+
 def test_constructed_expansion_feeds_a_plan(torch_cuda):
     """Plan(w, h) from the construction applies sum_k h_k * (w_k . u); the error to the
     true operator u -> sum_j T[(i - j) mod n][j] u[j] does not grow over nested hat spaces."""
@@ -84,6 +122,10 @@ def test_projection_argument_errors(torch_cuda):
     with pytest.raises(PceError) as e:
         pce.pce_construct_projection_1d(Tc.data_ptr(), 64, 4, h.data_ptr(), h.data_ptr())
     assert e.value.status == pce.PCE_ERR_INVALID
+    for m, alpha in ((4, 3), (5, 0), (6, 4)):     # m < alpha + 2, orders outside 1..3
+        with pytest.raises(PceError) as e:
+            pce.pce_construct_projection_bspline_1d(T.data_ptr(), 64, m, alpha, h.data_ptr(), h.data_ptr())
+        assert e.value.status == pce.PCE_ERR_INVALID
 
 
 # ---------------------------------------------------------------- SVD (Section 5.1)

@@ -16,24 +16,26 @@ from oracle import expansion as E
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("kind", ["whole_grid", "sectioned", "separable_tmem"])
+@pytest.mark.parametrize("kind", ["whole_grid", "sectioned", "separable_tmem", "separable_tmem_pruned"])
 def test_bounded_wait_times_out_and_recovers(kind):
     """The whole-grid column kernels, the sectioned column kernel
     (PCE_FLAG_SECTIONED, whose spectrum columns also arrive by bulk copy) and
-    the separable column kernels with tensor-memory state (column variant 2)."""
+    the separable column kernels with tensor-memory state (column variants 2 and 3)."""
     import torch
     from paper_1604_04374_gb300 import Plan, PceError, build, pce
     build.build()
     sectioned = kind == "sectioned"
     # 4 x 4 hats (m = 16): boxes of 511 rows, which a 1024-row section holds
-    pr = synth.problem_2d(1024, 64, 16 if sectioned else 4, 1, 41, "normal",
-                          (2, 2) if kind == "separable_tmem" else None)
+    pruned = kind == "separable_tmem_pruned"
+    m = 16 if (sectioned or pruned) else 4
+    grid = (4, 4) if m == 16 else (2, 2)
+    pr = synth.problem_2d(1024, 64, m, 1, 41, "normal", grid)
     dev = torch.device("cuda", 0)
-    if kind == "separable_tmem":
-        wy, wx = synth.hat_factors_2d(1024, 64, 2, 2)
+    if kind.startswith("separable_tmem"):
+        wy, wx = synth.hat_factors_2d(1024, 64, *grid)
         plan = Plan(wy=torch.from_numpy(wy).to(dev), wx=torch.from_numpy(wx).to(dev),
                     h=torch.from_numpy(pr.h).to(dev))
-        plan.set_tuning(0, 2, 0)
+        plan.set_tuning(0, 3 if pruned else 2, 0)
     else:
         plan = Plan(torch.from_numpy(pr.w).to(dev), h=torch.from_numpy(pr.h).to(dev),
                     flags=pce.PCE_FLAG_SECTIONED if sectioned else 0)

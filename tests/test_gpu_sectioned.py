@@ -98,6 +98,15 @@ def test_sectioned_full_size_workload_sampled(torch_cuda):
     flat = pts[:, 0] * 2048 + pts[:, 1]
     assert rel(ys.reshape(4, -1)[:, flat], E.apply_at(pr.u, pr.w, pr.h, pts)) < TOL
     assert rel(xs.reshape(4, -1)[:, flat], E.apply_adjoint_at(pr.u, pr.w, pr.h, pts)) < TOL
+    # every output of right-hand sides 0 and 3 against the compiled FP64 oracle:
+    # all 192 sections, every column CTA and every row CTA of both directions
+    from oracle import direct as C
+    for b in (0, 3):
+        yo = C.apply(pr.u[b:b + 1], pr.w, pr.h)
+        xo = C.apply_adjoint(pr.u[b:b + 1], pr.w, pr.h)
+        for got, ref in ((ys[b:b + 1], yo), (xs[b:b + 1], xo)):
+            assert rel(got, ref) < TOL
+            assert np.max(np.abs(got - ref)) < TOL * np.max(np.abs(ref))
 
 
 @pytest.mark.parametrize("ny,nx,m,batch", [(1024, 128, 16, 2), (2048, 256, 64, 1)])

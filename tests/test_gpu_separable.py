@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import synth
+from oracle import direct as C
 from oracle import expansion as E
 
 pytestmark = pytest.mark.gpu
@@ -216,16 +217,27 @@ def test_tensor_memory_columns_match_oracle(torch_cuda, case):
         h, u = pr.h, pr.u
     plan = Plan(wy=dev(torch, wy), wx=dev(torch, wx), h=dev(torch, h))
     assert plan.slots() == gx if case.startswith("hats") else plan.slots() == 2
-    plan.set_tuning(0, 2, 0)
-    assert plan.tuning()[1] == 2
     ud = dev(torch, u)
-    assert rel(host(plan.apply(ud)), E.apply(u, w, h)) < TOL
-    assert rel(host(plan.apply_adjoint(ud)), E.apply_adjoint(u, w, h)) < TOL
+    yo, xo = E.apply(u, w, h), E.apply_adjoint(u, w, h)
+    # variant 3 (pruned) needs every row factor inside 512 rows: not the 2 x 2 hats (1023 rows)
+    variants = (2,) if case == "hats_2x2" else (2, 3)
+    if case == "hats_2x2":
+        from paper_1604_04374_gb300 import PceError, pce
+        with pytest.raises(PceError) as e:
+            plan.set_tuning(0, 3, 0)
+        assert e.value.status == pce.PCE_ERR_UNSUPPORTED
+    outs = {}
+    for cv in variants:
+        plan.set_tuning(0, cv, 0)
+        assert plan.tuning()[1] == cv
+        outs[cv] = (host(plan.apply(ud)), host(plan.apply_adjoint(ud)))
+        assert rel(outs[cv][0], yo) < TOL, cv
+        assert rel(outs[cv][1], xo) < TOL, cv
     # the same plan on the register variant: same operator up to rounding
-    y2, x2 = host(plan.apply(ud)), host(plan.apply_adjoint(ud))
     plan.set_tuning(0, 0, 0)
-    assert rel(host(plan.apply(ud)), y2) < 2e-6
-    assert rel(host(plan.apply_adjoint(ud)), x2) < 2e-6
+    for cv in variants:
+        assert rel(host(plan.apply(ud)), outs[cv][0]) < 2e-6
+        assert rel(host(plan.apply_adjoint(ud)), outs[cv][1]) < 2e-6
     plan.close()
 
 
@@ -241,6 +253,9 @@ def test_tensor_memory_columns_on_the_bench_workload(torch_cuda):
     u = dev(torch, pr.u)
     plan.set_tuning(8, 0, 1)
     ya, xa = host(plan.apply(u)), host(plan.apply_adjoint(u))
+    plan.set_tuning(8, 3, 1)
+    y3, x3 = host(plan.apply(u)), host(plan.apply_adjoint(u))
+    assert rel(y3, ya) < 2e-6 and rel(x3, xa) < 2e-6
     plan.set_tuning(8, 2, 1)
     yb, xb = host(plan.apply(u)), host(plan.apply_adjoint(u))
     assert rel(yb, ya) < 2e-6 and rel(xb, xa) < 2e-6
@@ -264,11 +279,110 @@ def test_set_tuning_rejects_missing_variants(torch_cuda):
     from paper_1604_04374_gb300 import Plan, PceError, pce
     wy, wx, w, h, u = sep_problem(128, 64, 2, 2, 1, 93, random_h=True)
     p = Plan(wy=dev(torch, wy), wx=dev(torch, wx), h=dev(torch, h))   # 128 rows: general structures
-    for cv in (1, 2):
+    for cv in (1, 2, 3):
         with pytest.raises(PceError) as e:
             p.set_tuning(0, cv, 0)
         assert e.value.status == pce.PCE_ERR_UNSUPPORTED
     with pytest.raises(PceError) as e:
-        p.set_tuning(0, 3, 0)
+        p.set_tuning(0, 4, 0)
+    assert e.value.status == pce.PCE_ERR_INVALID
+    with pytest.raises(PceError) as e:       # one-warp rows need rows of 1024 points
+        p.set_tuning(0, 0, 2)
+    assert e.value.status == pce.PCE_ERR_UNSUPPORTED
+    with pytest.raises(PceError) as e:
+        p.set_tuning(0, 0, 3)
     assert e.value.status == pce.PCE_ERR_INVALID
     p.close()
+
+
+@pytest.mark.parametrize("col_variant", [0, 2, 3])
+def test_bench_configuration_every_output_against_oracle(torch_cuda, col_variant):
+    """The headline step as timed (1024 x 1024, m = 16, B = 8, separable plan, forward and
+    adjoint as one graph launch of a two-lane batch), both one-warp column variants:
+    every output of right-hand sides 0 and 7 against the compiled FP64 oracle, so every
+    column CTA (128 per right-hand side) and every row-pair CTA is covered."""
+    torch = torch_cuda
+    from paper_1604_04374_gb300 import Batch, Plan
+    pr = synth.workload("2d_1024_m16_b8")
+    wy, wx = synth.hat_factors_2d(1024, 1024, 4, 4)
+    plan = Plan(wy=dev(torch, wy), wx=dev(torch, wx), h=dev(torch, pr.h))
+    plan.set_tuning(8, col_variant, 1)
+    u = dev(torch, pr.u)
+    y, x = torch.empty_like(u), torch.empty_like(u)
+    b = Batch([(plan, u, y, False), (plan, u, x, True)], lanes=2)
+    b.launch()
+    torch.cuda.synchronize()
+    yh, xh = host(y), host(x)
+    b.close()
+    plan.close()
+    for k in (0, 7):
+        yo = C.apply(pr.u[k:k + 1], pr.w, pr.h)
+        xo = C.apply_adjoint(pr.u[k:k + 1], pr.w, pr.h)
+        for got, ref in ((yh[k:k + 1], yo), (xh[k:k + 1], xo)):
+            assert rel(got, ref) < TOL
+            assert np.max(np.abs(got - ref)) < TOL * np.max(np.abs(ref))
+
+
+def test_tuning_cache_round_trip_of_the_tensor_memory_variant(torch_cuda, tmp_path):
+    """A cached choice of column variant 2 is read back by a later plan of the same
+    operator (and ignored by a plan without the separable structures)."""
+    torch = torch_cuda
+    import json
+    from paper_1604_04374_gb300 import Plan
+    wy, wx, w, h, u = sep_problem(1024, 64, 4, 2, 2, 94, random_h=True)
+    cache = str(tmp_path / "t.jsonl")
+    p = Plan(wy=dev(torch, wy), wx=dev(torch, wx), h=dev(torch, h))
+    p.autotune(2, cache)
+    rec = json.loads(open(cache).read().splitlines()[0])
+    with open(cache, "a") as f:
+        f.write(json.dumps(dict(rec, variant=2, chunk=1, row_variant=0)) + "\n")
+    p2 = Plan(wy=dev(torch, wy), wx=dev(torch, wx), h=dev(torch, h))
+    assert p2.autotune(2, cache)[:3] == (1, 2, 0)
+    ud = dev(torch, u)
+    assert rel(host(p2.apply(ud)), E.apply(u, w, h)) < TOL
+    p.close()
+    p2.close()
+
+
+@pytest.mark.parametrize("case", ["separable_hats", "dense_hats", "dense_ragged", "rows_2048"])
+def test_one_warp_row_kernels_match_oracle(torch_cuda, case):
+    """Row variant 2 (the plain row transforms by one-warp kernels for rows of 1024
+    points, the windowed passes by the block kernels) against the FP64 oracle, forward
+    and adjoint, with separable and dense plans, windows whose column boxes wrap the
+    seam or are ragged, an odd batch, and 2048-row plans; equal to the block row
+    kernels (variant 1) up to rounding."""
+    torch = torch_cuda
+    from paper_1604_04374_gb300 import Plan
+    rng = np.random.default_rng(95)
+    if case == "separable_hats":
+        wy, wx, w, h, u = sep_problem(1024, 1024, 4, 4, 3, 96, random_h=True)
+        plan = Plan(wy=dev(torch, wy), wx=dev(torch, wx), h=dev(torch, h))
+    elif case == "dense_hats":
+        pr = synth.problem_2d(128, 1024, 8, 3, 97, "normal")
+        w, h, u = pr.w, pr.h, pr.u
+        plan = Plan(dev(torch, w), h=dev(torch, h))
+    elif case == "dense_ragged":
+        # random windows on boxes of odd sizes, one wrapping both axes
+        ny, nx, m = 64, 1024, 3
+        w = np.zeros((m, ny, nx), dtype=np.float32)
+        for k, (r0, nr, c0, nc) in enumerate([(5, 17, 1000, 77), (40, 31, 3, 511), (60, 9, 700, 1)]):
+            rr = (r0 + np.arange(nr)) % ny
+            cc = (c0 + np.arange(nc)) % nx
+            w[k][np.ix_(rr, cc)] = rng.uniform(0.2, 1.0, (nr, nc)).astype(np.float32)
+        pr = synth.problem_2d(ny, nx, 4, 5, 98, "normal")
+        h, u = pr.h[:m], pr.u
+        plan = Plan(dev(torch, w), h=dev(torch, h))
+    else:
+        pr = synth.problem_2d(2048, 1024, 4, 1, 99, "normal")
+        w, h, u = pr.w, pr.h, pr.u
+        plan = Plan(dev(torch, w), h=dev(torch, h))
+    ud = dev(torch, u)
+    cv = plan.tuning()[1]
+    plan.set_tuning(0, cv, 2)
+    y2, x2 = host(plan.apply(ud)), host(plan.apply_adjoint(ud))
+    assert rel(y2, C.apply(u, w, h)) < TOL
+    assert rel(x2, C.apply_adjoint(u, w, h)) < TOL
+    plan.set_tuning(0, cv, 1)
+    assert rel(host(plan.apply(ud)), y2) < 2e-6
+    assert rel(host(plan.apply_adjoint(ud)), x2) < 2e-6
+    plan.close()

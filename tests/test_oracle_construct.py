@@ -162,3 +162,63 @@ def test_svd_expansion_is_exact_for_a_rank_m_kernel():
     K = np.array([[T[(i - j) % n, j] for j in range(n)] for i in range(n)])
     u = rng.standard_normal((2, n))
     assert np.allclose(E.apply(u, w, h), u @ K.T, atol=1e-11)
+
+
+@pytest.mark.parametrize("alpha", [1, 2, 3])
+def test_bspline_closed_forms_follow_the_definition(alpha):
+    """Definition 2.2: B_{alpha,m} = m B_{0,m} * B_{alpha-1,m}, B_{0,m} the indicator of
+    [-1/(2m), 1/(2m)].  The recursion, evaluated by numerical convolution from the
+    indicator up (on unit knot spacing, m = 1), matches the piecewise polynomials; the
+    B-splines are even, supported on |u| < (alpha + 1) / 2, and their translates by the
+    nodes sum to one."""
+    h = 1e-4
+    s = np.arange(-0.5 + h / 2, 0.5, h)                     # midpoint rule over B_0's support
+    u = np.linspace(-3.0, 3.0, 241)
+    prev = lambda v: (np.abs(v) <= 0.5).astype(float)      # noqa: E731
+    for a in range(1, alpha + 1):
+        cur_vals = np.array([np.sum(prev(x - s)) * h for x in u])
+        prev_tab = (u.copy(), cur_vals)
+        prev = lambda v, t=prev_tab: np.interp(v, t[0], t[1], left=0.0, right=0.0)  # noqa: E731
+    np.testing.assert_allclose(C.cardinal_bspline(alpha, u), cur_vals, atol=5e-3 if alpha == 1 else 2e-3)
+    assert np.all(C.cardinal_bspline(alpha, u[np.abs(u) >= (alpha + 1) / 2]) == 0)
+    np.testing.assert_array_equal(C.cardinal_bspline(alpha, u), C.cardinal_bspline(alpha, -u))
+    B = C.bspline_basis(384, 12, alpha)
+    np.testing.assert_allclose(B.sum(axis=1), 1.0, atol=1e-14)
+    if alpha == 1:
+        np.testing.assert_array_equal(B, C.hat_basis(384, 12))
+
+
+@pytest.mark.parametrize("alpha", [2, 3])
+def test_bspline_projection_idempotent_and_orthogonal(alpha):
+    """Corollary 4.3 on B_{alpha,m}: rows already in the span come back exactly, and the
+    residual of a general T is orthogonal to every B-spline (normal equations)."""
+    rng = np.random.default_rng(9 + alpha)
+    n, m = 120, 10
+    B = C.bspline_basis(n, m, alpha)
+    C0 = rng.standard_normal((n, m))
+    np.testing.assert_allclose(C.projection_coefficients(C0 @ B.T, m, alpha), C0, atol=1e-9)
+    T = rng.standard_normal((n, n))
+    R = T - C.projection_coefficients(T, m, alpha) @ B.T
+    assert np.abs(R @ B).max() < 1e-10 * np.abs(T).max() * n
+
+
+def test_bspline_projection_rates_and_nesting():
+    """Corollary 4.3: for a smooth TVIR the projection error falls like m^-(alpha + 1)
+    for splines of degree alpha.  Odd orders have knots at multiples of 1/m, so the
+    dyadic spaces are nested and the error cannot increase; the cubic space beats the
+    hat space at every m."""
+    n = 1024
+    t = np.arange(n) / n
+    x = t - np.floor(t + 0.5)
+    s = 0.08 + 0.02 * np.cos(2 * np.pi * t)
+    T = np.exp(-(x[:, None] ** 2) / (2 * s[None, :] ** 2))
+    ms = (8, 16, 32, 64)
+    for alpha in (1, 2, 3):
+        errs = [np.linalg.norm(T - C.project_on_bsplines(T, m, alpha)) for m in ms]
+        slope = np.log(errs[-1] / errs[-2]) / np.log(2)
+        assert -(alpha + 1) - 0.4 < slope < -(alpha + 1) + 0.4, (alpha, slope)
+        if alpha % 2 == 1:
+            assert all(b <= a * (1 + 1e-12) for a, b in zip(errs, errs[1:])), (alpha, errs)
+    for m in ms:
+        assert (np.linalg.norm(T - C.project_on_bsplines(T, m, 3))
+                < np.linalg.norm(T - C.project_on_bsplines(T, m, 1)))
