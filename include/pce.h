@@ -417,6 +417,12 @@ pce_status pce_batch_destroy(pce_batch_t batch);
  */
 pce_status pce_batch_autotune(pce_batch_t batch, void* stream);
 pce_status pce_batch_tuning(pce_batch_t batch, int* col_policy, int* row_policy);
+/* pce_batch_set_tuning -- set the policies pce_batch_autotune would choose, by
+ * hand (column policy -1..3, row policy -1..2; a variant a task's plan does
+ * not have falls back to that plan's kernels as under autotuning), e.g. to
+ * give a second batch over the same plans the first one's choice.  Drops the
+ * captured graph.  Host only. */
+pce_status pce_batch_set_tuning(pce_batch_t batch, int col_policy, int row_policy);
 int pce_batch_tuning_log(pce_batch_t batch, int max_entries, int* col_policy, int* row_policy,
                          double* ms_per_run);
 

@@ -727,6 +727,21 @@ extern "C" int pce_batch_tuning_log(pce_batch_t b, int max_entries, int* col_pol
     return n;
 }
 
+extern "C" pce_status pce_batch_set_tuning(pce_batch_t b, int col_policy, int row_policy) {
+    if (!b) return fail(PCE_ERR_INVALID, "batch is NULL");
+    if (col_policy < -1 || col_policy > 3 || row_policy < -1 || row_policy > 2)
+        return fail(PCE_ERR_INVALID, "column policy must be -1..3 and row policy -1..2 (got %d, %d)", col_policy,
+                    row_policy);
+    for (size_t i = 0; i < b->scr.size(); ++i) {
+        b->scr[i].col_variant = col_policy;
+        b->scr[i].row_variant = row_policy;
+    }
+    b->col_policy = col_policy;
+    b->row_policy = row_policy;
+    b->drop_graph();
+    return PCE_OK;
+}
+
 extern "C" pce_status pce_batch_tuning(pce_batch_t b, int* col_policy, int* row_policy) {
     if (!b) return fail(PCE_ERR_INVALID, "batch is NULL");
     if (col_policy) *col_policy = b->col_policy;

@@ -47,6 +47,9 @@
 namespace pce {
 
 constexpr int kTmCols = 128;
+// the four-step twiddles: 31 table loads per FFT (false) or ten loads and 21
+// products (true, warpfft.cuh)
+constexpr bool kTmSplit = false;
 constexpr int kTmHold = 0;
 constexpr int kTmAcc = 64;
 // four transpose tiles and two row-factor buffers
@@ -84,6 +87,27 @@ __device__ __forceinline__ void tm_update8(unsigned tacc, int quarter, F&& f) {
 #pragma unroll
     for (int j = 0; j < 8; ++j) a[j] = f(8 * quarter + j, a[j]);
     tm_store8c(tacc + 16 * quarter, a);
+}
+
+// Rows i < nr of dst ([rows][NXh], columns col0 .. col0 + 3) from rows r0 + i
+// (mod 1024) of the CTA's swizzled staging tile.  Two columns per 16-byte store
+// when dst is 16-byte aligned and NXh a multiple of 4 (always for power-of-two
+// grids of 8 columns or more), else one per 8-byte store.
+__device__ __forceinline__ void store_cols(float2* __restrict__ dst, const float2* tile, int r0, int nr, int NXh,
+                                           int col0) {
+    if ((reinterpret_cast<unsigned long long>(dst) & 15) == 0 && (NXh & 3) == 0) {
+        for (int e = threadIdx.x; e < nr * 2; e += kWColWarps * 32) {
+            const int i = e >> 1, c = (e & 1) * 2;
+            const int g = wrap(r0 + i, kWarpN);
+            const float2 x0 = tile[tix(g, c)], x1 = tile[tix(g, c + 1)];
+            *reinterpret_cast<float4*>(dst + (long long)i * NXh + col0 + c) = make_float4(x0.x, x0.y, x1.x, x1.y);
+        }
+    } else {
+        for (int e = threadIdx.x; e < nr * kWColWarps; e += kWColWarps * 32) {
+            const int i = e >> 2, c = e & 3;
+            if (col0 + c < NXh) dst[(long long)i * NXh + col0 + c] = tile[tix(wrap(r0 + i, kWarpN), c)];
+        }
+    }
 }
 
 // X[(1024 - f) mod 1024] from a warp's transpose tile holding X[f] at f.
@@ -182,7 +206,7 @@ kt_cols_fwd(const float2* __restrict__ Z, long long z_bstride, long long z_kstri
         auto hook = [&] {
             if (bulk && lane == 0) bulk_load(tr, hhT + ((long long)k * NXh + col) * NY, NY * sizeof(float2), bar, skip_copy);
         };
-        warp_fft1024<false, true, decltype(hook), PRUNE>(v, tr, tw, hook);
+        warp_fft1024<false, kTmSplit, decltype(hook), PRUNE>(v, tr, tw, hook);
         if (bulk) {
             if (!mbar_wait(bar, parity, wait_limit)) {
                 failed = true;
@@ -226,17 +250,13 @@ kt_cols_fwd(const float2* __restrict__ Z, long long z_bstride, long long z_kstri
     }
     float2 acc[32];
     tm_load32c(t_acc, acc);
-    warp_fft1024<true>(acc, tr, tw);
+    warp_fft1024<true, kTmSplit>(acc, tr, tw);
     __syncthreads();   // every warp is done with its transpose tile: stage the four columns
     const int swl = tix_sw(lane, warp);
 #pragma unroll
     for (int mm = 0; mm < 32; ++mm) tile[4 * (lane + 32 * mm) + swl] = acc[mm];
     __syncthreads();
-    float2* Ab = A + b * a_bstride;
-    for (int e = threadIdx.x; e < NY * kWColWarps; e += kWColWarps * 32) {
-        const int i = e >> 2, c = e & 3;
-        if (col0 + c < NXh) Ab[(long long)i * NXh + col0 + c] = tile[tix(i, c)];
-    }
+    store_cols(A + b * a_bstride, tile, 0, NY, NXh, col0);
     tm_end(&tm_slot);
 }
 
@@ -287,7 +307,7 @@ kt_cols_adj(const float2* __restrict__ V, long long v_bstride, const float2* __r
                 bulk_load(tr, hhT + ((long long)__ldg(&sep.korder[0]) * NXh + col) * NY, NY * sizeof(float2), bar,
                           skip_copy);
         };
-        warp_fft1024<false, true, decltype(hook0)>(vv, tr, tw, hook0);
+        warp_fft1024<false, kTmSplit, decltype(hook0)>(vv, tr, tw, hook0);
         tm_store32c(t_hold, vv);
         tm_wait_st();
     }
@@ -344,7 +364,7 @@ kt_cols_adj(const float2* __restrict__ V, long long v_bstride, const float2* __r
                 bulk_load(tr, hhT + ((long long)kn * NXh + col) * NY, NY * sizeof(float2), bar, skip_copy);
         };
         // PRUNE: p[j], j < 16, are rows s_k + l + 32 j of the inverse FFT
-        warp_fft1024<true, true, decltype(hook), false, PRUNE>(p, tr, tw, hook);
+        warp_fft1024<true, kTmSplit, decltype(hook), false, PRUNE>(p, tr, tw, hook);
         // this term's row factors have landed; the other buffer was last read
         // in the previous term
         cp_async_wait_all();
@@ -391,12 +411,7 @@ kt_cols_adj(const float2* __restrict__ V, long long v_bstride, const float2* __r
             for (int mm = 0; mm < 32; ++mm) tile[4 * (lane + 32 * mm) + swl] = s[mm];
             __syncthreads();
             const Box bx = box[sl];
-            float2* Qs = Q + b * q_bstride + sl * q_kstride;
-            for (int e = threadIdx.x; e < bx.nr * kWColWarps; e += kWColWarps * 32) {
-                const int i = e >> 2, c = e & 3;
-                const int g = wrap(bx.r0 + i, NY);
-                if (col0 + c < NXh) Qs[(long long)i * NXh + col0 + c] = tile[tix(g, c)];
-            }
+            store_cols(Q + b * q_bstride + sl * q_kstride, tile, bx.r0, bx.nr, NXh, col0);
             __syncthreads();   // the transpose tiles are free again
             if (issue && lane == 0)
                 bulk_load(tr, hhT + ((long long)kn * NXh + col) * NY, NY * sizeof(float2), bar, skip_copy);

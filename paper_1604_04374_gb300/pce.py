@@ -105,6 +105,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
                                          ctypes.c_ulonglong, P, P, P, P]
     lib.pce_construct_svd_1d.restype = ctypes.c_int
     lib.pce_batch_tuning.argtypes = [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    lib.pce_batch_set_tuning.argtypes = [P, ctypes.c_int, ctypes.c_int]
+    lib.pce_batch_set_tuning.restype = ctypes.c_int
     lib.pce_batch_tuning_log.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
     lib.pce_batch_tuning_log.restype = ctypes.c_int
@@ -603,6 +605,10 @@ class Batch:
         """Pick the variant policies by timing the whole batch; returns (policies, log)."""
         pce_batch_autotune(self.handle, _stream_handle(stream))
         return pce_batch_tuning(self.handle), pce_batch_tuning_log(self.handle)
+
+    def set_tuning(self, col_policy: int, row_policy: int) -> None:
+        """Set the variant policies by hand (-1: every plan's own choice)."""
+        _check(load_library().pce_batch_set_tuning(self.handle, col_policy, row_policy))
 
     def close(self):
         if getattr(self, "handle", None):

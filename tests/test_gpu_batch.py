@@ -126,6 +126,15 @@ def test_batch_autotune_keeps_results(torch_cuda, mix):
     torch.cuda.synchronize()
     for i in range(len(ins)):
         assert rel(host(outs[i])[None], ref[i][None]) < 1e-6, i
+    # a second batch over the same plans given the same policies by hand computes the same bits
+    tasks2, outs2 = tasks_of(torch, mx, plans, ins)
+    b2 = Batch(tasks2, lanes=6)
+    b2.set_tuning(cp, rp)
+    b2.launch()
+    torch.cuda.synchronize()
+    for i in range(len(ins)):
+        assert np.array_equal(host(outs2[i]), host(outs[i])), i
+    b2.close()
     b.close()
 
 
