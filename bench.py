@@ -607,32 +607,37 @@ class Ctx:
             self.dist.destroy_process_group()
 
 
-def kernel_table(kern: dict, model: dict, hbm_peak: float):
+def kernel_table(kern: dict, model: dict, hbm_peak: float, units: int | None = None):
     """Per kernel kind: launches, average time, share of the summed kernel time, the work
     model's FP32 rate, its HBM rate of algorithmic bytes (and the fraction of the HBM
-    peak), and the scratch bytes per launch; with the kind of the largest share."""
+    peak), and the scratch bytes per launch; with the kind of the largest share.
+    `units`: how many times the model's work ran (timed steps x chunks of right-hand
+    sides per step); a kind launched several times per chunk (the slot-by-slot
+    schedule) is averaged per chunk, so that its rate is comparable with one launch
+    of the single-pass schedule."""
     kernels = {}
     for name, (ms, n) in kern.items():
         fl, by, scr = model.get(name, (0.0, 0.0, 0.0))
-        avg = ms / n
+        per = n // units if units and n % units == 0 and n >= units else 1
+        avg = ms / (n // per)
         gbs = by / (avg / 1000.0) / 1e9 if by else None
-        kernels[name] = {"launches": n, "avg_us": 1000.0 * avg, "share": None,
+        kernels[name] = {"launches": n, "launches_per_chunk": per, "avg_us": 1000.0 * avg, "share": None,
                          "tflops": fl / (avg / 1000.0) / 1e12 if fl else None,
                          "algorithmic_gbs": gbs, "hbm_frac": gbs / hbm_peak if gbs else None,
                          "scratch_bytes_per_launch": scr}
-    tot = sum(v["avg_us"] * v["launches"] for v in kernels.values()) or 1.0
+    tot = sum(v["avg_us"] * v["launches"] / v["launches_per_chunk"] for v in kernels.values()) or 1.0
     for v in kernels.values():
-        v["share"] = v["avg_us"] * v["launches"] / tot
+        v["share"] = v["avg_us"] * v["launches"] / v["launches_per_chunk"] / tot
     dom = max(kernels, key=lambda k: kernels[k]["share"]) if kernels else None
     return kernels, dom
 
 
 def plan_chunk(plan, batch: int) -> int:
-    """Right-hand sides per launch: batch / launches-per-direction (2D), batch (1D)."""
-    n = plan.launch_count(False, batch)
-    per = 3 if (len(plan.shape) == 2 or plan.shape[0] > 8192) else 1
-    chunks = max(1, n // per)
-    return math.ceil(batch / chunks)
+    """Right-hand sides per launch: the batch in equal chunks of at most the plan's chunk
+    (pce_plan_tuning), as the library splits it."""
+    chunk = max(1, plan.tuning()[0])
+    nch = math.ceil(batch / chunk)
+    return math.ceil(batch / nch)
 
 
 def rel_l2(got: np.ndarray, ref: np.ndarray) -> float:
@@ -806,7 +811,7 @@ def gpu_arm(args, pr: synth.Problem, ctx: Ctx, oracle_cache: dict, headline: boo
     sm_max = clocks.get("sm_max_mhz") or 2070.0
     fp32_peak = ctx.fp32_peak(sm_max)
     model = sectioned_work_model(pr, boxes, nb) if sectioned_plan else work_model(pr, boxes, nb, slots)
-    kernels, dom = kernel_table(kern, model, ctx.hbm_peak)
+    kernels, dom = kernel_table(kern, model, ctx.hbm_peak, seq_steps * math.ceil(B / nb))
     roof = None
     if dom:
         d = kernels[dom]

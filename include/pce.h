@@ -418,7 +418,7 @@ pce_status pce_batch_destroy(pce_batch_t batch);
 pce_status pce_batch_autotune(pce_batch_t batch, void* stream);
 pce_status pce_batch_tuning(pce_batch_t batch, int* col_policy, int* row_policy);
 /* pce_batch_set_tuning -- set the policies pce_batch_autotune would choose, by
- * hand (column policy -1..3, row policy -1..2; a variant a task's plan does
+ * hand (column policy -1..4, row policy -1..2; a variant a task's plan does
  * not have falls back to that plan's kernels as under autotuning), e.g. to
  * give a second batch over the same plans the first one's choice.  Drops the
  * captured graph.  Host only. */
@@ -443,7 +443,10 @@ pce_status pce_schedule_lpt(const double* cost, int n, int lanes, int* lane_of, 
  *     tensor memory (more warps per SM), 3 = variant 2 with pruned column
  *     transforms (separable plans whose row factors each lie in 512 rows
  *     starting on a multiple of 32: the forward FFT skips the zero half of
- *     its input, the adjoint computes the needed half of its output);
+ *     its input, the adjoint computes the needed half of its output), 4 =
+ *     variant 2 run slot by slot (separable plans with two or more
+ *     column-factor slots: the row pass and the column pass of one slot at a
+ *     time, so that one slot's intermediate and the accumulator fit in L2);
  *   - row-pass variant (2D): 0 = block Stockham rows, the adjoint with the
  *     next term's data prefetched into registers (2 CTAs per SM), 1 = block
  *     Stockham rows without prefetch (3 CTAs per SM), 2 = variant 1 with the
@@ -468,8 +471,9 @@ pce_status pce_plan_tuning(pce_plan_t plan, int* chunk, int* col_variant, int* r
  * larger values are clamped to it), col_variant and row_variant as above.
  * A column variant the plan has no kernels for is PCE_ERR_UNSUPPORTED
  * (1 needs a 2D plan with 1024 or 2048 rows, 2 a separable plan with 1024
- * rows, 3 such a plan whose row factors allow pruning); row variants 1
- * and 2 need a 2D plan, 2 also rows of 1024 points.  Changes no value an
+ * rows, 3 such a plan whose row factors allow pruning, 4 such a plan with
+ * two or more slots); row variants 1 and 2 need a 2D plan, 2 also rows of
+ * 1024 points.  Changes no value an
  * apply computes beyond rounding order.  Host only, no synchronisation. */
 pce_status pce_plan_set_tuning(pce_plan_t plan, int chunk, int col_variant, int row_variant);
 /* Every candidate the last timed pce_plan_autotune measured: writes up to

@@ -449,7 +449,7 @@ bool cache_lookup(const char* path, const std::string& key, int& chunk, int& var
         int cc = 0, vv = 0;
         double tt = 0.0;
         if (c && v && t && std::sscanf(c + 9, "%d", &cc) == 1 && std::sscanf(v + 11, "%d", &vv) == 1 &&
-            std::sscanf(t + 16, "%lf", &tt) == 1 && cc >= 1 && vv >= 0 && vv <= 3) {
+            std::sscanf(t + 16, "%lf", &tt) == 1 && cc >= 1 && vv >= 0 && vv <= 4) {
             chunk = cc;
             variant = vv;
             rvariant = rr;
@@ -489,7 +489,7 @@ extern "C" pce_status pce_plan_autotune(pce_plan_t p, int64_t batch, const char*
             p->tune_log.clear();
             p->run_chunk = std::min(c, cmax);
             const bool ok = p->ndims == 2 && (p->ny == 1024 || p->ny == 2048) && (v < 2 || p->sep) &&
-                            (v != 3 || p->sep_prune);
+                            (v != 3 || p->sep_prune) && (v != 4 || p->nslots > 1);
             p->col_variant = ok ? v : 0;
             p->row_variant = (p->ndims == 2 && (rv < 2 || p->nx == 1024)) ? rv : 0;
             p->tuned_ms = ms;
@@ -502,6 +502,7 @@ extern "C" pce_status pce_plan_autotune(pce_plan_t p, int64_t batch, const char*
     if (p->ndims == 2 && !p->sect && (p->ny == 1024 || p->ny == 2048)) variants.push_back(1);
     if (p->sep && !p->sect && p->ny == 1024) variants.push_back(2);
     if (p->sep && p->sep_prune && !p->sect && p->ny == 1024) variants.push_back(3);
+    if (p->sep && p->nslots > 1 && !p->sect && p->ny == 1024) variants.push_back(4);
     std::vector<int> rvariants = {0};
     if (p->ndims == 2 && !p->sect) rvariants.push_back(1);
     if (p->ndims == 2 && !p->sect && p->nx == 1024 && !(p->flags & PCE_FLAG_UNFUSED)) rvariants.push_back(2);
@@ -599,8 +600,8 @@ extern "C" pce_status pce_plan_autotune(pce_plan_t p, int64_t batch, const char*
 extern "C" pce_status pce_plan_set_tuning(pce_plan_t p, int chunk, int col_variant, int row_variant) {
     if (!p) return fail(PCE_ERR_INVALID, "plan is NULL");
     if (chunk < 0) return fail(PCE_ERR_INVALID, "chunk must be >= 0 (got %d)", chunk);
-    if (col_variant < 0 || col_variant > 3 || row_variant < 0 || row_variant > 2)
-        return fail(PCE_ERR_INVALID, "column variant must be 0..3 and row variant 0..2 (got %d, %d)", col_variant,
+    if (col_variant < 0 || col_variant > 4 || row_variant < 0 || row_variant > 2)
+        return fail(PCE_ERR_INVALID, "column variant must be 0..4 and row variant 0..2 (got %d, %d)", col_variant,
                     row_variant);
     if (col_variant == 1 && !(p->ndims == 2 && (p->ny == 1024 || p->ny == 2048)))
         return fail(PCE_ERR_UNSUPPORTED, "column variant 1 needs a 2D plan with 1024 or 2048 rows");
@@ -610,6 +611,8 @@ extern "C" pce_status pce_plan_set_tuning(pce_plan_t p, int chunk, int col_varia
         return fail(PCE_ERR_UNSUPPORTED,
                     "column variant 3 needs a separable plan with 1024 rows whose row factors each lie in "
                     "512 rows starting on a multiple of 32");
+    if (col_variant == 4 && !(p->sep && p->ny == 1024 && p->nslots > 1))
+        return fail(PCE_ERR_UNSUPPORTED, "column variant 4 needs a separable plan with 1024 rows and two or more slots");
     if (row_variant != 0 && p->ndims != 2) return fail(PCE_ERR_UNSUPPORTED, "row variants 1, 2 need a 2D plan");
     if (row_variant == 2 && p->nx != 1024)
         return fail(PCE_ERR_UNSUPPORTED, "row variant 2 needs rows of 1024 points");
@@ -729,8 +732,8 @@ extern "C" int pce_batch_tuning_log(pce_batch_t b, int max_entries, int* col_pol
 
 extern "C" pce_status pce_batch_set_tuning(pce_batch_t b, int col_policy, int row_policy) {
     if (!b) return fail(PCE_ERR_INVALID, "batch is NULL");
-    if (col_policy < -1 || col_policy > 3 || row_policy < -1 || row_policy > 2)
-        return fail(PCE_ERR_INVALID, "column policy must be -1..3 and row policy -1..2 (got %d, %d)", col_policy,
+    if (col_policy < -1 || col_policy > 4 || row_policy < -1 || row_policy > 2)
+        return fail(PCE_ERR_INVALID, "column policy must be -1..4 and row policy -1..2 (got %d, %d)", col_policy,
                     row_policy);
     for (size_t i = 0; i < b->scr.size(); ++i) {
         b->scr[i].col_variant = col_policy;

@@ -270,7 +270,7 @@ cudaError_t launch_cols_fwd_sep_tm(dim3 grid, cudaStream_t s, const float2* Z, l
     return cudaGetLastError();
 }
 
-cudaError_t launch_cols_adj_sep_tm(dim3 grid, cudaStream_t s, const float2* V, long long v_bstride,
+cudaError_t launch_cols_adj_sep_tm(dim3 grid, cudaStream_t s, float2* V, long long v_bstride,
                                    const float2* hhT, const float2* hN, const Box* box, int nxh, float2* Q,
                                    long long q_bstride, long long q_kstride, const float2* tw1024, int* status,
                                    long long wait_limit, int skip_copy, const SepTerms& sep) {

@@ -55,7 +55,16 @@ struct SepTerms {
     const int* korder = nullptr;   // [nterms] the terms to run, grouped by slot
     int nterms = 0;
     const int* kq0 = nullptr;      // [m] pruned column kernels: wy_k's rows lie in [32 kq0, 32 kq0 + 512)
+    // slot-by-slot schedule of the tensor-memory column kernels: the terms
+    // korder[t0 .. t1) of this pass (t1 < 0: all) and the pass's mode bits
+    int t0 = 0, t1 = -1, mode = 0;
 };
+// mode bits (forward): the accumulator starts from A (frequency domain) / the
+// pass ends with the inverse FFT (else A receives the frequency-domain sum)
+constexpr int kSepLoadAcc = 1, kSepFinal = 2;
+// mode bits (adjoint): V already holds its column spectrum / store the column
+// spectrum back into V for later passes
+constexpr int kSepSpecIn = 4, kSepSpecOut = 8;
 
 // i mod n for a power of two n (two's complement: also for negative i)
 __device__ __forceinline__ int wrap(int i, int n) { return i & (n - 1); }
@@ -302,7 +311,7 @@ k_rows_adj(const float2* __restrict__ Q, long long q_bstride, long long q_kstrid
            const WT* __restrict__ wbox, const Box* __restrict__ box,
            const int* __restrict__ kptr, const int* __restrict__ klist,
            float* __restrict__ dst, long long dst_bstride, float scale,
-           const float2* __restrict__ tw) {
+           const float2* __restrict__ tw, int kmin, int kmax, int accumulate) {
     constexpr int T = NX / kR;
     constexpr int FPC = 256 / T;
     constexpr int NXh = NX / 2;
@@ -317,14 +326,27 @@ k_rows_adj(const float2* __restrict__ Q, long long q_bstride, long long q_kstrid
     const bool pv = p < npairs;
     const int ga = 2 * p, gb = ga + 1;
 
-    // uniform trip count over the CTA's row pairs
+    // the row pair's entries with kmin <= k < kmax (each list is sorted by k, so
+    // they are contiguous); uniform trip count over the CTA's row pairs
+    auto range = [&](int ps, int& beg, int& cnt) {
+        int a = __ldg(&kptr[ps]), e = __ldg(&kptr[ps + 1]);
+        while (a < e && __ldg(&klist[a]) < kmin) ++a;
+        int z = a;
+        while (z < e && __ldg(&klist[z]) < kmax) ++z;
+        beg = a;
+        cnt = z - a;
+    };
     int nk = 0;
     for (int s = 0; s < FPC; ++s) {
         const int ps = blockIdx.x * FPC + s;
-        if (ps < npairs) nk = max(nk, __ldg(&kptr[ps + 1]) - __ldg(&kptr[ps]));
+        if (ps < npairs) {
+            int bs, cs;
+            range(ps, bs, cs);
+            nk = max(nk, cs);
+        }
     }
-    const int kbeg = pv ? __ldg(&kptr[p]) : 0;
-    const int kcnt = pv ? __ldg(&kptr[p + 1]) - kbeg : 0;
+    int kbeg = 0, kcnt = 0;
+    if (pv) range(p, kbeg, kcnt);
 
     auto term = [&](int t) {
         AdjTerm<WT> q;
@@ -388,8 +410,13 @@ k_rows_adj(const float2* __restrict__ Q, long long q_bstride, long long q_kstrid
 #pragma unroll
     for (int r = 0; r < kR; ++r) {
         const int n = j + r * T;
-        if (pv) xa[n] = acc[r].x * scale;
-        if (pv && gb < nrows) xb[n] = acc[r].y * scale;
+        if (accumulate) {   // a later pass of the slot-by-slot schedule adds its slots
+            if (pv) xa[n] += acc[r].x * scale;
+            if (pv && gb < nrows) xb[n] += acc[r].y * scale;
+        } else {
+            if (pv) xa[n] = acc[r].x * scale;
+            if (pv && gb < nrows) xb[n] = acc[r].y * scale;
+        }
     }
 }
 

@@ -43,7 +43,8 @@ cudaError_t launch_rows_c2r(int nx, dim3 grid, cudaStream_t s, const float2* src
 cudaError_t launch_rows_adj(int nx, dim3 grid, cudaStream_t s, const float2* Q, long long q_bstride,
                             long long q_kstride, int nrows, const void* wbox, bool lowp, const Box* box,
                             const int* kptr, const int* klist, float* dst, long long dst_bstride,
-                            float scale, const float2* tw, const float2* tw1024, int rv = 0);
+                            float scale, const float2* tw, const float2* tw1024, int rv = 0, int kmin = 0,
+                            int kmax = 1 << 30, int accumulate = 0);
 
 // One-warp plain row transforms for Nx = 1024 (wrows.cuh): the same results
 // and layouts as launch_rows_r2c without a window (row pairs of every row) and
@@ -112,7 +113,7 @@ cudaError_t launch_cols_fwd_sep_tm(dim3 grid, cudaStream_t s, const float2* Z, l
                                    long long z_kstride, const float2* hhT, const float2* hN, const Box* box,
                                    int nxh, float2* A, long long a_bstride, const float2* tw1024, int* status,
                                    long long wait_limit, int skip_copy, const SepTerms& sep);
-cudaError_t launch_cols_adj_sep_tm(dim3 grid, cudaStream_t s, const float2* V, long long v_bstride,
+cudaError_t launch_cols_adj_sep_tm(dim3 grid, cudaStream_t s, float2* V, long long v_bstride,
                                    const float2* hhT, const float2* hN, const Box* box, int nxh, float2* Q,
                                    long long q_bstride, long long q_kstride, const float2* tw1024, int* status,
                                    long long wait_limit, int skip_copy, const SepTerms& sep);

@@ -1019,6 +1019,14 @@ pce_status setup_separable(pce_plan* p, const float* wy, const float* wx, cudaSt
         PCE_CK(cudaGetLastError());
     }
     PCE_CK(cudaStreamSynchronize(s));   // the host vectors die at return
+    p->slot_item_off.assign(ns + 1, 0);
+    p->slot_term_off.assign(ns + 1, 0);
+    for (int j = 0; j < ns; ++j) {
+        p->slot_item_off[j + 1] = p->slot_item_off[j] + (vbox[j].nr + 1) / 2;
+        int n = 0;
+        for (int k : korder) n += kslot[k] == j;
+        p->slot_term_off[j + 1] = p->slot_term_off[j] + n;
+    }
     p->nslots = ns;
     p->nterms = (int)korder.size();
     p->nsitems = (int)items.size();
@@ -1569,7 +1577,14 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
     // separable fast path: one-warp column kernels only; variant 2 keeps the
     // per-warp column state in tensor memory
     const bool sepx = p->sep && warp;
-    const bool septm = sepx && (colv == 2 || colv == 3);
+    const bool septm = sepx && (colv == 2 || colv == 3 || colv == 4);
+    // variant 4: row pass and column pass slot by slot, so that one slot's Z and
+    // the accumulator A stay in L2 between them (slots without terms skipped)
+    std::vector<int> active;
+    if (septm && colv == 4)
+        for (int j = 0; j < p->nslots; ++j)
+            if (p->slot_term_off[j + 1] > p->slot_term_off[j]) active.push_back(j);
+    const bool slotwise = active.size() > 1;
     pce::SepTerms sept;
     sept.wrow = p->wrow;
     sept.kslot = p->d_kslot;
@@ -1596,7 +1611,60 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
         const int nb = (int)std::min<long long>(bal, batch - b0);
         const float* src = in + b0 * P;
         float* dst = out + b0 * P;
-        if (sepx && !adjoint) {
+        if (slotwise && !adjoint) {
+            for (size_t a = 0; a < active.size() && e == cudaSuccess; ++a) {
+                const int j = active[a];
+                const int i0 = p->slot_item_off[j], ni = p->slot_item_off[j + 1] - i0;
+                pce::SepTerms sj = septp;
+                sj.t0 = p->slot_term_off[j];
+                sj.t1 = p->slot_term_off[j + 1];
+                sj.mode = (a > 0 ? pce::kSepLoadAcc : 0) | (a + 1 == active.size() ? pce::kSepFinal : 0);
+                if (ni > 0)
+                    e = timed(p, PCE_KERNEL_ROWS_R2C_WINDOW, s, [&] {
+                        return pce::launch_rows_r2c(nx, true, dim3(r2c_blocks(ni, nx), nb), s, src, P, ny, p->wxbox,
+                                                    false, p->d_vbox, p->sitems + i0, ni, scr.Z, zb, p->zk_s, p->twx,
+                                                    p->tw1024);
+                    });
+                if (e == cudaSuccess)
+                    e = timed(p, PCE_KERNEL_COLS_FWD, s, [&] {
+                        return pce::launch_cols_fwd_sep_tm(dim3(nb, (nxh + cpc - 1) / cpc), s, scr.Z, zb, p->zk_s,
+                                                           tm_hT, tm_hN, p->d_vbox, nxh, scr.A, ab, p->tw1024,
+                                                           p->d_status, p->wait_limit, p->skip_copy, sj);
+                    });
+            }
+            if (e == cudaSuccess)
+                e = timed(p, PCE_KERNEL_ROWS_C2R, s, [&] {
+                    if (wrows) return pce::launch_wrows_c2r(nb, s, scr.A, ab, ny, dst, P, scale, p->tw1024);
+                    return pce::launch_rows_c2r(nx, dim3((npairs + fpc - 1) / fpc, nb), s, scr.A, ab,
+                                                ny, dst, P, scale, p->twx, p->tw1024);
+                });
+        } else if (slotwise) {
+            e = timed(p, PCE_KERNEL_ROWS_R2C, s, [&] {
+                if (wrows) return pce::launch_wrows_r2c(nb, s, src, P, ny, scr.A, ab, p->tw1024);
+                return pce::launch_rows_r2c(nx, false, dim3(r2c_blocks(npairs, nx), nb), s, src, P,
+                                            ny, nullptr, false, nullptr, nullptr, npairs, scr.A, ab, 0,
+                                            p->twx, p->tw1024);
+            });
+            for (size_t a = 0; a < active.size() && e == cudaSuccess; ++a) {
+                const int j = active[a];
+                pce::SepTerms sj = septp;
+                sj.t0 = p->slot_term_off[j];
+                sj.t1 = p->slot_term_off[j + 1];
+                // the first pass stores V's column spectrum in place for the later ones
+                sj.mode = a == 0 ? pce::kSepSpecOut : pce::kSepSpecIn;
+                e = timed(p, PCE_KERNEL_COLS_ADJ, s, [&] {
+                    return pce::launch_cols_adj_sep_tm(dim3(nb, (nxh + cpc - 1) / cpc), s, scr.A, ab, tm_hT, tm_hN,
+                                                       p->d_vbox, nxh, scr.Z, zb, p->zk_s, p->tw1024, p->d_status,
+                                                       p->wait_limit, p->skip_copy, sj);
+                });
+                if (e == cudaSuccess)
+                    e = timed(p, PCE_KERNEL_ROWS_ADJ, s, [&] {
+                        return pce::launch_rows_adj(nx, dim3((npairs + fpc - 1) / fpc, nb), s, scr.Z, zb, p->zk_s,
+                                                    ny, p->wxbox, false, p->d_vbox, p->skptr, p->sklist, dst, P,
+                                                    scale, p->twx, p->tw1024, brv, j, j + 1, a > 0 ? 1 : 0);
+                    });
+            }
+        } else if (sepx && !adjoint) {
             if (p->nsitems > 0)
                 e = timed(p, PCE_KERNEL_ROWS_R2C_WINDOW, s, [&] {
                     return pce::launch_rows_r2c(nx, true, dim3(r2c_blocks(p->nsitems, nx), nb), s, src, P, ny,

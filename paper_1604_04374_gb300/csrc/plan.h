@@ -63,7 +63,8 @@ struct pce_plan {
     int run_chunk = 0;          // right-hand sides per launch, <= bchunk
     int col_variant = 0;        // columns of 1024: 0 one-warp four-step, 1 radix-8 Stockham,
                                 // 2 (separable plans) one-warp with the warp state in tensor memory,
-                                // 3 the same with pruned column transforms (sep_prune)
+                                // 3 the same with pruned column transforms (sep_prune),
+                                // 4 variant 2 run slot by slot (row and column pass per slot)
     int row_variant = 0;        // adjoint row pass: 0 register prefetch, 1 none (3 CTAs per SM)
     double tuned_ms = 0.0;      // measured ms per right-hand side (forward + adjoint) / 2
     std::vector<double> tune_log;   // (chunk, col variant, row variant, ms per apply) per timed candidate
@@ -84,6 +85,10 @@ struct pce_plan {
     int* skptr = nullptr;       // G3 lists of the slots
     int* sklist = nullptr;
     long long zk_s = 0;         // float2 per slot (rows of the largest slot box x nx/2)
+    // slot-by-slot schedule (column variant 4): slot j's F1 items are
+    // sitems[slot_item_off[j] .. slot_item_off[j + 1]), its terms
+    // korder[slot_term_off[j] .. slot_term_off[j + 1])
+    std::vector<int> slot_item_off, slot_term_off;
     // pruned tensor-memory column kernels: every active term's row factor lies in
     // rows [32 kq0[k], 32 kq0[k] + 512) mod 1024; spectra rotated by W1024^{32 f kq0[k]}
     bool sep_prune = false;

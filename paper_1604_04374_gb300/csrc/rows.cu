@@ -62,7 +62,8 @@ cudaError_t launch_rows_c2r(int nx, dim3 grid, cudaStream_t s, const float2* src
 cudaError_t launch_rows_adj(int nx, dim3 grid, cudaStream_t s, const float2* Q, long long q_bstride,
                             long long q_kstride, int nrows, const void* wbox, bool lowp, const Box* box,
                             const int* kptr, const int* klist, float* dst, long long dst_bstride,
-                            float scale, const float2* tw, const float2* /*tw1024*/, int rv) {
+                            float scale, const float2* tw, const float2* /*tw1024*/, int rv, int kmin, int kmax,
+                            int accumulate) {
     using bf16 = __nv_bfloat16;
     switch (nx) {
 #define X(N)                                                                                   \
@@ -70,19 +71,19 @@ cudaError_t launch_rows_adj(int nx, dim3 grid, cudaStream_t s, const float2* Q, 
         if (lowp && rv)                                                                        \
             k_rows_adj<N, bf16, 1><<<grid, 256, 0, s>>>(Q, q_bstride, q_kstride, nrows,         \
                                                        static_cast<const bf16*>(wbox), box,    \
-                                                       kptr, klist, dst, dst_bstride, scale, tw); \
+                                                       kptr, klist, dst, dst_bstride, scale, tw, kmin, kmax, accumulate); \
         else if (lowp)                                                                         \
             k_rows_adj<N, bf16, 0><<<grid, 256, 0, s>>>(Q, q_bstride, q_kstride, nrows,         \
                                                        static_cast<const bf16*>(wbox), box,    \
-                                                       kptr, klist, dst, dst_bstride, scale, tw); \
+                                                       kptr, klist, dst, dst_bstride, scale, tw, kmin, kmax, accumulate); \
         else if (rv)                                                                           \
             k_rows_adj<N, float, 1><<<grid, 256, 0, s>>>(Q, q_bstride, q_kstride, nrows,        \
                                                         static_cast<const float*>(wbox), box,  \
-                                                        kptr, klist, dst, dst_bstride, scale, tw); \
+                                                        kptr, klist, dst, dst_bstride, scale, tw, kmin, kmax, accumulate); \
         else                                                                                   \
             k_rows_adj<N, float, 0><<<grid, 256, 0, s>>>(Q, q_bstride, q_kstride, nrows,        \
                                                         static_cast<const float*>(wbox), box,  \
-                                                        kptr, klist, dst, dst_bstride, scale, tw); \
+                                                        kptr, klist, dst, dst_bstride, scale, tw, kmin, kmax, accumulate); \
         break;
         PCE_ROW_SIZES(X)
 #undef X

@@ -141,7 +141,20 @@ kt_cols_fwd(const float2* __restrict__ Z, long long z_bstride, long long z_kstri
     const unsigned t_hold = tbase + kTmHold, t_acc = tbase + kTmAcc;
     unsigned parity = 0;
     bool failed = false;
-    {
+    const int swl = tix_sw(lane, warp);
+    const int mode = sep.t1 < 0 ? kSepFinal : sep.mode;
+    if (mode & kSepLoadAcc) {
+        // slot-by-slot schedule: the frequency-domain sum of the earlier passes
+        tile_load(tile, A + b * a_bstride, NY, NXh, col0);
+        cp_async_wait_all();
+        __syncthreads();
+        float2 a[32];
+#pragma unroll
+        for (int q = 0; q < 32; ++q) a[q] = tile[4 * (lane + 32 * q) + swl];
+        tm_store32c(t_acc, a);
+        tm_wait_st();
+        __syncthreads();   // the staging tile is read: the transpose tiles are free again
+    } else {
         float2 z[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) z[j] = make_float2(0.f, 0.f);
@@ -149,13 +162,14 @@ kt_cols_fwd(const float2* __restrict__ Z, long long z_bstride, long long z_kstri
         for (int qq = 0; qq < 4; ++qq) tm_store8c(t_acc + 16 * qq, z);
         tm_wait_st();
     }
-    const int tend = sep.nterms;
-    if (tend > 0) {
-        wy_load(wys, sep.wrow, __ldg(&sep.korder[0]));
+    const int tbeg = sep.t1 < 0 ? 0 : sep.t0;
+    const int tend = sep.t1 < 0 ? sep.nterms : sep.t1;
+    if (tbeg < tend) {
+        wy_load(wys + (tbeg & 1) * NY, sep.wrow, __ldg(&sep.korder[tbeg]));
         cp_async_commit();
     }
     int cur_slot = -1;
-    for (int t = 0; t < tend; ++t) {
+    for (int t = tbeg; t < tend; ++t) {
         const int k = __ldg(&sep.korder[t]);
         const int sl = __ldg(&sep.kslot[k]);
         cp_async_wait_all();
@@ -250,9 +264,8 @@ kt_cols_fwd(const float2* __restrict__ Z, long long z_bstride, long long z_kstri
     }
     float2 acc[32];
     tm_load32c(t_acc, acc);
-    warp_fft1024<true, kTmSplit>(acc, tr, tw);
+    if (mode & kSepFinal) warp_fft1024<true, kTmSplit>(acc, tr, tw);
     __syncthreads();   // every warp is done with its transpose tile: stage the four columns
-    const int swl = tix_sw(lane, warp);
 #pragma unroll
     for (int mm = 0; mm < 32; ++mm) tile[4 * (lane + 32 * mm) + swl] = acc[mm];
     __syncthreads();
@@ -265,7 +278,7 @@ kt_cols_fwd(const float2* __restrict__ Z, long long z_bstride, long long z_kstri
 // Q receives, per slot, S_j on the slot box rows.
 template <bool PRUNE>
 __global__ void __launch_bounds__(kWColWarps * 32, 4)
-kt_cols_adj(const float2* __restrict__ V, long long v_bstride, const float2* __restrict__ hhT,
+kt_cols_adj(float2* __restrict__ V, long long v_bstride, const float2* __restrict__ hhT,
             const float2* __restrict__ hN, const Box* __restrict__ box, int NXh, float2* __restrict__ Q,
             long long q_bstride, long long q_kstride, const float2* __restrict__ tw, int* __restrict__ status,
             long long wait_limit, int skip_copy, SepTerms sep) {
@@ -289,10 +302,12 @@ kt_cols_adj(const float2* __restrict__ V, long long v_bstride, const float2* __r
     const unsigned t_hold = tbase + kTmHold, t_acc = tbase + kTmAcc;
     unsigned parity = 0;
     bool failed = false;
-    const int tend = sep.nterms;
+    const int tbeg = sep.t1 < 0 ? 0 : sep.t0;
+    const int tend = sep.t1 < 0 ? sep.nterms : sep.t1;
+    const int mode = sep.t1 < 0 ? 0 : sep.mode;
     const int swl = tix_sw(lane, warp);
 
-    if (tend > 0) wy_load(wys, sep.wrow, __ldg(&sep.korder[0]));
+    if (tbeg < tend) wy_load(wys + (tbeg & 1) * NY, sep.wrow, __ldg(&sep.korder[tbeg]));
     tile_load(tile, V + b * v_bstride, NY, NXh, col0);
     cp_async_wait_all();
     __syncthreads();
@@ -301,21 +316,43 @@ kt_cols_adj(const float2* __restrict__ V, long long v_bstride, const float2* __r
 #pragma unroll
         for (int q = 0; q < 32; ++q) vv[q] = tile[4 * (lane + 32 * q) + swl];
         __syncthreads();   // the staging tile is read: the transpose tiles are free
-        // the spectrum of the first term arrives while the FFT of V finishes
-        auto hook0 = [&] {
-            if (use_bulk && tend > 0 && lane == 0)
-                bulk_load(tr, hhT + ((long long)__ldg(&sep.korder[0]) * NXh + col) * NY, NY * sizeof(float2), bar,
-                          skip_copy);
-        };
-        warp_fft1024<false, kTmSplit, decltype(hook0)>(vv, tr, tw, hook0);
+        const bool first_copy = use_bulk && tbeg < tend;
+        if (mode & kSepSpecIn) {
+            // an earlier pass stored the column spectrum: no FFT
+            if (first_copy && lane == 0)
+                bulk_load(tr, hhT + ((long long)__ldg(&sep.korder[tbeg]) * NXh + col) * NY, NY * sizeof(float2),
+                          bar, skip_copy);
+        } else {
+            // the spectrum of the first term arrives while the FFT of V finishes
+            // (after it, when the transpose tiles first stage the spectrum's store)
+            auto hook0 = [&] {
+                if (first_copy && !(mode & kSepSpecOut) && lane == 0)
+                    bulk_load(tr, hhT + ((long long)__ldg(&sep.korder[tbeg]) * NXh + col) * NY, NY * sizeof(float2),
+                              bar, skip_copy);
+            };
+            warp_fft1024<false, kTmSplit, decltype(hook0)>(vv, tr, tw, hook0);
+            if (mode & kSepSpecOut) {
+                // the column spectrum back into V for the later passes (in place: this
+                // CTA is the only reader of these four columns)
+                __syncthreads();
+#pragma unroll
+                for (int q = 0; q < 32; ++q) tile[4 * (lane + 32 * q) + swl] = vv[q];
+                __syncthreads();
+                store_cols(V + b * v_bstride, tile, 0, NY, NXh, col0);
+                __syncthreads();
+                if (first_copy && lane == 0)
+                    bulk_load(tr, hhT + ((long long)__ldg(&sep.korder[tbeg]) * NXh + col) * NY, NY * sizeof(float2),
+                              bar, skip_copy);
+            }
+        }
         tm_store32c(t_hold, vv);
         tm_wait_st();
     }
     int prev_slot = -1;
-    for (int t = 0; t < tend; ++t) {
+    for (int t = tbeg; t < tend; ++t) {
         const int k = __ldg(&sep.korder[t]);
         const int sl = __ldg(&sep.kslot[k]);
-        const int kn = t + 1 < tend ? __ldg(&sep.korder[t + 1]) : -1;
+        const int kn = t + 1 < tend ? __ldg(&sep.korder[t + 1]) : -1;   // within this pass
         const bool first = sl != prev_slot;
         const bool last = kn < 0 || __ldg(&sep.kslot[kn]) != sl;
         prev_slot = sl;

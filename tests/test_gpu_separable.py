@@ -219,8 +219,9 @@ def test_tensor_memory_columns_match_oracle(torch_cuda, case):
     assert plan.slots() == gx if case.startswith("hats") else plan.slots() == 2
     ud = dev(torch, u)
     yo, xo = E.apply(u, w, h), E.apply_adjoint(u, w, h)
-    # variant 3 (pruned) needs every row factor inside 512 rows: not the 2 x 2 hats (1023 rows)
-    variants = (2,) if case == "hats_2x2" else (2, 3)
+    # variant 3 (pruned) needs every row factor inside 512 rows: not the 2 x 2 hats (1023 rows);
+    # variant 4 (slot by slot) needs two or more slots
+    variants = (2, 4) if case == "hats_2x2" else (2, 3, 4)
     if case == "hats_2x2":
         from paper_1604_04374_gb300 import PceError, pce
         with pytest.raises(PceError) as e:
@@ -279,12 +280,12 @@ def test_set_tuning_rejects_missing_variants(torch_cuda):
     from paper_1604_04374_gb300 import Plan, PceError, pce
     wy, wx, w, h, u = sep_problem(128, 64, 2, 2, 1, 93, random_h=True)
     p = Plan(wy=dev(torch, wy), wx=dev(torch, wx), h=dev(torch, h))   # 128 rows: general structures
-    for cv in (1, 2, 3):
+    for cv in (1, 2, 3, 4):
         with pytest.raises(PceError) as e:
             p.set_tuning(0, cv, 0)
         assert e.value.status == pce.PCE_ERR_UNSUPPORTED
     with pytest.raises(PceError) as e:
-        p.set_tuning(0, 4, 0)
+        p.set_tuning(0, 5, 0)
     assert e.value.status == pce.PCE_ERR_INVALID
     with pytest.raises(PceError) as e:       # one-warp rows need rows of 1024 points
         p.set_tuning(0, 0, 2)
@@ -295,7 +296,7 @@ def test_set_tuning_rejects_missing_variants(torch_cuda):
     p.close()
 
 
-@pytest.mark.parametrize("col_variant", [0, 2, 3])
+@pytest.mark.parametrize("col_variant", [0, 2, 3, 4])
 def test_bench_configuration_every_output_against_oracle(torch_cuda, col_variant):
     """The headline step as timed (1024 x 1024, m = 16, B = 8, separable plan, forward and
     adjoint as one graph launch of a two-lane batch), both one-warp column variants:
@@ -385,4 +386,29 @@ def test_one_warp_row_kernels_match_oracle(torch_cuda, case):
     plan.set_tuning(0, cv, 1)
     assert rel(host(plan.apply(ud)), y2) < 2e-6
     assert rel(host(plan.apply_adjoint(ud)), x2) < 2e-6
+    plan.close()
+
+
+def test_slot_by_slot_schedule_in_batches_and_graphs(torch_cuda):
+    """Column variant 4 (row and column pass per slot) inside a two-lane batch replayed
+    as a graph, with a batch that needs two launches per direction: equal to the
+    single-pass variant 2 up to rounding, and to the oracle."""
+    torch = torch_cuda
+    from paper_1604_04374_gb300 import Batch, Plan
+    wy, wx, w, h, u = sep_problem(1024, 256, 4, 4, 5, 100, random_h=True)
+    plan = Plan(wy=dev(torch, wy), wx=dev(torch, wx), h=dev(torch, h))
+    ud = dev(torch, u)
+    plan.set_tuning(3, 2, 1)
+    y2, x2 = host(plan.apply(ud)), host(plan.apply_adjoint(ud))
+    plan.set_tuning(3, 4, 1)
+    y4, x4 = host(plan.apply(ud)), host(plan.apply_adjoint(ud))
+    assert rel(y4, y2) < 2e-6 and rel(x4, x2) < 2e-6
+    assert rel(y4, C.apply(u, w, h)) < TOL and rel(x4, C.apply_adjoint(u, w, h)) < TOL
+    y, x = torch.empty_like(ud), torch.empty_like(ud)
+    b = Batch([(plan, ud, y, False), (plan, ud, x, True)], lanes=2)
+    b.launch()
+    b.launch()
+    torch.cuda.synchronize()
+    assert np.array_equal(host(y), y4) and np.array_equal(host(x), x4)
+    b.close()
     plan.close()
