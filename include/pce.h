@@ -527,6 +527,36 @@ pce_status pce_construct_projection_bspline_1d(const float* T, int n, int m, int
                                                float* w_out, void* stream);
 
 /*
+ * pce_construct_projection_2d -- the L2 projection of a sampled 2D
+ * time-varying impulse response onto the tensor-product hats of a gy x gx
+ * node grid (Corollary 4.3 with the 2D windows of the workloads:
+ * B_k(y) = B_{1,gy}(y1 - i/gy) B_{1,gx}(y2 - l/gx), k = i gx + l, Definition
+ * 2.2 per axis).
+ *
+ *   T      : device, [ny][nx][sy][sx] float32: T[j][a][b] is the impulse
+ *            response at input position j = (r, c) at the shift
+ *            d = (a - sy/2, b - sx/2) (integer halves), i.e. the kernel is
+ *            K(x_i, y_j) = T[j][(i - j) + (sy/2, sx/2)] inside the window and
+ *            0 outside it (periodic indices).
+ *   ny, nx : grid, each in [4, 4096]; sy, sx: the shift window, in
+ *            [1, ny] x [1, nx]; gy, gx: node grid, each in [2, min(n, 64)].
+ *   h_out  : device, [gy gx][ny][nx] float32: h_k on the shift grid (origin at
+ *            index 0, periodic), the projection coefficients, zero outside
+ *            the window (FP64 sums and an FP64 Gram inverse).
+ *   wy_out : device, [gy gx][ny] float32: the row factor of window k.
+ *   wx_out : device, [gy gx][nx] float32: its column factor.
+ *
+ * The windows are w_k = wy_k (x) wx_k, so pce_plan_create_separable({ny, nx},
+ * gy gx, wy_out, wx_out, h_out, ...) applies the projected operator; the
+ * Gram matrix of product windows is the Kronecker product of the two 1D
+ * Gram matrices, so its inverse costs two small inversions.  Allocates and
+ * frees temporary device memory and synchronises `stream`.
+ * PCE_ERR_INVALID for bad sizes or host pointers.
+ */
+pce_status pce_construct_projection_2d(const float* T, int ny, int nx, int sy, int sx, int gy, int gx,
+                                       float* h_out, float* wy_out, float* wx_out, void* stream);
+
+/*
  * pce_construct_svd_1d -- the truncated singular value decomposition of a
  * sampled time-varying impulse response (Section 5.1): T(x, y) ~ sum_k
  * sigma_k f_k(x) e_k(y) with h_k = sigma_k f_k and w_k = e_k, the best rank-m

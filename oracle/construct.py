@@ -114,6 +114,25 @@ def project_on_bsplines(T: np.ndarray, m: int, alpha: int) -> np.ndarray:
     return projection_coefficients(T, m, alpha) @ bspline_basis(T.shape[1], m, alpha).T
 
 
+def tensor_hat_basis(shape, gy: int, gx: int) -> np.ndarray:
+    """[P][m] matrix of the 2D windows B_k(y) = B_{1,gy}(y1 - i/gy) B_{1,gx}(y2 - l/gx) on the
+    grid y = (r/Ny, c/Nx), k = i gx + l (the tensor-product hats of Definition 2.2 per axis,
+    flattened row-major over the grid)."""
+    ny, nx = shape
+    by = hat_basis(ny, gy)          # [ny][gy]
+    bx = hat_basis(nx, gx)          # [nx][gx]
+    return np.einsum("ri,cl->rcil", by, bx).reshape(ny * nx, gy * gx)
+
+
+def projection_coefficients_2d(T: np.ndarray, shape, gy: int, gx: int) -> np.ndarray:
+    """L2 projection of every row T(x_d, .) of a 2D TVIR onto the tensor-product hats
+    (Corollary 4.3 with the 2D windows of tensor_hat_basis): c(d) = argmin_c ||T(d, .) - B c||
+    on the sample grid, c = (B^T B)^{-1} B^T T(d, .).  T is [P][P] (shift d, input position
+    j, both flattened row-major); returns C [P][m] (h_k = C[:, k] on the shift grid)."""
+    B = tensor_hat_basis(shape, gy, gx)
+    return np.linalg.solve(B.T @ B, B.T @ np.asarray(T, dtype=np.float64).T).T
+
+
 def interpolate_on_hats(T: np.ndarray, m: int) -> np.ndarray:
     """Interpolation at the nodes y_k = k/m: T_m(x, y) = sum_k T(x, y_k) B_{1,m}(y - y_k).
 

@@ -7,7 +7,7 @@ behind the C ABI of include/pce.h.  This package is the thin Python binding:
 tensors into them.  There is no CPU fallback: without the built library or a
 CUDA device every call raises.
 """
-from .pce import (Batch, PceError, Plan, apply_batch, construct_projection_1d, pce_construct_projection_1d, pce_construct_projection_bspline_1d, construct_svd_1d, pce_construct_svd_1d, pce_apply_batch, pce_batch_create, pce_batch_destroy,
+from .pce import (Batch, PceError, Plan, apply_batch, construct_projection_1d, construct_projection_2d, pce_construct_projection_1d, pce_construct_projection_2d, pce_construct_projection_bspline_1d, construct_svd_1d, pce_construct_svd_1d, pce_apply_batch, pce_batch_create, pce_batch_destroy,
                   pce_batch_info, pce_batch_launch, pce_batch_run, pce_plan_autotune, pce_plan_tuning,
                   pce_schedule_lpt, pce_apply, pce_apply_adjoint, pce_apply_noalloc, pce_backward,
                   pce_backward_workspace_bytes, pce_last_error_string,
@@ -15,7 +15,7 @@ from .pce import (Batch, PceError, Plan, apply_batch, construct_projection_1d, p
                   pce_plan_destroy, pce_plan_hhat, pce_plan_info, pce_plan_set_timing,
                   pce_plan_timing, load_library)
 
-__all__ = ["Batch", "apply_batch", "construct_projection_1d", "pce_construct_projection_1d", "pce_construct_projection_bspline_1d", "construct_svd_1d", "pce_construct_svd_1d", "pce_apply_batch", "pce_batch_create", "pce_batch_destroy",
+__all__ = ["Batch", "apply_batch", "construct_projection_1d", "construct_projection_2d", "pce_construct_projection_1d", "pce_construct_projection_2d", "pce_construct_projection_bspline_1d", "construct_svd_1d", "pce_construct_svd_1d", "pce_apply_batch", "pce_batch_create", "pce_batch_destroy",
            "pce_batch_info", "pce_batch_launch", "pce_batch_run", "pce_plan_autotune", "pce_plan_tuning",
            "pce_schedule_lpt", "PceError", "Plan", "pce_apply", "pce_apply_adjoint", "pce_apply_noalloc", "pce_backward",
            "pce_backward_workspace_bytes", "ConvolutionProduct", "convolution_product", "pce_last_error_string",

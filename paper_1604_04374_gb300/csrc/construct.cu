@@ -193,6 +193,168 @@ extern "C" pce_status pce_construct_projection_1d(const float* T, int n, int m, 
 }
 
 // ---------------------------------------------------------------------------
+// 2D: the L2 projection of every row T(x_d, .) of a 2D TVIR onto the
+// tensor-product hats B_k(y) = B_{1,gy}(y1 - i/gy) B_{1,gx}(y2 - l/gx), k = i gx + l
+// (Corollary 4.3 with the windows of the 2D workloads).  The Gram matrix of
+// product windows is the Kronecker product of the 1D Gram matrices, so its
+// inverse is the Kronecker product of two small inverses (host, FP64).
+//
+//   R[k][s]  = sum_j T[j][s] wy_k[row j] wx_k[col j]    (device, FP64 sums over the window's box)
+//   h_k[d_s] = sum_k' (Gy^-1 (x) Gx^-1)[k][k'] R[k'][s]  (device, FP64)
+//
+// with s = (a, b) a position of the shift window and d_s = (a - sy/2, b - sx/2).
+// ---------------------------------------------------------------------------
+namespace {
+
+// wy[k][r] = B_{1,gy}(r/ny - i/gy), wx[k][c] = B_{1,gx}(c/nx - l/gx), k = i gx + l
+__global__ void k_hat_factors(int ny, int nx, int gy, int gx, float* wy, float* wx) {
+    const int m = gy * gx;
+    const long long total = (long long)m * (ny + nx);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(e / (ny + nx)), q = (int)(e % (ny + nx));
+        const int i = k / gx, l = k % gx;
+        if (q < ny) {
+            double t = (double)q / ny - (double)i / gy;
+            t -= rint(t);
+            wy[(long long)k * ny + q] = (float)cardinal_bspline(1, gy * t);
+        } else {
+            const int c = q - ny;
+            double t = (double)c / nx - (double)l / gx;
+            t -= rint(t);
+            wx[(long long)k * nx + c] = (float)cardinal_bspline(1, gx * t);
+        }
+    }
+}
+
+// R[k][s] = sum over the box of window k of T[j][s] wy_k[r] wx_k[c] (FP64), one thread per (k, s)
+__global__ void k_proj2d_rhs(const float* __restrict__ T, int ny, int nx, int S, int gy, int gx,
+                             const float* __restrict__ wy, const float* __restrict__ wx, double* __restrict__ R) {
+    const int m = gy * gx;
+    const long long total = (long long)m * S;
+    const int hy = ny / gy + 2, hx = nx / gx + 2;   // samples on each side of a node
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(e / S), sidx = (int)(e % S);
+        const int i = k / gx, l = k % gx;
+        const int ry = (int)(((long long)i * ny) / gy), cx = (int)(((long long)l * nx) / gx);
+        const int spy = min(ny, 2 * hy + 1), spx = min(nx, 2 * hx + 1);
+        double acc = 0.0;
+        for (int tr = 0; tr < spy; ++tr) {
+            int r = (ry - hy + tr) % ny;
+            if (r < 0) r += ny;
+            const float fy = wy[(long long)k * ny + r];
+            if (fy == 0.f) continue;
+            for (int tc = 0; tc < spx; ++tc) {
+                int c = (cx - hx + tc) % nx;
+                if (c < 0) c += nx;
+                const float fx = wx[(long long)k * nx + c];
+                if (fx == 0.f) continue;
+                acc += (double)T[((long long)r * nx + c) * S + sidx] * (double)fy * (double)fx;
+            }
+        }
+        R[e] = acc;
+    }
+}
+
+// h[k][d_s] = sum_k' Ginv[k][k'] R[k'][s]; the rest of h was zeroed
+__global__ void k_proj2d_solve(const double* __restrict__ R, const double* __restrict__ Ginv, int m, int S, int ny,
+                               int nx, int sy, int sx, float* __restrict__ h) {
+    const long long total = (long long)m * S;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(e / S), sidx = (int)(e % S);
+        double acc = 0.0;
+        for (int kk = 0; kk < m; ++kk) acc += Ginv[(long long)k * m + kk] * R[(long long)kk * S + sidx];
+        const int a = sidx / sx, b = sidx % sx;
+        int dr = (a - sy / 2) % ny, dc = (b - sx / 2) % nx;
+        if (dr < 0) dr += ny;
+        if (dc < 0) dc += nx;
+        h[((long long)k * ny + dr) * nx + dc] = (float)acc;
+    }
+}
+
+// Gram matrix of the float32 1D hats of one axis (FP64), from their device copy
+bool gram_1d(const std::vector<float>& w, int g, int n, std::vector<double>& G) {
+    G.assign((size_t)g * g, 0.0);
+    for (int a = 0; a < g; ++a)
+        for (int b = 0; b < g; ++b) {
+            double s = 0.0;
+            for (int j = 0; j < n; ++j) s += (double)w[(size_t)a * n + j] * (double)w[(size_t)b * n + j];
+            G[(size_t)a * g + b] = s;
+        }
+    return true;
+}
+
+}  // namespace
+
+extern "C" pce_status pce_construct_projection_2d(const float* T, int ny, int nx, int sy, int sx, int gy, int gx,
+                                                  float* h_out, float* wy_out, float* wx_out, void* stream) {
+    if (ny < 4 || nx < 4 || ny > 4096 || nx > 4096)
+        return fail(PCE_ERR_INVALID, "ny and nx must be in [4, 4096] (got %d, %d)", ny, nx);
+    if (sy < 1 || sy > ny || sx < 1 || sx > nx)
+        return fail(PCE_ERR_INVALID, "the shift window %d x %d must lie in [1, ny] x [1, nx]", sy, sx);
+    if (gy < 2 || gx < 2 || gy > std::min(ny, 64) || gx > std::min(nx, 64))
+        return fail(PCE_ERR_INVALID, "the node grid %d x %d must lie in [2, min(n, 64)] per axis", gy, gx);
+    if (!pce_rt::is_device_ptr(T) || !pce_rt::is_device_ptr(h_out) || !pce_rt::is_device_ptr(wy_out) ||
+        !pce_rt::is_device_ptr(wx_out))
+        return fail(PCE_ERR_INVALID, "T, h_out, wy_out and wx_out must be device pointers");
+    const int m = gy * gx, S = sy * sx;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    double* R = nullptr;
+    double* Gi = nullptr;
+    auto cleanup = [&]() {
+        if (R) cudaFree(R);
+        if (Gi) cudaFree(Gi);
+    };
+    cudaError_t e = cudaMalloc(&R, sizeof(double) * (size_t)m * S);
+    if (e == cudaSuccess) e = cudaMalloc(&Gi, sizeof(double) * (size_t)m * m);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h_out, 0, sizeof(float) * (size_t)m * ny * nx, s);
+    if (e == cudaSuccess) {
+        k_hat_factors<<<grid_of((long long)m * (ny + nx)), 256, 0, s>>>(ny, nx, gy, gx, wy_out, wx_out);
+        k_proj2d_rhs<<<grid_of((long long)m * S), 256, 0, s>>>(T, ny, nx, S, gy, gx, wy_out, wx_out, R);
+        e = cudaGetLastError();
+    }
+    // the 1D hats of each axis (rows k = i gx of wy, k = l of wx) for the Gram matrices
+    std::vector<float> hy((size_t)m * ny), hx((size_t)m * nx);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hy.data(), wy_out, sizeof(float) * hy.size(), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hx.data(), wx_out, sizeof(float) * hx.size(), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cleanup();
+        return fail(e == cudaErrorMemoryAllocation ? PCE_ERR_OOM : PCE_ERR_CUDA, "2D projection set-up: %s",
+                    cudaGetErrorString(e));
+    }
+    std::vector<float> by((size_t)gy * ny), bx((size_t)gx * nx);
+    for (int i = 0; i < gy; ++i)
+        std::copy(hy.begin() + (size_t)(i * gx) * ny, hy.begin() + (size_t)(i * gx + 1) * ny, by.begin() + (size_t)i * ny);
+    std::copy(hx.begin(), hx.begin() + (size_t)gx * nx, bx.begin());
+    std::vector<double> Gy, Gx, Gyi, Gxi;
+    gram_1d(by, gy, ny, Gy);
+    gram_1d(bx, gx, nx, Gx);
+    if (!invert(Gy, gy, Gyi) || !invert(Gx, gx, Gxi)) {
+        cleanup();
+        return fail(PCE_ERR_INVALID, "the Gram matrix of the %d x %d hats on %d x %d samples is singular", gy, gx,
+                    ny, nx);
+    }
+    std::vector<double> Ginv((size_t)m * m);
+    for (int i = 0; i < gy; ++i)
+        for (int l = 0; l < gx; ++l)
+            for (int i2 = 0; i2 < gy; ++i2)
+                for (int l2 = 0; l2 < gx; ++l2)
+                    Ginv[(size_t)(i * gx + l) * m + (i2 * gx + l2)] = Gyi[(size_t)i * gy + i2] * Gxi[(size_t)l * gx + l2];
+    e = cudaMemcpyAsync(Gi, Ginv.data(), sizeof(double) * Ginv.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        k_proj2d_solve<<<grid_of((long long)m * S), 256, 0, s>>>(R, Gi, m, S, ny, nx, sy, sx, h_out);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cleanup();
+    if (e != cudaSuccess) return fail(PCE_ERR_CUDA, "2D projection: %s", cudaGetErrorString(e));
+    return PCE_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Truncated SVD of the TVIR (Section 5.1): T(x, y) ~ sum_k sigma_k f_k(x) e_k(y)
 // with h_k = sigma_k f_k and w_k = e_k, the best rank-m approximation.  The
 // leading singular subspace is found by the randomised range finder with

@@ -101,6 +101,9 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
     lib.pce_construct_projection_1d.restype = ctypes.c_int
     lib.pce_construct_projection_bspline_1d.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, P]
     lib.pce_construct_projection_bspline_1d.restype = ctypes.c_int
+    I = ctypes.c_int
+    lib.pce_construct_projection_2d.argtypes = [P, I, I, I, I, I, I, P, P, P, P]
+    lib.pce_construct_projection_2d.restype = ctypes.c_int
     lib.pce_construct_svd_1d.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_ulonglong, P, P, P, P]
     lib.pce_construct_svd_1d.restype = ctypes.c_int
@@ -291,6 +294,30 @@ def pce_construct_projection_1d(T_ptr: int, n: int, m: int, h_ptr: int, w_ptr: i
 def pce_construct_projection_bspline_1d(T_ptr: int, n: int, m: int, alpha: int, h_ptr: int, w_ptr: int,
                                         stream: int = 0) -> None:
     _check(load_library().pce_construct_projection_bspline_1d(T_ptr, n, m, alpha, h_ptr, w_ptr, stream))
+
+
+def pce_construct_projection_2d(T_ptr: int, ny: int, nx: int, sy: int, sx: int, gy: int, gx: int, h_ptr: int,
+                                wy_ptr: int, wx_ptr: int, stream: int = 0) -> None:
+    _check(load_library().pce_construct_projection_2d(T_ptr, ny, nx, sy, sx, gy, gx, h_ptr, wy_ptr, wx_ptr, stream))
+
+
+def construct_projection_2d(T, gy: int, gx: int, stream=None):
+    """(h [m, ny, nx], wy [m, ny], wx [m, nx]) of the L2 projection of the windowed 2D TVIR
+    T [ny, nx, sy, sx] (impulse response at every input position over a centred shift
+    window) onto the tensor-product hats of a gy x gx node grid (pce_construct_projection_2d);
+    Plan(wy=wy, wx=wx, h=h) applies the projected operator."""
+    import torch
+    _need_cuda_f32(T, "T")
+    if T.dim() != 4:
+        raise ValueError("T must be [ny, nx, sy, sx]")
+    ny, nx, sy, sx = (int(v) for v in T.shape)
+    m = gy * gx
+    h = torch.empty((m, ny, nx), dtype=torch.float32, device=T.device)
+    wy = torch.empty((m, ny), dtype=torch.float32, device=T.device)
+    wx = torch.empty((m, nx), dtype=torch.float32, device=T.device)
+    pce_construct_projection_2d(T.data_ptr(), ny, nx, sy, sx, gy, gx, h.data_ptr(), wy.data_ptr(), wx.data_ptr(),
+                                _stream_handle(stream))
+    return h, wy, wx
 
 
 def pce_construct_svd_1d(T_ptr: int, n: int, m: int, oversample: int, power_iters: int, seed: int,

@@ -75,6 +75,10 @@ def test_construction_and_flag_errors_without_a_gpu(lib):
     proj = lib.pce_construct_projection_1d
     for n, m in ((8, 4), (1 << 19, 4), (64, 2), (64, 65)):
         assert proj(None, n, m, None, None, None) == pce.PCE_ERR_INVALID, (n, m)
+    p2 = lib.pce_construct_projection_2d
+    for args in ((16, 16, 5, 5, 1, 4), (16, 16, 5, 5, 4, 65), (16, 16, 0, 5, 4, 4), (3, 16, 1, 5, 2, 2),
+                 (16, 16, 5, 5, 4, 4)):   # the last one: valid sizes, NULL (host) pointers
+        assert p2(None, *args, None, None, None, None) == pce.PCE_ERR_INVALID, args
     bproj = lib.pce_construct_projection_bspline_1d
     for n, m, alpha in ((8, 5, 2), (64, 4, 3), (64, 3, 2), (64, 65, 2), (64, 8, 0), (64, 8, 4), (64, 8, 2)):
         # the last one is valid in size and order but has NULL (host) pointers

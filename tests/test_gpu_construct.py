@@ -217,3 +217,94 @@ def test_svd_argument_errors(torch_cuda):
     with pytest.raises(PceError) as e:
         pce.pce_construct_svd_1d(Tc.data_ptr(), 64, 4, 10, 2, 0, h.data_ptr(), h.data_ptr())
     assert e.value.status == pce.PCE_ERR_INVALID
+
+
+# ------------------------------------------------------- 2D projection (Corollary 4.3)
+
+def tvir_2d_windowed(ny, nx, sy, sx, scale=0.6):
+    """[ny][nx][sy][sx] float32: at every input position the workloads' anisotropic PSF
+    (narrowed by `scale`) on the centred shift window."""
+    T = np.zeros((ny, nx, sy, sx), dtype=np.float32)
+    for r in range(ny):
+        for c in range(nx):
+            sxp, syp, th = synth.psf_params_2d(c / nx, r / ny)
+            full = synth.aniso_psf_2d(ny, nx, scale * sxp, scale * syp, th)
+            rows = (np.arange(sy) - sy // 2) % ny
+            cols = (np.arange(sx) - sx // 2) % nx
+            T[r, c] = full[np.ix_(rows, cols)].astype(np.float32)
+    return T
+
+
+def dense_from_windowed(T):
+    """The [P][P] TVIR (shift d, input position j) the windowed form stands for."""
+    ny, nx, sy, sx = T.shape
+    P = ny * nx
+    D = np.zeros((P, P))
+    for r in range(ny):
+        for c in range(nx):
+            for a in range(sy):
+                for b in range(sx):
+                    d = ((a - sy // 2) % ny) * nx + (b - sx // 2) % nx
+                    D[d, r * nx + c] += T[r, c, a, b]
+    return D
+
+
+@pytest.mark.parametrize("ny,nx,sy,sx,gy,gx", [(16, 24, 7, 9, 4, 3), (32, 32, 11, 11, 4, 4), (16, 16, 16, 16, 2, 2)])
+def test_projection_2d_matches_oracle(torch_cuda, ny, nx, sy, sx, gy, gx):
+    torch = torch_cuda
+    from paper_1604_04374_gb300 import construct_projection_2d
+    T = tvir_2d_windowed(ny, nx, sy, sx)
+    h, wy, wx = construct_projection_2d(dev(torch, T), gy, gx)
+    h, wy, wx = (t.cpu().numpy().astype(np.float64) for t in (h, wy, wx))
+    B = C.tensor_hat_basis((ny, nx), gy, gx)                       # [P][m]
+    np.testing.assert_allclose(np.einsum("kr,kc->krc", wy, wx).reshape(gy * gx, -1), B.T, atol=1e-6)
+    ref = C.projection_coefficients_2d(dense_from_windowed(T), (ny, nx), gy, gx).T.reshape(gy * gx, ny, nx)
+    assert np.linalg.norm(h - ref) / np.linalg.norm(ref) < 1e-5
+
+
+def test_projection_2d_feeds_a_separable_plan(torch_cuda):
+    """The construction's output applied by a separable plan equals the oracle's expansion,
+    and the approximation of the true operator improves from a 2 x 2 to a 4 x 4 node grid."""
+    torch = torch_cuda
+    from paper_1604_04374_gb300 import Plan, construct_projection_2d
+    ny = nx = 32
+    T = tvir_2d_windowed(ny, nx, 13, 13)
+    D = dense_from_windowed(T)
+    u = np.random.default_rng(14).standard_normal((2, ny, nx)).astype(np.float32)
+    idx = np.indices((ny, nx)).reshape(2, -1).T
+    P = ny * nx
+    # the true operator: y[i] = sum_j T[(i - j) mod grid][j] u[j]
+    K = np.zeros((P, P))
+    for a, x in enumerate(idx):
+        d = (x[None, :] - idx) % np.array([ny, nx])
+        K[a] = D[d[:, 0] * nx + d[:, 1], np.arange(P)]
+    y_true = u.reshape(2, -1).astype(np.float64) @ K.T
+    errs = []
+    for g in (2, 4):
+        h, wy, wx = construct_projection_2d(dev(torch, T), g, g)
+        plan = Plan(wy=wy.contiguous(), wx=wx.contiguous(), h=h.contiguous())
+        y = plan.apply(dev(torch, u)).cpu().numpy().astype(np.float64)
+        w = np.einsum("kr,kc->krc", wy.cpu().numpy(), wx.cpu().numpy())
+        ref = E.apply(u, w, h.cpu().numpy())
+        assert np.linalg.norm(y - ref) / np.linalg.norm(ref) < 1e-5
+        errs.append(np.linalg.norm(y.reshape(2, -1) - y_true) / np.linalg.norm(y_true))
+        plan.close()
+    assert errs[1] < errs[0], errs
+
+
+def test_projection_2d_argument_errors(torch_cuda):
+    torch = torch_cuda
+    from paper_1604_04374_gb300 import pce
+    from paper_1604_04374_gb300.pce import PceError
+    T = torch.zeros((16, 16, 5, 5), device="cuda")
+    h = torch.empty((16, 16, 16), device="cuda")
+    w = torch.empty((16, 16), device="cuda")
+    for args in ((16, 16, 5, 5, 1, 4), (16, 16, 5, 5, 4, 65), (16, 16, 0, 5, 4, 4), (16, 16, 17, 5, 4, 4),
+                 (2, 16, 1, 5, 2, 2)):
+        with pytest.raises(PceError) as e:
+            pce.pce_construct_projection_2d(T.data_ptr(), *args, h.data_ptr(), w.data_ptr(), w.data_ptr())
+        assert e.value.status == pce.PCE_ERR_INVALID
+    with pytest.raises(PceError) as e:       # host memory
+        Th = torch.zeros((16, 16, 5, 5))
+        pce.pce_construct_projection_2d(Th.data_ptr(), 16, 16, 5, 5, 4, 4, h.data_ptr(), w.data_ptr(), w.data_ptr())
+    assert e.value.status == pce.PCE_ERR_INVALID

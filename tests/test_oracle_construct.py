@@ -222,3 +222,72 @@ def test_bspline_projection_rates_and_nesting():
     for m in ms:
         assert (np.linalg.norm(T - C.project_on_bsplines(T, m, 3))
                 < np.linalg.norm(T - C.project_on_bsplines(T, m, 1)))
+
+
+def _tvir_2d(shape, seed):
+    """A smooth space-varying 2D TVIR T[d][j] (shift d, input position j, flattened):
+    the anisotropic PSF family of the workloads evaluated at every input position."""
+    ny, nx = shape
+    P = ny * nx
+    T = np.zeros((P, P))
+    for r in range(ny):
+        for c in range(nx):
+            sx, sy, th = synth.psf_params_2d(c / nx, r / ny)
+            T[:, r * nx + c] = synth.aniso_psf_2d(ny, nx, 0.6 * sx, 0.6 * sy, th).reshape(-1)
+    return T
+
+
+def test_tensor_hat_projection_idempotent_orthogonal_and_separable():
+    """Corollary 4.3 with 2D tensor-product hats: rows in the span come back exactly, the
+    residual is orthogonal to every window, and the Gram matrix factors as the Kronecker
+    product of the 1D ones (the windows are products of 1D hats), so that a TVIR that is a
+    product of 1D TVIRs has the product of the 1D projections."""
+    shape, gy, gx = (12, 16), 3, 4
+    P = 12 * 16
+    B = C.tensor_hat_basis(shape, gy, gx)
+    assert B.shape == (P, gy * gx)
+    np.testing.assert_allclose(B.sum(axis=1), 1.0, atol=1e-14)       # partition of unity
+    rng = np.random.default_rng(17)
+    C0 = rng.standard_normal((P, gy * gx))
+    np.testing.assert_allclose(C.projection_coefficients_2d(C0 @ B.T, shape, gy, gx), C0, atol=1e-9)
+    T = rng.standard_normal((P, P))
+    R = T - C.projection_coefficients_2d(T, shape, gy, gx) @ B.T
+    assert np.abs(R @ B).max() < 1e-10 * np.abs(T).max() * P
+    by, bx = C.hat_basis(12, gy), C.hat_basis(16, gx)
+    np.testing.assert_allclose(B.T @ B, np.kron(by.T @ by, bx.T @ bx), atol=1e-12)
+    # product TVIR: T[(a,b)][(r,c)] = Ty[a][r] Tx[b][c] -> coefficients are products
+    Ty, Tx = rng.standard_normal((12, 12)), rng.standard_normal((16, 16))
+    Tp = np.einsum("ar,bc->abrc", Ty, Tx).reshape(P, P)
+    cp = C.projection_coefficients_2d(Tp, shape, gy, gx)
+    ref = np.einsum("ai,bl->abil", C.projection_coefficients(Ty, gy), C.projection_coefficients(Tx, gx)).reshape(P, -1)
+    np.testing.assert_allclose(cp, ref, atol=1e-10)
+
+
+def test_tensor_hat_projection_error_falls_on_refined_node_grids():
+    """Nested node grids (2 x 2 -> 4 x 4 -> 8 x 8 on a 32 x 32 grid) give non-increasing
+    projection errors (nested subspaces), and the expansion built from the coefficients
+    applies the projected operator through Eq. 1.4."""
+    shape = (32, 32)
+    T = _tvir_2d(shape, 0)
+    errs = []
+    for g in (2, 4, 8):
+        B = C.tensor_hat_basis(shape, g, g)
+        Tm = C.projection_coefficients_2d(T, shape, g, g) @ B.T
+        errs.append(np.linalg.norm(T - Tm))
+    assert errs[1] <= errs[0] * (1 + 1e-12) and errs[2] <= errs[1] * (1 + 1e-12), errs
+    assert errs[2] < 0.5 * errs[0], errs
+    # Lemma 3.1 on the grid: h_k = coefficient column k (over shifts), w_k = window k
+    g = 4
+    Cf = C.projection_coefficients_2d(T, shape, g, g)
+    B = C.tensor_hat_basis(shape, g, g)
+    h = Cf.T.reshape(g * g, *shape)
+    w = B.T.reshape(g * g, *shape)
+    u = np.random.default_rng(3).standard_normal((1,) + shape)
+    Tm = Cf @ B.T                                            # Tm[d][j]
+    idx = np.indices(shape).reshape(2, -1).T
+    # y[i] = sum_j Tm[(i - j) mod grid][j] u[j]
+    y_ref = np.zeros(32 * 32)
+    for a, x in enumerate(idx):
+        d = ((x[None, :] - idx) % np.array(shape))
+        y_ref[a] = np.sum(Tm[d[:, 0] * 32 + d[:, 1], np.arange(32 * 32)] * u.reshape(-1))
+    np.testing.assert_allclose(E.apply(u, w, h).reshape(-1), y_ref, atol=1e-12)
