@@ -172,7 +172,7 @@ pce_status pce_plan_create_from_spectra(pce_plan_t* out, int ndims, const int64_
  *
  * The operator is exactly that of pce_plan_create with w_k = wy_k (x) wx_k
  * (the plan also builds everything the general path needs).  For Ny = 1024
- * with FP32 storage and the fused kernels, applies take a faster path: terms
+ * or 512 with FP32 storage and the fused kernels, applies take a faster path: terms
  * whose column factors are bitwise equal share one set of row transforms,
  * since R2C_x(wy_k(y) wx_j(x) u) = wy_k(y) R2C_x(wx_j u): the forward row
  * pass transforms one row set per distinct column factor instead of one per
@@ -437,8 +437,10 @@ pce_status pce_schedule_lpt(const double* cost, int n, int lanes, int* lane_of, 
  * pce_plan_autotune -- time the plan's applies (forward + adjoint of `batch`
  * right-hand sides of a fixed pattern, L2 flushed between repetitions, best
  * of three) for every candidate and keep the fastest:
- *   - column FFT variant for Ny = 1024: 0 = one-warp 32 x 32 four-step
- *     (radix 32), 1 = block Stockham (radix 8), 2 (separable plans) = the
+ *   - column FFT variant for Ny = 512, 1024 and 2048: 0 = one-warp four-step
+ *     (1024 points: 32 x 32; 512 points: 16 x 32 with the last radix-2 split
+ *     over lane pairs; 2048 points: two such 1024-point warps per column),
+ *     1 = block Stockham (radix 8); for Ny = 1024 also 2 (separable plans) = the
  *     one-warp four-step with each warp's held column and accumulator in
  *     tensor memory (more warps per SM), 3 = variant 2 with pruned column
  *     transforms (separable plans whose row factors each lie in 512 rows
@@ -470,7 +472,7 @@ pce_status pce_plan_tuning(pce_plan_t plan, int* chunk, int* col_variant, int* r
  * hand: chunk = right-hand sides per launch (0 = the plan's scratch chunk;
  * larger values are clamped to it), col_variant and row_variant as above.
  * A column variant the plan has no kernels for is PCE_ERR_UNSUPPORTED
- * (1 needs a 2D plan with 1024 or 2048 rows, 2 a separable plan with 1024
+ * (1 needs a 2D plan with 512, 1024 or 2048 rows, 2 a separable plan with 1024
  * rows, 3 such a plan whose row factors allow pruning, 4 such a plan with
  * two or more slots); row variants 1 and 2 need a 2D plan, 2 also rows of
  * 1024 points.  Changes no value an

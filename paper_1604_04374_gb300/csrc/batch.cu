@@ -488,8 +488,9 @@ extern "C" pce_status pce_plan_autotune(pce_plan_t p, int64_t batch, const char*
         if (cache_lookup(cache_path, key, c, v, rv, ms)) {
             p->tune_log.clear();
             p->run_chunk = std::min(c, cmax);
-            const bool ok = p->ndims == 2 && (p->ny == 1024 || p->ny == 2048) && (v < 2 || p->sep) &&
-                            (v != 3 || p->sep_prune) && (v != 4 || p->nslots > 1);
+            const bool ok = p->ndims == 2 && (p->ny == 512 || p->ny == 1024 || p->ny == 2048) &&
+                            (v < 2 || (p->sep && p->ny == 1024)) && (v != 3 || p->sep_prune) &&
+                            (v != 4 || p->nslots > 1);
             p->col_variant = ok ? v : 0;
             p->row_variant = (p->ndims == 2 && (rv < 2 || p->nx == 1024)) ? rv : 0;
             p->tuned_ms = ms;
@@ -499,7 +500,7 @@ extern "C" pce_status pce_plan_autotune(pce_plan_t p, int64_t batch, const char*
     // candidates
     // a sectioned plan runs its own kernels and chunks: one candidate, timed
     std::vector<int> variants = {0};
-    if (p->ndims == 2 && !p->sect && (p->ny == 1024 || p->ny == 2048)) variants.push_back(1);
+    if (p->ndims == 2 && !p->sect && (p->ny == 512 || p->ny == 1024 || p->ny == 2048)) variants.push_back(1);
     if (p->sep && !p->sect && p->ny == 1024) variants.push_back(2);
     if (p->sep && p->sep_prune && !p->sect && p->ny == 1024) variants.push_back(3);
     if (p->sep && p->nslots > 1 && !p->sect && p->ny == 1024) variants.push_back(4);
@@ -603,8 +604,8 @@ extern "C" pce_status pce_plan_set_tuning(pce_plan_t p, int chunk, int col_varia
     if (col_variant < 0 || col_variant > 4 || row_variant < 0 || row_variant > 2)
         return fail(PCE_ERR_INVALID, "column variant must be 0..4 and row variant 0..2 (got %d, %d)", col_variant,
                     row_variant);
-    if (col_variant == 1 && !(p->ndims == 2 && (p->ny == 1024 || p->ny == 2048)))
-        return fail(PCE_ERR_UNSUPPORTED, "column variant 1 needs a 2D plan with 1024 or 2048 rows");
+    if (col_variant == 1 && !(p->ndims == 2 && (p->ny == 512 || p->ny == 1024 || p->ny == 2048)))
+        return fail(PCE_ERR_UNSUPPORTED, "column variant 1 needs a 2D plan with 512, 1024 or 2048 rows");
     if (col_variant == 2 && !(p->sep && p->ny == 1024))
         return fail(PCE_ERR_UNSUPPORTED, "column variant 2 needs a separable plan with 1024 rows");
     if (col_variant == 3 && !(p->sep && p->sep_prune))

@@ -1,4 +1,5 @@
-// cols.cu -- instances of the column-pass kernels for NY = 16 .. 2048.
+// cols.cu -- instances of the column-pass kernels for NY = 16 .. 2048 (one-warp
+// kernels for NY = 512, 1024 and, two warps per column, 2048).
 #include "kernels.cuh"
 #include "wkernels.cuh"
 #include "wkernels2.cuh"
@@ -107,7 +108,7 @@ cudaError_t launch_cols_fwd(int ny, dim3 grid, cudaStream_t s, const float2* Z, 
                             long long wait_limit, int skip_copy, bool warp,
                             const void* hN2, const float2* tw2048l) {
     // the warp-FFT column kernels index these tables: refuse to launch without them
-    if ((ny == kWarpN || ny == kW2N) && warp && (!tw1024 || !hhT)) return cudaErrorInvalidValue;
+    if ((ny == 512 || ny == kWarpN || ny == kW2N) && warp && (!tw1024 || !hhT)) return cudaErrorInvalidValue;
     if (ny == kW2N && warp && (!tw2048l || !hN2)) return cudaErrorInvalidValue;
     if (ny == kW2N && warp) {
         dim3 g2 = grid;
@@ -128,6 +129,18 @@ cudaError_t launch_cols_fwd(int ny, dim3 grid, cudaStream_t s, const float2* Z, 
                 hscale, m, box, nxh, A, a_bstride, tw1024, status, wait_limit, skip_copy);
         else
             kw_cols_fwd<float2><<<grid, kWColWarps * 32, kWColSmem, s>>>(
+                Z, z_bstride, z_kstride, static_cast<const float2*>(hhT), static_cast<const float2*>(hN),
+                hscale, m, box, nxh, A, a_bstride, tw1024, status, wait_limit, skip_copy);
+        return cudaGetLastError();
+    }
+    if (ny == 512 && warp) {
+        constexpr int sm = kw_col_smem<512>();
+        if (lowp)
+            kw_cols_fwd<__half2, false, 512><<<grid, kWColWarps * 32, sm, s>>>(
+                Z, z_bstride, z_kstride, static_cast<const __half2*>(hhT), static_cast<const __half2*>(hN),
+                hscale, m, box, nxh, A, a_bstride, tw1024, status, wait_limit, skip_copy);
+        else
+            kw_cols_fwd<float2, false, 512><<<grid, kWColWarps * 32, sm, s>>>(
                 Z, z_bstride, z_kstride, static_cast<const float2*>(hhT), static_cast<const float2*>(hN),
                 hscale, m, box, nxh, A, a_bstride, tw1024, status, wait_limit, skip_copy);
         return cudaGetLastError();
@@ -158,7 +171,7 @@ cudaError_t launch_cols_adj(int ny, dim3 grid, cudaStream_t s, const float2* V, 
                             const float2* tw, const void* hhT, const float2* tw1024, int* status,
                             long long wait_limit, int skip_copy, bool warp,
                             const void* hN2, const float2* tw2048l) {
-    if ((ny == kWarpN || ny == kW2N) && warp && (!tw1024 || !hhT)) return cudaErrorInvalidValue;
+    if ((ny == 512 || ny == kWarpN || ny == kW2N) && warp && (!tw1024 || !hhT)) return cudaErrorInvalidValue;
     if (ny == kW2N && warp && (!tw2048l || !hN2)) return cudaErrorInvalidValue;
     if (ny == kW2N && warp) {
         if (lowp)
@@ -178,6 +191,18 @@ cudaError_t launch_cols_adj(int ny, dim3 grid, cudaStream_t s, const float2* V, 
                 box, nxh, Q, q_bstride, q_kstride, tw1024, status, wait_limit, skip_copy);
         else
             kw_cols_adj<false, float2><<<grid, kWColWarps * 32, kWColSmem, s>>>(
+                V, v_bstride, static_cast<const float2*>(hhT), static_cast<const float2*>(hN), hscale, m,
+                box, nxh, Q, q_bstride, q_kstride, tw1024, status, wait_limit, skip_copy);
+        return cudaGetLastError();
+    }
+    if (ny == 512 && warp) {
+        constexpr int sm = kw_col_smem<512>();
+        if (lowp)
+            kw_cols_adj<false, __half2, false, 512><<<grid, kWColWarps * 32, sm, s>>>(
+                V, v_bstride, static_cast<const __half2*>(hhT), static_cast<const __half2*>(hN), hscale, m,
+                box, nxh, Q, q_bstride, q_kstride, tw1024, status, wait_limit, skip_copy);
+        else
+            kw_cols_adj<false, float2, false, 512><<<grid, kWColWarps * 32, sm, s>>>(
                 V, v_bstride, static_cast<const float2*>(hhT), static_cast<const float2*>(hN), hscale, m,
                 box, nxh, Q, q_bstride, q_kstride, tw1024, status, wait_limit, skip_copy);
         return cudaGetLastError();
@@ -232,25 +257,41 @@ cudaError_t launch_plain_cols_inv(int ny, dim3 grid, cudaStream_t s, const float
     return cudaGetLastError();
 }
 
-cudaError_t launch_cols_fwd_sep(dim3 grid, cudaStream_t s, const float2* Z, long long z_bstride,
+cudaError_t launch_cols_fwd_sep(int ny, dim3 grid, cudaStream_t s, const float2* Z, long long z_bstride,
                                 long long z_kstride, const float2* hhT, const float2* hN, int m,
                                 const Box* box, int nxh, float2* A, long long a_bstride,
                                 const float2* tw1024, int* status, long long wait_limit, int skip_copy,
                                 const SepTerms& sep) {
-    kw_cols_fwd<float2, true><<<grid, kWColWarps * 32, kWColSmem, s>>>(
-        Z, z_bstride, z_kstride, hhT, hN, nullptr, m, box, nxh, A, a_bstride, tw1024, status, wait_limit,
-        skip_copy, sep);
+    if (!tw1024 || !hhT) return cudaErrorInvalidValue;
+    if (ny == kWarpN)
+        kw_cols_fwd<float2, true><<<grid, kWColWarps * 32, kWColSmem, s>>>(
+            Z, z_bstride, z_kstride, hhT, hN, nullptr, m, box, nxh, A, a_bstride, tw1024, status, wait_limit,
+            skip_copy, sep);
+    else if (ny == 512)
+        kw_cols_fwd<float2, true, 512><<<grid, kWColWarps * 32, kw_col_smem<512>(), s>>>(
+            Z, z_bstride, z_kstride, hhT, hN, nullptr, m, box, nxh, A, a_bstride, tw1024, status, wait_limit,
+            skip_copy, sep);
+    else
+        return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 
-cudaError_t launch_cols_adj_sep(dim3 grid, cudaStream_t s, const float2* V, long long v_bstride,
+cudaError_t launch_cols_adj_sep(int ny, dim3 grid, cudaStream_t s, const float2* V, long long v_bstride,
                                 const float2* hhT, const float2* hN, int m, const Box* box, int nxh,
                                 float2* Q, long long q_bstride, long long q_kstride,
                                 const float2* tw1024, int* status, long long wait_limit, int skip_copy,
                                 const SepTerms& sep) {
-    kw_cols_adj<false, float2, true><<<grid, kWColWarps * 32, kWColSmem, s>>>(
-        V, v_bstride, hhT, hN, nullptr, m, box, nxh, Q, q_bstride, q_kstride, tw1024, status, wait_limit,
-        skip_copy, sep);
+    if (!tw1024 || !hhT) return cudaErrorInvalidValue;
+    if (ny == kWarpN)
+        kw_cols_adj<false, float2, true><<<grid, kWColWarps * 32, kWColSmem, s>>>(
+            V, v_bstride, hhT, hN, nullptr, m, box, nxh, Q, q_bstride, q_kstride, tw1024, status, wait_limit,
+            skip_copy, sep);
+    else if (ny == 512)
+        kw_cols_adj<false, float2, true, 512><<<grid, kWColWarps * 32, kw_col_smem<512>(), s>>>(
+            V, v_bstride, hhT, hN, nullptr, m, box, nxh, Q, q_bstride, q_kstride, tw1024, status, wait_limit,
+            skip_copy, sep);
+    else
+        return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 
@@ -293,6 +334,12 @@ cudaError_t launch_cols_adj_full(int ny, dim3 grid, cudaStream_t s, const float2
                                  long long wait_limit, int skip_copy) {
     if (ny == kWarpN) {
         kw_cols_adj<true, float2><<<grid, kWColWarps * 32, kWColSmem, s>>>(
+            V, v_bstride, hhT, hN, nullptr, m, box, nxh, Q, q_bstride, q_kstride, tw1024, status, wait_limit,
+            skip_copy);
+        return cudaGetLastError();
+    }
+    if (ny == 512 && hhT && tw1024) {
+        kw_cols_adj<true, float2, false, 512><<<grid, kWColWarps * 32, kw_col_smem<512>(), s>>>(
             V, v_bstride, hhT, hN, nullptr, m, box, nxh, Q, q_bstride, q_kstride, tw1024, status, wait_limit,
             skip_copy);
         return cudaGetLastError();

@@ -209,6 +209,96 @@ k_rows_r2c(const float* __restrict__ src, long long src_bstride, int nrows,
     }
 }
 
+// F1 by row pairs: the two input rows are loaded once, then windowed and
+// transformed for every term (or slot) whose box holds them -- the CSR lists
+// kptr/klist of the adjoint row pass -- writing Z[b][k] rows (row - r0 of the
+// box), as k_rows_r2c<NX, true> does item by item.  The separable plans'
+// slots share every row, so the loads of u are amortised over the slots
+// instead of repeated per slot.  Grid (ceil(npairs / FPC), batch), 256
+// threads, 64 registers (4 CTAs per SM).
+template <int NX, typename WT = float>
+__global__ void __launch_bounds__(256, 4)
+k_rows_r2c_pairs(const float* __restrict__ src, long long src_bstride, int nrows, const WT* __restrict__ wbox,
+                 const Box* __restrict__ box, const int* __restrict__ kptr, const int* __restrict__ klist,
+                 float2* __restrict__ dst, long long dst_bstride, long long dst_kstride,
+                 const float2* __restrict__ tw) {
+    constexpr int T = NX / kR;
+    constexpr int FPC = 256 / T;
+    constexpr int NXh = NX / 2;
+    __shared__ float2 sbuf[FPC * fft_region(NX)];
+    const int slot = threadIdx.x / T;
+    const int j = threadIdx.x - slot * T;
+    float2* b0 = sbuf + slot * fft_region(NX);
+    float2* b1 = b0 + pad_len(NX);
+    const int npairs = (nrows + 1) / 2;
+    const int p = blockIdx.x * FPC + slot;
+    const int b = blockIdx.y;
+    const bool pv = p < npairs;
+    const int ga = 2 * p, gb = ga + 1;
+    const bool hb = pv && gb < nrows;
+    // uniform trip count over the CTA's row pairs (the FFT has CTA barriers)
+    int nk = 0;
+    for (int s2 = 0; s2 < FPC; ++s2) {
+        const int ps = blockIdx.x * FPC + s2;
+        if (ps < npairs) nk = max(nk, __ldg(&kptr[ps + 1]) - __ldg(&kptr[ps]));
+    }
+    const int kbeg = pv ? __ldg(&kptr[p]) : 0;
+    const int kcnt = pv ? __ldg(&kptr[p + 1]) - kbeg : 0;
+    float ua[kR], ub[kR];
+    {
+        const float* sa = src + b * src_bstride + (long long)(pv ? ga : 0) * NX;
+        const float* sb = src + b * src_bstride + (long long)(hb ? gb : 0) * NX;
+#pragma unroll
+        for (int r = 0; r < kR; ++r) {
+            ua[r] = pv && kcnt > 0 ? __ldg(sa + j + r * T) : 0.f;
+            ub[r] = hb && kcnt > 0 ? __ldg(sb + j + r * T) : 0.f;
+        }
+    }
+    for (int t = 0; t < nk; ++t) {
+        const bool act = t < kcnt;
+        const int k = act ? __ldg(&klist[kbeg + t]) : 0;
+        const Box bx = box[k];
+        const int la = wrap(ga - bx.r0, nrows), lb = wrap(gb - bx.r0, nrows);
+        const bool va = act && la < bx.nr;
+        const bool vb = act && hb && lb < bx.nr;
+        const WT* wa = wbox + bx.woff + (long long)(va ? la : 0) * bx.ldw;
+        const WT* wb = wbox + bx.woff + (long long)(vb ? lb : 0) * bx.ldw;
+        float2 v[kR];
+#pragma unroll
+        for (int r = 0; r < kR; ++r) {
+            const int n = j + r * T;
+            const int cc = wrap(n - bx.c0, NX);
+            const bool in = cc < bx.nc;
+            v[r] = make_float2(va && in ? ldw(wa + cc) * ua[r] : 0.f, vb && in ? ldw(wb + cc) * ub[r] : 0.f);
+        }
+        fft<NX, false>(v, j, b0, b1, tw);
+        // split the spectra of the two real rows
+        float2* xs = b0;
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < kR; ++r) xs[padi(j + r * T)] = v[r];
+        __syncthreads();
+        float2* da = dst + b * dst_bstride + k * dst_kstride + (long long)la * NXh;
+        float2* db = dst + b * dst_bstride + k * dst_kstride + (long long)lb * NXh;
+#pragma unroll
+        for (int r = 0; r < kR / 2; ++r) {
+            const int f = j + r * T;
+            float2 A, B;
+            if (f == 0) {
+                A = make_float2(v[0].x, v[kR / 2].x);
+                B = make_float2(v[0].y, v[kR / 2].y);
+            } else {
+                const float2 z = v[r];
+                const float2 zm = xs[padi(NX - f)];
+                A = make_float2(0.5f * (z.x + zm.x), 0.5f * (z.y - zm.y));
+                B = make_float2(0.5f * (z.y + zm.y), -0.5f * (z.x - zm.x));
+            }
+            if (va) da[f] = A;
+            if (vb) db[f] = B;
+        }
+    }
+}
+
 // ---------------------------------------------------------------- rows C2R
 // Packed half spectra -> real rows (two rows per complex inverse FFT), times scale.
 // Value at frequency f in [0, NX) of the spectrum whose packed half is p

@@ -36,6 +36,13 @@ cudaError_t launch_rows_r2c(int nx, bool window, dim3 grid, cudaStream_t s,
                             float2* dst, long long dst_bstride, long long dst_kstride,
                             const float2* tw, const float2* tw1024);
 
+// F1 by row pairs (k_rows_r2c_pairs): the same output as launch_rows_r2c with a
+// window, the terms (or slots) of each row pair from the CSR lists kptr/klist.
+cudaError_t launch_rows_r2c_pairs(int nx, int nb, cudaStream_t s, const float* src, long long src_bstride,
+                                  int nrows, const void* wbox, bool lowp, const Box* box, const int* kptr,
+                                  const int* klist, float2* dst, long long dst_bstride, long long dst_kstride,
+                                  const float2* tw);
+
 cudaError_t launch_rows_c2r(int nx, dim3 grid, cudaStream_t s, const float2* src,
                             long long src_bstride, int nrows, float* dst, long long dst_bstride,
                             float scale, const float2* tw, const float2* tw1024);
@@ -93,14 +100,14 @@ cudaError_t launch_sec_c2r(int lc, bool win, dim3 grid, cudaStream_t s, const fl
                            const void* wbox, bool lowp, float* dst, long long dst_bstride, int nyg, int nxg,
                            float scale, const float2* tw);
 
-// Separable windows, Ny = 1024 (one-warp column kernels): Z / Q hold one slot
-// per column factor, box[] is indexed by slot.
-cudaError_t launch_cols_fwd_sep(dim3 grid, cudaStream_t s, const float2* Z, long long z_bstride,
+// Separable windows, Ny = 1024 or 512 (one-warp column kernels): Z / Q hold
+// one slot per column factor, box[] is indexed by slot.
+cudaError_t launch_cols_fwd_sep(int ny, dim3 grid, cudaStream_t s, const float2* Z, long long z_bstride,
                                 long long z_kstride, const float2* hhT, const float2* hN, int m,
                                 const Box* box, int nxh, float2* A, long long a_bstride,
                                 const float2* tw1024, int* status, long long wait_limit, int skip_copy,
                                 const SepTerms& sep);
-cudaError_t launch_cols_adj_sep(dim3 grid, cudaStream_t s, const float2* V, long long v_bstride,
+cudaError_t launch_cols_adj_sep(int ny, dim3 grid, cudaStream_t s, const float2* V, long long v_bstride,
                                 const float2* hhT, const float2* hN, int m, const Box* box, int nxh,
                                 float2* Q, long long q_bstride, long long q_kstride,
                                 const float2* tw1024, int* status, long long wait_limit, int skip_copy,

@@ -513,9 +513,9 @@ pce_status make_twiddles_l1(pce_plan* p, cudaStream_t s) {
 
 pce_status make_twiddles(pce_plan* p, cudaStream_t s) {
     if (p->l1) return make_twiddles_l1(p, s);
-    // the one-warp 1024-point FFT serves transforms of 1024 and, two warps per
-    // column, columns of 2048
-    if (p->nx == 1024 || (p->ndims == 2 && (p->ny == 1024 || p->ny == 2048))) {
+    // the one-warp FFTs index the 1024-point four-step table: transforms of
+    // 1024, columns of 2048 (two warps per column) and of 512 (rows 2p of it)
+    if (p->nx == 1024 || (p->ndims == 2 && (p->ny == 512 || p->ny == 1024 || p->ny == 2048))) {
         pce_status st0 = dev_alloc(&p->tw1024, 1024);
         if (st0) return st0;
         k_twiddles_1024<<<4, 256, 0, s>>>(p->tw1024);
@@ -870,7 +870,7 @@ pce_status create_common(pce_plan_t* out, int ndims, const int64_t* shape, int m
         cudaError_t e1 = cudaGetLastError();
         if (e1) return bail(fail(PCE_ERR_CUDA, "spectrum conjugation: %s", cudaGetErrorString(e1)));
     }
-    if (ndims == 2 && ny == 1024) {
+    if (ndims == 2 && (ny == 1024 || ny == 512)) {
         if ((st = dev_alloc(&p->hhT, (size_t)m * ny * nxh))) return bail(st);
         k_transpose_hh<<<grid_for((long long)m * ny * nxh), 256, 0, s>>>(p->hh, m, ny, nxh, p->hhT);
         cudaError_t e1 = cudaGetLastError();
@@ -909,10 +909,10 @@ __global__ void k_outer(const float* __restrict__ wy, const float* __restrict__ 
 // Slots of the separable fast path: one per distinct column factor (bitwise),
 // its column box, the union of its terms' row supports, the work lists of the
 // row passes over the slots, and the term order grouped by slot.  Only for
-// Ny = 1024 with FP32 storage; otherwise the plan keeps the general path.
+// Ny = 1024 or 512 with FP32 storage; otherwise the plan keeps the general path.
 pce_status setup_separable(pce_plan* p, const float* wy, const float* wx, cudaStream_t s) {
     const int m = p->m, ny = p->ny, nx = p->nx;
-    if (p->ndims != 2 || ny != 1024 || p->lowp || (p->flags & PCE_FLAG_UNFUSED)) return PCE_OK;
+    if (p->ndims != 2 || (ny != 1024 && ny != 512) || p->lowp || (p->flags & PCE_FLAG_UNFUSED)) return PCE_OK;
     std::vector<float> hy((size_t)m * ny), hx((size_t)m * nx);
     PCE_CK(cudaMemcpyAsync(hy.data(), wy, sizeof(float) * hy.size(), cudaMemcpyDeviceToHost, s));
     PCE_CK(cudaMemcpyAsync(hx.data(), wx, sizeof(float) * hx.size(), cudaMemcpyDeviceToHost, s));
@@ -997,10 +997,11 @@ pce_status setup_separable(pce_plan* p, const float* wy, const float* wx, cudaSt
     PCE_CK(cudaMemcpyAsync(p->skptr, kptr.data(), sizeof(int) * kptr.size(), cudaMemcpyHostToDevice, s));
     if (!klist.empty())
         PCE_CK(cudaMemcpyAsync(p->sklist, klist.data(), sizeof(int) * klist.size(), cudaMemcpyHostToDevice, s));
-    // pruned column kernels: every active term's row factor inside 512 rows that
-    // start on a multiple of 32 (the hats of a node grid with 4 or more rows)
+    // pruned column kernels (Ny = 1024): every active term's row factor inside
+    // 512 rows that start on a multiple of 32 (the hats of a node grid with 4 or
+    // more rows)
     std::vector<int> kq0(m, 0);
-    bool prune = !korder.empty() && p->hhT != nullptr && p->hN != nullptr;
+    bool prune = ny == 1024 && !korder.empty() && p->hhT != nullptr && p->hN != nullptr;
     for (int k : korder) {
         std::vector<unsigned char> rf(ny, 0);
         for (int r = 0; r < ny; ++r) rf[r] = hy[(size_t)k * ny + r] != 0.f;
@@ -1577,7 +1578,7 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
     // separable fast path: one-warp column kernels only; variant 2 keeps the
     // per-warp column state in tensor memory
     const bool sepx = p->sep && warp;
-    const bool septm = sepx && (colv == 2 || colv == 3 || colv == 4);
+    const bool septm = sepx && ny == 1024 && (colv == 2 || colv == 3 || colv == 4);
     // variant 4: row pass and column pass slot by slot, so that one slot's Z and
     // the accumulator A stay in L2 between them (slots without terms skipped)
     std::vector<int> active;
@@ -1667,6 +1668,9 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
         } else if (sepx && !adjoint) {
             if (p->nsitems > 0)
                 e = timed(p, PCE_KERNEL_ROWS_R2C_WINDOW, s, [&] {
+                    if (rowv == 2)
+                        return pce::launch_rows_r2c_pairs(nx, nb, s, src, P, ny, p->wxbox, false, p->d_vbox,
+                                                          p->skptr, p->sklist, scr.Z, zb, p->zk_s, p->twx);
                     return pce::launch_rows_r2c(nx, true, dim3(r2c_blocks(p->nsitems, nx), nb), s, src, P, ny,
                                                 p->wxbox, false, p->d_vbox, p->sitems, p->nsitems, scr.Z, zb,
                                                 p->zk_s, p->twx, p->tw1024);
@@ -1677,7 +1681,7 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
                         return pce::launch_cols_fwd_sep_tm(dim3(nb, (nxh + cpc - 1) / cpc), s, scr.Z, zb, p->zk_s,
                                                            tm_hT, tm_hN, p->d_vbox, nxh, scr.A, ab, p->tw1024,
                                                            p->d_status, p->wait_limit, p->skip_copy, septp);
-                    return pce::launch_cols_fwd_sep(dim3(nb, (nxh + cpc - 1) / cpc), s, scr.Z, zb, p->zk_s,
+                    return pce::launch_cols_fwd_sep(ny, dim3(nb, (nxh + cpc - 1) / cpc), s, scr.Z, zb, p->zk_s,
                                                     p->hhT, p->hN, m, p->d_vbox, nxh, scr.A, ab, p->tw1024,
                                                     p->d_status, p->wait_limit, p->skip_copy, sept);
                 });
@@ -1700,7 +1704,7 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
                         return pce::launch_cols_adj_sep_tm(dim3(nb, (nxh + cpc - 1) / cpc), s, scr.A, ab, tm_hT,
                                                            tm_hN, p->d_vbox, nxh, scr.Z, zb, p->zk_s, p->tw1024,
                                                            p->d_status, p->wait_limit, p->skip_copy, septp);
-                    return pce::launch_cols_adj_sep(dim3(nb, (nxh + cpc - 1) / cpc), s, scr.A, ab, p->hhT, p->hN,
+                    return pce::launch_cols_adj_sep(ny, dim3(nb, (nxh + cpc - 1) / cpc), s, scr.A, ab, p->hhT, p->hN,
                                                     m, p->d_vbox, nxh, scr.Z, zb, p->zk_s, p->tw1024,
                                                     p->d_status, p->wait_limit, p->skip_copy, sept);
                 });
@@ -1713,6 +1717,9 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
         } else if (!adjoint) {
             if (p->nitems > 0)
                 e = timed(p, PCE_KERNEL_ROWS_R2C_WINDOW, s, [&] {
+                    if (rowv == 2)
+                        return pce::launch_rows_r2c_pairs(nx, nb, s, src, P, ny, wstore(p), p->lowp, p->d_box,
+                                                          p->kptr, p->klist, scr.Z, zb, zk, p->twx);
                     return pce::launch_rows_r2c(nx, true, dim3(r2c_blocks(p->nitems, nx), nb), s, src,
                                                 P, ny, wstore(p), p->lowp, p->d_box, p->items, p->nitems, scr.Z,
                                                 zb, zk, p->twx, p->tw1024);

@@ -43,6 +43,35 @@ cudaError_t launch_rows_r2c(int nx, bool window, dim3 grid, cudaStream_t s,
     return cudaGetLastError();
 }
 
+cudaError_t launch_rows_r2c_pairs(int nx, int nb, cudaStream_t s, const float* src, long long src_bstride,
+                                  int nrows, const void* wbox, bool lowp, const Box* box, const int* kptr,
+                                  const int* klist, float2* dst, long long dst_bstride, long long dst_kstride,
+                                  const float2* tw) {
+    using bf16 = __nv_bfloat16;
+    const int npairs = (nrows + 1) / 2;
+    switch (nx) {
+#define X(N)                                                                                      \
+    case N: {                                                                                     \
+        const int fpc = rows_pairs_per_cta(N);                                                    \
+        const dim3 grid((npairs + fpc - 1) / fpc, nb);                                            \
+        if (lowp)                                                                                 \
+            k_rows_r2c_pairs<N, bf16><<<grid, 256, 0, s>>>(src, src_bstride, nrows,                \
+                                                         static_cast<const bf16*>(wbox), box, kptr, \
+                                                         klist, dst, dst_bstride, dst_kstride, tw); \
+        else                                                                                      \
+            k_rows_r2c_pairs<N, float><<<grid, 256, 0, s>>>(src, src_bstride, nrows,               \
+                                                          static_cast<const float*>(wbox), box, kptr, \
+                                                          klist, dst, dst_bstride, dst_kstride, tw); \
+        break;                                                                                    \
+    }
+        PCE_ROW_SIZES(X)
+#undef X
+        default:
+            return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_rows_c2r(int nx, dim3 grid, cudaStream_t s, const float2* src,
                             long long src_bstride, int nrows, float* dst, long long dst_bstride,
                             float scale, const float2* tw, const float2* /*tw1024*/) {

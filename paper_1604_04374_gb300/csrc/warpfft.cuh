@@ -179,14 +179,106 @@ __device__ __forceinline__ void warp_fft1024(float2 (&v)[32], float2* tile, cons
     dft32<INV, false, OUT_HALF>(v);
 }
 
-// Value X[1024 - f] for f = lane + 32 m, from the lane holding it: lane
-// (32 - lane) & 31, register 31 - m; lane 0 holds its own partner in
-// register (32 - m) & 31.
-__device__ __forceinline__ float2 warp_partner(const float2 (&v)[32], int lane, int M) {
+// In-register 16-point DFT, natural order in and out: n = 4 n1 + n2,
+// k = k1 + 4 k2, X[k1 + 4 k2] = sum_n2 W4^{n2 k2} W16^{n2 k1} sum_n1 x[4 n1 + n2] W4^{n1 k1}.
+template <bool INV>
+__device__ __forceinline__ void dft16(float2 (&a)[16]) {
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+        float2 x[4] = {a[n2], a[4 + n2], a[8 + n2], a[12 + n2]};
+        Dft<4, INV>::run(x);
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) a[4 * k1 + n2] = tw32<INV>(x[k1], 2 * n2 * k1);   // W16 = W32^2
+    }
+    float2 out[16];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+        float2 y[4] = {a[4 * k1], a[4 * k1 + 1], a[4 * k1 + 2], a[4 * k1 + 3]};
+        Dft<4, INV>::run(y);
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) out[k1 + 4 * k2] = y[k2];
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) a[i] = out[i];
+}
+
+// One-warp 512-point FFT with the layout of warp_fft1024: lane l holds
+// v[q] = x[l + 32 q] (q < 16) on entry and v[m] = X[l + 32 m] on exit.  With
+// n = l + 32 q and k = p + 16 j (p < 16, j < 32):
+//   X[p + 16 j] = sum_l W32^{l j} W512^{l p} sum_q x[l + 32 q] W16^{q p},
+//   1. a 16-point DFT over q in each lane's registers,
+//   2. the twiddles W512^{l p} = W1024^{2 l p} (the 1024-point table, rows 2p),
+//   3. the 32 x 16 block y[l][p] through a warp-private shared tile (the 16
+//      entries of row l XOR-swizzled by l & 15: conflict-free per half-warp),
+//   4. the 32-point DFTs over l, one per p, split by decimation in frequency
+//      over the lane pair (p, p + 16): lane p + 16 s forms
+//      a_s[l'] = (y[l'][p] + (-1)^s y[l' + 16][p]) W32^{s l'} (l' < 16) from the
+//      tile and takes its 16-point DFT, which gives X[p + 16 (2 j' + s)]
+//      = X[lane + 32 j'] (j' < 16): the natural layout again.
+// tile: 512 float2 private to the warp.  Hook and SPLIT as for warp_fft1024.
+template <bool INV, bool SPLIT = true, typename Hook = NoHook>
+__device__ __forceinline__ void warp_fft512(float2 (&v)[16], float2* tile, const float2* __restrict__ tw,
+                                            Hook hook = Hook()) {
+    const int lane = threadIdx.x & 31;
+    dft16<INV>(v);
+    __syncwarp();
+    if constexpr (SPLIT) {
+        // W512^{l p}, p = 8 a + b: W1024^{16 l a} W1024^{2 l b}
+        float2 wb[8], wa;
+#pragma unroll
+        for (int q = 1; q < 8; ++q) wb[q] = __ldg(&tw[2 * q * 32 + lane]);
+        wa = __ldg(&tw[16 * 32 + lane]);
+#pragma unroll
+        for (int p = 1; p < 16; ++p) {
+            const int bq = p & 7;
+            const float2 t = p < 8 ? wb[bq] : (bq == 0 ? wa : cmul(wa, wb[bq]));
+            v[p] = INV ? cmulc(v[p], t) : cmul(v[p], t);
+        }
+    } else {
+#pragma unroll
+        for (int p = 1; p < 16; ++p) {
+            const float2 t = __ldg(&tw[2 * p * 32 + lane]);
+            v[p] = INV ? cmulc(v[p], t) : cmul(v[p], t);
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int p = 0; p < 16; ++p) tile[lane * 16 + (p ^ (lane & 15))] = v[p];
+    __syncwarp();
+    const int p = lane & 15;
+    const bool odd = lane >= 16;
+    const float sg = odd ? -1.f : 1.f;
+#pragma unroll
+    for (int l = 0; l < 16; ++l) {
+        const float2 y0 = tile[l * 16 + (p ^ l)];
+        const float2 y1 = tile[(l + 16) * 16 + (p ^ l)];
+        float2 a = make_float2(fmaf(sg, y1.x, y0.x), fmaf(sg, y1.y, y0.y));
+        if (l > 0 && odd) a = tw32<INV>(a, l);
+        v[l] = a;
+    }
+    __syncwarp();
+    hook();
+    dft16<INV>(v);
+}
+
+// One-warp FFT of NY = 512 or 1024 points (NY / 32 values per lane).
+template <int NY, bool INV, bool SPLIT = true, typename Hook = NoHook>
+__device__ __forceinline__ void warp_fft(float2 (&v)[NY / 32], float2* tile, const float2* __restrict__ tw,
+                                         Hook hook = Hook()) {
+    static_assert(NY == 512 || NY == 1024, "one-warp FFT of 512 or 1024 points");
+    if constexpr (NY == 1024) warp_fft1024<INV, SPLIT, Hook>(v, tile, tw, hook);
+    else warp_fft512<INV, SPLIT, Hook>(v, tile, tw, hook);
+}
+
+// Value X[NY - f] for f = lane + 32 m (NY = 32 Q), from the lane holding it:
+// lane (32 - lane) & 31, register Q - 1 - m; lane 0 holds its own partner in
+// register (Q - m) & (Q - 1).
+template <int Q>
+__device__ __forceinline__ float2 warp_partner(const float2 (&v)[Q], int lane, int M) {
     float2 z;
-    z.x = __shfl_sync(0xffffffffu, v[31 - M].x, (32 - lane) & 31);
-    z.y = __shfl_sync(0xffffffffu, v[31 - M].y, (32 - lane) & 31);
-    if (lane == 0) z = v[(32 - M) & 31];
+    z.x = __shfl_sync(0xffffffffu, v[Q - 1 - M].x, (32 - lane) & 31);
+    z.y = __shfl_sync(0xffffffffu, v[Q - 1 - M].y, (32 - lane) & 31);
+    if (lane == 0) z = v[(Q - M) & (Q - 1)];
     return z;
 }
 

@@ -1,7 +1,7 @@
-// wkernels.cuh -- warp-FFT column kernels for columns of length Ny = 1024.
+// wkernels.cuh -- warp-FFT column kernels for columns of length Ny = 1024 and 512.
 // They compute exactly what the generic column kernels of kernels.cuh
 // compute, with the same global layouts (the spectra also in a transposed
-// copy), but every 1024-point column FFT is done by one warp (warpfft.cuh):
+// copy), but every column FFT (1024 or 512 points) is done by one warp (warpfft.cuh):
 // no CTA barrier inside an FFT and one shared-memory transpose per FFT,
 // where the generic kernel needs three barrier-separated exchanges.
 // (For the row passes the generic kernels stay faster: they keep 48 warps
@@ -23,10 +23,18 @@ namespace pce {
 
 constexpr int kWarpN = 1024;
 constexpr int kWColWarps = 4;          // columns per CTA of the column kernels
-// shared memory: the column tile, one 1024-point transpose tile per warp, and
-// two 1024-float buffers of row factors (separable windows)
-constexpr int kWColSmem = (kWarpN * kWColWarps + kWColWarps * kWarpN) * (int)sizeof(float2) +
-                          2 * kWarpN * (int)sizeof(float);
+// shared memory for columns of NY points: the column tile, one NY-point
+// transpose tile per warp, and two NY-float buffers of row factors (separable
+// windows)
+template <int NY>
+constexpr int kw_col_smem() {
+    return (NY * kWColWarps + kWColWarps * NY) * (int)sizeof(float2) + 2 * NY * (int)sizeof(float);
+}
+constexpr int kWColSmem = kw_col_smem<kWarpN>();
+// resident CTAs per SM the column kernels are compiled for: 3 at 1024 points
+// (168 registers), 5 at 512 points (at most 102 registers)
+template <int NY>
+constexpr int kw_col_min_ctas() { return NY == kWarpN ? 3 : 5; }
 
 // element (row, column c < 4) of the swizzled column tile
 __device__ __forceinline__ int tix(int row, int c) { return row * kWColWarps + (c ^ ((row >> 2) & 3)); }
@@ -102,38 +110,41 @@ __device__ __forceinline__ void tile_load(float2* tile, const float2* __restrict
     cp_async_commit();
 }
 
-// Separable windows: cooperative async copy of row factor wy_k (1024 floats)
+// Separable windows: cooperative async copy of row factor wy_k (NY floats)
 // into one of the two row-factor buffers (committed with the next group).
+template <int NY = kWarpN>
 __device__ __forceinline__ void wy_load(float* dst, const float* __restrict__ wrow, int k) {
-    const float* src = wrow + (long long)k * kWarpN;
-    for (int e = threadIdx.x; e < kWarpN / 4; e += kWColWarps * 32) cp_async16(dst + 4 * e, src + 4 * e);
+    const float* src = wrow + (long long)k * NY;
+    for (int e = threadIdx.x; e < NY / 4; e += kWColWarps * 32) cp_async16(dst + 4 * e, src + 4 * e);
 }
 
 // The DC/Nyquist column (column 0 of tile 0): separate the FFT of
 // DC + i Nyquist at f = lane + 32 m into A (DC) and B (Nyquist).
-__device__ __forceinline__ void warp_split(const float2 (&v)[32], int lane, int m, float2& A, float2& B) {
+template <int Q>
+__device__ __forceinline__ void warp_split(const float2 (&v)[Q], int lane, int m, float2& A, float2& B) {
     split_dc_nyq(v[m], warp_partner(v, lane, m), A, B);
 }
 
-// F2 for Ny = 1024.  Grid (batch, NXh / 4), 128 threads, kWColSmem bytes.
-// hhT: [m][NXh][1024] (column c's spectrum contiguous; c = 0: DC column),
-// hN: [m][1024] (Nyquist column).
+// F2 for Ny = NY (1024 or 512).  Grid (batch, NXh / 4), 128 threads,
+// kw_col_smem<NY>() bytes.
+// hhT: [m][NXh][NY] (column c's spectrum contiguous; c = 0: DC column),
+// hN: [m][NY] (Nyquist column).
 // SEP = false: Z holds one slot per term (box[k] rows of w_k . u's row spectra).
 // SEP = true: Z holds one slot per column factor (box[] indexed by slot), each
 // term's column is its slot's column times wy_k (row factor) on load, and a
 // slot's tile is loaded once for all of its terms.
-template <typename HT = float2, bool SEP = false>
-__global__ void __launch_bounds__(kWColWarps * 32, 3)
+template <typename HT = float2, bool SEP = false, int NY = kWarpN>
+__global__ void __launch_bounds__(kWColWarps * 32, kw_col_min_ctas<NY>())
 kw_cols_fwd(const float2* __restrict__ Z, long long z_bstride, long long z_kstride,
             const HT* __restrict__ hhT, const HT* __restrict__ hN, const float* __restrict__ hscale, int m,
             const Box* __restrict__ box, int NXh, float2* __restrict__ A, long long a_bstride,
             const float2* __restrict__ tw, int* __restrict__ status, long long wait_limit, int skip_copy,
             SepTerms sep = SepTerms{}) {
-    constexpr int NY = kWarpN;
+    constexpr int QN = NY / 32;   // values per lane
     extern __shared__ float2 smem[];
     float2* tile = smem;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float2* tr = smem + NY * kWColWarps + warp * kWarpN;
+    float2* tr = smem + NY * kWColWarps + warp * NY;
     const int b = blockIdx.x;
     const int col0 = blockIdx.y * kWColWarps;
     const int col = col0 + warp;
@@ -147,9 +158,9 @@ kw_cols_fwd(const float2* __restrict__ Z, long long z_bstride, long long z_kstri
     unsigned parity = 0;
     bool failed = false;
 
-    float2 acc[32];
+    float2 acc[QN];
 #pragma unroll
-    for (int i = 0; i < 32; ++i) acc[i] = make_float2(0.f, 0.f);
+    for (int i = 0; i < QN; ++i) acc[i] = make_float2(0.f, 0.f);
     // the sequence of terms: general, every term with a nonempty box in index
     // order (slot = term); separable, sep.korder (slot = sep.kslot[term])
     const int tend = SEP ? sep.nterms : m;
@@ -167,7 +178,7 @@ kw_cols_fwd(const float2* __restrict__ Z, long long z_bstride, long long z_kstri
     int cur_slot = -1;
     if (t < tend) {
         const int s0 = slot_of(kof(t));
-        if constexpr (SEP) wy_load(wys, sep.wrow, kof(t));
+        if constexpr (SEP) wy_load<NY>(wys, sep.wrow, kof(t));
         tile_load(tile, Zb + s0 * z_kstride, box[s0].nr, NXh, col0);
     }
     while (t < tend) {
@@ -181,23 +192,23 @@ kw_cols_fwd(const float2* __restrict__ Z, long long z_bstride, long long z_kstri
             __syncthreads();
             cur_slot = sl;
         }
-        float2 v[32];
+        float2 v[QN];
         if constexpr (SEP) {
             const float* wr = wys + (t & 1) * NY;
             if (bx.r0 == 0 && bx.nr == NY) {   // uniform: the slot holds every row in place
                 const float2* tb = tile + 4 * lane + tix_sw(lane, warp);
 #pragma unroll
-                for (int q = 0; q < 32; ++q) v[q] = cscale(tb[128 * q], wr[lane + 32 * q]);
+                for (int q = 0; q < QN; ++q) v[q] = cscale(tb[128 * q], wr[lane + 32 * q]);
             } else {
 #pragma unroll
-                for (int q = 0; q < 32; ++q) {
+                for (int q = 0; q < QN; ++q) {
                     const int i = wrap(lane + 32 * q - bx.r0, NY);
                     v[q] = (i < bx.nr) ? cscale(tile[tix(i, warp)], wr[lane + 32 * q]) : make_float2(0.f, 0.f);
                 }
             }
         } else {
 #pragma unroll
-            for (int q = 0; q < 32; ++q) {
+            for (int q = 0; q < QN; ++q) {
                 const int i = wrap(lane + 32 * q - bx.r0, NY);
                 v[q] = (i < bx.nr) ? tile[tix(i, warp)] : make_float2(0.f, 0.f);
             }
@@ -210,7 +221,7 @@ kw_cols_fwd(const float2* __restrict__ Z, long long z_bstride, long long z_kstri
         // tile while the FFT finishes
         const bool bulk = !dcn && cv && !failed;
         const float sk = hscale_of<HT>(hscale, k);
-        warp_fft1024<false>(v, tr, tw, [&] {
+        warp_fft<NY, false>(v, tr, tw, [&] {
             if (bulk && lane == 0)
                 bulk_load(tr, hhT + ((long long)k * NXh + col) * NY, NY * sizeof(HT), bar, skip_copy);
         });
@@ -229,7 +240,7 @@ kw_cols_fwd(const float2* __restrict__ Z, long long z_bstride, long long z_kstri
             const HT* h0 = hhT + (long long)k * NXh * NY;
             const HT* hn = hN + (long long)k * NY;
 #pragma unroll
-            for (int mm = 0; mm < 32; ++mm) {
+            for (int mm = 0; mm < QN; ++mm) {
                 const int f = lane + 32 * mm;
                 float2 a, bb;
                 warp_split(v, lane, mm, a, bb);
@@ -241,23 +252,23 @@ kw_cols_fwd(const float2* __restrict__ Z, long long z_bstride, long long z_kstri
         } else if (cv && !failed) {
             const HT* th = reinterpret_cast<const HT*>(tr);
 #pragma unroll
-            for (int mm = 0; mm < 32; ++mm) acc[mm] = cfma(lds_h(&th[lane + 32 * mm], sk), v[mm], acc[mm]);
+            for (int mm = 0; mm < QN; ++mm) acc[mm] = cfma(lds_h(&th[lane + 32 * mm], sk), v[mm], acc[mm]);
         }
         if constexpr (SEP) {
             // next term's row factors into the other buffer, last read in the
             // previous term (before this term's barrier)
             if (tn < tend) {
-                wy_load(wys + ((t + 1) & 1) * NY, sep.wrow, kof(tn));
+                wy_load<NY>(wys + ((t + 1) & 1) * NY, sep.wrow, kof(tn));
                 cp_async_commit();
             }
         }
         t = tn;
     }
-    warp_fft1024<true>(acc, tr, tw);
+    warp_fft<NY, true>(acc, tr, tw);
     __syncthreads();
     const int swl = tix_sw(lane, warp);
 #pragma unroll
-    for (int mm = 0; mm < 32; ++mm) tile[4 * (lane + 32 * mm) + swl] = acc[mm];
+    for (int mm = 0; mm < QN; ++mm) tile[4 * (lane + 32 * mm) + swl] = acc[mm];
     __syncthreads();
     float2* Ab = A + b * a_bstride;
     for (int e = threadIdx.x; e < NY * kWColWarps; e += kWColWarps * 32) {
@@ -266,24 +277,25 @@ kw_cols_fwd(const float2* __restrict__ Z, long long z_bstride, long long z_kstri
     }
 }
 
-// G1b + G2 for Ny = 1024 (FULL: every row of Q, for the window gradient).
+// G1b + G2 for Ny = NY (1024 or 512; FULL: every row of Q, for the window
+// gradient).
 // Grid (batch, NXh / 4).
 // SEP: Q receives one slot per column factor: S_j = sum over the slot's terms of
 // wy_k . IFFT_y(conj(hhat_k) V), on the slot box rows (box[] indexed by slot),
 // accumulated in the shared tile and stored once per slot.
-template <bool FULL, typename HT = float2, bool SEP = false>
-__global__ void __launch_bounds__(kWColWarps * 32, 3)
+template <bool FULL, typename HT = float2, bool SEP = false, int NY = kWarpN>
+__global__ void __launch_bounds__(kWColWarps * 32, kw_col_min_ctas<NY>())
 kw_cols_adj(const float2* __restrict__ V, long long v_bstride,
             const HT* __restrict__ hhT, const HT* __restrict__ hN, const float* __restrict__ hscale, int m,
             const Box* __restrict__ box, int NXh,
             float2* __restrict__ Q, long long q_bstride, long long q_kstride,
             const float2* __restrict__ tw, int* __restrict__ status, long long wait_limit, int skip_copy,
             SepTerms sep = SepTerms{}) {
-    constexpr int NY = kWarpN;
+    constexpr int QN = NY / 32;   // values per lane
     extern __shared__ float2 smem[];
     float2* tile = smem;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float2* tr = smem + NY * kWColWarps + warp * kWarpN;
+    float2* tr = smem + NY * kWColWarps + warp * NY;
     const int b = blockIdx.x;
     const int col0 = blockIdx.y * kWColWarps;
     const int col = col0 + warp;
@@ -310,18 +322,18 @@ kw_cols_adj(const float2* __restrict__ V, long long v_bstride,
     // SEP: row factors of the t-th term in buffer (t & 1), prefetched one term ahead
     float* wys = reinterpret_cast<float*>(smem + 2 * NY * kWColWarps);
     if constexpr (SEP) {
-        if (sep.nterms > 0) wy_load(wys, sep.wrow, __ldg(&sep.korder[0]));
+        if (sep.nterms > 0) wy_load<NY>(wys, sep.wrow, __ldg(&sep.korder[0]));
     }
     tile_load(tile, V + b * v_bstride, NY, NXh, col0);
     cp_async_wait_all();
     __syncthreads();
-    float2 vv[32];
+    float2 vv[QN];
 #pragma unroll
-    for (int q = 0; q < 32; ++q) vv[q] = tile[4 * (lane + 32 * q) + tix_sw(lane, warp)];
+    for (int q = 0; q < QN; ++q) vv[q] = tile[4 * (lane + 32 * q) + tix_sw(lane, warp)];
     int t = next_t(0);
     int prev_slot = -1;
     // the spectrum of the first term arrives while the FFT of V finishes
-    warp_fft1024<false, SEP>(vv, tr, tw, [&] {
+    warp_fft<NY, false, SEP>(vv, tr, tw, [&] {
         if (use_bulk && t < tend && lane == 0)
             bulk_load(tr, hhT + ((long long)kof(t) * NXh + col) * NY, NY * sizeof(HT), bar, skip_copy);
     });
@@ -345,13 +357,13 @@ kw_cols_adj(const float2* __restrict__ V, long long v_bstride,
             }
             parity ^= 1;
         }
-        float2 p[32];
+        float2 p[QN];
         const float sk = hscale_of<HT>(hscale, k);
         if (dcn) {
             const HT* h0 = hhT + (long long)k * NXh * NY;
             const HT* hn = hN + (long long)k * NY;
 #pragma unroll
-            for (int mm = 0; mm < 32; ++mm) {
+            for (int mm = 0; mm < QN; ++mm) {
                 const int f = lane + 32 * mm;
                 float2 a, bb;
                 warp_split(vv, lane, mm, a, bb);
@@ -364,13 +376,13 @@ kw_cols_adj(const float2* __restrict__ V, long long v_bstride,
         } else {
             const HT* th = reinterpret_cast<const HT*>(tr);
 #pragma unroll
-            for (int mm = 0; mm < 32; ++mm)
+            for (int mm = 0; mm < QN; ++mm)
                 p[mm] = (use_bulk && !failed) ? cmulc(vv[mm], lds_h(&th[lane + 32 * mm], sk))
                                               : make_float2(0.f, 0.f);
         }
         // the next term's spectrum arrives while this inverse FFT finishes
         const bool issue = use_bulk && !failed && tn < tend;
-        warp_fft1024<true, SEP>(p, tr, tw, [&] {
+        warp_fft<NY, true, SEP>(p, tr, tw, [&] {
             if (issue && lane == 0)
                 bulk_load(tr, hhT + ((long long)kn * NXh + col) * NY, NY * sizeof(HT), bar, skip_copy);
         });
@@ -381,17 +393,17 @@ kw_cols_adj(const float2* __restrict__ V, long long v_bstride,
             cp_async_wait_all();
             __syncthreads();
             if (tn < tend) {   // the other buffer was last read in the previous term
-                wy_load(wys + ((t + 1) & 1) * NY, sep.wrow, kn);
+                wy_load<NY>(wys + ((t + 1) & 1) * NY, sep.wrow, kn);
                 cp_async_commit();
             }
             const float* wr = wys + (t & 1) * NY;
             float2* col = tile + tix_sw(lane, warp) + 4 * lane;
             if (first) {
 #pragma unroll
-                for (int mm = 0; mm < 32; ++mm) col[128 * mm] = cscale(p[mm], wr[lane + 32 * mm]);
+                for (int mm = 0; mm < QN; ++mm) col[128 * mm] = cscale(p[mm], wr[lane + 32 * mm]);
             } else {
 #pragma unroll
-                for (int mm = 0; mm < 32; ++mm) col[128 * mm] = cadd(col[128 * mm], cscale(p[mm], wr[lane + 32 * mm]));
+                for (int mm = 0; mm < QN; ++mm) col[128 * mm] = cadd(col[128 * mm], cscale(p[mm], wr[lane + 32 * mm]));
             }
             if (last) {
                 __syncthreads();
@@ -405,7 +417,7 @@ kw_cols_adj(const float2* __restrict__ V, long long v_bstride,
         } else {
             __syncthreads();
 #pragma unroll
-            for (int mm = 0; mm < 32; ++mm) tile[4 * (lane + 32 * mm) + tix_sw(lane, warp)] = p[mm];
+            for (int mm = 0; mm < QN; ++mm) tile[4 * (lane + 32 * mm) + tix_sw(lane, warp)] = p[mm];
             __syncthreads();
             float2* Qk = Q + b * q_bstride + k * q_kstride;
             const int rows = FULL ? NY : bx.nr;

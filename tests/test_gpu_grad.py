@@ -51,7 +51,7 @@ def _case(shape, m, batch, seed):
 
 
 @pytest.mark.parametrize("shape,m,batch", [((64, 64), 4, 2), ((32, 128), 8, 3), ((16, 16), 4, 1),
-                                           ((16, 1024), 4, 2), ((1024, 16), 4, 1),
+                                           ((16, 1024), 4, 2), ((1024, 16), 4, 1), ((512, 16), 4, 2),
                                            ((256,), 4, 3), ((1024,), 8, 2), ((64,), 3, 1)])
 def test_backward_matches_oracle(torch_cuda, shape, m, batch):
     torch = torch_cuda

@@ -384,3 +384,31 @@ def test_2048_point_columns_variants_agree(torch_cuda, tmp_path):
     q = Plan(dev(torch, pr.w), h=dev(torch, pr.h), flags=pce.PCE_FLAG_PRODUCT_CONVOLUTION)
     assert rel_l2(host(q.apply(u)), E.product_convolution(pr.u, pr.w, pr.h)) < TOL
     assert rel_l2(host(q.apply_adjoint(u)), E.product_convolution_adjoint(pr.u, pr.w, pr.h)) < TOL
+
+
+@pytest.mark.parametrize("ny,nx,m,batch", [(512, 16, 4, 2), (512, 64, 8, 1), (512, 32, 16, 3)])
+def test_512_point_columns_one_warp_fft(torch_cuda, ny, nx, m, batch):
+    """Columns of 512: the one-warp 512-point FFT (16 values per lane, the last radix-2
+    split over lane pairs) in column variant 0 and the block Stockham kernels in variant 1,
+    forward and adjoint, FP32 and reduced storage, against the oracle; both variants
+    agree to rounding."""
+    torch = torch_cuda
+    from paper_1604_04374_gb300 import Plan, pce
+    pr = synth.problem_2d(ny, nx, m, batch, 400 + m, "normal")
+    u = dev(torch, pr.u)
+    ry, rx = E.apply(pr.u, pr.w, pr.h), E.apply_adjoint(pr.u, pr.w, pr.h)
+    outs = []
+    for cv in (0, 1):
+        plan = Plan(dev(torch, pr.w), h=dev(torch, pr.h))
+        plan.set_tuning(batch, cv, 0)
+        y, x = host(plan.apply(u)), host(plan.apply_adjoint(u))
+        assert rel_l2(y, ry) < TOL and rel_l2(x, rx) < TOL
+        outs.append((y, x))
+        plan.close()
+    assert rel_l2(outs[0][0], outs[1][0]) < TOL and rel_l2(outs[0][1], outs[1][1]) < TOL
+    lp = Plan(dev(torch, pr.w), h=dev(torch, pr.h), flags=pce.PCE_FLAG_LOWP_STORAGE)
+    assert rel_l2(host(lp.apply(u)), ry) < 3e-3
+    assert rel_l2(host(lp.apply_adjoint(u)), rx) < 3e-3
+    q = Plan(dev(torch, pr.w), h=dev(torch, pr.h), flags=pce.PCE_FLAG_PRODUCT_CONVOLUTION)
+    assert rel_l2(host(q.apply(u)), E.product_convolution(pr.u, pr.w, pr.h)) < TOL
+    assert rel_l2(host(q.apply_adjoint(u)), E.product_convolution_adjoint(pr.u, pr.w, pr.h)) < TOL

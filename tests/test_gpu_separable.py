@@ -55,8 +55,10 @@ def sep_problem(ny, nx, gy, gx, batch, seed, random_h=False):
     return wy, wx, pr.w, h, pr.u
 
 
-@pytest.mark.parametrize("ny,nx,gy,gx,batch", [(1024, 64, 2, 2, 2), (1024, 128, 4, 2, 1), (1024, 32, 8, 4, 3)])
+@pytest.mark.parametrize("ny,nx,gy,gx,batch", [(1024, 64, 2, 2, 2), (1024, 128, 4, 2, 1), (1024, 32, 8, 4, 3),
+                                                (512, 64, 4, 4, 2), (512, 32, 2, 2, 3), (512, 128, 8, 2, 1)])
 def test_separable_fast_path_matches_oracle(torch_cuda, ny, nx, gy, gx, batch):
+    """Ny = 1024 and 512 (one-warp column FFTs of 1024 or 512 points)."""
     torch = torch_cuda
     from paper_1604_04374_gb300 import Plan
     wy, wx, w, h, u = sep_problem(ny, nx, gy, gx, batch, 80 + gy + gx, random_h=True)
@@ -65,6 +67,15 @@ def test_separable_fast_path_matches_oracle(torch_cuda, ny, nx, gy, gx, batch):
     ud = dev(torch, u)
     assert rel(host(plan.apply(ud)), E.apply(u, w, h)) < TOL
     assert rel(host(plan.apply_adjoint(ud)), E.apply_adjoint(u, w, h)) < TOL
+    if ny == 512:
+        # the tensor-memory variants need 1024 rows
+        for cv in (2, 3, 4):
+            with pytest.raises(Exception):
+                plan.set_tuning(batch, cv, 0)
+        # variant 1 runs the general block kernels on the dense windows: same operator
+        plan.set_tuning(batch, 1, 1)
+        assert rel(host(plan.apply(ud)), E.apply(u, w, h)) < TOL
+        assert rel(host(plan.apply_adjoint(ud)), E.apply_adjoint(u, w, h)) < TOL
 
 
 def test_separable_equals_general_path_on_the_bench_workload_shape(torch_cuda):
