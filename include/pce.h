@@ -452,8 +452,10 @@ pce_status pce_schedule_lpt(const double* cost, int n, int lanes, int* lane_of, 
  *   - row-pass variant (2D): 0 = block Stockham rows, the adjoint with the
  *     next term's data prefetched into registers (2 CTAs per SM), 1 = block
  *     Stockham rows without prefetch (3 CTAs per SM), 2 = variant 1 with the
- *     plain row transforms (the adjoint's input R2C and the forward's output
- *     C2R) by one warp per row pair (rows of 1024 points);
+ *     forward's windowed R2C run by row pairs (each pair's rows loaded once
+ *     for all the terms or slots whose box holds them) and, for rows of 1024
+ *     points, the plain row transforms (the adjoint's input R2C and the
+ *     forward's output C2R) by one warp per row pair;
  *   - right-hand sides per launch: powers of two up to the plan's scratch
  *     chunk (2D plans and 1D plans above 8192 points).
  * 1D plans up to 8192 points have nothing to choose and are only timed.  The
@@ -474,8 +476,7 @@ pce_status pce_plan_tuning(pce_plan_t plan, int* chunk, int* col_variant, int* r
  * A column variant the plan has no kernels for is PCE_ERR_UNSUPPORTED
  * (1 needs a 2D plan with 512, 1024 or 2048 rows, 2 a separable plan with 1024
  * rows, 3 such a plan whose row factors allow pruning, 4 such a plan with
- * two or more slots); row variants 1 and 2 need a 2D plan, 2 also rows of
- * 1024 points.  Changes no value an
+ * two or more slots); row variants 1 and 2 need a 2D plan.  Changes no value an
  * apply computes beyond rounding order.  Host only, no synchronisation. */
 pce_status pce_plan_set_tuning(pce_plan_t plan, int chunk, int col_variant, int row_variant);
 /* Every candidate the last timed pce_plan_autotune measured: writes up to

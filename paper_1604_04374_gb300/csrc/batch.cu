@@ -488,11 +488,11 @@ extern "C" pce_status pce_plan_autotune(pce_plan_t p, int64_t batch, const char*
         if (cache_lookup(cache_path, key, c, v, rv, ms)) {
             p->tune_log.clear();
             p->run_chunk = std::min(c, cmax);
-            const bool ok = p->ndims == 2 && (p->ny == 512 || p->ny == 1024 || p->ny == 2048) &&
+            const bool ok = p->ndims == 2 && (p->ny == 512 || p->ny == 1024 || p->ny == 2048) && v >= 0 &&
                             (v < 2 || (p->sep && p->ny == 1024)) && (v != 3 || p->sep_prune) &&
                             (v != 4 || p->nslots > 1);
             p->col_variant = ok ? v : 0;
-            p->row_variant = (p->ndims == 2 && (rv < 2 || p->nx == 1024)) ? rv : 0;
+            p->row_variant = (p->ndims == 2 && rv >= 0 && rv <= 2) ? rv : 0;
             p->tuned_ms = ms;
             return PCE_OK;
         }
@@ -506,7 +506,7 @@ extern "C" pce_status pce_plan_autotune(pce_plan_t p, int64_t batch, const char*
     if (p->sep && p->nslots > 1 && !p->sect && p->ny == 1024) variants.push_back(4);
     std::vector<int> rvariants = {0};
     if (p->ndims == 2 && !p->sect) rvariants.push_back(1);
-    if (p->ndims == 2 && !p->sect && p->nx == 1024 && !(p->flags & PCE_FLAG_UNFUSED)) rvariants.push_back(2);
+    if (p->ndims == 2 && !p->sect && !(p->flags & PCE_FLAG_UNFUSED)) rvariants.push_back(2);
     std::vector<int> chunks;
     if ((p->ndims == 2 && !p->sect) || p->l1) {
         for (int c = 1; c < cmax; c *= 2) chunks.push_back(c);
@@ -615,8 +615,6 @@ extern "C" pce_status pce_plan_set_tuning(pce_plan_t p, int chunk, int col_varia
     if (col_variant == 4 && !(p->sep && p->ny == 1024 && p->nslots > 1))
         return fail(PCE_ERR_UNSUPPORTED, "column variant 4 needs a separable plan with 1024 rows and two or more slots");
     if (row_variant != 0 && p->ndims != 2) return fail(PCE_ERR_UNSUPPORTED, "row variants 1, 2 need a 2D plan");
-    if (row_variant == 2 && p->nx != 1024)
-        return fail(PCE_ERR_UNSUPPORTED, "row variant 2 needs rows of 1024 points");
     p->run_chunk = chunk == 0 ? 0 : std::min(chunk, p->bchunk);
     p->col_variant = col_variant;
     p->row_variant = row_variant;

@@ -191,8 +191,10 @@ def test_autotune_variants_and_cache(torch_cuda, tmp_path):
     cache = str(tmp_path / "tune.jsonl")
     plan = Plan(dev(torch, pr.w), h=dev(torch, pr.h))
     chunk, variant, rvariant, ms = plan.autotune(3, cache)
-    assert 1 <= chunk <= 3 and variant in (0, 1) and rvariant in (0, 1) and ms > 0
-    assert len(plan.tuning_log()) == 3 * 2 * 2
+    assert 1 <= chunk <= 3 and variant in (0, 1) and rvariant in (0, 1, 2) and ms > 0
+    # chunks 1..3 x column variants 0, 1 x row variants 0, 1, 2 (the row-pair windowed R2C
+    # serves rows of any length)
+    assert len(plan.tuning_log()) == 3 * 2 * 3
     lines = open(cache).read().splitlines()
     assert len(lines) == 1
     rec = json.loads(lines[0])
@@ -201,12 +203,13 @@ def test_autotune_variants_and_cache(torch_cuda, tmp_path):
     assert rel(host(plan.apply(u)), E.apply(pr.u, pr.w, pr.h)) < TOL
     assert rel(host(plan.apply_adjoint(u)), E.apply_adjoint(pr.u, pr.w, pr.h)) < TOL
     # a second plan of the same operator reads the cache; force the other variant through it
-    rec2 = dict(rec, variant=1 - variant, row_variant=1 - rvariant, chunk=1)
+    other_r = 1 if rvariant != 1 else 0
+    rec2 = dict(rec, variant=1 - variant, row_variant=other_r, chunk=1)
     with open(cache, "a") as f:
         f.write(json.dumps(rec2) + "\n")
     p2 = Plan(dev(torch, pr.w), h=dev(torch, pr.h))
     c2, v2, r2, _ = p2.autotune(3, cache)
-    assert (c2, v2, r2) == (1, 1 - variant, 1 - rvariant)
+    assert (c2, v2, r2) == (1, 1 - variant, other_r)
     assert p2.tuning_log() == []
     assert len(open(cache).read().splitlines()) == 2      # nothing appended
     assert rel(host(p2.apply(u)), E.apply(pr.u, pr.w, pr.h)) < TOL
@@ -224,7 +227,7 @@ def test_autotune_other_plans(torch_cuda, shape, m):
     plan = Plan(dev(torch, pr.w), h=dev(torch, pr.h))
     chunk, variant, rvariant, ms = plan.autotune(4)
     assert variant == 0 and ms > 0 and chunk >= 1
-    assert rvariant in ((0, 1) if len(shape) == 2 else (0,))
+    assert rvariant in ((0, 1, 2) if len(shape) == 2 else (0,))
     u = dev(torch, pr.u)
     assert rel(host(plan.apply(u)), E.apply(pr.u, pr.w, pr.h)) < TOL
     assert rel(host(plan.apply_adjoint(u)), E.apply_adjoint(pr.u, pr.w, pr.h)) < TOL

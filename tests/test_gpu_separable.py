@@ -298,9 +298,11 @@ def test_set_tuning_rejects_missing_variants(torch_cuda):
     with pytest.raises(PceError) as e:
         p.set_tuning(0, 5, 0)
     assert e.value.status == pce.PCE_ERR_INVALID
-    with pytest.raises(PceError) as e:       # one-warp rows need rows of 1024 points
-        p.set_tuning(0, 0, 2)
-    assert e.value.status == pce.PCE_ERR_UNSUPPORTED
+    # row variant 2 on rows of 64 points: the row-pair windowed R2C, block plain transforms
+    p.set_tuning(0, 0, 2)
+    ud = dev(torch, u)
+    assert rel(host(p.apply(ud)), E.apply(u, w, h)) < TOL
+    assert rel(host(p.apply_adjoint(ud)), E.apply_adjoint(u, w, h)) < TOL
     with pytest.raises(PceError) as e:
         p.set_tuning(0, 0, 3)
     assert e.value.status == pce.PCE_ERR_INVALID
