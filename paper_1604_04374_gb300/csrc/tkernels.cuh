@@ -368,8 +368,8 @@ kt_cols_adj(float2* __restrict__ V, long long v_bstride, const float2* __restric
             parity ^= 1;
         }
         float2 p[32];
-        tm_load32c(t_hold, p);
         if (dcn) {
+            tm_load32c(t_hold, p);
             const float2* h0 = hhT + (long long)k * NXh * NY;
             const float2* hn = hN + (long long)k * NY;
             __syncwarp();
@@ -389,9 +389,17 @@ kt_cols_adj(float2* __restrict__ V, long long v_bstride, const float2* __restric
             }
             __syncwarp();
         } else {
+            // V-hat times conj(hhat_k), a quarter of the column at a time (fewer
+            // values live at once than a whole-column load followed by the products)
+            const bool ok = use_bulk && !failed;
 #pragma unroll
-            for (int mm = 0; mm < 32; ++mm)
-                p[mm] = (use_bulk && !failed) ? cmulc(p[mm], tr[lane + 32 * mm]) : make_float2(0.f, 0.f);
+            for (int qq = 0; qq < 4; ++qq) {
+                float2 x[8];
+                tm_load8c(t_hold + 16 * qq, x);
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    p[8 * qq + j] = ok ? cmulc(x[j], tr[lane + 32 * (8 * qq + j)]) : make_float2(0.f, 0.f);
+            }
         }
         // the next term's spectrum arrives while this inverse FFT finishes; at
         // the end of a slot the transpose tiles stage the store first
