@@ -1013,6 +1013,14 @@ struct Cfg1d {
     static constexpr int SMEM = G * fft_region(N) * (int)sizeof(float2);
 };
 
+// Ask L2 for the `bytes` at p (one 128-byte line per thread of the CTA), so that
+// a latency-bound CTA finds them there when it reaches their loads.
+__device__ __forceinline__ void prefetch_l2_block(const void* p, long long bytes) {
+    const char* c = static_cast<const char*>(p);
+    for (long long o = 128ll * threadIdx.x; o < bytes; o += 128ll * blockDim.x)
+        asm volatile("prefetch.global.L2 [%0];\n" ::"l"(c + o));
+}
+
 // y_b = (1/N) C2R( sum_k hhat_k . R2C(w_k . u_b) ).  One CTA per b; each
 // slot takes pairs of terms (w_k u + i w_{k+1} u in one complex FFT) and
 // accumulates the half spectrum in registers; the slots' sums are reduced in
@@ -1032,6 +1040,12 @@ k_fwd_1d(const float* __restrict__ u, const WT* __restrict__ w,
     float2* b0 = smem + slot * fft_region(N);
     float2* b1 = b0 + pad_len(N);
     const int b = blockIdx.x;
+    // the twiddles and spectra are read stage by stage and after the first FFT:
+    // with few right-hand sides (a latency-bound launch) start them towards L2 now
+    if (gridDim.x <= 8) {
+        prefetch_l2_block(tw, (long long)FftPlan<N>::TWLEN * sizeof(float2));
+        prefetch_l2_block(hp, (long long)m * Nh * sizeof(HT));
+    }
     const float* ub = u + (long long)b * N;
     float ureg[kR];
 #pragma unroll
@@ -1131,6 +1145,14 @@ k_adj_1d(const float* __restrict__ vin, const WT* __restrict__ w,
     float2* b0 = smem + slot * fft_region(N);
     float2* b1 = b0 + pad_len(N);
     const int b = blockIdx.x;
+    // the twiddles, spectra and windows are read stage by stage and after the
+    // FFT of v: with few right-hand sides (a latency-bound launch) start them
+    // towards L2 now
+    if (gridDim.x <= 8) {
+        prefetch_l2_block(tw, (long long)FftPlan<N>::TWLEN * sizeof(float2));
+        prefetch_l2_block(hp, (long long)m * Nh * sizeof(HT));
+        prefetch_l2_block(w, (long long)m * N * sizeof(WT));
+    }
     const float* vb = vin + (long long)b * N;
     float2 V[kR];
 #pragma unroll
