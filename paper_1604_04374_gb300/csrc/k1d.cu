@@ -1,6 +1,7 @@
 // k1d.cu -- instances of the single-CTA 1D kernels for N = 16 .. 8192.
 #include "kernels.cuh"
 #include "k1d_large.cuh"
+#include "wk1d.cuh"
 #include "launch.h"
 
 namespace pce {
@@ -219,10 +220,22 @@ bool wide_1d(int batch, int m) {
     return Cfg1d<N, 1>::G > Cfg1d<N>::G && npairs > Cfg1d<N>::G && batch < 2 * 152;
 }
 
+// N = 1024 with few right-hand sides: the one-warp kernels (wk1d.cuh)
+bool warp_1d(int n, int batch, const float2* tw1024) { return n == kWarpN && tw1024 && batch < 2 * 152; }
+
 cudaError_t launch_fwd_1d(int n, int batch, cudaStream_t s, const float* u, const void* w,
                           const void* hp, const float* hscale, bool lowp, int m, float* y, float scale,
-                          const float2* tw) {
+                          const float2* tw, const float2* tw1024) {
     using bf16 = __nv_bfloat16;
+    if (warp_1d(n, batch, tw1024)) {
+        if (lowp)
+            kw_fwd_1d<bf16, __half2><<<batch, kW1dWarps * 32, 0, s>>>(
+                u, static_cast<const bf16*>(w), static_cast<const __half2*>(hp), hscale, m, y, scale, tw1024);
+        else
+            kw_fwd_1d<float, float2><<<batch, kW1dWarps * 32, 0, s>>>(
+                u, static_cast<const float*>(w), static_cast<const float2*>(hp), hscale, m, y, scale, tw1024);
+        return cudaGetLastError();
+    }
     switch (n) {
 #define X(N)                                                                                   \
     case N:                                                                                    \
@@ -254,8 +267,17 @@ cudaError_t launch_fwd_1d(int n, int batch, cudaStream_t s, const float* u, cons
 
 cudaError_t launch_adj_1d(int n, int batch, cudaStream_t s, const float* v, const void* w,
                           const void* hp, const float* hscale, bool lowp, int m, float* x, float scale,
-                          const float2* tw) {
+                          const float2* tw, const float2* tw1024) {
     using bf16 = __nv_bfloat16;
+    if (warp_1d(n, batch, tw1024)) {
+        if (lowp)
+            kw_adj_1d<bf16, __half2><<<batch, kW1dWarps * 32, 0, s>>>(
+                v, static_cast<const bf16*>(w), static_cast<const __half2*>(hp), hscale, m, x, scale, tw1024);
+        else
+            kw_adj_1d<float, float2><<<batch, kW1dWarps * 32, 0, s>>>(
+                v, static_cast<const float*>(w), static_cast<const float2*>(hp), hscale, m, x, scale, tw1024);
+        return cudaGetLastError();
+    }
     switch (n) {
 #define X(N)                                                                                   \
     case N:                                                                                    \

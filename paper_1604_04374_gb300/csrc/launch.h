@@ -145,13 +145,15 @@ cudaError_t launch_grad_1d(int n, int m, cudaStream_t s, const float* u, const f
                            const float* w, const float2* hp, int nb, float2* dh, float* dw,
                            float scale, int accumulate, const float2* tw);
 
+// tw1024 (may be NULL): the four-step table of the one-warp 1024-point FFT;
+// with it, N = 1024 and fewer than 304 right-hand sides run the one-warp kernels
 cudaError_t launch_fwd_1d(int n, int batch, cudaStream_t s, const float* u, const void* w,
                           const void* hp, const float* hscale, bool lowp, int m, float* y, float scale,
-                          const float2* tw);
+                          const float2* tw, const float2* tw1024 = nullptr);
 
 cudaError_t launch_adj_1d(int n, int batch, cudaStream_t s, const float* v, const void* w,
                           const void* hp, const float* hscale, bool lowp, int m, float* x, float scale,
-                          const float2* tw);
+                          const float2* tw, const float2* tw1024 = nullptr);
 
 cudaError_t launch_spec_1d(int n, int m, cudaStream_t s, const float* h, float2* hp,
                            const float2* tw);

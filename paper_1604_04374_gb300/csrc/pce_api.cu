@@ -1522,8 +1522,10 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
     if (p->ndims == 1) {
         e = timed(p, adjoint ? PCE_KERNEL_ADJ_1D : PCE_KERNEL_FWD_1D, s, [&] {
             return adjoint
-                ? pce::launch_adj_1d(nx, (int)batch, s, in, wstore(p), hstore(p), p->hscale, p->lowp, m, out, scale, p->twx)
-                : pce::launch_fwd_1d(nx, (int)batch, s, in, wstore(p), hstore(p), p->hscale, p->lowp, m, out, scale, p->twx);
+                ? pce::launch_adj_1d(nx, (int)batch, s, in, wstore(p), hstore(p), p->hscale, p->lowp, m, out, scale, p->twx,
+                                     p->tw1024)
+                : pce::launch_fwd_1d(nx, (int)batch, s, in, wstore(p), hstore(p), p->hscale, p->lowp, m, out, scale, p->twx,
+                                     p->tw1024);
         });
         if (e) return fail(PCE_ERR_CUDA, "1D apply launch: %s", cudaGetErrorString(e));
         return PCE_OK;
