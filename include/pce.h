@@ -440,13 +440,13 @@ pce_status pce_schedule_lpt(const double* cost, int n, int lanes, int* lane_of, 
  *   - column FFT variant for Ny = 512, 1024 and 2048: 0 = one-warp four-step
  *     (1024 points: 32 x 32; 512 points: 16 x 32 with the last radix-2 split
  *     over lane pairs; 2048 points: two such 1024-point warps per column),
- *     1 = block Stockham (radix 8); for Ny = 1024 also 2 (separable plans) = the
+ *     1 = block Stockham (radix 8); for Ny = 1024 and 512 also 2 (separable plans) = the
  *     one-warp four-step with each warp's held column and accumulator in
- *     tensor memory (more warps per SM), 3 = variant 2 with pruned column
+ *     tensor memory (more warps per SM), 3 (Ny = 1024) = variant 2 with pruned column
  *     transforms (separable plans whose row factors each lie in 512 rows
  *     starting on a multiple of 32: the forward FFT skips the zero half of
- *     its input, the adjoint computes the needed half of its output), 4 =
- *     variant 2 run slot by slot (separable plans with two or more
+ *     its input, the adjoint computes the needed half of its output), 4 (Ny =
+ *     1024) = variant 2 run slot by slot (separable plans with two or more
  *     column-factor slots: the row pass and the column pass of one slot at a
  *     time, so that one slot's intermediate and the accumulator fit in L2);
  *   - row-pass variant (2D): 0 = block Stockham rows, the adjoint with the
@@ -475,7 +475,7 @@ pce_status pce_plan_tuning(pce_plan_t plan, int* chunk, int* col_variant, int* r
  * larger values are clamped to it), col_variant and row_variant as above.
  * A column variant the plan has no kernels for is PCE_ERR_UNSUPPORTED
  * (1 needs a 2D plan with 512, 1024 or 2048 rows, 2 a separable plan with 1024
- * rows, 3 such a plan whose row factors allow pruning, 4 such a plan with
+ * or 512 rows, 3 a separable plan with 1024 rows whose row factors allow pruning, 4 such a plan with
  * two or more slots); row variants 1 and 2 need a 2D plan.  Changes no value an
  * apply computes beyond rounding order.  Host only, no synchronisation. */
 pce_status pce_plan_set_tuning(pce_plan_t plan, int chunk, int col_variant, int row_variant);

@@ -489,7 +489,8 @@ extern "C" pce_status pce_plan_autotune(pce_plan_t p, int64_t batch, const char*
             p->tune_log.clear();
             p->run_chunk = std::min(c, cmax);
             const bool ok = p->ndims == 2 && (p->ny == 512 || p->ny == 1024 || p->ny == 2048) && v >= 0 &&
-                            (v < 2 || (p->sep && p->ny == 1024)) && (v != 3 || p->sep_prune) &&
+                            (v < 2 || (p->sep && p->ny == 1024) || (v == 2 && p->sep && p->ny == 512)) &&
+                            (v != 3 || p->sep_prune) &&
                             (v != 4 || p->nslots > 1);
             p->col_variant = ok ? v : 0;
             p->row_variant = (p->ndims == 2 && rv >= 0 && rv <= 2) ? rv : 0;
@@ -501,7 +502,7 @@ extern "C" pce_status pce_plan_autotune(pce_plan_t p, int64_t batch, const char*
     // a sectioned plan runs its own kernels and chunks: one candidate, timed
     std::vector<int> variants = {0};
     if (p->ndims == 2 && !p->sect && (p->ny == 512 || p->ny == 1024 || p->ny == 2048)) variants.push_back(1);
-    if (p->sep && !p->sect && p->ny == 1024) variants.push_back(2);
+    if (p->sep && !p->sect && (p->ny == 1024 || p->ny == 512)) variants.push_back(2);
     if (p->sep && p->sep_prune && !p->sect && p->ny == 1024) variants.push_back(3);
     if (p->sep && p->nslots > 1 && !p->sect && p->ny == 1024) variants.push_back(4);
     std::vector<int> rvariants = {0};
@@ -606,8 +607,8 @@ extern "C" pce_status pce_plan_set_tuning(pce_plan_t p, int chunk, int col_varia
                     row_variant);
     if (col_variant == 1 && !(p->ndims == 2 && (p->ny == 512 || p->ny == 1024 || p->ny == 2048)))
         return fail(PCE_ERR_UNSUPPORTED, "column variant 1 needs a 2D plan with 512, 1024 or 2048 rows");
-    if (col_variant == 2 && !(p->sep && p->ny == 1024))
-        return fail(PCE_ERR_UNSUPPORTED, "column variant 2 needs a separable plan with 1024 rows");
+    if (col_variant == 2 && !(p->sep && (p->ny == 1024 || p->ny == 512)))
+        return fail(PCE_ERR_UNSUPPORTED, "column variant 2 needs a separable plan with 1024 or 512 rows");
     if (col_variant == 3 && !(p->sep && p->sep_prune))
         return fail(PCE_ERR_UNSUPPORTED,
                     "column variant 3 needs a separable plan with 1024 rows whose row factors each lie in "

@@ -295,11 +295,17 @@ cudaError_t launch_cols_adj_sep(int ny, dim3 grid, cudaStream_t s, const float2*
     return cudaGetLastError();
 }
 
-cudaError_t launch_cols_fwd_sep_tm(dim3 grid, cudaStream_t s, const float2* Z, long long z_bstride,
+cudaError_t launch_cols_fwd_sep_tm(int ny, dim3 grid, cudaStream_t s, const float2* Z, long long z_bstride,
                                    long long z_kstride, const float2* hhT, const float2* hN, const Box* box,
                                    int nxh, float2* A, long long a_bstride, const float2* tw1024, int* status,
                                    long long wait_limit, int skip_copy, const SepTerms& sep) {
     if (!tw1024 || !hhT) return cudaErrorInvalidValue;
+    if (ny == 512 && !sep.kq0) {   // 512-point columns: no pruned form
+        kt_cols_fwd<false, 512><<<grid, kWColWarps * 32, kt_smem<512>(), s>>>(
+            Z, z_bstride, z_kstride, hhT, hN, box, nxh, A, a_bstride, tw1024, status, wait_limit, skip_copy, sep);
+        return cudaGetLastError();
+    }
+    if (ny != kWarpN) return cudaErrorInvalidValue;
     if (sep.kq0)
         kt_cols_fwd<true><<<grid, kWColWarps * 32, kTColSmem, s>>>(Z, z_bstride, z_kstride, hhT, hN, box, nxh, A,
                                                                    a_bstride, tw1024, status, wait_limit, skip_copy,
@@ -311,11 +317,17 @@ cudaError_t launch_cols_fwd_sep_tm(dim3 grid, cudaStream_t s, const float2* Z, l
     return cudaGetLastError();
 }
 
-cudaError_t launch_cols_adj_sep_tm(dim3 grid, cudaStream_t s, float2* V, long long v_bstride,
+cudaError_t launch_cols_adj_sep_tm(int ny, dim3 grid, cudaStream_t s, float2* V, long long v_bstride,
                                    const float2* hhT, const float2* hN, const Box* box, int nxh, float2* Q,
                                    long long q_bstride, long long q_kstride, const float2* tw1024, int* status,
                                    long long wait_limit, int skip_copy, const SepTerms& sep) {
     if (!tw1024 || !hhT) return cudaErrorInvalidValue;
+    if (ny == 512 && !sep.kq0) {
+        kt_cols_adj<false, 512><<<grid, kWColWarps * 32, kt_smem<512>(), s>>>(
+            V, v_bstride, hhT, hN, box, nxh, Q, q_bstride, q_kstride, tw1024, status, wait_limit, skip_copy, sep);
+        return cudaGetLastError();
+    }
+    if (ny != kWarpN) return cudaErrorInvalidValue;
     if (sep.kq0)
         kt_cols_adj<true><<<grid, kWColWarps * 32, kTColSmem, s>>>(V, v_bstride, hhT, hN, box, nxh, Q, q_bstride,
                                                                    q_kstride, tw1024, status, wait_limit, skip_copy,

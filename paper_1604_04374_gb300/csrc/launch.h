@@ -113,14 +113,14 @@ cudaError_t launch_cols_adj_sep(int ny, dim3 grid, cudaStream_t s, const float2*
                                 const float2* tw1024, int* status, long long wait_limit, int skip_copy,
                                 const SepTerms& sep);
 
-// The same with the per-warp state in tensor memory (tkernels.cuh).  With
-// sep.kq0 set, the pruned kernels run and hhT / hN must be the rotated spectra
-// hhat_k[f] W1024^{32 f kq0[k]}.
-cudaError_t launch_cols_fwd_sep_tm(dim3 grid, cudaStream_t s, const float2* Z, long long z_bstride,
+// The same with the per-warp state in tensor memory (tkernels.cuh), Ny = 1024 or
+// 512.  With sep.kq0 set (Ny = 1024 only), the pruned kernels run and hhT / hN
+// must be the rotated spectra hhat_k[f] W1024^{32 f kq0[k]}.
+cudaError_t launch_cols_fwd_sep_tm(int ny, dim3 grid, cudaStream_t s, const float2* Z, long long z_bstride,
                                    long long z_kstride, const float2* hhT, const float2* hN, const Box* box,
                                    int nxh, float2* A, long long a_bstride, const float2* tw1024, int* status,
                                    long long wait_limit, int skip_copy, const SepTerms& sep);
-cudaError_t launch_cols_adj_sep_tm(dim3 grid, cudaStream_t s, float2* V, long long v_bstride,
+cudaError_t launch_cols_adj_sep_tm(int ny, dim3 grid, cudaStream_t s, float2* V, long long v_bstride,
                                    const float2* hhT, const float2* hN, const Box* box, int nxh, float2* Q,
                                    long long q_bstride, long long q_kstride, const float2* tw1024, int* status,
                                    long long wait_limit, int skip_copy, const SepTerms& sep);

@@ -1580,7 +1580,7 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
     // separable fast path: one-warp column kernels only; variant 2 keeps the
     // per-warp column state in tensor memory
     const bool sepx = p->sep && warp;
-    const bool septm = sepx && ny == 1024 && (colv == 2 || colv == 3 || colv == 4);
+    const bool septm = sepx && ((ny == 1024 && (colv == 2 || colv == 3 || colv == 4)) || (ny == 512 && colv == 2));
     // variant 4: row pass and column pass slot by slot, so that one slot's Z and
     // the accumulator A stay in L2 between them (slots without terms skipped)
     std::vector<int> active;
@@ -1630,7 +1630,7 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
                     });
                 if (e == cudaSuccess)
                     e = timed(p, PCE_KERNEL_COLS_FWD, s, [&] {
-                        return pce::launch_cols_fwd_sep_tm(dim3(nb, (nxh + cpc - 1) / cpc), s, scr.Z, zb, p->zk_s,
+                        return pce::launch_cols_fwd_sep_tm(ny, dim3(nb, (nxh + cpc - 1) / cpc), s, scr.Z, zb, p->zk_s,
                                                            tm_hT, tm_hN, p->d_vbox, nxh, scr.A, ab, p->tw1024,
                                                            p->d_status, p->wait_limit, p->skip_copy, sj);
                     });
@@ -1656,7 +1656,7 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
                 // the first pass stores V's column spectrum in place for the later ones
                 sj.mode = a == 0 ? pce::kSepSpecOut : pce::kSepSpecIn;
                 e = timed(p, PCE_KERNEL_COLS_ADJ, s, [&] {
-                    return pce::launch_cols_adj_sep_tm(dim3(nb, (nxh + cpc - 1) / cpc), s, scr.A, ab, tm_hT, tm_hN,
+                    return pce::launch_cols_adj_sep_tm(ny, dim3(nb, (nxh + cpc - 1) / cpc), s, scr.A, ab, tm_hT, tm_hN,
                                                        p->d_vbox, nxh, scr.Z, zb, p->zk_s, p->tw1024, p->d_status,
                                                        p->wait_limit, p->skip_copy, sj);
                 });
@@ -1680,7 +1680,7 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
             if (e == cudaSuccess)
                 e = timed(p, PCE_KERNEL_COLS_FWD, s, [&] {
                     if (septm)
-                        return pce::launch_cols_fwd_sep_tm(dim3(nb, (nxh + cpc - 1) / cpc), s, scr.Z, zb, p->zk_s,
+                        return pce::launch_cols_fwd_sep_tm(ny, dim3(nb, (nxh + cpc - 1) / cpc), s, scr.Z, zb, p->zk_s,
                                                            tm_hT, tm_hN, p->d_vbox, nxh, scr.A, ab, p->tw1024,
                                                            p->d_status, p->wait_limit, p->skip_copy, septp);
                     return pce::launch_cols_fwd_sep(ny, dim3(nb, (nxh + cpc - 1) / cpc), s, scr.Z, zb, p->zk_s,
@@ -1703,7 +1703,7 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
             if (e == cudaSuccess)
                 e = timed(p, PCE_KERNEL_COLS_ADJ, s, [&] {
                     if (septm)
-                        return pce::launch_cols_adj_sep_tm(dim3(nb, (nxh + cpc - 1) / cpc), s, scr.A, ab, tm_hT,
+                        return pce::launch_cols_adj_sep_tm(ny, dim3(nb, (nxh + cpc - 1) / cpc), s, scr.A, ab, tm_hT,
                                                            tm_hN, p->d_vbox, nxh, scr.Z, zb, p->zk_s, p->tw1024,
                                                            p->d_status, p->wait_limit, p->skip_copy, septp);
                     return pce::launch_cols_adj_sep(ny, dim3(nb, (nxh + cpc - 1) / cpc), s, scr.A, ab, p->hhT, p->hN,

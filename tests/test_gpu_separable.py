@@ -68,14 +68,16 @@ def test_separable_fast_path_matches_oracle(torch_cuda, ny, nx, gy, gx, batch):
     assert rel(host(plan.apply(ud)), E.apply(u, w, h)) < TOL
     assert rel(host(plan.apply_adjoint(ud)), E.apply_adjoint(u, w, h)) < TOL
     if ny == 512:
-        # the tensor-memory variants need 1024 rows
-        for cv in (2, 3, 4):
+        # the pruned and slot-by-slot tensor-memory variants need 1024 rows
+        for cv in (3, 4):
             with pytest.raises(Exception):
                 plan.set_tuning(batch, cv, 0)
-        # variant 1 runs the general block kernels on the dense windows: same operator
-        plan.set_tuning(batch, 1, 1)
-        assert rel(host(plan.apply(ud)), E.apply(u, w, h)) < TOL
-        assert rel(host(plan.apply_adjoint(ud)), E.apply_adjoint(u, w, h)) < TOL
+        # variant 2: the tensor-memory column kernels at 512 points; variant 1 runs the
+        # general block kernels on the dense windows: the same operator
+        for cv, rv in ((2, 0), (2, 1), (2, 2), (1, 1)):
+            plan.set_tuning(batch, cv, rv)
+            assert rel(host(plan.apply(ud)), E.apply(u, w, h)) < TOL
+            assert rel(host(plan.apply_adjoint(ud)), E.apply_adjoint(u, w, h)) < TOL
 
 
 def test_separable_equals_general_path_on_the_bench_workload_shape(torch_cuda):
