@@ -125,11 +125,12 @@ k_sec_r2c(const float* __restrict__ src, long long src_bstride, int NYg, int NXg
 // start, and serves every right-hand side (several sections of a term read
 // the same columns, so per-right-hand-side copies multiplied the traffic);
 // the one wait for it is bounded (status bit kStatusTimeout, products skipped
-// after it).  Shared memory: tile, transpose tiles, spectrum buffers (96 KB,
-// two CTAs per SM).
-constexpr int kSecColSmem = 2 * kSecLR * kWColWarps * 8 + kWColWarps * kSecLR * 8;
+// after it).  Shared memory: the staging tile, whose four quarters double as
+// the warps' transpose tiles, and the spectrum buffers (64 KB, three CTAs per
+// SM at up to 168 registers).
+constexpr int kSecColSmem = kSecLR * kWColWarps * 8 + kWColWarps * kSecLR * 8;
 template <bool CONJ, typename HT = float2>
-__global__ void __launch_bounds__(kWColWarps * 32, 2)
+__global__ void __launch_bounds__(kWColWarps * 32, 3)
 kw_sec_cols(const float2* __restrict__ Z, long long z_bstride, long long z_kstride, int nb,
             const HT* __restrict__ hsT, const HT* __restrict__ hsN, const float* __restrict__ hscale,
             const SecGeom* __restrict__ geo,
@@ -139,7 +140,7 @@ kw_sec_cols(const float2* __restrict__ Z, long long z_bstride, long long z_kstri
     extern __shared__ float2 smem[];
     float2* tile = smem;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float2* tr = smem + NY * kWColWarps + warp * kWarpN;
+    float2* tr = smem + warp * kWarpN;   // a quarter of the staging tile
     const int sec = blockIdx.x;   // section; its term is g.k
     const int col0 = blockIdx.y * kWColWarps;
     const int col = col0 + warp;
@@ -158,7 +159,7 @@ kw_sec_cols(const float2* __restrict__ Z, long long z_bstride, long long z_kstri
     const HT* hn = hsN + (long long)k * NY;
     const float sk = hscale_of<HT>(hscale, k);
     const int swl = tix_sw(lane, warp);
-    HT* hb = reinterpret_cast<HT*>(smem + 2 * NY * kWColWarps) + warp * NY;
+    HT* hb = reinterpret_cast<HT*>(smem + NY * kWColWarps) + warp * NY;
     const bool bulk = !dcn && cv;
     if (bulk && lane == 0) bulk_load(hb, hcol, NY * sizeof(HT), bar, skip_copy);
     for (int b = 0; b < nb; ++b) {
@@ -177,6 +178,7 @@ kw_sec_cols(const float2* __restrict__ Z, long long z_bstride, long long z_kstri
             const int i = wrap(lane + 32 * q - lo_r, NY);
             v[q] = (i < rows) ? tile[tix(i, warp)] : make_float2(0.f, 0.f);
         }
+        __syncthreads();   // every warp has read its rows: the transpose tiles are free
         warp_fft1024<false>(v, tr, twb);
         if (bulk && b == 0) {
             if (!mbar_wait(bar, parity, wait_limit)) {
@@ -219,7 +221,7 @@ kw_sec_cols(const float2* __restrict__ Z, long long z_bstride, long long z_kstri
             for (int mm = 0; mm < 32; ++mm) v[mm] = make_float2(0.f, 0.f);
         }
         warp_fft1024<true>(v, tr, twb);
-        __syncthreads();   // every warp has read its input rows from the tile
+        __syncthreads();   // every warp is done with its transpose tile
 #pragma unroll
         for (int q = 0; q < 32; ++q) tile[4 * (lane + 32 * q) + swl] = v[q];
         __syncthreads();
