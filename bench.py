@@ -65,13 +65,17 @@ SUB_CONFIGS = (
 )
 
 # DRAM bytes (read + write) per launch measured by ncu, keyed by (workload,
-# plan kind, kernel kind, column variant); valid only for the kernels as
-# captured, each entry naming its profile summary.
+# plan kind, kernel kind, column variant, right-hand sides per launch); valid
+# only for the kernels as captured, each entry naming its profile summary.
 MEASURED_TRAFFIC = {
-    ("2d_1024x1024_m16_b8", "separable", "cols_fwd", 2): (201.729280e6 + 21.671936e6,
-                                                          "profiles/kt_cols_2d_1024_m16_b8.md"),
-    ("2d_1024x1024_m16_b8", "separable", "cols_adj", 2): (101.006848e6 + 89.132800e6,
-                                                          "profiles/kt_cols_2d_1024_m16_b8.md"),
+    ("2d_1024x1024_m16_b8", "separable", "cols_fwd", 2, 8): (201.729280e6 + 21.671936e6,
+                                                             "profiles/kt_cols_2d_1024_m16_b8.md"),
+    ("2d_1024x1024_m16_b8", "separable", "cols_adj", 2, 8): (101.006848e6 + 89.132800e6,
+                                                             "profiles/kt_cols_2d_1024_m16_b8.md"),
+    ("2d_512x512_m16_b16", "separable", "cols_fwd", 2, 16): (84.358400e6 + 4.101632e6,
+                                                            "profiles/kt_cols_2d_512_m16_b16.md"),
+    ("2d_512x512_m16_b16", "separable", "cols_adj", 2, 16): (33.777408e6 + 18.606336e6,
+                                                            "profiles/kt_cols_2d_512_m16_b16.md"),
 }
 
 # ------------------------------------------------------------- algorithmic work
@@ -815,7 +819,7 @@ def gpu_arm(args, pr: synth.Problem, ctx: Ctx, oracle_cache: dict, headline: boo
     roof = None
     if dom:
         d = kernels[dom]
-        traffic = MEASURED_TRAFFIC.get((pr.name, kind, dom, col_variant)) if (nb == 8 and not args.lowp) else None
+        traffic = MEASURED_TRAFFIC.get((pr.name, kind, dom, col_variant, nb)) if not args.lowp else None
         roof = {"kernel": dom, "bound": "alu", "achieved": d["tflops"], "peak": fp32_peak,
                 "unit": "TFLOP/s", "frac": d["tflops"] / fp32_peak if d["tflops"] else None,
                 "peak_source": ctx.peak_source(sm_max),
