@@ -1,7 +1,7 @@
 """Failure detection without a GPU fault: a bounded wait that runs out.
 
-The one-warp column kernels (columns of length 1024, whole-grid and
-sectioned) wait on an mbarrier for a bulk copy of a spectrum column.  With the copies suppressed
+The one-warp column kernels (columns of length 1024 and 512, whole-grid,
+separable and sectioned) wait on an mbarrier for a bulk copy of a spectrum column.  With the copies suppressed
 (pce_plan_inject_wait_timeout), every wait gives up after a short bounded
 time, the kernels skip the dependent work, and the plan's status word turns
 the event into PCE_ERR_TIMEOUT on the host.  Nothing hangs and the context
@@ -16,11 +16,13 @@ from oracle import expansion as E
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("kind", ["whole_grid", "sectioned", "separable_tmem", "separable_tmem_pruned"])
+@pytest.mark.parametrize("kind", ["whole_grid", "sectioned", "separable_tmem", "separable_tmem_pruned",
+                                  "whole_grid_512", "separable_tmem_512"])
 def test_bounded_wait_times_out_and_recovers(kind):
     """The whole-grid column kernels, the sectioned column kernel
     (PCE_FLAG_SECTIONED, whose spectrum columns also arrive by bulk copy) and
-    the separable column kernels with tensor-memory state (column variants 2 and 3)."""
+    the separable column kernels with tensor-memory state (column variants 2 and 3),
+    at 1024 and 512 rows."""
     import torch
     from paper_1604_04374_gb300 import Plan, PceError, build, pce
     build.build()
@@ -29,10 +31,11 @@ def test_bounded_wait_times_out_and_recovers(kind):
     pruned = kind == "separable_tmem_pruned"
     m = 16 if (sectioned or pruned) else 4
     grid = (4, 4) if m == 16 else (2, 2)
-    pr = synth.problem_2d(1024, 64, m, 1, 41, "normal", grid)
+    ny = 512 if kind.endswith("_512") else 1024
+    pr = synth.problem_2d(ny, 64, m, 1, 41, "normal", grid)
     dev = torch.device("cuda", 0)
     if kind.startswith("separable_tmem"):
-        wy, wx = synth.hat_factors_2d(1024, 64, *grid)
+        wy, wx = synth.hat_factors_2d(ny, 64, *grid)
         plan = Plan(wy=torch.from_numpy(wy).to(dev), wx=torch.from_numpy(wx).to(dev),
                     h=torch.from_numpy(pr.h).to(dev))
         plan.set_tuning(0, 3 if pruned else 2, 0)
