@@ -454,7 +454,7 @@ pce_status pce_schedule_lpt(const double* cost, int n, int lanes, int* lane_of, 
  *     Stockham rows without prefetch (3 CTAs per SM), 2 = variant 1 with the
  *     forward's windowed R2C run by row pairs (each pair's rows loaded once
  *     for all the terms or slots whose box holds them) and, for rows of 1024
- *     points, the plain row transforms (the adjoint's input R2C and the
+ *     or 512 points, the plain row transforms (the adjoint's input R2C and the
  *     forward's output C2R) by one warp per row pair;
  *   - right-hand sides per launch: powers of two up to the plan's scratch
  *     chunk (2D plans and 1D plans above 8192 points).

@@ -53,12 +53,12 @@ cudaError_t launch_rows_adj(int nx, dim3 grid, cudaStream_t s, const float2* Q, 
                             float scale, const float2* tw, const float2* tw1024, int rv = 0, int kmin = 0,
                             int kmax = 1 << 30, int accumulate = 0);
 
-// One-warp plain row transforms for Nx = 1024 (wrows.cuh): the same results
+// One-warp plain row transforms for Nx = 1024 or 512 (wrows.cuh): the same results
 // and layouts as launch_rows_r2c without a window (row pairs of every row) and
 // launch_rows_c2r; one warp per row pair, grids derived from nrows.
-cudaError_t launch_wrows_r2c(int nb, cudaStream_t s, const float* src, long long src_bstride, int nrows,
+cudaError_t launch_wrows_r2c(int nx, int nb, cudaStream_t s, const float* src, long long src_bstride, int nrows,
                              float2* dst, long long dst_bstride, const float2* tw1024);
-cudaError_t launch_wrows_c2r(int nb, cudaStream_t s, const float2* src, long long src_bstride, int nrows, float* dst,
+cudaError_t launch_wrows_c2r(int nx, int nb, cudaStream_t s, const float2* src, long long src_bstride, int nrows, float* dst,
                              long long dst_bstride, float scale, const float2* tw1024);
 
 cudaError_t launch_cols_fwd(int ny, dim3 grid, cudaStream_t s, const float2* Z, long long z_bstride,

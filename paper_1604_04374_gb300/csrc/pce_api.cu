@@ -514,8 +514,9 @@ pce_status make_twiddles_l1(pce_plan* p, cudaStream_t s) {
 pce_status make_twiddles(pce_plan* p, cudaStream_t s) {
     if (p->l1) return make_twiddles_l1(p, s);
     // the one-warp FFTs index the 1024-point four-step table: transforms of
-    // 1024, columns of 2048 (two warps per column) and of 512 (rows 2p of it)
-    if (p->nx == 1024 || (p->ndims == 2 && (p->ny == 512 || p->ny == 1024 || p->ny == 2048))) {
+    // 1024, columns of 2048 (two warps per column), rows and columns of 512
+    // (rows 2p of it)
+    if (p->nx == 1024 || (p->ndims == 2 && (p->nx == 512 || p->ny == 512 || p->ny == 1024 || p->ny == 2048))) {
         pce_status st0 = dev_alloc(&p->tw1024, 1024);
         if (st0) return st0;
         k_twiddles_1024<<<4, 256, 0, s>>>(p->tw1024);
@@ -1604,8 +1605,9 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
     const long long zb = scr.zstride;
     const long long ab = scr.astride;
     // row variant 2: the plain row transforms by the one-warp row kernels (rows of
-    // 1024 points), the windowed passes by the block kernels without prefetch
-    const bool wrows = rowv == 2 && nx == 1024 && p->tw1024 != nullptr;
+    // 1024 or 512 points), the forward windowed pass by row pairs, the adjoint
+    // rows by the block kernels without prefetch
+    const bool wrows = rowv == 2 && (nx == 1024 || nx == 512) && p->tw1024 != nullptr;
     const int brv = rowv == 0 ? 0 : 1;
     const int fpc = pce::rows_pairs_per_cta(nx);
     const int cpc = pce::cols_columns_per_cta(ny);  // same for both variants
@@ -1637,13 +1639,13 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
             }
             if (e == cudaSuccess)
                 e = timed(p, PCE_KERNEL_ROWS_C2R, s, [&] {
-                    if (wrows) return pce::launch_wrows_c2r(nb, s, scr.A, ab, ny, dst, P, scale, p->tw1024);
+                    if (wrows) return pce::launch_wrows_c2r(nx, nb, s, scr.A, ab, ny, dst, P, scale, p->tw1024);
                     return pce::launch_rows_c2r(nx, dim3((npairs + fpc - 1) / fpc, nb), s, scr.A, ab,
                                                 ny, dst, P, scale, p->twx, p->tw1024);
                 });
         } else if (slotwise) {
             e = timed(p, PCE_KERNEL_ROWS_R2C, s, [&] {
-                if (wrows) return pce::launch_wrows_r2c(nb, s, src, P, ny, scr.A, ab, p->tw1024);
+                if (wrows) return pce::launch_wrows_r2c(nx, nb, s, src, P, ny, scr.A, ab, p->tw1024);
                 return pce::launch_rows_r2c(nx, false, dim3(r2c_blocks(npairs, nx), nb), s, src, P,
                                             ny, nullptr, false, nullptr, nullptr, npairs, scr.A, ab, 0,
                                             p->twx, p->tw1024);
@@ -1689,13 +1691,13 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
                 });
             if (e == cudaSuccess)
                 e = timed(p, PCE_KERNEL_ROWS_C2R, s, [&] {
-                    if (wrows) return pce::launch_wrows_c2r(nb, s, scr.A, ab, ny, dst, P, scale, p->tw1024);
+                    if (wrows) return pce::launch_wrows_c2r(nx, nb, s, scr.A, ab, ny, dst, P, scale, p->tw1024);
                     return pce::launch_rows_c2r(nx, dim3((npairs + fpc - 1) / fpc, nb), s, scr.A, ab,
                                                 ny, dst, P, scale, p->twx, p->tw1024);
                 });
         } else if (sepx) {
             e = timed(p, PCE_KERNEL_ROWS_R2C, s, [&] {
-                if (wrows) return pce::launch_wrows_r2c(nb, s, src, P, ny, scr.A, ab, p->tw1024);
+                if (wrows) return pce::launch_wrows_r2c(nx, nb, s, src, P, ny, scr.A, ab, p->tw1024);
                 return pce::launch_rows_r2c(nx, false, dim3(r2c_blocks(npairs, nx), nb), s, src, P,
                                             ny, nullptr, false, nullptr, nullptr, npairs, scr.A, ab, 0,
                                             p->twx, p->tw1024);
@@ -1734,13 +1736,13 @@ pce_status apply_impl(pce_plan_t p, const float* in, float* out, int64_t batch, 
                 });
             if (e == cudaSuccess)
                 e = timed(p, PCE_KERNEL_ROWS_C2R, s, [&] {
-                    if (wrows) return pce::launch_wrows_c2r(nb, s, scr.A, ab, ny, dst, P, scale, p->tw1024);
+                    if (wrows) return pce::launch_wrows_c2r(nx, nb, s, scr.A, ab, ny, dst, P, scale, p->tw1024);
                     return pce::launch_rows_c2r(nx, dim3((npairs + fpc - 1) / fpc, nb), s, scr.A, ab,
                                                 ny, dst, P, scale, p->twx, p->tw1024);
                 });
         } else {
             e = timed(p, PCE_KERNEL_ROWS_R2C, s, [&] {
-                if (wrows) return pce::launch_wrows_r2c(nb, s, src, P, ny, scr.A, ab, p->tw1024);
+                if (wrows) return pce::launch_wrows_r2c(nx, nb, s, src, P, ny, scr.A, ab, p->tw1024);
                 return pce::launch_rows_r2c(nx, false, dim3(r2c_blocks(npairs, nx), nb), s, src, P,
                                             ny, nullptr, false, nullptr, nullptr, npairs, scr.A, ab, 0,
                                             p->twx, p->tw1024);

@@ -122,21 +122,32 @@ cudaError_t launch_rows_adj(int nx, dim3 grid, cudaStream_t s, const float2* Q, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_wrows_r2c(int nb, cudaStream_t s, const float* src, long long src_bstride, int nrows,
+cudaError_t launch_wrows_r2c(int nx, int nb, cudaStream_t s, const float* src, long long src_bstride, int nrows,
                              float2* dst, long long dst_bstride, const float2* tw1024) {
     if (!tw1024) return cudaErrorInvalidValue;
     const int npairs = (nrows + 1) / 2;
-    kw_rows_r2c<<<dim3((npairs + kWRowWarps - 1) / kWRowWarps, nb), kWRowWarps * 32, 0, s>>>(
-        src, src_bstride, nrows, dst, dst_bstride, tw1024);
+    const dim3 grid((npairs + kWRowWarps - 1) / kWRowWarps, nb);
+    if (nx == kWarpN)
+        kw_rows_r2c<kWarpN><<<grid, kWRowWarps * 32, 0, s>>>(src, src_bstride, nrows, dst, dst_bstride, tw1024);
+    else if (nx == 512)
+        kw_rows_r2c<512><<<grid, kWRowWarps * 32, 0, s>>>(src, src_bstride, nrows, dst, dst_bstride, tw1024);
+    else
+        return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 
-cudaError_t launch_wrows_c2r(int nb, cudaStream_t s, const float2* src, long long src_bstride, int nrows, float* dst,
-                             long long dst_bstride, float scale, const float2* tw1024) {
+cudaError_t launch_wrows_c2r(int nx, int nb, cudaStream_t s, const float2* src, long long src_bstride, int nrows,
+                             float* dst, long long dst_bstride, float scale, const float2* tw1024) {
     if (!tw1024) return cudaErrorInvalidValue;
     const int npairs = (nrows + 1) / 2;
-    kw_rows_c2r<<<dim3((npairs + kWRowWarps - 1) / kWRowWarps, nb), kWRowWarps * 32, 0, s>>>(
-        src, src_bstride, nrows, dst, dst_bstride, scale, tw1024);
+    const dim3 grid((npairs + kWRowWarps - 1) / kWRowWarps, nb);
+    if (nx == kWarpN)
+        kw_rows_c2r<kWarpN><<<grid, kWRowWarps * 32, 0, s>>>(src, src_bstride, nrows, dst, dst_bstride, scale,
+                                                              tw1024);
+    else if (nx == 512)
+        kw_rows_c2r<512><<<grid, kWRowWarps * 32, 0, s>>>(src, src_bstride, nrows, dst, dst_bstride, scale, tw1024);
+    else
+        return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 

@@ -1,6 +1,6 @@
 """GPU: plans with tensor-product windows w_k = wy_k (x) wx_k (pce_plan_create_separable).
 
-For Ny = 1024 (FP32 storage) the applies take the separable fast path (one
+For Ny = 1024 or 512 (FP32 storage) the applies take the separable fast path (one
 row-transform slot per distinct column factor); its outputs are checked
 against the FP64 oracle on the dense windows outer(wy_k, wx_k), and against
 the general path of pce_plan_create on the same dense windows.  Other sizes
@@ -360,10 +360,11 @@ def test_tuning_cache_round_trip_of_the_tensor_memory_variant(torch_cuda, tmp_pa
     p2.close()
 
 
-@pytest.mark.parametrize("case", ["separable_hats", "dense_hats", "dense_ragged", "rows_2048"])
+@pytest.mark.parametrize("case", ["separable_hats", "dense_hats", "dense_ragged", "rows_2048",
+                                  "separable_hats_512", "dense_ragged_512"])
 def test_one_warp_row_kernels_match_oracle(torch_cuda, case):
-    """Row variant 2 (the plain row transforms by one-warp kernels for rows of 1024
-    points, the windowed passes by the block kernels) against the FP64 oracle, forward
+    """Row variant 2 (the plain row transforms by one-warp kernels for rows of 1024 or
+    512 points, the forward windowed pass by row pairs) against the FP64 oracle, forward
     and adjoint, with separable and dense plans, windows whose column boxes wrap the
     seam or are ragged, an odd batch, and 2048-row plans; equal to the block row
     kernels (variant 1) up to rounding."""
@@ -373,15 +374,20 @@ def test_one_warp_row_kernels_match_oracle(torch_cuda, case):
     if case == "separable_hats":
         wy, wx, w, h, u = sep_problem(1024, 1024, 4, 4, 3, 96, random_h=True)
         plan = Plan(wy=dev(torch, wy), wx=dev(torch, wx), h=dev(torch, h))
+    elif case == "separable_hats_512":
+        wy, wx, w, h, u = sep_problem(512, 512, 4, 4, 3, 94, random_h=True)
+        plan = Plan(wy=dev(torch, wy), wx=dev(torch, wx), h=dev(torch, h))
     elif case == "dense_hats":
         pr = synth.problem_2d(128, 1024, 8, 3, 97, "normal")
         w, h, u = pr.w, pr.h, pr.u
         plan = Plan(dev(torch, w), h=dev(torch, h))
-    elif case == "dense_ragged":
+    elif case in ("dense_ragged", "dense_ragged_512"):
         # random windows on boxes of odd sizes, one wrapping both axes
-        ny, nx, m = 64, 1024, 3
+        ny, nx, m = 64, (1024 if case == "dense_ragged" else 512), 3
         w = np.zeros((m, ny, nx), dtype=np.float32)
-        for k, (r0, nr, c0, nc) in enumerate([(5, 17, 1000, 77), (40, 31, 3, 511), (60, 9, 700, 1)]):
+        boxes = [(5, 17, 1000, 77), (40, 31, 3, 511), (60, 9, 700, 1)] if nx == 1024 else \
+            [(5, 17, 480, 77), (40, 31, 3, 255), (60, 9, 300, 1)]
+        for k, (r0, nr, c0, nc) in enumerate(boxes):
             rr = (r0 + np.arange(nr)) % ny
             cc = (c0 + np.arange(nc)) % nx
             w[k][np.ix_(rr, cc)] = rng.uniform(0.2, 1.0, (nr, nc)).astype(np.float32)
